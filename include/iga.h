@@ -1,0 +1,233 @@
+/*
+ * libiga -- low-rank isogeometric assembly, Kronecker/TT operator apply and
+ * block-AMEn KKT solve on one GB300 (sm_103a).
+ *
+ * Method: Buenger, Dolgov, Stoll, "A low-rank tensor method for
+ * PDE-constrained optimization with isogeometric analysis".
+ *
+ * Conventions shared by every entry point
+ *   - All calls are asynchronous on the stream given to iga_create() unless
+ *     stated otherwise; calls that return host values synchronise that stream.
+ *   - "device" pointers are CUDA global-memory addresses owned by the caller
+ *     and only borrowed for the duration of the call; "host" pointers are
+ *     plain host memory, also borrowed.
+ *   - Handles (iga_ctx, iga_op, iga_tt) are owned by the library and freed
+ *     by the matching destroy call.
+ *   - Errors are returned as iga_status; iga_last_error() gives a text.
+ *     No call aborts the process or traps on the GPU.
+ *   - Tensors over the tensor-product index (i1, i2, i3) are stored in C
+ *     order (i3 fastest).  Operators act on the Dirichlet-reduced space:
+ *     the first and last basis function of every direction are omitted
+ *     (Sec. 4, discrete quadratic problem).
+ *   - Banded univariate matrices are stored row-major as band[i][o] with
+ *     A(i, i + o - p), o = 0..2p, entries outside the matrix are zero.
+ */
+#ifndef IGA_H
+#define IGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IGA_OK = 0,
+  IGA_EINVAL = 1,      /* invalid argument (sizes, knots, null pointers) */
+  IGA_ENOMEM = 2,      /* device or host allocation failed */
+  IGA_ECUDA = 3,       /* CUDA runtime / cuBLAS error */
+  IGA_ENOCONV = 4,     /* iteration limit reached before the tolerance */
+  IGA_ENONFINITE = 5,  /* NaN or Inf detected in a reduction */
+  IGA_ETIMEOUT = 6     /* a bounded device wait gave up */
+} iga_status;
+
+typedef enum { IGA_FP64 = 0, IGA_FP32 = 1, IGA_TF32 = 2 } iga_prec;
+
+enum { IGA_GEO_NURBS = 0, IGA_GEO_NURBS_TWIST = 1 };
+enum { IGA_TARGET_ZERO = 0, IGA_TARGET_SINPROD = 1, IGA_TARGET_GAUSS = 2 };
+
+typedef struct iga_ctx iga_ctx;
+typedef struct iga_op iga_op;
+typedef struct iga_tt iga_tt;
+
+/* Geometry map G = C : B(xhat) (Sec. 2, eq. geometryMapping), rational when
+ * the weights differ (NURBS curve definition of Sec. 2).  kind
+ * IGA_GEO_NURBS_TWIST composes G with a rotation by twist * z about e_z. */
+typedef struct {
+  int kind;
+  int degree[3];
+  int nknots[3];
+  const double* knots[3];   /* host; open knot vectors (eq. knotVector) */
+  int nctrl[3];             /* nctrl[d] = nknots[d] - degree[d] - 1 */
+  const double* ctrl_hw;    /* host; [i1][i2][i3][4] = (w x, w y, w z, w) */
+  double twist;             /* radians per unit z */
+} iga_geometry;
+
+/* Trial/test B-spline space (Sec. 2, tensor-product spline space) and the
+ * Gauss rule used for every integral: nquad points per element and
+ * direction. */
+typedef struct {
+  int degree[3];
+  int nknots[3];
+  const double* knots[3];   /* host; open knot vectors */
+  int nquad;                /* 1..16 */
+} iga_space;
+
+/* Desired state yhat of the control problem (Sec. 1 / Sec. 4):
+ * SINPROD: prod_k sin(pi x_k);  GAUSS: exp(-|x - c|^2 / params[3]),
+ * c = params[0..2]. */
+typedef struct {
+  int kind;
+  double params[4];
+} iga_target;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context bound to the CUDA stream `stream` (a cudaStream_t, may
+ * be NULL for the legacy default stream) on the current device. */
+iga_status iga_create(iga_ctx** ctx, void* stream);
+void iga_destroy(iga_ctx* ctx);
+const char* iga_last_error(const iga_ctx* ctx);
+/* Number of kernels this context has launched so far (all entry points). */
+uint64_t iga_launch_count(const iga_ctx* ctx);
+/* Device bytes currently held by the context's scratch pool. */
+size_t iga_scratch_bytes(const iga_ctx* ctx);
+
+/* ---- (a1, a2) geometry sampling ------------------------------------- */
+
+/* Sample the geometry weights on the tensor Gauss grid of `space`
+ * (Sec. 2: omega = |det grad G|, Q = (J^T J)^{-1} omega, J = dG/dxhat;
+ * Sec. 3 eq. weightEquationSystem samples omega on a point grid).
+ * Every sample is multiplied by the tensor Gauss weight g1 g2 g3.
+ * out: device, 8 consecutive tensors of shape (Q1, Q2, Q3), Q_d = E_d * nquad:
+ *   [0] omega g, [1] q11 g, [2] q12 g, [3] q13 g, [4] q22 g, [5] q23 g,
+ *   [6] q33 g, [7] yhat(G) omega g.
+ * Fails with IGA_EINVAL on invalid knots or a non-positive Jacobian
+ * determinant (detected on the device, reported after the call). */
+iga_status iga_sample_weights(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                              const iga_target* target, double* out);
+
+/* ---- (a3) TT-SVD ------------------------------------------------------ */
+
+/* TT decomposition of a device tensor W of shape (n1, n2, n3) (Sec. 3,
+ * eq. tt and the TT-SVD named after eq. weightEquationSolve): truncation of
+ * each unfolding at tol * ref / sqrt(2), ref = norm_ref if > 0 else ||W||_F;
+ * ranks are capped at rmax.  A tensor with ||W||_F <= tol * ref gives a
+ * rank-0 TT (*out = NULL, IGA_OK).  FP64 throughout.  Synchronises. */
+iga_status iga_tt_svd(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol,
+                      double norm_ref, int rmax, iga_tt** out);
+/* n[3] and ranks r[2] of a TT; core d copied to host buffer `core`
+ * (shape (r_{d-1}, n_d, r_d), C order).  Synchronises. */
+iga_status iga_tt_info(const iga_tt* tt, int n[3], int r[2]);
+iga_status iga_tt_core(iga_ctx* ctx, const iga_tt* tt, int d, double* core);
+/* Expand to a full device tensor (n1, n2, n3), FP64. */
+iga_status iga_tt_full(iga_ctx* ctx, const iga_tt* tt, double* out);
+void iga_tt_destroy(iga_tt* tt);
+
+/* ---- (a4) batched univariate assembly ------------------------------- */
+
+/* Univariate weighted Gauss-quadrature matrices of one direction d
+ * (Sec. 3, eqs. massMatrix1D and the stiffness factors K_kl^(d)):
+ *   band[t][i][o] = sum_{e,q} w[t][e*nquad+q] phi_i(x_eq) psi_j(x_eq),
+ *   j = i + o - p, phi = B or B' (deriv_row), psi = B or B' (deriv_col).
+ * w: device (T, E*nquad); band: device (T, nrow, 2p+1) with nrow = n
+ * (interior = 0) or n - 2 (interior = 1: Dirichlet rows and columns
+ * omitted). */
+iga_status iga_assemble_bands(iga_ctx* ctx, const iga_space* space, int d, const double* w,
+                              int T, int deriv_row, int deriv_col, int interior, double* band);
+
+/* ---- composite assembly (a1..a4) ------------------------------------ */
+
+/* Low-rank assembly of the Dirichlet-reduced mass and stiffness operators
+ * and of the load vector b_i = int yhat(G) beta_i omega (Sec. 3 eqs.
+ * massFinal / stiffnessFinal with the TT cores of eq. TTranks as the
+ * Kronecker terms).  Q entries are truncated relative to the norm of all of
+ * Q.  Outputs are library-owned; *load is NULL for a zero target. */
+iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                                const iga_target* target, double tol, iga_op** M, iga_op** K,
+                                iga_tt** load);
+
+/* Operator structure: interior sizes n[3], degrees p[3], number of blocks
+ * (one per TT weight term group), summed TT-matrix ranks R[2] and device
+ * bytes of its factors. */
+iga_status iga_op_info(const iga_op* op, int n[3], int p[3], int* nblocks, int R[2],
+                       size_t* bytes);
+/* Ranks (R1, R2) of block k. */
+iga_status iga_op_block(const iga_op* op, int k, int R[2]);
+/* Copy the bands of direction d of block k to host: d=0: (R1, n1, 2p+1),
+ * d=1: (R1, R2, n2, 2p+1), d=2: (R2, n3, 2p+1).  Synchronises. */
+iga_status iga_op_bands(iga_ctx* ctx, const iga_op* op, int k, int d, double* host);
+void iga_op_destroy(iga_op* op);
+
+/* ---- (a5) Kronecker-sum apply --------------------------------------- */
+
+/* y = alpha * A x + beta * y with A = sum_blocks sum_{r1,r2}
+ * A1[r1] (x) A2[r1,r2] (x) A3[r2] (Sec. 5, eqs. M_kron / K_kron; kron
+ * ordering kron(A1, kron(A2, A3)) on C-ordered x).  x, y: device, length
+ * n1 n2 n3, double (IGA_FP64) or float (IGA_FP32); x and y must not
+ * overlap. */
+iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
+                          double beta, void* y, iga_prec prec);
+
+/* out = KKT z for the stationary KKT matrix (Sec. 4 eq. KKTSystem with one
+ * time step and tau = 1):  [[M, 0, K^T], [0, beta M, -M], [K, -M, 0]].
+ * z, out: device, 3N (y, u, lambda stacked), precision as above. */
+iga_status iga_kkt_apply(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                         const void* z, void* out, iga_prec prec);
+
+/* ---- (c) block-AMEn local-system matvec ----------------------------- */
+
+/* Projected operator apply at one TT core (Sec. 5, eq. KKT_red, assembled
+ * factor by factor):
+ *   y(a,i,b) = sum_{al,be} PhiL[al](a,a') A[al][be](i,i') PhiR[be](b,b') x(a',i',b')
+ * PhiL: device (R0, r0, r0); bands: device (R0, R1, n, 2p+1) banded A;
+ * PhiR: device (R1, r1, r1); x, y: device (nvec, r0, n, r1) for nvec
+ * independent vectors.  Precision: IGA_FP64 (double in/out) or IGA_FP32
+ * (float in/out, FP32 arithmetic).  bandmask (host, R0*R1 bytes, may be
+ * NULL) marks which (al, be) bands are nonzero. */
+iga_status iga_amen_local_matvec(iga_ctx* ctx, int r0, int n, int r1, int R0, int R1, int p,
+                                 const void* PhiL, const void* bands, const void* PhiR,
+                                 const unsigned char* bandmask, int nvec, const void* x, void* y,
+                                 iga_prec prec);
+
+/* ---- KKT solve (a6..a8) ---------------------------------------------- */
+
+typedef struct {
+  double tol;          /* stop when ||rhs - KKT z||_2 / ||rhs||_2 <= tol */
+  double inner_tol;    /* AMEn truncation / local tolerance per correction */
+  int max_sweeps;      /* AMEn sweeps per correction */
+  int kick_rank;       /* AMEn enrichment rank */
+  int rmax;            /* TT rank cap */
+  int local_maxit;     /* Krylov iterations per local system */
+  int refine_max;      /* outer FP64 refinement steps */
+  int precision;       /* IGA_FP64 or IGA_FP32 for the AMEn contractions */
+  int verbose;         /* print one line per sweep to stderr */
+} iga_solve_opts;
+
+typedef struct {
+  int sweeps;          /* AMEn sweeps over all corrections */
+  int refinements;     /* FP64 refinement steps taken */
+  int max_rank;        /* largest TT rank of the solution components */
+  int local_iters;     /* Krylov iterations over all local solves */
+  double residual;     /* final ||rhs - KKT z|| / ||rhs|| in FP64 */
+  double seconds;      /* wall time of the solve */
+} iga_solve_info;
+
+/* Fill opts with defaults. */
+void iga_solve_opts_default(iga_solve_opts* opts);
+
+/* Solve the stationary KKT system with rhs = [b; 0; 0], b the load vector
+ * (TT), by block AMEn (Sec. 5: block TT eq. btt, SVD moves eqs. svd1/svd2,
+ * reduced KKT eq. KKT_red) inside FP64 iterative refinement of the full
+ * residual.  y, u, lam: device FP64 vectors of length N (full format).
+ * Returns IGA_ENOCONV (with the best iterate written) when the tolerance
+ * is not reached. */
+iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K, const iga_tt* load,
+                              double beta, const iga_solve_opts* opts, double* y, double* u,
+                              double* lam, iga_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGA_H */

@@ -1,0 +1,413 @@
+// C ABI of libiga: context, handles and the composite low-rank assembly.
+//
+// iga_lowrank_assemble follows Sec. 3: sample omega, Q (and the load
+// density) on the tensor Gauss grid, TT-SVD each sample tensor (eq. tt), and
+// assemble one banded univariate matrix per TT core slice (eqs.
+// massMatrix1D, stiffnessFinal), so that M = sum (x)_d M_d and
+// K = sum_{k,l} sum (x)_d K_kl^(d) with the core slices of eq. TTranks.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+void set_error(iga_ctx* ctx, const std::string& m) {
+  if (ctx) ctx->err = m;
+}
+
+void sample_weights_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+                         const iga_target* target, double* out);
+
+// (r0, Q, r1) core -> (r0 * r1, Q) slices
+__global__ void core_to_slices_kernel(const double* __restrict__ c, int r0, int Q, int r1,
+                                      double* __restrict__ s) {
+  size_t total = (size_t)r0 * Q * r1;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int b = (int)(i % r1);
+  size_t t = i / r1;
+  int q = (int)(t % Q);
+  int a = (int)(t / Q);
+  s[((size_t)a * r1 + b) * Q + q] = c[i];
+}
+
+// (r0 * r1, n) slices -> (r0, n, r1) core
+__global__ void slices_to_core_kernel(const double* __restrict__ s, int r0, int n, int r1,
+                                      double* __restrict__ c) {
+  size_t total = (size_t)r0 * n * r1;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int b = (int)(i % r1);
+  size_t t = i / r1;
+  int j = (int)(t % n);
+  int a = (int)(t / n);
+  c[i] = s[((size_t)a * r1 + b) * n + j];
+}
+
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+static void core_slices(iga_ctx* ctx, const double* core, int r0, int Q, int r1, double* out) {
+  size_t total = (size_t)r0 * Q * r1;
+  IGA_LAUNCH(ctx, core_to_slices_kernel, (unsigned)((total + 255) / 256), 256, 0, core, r0, Q, r1,
+             out);
+}
+
+// Append one block (the operator term of a TT weight with given derivative
+// pattern) to the band lists of an operator under construction.
+struct OpBuilder {
+  std::vector<OpBlock> blocks;
+  std::vector<std::vector<double>> host;    // unused: bands stay on the device
+  std::vector<DevBuf<double>> parts[3];
+  size_t count[3] = {0, 0, 0};
+};
+
+static void add_block(iga_ctx* ctx, const SpaceTables& st, const iga_tt* tt, const int deriv[3][2],
+                      OpBuilder& B) {
+  OpBlock blk;
+  blk.R1 = tt->r[0];
+  blk.R2 = tt->r[1];
+  int rl[4] = {1, tt->r[0], tt->r[1], 1};
+  for (int d = 0; d < 3; ++d) {
+    const DirTables& T = st.dir[d];
+    int Q = T.E * T.q;
+    int nT = rl[d] * rl[d + 1];
+    double* sl = scratch<double>(ctx, SLOT_ASM_W, (size_t)nT * Q);
+    core_slices(ctx, tt->core[d].p, rl[d], Q, rl[d + 1], sl);
+    DevBuf<double> band((size_t)nT * (T.n - 2) * (2 * T.p + 1));
+    launch_assemble_bands(ctx, T, sl, nT, deriv[d][0], deriv[d][1], 1, band.p);
+    blk.off[d] = B.count[d];
+    blk.deriv[d][0] = deriv[d][0];
+    blk.deriv[d][1] = deriv[d][1];
+    B.count[d] += nT;
+    B.parts[d].push_back(std::move(band));
+    // the slice buffer is reused by the next launch on the same stream: no sync needed
+  }
+  B.blocks.push_back(blk);
+}
+
+static iga_op* finish_op(iga_ctx* ctx, const SpaceTables& st, OpBuilder& B) {
+  auto* op = new iga_op();
+  try {
+    for (int d = 0; d < 3; ++d) {
+      op->n[d] = st.dir[d].n - 2;
+      op->p[d] = st.dir[d].p;
+      size_t len = (size_t)op->n[d] * (2 * op->p[d] + 1);
+      op->nbands[d] = B.count[d];
+      op->band64[d].alloc(std::max<size_t>(1, B.count[d] * len));
+      op->band32[d].alloc(std::max<size_t>(1, B.count[d] * len));
+      size_t off = 0;
+      for (auto& part : B.parts[d]) {
+        IGA_CUDA(cudaMemcpyAsync(op->band64[d].p + off, part.p, part.n * 8,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+        off += part.n;
+      }
+      size_t n = B.count[d] * len;
+      if (n)
+        IGA_LAUNCH(ctx, to_float_kernel, (unsigned)((n + 255) / 256), 256, 0, op->band64[d].p,
+                   op->band32[d].p, n);
+    }
+    op->blocks = B.blocks;
+    op->rank1 = true;
+    for (auto& b : op->blocks) op->rank1 = op->rank1 && b.R1 == 1 && b.R2 == 1;
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  } catch (...) {
+    delete op;
+    throw;
+  }
+  return op;
+}
+
+static iga_tt* load_tt(iga_ctx* ctx, const SpaceTables& st, const iga_tt* f) {
+  auto* tt = new iga_tt();
+  try {
+    int rl[4] = {1, f->r[0], f->r[1], 1};
+    tt->r[0] = f->r[0];
+    tt->r[1] = f->r[1];
+    for (int d = 0; d < 3; ++d) {
+      const DirTables& T = st.dir[d];
+      int Q = T.E * T.q;
+      int nT = rl[d] * rl[d + 1];
+      int ni = T.n - 2;
+      tt->n[d] = ni;
+      double* sl = scratch<double>(ctx, SLOT_ASM_W, (size_t)nT * Q);
+      core_slices(ctx, f->core[d].p, rl[d], Q, rl[d + 1], sl);
+      double* vec = scratch<double>(ctx, SLOT_MISC0, (size_t)nT * ni);
+      launch_load_vectors(ctx, T, sl, nT, 1, vec);
+      tt->core[d].alloc((size_t)nT * ni);
+      size_t total = (size_t)nT * ni;
+      IGA_LAUNCH(ctx, slices_to_core_kernel, (unsigned)((total + 255) / 256), 256, 0, vec, rl[d],
+                 ni, rl[d + 1], tt->core[d].p);
+    }
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  } catch (...) {
+    delete tt;
+    throw;
+  }
+  return tt;
+}
+
+static void kkt_apply_impl(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                           const void* z, void* out, iga_prec prec) {
+  IGA_REQUIRE(M && K && z && out, "kkt_apply: null argument");
+  for (int d = 0; d < 3; ++d) IGA_REQUIRE(M->n[d] == K->n[d], "kkt_apply: M and K sizes differ");
+  size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
+  size_t es = prec == IGA_FP64 ? 8 : 4;
+  const char* zc = static_cast<const char*>(z);
+  char* oc = static_cast<char*>(out);
+  const void* y = zc;
+  const void* u = zc + N * es;
+  const void* l = zc + 2 * N * es;
+  void* o1 = oc;
+  void* o2 = oc + N * es;
+  void* o3 = oc + 2 * N * es;
+  // K is symmetric by construction (the (k,l) and (l,k) blocks share the
+  // weight q_kl = q_lk and have transposed factors), so K^T = K.
+  kron_apply_impl(ctx, M, 1.0, y, 0.0, o1, prec);
+  kron_apply_impl(ctx, K, 1.0, l, 1.0, o1, prec);
+  kron_apply_impl(ctx, M, beta, u, 0.0, o2, prec);
+  kron_apply_impl(ctx, M, -1.0, l, 1.0, o2, prec);
+  kron_apply_impl(ctx, K, 1.0, y, 0.0, o3, prec);
+  kron_apply_impl(ctx, M, -1.0, u, 1.0, o3, prec);
+}
+
+void kkt_apply_internal(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                        const void* z, void* out, iga_prec prec) {
+  kkt_apply_impl(ctx, M, K, beta, z, out, prec);
+}
+
+}  // namespace iga
+
+using namespace iga;
+
+#define IGA_TRY(ctx, ...)                                                         \
+  try {                                                                           \
+    __VA_ARGS__;                                                                  \
+    return IGA_OK;                                                                \
+  } catch (const ::iga::Error& e) {                                               \
+    set_error(ctx, e.what());                                                     \
+    return e.status;                                                              \
+  } catch (const std::bad_alloc&) {                                               \
+    set_error(ctx, "host allocation failed");                                     \
+    return IGA_ENOMEM;                                                            \
+  } catch (const std::exception& e) {                                             \
+    set_error(ctx, e.what());                                                     \
+    return IGA_ECUDA;                                                             \
+  }
+
+extern "C" {
+
+iga_status iga_create(iga_ctx** out, void* stream) {
+  if (!out) return IGA_EINVAL;
+  *out = nullptr;
+  iga_ctx* ctx = nullptr;
+  try {
+    ctx = new iga_ctx();
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    IGA_CUDA(cudaGetDevice(&ctx->device));
+    IGA_BLAS(cublasCreate(&ctx->blas));
+    IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
+    IGA_CUDA(cudaMalloc((void**)&ctx->dflag, 64 * sizeof(int)));
+    IGA_CUDA(cudaMallocHost((void**)&ctx->hflag, 64 * sizeof(int)));
+    *out = ctx;
+    return IGA_OK;
+  } catch (const ::iga::Error& e) {
+    if (ctx) iga_destroy(ctx);
+    return e.status;
+  } catch (...) {
+    if (ctx) iga_destroy(ctx);
+    return IGA_ENOMEM;
+  }
+}
+
+void iga_destroy(iga_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->scratch.clear();
+  if (ctx->blas) cublasDestroy(ctx->blas);
+  if (ctx->dflag) cudaFree(ctx->dflag);
+  if (ctx->hflag) cudaFreeHost(ctx->hflag);
+  delete ctx;
+}
+
+const char* iga_last_error(const iga_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t iga_launch_count(const iga_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+size_t iga_scratch_bytes(const iga_ctx* ctx) { return ctx ? ctx->scratch_bytes() : 0; }
+
+iga_status iga_sample_weights(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                              const iga_target* target, double* out) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    SpaceTables st;
+    build_space_tables(ctx, space, st);
+    sample_weights_impl(ctx, geo, st, target, out);
+  })
+}
+
+iga_status iga_tt_svd(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol,
+                      double norm_ref, int rmax, iga_tt** out) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, tt_svd3(ctx, W, n1, n2, n3, tol, norm_ref, rmax, out))
+}
+
+iga_status iga_tt_info(const iga_tt* tt, int n[3], int r[2]) {
+  if (!tt) return IGA_EINVAL;
+  for (int d = 0; d < 3; ++d) if (n) n[d] = tt->n[d];
+  if (r) { r[0] = tt->r[0]; r[1] = tt->r[1]; }
+  return IGA_OK;
+}
+
+iga_status iga_tt_core(iga_ctx* ctx, const iga_tt* tt, int d, double* core) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(tt && core && d >= 0 && d < 3, "tt_core: bad argument");
+    IGA_CUDA(cudaMemcpyAsync(core, tt->core[d].p, tt->core[d].n * 8, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  })
+}
+
+iga_status iga_tt_full(iga_ctx* ctx, const iga_tt* tt, double* out) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, tt_full_impl(ctx, tt, out))
+}
+
+void iga_tt_destroy(iga_tt* tt) { delete tt; }
+
+iga_status iga_assemble_bands(iga_ctx* ctx, const iga_space* space, int d, const double* w, int T,
+                              int deriv_row, int deriv_col, int interior, double* band) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(d >= 0 && d < 3 && w && band && T >= 0, "assemble_bands: bad argument");
+    IGA_REQUIRE(interior == 0 || interior == 1, "assemble_bands: interior must be 0 or 1");
+    SpaceTables st;
+    build_space_tables(ctx, space, st);
+    launch_assemble_bands(ctx, st.dir[d], w, T, deriv_row != 0, deriv_col != 0, interior, band);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  })
+}
+
+iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                                const iga_target* target, double tol, iga_op** M, iga_op** K,
+                                iga_tt** load) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(M && K, "lowrank_assemble: null output");
+    IGA_REQUIRE(tol >= 0.0, "lowrank_assemble: negative tolerance");
+    *M = nullptr;
+    *K = nullptr;
+    if (load) *load = nullptr;
+    SpaceTables st;
+    build_space_tables(ctx, space, st);
+    int Q[3];
+    for (int d = 0; d < 3; ++d) Q[d] = st.dir[d].E * st.dir[d].q;
+    size_t S = (size_t)Q[0] * Q[1] * Q[2];
+    double* samples = scratch<double>(ctx, SLOT_ASM_SAMPLES, 8 * S);
+    sample_weights_impl(ctx, geo, st, target, samples);
+    // norms: omega, each q entry (off-diagonals count twice in ||Q||_F), load
+    double qn2 = 0.0;
+    for (int c = 1; c <= 6; ++c) {
+      double v = device_norm2(ctx, samples + c * S, S);
+      qn2 += (c == 2 || c == 3 || c == 5) ? 2 * v * v : v * v;
+    }
+    double qnorm = std::sqrt(qn2);
+    iga_tt* tts[8] = {nullptr};
+    struct Guard {
+      iga_tt** t;
+      ~Guard() { for (int i = 0; i < 8; ++i) delete t[i]; }
+    } guard{tts};
+    tt_svd3(ctx, samples, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[0]);
+    for (int c = 1; c <= 6; ++c) tt_svd3(ctx, samples + c * S, Q[0], Q[1], Q[2], tol, qnorm, 0, &tts[c]);
+    if (target && target->kind != IGA_TARGET_ZERO)
+      tt_svd3(ctx, samples + 7 * S, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[7]);
+    IGA_REQUIRE(tts[0] != nullptr, "lowrank_assemble: omega is zero");
+    OpBuilder bm, bk;
+    int dm[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    add_block(ctx, st, tts[0], dm, bm);
+    // q index of the (k,l) entry in the sample layout: 11 12 13 22 23 33
+    const int qidx[3][3] = {{1, 2, 3}, {2, 4, 5}, {3, 5, 6}};
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        const iga_tt* t = tts[qidx[k][l]];
+        if (!t) continue;
+        int dk[3][2];
+        for (int d = 0; d < 3; ++d) {
+          dk[d][0] = (l == d);      // delta(l,d) on the row (test) function
+          dk[d][1] = (k == d);      // delta(k,d) on the column (trial) function
+        }
+        add_block(ctx, st, t, dk, bk);
+      }
+    iga_op* m = finish_op(ctx, st, bm);
+    iga_op* kk = nullptr;
+    try {
+      kk = finish_op(ctx, st, bk);
+      if (load && tts[7]) *load = load_tt(ctx, st, tts[7]);
+    } catch (...) {
+      delete m;
+      delete kk;
+      throw;
+    }
+    *M = m;
+    *K = kk;
+  })
+}
+
+iga_status iga_op_info(const iga_op* op, int n[3], int p[3], int* nblocks, int R[2],
+                       size_t* bytes) {
+  if (!op) return IGA_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (n) n[d] = op->n[d];
+    if (p) p[d] = op->p[d];
+  }
+  if (nblocks) *nblocks = (int)op->blocks.size();
+  if (R) {
+    R[0] = 0;
+    R[1] = 0;
+    for (auto& b : op->blocks) { R[0] += b.R1; R[1] += b.R2; }
+  }
+  if (bytes) *bytes = op->bytes();
+  return IGA_OK;
+}
+
+iga_status iga_op_block(const iga_op* op, int k, int R[2]) {
+  if (!op || k < 0 || k >= (int)op->blocks.size() || !R) return IGA_EINVAL;
+  R[0] = op->blocks[k].R1;
+  R[1] = op->blocks[k].R2;
+  return IGA_OK;
+}
+
+iga_status iga_op_bands(iga_ctx* ctx, const iga_op* op, int k, int d, double* host) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(op && host && d >= 0 && d < 3 && k >= 0 && k < (int)op->blocks.size(),
+                "op_bands: bad argument");
+    const OpBlock& b = op->blocks[k];
+    size_t cnt = d == 0 ? b.R1 : (d == 1 ? (size_t)b.R1 * b.R2 : b.R2);
+    size_t len = (size_t)op->n[d] * (2 * op->p[d] + 1);
+    IGA_CUDA(cudaMemcpyAsync(host, op->band64[d].p + b.off[d] * len, cnt * len * 8,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  })
+}
+
+void iga_op_destroy(iga_op* op) { delete op; }
+
+iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
+                          double beta, void* y, iga_prec prec) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, kron_apply_impl(ctx, A, alpha, x, beta, y, prec))
+}
+
+iga_status iga_kkt_apply(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                         const void* z, void* out, iga_prec prec) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, kkt_apply_impl(ctx, M, K, beta, z, out, prec))
+}
+
+}  // extern "C"

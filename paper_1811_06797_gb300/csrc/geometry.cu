@@ -1,0 +1,373 @@
+// Geometry sampling (steps a1, a2): Gauss rule, B-spline tables, and the
+// per-point NURBS Jacobian, omega = |det J| and Q = (J^T J)^{-1} omega.
+//
+// Sec. 2 (knot vectors, Cox-de Boor recursion, NURBS map G = C : B),
+// Sec. 2 after eq. stiffness (omega and Q), Sec. 3 eq. weightEquationSystem
+// (the weights are sampled on a tensor point grid).
+#include <algorithm>
+#include <cmath>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+constexpr int MAXP = 8;
+
+void check_knots(const double* k, int nk, int p, const char* what) {
+  IGA_REQUIRE(k != nullptr, std::string(what) + ": null knot vector");
+  IGA_REQUIRE(p >= 0 && p <= MAXP, std::string(what) + ": degree must be in 0..8");
+  int n = nk - p - 1;
+  IGA_REQUIRE(n >= p + 1, std::string(what) + ": too few knots for the degree");
+  for (int i = 0; i + 1 < nk; ++i)
+    IGA_REQUIRE(k[i] <= k[i + 1], std::string(what) + ": knots must be nondecreasing");
+  for (int i = 0; i <= p; ++i)
+    IGA_REQUIRE(k[i] == 0.0 && k[nk - 1 - i] == 1.0,
+                std::string(what) + ": end knots must be 0 and 1 with multiplicity p+1");
+  int run = 1;
+  for (int i = p + 1; i < n; ++i) {
+    run = (k[i] == k[i - 1]) ? run + 1 : 1;
+    IGA_REQUIRE(k[i] > 0.0 && k[i] < 1.0, std::string(what) + ": interior knot outside (0,1)");
+    IGA_REQUIRE(run <= p, std::string(what) + ": interior knot multiplicity exceeds degree");
+  }
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_q.
+static void gauss_rule(int q, std::vector<double>& t, std::vector<double>& w) {
+  t.resize(q);
+  w.resize(q);
+  for (int k = 0; k < q; ++k) {
+    double x = std::cos(M_PI * (k + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int j = 2; j <= q; ++j) {
+        double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (q == 1) { p1 = x; p0 = 1.0; }
+      dp = q * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = x;
+      for (int j = 2; j <= q; ++j) {
+        double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (q == 1) { p1 = x; p0 = 1.0; }
+      dp = q * (x * p1 - p0) / (x * x - 1.0);
+    }
+    t[q - 1 - k] = x;          // ascending order
+    w[q - 1 - k] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+// span index mu with k[mu] <= x < k[mu+1] (the last nonempty span for x = 1)
+__device__ __forceinline__ int find_span(const double* k, int nk, int p, double x) {
+  int n = nk - p - 1;
+  if (x >= k[n]) {
+    int mu = n - 1;
+    while (mu > p && k[mu] == k[mu + 1]) --mu;
+    return mu;
+  }
+  int lo = p, hi = n;           // k[lo] <= x < k[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (x < k[mid]) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+// The p+1 B-splines beta_{mu-p..mu} of degree p that are nonzero at x, and
+// their first derivatives, by the Cox-de Boor recursion restricted to the
+// nonzero functions (beta_{i,0} = 1 on span mu; degree j from degree j-1).
+__device__ void local_basis(const double* k, int mu, int p, double x, double* N, double* dN) {
+  double B[MAXP + 2], Bp[MAXP + 2];
+  B[0] = 1.0;                       // degree 0: only beta_mu
+  for (int a = 0; a <= p; ++a) Bp[a] = 0.0;
+  if (p == 0) Bp[0] = 0.0;
+  for (int j = 1; j <= p; ++j) {
+    if (j == p)
+      for (int a = 0; a < j; ++a) Bp[a] = B[a];   // degree p-1 values, i = mu-p+1+a
+    double nb[MAXP + 2];
+    for (int a = 0; a <= j; ++a) {
+      int i = mu - j + a;
+      double v = 0.0;
+      if (a - 1 >= 0) {               // beta_{i, j-1} (old index a-1)
+        double d1 = k[i + j] - k[i];
+        if (d1 > 0.0) v += (x - k[i]) / d1 * B[a - 1];
+      }
+      if (a <= j - 1) {               // beta_{i+1, j-1} (old index a)
+        double d2 = k[i + j + 1] - k[i + 1];
+        if (d2 > 0.0) v += (k[i + j + 1] - x) / d2 * B[a];
+      }
+      nb[a] = v;
+    }
+    for (int a = 0; a <= j; ++a) B[a] = nb[a];
+  }
+  for (int a = 0; a <= p; ++a) N[a] = B[a];
+  if (p == 0) { dN[0] = 0.0; return; }
+  // beta'_{i,p} = p [beta_{i,p-1} / (k_{i+p} - k_i) - beta_{i+1,p-1} / (k_{i+p+1} - k_{i+1})]
+  for (int a = 0; a <= p; ++a) {
+    int i = mu - p + a;
+    double v = 0.0;
+    if (a - 1 >= 0) {
+      double d1 = k[i + p] - k[i];
+      if (d1 > 0.0) v += Bp[a - 1] / d1;
+    }
+    if (a <= p - 1) {
+      double d2 = k[i + p + 1] - k[i + 1];
+      if (d2 > 0.0) v -= Bp[a] / d2;
+    }
+    dN[a] = p * v;
+  }
+}
+
+// Basis tables at a list of points: span[pt], V[pt][a], D[pt][a], a = 0..p.
+__global__ void basis_table_kernel(const double* __restrict__ knots, int nk, int p,
+                                   const double* __restrict__ x, int npts, int* __restrict__ span,
+                                   double* __restrict__ V, double* __restrict__ D) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npts) return;
+  double xx = x[t];
+  int mu = find_span(knots, nk, p, xx);
+  double N[MAXP + 1], dN[MAXP + 1];
+  local_basis(knots, mu, p, xx, N, dN);
+  if (span) span[t] = mu;
+  for (int a = 0; a <= p; ++a) {
+    V[t * (p + 1) + a] = N[a];
+    D[t * (p + 1) + a] = dN[a];
+  }
+}
+
+static void basis_tables(iga_ctx* ctx, const std::vector<double>& knots, int p,
+                         const double* dx, int npts, int* dspan, double* dV, double* dD) {
+  DevBuf<double> dk(knots.size());
+  IGA_CUDA(cudaMemcpyAsync(dk.p, knots.data(), knots.size() * 8, cudaMemcpyHostToDevice,
+                           ctx->stream));
+  int threads = 128;
+  IGA_LAUNCH(ctx, basis_table_kernel, (npts + threads - 1) / threads, threads, 0, dk.p,
+             (int)knots.size(), p, dx, npts, dspan, dV, dD);
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));   // dk is released on return
+}
+
+void build_space_tables(iga_ctx* ctx, const iga_space* sp, SpaceTables& st) {
+  IGA_REQUIRE(sp != nullptr, "null space");
+  IGA_REQUIRE(sp->nquad >= 1 && sp->nquad <= 16, "nquad must be in 1..16");
+  st.nquad = sp->nquad;
+  std::vector<double> t, w;
+  gauss_rule(sp->nquad, t, w);
+  for (int d = 0; d < 3; ++d) {
+    DirTables& T = st.dir[d];
+    int p = sp->degree[d];
+    check_knots(sp->knots[d], sp->nknots[d], p, "space");
+    T.p = p;
+    T.q = sp->nquad;
+    T.knots.assign(sp->knots[d], sp->knots[d] + sp->nknots[d]);
+    T.n = sp->nknots[d] - p - 1;
+    IGA_REQUIRE(T.n >= 3, "space needs at least 3 basis functions per direction");
+    // elements = nonempty spans; first nonzero basis function on each
+    std::vector<double> u;
+    for (double v : T.knots) if (u.empty() || v > u.back()) u.push_back(v);
+    T.E = (int)u.size() - 1;
+    T.first.resize(T.E);
+    T.xq.resize((size_t)T.E * T.q);
+    T.gq.resize((size_t)T.E * T.q);
+    for (int e = 0; e < T.E; ++e) {
+      double a = u[e], b = u[e + 1];
+      int mu = (int)(std::upper_bound(T.knots.begin(), T.knots.end(), a) - T.knots.begin()) - 1;
+      T.first[e] = mu - p;
+      for (int j = 0; j < T.q; ++j) {
+        T.xq[(size_t)e * T.q + j] = 0.5 * (a + b) + 0.5 * (b - a) * t[j];
+        T.gq[(size_t)e * T.q + j] = 0.5 * (b - a) * w[j];
+      }
+    }
+    T.elo.assign(T.n, T.E);
+    T.ehi.assign(T.n, -1);
+    for (int e = 0; e < T.E; ++e)
+      for (int a = 0; a <= p; ++a) {
+        int i = T.first[e] + a;
+        T.elo[i] = std::min(T.elo[i], e);
+        T.ehi[i] = std::max(T.ehi[i], e);
+      }
+    int npts = T.E * T.q;
+    T.dx.alloc(npts);
+    T.dV.alloc((size_t)npts * (p + 1));
+    T.dD.alloc((size_t)npts * (p + 1));
+    T.dfirst.alloc(T.E);
+    T.delo.alloc(T.n);
+    T.dehi.alloc(T.n);
+    IGA_CUDA(cudaMemcpyAsync(T.dx.p, T.xq.data(), npts * 8, cudaMemcpyHostToDevice, ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(T.dfirst.p, T.first.data(), T.E * 4, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(T.delo.p, T.elo.data(), T.n * 4, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(T.dehi.p, T.ehi.data(), T.n * 4, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    basis_tables(ctx, T.knots, p, T.dx.p, npts, nullptr, T.dV.p, T.dD.p);
+  }
+}
+
+struct GeoDev {
+  const double* V[3];
+  const double* D[3];
+  const int* span[3];
+  const double* g[3];
+  int pg[3];
+  int nc[3];
+  int Q[3];
+  const double* ctrl;
+  int kind;
+  double twist;
+  int tkind;
+  double tp[4];
+};
+
+// One thread per tensor Gauss point: geometry map and derivatives from the
+// nonzero control points, quotient rule for the rational map, optional
+// twist, then omega, Q and the load density, all times g1 g2 g3.
+__global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* __restrict__ flag) {
+  size_t Q12 = (size_t)G.Q[1] * G.Q[2];
+  size_t total = (size_t)G.Q[0] * Q12;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int i1 = (int)(t / Q12);
+  int rem = (int)(t - (size_t)i1 * Q12);
+  int i2 = rem / G.Q[2];
+  int i3 = rem - i2 * G.Q[2];
+  const int p1 = G.pg[0], p2 = G.pg[1], p3 = G.pg[2];
+  const double* V1 = G.V[0] + (size_t)i1 * (p1 + 1);
+  const double* D1 = G.D[0] + (size_t)i1 * (p1 + 1);
+  const double* V2 = G.V[1] + (size_t)i2 * (p2 + 1);
+  const double* D2 = G.D[1] + (size_t)i2 * (p2 + 1);
+  const double* V3 = G.V[2] + (size_t)i3 * (p3 + 1);
+  const double* D3 = G.D[2] + (size_t)i3 * (p3 + 1);
+  int s1 = G.span[0][i1] - p1, s2 = G.span[1][i2] - p2, s3 = G.span[2][i3] - p3;
+  double A[4] = {0, 0, 0, 0}, dA[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int a = 0; a <= p1; ++a) {
+    for (int b = 0; b <= p2; ++b) {
+      double vv = V1[a] * V2[b], dv = D1[a] * V2[b], vd = V1[a] * D2[b];
+      const double* C = G.ctrl + (((size_t)(s1 + a) * G.nc[1] + (s2 + b)) * G.nc[2] + s3) * 4;
+      for (int c = 0; c <= p3; ++c) {
+        double w0 = vv * V3[c], w1 = dv * V3[c], w2 = vd * V3[c], w3 = vv * D3[c];
+        for (int m = 0; m < 4; ++m) {
+          double cm = __ldg(C + c * 4 + m);
+          A[m] += w0 * cm;
+          dA[0][m] += w1 * cm;
+          dA[1][m] += w2 * cm;
+          dA[2][m] += w3 * cm;
+        }
+      }
+    }
+  }
+  double iw = 1.0 / A[3];
+  double X[3] = {A[0] * iw, A[1] * iw, A[2] * iw};
+  double J[3][3];                                    // J[a][k] = dG_a / dxhat_k
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) J[a][k] = (dA[k][a] - X[a] * dA[k][3]) * iw;
+  if (G.kind == IGA_GEO_NURBS_TWIST) {
+    double th = G.twist * X[2];
+    double c = cos(th), s = sin(th);
+    double x = X[0], y = X[1];
+    double J0[3], J1[3];
+    for (int k = 0; k < 3; ++k) {
+      J0[k] = c * J[0][k] - s * J[1][k] + G.twist * (-s * x - c * y) * J[2][k];
+      J1[k] = s * J[0][k] + c * J[1][k] + G.twist * (c * x - s * y) * J[2][k];
+    }
+    for (int k = 0; k < 3; ++k) { J[0][k] = J0[k]; J[1][k] = J1[k]; }
+    X[0] = c * x - s * y;
+    X[1] = s * x + c * y;
+  }
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  if (!(det != 0.0) || !isfinite(det)) atomicOr(flag, 1);
+  double adet = fabs(det);
+  // metric m = J^T J; Q = adj(m) / det(m) * |det J| = adj(m) / |det J|
+  double m[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) m[k][l] = J[0][k] * J[0][l] + J[1][k] * J[1][l] + J[2][k] * J[2][l];
+  double inv = 1.0 / adet;
+  double q11 = (m[1][1] * m[2][2] - m[1][2] * m[2][1]) * inv;
+  double q12 = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) * inv;
+  double q13 = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) * inv;
+  double q22 = (m[0][0] * m[2][2] - m[0][2] * m[2][0]) * inv;
+  double q23 = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) * inv;
+  double q33 = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) * inv;
+  double yh = 0.0;
+  if (G.tkind == IGA_TARGET_SINPROD) {
+    yh = sin(M_PI * X[0]) * sin(M_PI * X[1]) * sin(M_PI * X[2]);
+  } else if (G.tkind == IGA_TARGET_GAUSS) {
+    double dx = X[0] - G.tp[0], dy = X[1] - G.tp[1], dz = X[2] - G.tp[2];
+    yh = exp(-(dx * dx + dy * dy + dz * dz) / G.tp[3]);
+  }
+  double g = G.g[0][i1] * G.g[1][i2] * G.g[2][i3];
+  out[t] = adet * g;
+  out[total + t] = q11 * g;
+  out[2 * total + t] = q12 * g;
+  out[3 * total + t] = q13 * g;
+  out[4 * total + t] = q22 * g;
+  out[5 * total + t] = q23 * g;
+  out[6 * total + t] = q33 * g;
+  out[7 * total + t] = yh * adet * g;
+}
+
+void sample_weights_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+                         const iga_target* target, double* out) {
+  IGA_REQUIRE(geo != nullptr && out != nullptr, "null geometry or output");
+  IGA_REQUIRE(geo->kind == IGA_GEO_NURBS || geo->kind == IGA_GEO_NURBS_TWIST,
+              "unknown geometry kind");
+  IGA_REQUIRE(geo->ctrl_hw != nullptr, "null control net");
+  GeoDev G{};
+  std::vector<DevBuf<double>> keep;
+  DevBuf<double> gV[3], gD[3], gw[3];
+  DevBuf<int> gspan[3];
+  size_t nctrl = 1;
+  for (int d = 0; d < 3; ++d) {
+    check_knots(geo->knots[d], geo->nknots[d], geo->degree[d], "geometry");
+    IGA_REQUIRE(geo->nctrl[d] == geo->nknots[d] - geo->degree[d] - 1,
+                "geometry: nctrl must equal nknots - degree - 1");
+    nctrl *= geo->nctrl[d];
+    const DirTables& T = st.dir[d];
+    int npts = T.E * T.q;
+    std::vector<double> k(geo->knots[d], geo->knots[d] + geo->nknots[d]);
+    gV[d].alloc((size_t)npts * (geo->degree[d] + 1));
+    gD[d].alloc((size_t)npts * (geo->degree[d] + 1));
+    gspan[d].alloc(npts);
+    gw[d].alloc(npts);
+    IGA_CUDA(cudaMemcpyAsync(gw[d].p, T.gq.data(), npts * 8, cudaMemcpyHostToDevice, ctx->stream));
+    basis_tables(ctx, k, geo->degree[d], T.dx.p, npts, gspan[d].p, gV[d].p, gD[d].p);
+    G.V[d] = gV[d].p;
+    G.D[d] = gD[d].p;
+    G.span[d] = gspan[d].p;
+    G.g[d] = gw[d].p;
+    G.pg[d] = geo->degree[d];
+    G.nc[d] = geo->nctrl[d];
+    G.Q[d] = npts;
+  }
+  DevBuf<double> ctrl(nctrl * 4);
+  IGA_CUDA(cudaMemcpyAsync(ctrl.p, geo->ctrl_hw, nctrl * 4 * 8, cudaMemcpyHostToDevice,
+                           ctx->stream));
+  G.ctrl = ctrl.p;
+  G.kind = geo->kind;
+  G.twist = geo->twist;
+  G.tkind = target ? target->kind : IGA_TARGET_ZERO;
+  IGA_REQUIRE(G.tkind >= 0 && G.tkind <= 2, "unknown target kind");
+  for (int i = 0; i < 4; ++i) G.tp[i] = target ? target->params[i] : 0.0;
+  if (G.tkind == IGA_TARGET_GAUSS) IGA_REQUIRE(G.tp[3] > 0.0, "target width must be > 0");
+  IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
+  size_t total = (size_t)G.Q[0] * G.Q[1] * G.Q[2];
+  int threads = 256;
+  IGA_LAUNCH(ctx, sample_weights_kernel, (unsigned)((total + threads - 1) / threads), threads, 0,
+             G, out, ctx->dflag);
+  IGA_CUDA(cudaMemcpyAsync(ctx->hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  IGA_REQUIRE(*ctx->hflag == 0, "geometry: zero or non-finite Jacobian determinant");
+}
+
+}  // namespace iga

@@ -1,0 +1,209 @@
+// Internal declarations shared by the libiga translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/iga.h"
+
+namespace iga {
+
+// Error carried from the internals to the C ABI boundary (never crosses it).
+struct Error : public std::runtime_error {
+  iga_status status;
+  Error(iga_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define IGA_REQUIRE(cond, msg)                                                   \
+  do {                                                                           \
+    if (!(cond)) throw ::iga::Error(IGA_EINVAL, std::string(msg));               \
+  } while (0)
+
+#define IGA_CUDA(call)                                                           \
+  do {                                                                           \
+    cudaError_t e__ = (call);                                                    \
+    if (e__ != cudaSuccess) {                                                    \
+      if (e__ == cudaErrorMemoryAllocation)                                      \
+        throw ::iga::Error(IGA_ENOMEM, std::string(#call) + ": " +               \
+                                           cudaGetErrorString(e__));             \
+      throw ::iga::Error(IGA_ECUDA, std::string(#call) + ": " +                  \
+                                        cudaGetErrorString(e__));                \
+    }                                                                            \
+  } while (0)
+
+#define IGA_BLAS(call)                                                           \
+  do {                                                                           \
+    cublasStatus_t s__ = (call);                                                 \
+    if (s__ != CUBLAS_STATUS_SUCCESS)                                            \
+      throw ::iga::Error(IGA_ECUDA, std::string(#call) + ": cublas status " +    \
+                                        std::to_string((int)s__));               \
+  } while (0)
+
+// Launch on the context stream, count it, and surface launch errors.
+#define IGA_LAUNCH(ctx, kernel, grid, block, smem, ...)                          \
+  do {                                                                           \
+    kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);             \
+    (ctx)->launches++;                                                           \
+    IGA_CUDA(cudaGetLastError());                                                \
+  } while (0)
+
+// Device buffer owned by RAII (library-internal allocations only).
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t count) { alloc(count); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    IGA_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+    n = count;
+  }
+  void ensure(size_t count) { if (count > n) alloc(count); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DevBuf() { release(); }
+};
+
+// Per-direction quadrature and basis tables of a tensor B-spline space.
+struct DirTables {
+  int p = 0, n = 0, E = 0, q = 0;
+  std::vector<double> knots;          // host copy
+  std::vector<double> xq, gq;         // host: Gauss points / weights, E*q
+  std::vector<int> first;             // host: first nonzero basis index per element
+  std::vector<int> elo, ehi;          // host: element range of each basis function
+  DevBuf<double> dx;                  // device E*q points
+  DevBuf<double> dV, dD;              // device (E, q, p+1) values / derivatives
+  DevBuf<int> dfirst, delo, dehi;     // device copies
+};
+
+struct SpaceTables {
+  DirTables dir[3];
+  int nquad = 0;
+};
+
+// Device-resident Kronecker / TT-matrix operator (Dirichlet-reduced).
+struct OpBlock {
+  int R1 = 1, R2 = 1;
+  size_t off[3] = {0, 0, 0};          // offsets (in bands) into the per-direction arrays
+  int deriv[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+};
+
+}  // namespace iga
+
+struct iga_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  uint64_t launches = 0;
+  cublasHandle_t blas = nullptr;
+  std::vector<iga::DevBuf<char>> scratch;   // reusable scratch slots
+  int* dflag = nullptr;                     // device status flags (zeroed per use)
+  int* hflag = nullptr;                     // pinned host mirror
+  size_t scratch_bytes() const {
+    size_t s = 0;
+    for (auto& b : scratch) s += b.n;
+    return s;
+  }
+};
+
+struct iga_op {
+  int n[3] = {0, 0, 0};               // interior sizes
+  int p[3] = {0, 0, 0};
+  std::vector<iga::OpBlock> blocks;
+  size_t nbands[3] = {0, 0, 0};
+  iga::DevBuf<double> band64[3];      // (nbands[d], n[d], 2p+1)
+  iga::DevBuf<float> band32[3];
+  bool rank1 = true;
+  size_t bytes() const {
+    size_t s = 0;
+    for (int d = 0; d < 3; ++d) s += band64[d].n * 8 + band32[d].n * 4;
+    return s;
+  }
+};
+
+struct iga_tt {
+  int n[3] = {0, 0, 0};
+  int r[2] = {1, 1};
+  iga::DevBuf<double> core[3];        // (r_{d-1}, n_d, r_d), C order
+};
+
+namespace iga {
+
+// scratch slot helper: returns a device pointer with at least `bytes` bytes
+template <typename T>
+T* scratch(iga_ctx* ctx, int slot, size_t count) {
+  if ((int)ctx->scratch.size() <= slot) ctx->scratch.resize(slot + 1);
+  auto& b = ctx->scratch[slot];
+  size_t bytes = count * sizeof(T);
+  if (bytes > b.n) {
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    b.alloc(bytes + (bytes >> 3) + 256);
+  }
+  return reinterpret_cast<T*>(b.p);
+}
+
+// scratch slot numbers (kept apart so nested helpers do not collide)
+enum {
+  SLOT_TTSVD_OMEGA = 0, SLOT_TTSVD_Y, SLOT_TTSVD_Q, SLOT_TTSVD_BT, SLOT_TTSVD_G, SLOT_TTSVD_V,
+  SLOT_TTSVD_W, SLOT_TTSVD_C, SLOT_TTSVD_NORM, SLOT_ASM_W, SLOT_ASM_SAMPLES, SLOT_KRON_Z,
+  SLOT_KRON_Z2, SLOT_LOCAL_T1, SLOT_LOCAL_T2, SLOT_KKT_TMP, SLOT_MISC0, SLOT_MISC1,
+  SLOT_AMEN_BASE = 32
+};
+
+// geometry.cu
+void build_space_tables(iga_ctx* ctx, const iga_space* sp, SpaceTables& t);
+void check_knots(const double* k, int nk, int p, const char* what);
+
+// assembly.cu
+void launch_assemble_bands(iga_ctx* ctx, const DirTables& t, const double* w, int T, int drow,
+                           int dcol, int interior, double* band);
+void launch_load_vectors(iga_ctx* ctx, const DirTables& t, const double* w, int T, int interior,
+                         double* out);
+
+// linalg.cu
+void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, double norm_ref,
+             int rmax, iga_tt** out);
+double device_norm2(iga_ctx* ctx, const double* x, size_t n);   // synchronises
+void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k);  // device, col-major
+void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k);  // Y overwritten
+void fill_gaussian(iga_ctx* ctx, double* x, size_t n, uint64_t seed);
+void transpose_cm(iga_ctx* ctx, const double* A, int rows, int cols, double* B);
+
+// local.cu
+void tt_full_impl(iga_ctx* ctx, const iga_tt* tt, double* out);
+void gemm_rm(iga_ctx* ctx, int M, int N, int K, const double* A, const double* B, double* C,
+             double beta = 0.0);
+template <typename T>
+void local_matvec_t(iga_ctx* ctx, int r0, int n, int r1, int R0, int R1, int p, const T* PhiL,
+                    const T* bands, const T* PhiR, const unsigned char* dmask, int nv, const T* x,
+                    T* y, T* t1, T* t2);
+
+// api.cu
+void kkt_apply_internal(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta, const void* z,
+                        void* out, iga_prec prec);
+
+// kron.cu
+void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
+                     void* y, iga_prec prec);
+
+void set_error(iga_ctx* ctx, const std::string& m);
+
+}  // namespace iga

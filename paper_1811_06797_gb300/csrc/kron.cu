@@ -1,0 +1,292 @@
+// Kronecker-sum operator apply (step a5):
+//   y = alpha * sum_blocks sum_{r1,r2} (A1[r1] (x) A2[r1,r2] (x) A3[r2]) x + beta * y
+// (Sec. 5 eqs. M_kron / K_kron; the univariate factors are banded with
+// half-bandwidth p).
+//
+// Rank-1 blocks (every block of the configurations with exact-rank
+// geometry) go through one fused kernel: a CTA owns an output tile
+// T1 x T2 x T3, computes the mode-3 product on the tile plus its halo in
+// directions 1 and 2 (reading x through L1), then the mode-2 and mode-1
+// products in shared memory, for every term in turn, and writes y once.
+// x is read from HBM once per tile (halo re-reads hit L1/L2) and y written
+// once.  TT-matrix blocks (ranks > 1) use staged single-mode products with
+// full-size intermediates.
+#include <algorithm>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+constexpr int KRON_MAXTERMS = 32;
+constexpr int KRON_THREADS = 256;
+constexpr int KRON_MAXOUT = 32;    // outputs per thread held in registers
+
+template <typename T>
+struct KronTerms {
+  const T* b[3][KRON_MAXTERMS];
+  int nterms;
+};
+
+struct KronTile {
+  int n1, n2, n3;
+  int T1, T2, T3;
+  int nt2, nt3;     // tiles along 2 and 3
+};
+
+template <typename T, int P>
+__global__ void __launch_bounds__(KRON_THREADS)
+kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __restrict__ x,
+                  T* __restrict__ y) {
+  constexpr int B = 2 * P + 1;
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int T1 = g.T1, T2 = g.T2, T3 = g.T3;
+  const int H1 = T1 + 2 * P, H2 = T2 + 2 * P;
+  T* z3 = sm;                                   // H1 * H2 * T3
+  T* z2 = z3 + (size_t)H1 * H2 * T3;            // H1 * T2 * T3
+  T* a1 = z2 + (size_t)H1 * T2 * T3;            // T1 * B
+  T* a2 = a1 + T1 * B;                          // T2 * B
+  T* a3 = a2 + T2 * B;                          // T3 * B
+  int bid = blockIdx.x;
+  int t3 = bid % g.nt3;
+  int t2 = (bid / g.nt3) % g.nt2;
+  int t1 = bid / (g.nt3 * g.nt2);
+  const int I1 = t1 * T1, I2 = t2 * T2, I3 = t3 * T3;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  const int nout = T1 * T2 * T3;
+  T acc[KRON_MAXOUT];
+#pragma unroll
+  for (int k = 0; k < KRON_MAXOUT; ++k) acc[k] = T(0);
+
+  for (int t = 0; t < terms.nterms; ++t) {
+    const T* A1 = terms.b[0][t];
+    const T* A2 = terms.b[1][t];
+    const T* A3 = terms.b[2][t];
+    for (int idx = threadIdx.x; idx < (T1 + T2 + T3) * B; idx += blockDim.x) {
+      int r = idx / B, o = idx - r * B;
+      T v = T(0);
+      if (r < T1) { int i = I1 + r; if (i < n1) v = A1[(size_t)i * B + o]; a1[r * B + o] = v; }
+      else if (r < T1 + T2) { int i = I2 + r - T1; if (i < n2) v = A2[(size_t)i * B + o]; a2[(r - T1) * B + o] = v; }
+      else { int i = I3 + r - T1 - T2; if (i < n3) v = A3[(size_t)i * B + o]; a3[(r - T1 - T2) * B + o] = v; }
+    }
+    __syncthreads();
+    // mode 3 on the (H1 x H2) halo slab of the i3 tile
+    for (int idx = threadIdx.x; idx < H1 * H2 * T3; idx += blockDim.x) {
+      int k = idx % T3;
+      int ac = idx / T3;
+      int c = ac % H2, a = ac / H2;
+      int j1 = I1 + a - P, j2 = I2 + c - P, i3 = I3 + k;
+      T s = T(0);
+      if (j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < n2 && i3 < n3) {
+        const T* xr = x + ((size_t)j1 * n2 + j2) * n3;
+#pragma unroll
+        for (int o = 0; o < B; ++o) {
+          int j3 = i3 + o - P;
+          if (j3 >= 0 && j3 < n3) s += a3[k * B + o] * __ldg(xr + j3);
+        }
+      }
+      z3[idx] = s;
+    }
+    __syncthreads();
+    // mode 2: z2[a][c][k] = sum_o A2(I2+c, I2+c+o-P) z3[a][c+o][k]
+    for (int idx = threadIdx.x; idx < H1 * T2 * T3; idx += blockDim.x) {
+      int k = idx % T3;
+      int ac = idx / T3;
+      int c = ac % T2, a = ac / T2;
+      T s = T(0);
+#pragma unroll
+      for (int o = 0; o < B; ++o) s += a2[c * B + o] * z3[((size_t)a * H2 + c + o) * T3 + k];
+      z2[idx] = s;
+    }
+    __syncthreads();
+    // mode 1 into the register accumulators
+#pragma unroll
+    for (int m = 0; m < KRON_MAXOUT; ++m) {
+      int idx = threadIdx.x + m * KRON_THREADS;
+      if (idx < nout) {
+        int k = idx % T3;
+        int ac = idx / T3;
+        int c = ac % T2, a = ac / T2;
+        T s = T(0);
+#pragma unroll
+        for (int o = 0; o < B; ++o) s += a1[a * B + o] * z2[((size_t)(a + o) * T2 + c) * T3 + k];
+        acc[m] += s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < KRON_MAXOUT; ++m) {
+    int idx = threadIdx.x + m * KRON_THREADS;
+    if (idx < nout) {
+      int k = idx % T3;
+      int ac = idx / T3;
+      int c = ac % T2, a = ac / T2;
+      int i1 = I1 + a, i2 = I2 + c, i3 = I3 + k;
+      if (i1 < n1 && i2 < n2 && i3 < n3) {
+        size_t o = ((size_t)i1 * n2 + i2) * n3 + i3;
+        T v = alpha * acc[m];
+        if (beta != T(0)) v += beta * y[o];
+        y[o] = v;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void scale_kernel(T* __restrict__ y, size_t n, T a) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] *= a;
+}
+
+// single-mode banded product:  y (+)= A (along `mode`) x,  A band (n_mode, 2P+1)
+template <typename T, int P>
+__global__ void mode_product_kernel(const T* __restrict__ A, int mode, int n1, int n2, int n3,
+                                    const T* __restrict__ x, T* __restrict__ y, T alpha,
+                                    int accumulate) {
+  constexpr int B = 2 * P + 1;
+  size_t N = (size_t)n1 * n2 * n3;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  int i3 = (int)(idx % n3);
+  size_t r = idx / n3;
+  int i2 = (int)(r % n2), i1 = (int)(r / n2);
+  int nm = mode == 0 ? n1 : (mode == 1 ? n2 : n3);
+  int im = mode == 0 ? i1 : (mode == 1 ? i2 : i3);
+  size_t stride = mode == 0 ? (size_t)n2 * n3 : (mode == 1 ? (size_t)n3 : 1);
+  const T* row = A + (size_t)im * B;
+  T s = T(0);
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    int j = im + o - P;
+    if (j >= 0 && j < nm) s += row[o] * x[idx + (ptrdiff_t)(j - im) * (ptrdiff_t)stride];
+  }
+  y[idx] = accumulate ? y[idx] + alpha * s : alpha * s;
+}
+
+template <typename T>
+static const T* band_ptr(const iga_op* A, int d, size_t k) {
+  size_t len = (size_t)A->n[d] * (2 * A->p[d] + 1);
+  if constexpr (sizeof(T) == 8) return A->band64[d].p + k * len;
+  else return A->band32[d].p + k * len;
+}
+
+template <typename T, int P>
+static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y) {
+  KronTile g{};
+  g.n1 = A->n[0]; g.n2 = A->n[1]; g.n3 = A->n[2];
+  // tile: full i3 when it fits the per-thread register budget, 8 x 8 in (i1, i2)
+  g.T1 = std::min(8, g.n1);
+  g.T2 = std::min(8, g.n2);
+  constexpr int Bw = 2 * P + 1;
+  int maxT3 = KRON_MAXOUT * KRON_THREADS / (g.T1 * g.T2);
+  {
+    // shared memory: (H1 H2 + H1 T2 + B) T3 + (T1 + T2) B elements of T
+    size_t budget = 220 * 1024 / sizeof(T);
+    size_t per3 = (size_t)(g.T1 + 2 * P) * (g.T2 + 2 * P) + (size_t)(g.T1 + 2 * P) * g.T2 + Bw;
+    int m3 = (int)((budget - (size_t)(g.T1 + g.T2) * Bw) / per3);
+    maxT3 = std::min(maxT3, m3);
+  }
+  int nchunks = (g.n3 + maxT3 - 1) / maxT3;
+  g.T3 = (g.n3 + nchunks - 1) / nchunks;
+  g.nt2 = (g.n2 + g.T2 - 1) / g.T2;
+  g.nt3 = (g.n3 + g.T3 - 1) / g.T3;
+  int nt1 = (g.n1 + g.T1 - 1) / g.T1;
+  constexpr int B = 2 * P + 1;
+  size_t H1 = g.T1 + 2 * P, H2 = g.T2 + 2 * P;
+  size_t smem = (H1 * H2 * g.T3 + H1 * g.T2 * g.T3 + (size_t)(g.T1 + g.T2 + g.T3) * B) * sizeof(T);
+  IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: tile does not fit in shared memory");
+  static bool attr_set = false;
+  if (!attr_set) {
+    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set = true;
+  }
+  // terms in chunks of KRON_MAXTERMS (beta applies to the first chunk only)
+  size_t nterm = A->blocks.size();
+  for (size_t c0 = 0; c0 < nterm || c0 == 0; c0 += KRON_MAXTERMS) {
+    KronTerms<T> terms{};
+    int cnt = 0;
+    for (size_t t = c0; t < std::min(nterm, c0 + KRON_MAXTERMS); ++t, ++cnt)
+      for (int d = 0; d < 3; ++d) terms.b[d][cnt] = band_ptr<T>(A, d, A->blocks[t].off[d]);
+    terms.nterms = cnt;
+    T bt = (c0 == 0) ? beta : T(1);
+    IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P>), (unsigned)(nt1 * g.nt2 * g.nt3), KRON_THREADS, smem,
+               terms, g, alpha, bt, x, y);
+    if (nterm == 0) break;
+  }
+}
+
+template <typename T, int P>
+static void mode_product(iga_ctx* ctx, const T* band, int mode, const int* n, const T* x, T* y,
+                         T alpha, int accumulate) {
+  size_t N = (size_t)n[0] * n[1] * n[2];
+  int threads = 256;
+  IGA_LAUNCH(ctx, (mode_product_kernel<T, P>), (unsigned)((N + threads - 1) / threads), threads, 0,
+             band, mode, n[0], n[1], n[2], x, y, alpha, accumulate);
+}
+
+template <typename T, int P>
+static void kron_general(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y) {
+  const int* n = A->n;
+  size_t N = (size_t)n[0] * n[1] * n[2];
+  // y <- beta y first, then accumulate every block
+  if (beta == T(0)) IGA_CUDA(cudaMemsetAsync(y, 0, N * sizeof(T), ctx->stream));
+  else if (beta != T(1))
+    IGA_LAUNCH(ctx, scale_kernel<T>, (unsigned)((N + 255) / 256), 256, 0, y, N, beta);
+  for (const OpBlock& blk : A->blocks) {
+    if (blk.R1 == 1 && blk.R2 == 1) {
+      T* z3 = scratch<T>(ctx, SLOT_KRON_Z, N);
+      T* z2 = scratch<T>(ctx, SLOT_KRON_Z2, N);
+      mode_product<T, P>(ctx, band_ptr<T>(A, 2, blk.off[2]), 2, n, x, z3, T(1), 0);
+      mode_product<T, P>(ctx, band_ptr<T>(A, 1, blk.off[1]), 1, n, z3, z2, T(1), 0);
+      mode_product<T, P>(ctx, band_ptr<T>(A, 0, blk.off[0]), 0, n, z2, y, alpha, 1);
+      continue;
+    }
+    T* z3 = scratch<T>(ctx, SLOT_KRON_Z, N * blk.R2);
+    T* z2 = scratch<T>(ctx, SLOT_KRON_Z2, N);
+    for (int b = 0; b < blk.R2; ++b)
+      mode_product<T, P>(ctx, band_ptr<T>(A, 2, blk.off[2] + b), 2, n, x, z3 + b * N, T(1), 0);
+    for (int a = 0; a < blk.R1; ++a) {
+      for (int b = 0; b < blk.R2; ++b)
+        mode_product<T, P>(ctx, band_ptr<T>(A, 1, blk.off[1] + (size_t)a * blk.R2 + b), 1, n,
+                           z3 + b * N, z2, T(1), b > 0);
+      mode_product<T, P>(ctx, band_ptr<T>(A, 0, blk.off[0] + a), 0, n, z2, y, alpha, 1);
+    }
+  }
+}
+
+template <typename T>
+static void kron_dispatch(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
+                          void* y) {
+  int P = A->p[0];
+  IGA_REQUIRE(A->p[1] == P && A->p[2] == P, "kron_apply: equal degrees per direction required");
+  const T* xx = static_cast<const T*>(x);
+  T* yy = static_cast<T*>(y);
+  bool fused = A->rank1 && A->blocks.size() <= 64;
+  switch (P) {
+#define IGA_KRON_CASE(PP)                                                                   \
+  case PP:                                                                                  \
+    if (fused) kron_rank1<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy);                        \
+    else kron_general<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy);                            \
+    break;
+    IGA_KRON_CASE(1)
+    IGA_KRON_CASE(2)
+    IGA_KRON_CASE(3)
+    IGA_KRON_CASE(4)
+#undef IGA_KRON_CASE
+    default:
+      throw Error(IGA_EINVAL, "kron_apply: degree must be 1..4");
+  }
+}
+
+void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
+                     void* y, iga_prec prec) {
+  IGA_REQUIRE(A != nullptr && x != nullptr && y != nullptr, "kron_apply: null argument");
+  IGA_REQUIRE(x != y, "kron_apply: x and y must not overlap");
+  if (prec == IGA_FP64) kron_dispatch<double>(ctx, A, alpha, x, beta, y);
+  else if (prec == IGA_FP32) kron_dispatch<float>(ctx, A, alpha, x, beta, y);
+  else throw Error(IGA_EINVAL, "kron_apply: precision must be IGA_FP64 or IGA_FP32");
+}
+
+}  // namespace iga

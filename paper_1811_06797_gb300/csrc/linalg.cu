@@ -1,0 +1,405 @@
+// Small dense FP64 linear algebra on the device and the TT-SVD (step a3).
+//
+// TT-SVD (Sec. 3 after eq. weightEquationSolve; format of eq. tt): the two
+// unfoldings of a 3-way tensor are truncated one after the other at
+// tol * ref / sqrt(D - 1).  Each truncated SVD is computed as
+//   sketch  Y = A Omega (Gaussian Omega, k columns, k doubled until the
+//           smallest sketched singular value is below the threshold),
+//   Householder QR of Y,
+//   B^T = A^T Q and the eigen-decomposition of B B^T by cyclic Jacobi,
+//   taken twice (the second Gram matrix is nearly diagonal, which gives
+//   the small singular values to relative accuracy),
+// and the kept factor is recomputed exactly as U^T A.  Large products go to
+// cuBLAS DGEMM; the QR, Jacobi and helper kernels are below.
+#include <algorithm>
+#include <cmath>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum, result valid in every thread; `red` holds >= 32 doubles
+__device__ double block_sum(double v, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void sumsq_kernel(const double* __restrict__ x, size_t n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double v = x[i];
+    acc += v * v;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+double device_norm2(iga_ctx* ctx, const double* x, size_t n) {
+  double* acc = scratch<double>(ctx, SLOT_TTSVD_NORM, 1);
+  IGA_CUDA(cudaMemsetAsync(acc, 0, 8, ctx->stream));
+  if (n > 0) {
+    int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+    IGA_LAUNCH(ctx, sumsq_kernel, blocks, 256, 0, x, n, acc);
+  }
+  double h = 0.0;
+  IGA_CUDA(cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  return std::sqrt(h);
+}
+
+// counter-based Gaussian numbers: splitmix64 hash -> two uniforms -> Box-Muller
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_kernel(double* __restrict__ x, size_t n, uint64_t seed) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    uint64_t h1 = splitmix64(seed ^ (2 * i)), h2 = splitmix64(seed ^ (2 * i + 1) ^ 0x5bd1e995ull);
+    double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);   // (0, 1]
+    double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);           // [0, 1)
+    x[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+void fill_gaussian(iga_ctx* ctx, double* x, size_t n, uint64_t seed) {
+  if (n == 0) return;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  IGA_LAUNCH(ctx, gaussian_kernel, blocks, 256, 0, x, n, seed);
+}
+
+// B (cols x rows, col-major) = A^T for A (rows x cols, col-major)
+__global__ void transpose_kernel(const double* __restrict__ A, int rows, int cols,
+                                 double* __restrict__ B) {
+  __shared__ double tile[32][33];
+  int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int r = bx + threadIdx.x, c = by + j;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = A[(size_t)c * rows + r];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    int c = by + threadIdx.x, r = bx + j;
+    if (r < rows && c < cols) B[(size_t)r * cols + c] = tile[threadIdx.x][j];
+  }
+}
+
+void transpose_cm(iga_ctx* ctx, const double* A, int rows, int cols, double* B) {
+  if (rows == 0 || cols == 0) return;
+  dim3 grid((rows + 31) / 32, (cols + 31) / 32), block(32, 8);
+  IGA_LAUNCH(ctx, transpose_kernel, grid, block, 0, A, rows, cols, B);
+}
+
+// --------------------------------------------------------- Householder QR
+
+// Y (m x k, col-major) -> Q (m x k) with orthonormal columns spanning Y.
+// One block; warps own columns for the reflector applications.
+__global__ void householder_qr_kernel(double* __restrict__ Y, double* __restrict__ Q, int m,
+                                      int k) {
+  extern __shared__ double sm[];
+  double* vtv = sm;            // k
+  double* red = sm + k;        // 32
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    double* x = Y + (size_t)j * m;
+    double s = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += x[i] * x[i];
+    double nrm2 = block_sum(s, red);
+    double x0 = x[j];
+    double nrm = sqrt(nrm2);
+    double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    double v0 = x0 - alpha;
+    // v = x with v_j = x_j - alpha; v^T v = nrm2 - x0^2 + v0^2
+    double vv = nrm2 - x0 * x0 + v0 * v0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      vtv[j] = (nrm > 0.0 && vv > 0.0) ? vv : 0.0;
+      x[j] = v0;
+    }
+    __syncthreads();
+    double tv = vtv[j];
+    if (tv == 0.0) continue;
+    for (int c = j + 1 + wid; c < k; c += nw) {
+      double* y = Y + (size_t)c * m;
+      double d = 0.0;
+      for (int i = j + lane; i < m; i += 32) d += x[i] * y[i];
+      d = warp_sum(d);
+      double f = 2.0 * d / tv;
+      for (int i = j + lane; i < m; i += 32) y[i] -= f * x[i];
+    }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{k-1} [I; 0], applied from the last reflector
+  for (size_t t = threadIdx.x; t < (size_t)m * k; t += blockDim.x) {
+    int i = (int)(t % m), c = (int)(t / m);
+    Q[t] = (i == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    double tv = vtv[j];
+    if (tv == 0.0) continue;
+    const double* x = Y + (size_t)j * m;
+    for (int c = wid; c < k; c += nw) {
+      double* q = Q + (size_t)c * m;
+      double d = 0.0;
+      for (int i = j + lane; i < m; i += 32) d += x[i] * q[i];
+      d = warp_sum(d);
+      double f = 2.0 * d / tv;
+      for (int i = j + lane; i < m; i += 32) q[i] -= f * x[i];
+    }
+    __syncthreads();
+  }
+}
+
+void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
+  IGA_REQUIRE(k >= 1 && k <= 1024 && m >= k, "householder_qr: bad sizes");
+  size_t smem = (size_t)(k + 32) * sizeof(double);
+  IGA_LAUNCH(ctx, householder_qr_kernel, 1, 1024, smem, Y, Q, m, k);
+}
+
+// ----------------------------------------------------------- Jacobi eigen
+
+// Symmetric A (k x k, col-major) -> eigenvalues w (descending) and
+// eigenvectors V (columns).  Cyclic Jacobi with round-robin parallel
+// ordering: each round applies k/2 disjoint rotations (rows, then columns).
+// At most 40 sweeps; stops when the off-diagonal norm is below 1e-15 times
+// the Frobenius norm.  A is overwritten.
+__global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ Vwork,
+                                  double* __restrict__ Vout, double* __restrict__ w, int k,
+                                  int use_smem) {
+  extern __shared__ double sm[];
+  int kk = k + (k & 1);
+  int npair = kk / 2;
+  double* cs = sm;                 // npair
+  double* sn = sm + npair;         // npair
+  int* pp = (int*)(sm + 2 * npair);
+  int* qq = pp + npair;
+  double* red = sm + 2 * npair + npair + 1;   // 32 doubles, after 2*npair ints (npair+1 dbl)
+  double* A = Ag;
+  double* V = Vwork;
+  if (use_smem) {
+    A = red + 32;
+    V = A + (size_t)k * k;
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) A[t] = Ag[t];
+  }
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) V[t] = ((t % k) == (t / k)) ? 1.0 : 0.0;
+  __syncthreads();
+  double fro2 = 0.0;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) fro2 += A[t] * A[t];
+  fro2 = block_sum(fro2, red);
+  for (int sweep = 0; sweep < 40 && k > 1; ++sweep) {
+    double off2 = 0.0;
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x)
+      if ((t % k) != (t / k)) off2 += A[t] * A[t];
+    off2 = block_sum(off2, red);
+    if (off2 <= 1e-30 * fro2 || off2 == 0.0) break;
+    for (int r = 0; r < kk - 1; ++r) {
+      for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+        int p, q;
+        if (i == 0) { p = kk - 1; q = r; }
+        else { p = (r + i) % (kk - 1); q = (r - i + kk - 1) % (kk - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < k) {
+          double apq = A[(size_t)q * k + p];
+          if (apq != 0.0) {
+            double app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
+            double tau = (aqq - app) / (2.0 * apq);
+            double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                    : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs[i] = c; sn[i] = s; pp[i] = p; qq[i] = q;
+      }
+      __syncthreads();
+      // rows p, q of A:  a_p <- c a_p - s a_q,  a_q <- s a_p + c a_q
+      for (int t = threadIdx.x; t < npair * k; t += blockDim.x) {
+        int i = t / k, col = t % k;
+        int p = pp[i], q = qq[i];
+        if (q >= k || sn[i] == 0.0) continue;
+        double c = cs[i], s = sn[i];
+        double ap = A[(size_t)col * k + p], aq = A[(size_t)col * k + q];
+        A[(size_t)col * k + p] = c * ap - s * aq;
+        A[(size_t)col * k + q] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns p, q of A and V
+      for (int t = threadIdx.x; t < npair * k; t += blockDim.x) {
+        int i = t / k, row = t % k;
+        int p = pp[i], q = qq[i];
+        if (q >= k || sn[i] == 0.0) continue;
+        double c = cs[i], s = sn[i];
+        double ap = A[(size_t)p * k + row], aq = A[(size_t)q * k + row];
+        A[(size_t)p * k + row] = c * ap - s * aq;
+        A[(size_t)q * k + row] = s * ap + c * aq;
+        double vp = V[(size_t)p * k + row], vq = V[(size_t)q * k + row];
+        V[(size_t)p * k + row] = c * vp - s * vq;
+        V[(size_t)q * k + row] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort descending: rank of each eigenvalue, then scatter columns
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double wi = A[(size_t)i * k + i];
+    int rank = 0;
+    for (int j = 0; j < k; ++j) {
+      double wj = A[(size_t)j * k + j];
+      if (wj > wi || (wj == wi && j < i)) ++rank;
+    }
+    w[rank] = wi;
+    for (int row = 0; row < k; ++row) Vout[(size_t)rank * k + row] = V[(size_t)i * k + row];
+  }
+  __syncthreads();
+}
+
+void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k) {
+  IGA_REQUIRE(k >= 1 && k <= 512, "jacobi_eig: k out of range");
+  int kk = k + (k & 1);
+  size_t head = (size_t)(2 * (kk / 2) + (kk / 2) + 1 + 32) * sizeof(double);
+  size_t full = head + 2 * (size_t)k * k * sizeof(double);
+  int use_smem = full <= 200 * 1024;
+  size_t smem = use_smem ? full : head;
+  // without shared memory the rotations accumulate in a global work array and
+  // the sorted eigenvectors are scattered from there into V
+  double* Vw = use_smem ? nullptr : scratch<double>(ctx, SLOT_MISC1, (size_t)k * k);
+  if (smem > 48 * 1024)
+    IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  IGA_LAUNCH(ctx, jacobi_eig_kernel, 1, 512, smem, A, Vw, V, w, k, use_smem);
+}
+
+// ----------------------------------------------------------------- TT-SVD
+
+static void gemm(iga_ctx* ctx, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+                 const double* A, int lda, const double* B, int ldb, double* C, int ldc) {
+  const double one = 1.0, zero = 0.0;
+  IGA_BLAS(cublasDgemm(ctx->blas, ta, tb, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc));
+}
+
+// Truncated left singular factor of A (ns x m): A = X^T with X col-major
+// (m x ns) when xT == false, A = Z with Z col-major (ns x m) when xT == true.
+// Returns the rank r, U (ns x r) col-major in Uout, Ct = A^T U (m x r)
+// col-major in Ctout.  Both outputs are (re)allocated here.
+static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, double delta,
+                     int rmax, DevBuf<double>& Uout, DevBuf<double>& Ctout, uint64_t seed) {
+  int k = std::min(ns, 16);
+  std::vector<double> lam;
+  double* Q = nullptr;
+  double* V = nullptr;
+  int r = 1;
+  for (;;) {
+    double* Om = scratch<double>(ctx, SLOT_TTSVD_OMEGA, (size_t)m * k);
+    double* Y = scratch<double>(ctx, SLOT_TTSVD_Y, (size_t)ns * k);
+    Q = scratch<double>(ctx, SLOT_TTSVD_Q, (size_t)ns * k);
+    double* Bt = scratch<double>(ctx, SLOT_TTSVD_BT, (size_t)m * k * 2);
+    double* Bt2 = Bt + (size_t)m * k;
+    double* G = scratch<double>(ctx, SLOT_TTSVD_G, (size_t)k * k * 2 + k);
+    double* wv = G + (size_t)k * k * 2;
+    V = scratch<double>(ctx, SLOT_TTSVD_V, (size_t)k * k * 3);
+    double* V1 = V + (size_t)k * k;
+    double* V2 = V1 + (size_t)k * k;
+    fill_gaussian(ctx, Om, (size_t)m * k, seed + (uint64_t)k * 7919u);
+    if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, k, m, X, m, Om, m, Y, ns);
+    else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, k, m, X, ns, Om, m, Y, ns);
+    householder_qr(ctx, Y, Q, ns, k);
+    if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, ns, X, m, Q, ns, Bt, m);
+    else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, m, k, ns, X, ns, Q, ns, Bt, m);
+    // first Gram pass
+    gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt, m, Bt, m, G, k);
+    jacobi_eig(ctx, G, V1, wv, k);
+    // second pass on the rotated factor: nearly diagonal Gram matrix
+    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
+    gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
+    jacobi_eig(ctx, G, V2, wv, k);
+    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, V1, k, V2, k, V, k);
+    lam.resize(k);
+    IGA_CUDA(cudaMemcpyAsync(lam.data(), wv, k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    double smin = std::sqrt(std::max(lam[k - 1], 0.0));
+    if (k >= ns || smin <= 0.1 * delta || k >= 256) break;
+    k = std::min(ns, 2 * k);
+  }
+  // smallest r with the tail of the sketched spectrum below delta
+  std::vector<double> tail(k + 1, 0.0);
+  for (int i = k - 1; i >= 0; --i) tail[i] = tail[i + 1] + std::max(lam[i], 0.0);
+  r = k;
+  for (int i = 1; i <= k; ++i)
+    if (std::sqrt(tail[i]) <= delta) { r = i; break; }
+  r = std::max(1, std::min(r, rmax));
+  Uout.alloc((size_t)ns * r);
+  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, r, k, Q, ns, V, k, Uout.p, ns);
+  Ctout.alloc((size_t)m * r);
+  if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, r, ns, X, m, Uout.p, ns, Ctout.p, m);
+  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, m, r, ns, X, ns, Uout.p, ns, Ctout.p, m);
+  return r;
+}
+
+void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, double norm_ref,
+             int rmax, iga_tt** out) {
+  IGA_REQUIRE(W != nullptr && out != nullptr, "tt_svd: null pointer");
+  IGA_REQUIRE(n1 > 0 && n2 > 0 && n3 > 0, "tt_svd: empty tensor");
+  IGA_REQUIRE(tol >= 0.0, "tt_svd: negative tolerance");
+  if (rmax <= 0) rmax = 1 << 30;
+  *out = nullptr;
+  size_t N = (size_t)n1 * n2 * n3;
+  double nrm = device_norm2(ctx, W, N);
+  double ref = norm_ref > 0.0 ? norm_ref : nrm;
+  if (nrm == 0.0 || nrm <= tol * ref) return;            // rank 0
+  double delta = tol * ref / std::sqrt(2.0);
+  IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
+  // first unfolding (n1 x n2 n3): memory is X col-major (n2 n3 x n1)
+  DevBuf<double> U1, C1, U2, C2;
+  int m1 = n2 * n3;
+  IGA_REQUIRE((size_t)n2 * n3 < (1u << 31), "tt_svd: unfolding too large");
+  int r1 = rsvd_left(ctx, W, false, n1, m1, delta, rmax, U1, C1, 0x1811ull);
+  // C1 col-major (m1 x r1) == row-major (r1, n2, n3): second unfolding
+  // (r1 n2 x n3), memory Z col-major (n3 x r1 n2); right factor from A^T = Z
+  int m2 = r1 * n2;
+  int r2 = rsvd_left(ctx, C1.p, true, n3, m2, delta, rmax, U2, C2, 0x0797ull);
+  auto* tt = new iga_tt();
+  tt->n[0] = n1; tt->n[1] = n2; tt->n[2] = n3;
+  tt->r[0] = r1; tt->r[1] = r2;
+  try {
+    tt->core[0].alloc((size_t)n1 * r1);
+    transpose_cm(ctx, U1.p, n1, r1, tt->core[0].p);       // (n1 x r1) cm -> row-major (n1, r1)
+    tt->core[1].alloc((size_t)m2 * r2);
+    transpose_cm(ctx, C2.p, m2, r2, tt->core[1].p);       // (m2 x r2) cm -> row-major (r1,n2,r2)
+    tt->core[2].alloc((size_t)r2 * n3);
+    IGA_CUDA(cudaMemcpyAsync(tt->core[2].p, U2.p, (size_t)r2 * n3 * 8, cudaMemcpyDeviceToDevice,
+                             ctx->stream));               // (n3 x r2) cm == row-major (r2, n3)
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  } catch (...) {
+    delete tt;
+    throw;
+  }
+  *out = tt;
+}
+
+}  // namespace iga

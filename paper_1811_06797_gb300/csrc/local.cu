@@ -1,0 +1,169 @@
+// Block-AMEn local-system matvec (part (c) of the hot path).
+//
+// Sec. 5, eq. KKT_red: with the frame matrix F_{!=d} of eq. frame, every
+// block of the KKT matrix is projected as F^T A F.  For a TT-matrix A with
+// cores A_d[al, be] this projection is assembled factor by factor (Sec. 5,
+// "multiplication of tensor trains factor by factor"):
+//   (F^T A F) x = sum_{al,be} PhiL[al] (x) A_d[al,be] (x) PhiR[be] x,
+// applied in three contractions:
+//   t1[be](a', i', b) = sum_b' PhiR[be](b, b') x(a', i', b')        (dense, r1 x r1)
+//   t2[al](a', i, b)  = sum_be sum_o A_d[al,be](i, i+o-p) t1[be](a', i+o-p, b)  (banded)
+//   y(a, i, b)        = sum_al sum_a' PhiL[al](a, a') t2[al](a', i, b)          (dense, r0 x r0)
+// nvec independent vectors share one set of interfaces.
+#include <algorithm>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+template <typename T>
+__global__ void local_right_kernel(const T* __restrict__ PhiR, const T* __restrict__ x, int R1,
+                                   int nv, int r0, int n, int r1, T* __restrict__ t1) {
+  // t1[be][v][a'][i'][b] = sum_b' PhiR[be][b][b'] x[v][a'][i'][b']
+  size_t per = (size_t)nv * r0 * n * r1;
+  size_t total = (size_t)R1 * per;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int b = (int)(idx % r1);
+  size_t row = (idx % per) / r1;         // (v, a', i')
+  int be = (int)(idx / per);
+  const T* ph = PhiR + ((size_t)be * r1 + b) * r1;
+  const T* xr = x + row * r1;
+  T s = T(0);
+  for (int c = 0; c < r1; ++c) s += ph[c] * xr[c];
+  t1[idx] = s;
+}
+
+template <typename T>
+__global__ void local_band_kernel(const T* __restrict__ bands, const unsigned char* __restrict__ mask,
+                                  const T* __restrict__ t1, int R0, int R1, int nv, int r0, int n,
+                                  int r1, int p, T* __restrict__ t2) {
+  // t2[al][v][a'][i][b] = sum_be sum_o A[al][be][i][o] t1[be][v][a'][i+o-p][b]
+  const int B = 2 * p + 1;
+  size_t per = (size_t)nv * r0 * n * r1;
+  size_t total = (size_t)R0 * per;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int b = (int)(idx % r1);
+  size_t q = idx / r1;
+  int i = (int)(q % n);
+  size_t va = (q / n) % ((size_t)nv * r0);
+  int al = (int)(idx / per);
+  T s = T(0);
+  for (int be = 0; be < R1; ++be) {
+    if (mask && !mask[al * R1 + be]) continue;
+    const T* row = bands + (((size_t)al * R1 + be) * n + i) * B;
+    const T* src = t1 + (size_t)be * per + (va * n) * r1 + b;
+    for (int o = 0; o < B; ++o) {
+      int j = i + o - p;
+      if (j >= 0 && j < n) s += row[o] * src[(size_t)j * r1];
+    }
+  }
+  t2[idx] = s;
+}
+
+template <typename T>
+__global__ void local_left_kernel(const T* __restrict__ PhiL, const T* __restrict__ t2, int R0,
+                                  int nv, int r0, int n, int r1, T* __restrict__ y) {
+  // y[v][a][i][b] = sum_al sum_a' PhiL[al][a][a'] t2[al][v][a'][i][b]
+  size_t per = (size_t)nv * r0 * n * r1;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per) return;
+  size_t ib = idx % ((size_t)n * r1);
+  size_t va = idx / ((size_t)n * r1);
+  int a = (int)(va % r0);
+  size_t v = va / r0;
+  T s = T(0);
+  size_t nr = (size_t)n * r1;
+  for (int al = 0; al < R0; ++al) {
+    const T* ph = PhiL + ((size_t)al * r0 + a) * r0;
+    const T* src = t2 + (size_t)al * per + v * r0 * nr + ib;
+    for (int c = 0; c < r0; ++c) s += ph[c] * src[(size_t)c * nr];
+  }
+  y[idx] = s;
+}
+
+template <typename T>
+void local_matvec_t(iga_ctx* ctx, int r0, int n, int r1, int R0, int R1, int p, const T* PhiL,
+                    const T* bands, const T* PhiR, const unsigned char* dmask, int nv, const T* x,
+                    T* y, T* t1, T* t2) {
+  size_t per = (size_t)nv * r0 * n * r1;
+  if (per == 0) return;
+  int th = 256;
+  IGA_LAUNCH(ctx, local_right_kernel<T>, (unsigned)((R1 * per + th - 1) / th), th, 0, PhiR, x, R1,
+             nv, r0, n, r1, t1);
+  IGA_LAUNCH(ctx, local_band_kernel<T>, (unsigned)((R0 * per + th - 1) / th), th, 0, bands, dmask,
+             t1, R0, R1, nv, r0, n, r1, p, t2);
+  IGA_LAUNCH(ctx, local_left_kernel<T>, (unsigned)((per + th - 1) / th), th, 0, PhiL, t2, R0, nv,
+             r0, n, r1, y);
+}
+
+template void local_matvec_t<double>(iga_ctx*, int, int, int, int, int, int, const double*,
+                                     const double*, const double*, const unsigned char*, int,
+                                     const double*, double*, double*, double*);
+template void local_matvec_t<float>(iga_ctx*, int, int, int, int, int, int, const float*,
+                                    const float*, const float*, const unsigned char*, int,
+                                    const float*, float*, float*, float*);
+
+// row-major C (M x N) = A (M x K) B (K x N)
+void gemm_rm(iga_ctx* ctx, int M, int N, int K, const double* A, const double* B, double* C,
+             double beta) {
+  const double one = 1.0;
+  IGA_BLAS(cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, N, M, K, &one, B, N, A, K, &beta, C,
+                       N));
+}
+
+void tt_full_impl(iga_ctx* ctx, const iga_tt* tt, double* out) {
+  IGA_REQUIRE(tt && out, "tt_full: null argument");
+  IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
+  int n1 = tt->n[0], n2 = tt->n[1], n3 = tt->n[2], r1 = tt->r[0], r2 = tt->r[1];
+  double* t12 = scratch<double>(ctx, SLOT_MISC0, (size_t)n1 * n2 * r2);
+  gemm_rm(ctx, n1, n2 * r2, r1, tt->core[0].p, tt->core[1].p, t12);
+  gemm_rm(ctx, n1 * n2, n3, r2, t12, tt->core[2].p, out);
+}
+
+}  // namespace iga
+
+using namespace iga;
+
+extern "C" iga_status iga_amen_local_matvec(iga_ctx* ctx, int r0, int n, int r1, int R0, int R1,
+                                            int p, const void* PhiL, const void* bands,
+                                            const void* PhiR, const unsigned char* bandmask,
+                                            int nvec, const void* x, void* y, iga_prec prec) {
+  if (!ctx) return IGA_EINVAL;
+  try {
+    IGA_REQUIRE(r0 > 0 && n > 0 && r1 > 0 && R0 > 0 && R1 > 0 && p >= 0 && nvec > 0,
+                "local_matvec: sizes must be positive");
+    IGA_REQUIRE(PhiL && bands && PhiR && x && y, "local_matvec: null pointer");
+    IGA_REQUIRE(x != y, "local_matvec: x and y must not overlap");
+    unsigned char* dmask = nullptr;
+    if (bandmask) {
+      dmask = scratch<unsigned char>(ctx, SLOT_MISC1, (size_t)R0 * R1);
+      IGA_CUDA(cudaMemcpyAsync(dmask, bandmask, (size_t)R0 * R1, cudaMemcpyHostToDevice,
+                               ctx->stream));
+    }
+    size_t per = (size_t)nvec * r0 * n * r1;
+    if (prec == IGA_FP64) {
+      double* t1 = scratch<double>(ctx, SLOT_LOCAL_T1, per * R1);
+      double* t2 = scratch<double>(ctx, SLOT_LOCAL_T2, per * R0);
+      local_matvec_t<double>(ctx, r0, n, r1, R0, R1, p, (const double*)PhiL, (const double*)bands,
+                             (const double*)PhiR, dmask, nvec, (const double*)x, (double*)y, t1,
+                             t2);
+    } else if (prec == IGA_FP32) {
+      float* t1 = scratch<float>(ctx, SLOT_LOCAL_T1, per * R1);
+      float* t2 = scratch<float>(ctx, SLOT_LOCAL_T2, per * R0);
+      local_matvec_t<float>(ctx, r0, n, r1, R0, R1, p, (const float*)PhiL, (const float*)bands,
+                            (const float*)PhiR, dmask, nvec, (const float*)x, (float*)y, t1, t2);
+    } else {
+      throw Error(IGA_EINVAL, "local_matvec: precision must be IGA_FP64 or IGA_FP32");
+    }
+    if (bandmask) IGA_CUDA(cudaStreamSynchronize(ctx->stream));   // host mask lifetime
+    return IGA_OK;
+  } catch (const Error& e) {
+    set_error(ctx, e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    set_error(ctx, e.what());
+    return IGA_ECUDA;
+  }
+}

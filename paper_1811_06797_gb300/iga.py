@@ -1,0 +1,381 @@
+"""ctypes binding of libiga (argument marshalling only).
+
+Every function here forwards to the C entry point of the same name in
+``libiga.so`` (declared in include/iga.h).  Device buffers are torch CUDA
+tensors passed by pointer; host arrays are numpy arrays.  There is no
+fallback path: if the library is missing or a call fails, an exception is
+raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libiga.so")
+_lib = None
+
+IGA_FP64, IGA_FP32, IGA_TF32 = 0, 1, 2
+STATUS = {0: "IGA_OK", 1: "IGA_EINVAL", 2: "IGA_ENOMEM", 3: "IGA_ECUDA", 4: "IGA_ENOCONV",
+          5: "IGA_ENONFINITE", 6: "IGA_ETIMEOUT"}
+
+
+class IgaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Geometry_(C.Structure):
+    _fields_ = [("kind", C.c_int), ("degree", C.c_int * 3), ("nknots", C.c_int * 3),
+                ("knots", C.POINTER(C.c_double) * 3), ("nctrl", C.c_int * 3),
+                ("ctrl_hw", C.POINTER(C.c_double)), ("twist", C.c_double)]
+
+
+class Space_(C.Structure):
+    _fields_ = [("degree", C.c_int * 3), ("nknots", C.c_int * 3),
+                ("knots", C.POINTER(C.c_double) * 3), ("nquad", C.c_int)]
+
+
+class Target_(C.Structure):
+    _fields_ = [("kind", C.c_int), ("params", C.c_double * 4)]
+
+
+class SolveOpts_(C.Structure):
+    _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("max_sweeps", C.c_int),
+                ("kick_rank", C.c_int), ("rmax", C.c_int), ("local_maxit", C.c_int),
+                ("refine_max", C.c_int), ("precision", C.c_int), ("verbose", C.c_int)]
+
+
+class SolveInfo_(C.Structure):
+    _fields_ = [("sweeps", C.c_int), ("refinements", C.c_int), ("max_rank", C.c_int),
+                ("local_iters", C.c_int), ("residual", C.c_double), ("seconds", C.c_double)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libiga.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise IgaError(1, f"libiga.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(_LIB_PATH)
+    vp, i, d, st = C.c_void_p, C.c_int, C.c_double, C.c_int
+    P = C.POINTER
+    sig = {
+        "iga_create": (st, [P(vp), vp]),
+        "iga_destroy": (None, [vp]),
+        "iga_last_error": (C.c_char_p, [vp]),
+        "iga_launch_count": (C.c_uint64, [vp]),
+        "iga_scratch_bytes": (C.c_size_t, [vp]),
+        "iga_sample_weights": (st, [vp, P(Geometry_), P(Space_), P(Target_), vp]),
+        "iga_tt_svd": (st, [vp, vp, i, i, i, d, d, i, P(vp)]),
+        "iga_tt_info": (st, [vp, P(C.c_int), P(C.c_int)]),
+        "iga_tt_core": (st, [vp, vp, i, vp]),
+        "iga_tt_full": (st, [vp, vp, vp]),
+        "iga_tt_destroy": (None, [vp]),
+        "iga_assemble_bands": (st, [vp, P(Space_), i, vp, i, i, i, i, vp]),
+        "iga_lowrank_assemble": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, P(vp), P(vp),
+                                      P(vp)]),
+        "iga_op_info": (st, [vp, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int),
+                             P(C.c_size_t)]),
+        "iga_op_block": (st, [vp, i, P(C.c_int)]),
+        "iga_op_bands": (st, [vp, vp, i, i, vp]),
+        "iga_op_destroy": (None, [vp]),
+        "iga_kron_apply": (st, [vp, vp, d, vp, d, vp, i]),
+        "iga_kkt_apply": (st, [vp, vp, vp, d, vp, vp, i]),
+        "iga_amen_local_matvec": (st, [vp, i, i, i, i, i, i, vp, vp, vp, vp, i, vp, vp, i]),
+        "iga_solve_opts_default": (None, [P(SolveOpts_)]),
+        "iga_kkt_solve_amen": (st, [vp, vp, vp, vp, d, P(SolveOpts_), vp, vp, vp,
+                                    P(SolveInfo_)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(_HERE), "include", "iga.h")).read()
+    return sorted(set(re.findall(r"\b(iga_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = lib().iga_last_error(ctx.handle if ctx is not None else None)
+        raise IgaError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device pointer of a contiguous torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise IgaError(1, "expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise IgaError(1, "expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _prec(t):
+    import torch
+    if t.dtype == torch.float64:
+        return IGA_FP64
+    if t.dtype == torch.float32:
+        return IGA_FP32
+    raise IgaError(1, f"unsupported dtype {t.dtype}")
+
+
+class Context:
+    """An iga_ctx bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        st = lib().iga_create(C.byref(h), C.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise IgaError(st, "iga_create failed")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().iga_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return int(lib().iga_launch_count(self.handle))
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(lib().iga_scratch_bytes(self.handle))
+
+    def last_error(self) -> str:
+        return lib().iga_last_error(self.handle).decode()
+
+
+class _Keep:
+    """Holds host arrays alive while a C struct points into them."""
+
+    def __init__(self):
+        self.items = []
+
+    def arr(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.items.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def geometry_struct(geo, keep):
+    g = Geometry_()
+    g.kind = int(geo.kind)
+    for d in range(3):
+        g.degree[d] = int(geo.degree[d])
+        g.nknots[d] = len(geo.knots[d])
+        g.knots[d] = keep.arr(geo.knots[d])
+        g.nctrl[d] = int(geo.ctrl.shape[d])
+    g.ctrl_hw = keep.arr(geo.homogeneous())
+    g.twist = float(geo.twist)
+    return g
+
+
+def space_struct(space, keep):
+    s = Space_()
+    for d in range(3):
+        s.degree[d] = int(space.degree[d])
+        s.nknots[d] = len(space.knots[d])
+        s.knots[d] = keep.arr(space.knots[d])
+    s.nquad = int(space.nquad)
+    return s
+
+
+def target_struct(target):
+    t = Target_()
+    if target is None:
+        t.kind = 0
+        return t
+    t.kind = int(target.kind)
+    for k, v in enumerate(target.params()):
+        t.params[k] = float(v)
+    return t
+
+
+class TT:
+    """Library-owned TT tensor (iga_tt)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def info(self):
+        n = (C.c_int * 3)()
+        r = (C.c_int * 2)()
+        _check(None, lib().iga_tt_info(self.handle, n, r))
+        return tuple(n), tuple(r)
+
+    def core(self, ctx, d):
+        n, r = self.info()
+        rl = (1, r[0], r[1], 1)
+        out = np.empty((rl[d], n[d], rl[d + 1]))
+        _check(ctx, lib().iga_tt_core(ctx.handle, self.handle, d, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def cores(self, ctx):
+        return [self.core(ctx, d) for d in range(3)]
+
+    def full(self, ctx, out):
+        _check(ctx, lib().iga_tt_full(ctx.handle, self.handle, _ptr(out)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.iga_tt_destroy(self.handle)
+            self.handle = None
+
+
+class Op:
+    """Library-owned Kronecker / TT-matrix operator (iga_op)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def info(self):
+        n = (C.c_int * 3)()
+        p = (C.c_int * 3)()
+        nb = C.c_int()
+        R = (C.c_int * 2)()
+        by = C.c_size_t()
+        _check(None, lib().iga_op_info(self.handle, n, p, C.byref(nb), R, C.byref(by)))
+        return {"n": tuple(n), "p": tuple(p), "nblocks": nb.value, "R": tuple(R),
+                "bytes": by.value}
+
+    def block_ranks(self, k):
+        R = (C.c_int * 2)()
+        _check(None, lib().iga_op_block(self.handle, k, R))
+        return tuple(R)
+
+    def bands(self, ctx, k, d):
+        inf = self.info()
+        R1, R2 = self.block_ranks(k)
+        b = 2 * inf["p"][d] + 1
+        n = inf["n"][d]
+        shape = {0: (R1, n, b), 1: (R1, R2, n, b), 2: (R2, n, b)}[d]
+        out = np.empty(shape)
+        _check(ctx, lib().iga_op_bands(ctx.handle, self.handle, k, d,
+                                       out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.iga_op_destroy(self.handle)
+            self.handle = None
+
+
+def iga_sample_weights(ctx, geometry, space, target, out):
+    keep = _Keep()
+    g = geometry_struct(geometry, keep)
+    s = space_struct(space, keep)
+    t = target_struct(target)
+    _check(ctx, lib().iga_sample_weights(ctx.handle, C.byref(g), C.byref(s), C.byref(t), _ptr(out)))
+    return out
+
+
+def iga_tt_svd(ctx, W, tol, norm_ref=0.0, rmax=0):
+    h = C.c_void_p()
+    n1, n2, n3 = W.shape
+    _check(ctx, lib().iga_tt_svd(ctx.handle, _ptr(W), n1, n2, n3, float(tol), float(norm_ref),
+                                 int(rmax), C.byref(h)))
+    return TT(h) if h.value else None
+
+
+def iga_assemble_bands(ctx, space, d, w, deriv_row, deriv_col, interior, band):
+    keep = _Keep()
+    s = space_struct(space, keep)
+    T = w.shape[0]
+    _check(ctx, lib().iga_assemble_bands(ctx.handle, C.byref(s), d, _ptr(w), T, int(deriv_row),
+                                         int(deriv_col), int(interior), _ptr(band)))
+    return band
+
+
+def iga_lowrank_assemble(ctx, geometry, space, target, tol):
+    keep = _Keep()
+    g = geometry_struct(geometry, keep)
+    s = space_struct(space, keep)
+    t = target_struct(target)
+    hm, hk, hl = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(ctx, lib().iga_lowrank_assemble(ctx.handle, C.byref(g), C.byref(s), C.byref(t),
+                                           float(tol), C.byref(hm), C.byref(hk), C.byref(hl)))
+    return Op(hm), Op(hk), (TT(hl) if hl.value else None)
+
+
+def iga_kron_apply(ctx, A, alpha, x, beta, y):
+    if x.dtype != y.dtype:
+        raise IgaError(1, "x and y dtypes differ")
+    _check(ctx, lib().iga_kron_apply(ctx.handle, A.handle, float(alpha), _ptr(x), float(beta),
+                                     _ptr(y), _prec(x)))
+    return y
+
+
+def iga_kkt_apply(ctx, M, K, beta, z, out):
+    if z.dtype != out.dtype:
+        raise IgaError(1, "z and out dtypes differ")
+    _check(ctx, lib().iga_kkt_apply(ctx.handle, M.handle, K.handle, float(beta), _ptr(z),
+                                    _ptr(out), _prec(z)))
+    return out
+
+
+def iga_amen_local_matvec(ctx, PhiL, bands, PhiR, x, y, bandmask=None):
+    """PhiL (R0,r0,r0), bands (R0,R1,n,2p+1), PhiR (R1,r1,r1), x/y (nvec,r0,n,r1)."""
+    R0, r0, _ = PhiL.shape
+    R1, r1, _ = PhiR.shape
+    n, b = bands.shape[2], bands.shape[3]
+    nvec = x.shape[0]
+    mask = None
+    if bandmask is not None:
+        m = np.ascontiguousarray(bandmask, dtype=np.uint8)
+        mask = m.ctypes.data_as(C.POINTER(C.c_ubyte))
+    _check(ctx, lib().iga_amen_local_matvec(ctx.handle, r0, n, r1, R0, R1, (b - 1) // 2,
+                                            _ptr(PhiL), _ptr(bands), _ptr(PhiR), mask, nvec,
+                                            _ptr(x), _ptr(y), _prec(x)))
+    return y
+
+
+def solve_opts(**kw):
+    o = SolveOpts_()
+    lib().iga_solve_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise IgaError(1, f"unknown solve option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def iga_kkt_solve_amen(ctx, M, K, load, beta, y, u, lam, **opts):
+    o = solve_opts(**opts)
+    info = SolveInfo_()
+    st = lib().iga_kkt_solve_amen(ctx.handle, M.handle, K.handle,
+                                  load.handle if load is not None else None, float(beta),
+                                  C.byref(o), _ptr(y), _ptr(u), _ptr(lam), C.byref(info))
+    res = {f: getattr(info, f) for f, _ in SolveInfo_._fields_}
+    if st not in (0, 4):
+        _check(ctx, st)
+    res["converged"] = st == 0
+    return res

@@ -1,0 +1,109 @@
+"""GPU parity of the Kronecker-sum apply (a5), KKT apply and AMEn local matvec (c)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.amen import local_matvec
+from oracle.assemble import Discretisation, assemble_band, band_to_csr
+from oracle.kkt import kkt_matrix
+from oracle.lowrank import band_dense, kron_apply, kron_matrix
+from paper_1811_06797_gb300 import workloads as wl
+from gpu_util import ctx_and_torch, op_terms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return ctx_and_torch()
+
+
+def _ops(env, name, p, E, tol=1e-12):
+    ctx, torch, iga = env
+    geo = {"cube": wl.unit_cube(), "annulus": wl.quarter_annulus(),
+           "twisted": wl.quarter_annulus(twist=math.pi / 4), "random": wl.random_volume()}[name]
+    space = wl.uniform_space(p, E)
+    return iga.iga_lowrank_assemble(ctx, geo, space, wl.Target(wl.TARGET_SINPROD), tol)
+
+
+@pytest.mark.parametrize("name,p,E", [("cube", 2, 16), ("annulus", 3, 9), ("twisted", 1, 13),
+                                      ("random", 2, 5), ("annulus", 4, 7)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_kron_apply(env, name, p, E, prec):
+    ctx, torch, iga = env
+    M, K, _ = _ops(env, name, p, E, 1e-6 if name == "random" else 1e-12)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    rng = np.random.default_rng(2)
+    for op in (M, K):
+        terms = op_terms(ctx, op)
+        N = int(np.prod(op.info()["n"]))
+        x = rng.standard_normal(N)
+        y0 = rng.standard_normal(N)
+        ref = 0.7 * kron_apply(terms, x) - 1.3 * y0
+        xt = torch.tensor(x, device="cuda", dtype=dt)
+        yt = torch.tensor(y0, device="cuda", dtype=dt)
+        iga.iga_kron_apply(ctx, op, 0.7, xt, -1.3, yt)
+        got = yt.double().cpu().numpy()
+        tol = 1e-13 if prec == "fp64" else 2e-6
+        assert np.linalg.norm(got - ref) < tol * np.linalg.norm(ref)
+        # beta = 0 ignores whatever y holds (NaN included)
+        yt.fill_(float("nan"))
+        iga.iga_kron_apply(ctx, op, 1.0, xt, 0.0, yt)
+        assert np.linalg.norm(yt.double().cpu().numpy() - kron_apply(terms, x)) < tol * np.linalg.norm(ref) * 3
+
+
+def test_kkt_apply_against_oracle_assembly(env):
+    ctx, torch, iga = env
+    work = wl.small(wl.quarter_annulus(twist=math.pi / 4), 2, 5, beta=1e-3)
+    M, K, _ = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, 1e-12)
+    disc = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+    Mb, Kb, _ = assemble_band(work.geometry, disc)
+    A = kkt_matrix(band_to_csr(Mb, True), band_to_csr(Kb, True), work.beta)
+    z = np.random.default_rng(3).standard_normal(A.shape[0])
+    out = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+    iga.iga_kkt_apply(ctx, M, K, work.beta, torch.tensor(z, device="cuda"), out)
+    ref = A @ z
+    assert np.linalg.norm(out.cpu().numpy() - ref) < 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("r0,n,r1,R0,R1,p,nvec", [(1, 17, 5, 1, 3, 2, 3), (6, 11, 7, 3, 2, 3, 2),
+                                                 (9, 20, 1, 4, 1, 1, 1), (16, 33, 12, 2, 2, 3, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_local_matvec(env, r0, n, r1, R0, R1, p, nvec, prec):
+    ctx, torch, iga = env
+    rng = np.random.default_rng(r0 * 100 + r1)
+    PhiL = rng.standard_normal((R0, r0, r0))
+    PhiR = rng.standard_normal((R1, r1, r1))
+    b = 2 * p + 1
+    bands = rng.standard_normal((R0, R1, n, b))
+    mask = rng.random((R0, R1)) < 0.7
+    mask[0, 0] = True
+    bands[~mask] = 0.0
+    for i in range(n):                 # band entries outside the matrix are zero
+        for o in range(b):
+            if not 0 <= i + o - p < n:
+                bands[:, :, i, o] = 0.0
+    x = rng.standard_normal((nvec, r0, n, r1))
+    Ad = [[band_dense(bands[a, c]) for c in range(R1)] for a in range(R0)]
+    ref = np.stack([local_matvec(PhiL, Ad, PhiR, x[v]) for v in range(nvec)])
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    T = lambda a: torch.tensor(a, device="cuda", dtype=dt)
+    y = torch.empty(x.shape, dtype=dt, device="cuda")
+    for m in (None, mask):
+        iga.iga_amen_local_matvec(ctx, T(PhiL), T(bands), T(PhiR), T(x), y, bandmask=m)
+        tol = 1e-13 if prec == "fp64" else 1e-5
+        assert np.linalg.norm(y.double().cpu().numpy() - ref) < tol * np.linalg.norm(ref)
+
+
+def test_errors_are_reported(env):
+    ctx, torch, iga = env
+    M, K, _ = _ops(env, "cube", 2, 4)
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(iga.IgaError):
+        iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, x)      # aliasing rejected
+    bad = wl.small(wl.unit_cube(), 2, 4)
+    bad.space.knots = (np.array([0, 0, 0.5, 1, 1, 1.0]),) + bad.space.knots[1:]
+    with pytest.raises(iga.IgaError) as e:
+        iga.iga_lowrank_assemble(ctx, bad.geometry, bad.space, bad.target, 1e-8)
+    assert e.value.status == 1 and "end knots" in str(e.value)
