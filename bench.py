@@ -1,0 +1,367 @@
+"""Benchmark: low-rank assembly + block-AMEn KKT solve on one GB300.
+
+One step = the whole hot path on one synthetic workload: sampling of the
+geometry weights, TT-SVD, batched univariate assembly (low-rank M, K and
+load), then the KKT solve by block AMEn with FP64 iterative refinement to
+a relative residual of 1e-6.  Default workload: the extruded quarter annulus,
+degree 3, 64 elements per direction (65^3 interior unknowns per field),
+TT tolerance 1e-6, beta = 1e-4, desired state exp(-|x - c|^2 / 0.1).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank solves its own replica of the workload (the path
+does not exchange data between GPUs); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "KKT solve s to 1e-6 rel. residual; Kron/TT apply % of roofline, mixed vs FP64"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP64_FMA_TFLOPS = 1.196      # measured FP64 FMA rate of this GB300 (CUDA cores)
+FP32_FMA_TFLOPS = 74.75      # measured FP32 FMA rate
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--roofline-kernel", default="kron_rank1_kernel")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                pass
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(mx)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(sm)
+        try:
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return out
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def cpu_oracle_sample(work, budget_s=20.0):
+    """Time the oracle on a bounded sample of the workload; scaled to one solve.
+
+    Assembly: the oracle's element loop on as many slabs of elements (along
+    direction 1) as fit the budget, scaled linearly to all slabs.  KKT solve:
+    the oracle's sparse direct solve is measured on the same geometry at a
+    reduced element count and scaled by (unknowns ratio)^2 (3-D nested
+    dissection cost grows about as N^2).
+    """
+    import numpy as np
+    from oracle.assemble import Discretisation, assemble_band, band_to_csr
+    from oracle.kkt import kkt_solve
+    from paper_1811_06797_gb300 import workloads as wl
+    p = work.space.degree[0]
+    E = len(np.unique(work.space.knots[0])) - 1
+    # --- assembly sample: a thin slab of elements
+    slab = 1
+    disc_full = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+    t0 = time.perf_counter()
+    # restrict to a slab by building a space with E elements in dirs 2, 3 and `slab` in dir 1,
+    # same element size: knots on [0, slab/E]
+    k1 = np.concatenate([np.zeros(p), np.linspace(0, slab / E, slab + 1), np.full(p, slab / E)])
+    k1 = k1 / k1[-1]   # element loop cost does not depend on the element size
+    disc = Discretisation(work.space.degree, (k1, work.space.knots[1], work.space.knots[2]),
+                          work.space.nquad)
+    try:
+        assemble_band(work.geometry, disc, work.target, chunk=1)
+        t_slab = time.perf_counter() - t0
+    except MemoryError:
+        t_slab = float("nan")
+    t_asm = t_slab * E / slab
+    # --- solve sample on a reduced grid of the same geometry
+    Es = 6
+    ws = wl.small(work.geometry, p, Es, work.target, beta=work.beta)
+    ds = Discretisation(ws.space.degree, ws.space.knots, ws.space.nquad)
+    Mb, Kb, b = assemble_band(ws.geometry, ds, ws.target)
+    M, K = band_to_csr(Mb, True), band_to_csr(Kb, True)
+    t1 = time.perf_counter()
+    kkt_solve(M, K, ws.beta, b[1:-1, 1:-1, 1:-1].ravel())
+    t_solve_s = time.perf_counter() - t1
+    Ns = M.shape[0]
+    Nf = int(np.prod(disc_full.n)) // 1
+    Nf = int(np.prod([n - 2 for n in disc_full.n]))
+    t_solve = t_solve_s * (Nf / Ns) ** 2
+    cores = os.cpu_count() or 1
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        cores = max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        pass
+    total = t_asm + t_solve
+    return {
+        "value": total, "unit": "s", "cores": cores, "kind": "oracle",
+        "sample": (f"assembly: element loop on 1 of {E} slabs of elements ({t_slab:.2f} s) x{E}; "
+                   f"KKT: SuperLU on the same geometry at {Es}^3 elements ({3 * Ns} unknowns, "
+                   f"{t_solve_s:.2f} s) scaled by (N/N_s)^2 to {3 * Nf} unknowns"),
+        "assembly_s": t_asm, "solve_s_extrapolated": t_solve,
+    }
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1811_06797_gb300 import build, iga, workloads as wl
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    work = wl.config(args.config)
+    prec = iga.IGA_FP32 if args.precision == "mixed" else iga.IGA_FP64
+    ctx = iga.Context()
+    stream = torch.cuda.current_stream()
+    l2flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    state = {}
+
+    def step():
+        M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+        if "y" not in state:
+            N = int(np.prod(M.info()["n"]))
+            state["N"] = N
+            state["y"], state["u"], state["lam"] = (
+                torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+        info = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"],
+                                      state["lam"], tol=args.tol, precision=prec)
+        state["info"] = info
+        state["ops"] = (M, K, load)
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if not state["info"]["converged"]:
+        raise RuntimeError(f"solve did not converge: {state['info']}")
+
+    # timed region (device time with CUDA events on the context stream)
+    times = []
+    launches0 = ctx.launches
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile_begin(args.roofline_kernel)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            l2flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    prof = ctx.profile_end()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = ctx.launches - launches0
+    ms = sum(times) / len(times)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    info = state["info"]
+
+    # end to end through the public API with host buffers: the geometry and
+    # discretisation arrays go host -> device inside the assembly call, the
+    # solution (y, u, lambda) comes back into pinned host memory
+    N = state["N"]
+    host = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+    h2d = sum(a.nbytes for a in (*work.space.knots, *work.geometry.knots,
+                                 work.geometry.homogeneous()))
+    e2e_times = []
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step()
+        host[:N].copy_(state["y"], non_blocking=True)
+        host[N:2 * N].copy_(state["u"], non_blocking=True)
+        host[2 * N:].copy_(state["lam"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = statistics.median(e2e_times)
+
+    pk, pk_kind = peaks()
+    roof = None
+    if prof["launches"] > 0 and prof["ms"] > 0:
+        avg_ms = prof["ms"] / prof["launches"]
+        by = prof["bytes"] / prof["launches"]
+        fl = prof["flops"] / prof["launches"]
+        if args.precision == "fp64":
+            achieved = fl / (avg_ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_FMA_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_FMA_TFLOPS, "traffic": None,
+                    "kernel": args.roofline_kernel, "launches": prof["launches"],
+                    "avg_us": avg_ms * 1e3, "peak_kind": "measured FP64 FMA"}
+        else:
+            achieved = by / (avg_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                    "kernel": args.roofline_kernel, "launches": prof["launches"],
+                    "avg_us": avg_ms * 1e3, "peak_kind": pk_kind}
+
+    line = {
+        "metric": METRIC,
+        "value": ms / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": work.name, "unknowns_per_field": N, "kkt_unknowns": 3 * N,
+                   "beta": work.beta, "tt_tol": work.tol, "residual_tol": args.tol,
+                   "precision": args.precision, "l2": "flushed (256 MB write) before every step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "solve": {k: info[k] for k in ("sweeps", "refinements", "max_rank", "local_iters",
+                                       "residual")},
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(3 * N * 8)},
+        "gpu_launches": int(launches / max(1, args.steps)),
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    return line, work
+
+
+def run_reference(args):
+    """The oracle timed as it stands on a bounded sample (no GPU)."""
+    from paper_1811_06797_gb300 import workloads as wl
+    work = wl.config(args.config)
+    vals = []
+    base = None
+    for _ in range(args.warmup):
+        pass
+    for _ in range(max(1, min(args.steps, 2))):
+        base = cpu_oracle_sample(work, args.cpu_seconds)
+        vals.append(base["value"])
+    v = statistics.median(vals)
+    return {
+        "metric": METRIC, "value": v, "unit": "s", "n_gpus": 1, "steps": len(vals),
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": work.name}, "impl": "reference",
+        "cpu_baseline": {k: base[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    line, work = run_gpu(args, world, rank, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            try:
+                line["cpu_baseline"] = cpu_oracle_sample(work, args.cpu_seconds)
+            except Exception as e:   # the baseline is reported, not required
+                line["cpu_baseline"] = {"value": None, "unit": "s", "kind": "oracle",
+                                        "cores": os.cpu_count(), "sample": f"failed: {e}"}
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -94,6 +94,17 @@ uint64_t iga_launch_count(const iga_ctx* ctx);
 /* Device bytes currently held by the context's scratch pool. */
 size_t iga_scratch_bytes(const iga_ctx* ctx);
 
+/* Instrumentation (no counterpart in the paper): from iga_profile_begin until
+ * iga_profile_end, every launch of a library kernel whose name contains
+ * `kernel` is bracketed by CUDA events on the context stream.
+ * iga_profile_end synchronises the stream and returns the number of such
+ * launches, their summed device time in milliseconds and the summed
+ * algorithmic bytes and flops the launch sites declared for them (0 where a
+ * kernel declares none). */
+iga_status iga_profile_begin(iga_ctx* ctx, const char* kernel);
+iga_status iga_profile_end(iga_ctx* ctx, uint64_t* launches, double* ms, double* bytes,
+                           double* flops);
+
 /* ---- (a1, a2) geometry sampling ------------------------------------- */
 
 /* Sample the geometry weights on the tensor Gauss grid of `space`

@@ -1,5 +1,1064 @@
-// Block-AMEn KKT solve (steps a6..a8): placeholder until the solver lands.
+// Block-AMEn solve of the stationary KKT system (steps a6, a7, a8).
+//
+// Sec. 5: the three solution components f = [y, u, lambda] share one block
+// TT (eq. btt) whose block index sits in the core being updated.  For core d
+// the reduced KKT system (eq. KKT_red) is solved with the projected blocks
+// F^T M F, F^T K F assembled factor by factor (interfaces Phi); the block
+// index then moves to the neighbouring core by a truncated SVD (eqs. svd1 /
+// svd2), and the new frame core is orthogonal (Sec. 5, last paragraph).
+//
+// Design on one GB300 (what differs from the paper's CPU method):
+//  * the right-hand side and the solution are also kept as full FP64
+//    vectors in HBM; after every local solve the exact full residual is
+//    formed with the fused Kronecker apply, and the AMEn enrichment
+//    (residual-based rank kick, cited but not spelled out in the paper)
+//    takes a Gaussian sketch of the residual projected onto the current
+//    left (forward sweep) or right (backward sweep) frame;
+//  * the local KKT system is solved by restarted GMRES with a
+//    "transformed block-Jacobi" preconditioner: the interfaces are brought
+//    to the generalised eigenbasis of (sum Phi^K, Phi^M) on each side, and
+//    for every pair of rank indices (a, b) the 3n x 3n local KKT block is
+//    factorised exactly by banded LU with partial pivoting;
+//  * mixed precision: local matvecs, preconditioner and GMRES run in FP32
+//    (IGA_FP32) or FP64 (IGA_FP64); interfaces, SVD moves, residuals and the
+//    outer iterative refinement z <- z + delta run in FP64.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
 #include "iga_internal.cuh"
+
+namespace iga {
+
+// ------------------------------------------------------------------ kernels
+
+// out[g] = sum_{nz in group g} band[nz] (x)_mode-2 in[src[nz]]
+// for tensors (r, n, r1) per group/source (banded along the middle index).
+template <typename T>
+__global__ void band_group_kernel(const T* __restrict__ band, const int* __restrict__ gptr,
+                                  const int* __restrict__ src, const long long* __restrict__ boff,
+                                  const T* __restrict__ in, int G, int r, int n, int r1, int p,
+                                  T* __restrict__ out) {
+  const int B = 2 * p + 1;
+  size_t per = (size_t)r * n * r1;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)G * per) return;
+  int g = (int)(idx / per);
+  size_t rem = idx - (size_t)g * per;
+  int b = (int)(rem % r1);
+  size_t q = rem / r1;
+  int i = (int)(q % n);
+  int a = (int)(q / n);
+  T s = T(0);
+  for (int z = gptr[g]; z < gptr[g + 1]; ++z) {
+    const T* row = band + boff[z] + (size_t)i * B;
+    const T* x = in + (size_t)src[z] * per + (size_t)a * n * r1 + b;
+    for (int o = 0; o < B; ++o) {
+      int j = i + o - p;
+      if (j >= 0 && j < n) s += row[o] * x[(size_t)j * r1];
+    }
+  }
+  out[idx] = s;
+}
+
+// t[s][v](a,i,b) = sum_b' R[s](b,b') x[v](a,i,b')   (nv vectors, S right factors)
+template <typename T>
+__global__ void right_mult_kernel(const T* __restrict__ R, const T* __restrict__ x, int S, int nv,
+                                  int r0, int n, int r1, int transR, T* __restrict__ t) {
+  size_t per = (size_t)nv * r0 * n * r1;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)S * per) return;
+  int s = (int)(idx / per);
+  size_t rem = idx - (size_t)s * per;
+  int b = (int)(rem % r1);
+  size_t row = rem / r1;
+  const T* Rs = R + (size_t)s * r1 * r1;
+  const T* xr = x + row * r1;
+  T acc = T(0);
+  if (!transR)
+    for (int c = 0; c < r1; ++c) acc += Rs[(size_t)b * r1 + c] * xr[c];
+  else
+    for (int c = 0; c < r1; ++c) acc += Rs[(size_t)c * r1 + b] * xr[c];
+  t[idx] = acc;
+}
+
+// y[v](a,i,b) = sum_s sum_a' L[s](a,a') t[s][v](a',i,b)   (sum over S left factors)
+template <typename T>
+__global__ void left_mult_kernel(const T* __restrict__ L, const T* __restrict__ t, int S, int nv,
+                                 int r0, int n, int r1, int transL, T* __restrict__ y) {
+  size_t per = (size_t)nv * r0 * n * r1;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per) return;
+  size_t nr = (size_t)n * r1;
+  size_t ib = idx % nr;
+  size_t va = idx / nr;
+  int a = (int)(va % r0);
+  size_t v = va / r0;
+  T acc = T(0);
+  for (int s = 0; s < S; ++s) {
+    const T* Ls = L + (size_t)s * r0 * r0;
+    const T* src = t + (size_t)s * per + v * r0 * nr + ib;
+    if (!transL)
+      for (int c = 0; c < r0; ++c) acc += Ls[(size_t)a * r0 + c] * src[(size_t)c * nr];
+    else
+      for (int c = 0; c < r0; ++c) acc += Ls[(size_t)c * r0 + a] * src[(size_t)c * nr];
+  }
+  y[idx] = acc;
+}
+
+// local KKT combination: out = [My + K lam, beta Mu - M lam, K y - M u]
+template <typename T>
+__global__ void kkt_combine_kernel(const T* __restrict__ Mv, const T* __restrict__ Kv, size_t L,
+                                   T beta, T* __restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  out[i] = Mv[i] + Kv[2 * L + i];
+  out[L + i] = beta * Mv[L + i] - Mv[2 * L + i];
+  out[2 * L + i] = Kv[i] - Mv[L + i];
+}
+
+// (3, r, n, r1) block core -> row-major ((a,i) x (l,b)) matrix
+__global__ void permute_fwd_kernel(const double* __restrict__ Xh, int r, int n, int r1,
+                                   double* __restrict__ Mx) {
+  size_t total = (size_t)3 * r * n * r1;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int b = (int)(idx % r1);
+  size_t q = idx / r1;
+  int i = (int)(q % n);
+  size_t la = q / n;
+  int a = (int)(la % r);
+  int l = (int)(la / r);
+  Mx[((size_t)a * n + i) * (3 * r1) + (size_t)l * r1 + b] = Xh[idx];
+}
+
+__global__ void scale_rows_kernel(double* __restrict__ A, int rows, int cols,
+                                  const double* __restrict__ w) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)rows * cols) return;
+  int r = (int)(idx / cols);
+  double s = w[r];
+  A[idx] = s > 0.0 ? A[idx] / sqrt(s) : 0.0;
+}
+
+__global__ void inv_sqrt_abs_kernel(const double* __restrict__ w, int k, double floor_rel,
+                                    double* __restrict__ out) {
+  // out_i = 1/sqrt(|w_i|) with |w_i| floored at floor_rel * max|w|
+  double mx = 0.0;
+  for (int j = 0; j < k; ++j) mx = fmax(mx, fabs(w[j]));
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  double v = fmax(fabs(w[i]), floor_rel * mx);
+  out[i] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+}
+
+// B = U diag(s) (U col-major k x k -> B col-major)
+__global__ void scale_cols_cm_kernel(const double* __restrict__ U, const double* __restrict__ s,
+                                     int k, double* __restrict__ B) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * k) return;
+  B[idx] = U[idx] * s[idx / k];
+}
+
+// sum over the first index: out(a,b) = sum_s P[s](a,b)
+__global__ void sum_slices_kernel(const double* __restrict__ P, int S, int r,
+                                  double* __restrict__ out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= r * r) return;
+  double acc = 0.0;
+  for (int s = 0; s < S; ++s) acc += P[(size_t)s * r * r + idx];
+  int a = idx / r, b = idx % r;
+  (void)a; (void)b;
+  out[idx] = acc;
+}
+
+__global__ void symmetrize_kernel(double* __restrict__ A, int r) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= r * r) return;
+  int a = idx / r, b = idx % r;
+  if (a < b) {
+    double v = 0.5 * (A[(size_t)a * r + b] + A[(size_t)b * r + a]);
+    A[(size_t)a * r + b] = v;
+    A[(size_t)b * r + a] = v;
+  }
+}
+
+// diag entries d[s](a) = sum_{x,y} V(x,a) P[s](x,y) V(y,a)   (V col-major r x r)
+__global__ void diag_sandwich_kernel(const double* __restrict__ P, const double* __restrict__ V,
+                                     int S, int r, double* __restrict__ d) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * r) return;
+  int s = idx / r, a = idx % r;
+  const double* Ps = P + (size_t)s * r * r;
+  const double* va = V + (size_t)a * r;
+  double acc = 0.0;
+  for (int x = 0; x < r; ++x) {
+    double t = 0.0;
+    for (int y = 0; y < r; ++y) t += Ps[(size_t)x * r + y] * va[y];
+    acc += va[x] * t;
+  }
+  d[idx] = acc;
+}
+
+template <typename T>
+__global__ void to_type_kernel(const double* __restrict__ a, T* __restrict__ b, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)a[i];
+}
+
+template <typename T>
+__global__ void from_type_kernel(const T* __restrict__ a, double* __restrict__ b, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a,
+                            size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
+__global__ void sub_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ c, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = a[i] - b[i];
+}
+
+template <typename T>
+__global__ void scale_by_dev_kernel(T* __restrict__ x, const T* __restrict__ s, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T v = *s;
+  if (i < n) x[i] = v > T(0) ? x[i] / v : T(0);
+}
+
+// --------------------------------------------- banded LU of the local KKT blocks
+//
+// For every rank pair (a, b) the 3n x 3n local KKT block
+//   [[M_ab, 0, K_ab^T], [0, beta M_ab, -M_ab], [K_ab, -M_ab, 0]]
+// is stored node-interleaved (unknown 3 i + l) with kl = ku = 3p + 2 and
+// factorised by Gaussian elimination with partial pivoting inside the band
+// (row-wise window storage, width 2 kl + ku + 1; multipliers stored without
+// later interchanges, as in the unblocked banded LU of the textbooks).
+// One thread owns one block; element (blk, row, w) lives at
+// ((row * W + w) * NB + blk) so that a warp touches consecutive addresses.
+
+struct BandLayout {
+  int n, p, kl, ku, W, N, NB, r0, r1;
+};
+
+template <typename T>
+__device__ __forceinline__ T& bel(T* A, const BandLayout& L, int blk, int row, int col) {
+  return A[((size_t)row * L.W + (col - row + L.kl)) * L.NB + blk];
+}
+
+template <typename T>
+__global__ void kkt_block_factor_kernel(
+    BandLayout L, T beta,
+    const T* __restrict__ bandM, const int* __restrict__ nzM_l, const int* __restrict__ nzM_r,
+    const long long* __restrict__ nzM_off, int nnzM,
+    const T* __restrict__ bandK, const int* __restrict__ nzK_l, const int* __restrict__ nzK_r,
+    const long long* __restrict__ nzK_off, int nnzK,
+    const T* __restrict__ dLM, const T* __restrict__ dRM, const T* __restrict__ dLK,
+    const T* __restrict__ dRK, T* __restrict__ A, int* __restrict__ piv, int* __restrict__ flag) {
+  int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= L.NB) return;
+  int a = blk / L.r1, b = blk % L.r1;
+  const int n = L.n, p = L.p, B = 2 * p + 1;
+  // zero the band storage of this block
+  for (int row = 0; row < L.N; ++row)
+    for (int w = 0; w < L.W; ++w) A[((size_t)row * L.W + w) * L.NB + blk] = T(0);
+  // assemble
+  for (int i = 0; i < n; ++i) {
+    for (int o = 0; o < B; ++o) {
+      int j = i + o - p;
+      if (j < 0 || j >= n) continue;
+      T m = T(0), k = T(0), kt = T(0);
+      for (int z = 0; z < nnzM; ++z)
+        m += dLM[(size_t)nzM_l[z] * L.r0 + a] * dRM[(size_t)nzM_r[z] * L.r1 + b] *
+             bandM[nzM_off[z] + (size_t)i * B + o];
+      for (int z = 0; z < nnzK; ++z) {
+        T s = dLK[(size_t)nzK_l[z] * L.r0 + a] * dRK[(size_t)nzK_r[z] * L.r1 + b];
+        k += s * bandK[nzK_off[z] + (size_t)i * B + o];
+        // K^T (i, j) = K (j, i): band entry of row j at offset i - j + p
+        kt += s * bandK[nzK_off[z] + (size_t)j * B + (i - j + p)];
+      }
+      bel(A, L, blk, 3 * i + 0, 3 * j + 0) += m;
+      bel(A, L, blk, 3 * i + 0, 3 * j + 2) += kt;
+      bel(A, L, blk, 3 * i + 1, 3 * j + 1) += beta * m;
+      bel(A, L, blk, 3 * i + 1, 3 * j + 2) += -m;
+      bel(A, L, blk, 3 * i + 2, 3 * j + 0) += k;
+      bel(A, L, blk, 3 * i + 2, 3 * j + 1) += -m;
+    }
+  }
+  // banded LU with partial pivoting
+  const int N = L.N, kl = L.kl, ku = L.ku;
+  for (int k = 0; k < N; ++k) {
+    int last = min(N - 1, k + kl);
+    int pr = k;
+    T best = fabs(bel(A, L, blk, k, k));
+    for (int i = k + 1; i <= last; ++i) {
+      T v = fabs(bel(A, L, blk, i, k));
+      if (v > best) { best = v; pr = i; }
+    }
+    piv[(size_t)k * L.NB + blk] = pr;
+    int jend = min(N - 1, k + kl + ku);
+    if (pr != k)
+      for (int j = k; j <= jend; ++j) {
+        T t = bel(A, L, blk, k, j);
+        bel(A, L, blk, k, j) = bel(A, L, blk, pr, j);
+        bel(A, L, blk, pr, j) = t;
+      }
+    T d = bel(A, L, blk, k, k);
+    if (d == T(0)) { atomicOr(flag, 2); continue; }
+    for (int i = k + 1; i <= last; ++i) {
+      T l = bel(A, L, blk, i, k) / d;
+      bel(A, L, blk, i, k) = l;
+      if (l != T(0))
+        for (int j = k + 1; j <= jend; ++j) bel(A, L, blk, i, j) -= l * bel(A, L, blk, k, j);
+    }
+  }
+}
+
+// solve every block system in place; the right-hand side of block (a, b) is
+// v[l](a, i, b) of a (3, r0, n, r1) tensor (node-interleaved as 3 i + l)
+template <typename T>
+__global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ A,
+                                       const int* __restrict__ piv, T* __restrict__ v) {
+  int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk >= L.NB) return;
+  int a = blk / L.r1, b = blk % L.r1;
+  const int n = L.n, N = L.N, kl = L.kl, ku = L.ku;
+  size_t comp = (size_t)L.r0 * n * L.r1;
+  auto at = [&](int I) -> T& {
+    int i = I / 3, l = I - 3 * i;
+    return v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b];
+  };
+  for (int k = 0; k < N; ++k) {
+    int pr = piv[(size_t)k * L.NB + blk];
+    if (pr != k) { T t = at(k); at(k) = at(pr); at(pr) = t; }
+    T bk = at(k);
+    int last = min(N - 1, k + kl);
+    for (int i = k + 1; i <= last; ++i) at(i) -= bel(const_cast<T*>(A), L, blk, i, k) * bk;
+  }
+  for (int k = N - 1; k >= 0; --k) {
+    T s = at(k);
+    int jend = min(N - 1, k + kl + ku);
+    for (int j = k + 1; j <= jend; ++j) s -= bel(const_cast<T*>(A), L, blk, k, j) * at(j);
+    T d = bel(const_cast<T*>(A), L, blk, k, k);
+    at(k) = d != T(0) ? s / d : T(0);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+static inline unsigned nblk(size_t n, int th = 256) { return (unsigned)((n + th - 1) / th); }
+
+// row-major C (M x N, ldc) = alpha op(A) op(B) + beta C with row-major A, B
+static void rm_gemm(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const double* A, int lda,
+                    const double* B, int ldb, double* C, int ldc, double alpha = 1.0,
+                    double beta = 0.0) {
+  if (M == 0 || N == 0) return;
+  IGA_BLAS(cublasDgemm(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N, tA ? CUBLAS_OP_T : CUBLAS_OP_N,
+                       N, M, K, &alpha, B, ldb, A, lda, &beta, C, ldc));
+}
+
+// nonzero pattern of one TT-matrix core of an operator
+struct CoreNZ {
+  int R0 = 1, R1 = 1;
+  std::vector<int> l, r;                  // (alpha, beta) of every nonzero band
+  std::vector<long long> off;             // element offset of the band in band64/band32[d]
+  DevBuf<int> dl, dr, rowptr, rowsrc, colptr, colsrc;
+  DevBuf<long long> doff, rowoff, coloff;
+};
+
+static void build_core_nz(const iga_op* op, int d, CoreNZ& c) {
+  c.l.clear(); c.r.clear(); c.off.clear();
+  size_t len = (size_t)op->n[d] * (2 * op->p[d] + 1);
+  int a0 = 0, b0 = 0;
+  for (const OpBlock& blk : op->blocks) {
+    if (d == 0) {
+      for (int a = 0; a < blk.R1; ++a) {
+        c.l.push_back(0); c.r.push_back(a0 + a);
+        c.off.push_back((long long)((blk.off[0] + a) * len));
+      }
+    } else if (d == 1) {
+      for (int a = 0; a < blk.R1; ++a)
+        for (int b = 0; b < blk.R2; ++b) {
+          c.l.push_back(a0 + a); c.r.push_back(b0 + b);
+          c.off.push_back((long long)((blk.off[1] + (size_t)a * blk.R2 + b) * len));
+        }
+    } else {
+      for (int b = 0; b < blk.R2; ++b) {
+        c.l.push_back(b0 + b); c.r.push_back(0);
+        c.off.push_back((long long)((blk.off[2] + b) * len));
+      }
+    }
+    a0 += blk.R1;
+    b0 += blk.R2;
+  }
+  c.R0 = d == 0 ? 1 : (d == 1 ? a0 : b0);
+  c.R1 = d == 0 ? a0 : (d == 1 ? b0 : 1);
+  int nnz = (int)c.l.size();
+  // CSR by left index (groups = alpha, sources = beta) and CSC (groups = beta, sources = alpha)
+  std::vector<int> rp(c.R0 + 1, 0), cp(c.R1 + 1, 0), rs(nnz), cs(nnz);
+  std::vector<long long> ro(nnz), co(nnz);
+  for (int z = 0; z < nnz; ++z) { rp[c.l[z] + 1]++; cp[c.r[z] + 1]++; }
+  for (int i = 0; i < c.R0; ++i) rp[i + 1] += rp[i];
+  for (int i = 0; i < c.R1; ++i) cp[i + 1] += cp[i];
+  std::vector<int> rf(rp.begin(), rp.end() - 1), cf(cp.begin(), cp.end() - 1);
+  for (int z = 0; z < nnz; ++z) {
+    int pr = rf[c.l[z]]++;
+    rs[pr] = c.r[z]; ro[pr] = c.off[z];
+    int pc = cf[c.r[z]]++;
+    cs[pc] = c.l[z]; co[pc] = c.off[z];
+  }
+  auto up = [](auto& buf, const auto& v) {
+    using E = typename std::decay_t<decltype(v)>::value_type;
+    buf.alloc(std::max<size_t>(1, v.size()));
+    if (!v.empty())
+      IGA_CUDA(cudaMemcpy(buf.p, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice));
+  };
+  up(c.dl, c.l); up(c.dr, c.r); up(c.doff, c.off);
+  up(c.rowptr, rp); up(c.rowsrc, rs); up(c.rowoff, ro);
+  up(c.colptr, cp); up(c.colsrc, cs); up(c.coloff, co);
+}
+
+template <typename T>
+static const T* bands_of(const iga_op* op, int d) {
+  if constexpr (sizeof(T) == 8) return op->band64[d].p;
+  else return op->band32[d].p;
+}
+
+template <typename T>
+struct Solver {
+  iga_ctx* ctx;
+  const iga_op* op[2];                 // 0: M, 1: K
+  double beta;
+  int n[3];
+  size_t N;
+  int r[4];
+  int kick, rmax;
+  double inner_tol;
+  CoreNZ nz[2][3];
+  DevBuf<double> X[3];                 // TT cores (FP64 master)
+  DevBuf<double> Xh;                   // block core (3, r_d, n_d, r_{d+1})
+  DevBuf<double> PhiL[2][4], PhiR[2][4];   // PhiL[o][d]: (R_{d-1}, r_d, r_d) left of core d
+  DevBuf<T> PLt[2], PRt[2];            // precision-T copies for the current core
+  int local_iters = 0;
+  uint64_t seed = 0x51ed2701ull;
+  int verbose = 0;
+
+  // ---- small helpers
+  double* slot(int k, size_t n) { return scratch<double>(ctx, SLOT_AMEN_BASE + k, n); }
+  T* tslot(int k, size_t n) { return scratch<T>(ctx, SLOT_AMEN_BASE + k, n); }
+
+  int Rl(int o, int d) const { return nz[o][d].R0; }   // left TT-matrix rank of core d
+  int Rr(int o, int d) const { return nz[o][d].R1; }
+
+  // interfaces ------------------------------------------------------------
+  void left_update(int o, int d) {          // PhiL[o][d+1] from PhiL[o][d] and X[d]
+    const CoreNZ& c = nz[o][d];
+    int r0 = r[d], nn = n[d], r1 = r[d + 1];
+    size_t per = (size_t)r0 * nn * r1;
+    double* u = slot(0, per * c.R0);
+    double* w = slot(1, per * c.R1);
+    // u[al] = PhiL[al] X  (r0 x n r1 each)
+    for (int al = 0; al < c.R0; ++al)
+      rm_gemm(ctx, false, false, r0, nn * r1, r0, PhiL[o][d].p + (size_t)al * r0 * r0, r0, X[d].p,
+              nn * r1, u + al * per, nn * r1);
+    IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R1 * per), 256, 0, op[o]->band64[d].p,
+               c.colptr.p, c.colsrc.p, c.coloff.p, u, c.R1, r0, nn, r1, op[o]->p[d], w);
+    PhiL[o][d + 1].ensure((size_t)c.R1 * r1 * r1);
+    for (int be = 0; be < c.R1; ++be)
+      rm_gemm(ctx, true, false, r1, r1, r0 * nn, X[d].p, r1, w + be * per, r1,
+              PhiL[o][d + 1].p + (size_t)be * r1 * r1, r1);
+  }
+
+  void right_update(int o, int d) {         // PhiR[o][d-1] from PhiR[o][d] and X[d]
+    const CoreNZ& c = nz[o][d];
+    int r0 = r[d], nn = n[d], r1 = r[d + 1];
+    size_t per = (size_t)r0 * nn * r1;
+    double* u = slot(0, per * c.R1);
+    double* w = slot(1, per * c.R0);
+    for (int be = 0; be < c.R1; ++be)
+      rm_gemm(ctx, false, true, r0 * nn, r1, r1, X[d].p, r1, PhiR[o][d].p + (size_t)be * r1 * r1,
+              r1, u + be * per, r1);
+    IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R0 * per), 256, 0, op[o]->band64[d].p,
+               c.rowptr.p, c.rowsrc.p, c.rowoff.p, u, c.R0, r0, nn, r1, op[o]->p[d], w);
+    PhiR[o][d - 1].ensure((size_t)c.R0 * r0 * r0);
+    for (int al = 0; al < c.R0; ++al)
+      rm_gemm(ctx, false, true, r0, r0, nn * r1, X[d].p, nn * r1, w + al * per, nn * r1,
+              PhiR[o][d - 1].p + (size_t)al * r0 * r0, r0);
+  }
+
+  void set_ones(DevBuf<double>& b) {
+    b.ensure(1);
+    double one = 1.0;
+    IGA_CUDA(cudaMemcpyAsync(b.p, &one, 8, cudaMemcpyHostToDevice, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+
+  // full tensors ----------------------------------------------------------
+  // frame pieces: Xr = X_{>0} (r1 x n2 n3), Xl = X_{<2} (n1 n2 x r2)
+  void right_frame(double* Xr) {
+    rm_gemm(ctx, false, false, r[1] * n[1], n[2], r[2], X[1].p, r[2], X[2].p, n[2], Xr, n[2]);
+  }
+  void left_frame(double* Xl) {
+    rm_gemm(ctx, false, false, n[0], n[1] * r[2], r[1], X[0].p, r[1], X[1].p, n[1] * r[2], Xl,
+            n[1] * r[2]);
+  }
+
+  // local rhs F_{!=d}^T f_l for the three components of a full (3, N) tensor
+  void project(const double* F, int d, double* rhs) {
+    int n1 = n[0], n2 = n[1], n3 = n[2];
+    size_t loc = (size_t)r[d] * n[d] * r[d + 1];
+    if (d == 0) {
+      double* Xr = slot(2, (size_t)r[1] * n2 * n3);
+      right_frame(Xr);
+      for (int l = 0; l < 3; ++l)
+        rm_gemm(ctx, false, true, n1, r[1], n2 * n3, F + l * N, n2 * n3, Xr, n2 * n3,
+                rhs + l * loc, r[1]);
+    } else if (d == 1) {
+      double* s = slot(2, (size_t)n1 * n2 * r[2]);
+      for (int l = 0; l < 3; ++l) {
+        rm_gemm(ctx, false, true, n1 * n2, r[2], n3, F + l * N, n3, X[2].p, n3, s, r[2]);
+        rm_gemm(ctx, true, false, r[1], n2 * r[2], n1, X[0].p, r[1], s, n2 * r[2], rhs + l * loc,
+                n2 * r[2]);
+      }
+    } else {
+      double* Xl = slot(2, (size_t)n1 * n2 * r[2]);
+      left_frame(Xl);
+      for (int l = 0; l < 3; ++l)
+        rm_gemm(ctx, true, false, r[2], n3, n1 * n2, Xl, r[2], F + l * N, n3, rhs + l * loc, n3);
+    }
+  }
+
+  // full (3, N) tensor of the TT with block core Xh at position d
+  void expand(int d, double* out) {
+    int n1 = n[0], n2 = n[1], n3 = n[2];
+    size_t loc = (size_t)r[d] * n[d] * r[d + 1];
+    if (d == 0) {
+      double* Xr = slot(2, (size_t)r[1] * n2 * n3);
+      right_frame(Xr);
+      for (int l = 0; l < 3; ++l)
+        rm_gemm(ctx, false, false, n1, n2 * n3, r[1], Xh.p + l * loc, r[1], Xr, n2 * n3,
+                out + l * N, n2 * n3);
+    } else if (d == 1) {
+      double* t = slot(2, (size_t)n1 * n2 * r[2]);
+      for (int l = 0; l < 3; ++l) {
+        rm_gemm(ctx, false, false, n1, n2 * r[2], r[1], X[0].p, r[1], Xh.p + l * loc, n2 * r[2],
+                t, n2 * r[2]);
+        rm_gemm(ctx, false, false, n1 * n2, n3, r[2], t, r[2], X[2].p, n3, out + l * N, n3);
+      }
+    } else {
+      double* Xl = slot(2, (size_t)n1 * n2 * r[2]);
+      left_frame(Xl);
+      for (int l = 0; l < 3; ++l)
+        rm_gemm(ctx, false, false, n1 * n2, n3, r[2], Xl, r[2], Xh.p + l * loc, n3, out + l * N,
+                n3);
+    }
+  }
+
+  // Gaussian sketch of the residual projected on the left frame (forward) or
+  // right frame (backward) of core d; returns E^T row-major (kick x m)
+  void sketch(const double* res, int d, bool forward, double* Et, int m) {
+    int n1 = n[0], n2 = n[1], n3 = n[2];
+    int k = kick;
+    double* E = slot(3, (size_t)m * k);
+    if (forward && d == 0) {
+      double* Om = slot(4, (size_t)3 * n2 * n3 * k);
+      fill_gaussian(ctx, Om, (size_t)3 * n2 * n3 * k, seed++);
+      for (int l = 0; l < 3; ++l)
+        rm_gemm(ctx, true, true, k, n1, n2 * n3, Om + (size_t)l * n2 * n3 * k, k, res + l * N,
+                n2 * n3, Et, n1, 1.0, l ? 1.0 : 0.0);
+      return;
+    }
+    if (forward && d == 1) {
+      double* Om = slot(4, (size_t)3 * n3 * k);
+      double* t = slot(5, (size_t)n1 * n2 * k);
+      fill_gaussian(ctx, Om, (size_t)3 * n3 * k, seed++);
+      for (int l = 0; l < 3; ++l) {
+        rm_gemm(ctx, false, false, n1 * n2, k, n3, res + l * N, n3, Om + (size_t)l * n3 * k, k, t, k);
+        rm_gemm(ctx, true, false, r[1], n2 * k, n1, X[0].p, r[1], t, n2 * k, E, n2 * k, 1.0,
+                l ? 1.0 : 0.0);
+      }
+      transpose_cm(ctx, E, k, m, Et);   // E row-major (m x k) == col-major (k x m) -> (m x k) cm
+      return;
+    }
+    if (!forward && d == 2) {
+      double* Om = slot(4, (size_t)3 * n1 * n2 * k);
+      fill_gaussian(ctx, Om, (size_t)3 * n1 * n2 * k, seed++);
+      for (int l = 0; l < 3; ++l)
+        rm_gemm(ctx, true, false, n3, k, n1 * n2, res + l * N, n3, Om + (size_t)l * n1 * n2 * k, k,
+                E, k, 1.0, l ? 1.0 : 0.0);
+      transpose_cm(ctx, E, k, m, Et);
+      return;
+    }
+    // backward, d == 1: basis in (n2 r2)
+    double* Om = slot(4, (size_t)3 * n1 * k);
+    double* s = slot(5, (size_t)n1 * n2 * r[2]);
+    fill_gaussian(ctx, Om, (size_t)3 * n1 * k, seed++);
+    for (int l = 0; l < 3; ++l) {
+      rm_gemm(ctx, false, true, n1 * n2, r[2], n3, res + l * N, n3, X[2].p, n3, s, r[2]);
+      rm_gemm(ctx, true, false, n2 * r[2], k, n1, s, n2 * r[2], Om + (size_t)l * n1 * k, k, E, k,
+              1.0, l ? 1.0 : 0.0);
+    }
+    transpose_cm(ctx, E, k, m, Et);
+  }
+
+  // truncation rank from descending eigenvalues of a Gram matrix
+  int trunc_rank(const std::vector<double>& lam, double rel) {
+    double tot = 0.0;
+    for (double v : lam) tot += std::max(v, 0.0);
+    double thr2 = rel * rel * tot;
+    double tail = 0.0;
+    int k = (int)lam.size();
+    int rk = k;
+    for (int i = k - 1; i >= 1; --i) {
+      tail += std::max(lam[i], 0.0);
+      if (tail > thr2) break;
+      rk = i;
+    }
+    return std::max(1, std::min(rk, rmax));
+  }
+
+  // move the block index from core d to d+1 (forward) with enrichment
+  void move_forward(int d, const double* res) {
+    int r0 = r[d], nn = n[d], r1 = r[d + 1];
+    int m = r0 * nn, c3 = 3 * r1;
+    double* Mx = slot(6, (size_t)m * c3);
+    IGA_LAUNCH(ctx, permute_fwd_kernel, nblk((size_t)m * c3), 256, 0, Xh.p, r0, nn, r1, Mx);
+    double* G = slot(7, (size_t)c3 * c3);
+    double* V = slot(8, (size_t)c3 * c3);
+    double* w = slot(9, c3);
+    rm_gemm(ctx, true, false, c3, c3, m, Mx, c3, Mx, c3, G, c3);
+    jacobi_eig(ctx, G, V, w, c3);        // V col-major: columns = right singular vectors
+    std::vector<double> lam(c3);
+    IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    int rk = std::min(trunc_rank(lam, 0.1 * inner_tol), m);
+    int kk = std::max(0, std::min(kick, m - rk));
+    int nr = rk + kk;
+    double* Y = slot(10, (size_t)m * nr);           // col-major (m x nr): [U_k, E]
+    // U_k^T = Sigma^-1 V_k^T Mx^T  (row-major rk x m == col-major m x rk)
+    rm_gemm(ctx, false, true, rk, m, c3, V, c3, Mx, c3, Y, m);
+    IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
+    if (kk > 0) {
+      int keep = kick;
+      kick = kk;
+      sketch(res, d, true, Y + (size_t)rk * m, m);
+      kick = keep;
+    }
+    double* Q = slot(11, (size_t)m * nr);
+    householder_qr(ctx, Y, Q, m, nr);
+    X[d].ensure((size_t)m * nr);
+    transpose_cm(ctx, Q, m, nr, X[d].p);
+    double* coef = slot(12, (size_t)nr * c3);
+    rm_gemm(ctx, false, false, nr, c3, m, Q, m, Mx, c3, coef, c3);
+    int n2 = n[d + 1], r2 = r[d + 2];
+    Xh.ensure((size_t)3 * nr * n2 * r2);
+    for (int l = 0; l < 3; ++l)
+      rm_gemm(ctx, false, false, nr, n2 * r2, r1, coef + l * r1, c3, X[d + 1].p, n2 * r2,
+              Xh.p + (size_t)l * nr * n2 * r2, n2 * r2);
+    r[d + 1] = nr;
+    left_update(0, d);
+    left_update(1, d);
+  }
+
+  // move the block index from core d to d-1 (backward) with enrichment
+  void move_backward(int d, const double* res) {
+    int r0 = r[d], nn = n[d], r1 = r[d + 1];
+    int m = nn * r1, c3 = 3 * r0;
+    const double* Mx = Xh.p;                         // row-major (3 r0 x n r1)
+    double* G = slot(7, (size_t)c3 * c3);
+    double* V = slot(8, (size_t)c3 * c3);
+    double* w = slot(9, c3);
+    rm_gemm(ctx, false, true, c3, c3, m, Mx, m, Mx, m, G, c3);
+    jacobi_eig(ctx, G, V, w, c3);                   // columns: left singular vectors
+    std::vector<double> lam(c3);
+    IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    int rk = std::min(trunc_rank(lam, 0.1 * inner_tol), m);
+    int kk = std::max(0, std::min(kick, m - rk));
+    int nr = rk + kk;
+    double* Y = slot(10, (size_t)m * nr);
+    // W_k^T = Sigma^-1 U_k^T Mx (row-major rk x m == col-major m x rk)
+    rm_gemm(ctx, false, false, rk, m, c3, V, c3, Mx, m, Y, m);
+    IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
+    if (kk > 0) {
+      int keep = kick;
+      kick = kk;
+      sketch(res, d, false, Y + (size_t)rk * m, m);
+      kick = keep;
+    }
+    double* Q = slot(11, (size_t)m * nr);
+    householder_qr(ctx, Y, Q, m, nr);
+    double* coef = slot(12, (size_t)c3 * nr);       // row-major (3 r0 x nr) = Mx Q
+    rm_gemm(ctx, false, true, c3, nr, m, Mx, m, Q, m, coef, nr);
+    X[d].ensure((size_t)m * nr);
+    IGA_CUDA(cudaMemcpyAsync(X[d].p, Q, (size_t)m * nr * 8, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    int rp = r[d - 1], np = n[d - 1];
+    double* nXh = slot(13, (size_t)3 * rp * np * nr);
+    for (int l = 0; l < 3; ++l)
+      rm_gemm(ctx, false, false, rp * np, nr, r0, X[d - 1].p, r0, coef + (size_t)l * r0 * nr, nr,
+              nXh + (size_t)l * rp * np * nr, nr);
+    Xh.ensure((size_t)3 * rp * np * nr);
+    IGA_CUDA(cudaMemcpyAsync(Xh.p, nXh, (size_t)3 * rp * np * nr * 8, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    r[d] = nr;
+    right_update(0, d);
+    right_update(1, d);
+  }
+
+  // ---- local KKT operator in precision T
+  struct Local {
+    int d, r0, nn, r1;
+    size_t L;                            // per component
+  };
+
+  void local_op(const Local& c, const T* x, T* y) {
+    size_t per = (size_t)3 * c.L;
+    T* Mv = tslot(20, per);
+    T* Kv = tslot(21, per);
+    for (int o = 0; o < 2; ++o) {
+      const CoreNZ& z = nz[o][c.d];
+      T* t1 = tslot(22, per * z.R1);
+      T* t2 = tslot(23, per * z.R0);
+      T* out = o ? Kv : Mv;
+      IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per * z.R1), 256, 0, PRt[o].p, x, z.R1, 3, c.r0,
+                 c.nn, c.r1, 0, t1);
+      IGA_LAUNCH(ctx, band_group_kernel<T>, nblk(per * z.R0), 256, 0, bands_of<T>(op[o], c.d),
+                 z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, 3 * c.r0, c.nn, c.r1,
+                 op[o]->p[c.d], t2);
+      IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, PLt[o].p, t2, z.R0, 3, c.r0, c.nn,
+                 c.r1, 0, out);
+    }
+    IGA_LAUNCH(ctx, kkt_combine_kernel<T>, nblk(c.L), 256, 0, Mv, Kv, c.L, (T)beta, y);
+  }
+
+  // ---- preconditioner
+  BandLayout BL{};
+  DevBuf<T> VLt, VRt;                    // transforms (col-major r x r)
+  void precond_setup(const Local& c) {
+    int r0 = c.r0, r1 = c.r1;
+    auto gen_eig = [&](const DevBuf<double>& PM, int SM, const DevBuf<double>& PK, int SK, int rr,
+                       int slotbase, DevBuf<T>& Vout, double* dM, double* dK) {
+      double* Tm = slot(slotbase + 0, (size_t)rr * rr);
+      double* Sm = slot(slotbase + 1, (size_t)rr * rr);
+      double* U = slot(slotbase + 2, (size_t)rr * rr);
+      double* w = slot(slotbase + 3, rr);
+      double* s = slot(slotbase + 4, rr);
+      double* B = slot(slotbase + 5, (size_t)rr * rr);
+      double* C = slot(slotbase + 6, (size_t)rr * rr);
+      double* V = slot(slotbase + 7, (size_t)rr * rr);
+      IGA_LAUNCH(ctx, sum_slices_kernel, nblk(rr * rr), 256, 0, PM.p, SM, rr, Tm);
+      IGA_LAUNCH(ctx, sum_slices_kernel, nblk(rr * rr), 256, 0, PK.p, SK, rr, Sm);
+      IGA_LAUNCH(ctx, symmetrize_kernel, nblk(rr * rr), 256, 0, Tm, rr);
+      IGA_LAUNCH(ctx, symmetrize_kernel, nblk(rr * rr), 256, 0, Sm, rr);
+      if (rr == 1) {
+        double one = 1.0;
+        IGA_CUDA(cudaMemcpyAsync(V, &one, 8, cudaMemcpyHostToDevice, ctx->stream));
+      } else {
+        jacobi_eig(ctx, Tm, U, w, rr);                                  // T = U diag(w) U^T
+        IGA_LAUNCH(ctx, inv_sqrt_abs_kernel, nblk(rr), 256, 0, w, rr, 1e-14, s);
+        IGA_LAUNCH(ctx, scale_cols_cm_kernel, nblk(rr * rr), 256, 0, U, s, rr, B);   // U s
+        // T^{-1/2} = (U s) U^T  (col-major) -> compute as row-major products of transposes
+        rm_gemm(ctx, true, false, rr, rr, rr, U, rr, B, rr, Tm, rr);   // Tm = U B^T ... symmetric
+        // C = Tm S Tm
+        rm_gemm(ctx, false, false, rr, rr, rr, Tm, rr, Sm, rr, B, rr);
+        rm_gemm(ctx, false, false, rr, rr, rr, B, rr, Tm, rr, C, rr);
+        IGA_LAUNCH(ctx, symmetrize_kernel, nblk(rr * rr), 256, 0, C, rr);
+        jacobi_eig(ctx, C, U, w, rr);                                   // C = W diag W^T
+        // V = Tm W (col-major): as row-major V^T = W^T Tm
+        rm_gemm(ctx, false, false, rr, rr, rr, U, rr, Tm, rr, V, rr);
+      }
+      IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(SM * rr), 256, 0, PM.p, V, SM, rr, dM);
+      IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(SK * rr), 256, 0, PK.p, V, SK, rr, dK);
+      Vout.ensure((size_t)rr * rr);
+      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(rr * rr), 256, 0, V, Vout.p, (size_t)rr * rr);
+    };
+    const CoreNZ& zM = nz[0][c.d];
+    const CoreNZ& zK = nz[1][c.d];
+    double* dLM = slot(40, (size_t)zM.R0 * r0);
+    double* dLK = slot(41, (size_t)zK.R0 * r0);
+    double* dRM = slot(42, (size_t)zM.R1 * r1);
+    double* dRK = slot(43, (size_t)zK.R1 * r1);
+    gen_eig(PhiL[0][c.d], zM.R0, PhiL[1][c.d], zK.R0, r0, 50, VLt, dLM, dLK);
+    gen_eig(PhiR[0][c.d], zM.R1, PhiR[1][c.d], zK.R1, r1, 60, VRt, dRM, dRK);
+    T* tdLM = tslot(44, (size_t)zM.R0 * r0);
+    T* tdLK = tslot(45, (size_t)zK.R0 * r0);
+    T* tdRM = tslot(46, (size_t)zM.R1 * r1);
+    T* tdRK = tslot(47, (size_t)zK.R1 * r1);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zM.R0 * r0), 256, 0, dLM, tdLM, (size_t)zM.R0 * r0);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zK.R0 * r0), 256, 0, dLK, tdLK, (size_t)zK.R0 * r0);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zM.R1 * r1), 256, 0, dRM, tdRM, (size_t)zM.R1 * r1);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zK.R1 * r1), 256, 0, dRK, tdRK, (size_t)zK.R1 * r1);
+    BL.n = c.nn;
+    BL.p = op[0]->p[c.d];
+    BL.kl = BL.ku = 3 * BL.p + 2;
+    BL.W = 2 * BL.kl + BL.ku + 1;
+    BL.N = 3 * c.nn;
+    BL.r0 = r0;
+    BL.r1 = r1;
+    BL.NB = r0 * r1;
+    T* A = tslot(48, (size_t)BL.N * BL.W * BL.NB);
+    int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, (size_t)BL.N * BL.NB);
+    IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
+    IGA_LAUNCH(ctx, kkt_block_factor_kernel<T>, nblk(BL.NB, 64), 64, 0, BL, (T)beta,
+               bands_of<T>(op[0], c.d), zM.dl.p, zM.dr.p, zM.doff.p, (int)zM.l.size(),
+               bands_of<T>(op[1], c.d), zK.dl.p, zK.dr.p, zK.doff.p, (int)zK.l.size(), tdLM, tdRM,
+               tdLK, tdRK, A, piv, ctx->dflag);
+  }
+
+  void precond_apply(const Local& c, const T* v, T* z) {
+    size_t per = (size_t)3 * c.L;
+    T* t = tslot(24, per);
+    T* A = tslot(48, 1);
+    int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, 1);
+    // w = VL^T v VR
+    IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
+    IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
+    IGA_LAUNCH(ctx, kkt_block_solve_kernel<T>, nblk(BL.NB, 64), 64, 0, BL, A, piv, z);
+    // back: VL z VR^T
+    IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, z, 1, 3, c.r0, c.nn, c.r1, 1, t);
+    IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 1, z);
+  }
+
+  // ---- restarted right-preconditioned GMRES in precision T; returns iterations
+  int gmres(const Local& c, const T* b, T* x, double tol_abs, int maxit) {
+    const int m = 40;
+    size_t Lv = 3 * c.L;
+    T* Vb = tslot(25, Lv * (m + 1));
+    T* Zb = tslot(26, Lv * m);
+    T* w = tslot(27, Lv);
+    T* hd = tslot(28, 3 * (m + 2));
+    T* cst = tslot(29, 8);
+    T hc[4] = {T(1), T(0), T(-1), T(0)};
+    IGA_CUDA(cudaMemcpyAsync(cst, hc, sizeof(hc), cudaMemcpyHostToDevice, ctx->stream));
+    const T* one = cst;
+    const T* zero = cst + 1;
+    const T* mone = cst + 2;
+    IGA_BLAS(cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_DEVICE));
+    auto gemv = [&](cublasOperation_t t, int rows, int cols, const T* al, const T* A, const T* xx,
+                    const T* be, T* yy) {
+      if constexpr (sizeof(T) == 8)
+        IGA_BLAS(cublasDgemv(ctx->blas, t, rows, cols, al, A, rows, xx, 1, be, yy, 1));
+      else
+        IGA_BLAS(cublasSgemv(ctx->blas, t, rows, cols, al, A, rows, xx, 1, be, yy, 1));
+    };
+    auto nrm2 = [&](const T* xx, T* out) {
+      if constexpr (sizeof(T) == 8) IGA_BLAS(cublasDnrm2(ctx->blas, (int)Lv, xx, 1, out));
+      else IGA_BLAS(cublasSnrm2(ctx->blas, (int)Lv, xx, 1, out));
+    };
+    int it = 0;
+    std::vector<T> hh(3 * (m + 2));
+    std::vector<double> H((m + 1) * m), g(m + 1), cs(m), sn(m);
+    bool done = false;
+    try {
+      while (!done && it < maxit) {
+        // r = b - A x
+        local_op(c, x, w);
+        if constexpr (sizeof(T) == 8)
+          IGA_BLAS(cublasDgeam(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)Lv, 1, one, b, (int)Lv,
+                               mone, w, (int)Lv, Vb, (int)Lv));
+        else
+          IGA_BLAS(cublasSgeam(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)Lv, 1, one, b, (int)Lv,
+                               mone, w, (int)Lv, Vb, (int)Lv));
+        nrm2(Vb, hd);
+        IGA_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+        IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+        double beta0 = (double)hh[0];
+        if (!std::isfinite(beta0)) throw Error(IGA_ENONFINITE, "local GMRES: non-finite residual");
+        if (beta0 <= tol_abs) break;
+        IGA_LAUNCH(ctx, scale_by_dev_kernel<T>, nblk(Lv), 256, 0, Vb, hd, Lv);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta0;
+        int k = 0;
+        for (; k < m && it < maxit; ++k, ++it) {
+          T* vk = Vb + (size_t)k * Lv;
+          T* zk = Zb + (size_t)k * Lv;
+          precond_apply(c, vk, zk);
+          local_op(c, zk, w);
+          // classical Gram-Schmidt, twice
+          T* h1 = hd;
+          T* h2 = hd + (m + 2);
+          gemv(CUBLAS_OP_T, (int)Lv, k + 1, one, Vb, w, zero, h1);
+          gemv(CUBLAS_OP_N, (int)Lv, k + 1, mone, Vb, h1, one, w);
+          gemv(CUBLAS_OP_T, (int)Lv, k + 1, one, Vb, w, zero, h2);
+          gemv(CUBLAS_OP_N, (int)Lv, k + 1, mone, Vb, h2, one, w);
+          T* nr = hd + 2 * (m + 2);
+          nrm2(w, nr);
+          IGA_CUDA(cudaMemcpyAsync(hh.data(), hd, 3 * (m + 2) * sizeof(T), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+          T* vn = Vb + (size_t)(k + 1) * Lv;
+          IGA_CUDA(cudaMemcpyAsync(vn, w, Lv * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+          IGA_LAUNCH(ctx, scale_by_dev_kernel<T>, nblk(Lv), 256, 0, vn, nr, Lv);
+          IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+          for (int j = 0; j <= k; ++j) H[j * m + k] = (double)hh[j] + (double)hh[(m + 2) + j];
+          double hn = (double)hh[2 * (m + 2)];
+          if (!std::isfinite(hn)) throw Error(IGA_ENONFINITE, "local GMRES: non-finite vector");
+          for (int j = 0; j < k; ++j) {
+            double t = cs[j] * H[j * m + k] + sn[j] * H[(j + 1) * m + k];
+            H[(j + 1) * m + k] = -sn[j] * H[j * m + k] + cs[j] * H[(j + 1) * m + k];
+            H[j * m + k] = t;
+          }
+          double den = std::hypot(H[k * m + k], hn);
+          cs[k] = den > 0 ? H[k * m + k] / den : 1.0;
+          sn[k] = den > 0 ? hn / den : 0.0;
+          H[k * m + k] = den;
+          g[k + 1] = -sn[k] * g[k];
+          g[k] = cs[k] * g[k];
+          if (std::fabs(g[k + 1]) <= tol_abs || hn == 0.0) { ++k; ++it; done = true; break; }
+        }
+        // solve the triangular system and update x += Z y
+        int kk = k;
+        std::vector<double> y(kk, 0.0);
+        for (int i = kk - 1; i >= 0; --i) {
+          double s = g[i];
+          for (int j = i + 1; j < kk; ++j) s -= H[i * m + j] * y[j];
+          y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+        }
+        std::vector<T> yt(kk);
+        for (int i = 0; i < kk; ++i) yt[i] = (T)y[i];
+        IGA_CUDA(cudaMemcpyAsync(hd, yt.data(), kk * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+        if (kk > 0) gemv(CUBLAS_OP_N, (int)Lv, kk, one, Zb, hd, one, x);
+        IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+      }
+    } catch (...) {
+      cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST);
+      throw;
+    }
+    IGA_BLAS(cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST));
+    return it;
+  }
+
+  // solve the local KKT system at core d (rhs from the full residual F)
+  void local_solve(int d, const double* F, double tol_abs, int maxit) {
+    Local c{d, r[d], n[d], r[d + 1], (size_t)r[d] * n[d] * r[d + 1]};
+    size_t per = 3 * c.L;
+    double* rhs = slot(14, per);
+    project(F, d, rhs);
+    for (int o = 0; o < 2; ++o) {
+      size_t nl = (size_t)nz[o][d].R0 * r[d] * r[d];
+      size_t nr = (size_t)nz[o][d].R1 * r[d + 1] * r[d + 1];
+      PLt[o].ensure(nl);
+      PRt[o].ensure(nr);
+      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(nl), 256, 0, PhiL[o][d].p, PLt[o].p, nl);
+      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(nr), 256, 0, PhiR[o][d].p, PRt[o].p, nr);
+    }
+    precond_setup(c);
+    T* bt = tslot(30, per);
+    T* xt = tslot(31, per);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, rhs, bt, per);
+    // warm start from the current block core
+    Xh.ensure(per);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, Xh.p, xt, per);
+    local_iters += gmres(c, bt, xt, tol_abs, maxit);
+    IGA_LAUNCH(ctx, from_type_kernel<T>, nblk(per), 256, 0, xt, Xh.p, per);
+  }
+};
+
+// full FP64 KKT residual res = F - KKT z, returns ||res||_2 (synchronises)
+static double kkt_residual(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                           const double* F, const double* z, double* res, size_t N) {
+  double* tmp = scratch<double>(ctx, SLOT_KKT_TMP, 3 * N);
+  kkt_apply_internal(ctx, M, K, beta, z, tmp, IGA_FP64);
+  IGA_LAUNCH(ctx, sub_kernel, nblk(3 * N), 256, 0, F, tmp, res, 3 * N);
+  return device_norm2(ctx, res, 3 * N);
+}
+
+template <typename T>
+static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                           const double* F, double Fnorm, double tol, const iga_solve_opts* o,
+                           double* delta, int* sweeps_out, int* maxrank, int* liters, double* resid) {
+  Solver<T> S;
+  S.ctx = ctx;
+  S.op[0] = M;
+  S.op[1] = K;
+  S.beta = beta;
+  for (int d = 0; d < 3; ++d) S.n[d] = M->n[d];
+  S.N = (size_t)S.n[0] * S.n[1] * S.n[2];
+  S.kick = std::max(1, o->kick_rank);
+  S.rmax = std::max(2, o->rmax);
+  S.inner_tol = tol;
+  S.verbose = o->verbose;
+  size_t N = S.N;
+  for (int op = 0; op < 2; ++op)
+    for (int d = 0; d < 3; ++d) build_core_nz(S.op[op], d, S.nz[op][d]);
+  // initial TT: rank kick Gaussian cores, right-orthogonalised by QR; block index at core 0
+  int r0 = std::min({S.kick, S.n[0], S.n[1] * S.n[2]});
+  int r1 = std::min({S.kick, S.n[2], S.n[0] * S.n[1]});
+  S.r[0] = 1; S.r[1] = r0; S.r[2] = r1; S.r[3] = 1;
+  {
+    // X[2] = Q^T of a Gaussian (n3 x r2) block; X[1] = Q^T of a Gaussian (n2 r2 x r1) block
+    double* Y = S.slot(10, (size_t)S.n[2] * r1);
+    double* Q = S.slot(11, (size_t)S.n[2] * r1);
+    fill_gaussian(ctx, Y, (size_t)S.n[2] * r1, 77);
+    householder_qr(ctx, Y, Q, S.n[2], r1);
+    S.X[2].alloc((size_t)r1 * S.n[2]);
+    IGA_CUDA(cudaMemcpyAsync(S.X[2].p, Q, (size_t)r1 * S.n[2] * 8, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    int m = S.n[1] * r1;
+    double* Y2 = S.slot(10, (size_t)m * r0);
+    double* Q2 = S.slot(11, (size_t)m * r0);
+    fill_gaussian(ctx, Y2, (size_t)m * r0, 78);
+    householder_qr(ctx, Y2, Q2, m, r0);
+    S.X[1].alloc((size_t)r0 * m);
+    IGA_CUDA(cudaMemcpyAsync(S.X[1].p, Q2, (size_t)r0 * m * 8, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    S.X[0].alloc((size_t)S.n[0] * r0);
+    S.Xh.alloc((size_t)3 * S.n[0] * r0);
+    IGA_CUDA(cudaMemsetAsync(S.Xh.p, 0, (size_t)3 * S.n[0] * r0 * 8, ctx->stream));
+  }
+  for (int op = 0; op < 2; ++op) {
+    S.set_ones(S.PhiL[op][0]);
+    S.set_ones(S.PhiR[op][2]);
+    S.right_update(op, 2);
+    S.right_update(op, 1);
+  }
+  double* res = S.slot(15, 3 * N);
+  double rel = 1.0;
+  int sweep = 0;
+  int maxsw = std::max(1, o->max_sweeps);
+  double tol_abs = 0.1 * tol * Fnorm;
+  int maxit = std::max(1, o->local_maxit);
+  for (sweep = 0; sweep < maxsw; ++sweep) {
+    bool fwd = (sweep % 2) == 0;
+    int order[3] = {0, 1, 2};
+    if (!fwd) { order[0] = 2; order[2] = 0; }
+    for (int s = 0; s < 3; ++s) {
+      int d = order[s];
+      if (sweep > 0 && s == 0) {
+        // the first core of this sweep was solved last in the previous sweep
+        if (fwd) S.move_forward(d, res);
+        else S.move_backward(d, res);
+        continue;
+      }
+      S.local_solve(d, F, tol_abs, maxit);
+      S.expand(d, delta);
+      double rn = kkt_residual(ctx, M, K, beta, F, delta, res, N);
+      rel = rn / Fnorm;
+      if (S.verbose)
+        fprintf(stderr, "[amen] sweep %d core %d ranks (%d,%d) local_it %d resid %.3e\n", sweep,
+                d, S.r[1], S.r[2], S.local_iters, rel);
+      if (rel <= tol) { ++sweep; goto done; }
+      if (s < 2) {
+        if (fwd) S.move_forward(d, res);
+        else S.move_backward(d, res);
+      }
+    }
+  }
+done:
+  *sweeps_out += sweep;
+  *maxrank = std::max(*maxrank, std::max(S.r[1], S.r[2]));
+  *liters += S.local_iters;
+  *resid = rel;
+  return rel <= tol;
+}
+
+}  // namespace iga
 
 using namespace iga;
 
@@ -9,17 +1068,94 @@ extern "C" void iga_solve_opts_default(iga_solve_opts* o) {
   o->inner_tol = 1e-3;
   o->max_sweeps = 8;
   o->kick_rank = 4;
-  o->rmax = 128;
-  o->local_maxit = 200;
-  o->refine_max = 6;
+  o->rmax = 160;
+  o->local_maxit = 400;
+  o->refine_max = 8;
   o->precision = IGA_FP32;
   o->verbose = 0;
 }
 
-extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op*, const iga_op*, const iga_tt*,
-                                         double, const iga_solve_opts*, double*, double*, double*,
-                                         iga_solve_info*) {
+extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                                         const iga_tt* load, double beta,
+                                         const iga_solve_opts* opts, double* y, double* u,
+                                         double* lam, iga_solve_info* info) {
   if (!ctx) return IGA_EINVAL;
-  set_error(ctx, "iga_kkt_solve_amen: solver not built in this revision");
-  return IGA_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    IGA_REQUIRE(M && K && y && u && lam, "kkt_solve_amen: null argument");
+    IGA_REQUIRE(beta > 0.0, "kkt_solve_amen: beta must be positive");
+    for (int d = 0; d < 3; ++d)
+      IGA_REQUIRE(M->n[d] == K->n[d] && M->p[d] == K->p[d], "kkt_solve_amen: M, K mismatch");
+    iga_solve_opts o;
+    if (opts) o = *opts; else iga_solve_opts_default(&o);
+    IGA_REQUIRE(o.tol > 0.0 && o.inner_tol > 0.0, "kkt_solve_amen: tolerances must be > 0");
+    IGA_REQUIRE(o.precision == IGA_FP64 || o.precision == IGA_FP32,
+                "kkt_solve_amen: precision must be IGA_FP64 or IGA_FP32");
+    IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
+    size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
+    // rhs F = [b; 0; 0] (full FP64); z = 0
+    double* F = scratch<double>(ctx, SLOT_AMEN_BASE - 4, 3 * N);
+    double* z = scratch<double>(ctx, SLOT_AMEN_BASE - 3, 3 * N);
+    double* delta = scratch<double>(ctx, SLOT_AMEN_BASE - 2, 3 * N);
+    double* r = scratch<double>(ctx, SLOT_AMEN_BASE - 1, 3 * N);
+    IGA_CUDA(cudaMemsetAsync(F, 0, 3 * N * 8, ctx->stream));
+    IGA_CUDA(cudaMemsetAsync(z, 0, 3 * N * 8, ctx->stream));
+    if (load) {
+      for (int d = 0; d < 3; ++d)
+        IGA_REQUIRE(load->n[d] == M->n[d], "kkt_solve_amen: load size mismatch");
+      tt_full_impl(ctx, load, F);
+    }
+    double Fn = device_norm2(ctx, F, 3 * N);
+    iga_solve_info inf{};
+    double rel = 0.0;
+    bool ok = Fn == 0.0;
+    if (!ok) {
+      double rn = Fn;
+      IGA_CUDA(cudaMemcpyAsync(r, F, 3 * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+      double inner = o.precision == IGA_FP64 ? o.tol : std::max(o.inner_tol, o.tol);
+      for (int it = 0; it <= o.refine_max; ++it) {
+        rel = rn / Fn;
+        if (rel <= o.tol) { ok = true; break; }
+        if (it == o.refine_max) break;
+        // correction: KKT delta = r to relative accuracy `inner` (capped so the
+        // last step does not overshoot the target much)
+        double itol = std::max(inner, 0.5 * o.tol * Fn / rn);
+        double cres = 1.0;
+        if (o.precision == IGA_FP64)
+          amen_correction<double>(ctx, M, K, beta, r, rn, itol, &o, delta, &inf.sweeps,
+                                  &inf.max_rank, &inf.local_iters, &cres);
+        else
+          amen_correction<float>(ctx, M, K, beta, r, rn, itol, &o, delta, &inf.sweeps,
+                                 &inf.max_rank, &inf.local_iters, &cres);
+        IGA_LAUNCH(ctx, axpy_kernel, nblk(3 * N), 256, 0, z, delta, 1.0, 3 * N);
+        rn = kkt_residual(ctx, M, K, beta, F, z, r, N);
+        inf.refinements = it + 1;
+        if (o.verbose)
+          fprintf(stderr, "[amen] refinement %d: correction resid %.3e, total resid %.3e\n", it,
+                  cres, rn / Fn);
+      }
+      rel = rn / Fn;
+      ok = rel <= o.tol;
+    }
+    IGA_CUDA(cudaMemcpyAsync(y, z, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(u, z + N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(lam, z + 2 * N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    inf.residual = rel;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    if (!ok) {
+      set_error(ctx, "kkt_solve_amen: tolerance not reached");
+      return IGA_ENOCONV;
+    }
+    return IGA_OK;
+  } catch (const Error& e) {
+    cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST);
+    set_error(ctx, e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST);
+    set_error(ctx, e.what());
+    return IGA_ECUDA;
+  }
 }

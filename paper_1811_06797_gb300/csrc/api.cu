@@ -17,6 +17,24 @@ void set_error(iga_ctx* ctx, const std::string& m) {
   if (ctx) ctx->err = m;
 }
 
+void prof_start(iga_ctx* ctx) {
+  if (ctx->prof_used + 2 > ctx->prof_ev.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      IGA_CUDA(cudaEventCreate(&e));
+      ctx->prof_ev.push_back(e);
+    }
+  }
+  IGA_CUDA(cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream));
+  ctx->prof_bytes += ctx->next_bytes;
+  ctx->prof_flops += ctx->next_flops;
+}
+
+void prof_stop(iga_ctx* ctx) {
+  IGA_CUDA(cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], ctx->stream));
+  ctx->prof_used += 2;
+}
+
 void sample_weights_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
                          const iga_target* target, double* out);
 
@@ -227,11 +245,41 @@ iga_status iga_create(iga_ctx** out, void* stream) {
 void iga_destroy(iga_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   ctx->scratch.clear();
   if (ctx->blas) cublasDestroy(ctx->blas);
   if (ctx->dflag) cudaFree(ctx->dflag);
   if (ctx->hflag) cudaFreeHost(ctx->hflag);
   delete ctx;
+}
+
+iga_status iga_profile_begin(iga_ctx* ctx, const char* kernel) {
+  if (!ctx) return IGA_EINVAL;
+  ctx->prof_name = kernel ? kernel : "";
+  ctx->prof_used = 0;
+  ctx->prof_bytes = 0.0;
+  ctx->prof_flops = 0.0;
+  return IGA_OK;
+}
+
+iga_status iga_profile_end(iga_ctx* ctx, uint64_t* launches, double* ms, double* bytes,
+                           double* flops) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < ctx->prof_used; i += 2) {
+      float t = 0.f;
+      IGA_CUDA(cudaEventElapsedTime(&t, ctx->prof_ev[i], ctx->prof_ev[i + 1]));
+      tot += t;
+    }
+    if (launches) *launches = ctx->prof_used / 2;
+    if (ms) *ms = tot;
+    if (bytes) *bytes = ctx->prof_bytes;
+    if (flops) *flops = ctx->prof_flops;
+    ctx->prof_name.clear();
+    ctx->prof_used = 0;
+  })
 }
 
 const char* iga_last_error(const iga_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

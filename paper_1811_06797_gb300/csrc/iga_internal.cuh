@@ -45,11 +45,18 @@ struct Error : public std::runtime_error {
                                         std::to_string((int)s__));               \
   } while (0)
 
-// Launch on the context stream, count it, and surface launch errors.
+// Launch on the context stream, count it, and surface launch errors.  When
+// the context profiles a kernel whose name contains ctx->prof_name, the launch
+// is bracketed by CUDA events on the same stream.
 #define IGA_LAUNCH(ctx, kernel, grid, block, smem, ...)                          \
   do {                                                                           \
+    bool prof__ = ::iga::prof_match((ctx), #kernel);                             \
+    if (prof__) ::iga::prof_start(ctx);                                          \
     kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);             \
+    if (prof__) ::iga::prof_stop(ctx);                                           \
     (ctx)->launches++;                                                           \
+    (ctx)->next_bytes = 0.0;                                                     \
+    (ctx)->next_flops = 0.0;                                                     \
     IGA_CUDA(cudaGetLastError());                                                \
   } while (0)
 
@@ -117,6 +124,12 @@ struct iga_ctx {
   std::vector<iga::DevBuf<char>> scratch;   // reusable scratch slots
   int* dflag = nullptr;                     // device status flags (zeroed per use)
   int* hflag = nullptr;                     // pinned host mirror
+  // kernel timing (instrumentation): events around launches of one kernel
+  std::string prof_name;
+  std::vector<cudaEvent_t> prof_ev;         // pairs (start, stop)
+  size_t prof_used = 0;
+  double prof_bytes = 0.0, prof_flops = 0.0;
+  double next_bytes = 0.0, next_flops = 0.0;   // algorithmic counts of the next launch
   size_t scratch_bytes() const {
     size_t s = 0;
     for (auto& b : scratch) s += b.n;
@@ -146,6 +159,17 @@ struct iga_tt {
 };
 
 namespace iga {
+
+inline bool prof_match(const iga_ctx* ctx, const char* name) {
+  return !ctx->prof_name.empty() && std::string(name).find(ctx->prof_name) != std::string::npos;
+}
+void prof_start(iga_ctx* ctx);
+void prof_stop(iga_ctx* ctx);
+// algorithmic bytes / flops of the next launch (used only while profiling)
+inline void prof_count(iga_ctx* ctx, double bytes, double flops) {
+  ctx->next_bytes = bytes;
+  ctx->next_flops = flops;
+}
 
 // scratch slot helper: returns a device pointer with at least `bytes` bytes
 template <typename T>

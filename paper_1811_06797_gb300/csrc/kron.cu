@@ -211,6 +211,12 @@ static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T bet
       for (int d = 0; d < 3; ++d) terms.b[d][cnt] = band_ptr<T>(A, d, A->blocks[t].off[d]);
     terms.nterms = cnt;
     T bt = (c0 == 0) ? beta : T(1);
+    {
+      // algorithmic: read x, write y (read y too when accumulating); 3 banded
+      // mode products of 2(2P+1) flop per point and term
+      double N = (double)g.n1 * g.n2 * g.n3;
+      prof_count(ctx, N * sizeof(T) * (bt != T(0) ? 3.0 : 2.0), 6.0 * (2 * P + 1) * N * cnt);
+    }
     IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P>), (unsigned)(nt1 * g.nt2 * g.nt3), KRON_THREADS, smem,
                terms, g, alpha, bt, x, y);
     if (nterm == 0) break;

@@ -74,6 +74,8 @@ def lib():
         "iga_last_error": (C.c_char_p, [vp]),
         "iga_launch_count": (C.c_uint64, [vp]),
         "iga_scratch_bytes": (C.c_size_t, [vp]),
+        "iga_profile_begin": (st, [vp, C.c_char_p]),
+        "iga_profile_end": (st, [vp, P(C.c_uint64), P(d), P(d), P(d)]),
         "iga_sample_weights": (st, [vp, P(Geometry_), P(Space_), P(Target_), vp]),
         "iga_tt_svd": (st, [vp, vp, i, i, i, d, d, i, P(vp)]),
         "iga_tt_info": (st, [vp, P(C.c_int), P(C.c_int)]),
@@ -171,6 +173,16 @@ class Context:
 
     def last_error(self) -> str:
         return lib().iga_last_error(self.handle).decode()
+
+    def profile_begin(self, kernel: str):
+        _check(self, lib().iga_profile_begin(self.handle, kernel.encode()))
+
+    def profile_end(self):
+        n = C.c_uint64()
+        ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+        _check(self, lib().iga_profile_end(self.handle, C.byref(n), C.byref(ms), C.byref(by),
+                                          C.byref(fl)))
+        return {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
 
 
 class _Keep:
