@@ -158,7 +158,7 @@ def cpu_oracle_sample(work, budget_s=20.0):
         t_slab = float("nan")
     t_asm = t_slab * E / slab
     # --- solve sample on a reduced grid of the same geometry
-    Es = 6
+    Es = 10
     ws = wl.small(work.geometry, p, Es, work.target, beta=work.beta)
     ds = Discretisation(ws.space.degree, ws.space.knots, ws.space.nquad)
     Mb, Kb, b = assemble_band(ws.geometry, ds, ws.target)
