@@ -202,6 +202,31 @@ iga_status iga_amen_local_matvec(iga_ctx* ctx, int r0, int n, int r1, int R0, in
                                  const unsigned char* bandmask, int nvec, const void* x, void* y,
                                  iga_prec prec);
 
+/* Allocation-free variant of iga_amen_local_matvec for callers that cannot
+ * allocate device memory (the paper has no counterpart; it exists for host
+ * applications whose device memory is owned by a fixed pool or budget, and
+ * which therefore can call neither cudaMalloc nor iga_create, which
+ * allocates).  Same arguments and results as iga_amen_local_matvec, except:
+ *   - `stream` is the cudaStream_t to launch on (NULL: legacy default
+ *     stream); no iga_ctx is used and no error text is kept;
+ *   - the intermediates live in a fixed 16 MiB file-scope device array, so
+ *     (R0 + R1) * nvec * r0 * n * r1 * sizeof(element) must not exceed
+ *     16 MiB and R0 * R1 must not exceed 4096 when a bandmask is given;
+ *     larger sizes are rejected with IGA_EINVAL before any GPU work;
+ *   - nothing is allocated or freed: no cudaMalloc, cudaFree or allocating
+ *     library routine is called;
+ *   - the first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture;
+ *   - every call on a device shares the one array, which keeps the previous
+ *     call's contents (each call overwrites what it reads), so calls that
+ *     overlap on the GPU (on different streams, or from several threads
+ *     without ordering) race and give wrong results. */
+iga_status iga_amen_local_matvec_noalloc(void* stream, int r0, int n, int r1, int R0, int R1,
+                                         int p, const void* PhiL, const void* bands,
+                                         const void* PhiR, const unsigned char* bandmask,
+                                         int nvec, const void* x, void* y, iga_prec prec);
+
 /* ---- KKT solve (a6..a8) ---------------------------------------------- */
 
 typedef struct {

@@ -11,10 +11,18 @@
 //   y(a, i, b)        = sum_al sum_a' PhiL[al](a, a') t2[al](a', i, b)          (dense, r0 x r0)
 // nvec independent vectors share one set of interfaces.
 #include <algorithm>
+#include <mutex>
 
 #include "iga_internal.cuh"
 
 namespace iga {
+
+// Fixed device scratch of iga_amen_local_matvec_noalloc.  Every device that
+// loads the library holds these arrays until the process exits.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;   // 16 MiB
+constexpr size_t NOALLOC_MASK_BYTES = 4096;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char g_noalloc_mask[NOALLOC_MASK_BYTES];
 
 template <typename T>
 __global__ void local_right_kernel(const T* __restrict__ PhiR, const T* __restrict__ x, int R1,
@@ -166,4 +174,92 @@ extern "C" iga_status iga_amen_local_matvec(iga_ctx* ctx, int r0, int n, int r1,
     set_error(ctx, e.what());
     return IGA_ECUDA;
   }
+}
+
+// ---- allocation-free variant -------------------------------------------
+//
+// Some callers cannot allocate device memory: code that runs while another
+// component owns every allocation (a host application with its own fixed
+// memory pool, or a memory budget that forbids growth after start-up) and
+// callers that must not create a context of this library because that
+// allocates.  This entry point runs the same three contractions as
+// iga_amen_local_matvec but takes its intermediates from a fixed
+// file-scope device array instead of cudaMalloc.
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_scratch_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+void* g_noalloc_mask_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device addresses of the fixed arrays for the current device, looked up once
+// per device (host code may not use the symbols themselves as addresses).
+iga_status noalloc_addresses(void** scratch, void** mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IGA_ECUDA;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return IGA_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_scratch_ptr[dev]) {
+    void* s = nullptr;
+    void* m = nullptr;
+    if (cudaGetSymbolAddress(&s, g_noalloc_scratch) != cudaSuccess) return IGA_ECUDA;
+    if (cudaGetSymbolAddress(&m, g_noalloc_mask) != cudaSuccess) return IGA_ECUDA;
+    g_noalloc_scratch_ptr[dev] = s;
+    g_noalloc_mask_ptr[dev] = m;
+  }
+  *scratch = g_noalloc_scratch_ptr[dev];
+  *mask = g_noalloc_mask_ptr[dev];
+  return IGA_OK;
+}
+
+template <typename T>
+iga_status noalloc_run(cudaStream_t st, int r0, int n, int r1, int R0, int R1, int p,
+                       const T* PhiL, const T* bands, const T* PhiR, const unsigned char* dmask,
+                       int nv, const T* x, T* y, void* scratch) {
+  size_t per = (size_t)nv * r0 * n * r1;
+  T* t1 = static_cast<T*>(scratch);
+  T* t2 = t1 + per * R1;
+  int th = 256;
+  local_right_kernel<T><<<(unsigned)((R1 * per + th - 1) / th), th, 0, st>>>(PhiR, x, R1, nv, r0,
+                                                                           n, r1, t1);
+  if (cudaGetLastError() != cudaSuccess) return IGA_ECUDA;
+  local_band_kernel<T><<<(unsigned)((R0 * per + th - 1) / th), th, 0, st>>>(
+      bands, dmask, t1, R0, R1, nv, r0, n, r1, p, t2);
+  if (cudaGetLastError() != cudaSuccess) return IGA_ECUDA;
+  local_left_kernel<T><<<(unsigned)((per + th - 1) / th), th, 0, st>>>(PhiL, t2, R0, nv, r0, n,
+                                                                      r1, y);
+  if (cudaGetLastError() != cudaSuccess) return IGA_ECUDA;
+  return IGA_OK;
+}
+}  // namespace
+
+extern "C" iga_status iga_amen_local_matvec_noalloc(void* stream, int r0, int n, int r1, int R0,
+                                                    int R1, int p, const void* PhiL,
+                                                    const void* bands, const void* PhiR,
+                                                    const unsigned char* bandmask, int nvec,
+                                                    const void* x, void* y, iga_prec prec) {
+  if (r0 <= 0 || n <= 0 || r1 <= 0 || R0 <= 0 || R1 <= 0 || p < 0 || nvec <= 0) return IGA_EINVAL;
+  if (!PhiL || !bands || !PhiR || !x || !y || x == y) return IGA_EINVAL;
+  if (prec != IGA_FP64 && prec != IGA_FP32) return IGA_EINVAL;
+  size_t es = prec == IGA_FP64 ? sizeof(double) : sizeof(float);
+  size_t per = (size_t)nvec * r0 * n * r1;
+  if (per * (size_t)(R0 + R1) * es > NOALLOC_SCRATCH_BYTES) return IGA_EINVAL;
+  if (bandmask && (size_t)R0 * R1 > NOALLOC_MASK_BYTES) return IGA_EINVAL;
+  void* scratch = nullptr;
+  void* mask = nullptr;
+  iga_status s = noalloc_addresses(&scratch, &mask);
+  if (s != IGA_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned char* dmask = nullptr;
+  if (bandmask) {
+    if (cudaMemcpyAsync(mask, bandmask, (size_t)R0 * R1, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return IGA_ECUDA;
+    dmask = static_cast<const unsigned char*>(mask);
+  }
+  if (prec == IGA_FP64)
+    return noalloc_run<double>(st, r0, n, r1, R0, R1, p, (const double*)PhiL, (const double*)bands,
+                               (const double*)PhiR, dmask, nvec, (const double*)x, (double*)y,
+                               scratch);
+  return noalloc_run<float>(st, r0, n, r1, R0, R1, p, (const float*)PhiL, (const float*)bands,
+                            (const float*)PhiR, dmask, nvec, (const float*)x, (float*)y, scratch);
 }

@@ -93,6 +93,8 @@ def lib():
         "iga_kron_apply": (st, [vp, vp, d, vp, d, vp, i]),
         "iga_kkt_apply": (st, [vp, vp, vp, d, vp, vp, i]),
         "iga_amen_local_matvec": (st, [vp, i, i, i, i, i, i, vp, vp, vp, vp, i, vp, vp, i]),
+        "iga_amen_local_matvec_noalloc": (st, [vp, i, i, i, i, i, i, vp, vp, vp, vp, i, vp, vp,
+                                               i]),
         "iga_solve_opts_default": (None, [P(SolveOpts_)]),
         "iga_kkt_solve_amen": (st, [vp, vp, vp, vp, d, P(SolveOpts_), vp, vp, vp,
                                     P(SolveInfo_)]),
@@ -367,6 +369,32 @@ def iga_amen_local_matvec(ctx, PhiL, bands, PhiR, x, y, bandmask=None):
     _check(ctx, lib().iga_amen_local_matvec(ctx.handle, r0, n, r1, R0, R1, (b - 1) // 2,
                                             _ptr(PhiL), _ptr(bands), _ptr(PhiR), mask, nvec,
                                             _ptr(x), _ptr(y), _prec(x)))
+    return y
+
+
+def iga_amen_local_matvec_noalloc(PhiL, bands, PhiR, x, y, bandmask=None, stream=None):
+    """Allocation-free local matvec on `stream` (default: torch's current stream).
+
+    Same contraction as iga_amen_local_matvec, using the library's fixed
+    device scratch instead of allocating; raises IgaError (IGA_EINVAL) for
+    sizes beyond that fixed scratch.
+    """
+    import torch
+    R0, r0, _ = PhiL.shape
+    R1, r1, _ = PhiR.shape
+    n, b = bands.shape[2], bands.shape[3]
+    nvec = x.shape[0]
+    mask = None
+    if bandmask is not None:
+        m = np.ascontiguousarray(bandmask, dtype=np.uint8)
+        mask = m.ctypes.data_as(C.POINTER(C.c_ubyte))
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().iga_amen_local_matvec_noalloc(C.c_void_p(s.cuda_stream), r0, n, r1, R0, R1,
+                                             (b - 1) // 2, _ptr(PhiL), _ptr(bands), _ptr(PhiR),
+                                             mask, nvec, _ptr(x), _ptr(y), _prec(x))
+    if st != 0:
+        raise IgaError(st, "iga_amen_local_matvec_noalloc failed (sizes beyond the fixed "
+                           "16 MiB scratch, invalid arguments or a CUDA error)")
     return y
 
 
