@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", type=int, default=2)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -257,6 +257,32 @@ def run_gpu(args, world, rank, local):
     clocks = clk.summary()
     info = state["info"]
 
+    # the other precision path, same workload (solve only, assembly excluded)
+    other = iga.IGA_FP32 if prec == iga.IGA_FP64 else iga.IGA_FP64
+    M, K, load = state["ops"]
+    iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"], state["lam"],
+                           tol=args.tol, precision=other)
+    paths = {}
+    for pr in (prec, other):
+        ts = []
+        for _ in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inf = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"],
+                                         state["lam"], tol=args.tol, precision=pr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        key = "fp64" if pr == iga.IGA_FP64 else "mixed"
+        paths[key] = {"solve_s": statistics.median(ts) / 1e3, "sweeps": inf["sweeps"],
+                      "max_rank": inf["max_rank"], "local_iters": inf["local_iters"],
+                      "residual": inf["residual"], "converged": inf["converged"]}
+    # restore the headline solution in y, u, lam
+    iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"], state["lam"],
+                           tol=args.tol, precision=prec)
+
     # end to end through the public API with host buffers: the geometry and
     # discretisation arrays go host -> device inside the assembly call, the
     # solution (y, u, lambda) comes back into pinned host memory
@@ -314,6 +340,7 @@ def run_gpu(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "solve": {k: info[k] for k in ("sweeps", "refinements", "max_rank", "local_iters",
                                        "residual")},
+        "paths": paths,
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(3 * N * 8)},
         "gpu_launches": int(launches / max(1, args.steps)),

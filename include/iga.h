@@ -231,7 +231,7 @@ iga_status iga_amen_local_matvec_noalloc(void* stream, int r0, int n, int r1, in
 
 typedef struct {
   double tol;          /* stop when ||rhs - KKT z||_2 / ||rhs||_2 <= tol */
-  double inner_tol;    /* AMEn truncation / local tolerance per correction */
+  double inner_tol;    /* tolerance of each AMEn correction (0: tol itself) */
   int max_sweeps;      /* AMEn sweeps per correction */
   int kick_rank;       /* AMEn enrichment rank */
   int rmax;            /* TT rank cap */

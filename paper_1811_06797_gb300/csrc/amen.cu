@@ -213,6 +213,12 @@ __global__ void from_type_kernel(const T* __restrict__ a, double* __restrict__ b
   if (i < n) b[i] = (double)a[i];
 }
 
+template <typename T>
+__global__ void axpy_from_type_kernel(double* __restrict__ y, const T* __restrict__ x, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += (double)x[i];
+}
+
 __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a,
                             size_t n) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -238,18 +244,20 @@ __global__ void scale_by_dev_kernel(T* __restrict__ x, const T* __restrict__ s, 
 //   [[M_ab, 0, K_ab^T], [0, beta M_ab, -M_ab], [K_ab, -M_ab, 0]]
 // is stored node-interleaved (unknown 3 i + l) with kl = ku = 3p + 2 and
 // factorised by Gaussian elimination with partial pivoting inside the band
-// (row-wise window storage, width 2 kl + ku + 1; multipliers stored without
+// (row-wise window storage of width 2 kl + ku + 1; multipliers stored without
 // later interchanges, as in the unblocked banded LU of the textbooks).
-// One thread owns one block; element (blk, row, w) lives at
-// ((row * W + w) * NB + blk) so that a warp touches consecutive addresses.
+// One warp owns one block: the pivot search is a warp arg-max, the row swap
+// and the rank-1 update of the (kl x (kl + ku)) window are spread over the
+// lanes.  The factor is built in shared memory when it fits and written to
+// global memory as [block][row][w].
 
 struct BandLayout {
   int n, p, kl, ku, W, N, NB, r0, r1;
 };
 
 template <typename T>
-__device__ __forceinline__ T& bel(T* A, const BandLayout& L, int blk, int row, int col) {
-  return A[((size_t)row * L.W + (col - row + L.kl)) * L.NB + blk];
+__device__ __forceinline__ T& bwin(T* A, const BandLayout& L, int row, int col) {
+  return A[(size_t)row * L.W + (col - row + L.kl)];
 }
 
 template <typename T>
@@ -260,93 +268,131 @@ __global__ void kkt_block_factor_kernel(
     const T* __restrict__ bandK, const int* __restrict__ nzK_l, const int* __restrict__ nzK_r,
     const long long* __restrict__ nzK_off, int nnzK,
     const T* __restrict__ dLM, const T* __restrict__ dRM, const T* __restrict__ dLK,
-    const T* __restrict__ dRK, T* __restrict__ A, int* __restrict__ piv, int* __restrict__ flag) {
-  int blk = blockIdx.x * blockDim.x + threadIdx.x;
+    const T* __restrict__ dRK, T* __restrict__ Aout, int* __restrict__ piv, int* __restrict__ flag,
+    int use_smem) {
+  extern __shared__ unsigned char smraw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int blk = blockIdx.x * wpb + warp;
   if (blk >= L.NB) return;
-  int a = blk / L.r1, b = blk % L.r1;
+  const size_t per = (size_t)L.N * L.W;
+  T* A = use_smem ? reinterpret_cast<T*>(smraw) + (size_t)warp * per : Aout + (size_t)blk * per;
+  const int a = blk / L.r1, b = blk % L.r1;
   const int n = L.n, p = L.p, B = 2 * p + 1;
-  // zero the band storage of this block
-  for (int row = 0; row < L.N; ++row)
-    for (int w = 0; w < L.W; ++w) A[((size_t)row * L.W + w) * L.NB + blk] = T(0);
-  // assemble
-  for (int i = 0; i < n; ++i) {
-    for (int o = 0; o < B; ++o) {
-      int j = i + o - p;
-      if (j < 0 || j >= n) continue;
-      T m = T(0), k = T(0), kt = T(0);
-      for (int z = 0; z < nnzM; ++z)
-        m += dLM[(size_t)nzM_l[z] * L.r0 + a] * dRM[(size_t)nzM_r[z] * L.r1 + b] *
-             bandM[nzM_off[z] + (size_t)i * B + o];
-      for (int z = 0; z < nnzK; ++z) {
-        T s = dLK[(size_t)nzK_l[z] * L.r0 + a] * dRK[(size_t)nzK_r[z] * L.r1 + b];
-        k += s * bandK[nzK_off[z] + (size_t)i * B + o];
-        // K^T (i, j) = K (j, i): band entry of row j at offset i - j + p
-        kt += s * bandK[nzK_off[z] + (size_t)j * B + (i - j + p)];
-      }
-      bel(A, L, blk, 3 * i + 0, 3 * j + 0) += m;
-      bel(A, L, blk, 3 * i + 0, 3 * j + 2) += kt;
-      bel(A, L, blk, 3 * i + 1, 3 * j + 1) += beta * m;
-      bel(A, L, blk, 3 * i + 1, 3 * j + 2) += -m;
-      bel(A, L, blk, 3 * i + 2, 3 * j + 0) += k;
-      bel(A, L, blk, 3 * i + 2, 3 * j + 1) += -m;
+  for (size_t e = lane; e < per; e += 32) A[e] = T(0);
+  __syncwarp();
+  // assemble the block: every (i, o) writes six distinct entries
+  for (int e = lane; e < n * B; e += 32) {
+    int i = e / B, o = e - i * B;
+    int j = i + o - p;
+    if (j < 0 || j >= n) continue;
+    T m = T(0), k = T(0), kt = T(0);
+    for (int z = 0; z < nnzM; ++z)
+      m += dLM[(size_t)nzM_l[z] * L.r0 + a] * dRM[(size_t)nzM_r[z] * L.r1 + b] *
+           bandM[nzM_off[z] + (size_t)i * B + o];
+    for (int z = 0; z < nnzK; ++z) {
+      T s = dLK[(size_t)nzK_l[z] * L.r0 + a] * dRK[(size_t)nzK_r[z] * L.r1 + b];
+      k += s * bandK[nzK_off[z] + (size_t)i * B + o];
+      kt += s * bandK[nzK_off[z] + (size_t)j * B + (i - j + p)];    // K^T(i,j) = K(j,i)
     }
+    bwin(A, L, 3 * i + 0, 3 * j + 0) = m;
+    bwin(A, L, 3 * i + 0, 3 * j + 2) = kt;
+    bwin(A, L, 3 * i + 1, 3 * j + 1) = beta * m;
+    bwin(A, L, 3 * i + 1, 3 * j + 2) = -m;
+    bwin(A, L, 3 * i + 2, 3 * j + 0) = k;
+    bwin(A, L, 3 * i + 2, 3 * j + 1) = -m;
   }
-  // banded LU with partial pivoting
+  __syncwarp();
   const int N = L.N, kl = L.kl, ku = L.ku;
+  int* pv = piv + (size_t)blk * N;
   for (int k = 0; k < N; ++k) {
-    int last = min(N - 1, k + kl);
-    int pr = k;
-    T best = fabs(bel(A, L, blk, k, k));
-    for (int i = k + 1; i <= last; ++i) {
-      T v = fabs(bel(A, L, blk, i, k));
-      if (v > best) { best = v; pr = i; }
+    const int last = min(N - 1, k + kl);
+    const int cnt = last - k + 1;
+    T v = T(-1);
+    int idx = k;
+    if (lane < cnt) { v = fabs(bwin(A, L, k + lane, k)); idx = k + lane; }
+    for (int off = 16; off > 0; off >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, v, off);
+      int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
     }
-    piv[(size_t)k * L.NB + blk] = pr;
-    int jend = min(N - 1, k + kl + ku);
-    if (pr != k)
-      for (int j = k; j <= jend; ++j) {
-        T t = bel(A, L, blk, k, j);
-        bel(A, L, blk, k, j) = bel(A, L, blk, pr, j);
-        bel(A, L, blk, pr, j) = t;
+    const int pr = idx;
+    const int jend = min(N - 1, k + kl + ku);
+    if (lane == 0) pv[k] = pr;
+    if (pr != k) {
+      for (int j = k + lane; j <= jend; j += 32) {
+        T t = bwin(A, L, k, j);
+        bwin(A, L, k, j) = bwin(A, L, pr, j);
+        bwin(A, L, pr, j) = t;
       }
-    T d = bel(A, L, blk, k, k);
-    if (d == T(0)) { atomicOr(flag, 2); continue; }
-    for (int i = k + 1; i <= last; ++i) {
-      T l = bel(A, L, blk, i, k) / d;
-      bel(A, L, blk, i, k) = l;
-      if (l != T(0))
-        for (int j = k + 1; j <= jend; ++j) bel(A, L, blk, i, j) -= l * bel(A, L, blk, k, j);
     }
+    __syncwarp();
+    const T d = bwin(A, L, k, k);
+    if (d == T(0)) {
+      if (lane == 0) atomicOr(flag, 2);
+      continue;
+    }
+    for (int t = 1 + lane; t < cnt; t += 32) bwin(A, L, k + t, k) /= d;
+    __syncwarp();
+    const int rows = cnt - 1, width = jend - k;
+    for (int e = lane; e < rows * width; e += 32) {
+      int i = k + 1 + e / width, j = k + 1 + e % width;
+      bwin(A, L, i, j) -= bwin(A, L, i, k) * bwin(A, L, k, j);
+    }
+    __syncwarp();
+  }
+  if (use_smem) {
+    T* G = Aout + (size_t)blk * per;
+    for (size_t e = lane; e < per; e += 32) G[e] = A[e];
   }
 }
 
-// solve every block system in place; the right-hand side of block (a, b) is
-// v[l](a, i, b) of a (3, r0, n, r1) tensor (node-interleaved as 3 i + l)
+// Solve every block system in place; the right-hand side of block (a, b) is
+// v[l](a, i, b) of a (3, r0, n, r1) tensor (node-interleaved as 3 i + l).
+// One warp per block, the working vector in shared memory.
 template <typename T>
-__global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ A,
+__global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
                                        const int* __restrict__ piv, T* __restrict__ v) {
-  int blk = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ unsigned char smraw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int blk = blockIdx.x * wpb + warp;
   if (blk >= L.NB) return;
-  int a = blk / L.r1, b = blk % L.r1;
-  const int n = L.n, N = L.N, kl = L.kl, ku = L.ku;
-  size_t comp = (size_t)L.r0 * n * L.r1;
-  auto at = [&](int I) -> T& {
+  const int N = L.N, n = L.n, kl = L.kl, ku = L.ku;
+  T* s = reinterpret_cast<T*>(smraw) + (size_t)warp * N;
+  const T* A = Aall + (size_t)blk * N * L.W;
+  const int* pv = piv + (size_t)blk * N;
+  const int a = blk / L.r1, b = blk % L.r1;
+  const size_t comp = (size_t)L.r0 * n * L.r1;
+  for (int I = lane; I < N; I += 32) {
     int i = I / 3, l = I - 3 * i;
-    return v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b];
-  };
+    s[I] = v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b];
+  }
+  __syncwarp();
   for (int k = 0; k < N; ++k) {
-    int pr = piv[(size_t)k * L.NB + blk];
-    if (pr != k) { T t = at(k); at(k) = at(pr); at(pr) = t; }
-    T bk = at(k);
-    int last = min(N - 1, k + kl);
-    for (int i = k + 1; i <= last; ++i) at(i) -= bel(const_cast<T*>(A), L, blk, i, k) * bk;
+    const int pr = pv[k];
+    T sk = s[pr];
+    __syncwarp();
+    if (pr != k && lane == 0) { s[pr] = s[k]; s[k] = sk; }
+    __syncwarp();
+    const int last = min(N - 1, k + kl);
+    for (int t = 1 + lane; t <= last - k; t += 32) s[k + t] -= A[(size_t)(k + t) * L.W + (k - (k + t) + kl)] * sk;
+    __syncwarp();
   }
   for (int k = N - 1; k >= 0; --k) {
-    T s = at(k);
-    int jend = min(N - 1, k + kl + ku);
-    for (int j = k + 1; j <= jend; ++j) s -= bel(const_cast<T*>(A), L, blk, k, j) * at(j);
-    T d = bel(const_cast<T*>(A), L, blk, k, k);
-    at(k) = d != T(0) ? s / d : T(0);
+    const int jend = min(N - 1, k + kl + ku);
+    T part = T(0);
+    for (int j = k + 1 + lane; j <= jend; j += 32) part += A[(size_t)k * L.W + (j - k + kl)] * s[j];
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (lane == 0) {
+      T d = A[(size_t)k * L.W + kl];
+      s[k] = d != T(0) ? (s[k] - part) / d : T(0);
+    }
+    __syncwarp();
+  }
+  for (int I = lane; I < N; I += 32) {
+    int i = I / 3, l = I - 3 * i;
+    v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b] = s[I];
   }
 }
 
@@ -718,24 +764,41 @@ struct Solver {
     size_t L;                            // per component
   };
 
-  void local_op(const Local& c, const T* x, T* y) {
+  // local KKT operator applied with interfaces PL/PR and bands of type U:
+  // out = [M y + K lam, beta M u - M lam, K y - M u]
+  template <typename U>
+  void local_op_u(const Local& c, const U* const PL[2], const U* const PR[2], const U* x, U* y,
+                  int sb) {
     size_t per = (size_t)3 * c.L;
-    T* Mv = tslot(20, per);
-    T* Kv = tslot(21, per);
+    U* Mv = scratch<U>(ctx, SLOT_AMEN_BASE + sb, per);
+    U* Kv = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 1, per);
     for (int o = 0; o < 2; ++o) {
       const CoreNZ& z = nz[o][c.d];
-      T* t1 = tslot(22, per * z.R1);
-      T* t2 = tslot(23, per * z.R0);
-      T* out = o ? Kv : Mv;
-      IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per * z.R1), 256, 0, PRt[o].p, x, z.R1, 3, c.r0,
+      U* t1 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 2, per * z.R1);
+      U* t2 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 3, per * z.R0);
+      U* out = o ? Kv : Mv;
+      IGA_LAUNCH(ctx, right_mult_kernel<U>, nblk(per * z.R1), 256, 0, PR[o], x, z.R1, 3, c.r0,
                  c.nn, c.r1, 0, t1);
-      IGA_LAUNCH(ctx, band_group_kernel<T>, nblk(per * z.R0), 256, 0, bands_of<T>(op[o], c.d),
+      IGA_LAUNCH(ctx, band_group_kernel<U>, nblk(per * z.R0), 256, 0, bands_of<U>(op[o], c.d),
                  z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, 3 * c.r0, c.nn, c.r1,
                  op[o]->p[c.d], t2);
-      IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, PLt[o].p, t2, z.R0, 3, c.r0, c.nn,
+      IGA_LAUNCH(ctx, left_mult_kernel<U>, nblk(per), 256, 0, PL[o], t2, z.R0, 3, c.r0, c.nn,
                  c.r1, 0, out);
     }
-    IGA_LAUNCH(ctx, kkt_combine_kernel<T>, nblk(c.L), 256, 0, Mv, Kv, c.L, (T)beta, y);
+    IGA_LAUNCH(ctx, kkt_combine_kernel<U>, nblk(c.L), 256, 0, Mv, Kv, c.L, (U)beta, y);
+  }
+
+  void local_op(const Local& c, const T* x, T* y) {
+    const T* PL[2] = {PLt[0].p, PLt[1].p};
+    const T* PR[2] = {PRt[0].p, PRt[1].p};
+    local_op_u<T>(c, PL, PR, x, y, 20);
+  }
+
+  // FP64 local operator on the FP64 interfaces (for local iterative refinement)
+  void local_op64(const Local& c, const double* x, double* y) {
+    const double* PL[2] = {PhiL[0][c.d].p, PhiL[1][c.d].p};
+    const double* PR[2] = {PhiR[0][c.d].p, PhiR[1][c.d].p};
+    local_op_u<double>(c, PL, PR, x, y, 70);
   }
 
   // ---- preconditioner
@@ -806,10 +869,21 @@ struct Solver {
     T* A = tslot(48, (size_t)BL.N * BL.W * BL.NB);
     int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, (size_t)BL.N * BL.NB);
     IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
-    IGA_LAUNCH(ctx, kkt_block_factor_kernel<T>, nblk(BL.NB, 64), 64, 0, BL, (T)beta,
+    size_t perw = (size_t)BL.N * BL.W * sizeof(T);
+    int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perw));
+    int use_smem = perw <= 200 * 1024;
+    size_t smem = use_smem ? perw * wpb : 0;
+    if (!use_smem) wpb = 4;
+    static bool attr = false;
+    if (!attr) {
+      IGA_CUDA(cudaFuncSetAttribute(kkt_block_factor_kernel<T>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+      attr = true;
+    }
+    IGA_LAUNCH(ctx, kkt_block_factor_kernel<T>, nblk(BL.NB, wpb), 32 * wpb, smem, BL, (T)beta,
                bands_of<T>(op[0], c.d), zM.dl.p, zM.dr.p, zM.doff.p, (int)zM.l.size(),
                bands_of<T>(op[1], c.d), zK.dl.p, zK.dr.p, zK.doff.p, (int)zK.l.size(), tdLM, tdRM,
-               tdLK, tdRK, A, piv, ctx->dflag);
+               tdLK, tdRK, A, piv, ctx->dflag, use_smem);
   }
 
   void precond_apply(const Local& c, const T* v, T* z) {
@@ -820,7 +894,17 @@ struct Solver {
     // w = VL^T v VR
     IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
     IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
-    IGA_LAUNCH(ctx, kkt_block_solve_kernel<T>, nblk(BL.NB, 64), 64, 0, BL, A, piv, z);
+    {
+      const int wpb = 4;
+      static bool attr = false;
+      if (!attr) {
+        IGA_CUDA(cudaFuncSetAttribute(kkt_block_solve_kernel<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+        attr = true;
+      }
+      IGA_LAUNCH(ctx, kkt_block_solve_kernel<T>, nblk(BL.NB, wpb), 32 * wpb,
+                 (size_t)wpb * BL.N * sizeof(T), BL, A, piv, z);
+    }
     // back: VL z VR^T
     IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, z, 1, 3, c.r0, c.nn, c.r1, 1, t);
     IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 1, z);
@@ -955,8 +1039,33 @@ struct Solver {
     // warm start from the current block core
     Xh.ensure(per);
     IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, Xh.p, xt, per);
-    local_iters += gmres(c, bt, xt, tol_abs, maxit);
-    IGA_LAUNCH(ctx, from_type_kernel<T>, nblk(per), 256, 0, xt, Xh.p, per);
+    if constexpr (sizeof(T) == 8) {
+      local_iters += gmres(c, bt, xt, tol_abs, maxit);
+      IGA_LAUNCH(ctx, from_type_kernel<T>, nblk(per), 256, 0, xt, Xh.p, per);
+    } else {
+      // FP32 Krylov solves with FP64 local iterative refinement: the local
+      // residual is formed with the FP64 interfaces and bands, and FP32
+      // corrections are added to the FP64 block core until it meets tol_abs
+      // refine well below the SVD truncation threshold so that FP32 round-off
+      // in the block core does not show up as extra TT rank
+      double rn = device_norm2(ctx, rhs, per);
+      double tref = std::min(tol_abs, 1e-9 * rn);
+      double t32 = std::max(tref, 2e-6 * rn);
+      local_iters += gmres(c, bt, xt, t32, maxit);
+      IGA_LAUNCH(ctx, from_type_kernel<T>, nblk(per), 256, 0, xt, Xh.p, per);
+      double* r64 = slot(15 + 60, per);
+      double* ax = slot(16 + 60, per);
+      for (int it = 0; it < 4; ++it) {
+        local_op64(c, Xh.p, ax);
+        IGA_LAUNCH(ctx, sub_kernel, nblk(per), 256, 0, rhs, ax, r64, per);
+        double res = device_norm2(ctx, r64, per);
+        if (res <= tref || !std::isfinite(res)) break;
+        IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, r64, bt, per);
+        IGA_CUDA(cudaMemsetAsync(xt, 0, per * sizeof(T), ctx->stream));
+        local_iters += gmres(c, bt, xt, std::max(tref, 2e-6 * res), maxit);
+        IGA_LAUNCH(ctx, axpy_from_type_kernel<T>, nblk(per), 256, 0, Xh.p, xt, per);
+      }
+    }
   }
 };
 
@@ -1065,13 +1174,13 @@ using namespace iga;
 extern "C" void iga_solve_opts_default(iga_solve_opts* o) {
   if (!o) return;
   o->tol = 1e-6;
-  o->inner_tol = 1e-3;
+  o->inner_tol = 0.0;     // 0: each AMEn correction aims at tol directly
   o->max_sweeps = 8;
   o->kick_rank = 4;
   o->rmax = 160;
   o->local_maxit = 400;
   o->refine_max = 8;
-  o->precision = IGA_FP32;
+  o->precision = IGA_FP64;
   o->verbose = 0;
 }
 
@@ -1088,7 +1197,7 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
       IGA_REQUIRE(M->n[d] == K->n[d] && M->p[d] == K->p[d], "kkt_solve_amen: M, K mismatch");
     iga_solve_opts o;
     if (opts) o = *opts; else iga_solve_opts_default(&o);
-    IGA_REQUIRE(o.tol > 0.0 && o.inner_tol > 0.0, "kkt_solve_amen: tolerances must be > 0");
+    IGA_REQUIRE(o.tol > 0.0 && o.inner_tol >= 0.0, "kkt_solve_amen: bad tolerances");
     IGA_REQUIRE(o.precision == IGA_FP64 || o.precision == IGA_FP32,
                 "kkt_solve_amen: precision must be IGA_FP64 or IGA_FP32");
     IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
@@ -1112,7 +1221,7 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     if (!ok) {
       double rn = Fn;
       IGA_CUDA(cudaMemcpyAsync(r, F, 3 * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-      double inner = o.precision == IGA_FP64 ? o.tol : std::max(o.inner_tol, o.tol);
+      double inner = std::max(o.inner_tol, o.tol);
       for (int it = 0; it <= o.refine_max; ++it) {
         rel = rn / Fn;
         if (rel <= o.tol) { ok = true; break; }

@@ -188,6 +188,12 @@ static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T bet
     maxT3 = std::min(maxT3, m3);
   }
   int nchunks = (g.n3 + maxT3 - 1) / maxT3;
+  {
+    // enough CTAs to cover every SM twice, down to i3 tiles of 16
+    int base = ((g.n1 + g.T1 - 1) / g.T1) * ((g.n2 + g.T2 - 1) / g.T2);
+    int maxchunks = std::max(1, (g.n3 + 15) / 16);
+    while (base * nchunks < 2 * 152 && nchunks < maxchunks) ++nchunks;
+  }
   g.T3 = (g.n3 + nchunks - 1) / nchunks;
   g.nt2 = (g.n2 + g.T2 - 1) / g.T2;
   g.nt3 = (g.n3 + g.T3 - 1) / g.T3;

@@ -185,11 +185,13 @@ void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
 // Symmetric A (k x k, col-major) -> eigenvalues w (descending) and
 // eigenvectors V (columns).  Cyclic Jacobi with round-robin parallel
 // ordering: each round applies k/2 disjoint rotations (rows, then columns).
-// At most 40 sweeps; stops when the off-diagonal norm is below 1e-15 times
-// the Frobenius norm.  A is overwritten.
+// At most 40 sweeps; stops when the off-diagonal norm is below 1e-14 times
+// the Frobenius norm.  A is overwritten.  Storage: mode 2 keeps A and V in
+// shared memory, mode 1 keeps A in shared memory and V in global memory,
+// mode 0 keeps both in global memory.
 __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ Vwork,
                                   double* __restrict__ Vout, double* __restrict__ w, int k,
-                                  int use_smem) {
+                                  int mode) {
   extern __shared__ double sm[];
   int kk = k + (k & 1);
   int npair = kk / 2;
@@ -197,14 +199,14 @@ __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ 
   double* sn = sm + npair;         // npair
   int* pp = (int*)(sm + 2 * npair);
   int* qq = pp + npair;
-  double* red = sm + 2 * npair + npair + 1;   // 32 doubles, after 2*npair ints (npair+1 dbl)
+  double* red = sm + 2 * npair + npair + 1;   // 32 doubles
   double* A = Ag;
   double* V = Vwork;
-  if (use_smem) {
+  if (mode >= 1) {
     A = red + 32;
-    V = A + (size_t)k * k;
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) A[t] = Ag[t];
   }
+  if (mode == 2) V = A + (size_t)k * k;
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) V[t] = ((t % k) == (t / k)) ? 1.0 : 0.0;
   __syncthreads();
   double fro2 = 0.0;
@@ -215,7 +217,7 @@ __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ 
     for (int t = threadIdx.x; t < k * k; t += blockDim.x)
       if ((t % k) != (t / k)) off2 += A[t] * A[t];
     off2 = block_sum(off2, red);
-    if (off2 <= 1e-30 * fro2 || off2 == 0.0) break;
+    if (off2 <= 1e-28 * fro2 || off2 == 0.0) break;
     for (int r = 0; r < kk - 1; ++r) {
       for (int i = threadIdx.x; i < npair; i += blockDim.x) {
         int p, q;
@@ -225,8 +227,8 @@ __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ 
         double c = 1.0, s = 0.0;
         if (q < k) {
           double apq = A[(size_t)q * k + p];
-          if (apq != 0.0) {
-            double app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
+          double app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
+          if (apq != 0.0 && fabs(apq) > 1e-300 + 1e-17 * sqrt(fabs(app * aqq))) {
             double tau = (aqq - app) / (2.0 * apq);
             double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
                                     : -1.0 / (-tau + sqrt(1.0 + tau * tau));
@@ -240,8 +242,8 @@ __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ 
       // rows p, q of A:  a_p <- c a_p - s a_q,  a_q <- s a_p + c a_q
       for (int t = threadIdx.x; t < npair * k; t += blockDim.x) {
         int i = t / k, col = t % k;
+        if (sn[i] == 0.0) continue;
         int p = pp[i], q = qq[i];
-        if (q >= k || sn[i] == 0.0) continue;
         double c = cs[i], s = sn[i];
         double ap = A[(size_t)col * k + p], aq = A[(size_t)col * k + q];
         A[(size_t)col * k + p] = c * ap - s * aq;
@@ -251,8 +253,8 @@ __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ 
       // columns p, q of A and V
       for (int t = threadIdx.x; t < npair * k; t += blockDim.x) {
         int i = t / k, row = t % k;
+        if (sn[i] == 0.0) continue;
         int p = pp[i], q = qq[i];
-        if (q >= k || sn[i] == 0.0) continue;
         double c = cs[i], s = sn[i];
         double ap = A[(size_t)p * k + row], aq = A[(size_t)q * k + row];
         A[(size_t)p * k + row] = c * ap - s * aq;
@@ -280,19 +282,23 @@ __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ 
 }
 
 void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k) {
-  IGA_REQUIRE(k >= 1 && k <= 512, "jacobi_eig: k out of range");
+  IGA_REQUIRE(k >= 1 && k <= 1024, "jacobi_eig: k out of range");
   int kk = k + (k & 1);
   size_t head = (size_t)(2 * (kk / 2) + (kk / 2) + 1 + 32) * sizeof(double);
-  size_t full = head + 2 * (size_t)k * k * sizeof(double);
-  int use_smem = full <= 200 * 1024;
-  size_t smem = use_smem ? full : head;
-  // without shared memory the rotations accumulate in a global work array and
-  // the sorted eigenvectors are scattered from there into V
-  double* Vw = use_smem ? nullptr : scratch<double>(ctx, SLOT_MISC1, (size_t)k * k);
-  if (smem > 48 * 1024)
+  size_t one = (size_t)k * k * sizeof(double);
+  const size_t limit = 220 * 1024;
+  int mode = head + 2 * one <= limit ? 2 : (head + one <= limit ? 1 : 0);
+  size_t smem = head + (mode == 2 ? 2 * one : (mode == 1 ? one : 0));
+  // with V outside shared memory the rotations accumulate in a global work
+  // array and the sorted eigenvectors are scattered from there into V
+  double* Vw = mode == 2 ? nullptr : scratch<double>(ctx, SLOT_MISC1, (size_t)k * k);
+  static bool attr = false;
+  if (!attr) {
     IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-  IGA_LAUNCH(ctx, jacobi_eig_kernel, 1, 512, smem, A, Vw, V, w, k, use_smem);
+                                  (int)limit));
+    attr = true;
+  }
+  IGA_LAUNCH(ctx, jacobi_eig_kernel, 1, 1024, smem, A, Vw, V, w, k, mode);
 }
 
 // ----------------------------------------------------------------- TT-SVD

@@ -44,6 +44,9 @@ CASES = [
                          wl.Target(wl.TARGET_GAUSS, wl.ANNULUS_CENTROID, 0.1), beta=1e-4, tol=1e-12)),
     ("twisted", wl.small(wl.quarter_annulus(twist=math.pi / 4), 2, 9,
                          wl.Target(wl.TARGET_GAUSS, wl.ANNULUS_CENTROID, 0.1), beta=1e-3, tol=1e-12)),
+    # TT-matrix operators with weight ranks > 1 (random cubic volume)
+    ("random", wl.small(wl.random_volume(), 2, 6, wl.Target(wl.TARGET_SINPROD), beta=1e-4,
+                        tol=1e-12)),
 ]
 
 
@@ -76,3 +79,18 @@ def test_solve_reports_no_convergence(env):
     work = CASES[2][1]
     info, *_ = _solve(env, work, tol=1e-12, refine_max=0, max_sweeps=1)
     assert not info["converged"] and info["residual"] > 1e-12
+
+
+def test_random_volume_truncated_operator(env):
+    """Weights truncated at 1e-6: the solve matches the direct solve of the
+    oracle's exact matrices up to the truncation error of the operator."""
+    ctx, torch, iga = env
+    work = wl.small(wl.random_volume(), 2, 6, wl.Target(wl.TARGET_SINPROD), beta=1e-3, tol=1e-6)
+    info, y, u, lam = _solve(env, work, tol=1e-9, precision=0)
+    assert info["converged"], info
+    M, K, b = _oracle_system(work)
+    yo, uo, lo = kkt_solve(M, K, work.beta, b)
+    assert _rel(y, yo) < 1e-4 and _rel(lam, lo) < 1e-4
+    # and the operator really has TT ranks above one
+    Mop, Kop, _ = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    assert max(Mop.info()["R"]) > 1
