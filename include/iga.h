@@ -159,6 +159,27 @@ iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga
                                 const iga_target* target, double tol, iga_op** M, iga_op** K,
                                 iga_tt** load);
 
+/* The eight sampled weights of the composite assembly as TT tensors on the
+ * Gauss grid (Sec. 3: omega g, q11 g, q12 g, q13 g, q22 g, q23 g, q33 g and
+ * the load density yhat(G) omega g), truncated as in iga_lowrank_assemble.
+ * out[c] is NULL for a rank-0 (zero) tensor.  Library-owned. */
+iga_status iga_weight_tts(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                          const iga_target* target, double tol, iga_tt* out[8]);
+/* TT from device cores (copied): core d has shape (r_{d-1}, n_d, r_d),
+ * r_0 = r_3 = 1. */
+iga_status iga_tt_from_cores(iga_ctx* ctx, const int n[3], const int r[2],
+                             const double* const cores[3], iga_tt** out);
+/* Dirichlet-reduced M and K from weight TTs on the Gauss grid of `space`
+ * (weights[0] = omega g, weights[1..6] = q11, q12, q13, q22, q23, q33 times
+ * g, NULL = zero weight): the univariate assembly step alone (Sec. 3, eqs.
+ * massFinal and stiffnessFinal, with q_lk = q_kl). */
+iga_status iga_ops_from_weights(iga_ctx* ctx, const iga_space* space,
+                                const iga_tt* const weights[7], iga_op** M, iga_op** K);
+/* Load vector TT from the TT of the load density (sampled yhat(G) omega g):
+ * b_i = sum_{e,q} f(e, q) beta_i(x_eq) per direction, Dirichlet-reduced. */
+iga_status iga_load_from_density(iga_ctx* ctx, const iga_space* space, const iga_tt* density,
+                                 iga_tt** load);
+
 /* Operator structure: interior sizes n[3], degrees p[3], number of blocks
  * (one per TT weight term group), summed TT-matrix ranks R[2] and device
  * bytes of its factors. */
@@ -226,6 +247,42 @@ iga_status iga_amen_local_matvec_noalloc(void* stream, int r0, int n, int r1, in
                                          int p, const void* PhiL, const void* bands,
                                          const void* PhiR, const unsigned char* bandmask,
                                          int nvec, const void* x, void* y, iga_prec prec);
+
+/* ---- adjoint / gradient (a9) ----------------------------------------- */
+
+/* Solve A x = b for A = M or A = K (both symmetric positive definite after
+ * the Dirichlet reduction) by preconditioned conjugate gradients in FP64.
+ * The preconditioner is the fast-diagonalisation inverse of
+ * sum_d c_d Kt_d (x) Mt_e (x) Mt_f built from the mass factors of M and the
+ * derivative factors of the q_dd blocks of K (K may be NULL when A == M).
+ * x holds the initial guess on entry.  b, x: device, length N.  Returns
+ * IGA_ENOCONV when ||b - A x|| > tol ||b|| after maxit iterations. */
+iga_status iga_spd_solve(iga_ctx* ctx, const iga_op* A, const iga_op* M, const iga_op* K,
+                         const double* b, double* x, double tol, int maxit, int* iters,
+                         double* relres);
+
+/* Reduced objective and gradient for nbatch controls (Sec. 4, Lagrangian
+ * and KKT conditions, stationary reading): for each control u_s
+ *   K y = M u,  K^T lam = b - M y,  grad = beta M u - M lam,
+ *   J = 1/2 y^T M y - b^T y + beta/2 u^T M u (without the constant
+ *   1/2 int yhat^2 omega).
+ * u, grad, y, lam: device (nbatch, N); J: host (nbatch).  The state and
+ * adjoint solves run to relative residual tol. */
+iga_status iga_reduced_gradient(iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                                const iga_tt* load, double beta, int nbatch, const double* u,
+                                double tol, double* grad, double* y, double* lam, double* J);
+
+/* Derivative of the reduced objective with respect to the univariate weight
+ * factors (the reverse of the univariate assembly, Sec. 3 eq. massMatrix1D):
+ * for the TT of every weight c (omega, q11, q12, q13, q22, q23, q33) with
+ * ranks (1, 1) and every direction d, grad_w[c][d][e*nquad + q] =
+ * dJ/dw_{c,d}(e, q) at the state y, control u and adjoint lam returned by
+ * iga_reduced_gradient (the load vector is held fixed).  grad_w: device,
+ * 7 * (Q1 + Q2 + Q3) doubles, Q_d = E_d nquad; weights absent from M and K
+ * get zeros.  Every block of M and K must have TT ranks (1, 1). */
+iga_status iga_weight_gradient(iga_ctx* ctx, const iga_space* space, const iga_op* M,
+                               const iga_op* K, double beta, const double* y, const double* u,
+                               const double* lam, double* grad_w);
 
 /* ---- KKT solve (a6..a8) ---------------------------------------------- */
 

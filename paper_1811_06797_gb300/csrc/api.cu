@@ -198,6 +198,67 @@ void kkt_apply_internal(iga_ctx* ctx, const iga_op* M, const iga_op* K, double b
   kkt_apply_impl(ctx, M, K, beta, z, out, prec);
 }
 
+// Sample the eight weight tensors and TT-compress them (Sec. 3): omega g,
+// the six entries of Q g (truncated relative to ||Q||_F over all nine
+// entries), and the load density yhat(G) omega g.  Rank-0 tensors stay NULL.
+void weight_tts_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+                     const iga_target* target, double tol, iga_tt* tts[8]) {
+  int Q[3];
+  for (int d = 0; d < 3; ++d) Q[d] = st.dir[d].E * st.dir[d].q;
+  size_t S = (size_t)Q[0] * Q[1] * Q[2];
+  double* samples = scratch<double>(ctx, SLOT_ASM_SAMPLES, 8 * S);
+  sample_weights_impl(ctx, geo, st, target, samples);
+  double qn2 = 0.0;
+  for (int c = 1; c <= 6; ++c) {
+    double v = device_norm2(ctx, samples + c * S, S);
+    qn2 += (c == 2 || c == 3 || c == 5) ? 2 * v * v : v * v;
+  }
+  double qnorm = std::sqrt(qn2);
+  try {
+    tt_svd3(ctx, samples, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[0]);
+    for (int c = 1; c <= 6; ++c)
+      tt_svd3(ctx, samples + c * S, Q[0], Q[1], Q[2], tol, qnorm, 0, &tts[c]);
+    if (target && target->kind != IGA_TARGET_ZERO)
+      tt_svd3(ctx, samples + 7 * S, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[7]);
+  } catch (...) {
+    for (int c = 0; c < 8; ++c) { delete tts[c]; tts[c] = nullptr; }
+    throw;
+  }
+}
+
+// M from the TT of omega g; K from the TTs of q_kl g with the derivative
+// pattern delta(l,d) on the row and delta(k,d) on the column factor
+// (Sec. 3, eqs. massFinal and stiffnessFinal); q_lk shares the TT of q_kl.
+void ops_from_weights_impl(iga_ctx* ctx, const SpaceTables& st, const iga_tt* const w[7],
+                           iga_op** M, iga_op** K) {
+  IGA_REQUIRE(w[0] != nullptr, "operators: omega weight missing");
+  OpBuilder bm, bk;
+  int dm[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  add_block(ctx, st, w[0], dm, bm);
+  const int qidx[3][3] = {{1, 2, 3}, {2, 4, 5}, {3, 5, 6}};
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      const iga_tt* t = w[qidx[k][l]];
+      if (!t) continue;
+      int dk[3][2];
+      for (int d = 0; d < 3; ++d) {
+        dk[d][0] = (l == d);
+        dk[d][1] = (k == d);
+      }
+      add_block(ctx, st, t, dk, bk);
+    }
+  iga_op* m = finish_op(ctx, st, bm);
+  iga_op* kk = nullptr;
+  try {
+    kk = finish_op(ctx, st, bk);
+  } catch (...) {
+    delete m;
+    throw;
+  }
+  *M = m;
+  *K = kk;
+}
+
 }  // namespace iga
 
 using namespace iga;
@@ -341,6 +402,78 @@ iga_status iga_assemble_bands(iga_ctx* ctx, const iga_space* space, int d, const
   })
 }
 
+iga_status iga_weight_tts(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                          const iga_target* target, double tol, iga_tt* out[8]) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(out != nullptr, "weight_tts: null output");
+    IGA_REQUIRE(tol >= 0.0, "weight_tts: negative tolerance");
+    for (int c = 0; c < 8; ++c) out[c] = nullptr;
+    SpaceTables st;
+    build_space_tables(ctx, space, st);
+    weight_tts_impl(ctx, geo, st, target, tol, out);
+  })
+}
+
+iga_status iga_tt_from_cores(iga_ctx* ctx, const int n[3], const int r[2],
+                             const double* const cores[3], iga_tt** out) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(n && r && cores && out, "tt_from_cores: null argument");
+    IGA_REQUIRE(n[0] > 0 && n[1] > 0 && n[2] > 0 && r[0] > 0 && r[1] > 0,
+                "tt_from_cores: sizes must be positive");
+    *out = nullptr;
+    auto* tt = new iga_tt();
+    try {
+      int rl[4] = {1, r[0], r[1], 1};
+      for (int d = 0; d < 3; ++d) {
+        IGA_REQUIRE(cores[d] != nullptr, "tt_from_cores: null core");
+        tt->n[d] = n[d];
+        size_t cnt = (size_t)rl[d] * n[d] * rl[d + 1];
+        tt->core[d].alloc(cnt);
+        IGA_CUDA(cudaMemcpyAsync(tt->core[d].p, cores[d], cnt * 8, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+      }
+      tt->r[0] = r[0];
+      tt->r[1] = r[1];
+      IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+      delete tt;
+      throw;
+    }
+    *out = tt;
+  })
+}
+
+iga_status iga_ops_from_weights(iga_ctx* ctx, const iga_space* space,
+                                const iga_tt* const weights[7], iga_op** M, iga_op** K) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(weights && M && K, "ops_from_weights: null argument");
+    *M = nullptr;
+    *K = nullptr;
+    SpaceTables st;
+    build_space_tables(ctx, space, st);
+    for (int c = 0; c < 7; ++c)
+      if (weights[c])
+        for (int d = 0; d < 3; ++d)
+          IGA_REQUIRE(weights[c]->n[d] == st.dir[d].E * st.dir[d].q,
+                      "ops_from_weights: weight TT is not on the Gauss grid of the space");
+    ops_from_weights_impl(ctx, st, weights, M, K);
+  })
+}
+
+iga_status iga_load_from_density(iga_ctx* ctx, const iga_space* space, const iga_tt* density,
+                                 iga_tt** load) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(density && load, "load_from_density: null argument");
+    SpaceTables st;
+    build_space_tables(ctx, space, st);
+    *load = load_tt(ctx, st, density);
+  })
+}
+
 iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
                                 const iga_target* target, double tol, iga_op** M, iga_op** K,
                                 iga_tt** load) {
@@ -353,56 +486,26 @@ iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga
     if (load) *load = nullptr;
     SpaceTables st;
     build_space_tables(ctx, space, st);
-    int Q[3];
-    for (int d = 0; d < 3; ++d) Q[d] = st.dir[d].E * st.dir[d].q;
-    size_t S = (size_t)Q[0] * Q[1] * Q[2];
-    double* samples = scratch<double>(ctx, SLOT_ASM_SAMPLES, 8 * S);
-    sample_weights_impl(ctx, geo, st, target, samples);
-    // norms: omega, each q entry (off-diagonals count twice in ||Q||_F), load
-    double qn2 = 0.0;
-    for (int c = 1; c <= 6; ++c) {
-      double v = device_norm2(ctx, samples + c * S, S);
-      qn2 += (c == 2 || c == 3 || c == 5) ? 2 * v * v : v * v;
-    }
-    double qnorm = std::sqrt(qn2);
     iga_tt* tts[8] = {nullptr};
     struct Guard {
       iga_tt** t;
       ~Guard() { for (int i = 0; i < 8; ++i) delete t[i]; }
     } guard{tts};
-    tt_svd3(ctx, samples, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[0]);
-    for (int c = 1; c <= 6; ++c) tt_svd3(ctx, samples + c * S, Q[0], Q[1], Q[2], tol, qnorm, 0, &tts[c]);
-    if (target && target->kind != IGA_TARGET_ZERO)
-      tt_svd3(ctx, samples + 7 * S, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[7]);
+    weight_tts_impl(ctx, geo, st, target, tol, tts);
     IGA_REQUIRE(tts[0] != nullptr, "lowrank_assemble: omega is zero");
-    OpBuilder bm, bk;
-    int dm[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-    add_block(ctx, st, tts[0], dm, bm);
-    // q index of the (k,l) entry in the sample layout: 11 12 13 22 23 33
-    const int qidx[3][3] = {{1, 2, 3}, {2, 4, 5}, {3, 5, 6}};
-    for (int k = 0; k < 3; ++k)
-      for (int l = 0; l < 3; ++l) {
-        const iga_tt* t = tts[qidx[k][l]];
-        if (!t) continue;
-        int dk[3][2];
-        for (int d = 0; d < 3; ++d) {
-          dk[d][0] = (l == d);      // delta(l,d) on the row (test) function
-          dk[d][1] = (k == d);      // delta(k,d) on the column (trial) function
-        }
-        add_block(ctx, st, t, dk, bk);
+    const iga_tt* w[7] = {tts[0], tts[1], tts[2], tts[3], tts[4], tts[5], tts[6]};
+    ops_from_weights_impl(ctx, st, w, M, K);
+    if (load && tts[7]) {
+      try {
+        *load = load_tt(ctx, st, tts[7]);
+      } catch (...) {
+        delete *M;
+        delete *K;
+        *M = nullptr;
+        *K = nullptr;
+        throw;
       }
-    iga_op* m = finish_op(ctx, st, bm);
-    iga_op* kk = nullptr;
-    try {
-      kk = finish_op(ctx, st, bk);
-      if (load && tts[7]) *load = load_tt(ctx, st, tts[7]);
-    } catch (...) {
-      delete m;
-      delete kk;
-      throw;
     }
-    *M = m;
-    *K = kk;
   })
 }
 

@@ -221,6 +221,10 @@ void local_matvec_t(iga_ctx* ctx, int r0, int n, int r1, int R0, int R1, int p, 
                     T* y, T* t1, T* t2);
 
 // api.cu
+void weight_tts_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+                     const iga_target* target, double tol, iga_tt* tts[8]);
+void ops_from_weights_impl(iga_ctx* ctx, const SpaceTables& st, const iga_tt* const w[7],
+                           iga_op** M, iga_op** K);
 void kkt_apply_internal(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta, const void* z,
                         void* out, iga_prec prec);
 

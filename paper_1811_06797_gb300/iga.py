@@ -85,6 +85,13 @@ def lib():
         "iga_assemble_bands": (st, [vp, P(Space_), i, vp, i, i, i, i, vp]),
         "iga_lowrank_assemble": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, P(vp), P(vp),
                                       P(vp)]),
+        "iga_weight_tts": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, P(vp)]),
+        "iga_tt_from_cores": (st, [vp, P(C.c_int), P(C.c_int), P(vp), P(vp)]),
+        "iga_ops_from_weights": (st, [vp, P(Space_), P(vp), P(vp), P(vp)]),
+        "iga_load_from_density": (st, [vp, P(Space_), vp, P(vp)]),
+        "iga_spd_solve": (st, [vp, vp, vp, vp, vp, vp, d, i, P(C.c_int), P(d)]),
+        "iga_reduced_gradient": (st, [vp, vp, vp, vp, d, i, vp, d, vp, vp, vp, P(d)]),
+        "iga_weight_gradient": (st, [vp, P(Space_), vp, vp, d, vp, vp, vp, vp]),
         "iga_op_info": (st, [vp, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int),
                              P(C.c_size_t)]),
         "iga_op_block": (st, [vp, i, P(C.c_int)]),
@@ -338,6 +345,76 @@ def iga_lowrank_assemble(ctx, geometry, space, target, tol):
     _check(ctx, lib().iga_lowrank_assemble(ctx.handle, C.byref(g), C.byref(s), C.byref(t),
                                            float(tol), C.byref(hm), C.byref(hk), C.byref(hl)))
     return Op(hm), Op(hk), (TT(hl) if hl.value else None)
+
+
+def iga_weight_tts(ctx, geometry, space, target, tol):
+    """The 8 sampled weight TTs (omega, q11, q12, q13, q22, q23, q33, load density)."""
+    keep = _Keep()
+    g = geometry_struct(geometry, keep)
+    s = space_struct(space, keep)
+    t = target_struct(target)
+    hs = (C.c_void_p * 8)()
+    _check(ctx, lib().iga_weight_tts(ctx.handle, C.byref(g), C.byref(s), C.byref(t), float(tol),
+                                     hs))
+    return [TT(C.c_void_p(h)) if h else None for h in hs]
+
+
+def iga_tt_from_cores(ctx, cores):
+    """TT from three device core tensors (1,n1,r1), (r1,n2,r2), (r2,n3,1)."""
+    n = (C.c_int * 3)(*[c.shape[1] for c in cores])
+    r = (C.c_int * 2)(cores[0].shape[2], cores[1].shape[2])
+    ptrs = (C.c_void_p * 3)(*[c.data_ptr() for c in cores])
+    for c in cores:
+        _ptr(c)
+    h = C.c_void_p()
+    _check(ctx, lib().iga_tt_from_cores(ctx.handle, n, r, ptrs, C.byref(h)))
+    return TT(h)
+
+
+def iga_ops_from_weights(ctx, space, weights):
+    """M, K from 7 weight TTs (omega, q11, q12, q13, q22, q23, q33; None = zero)."""
+    keep = _Keep()
+    s = space_struct(space, keep)
+    hs = (C.c_void_p * 7)(*[(w.handle.value if w is not None else None) for w in weights])
+    hm, hk = C.c_void_p(), C.c_void_p()
+    _check(ctx, lib().iga_ops_from_weights(ctx.handle, C.byref(s), hs, C.byref(hm), C.byref(hk)))
+    return Op(hm), Op(hk)
+
+
+def iga_load_from_density(ctx, space, density):
+    keep = _Keep()
+    s = space_struct(space, keep)
+    h = C.c_void_p()
+    _check(ctx, lib().iga_load_from_density(ctx.handle, C.byref(s), density.handle, C.byref(h)))
+    return TT(h)
+
+
+def iga_spd_solve(ctx, A, M, K, b, x, tol=1e-12, maxit=2000):
+    it = C.c_int()
+    rr = C.c_double()
+    _check(ctx, lib().iga_spd_solve(ctx.handle, A.handle, M.handle,
+                                    K.handle if K is not None else None, _ptr(b), _ptr(x),
+                                    float(tol), int(maxit), C.byref(it), C.byref(rr)))
+    return {"iters": it.value, "relres": rr.value}
+
+
+def iga_reduced_gradient(ctx, M, K, load, beta, u, grad, y, lam, tol=1e-12):
+    """u, grad, y, lam: (nbatch, N) or (N,) FP64 device tensors; returns J per control."""
+    nbatch = 1 if u.dim() == 1 else u.shape[0]
+    J = (C.c_double * nbatch)()
+    _check(ctx, lib().iga_reduced_gradient(ctx.handle, M.handle, K.handle,
+                                           load.handle if load is not None else None,
+                                           float(beta), nbatch, _ptr(u), float(tol), _ptr(grad),
+                                           _ptr(y), _ptr(lam), J))
+    return np.array(J[:])
+
+
+def iga_weight_gradient(ctx, space, M, K, beta, y, u, lam, grad_w):
+    keep = _Keep()
+    s = space_struct(space, keep)
+    _check(ctx, lib().iga_weight_gradient(ctx.handle, C.byref(s), M.handle, K.handle, float(beta),
+                                          _ptr(y), _ptr(u), _ptr(lam), _ptr(grad_w)))
+    return grad_w
 
 
 def iga_kron_apply(ctx, A, alpha, x, beta, y):
