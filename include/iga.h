@@ -296,6 +296,8 @@ typedef struct {
   int refine_max;      /* outer FP64 refinement steps */
   int precision;       /* IGA_FP64 or IGA_FP32 for the AMEn contractions */
   int verbose;         /* print one line per sweep to stderr */
+  double trunc_tol;    /* relative SVD truncation of each field in the block
+                          core when the block index moves (0: tol / 1000) */
 } iga_solve_opts;
 
 typedef struct {

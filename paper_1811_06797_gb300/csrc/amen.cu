@@ -133,6 +133,36 @@ __global__ void permute_fwd_kernel(const double* __restrict__ Xh, int r, int n, 
   Mx[((size_t)a * n + i) * (3 * r1) + (size_t)l * r1 + b] = Xh[idx];
 }
 
+// Normalise the three field components inside a block Gram matrix: for the
+// index layout (l, j), j < r, G_(l j),(m k) *= s_l s_m with s_l = 1 / ||block l||,
+// ||block l||^2 = sum_j G_(l j),(l j).  Returns the scales in s (3 values).
+__global__ void gram_block_scale_kernel(double* __restrict__ G, int r, double* __restrict__ s) {
+  __shared__ double sc[3];
+  int k = 3 * r;
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int j = 0; j < r; ++j) {
+      int i = threadIdx.x * r + j;
+      t += G[(size_t)i * k + i];
+    }
+    sc[threadIdx.x] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    s[threadIdx.x] = sc[threadIdx.x];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    int a = idx / k, b = idx % k;
+    G[idx] *= sc[a / r] * sc[b / r];
+  }
+}
+
+// V (k x k col-major, k = 3 r): row i scaled by s[i / r]
+__global__ void scale_vrows_kernel(double* __restrict__ V, int r, const double* __restrict__ s) {
+  int k = 3 * r;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * k) return;
+  V[idx] *= s[(idx % k) / r];
+}
+
 __global__ void scale_rows_kernel(double* __restrict__ A, int rows, int cols,
                                   const double* __restrict__ w) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -486,6 +516,7 @@ struct Solver {
   int r[4];
   int kick, rmax;
   double inner_tol;
+  double trunc_tol;
   CoreNZ nz[2][3];
   DevBuf<double> X[3];                 // TT cores (FP64 master)
   DevBuf<double> Xh;                   // block core (3, r_d, n_d, r_{d+1})
@@ -679,11 +710,17 @@ struct Solver {
     double* V = slot(8, (size_t)c3 * c3);
     double* w = slot(9, c3);
     rm_gemm(ctx, true, false, c3, c3, m, Mx, c3, Mx, c3, G, c3);
+    // the rank decision treats y, u and lambda alike: each component of the
+    // block core is normalised before the eigen-decomposition (the kept
+    // coefficients below are exact projections of the unscaled core)
+    double* sc = slot(17, 3);
+    IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r1, sc);
     jacobi_eig(ctx, G, V, w, c3);        // V col-major: columns = right singular vectors
+    IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r1, sc);
     std::vector<double> lam(c3);
     IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-    int rk = std::min(trunc_rank(lam, 0.1 * inner_tol), m);
+    int rk = std::min(trunc_rank(lam, trunc_tol), m);
     int kk = std::max(0, std::min(kick, m - rk));
     int nr = rk + kk;
     double* Y = slot(10, (size_t)m * nr);           // col-major (m x nr): [U_k, E]
@@ -721,11 +758,14 @@ struct Solver {
     double* V = slot(8, (size_t)c3 * c3);
     double* w = slot(9, c3);
     rm_gemm(ctx, false, true, c3, c3, m, Mx, m, Mx, m, G, c3);
+    double* sc = slot(17, 3);
+    IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r0, sc);
     jacobi_eig(ctx, G, V, w, c3);                   // columns: left singular vectors
+    IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r0, sc);
     std::vector<double> lam(c3);
     IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-    int rk = std::min(trunc_rank(lam, 0.1 * inner_tol), m);
+    int rk = std::min(trunc_rank(lam, trunc_tol), m);
     int kk = std::max(0, std::min(kick, m - rk));
     int nr = rk + kk;
     double* Y = slot(10, (size_t)m * nr);
@@ -1092,6 +1132,9 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   S.kick = std::max(1, o->kick_rank);
   S.rmax = std::max(2, o->rmax);
   S.inner_tol = tol;
+  // per-field truncation: the KKT residual amplifies the truncation error of
+  // the solution, so truncate well below the residual target
+  S.trunc_tol = o->trunc_tol > 0.0 ? o->trunc_tol : 1e-3 * tol;
   S.verbose = o->verbose;
   size_t N = S.N;
   for (int op = 0; op < 2; ++op)
@@ -1182,6 +1225,7 @@ extern "C" void iga_solve_opts_default(iga_solve_opts* o) {
   o->refine_max = 8;
   o->precision = IGA_FP64;
   o->verbose = 0;
+  o->trunc_tol = 0.0;
 }
 
 extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K,
