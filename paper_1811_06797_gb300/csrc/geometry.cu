@@ -221,49 +221,95 @@ struct GeoDev {
   int nc[3];
   int Q[3];
   const double* ctrl;
+  const double* H2;       // sum-factorised partial sums (stage 2 output)
   int kind;
   double twist;
   int tkind;
   double tp[4];
 };
 
-// One thread per tensor Gauss point: geometry map and derivatives from the
-// nonzero control points, quotient rule for the rational map, optional
-// twist, then omega, Q and the load density, all times g1 g2 g3.
+// Sum factorisation of the homogeneous map and its parametric derivatives
+// (Sec. 2, eq. geometryMapping: G = C : B with B the tensor-product basis):
+//   stage 3: H3[A][B][i3][m][v]   = sum_c (B3 | B3')(x3) C[A][B][c][m]
+//   stage 2: H2[A][i2][i3][m][w]  = sum_b (B2 | B2')(x2) H3[A][b][i3][m][.]
+//            w = (B2 B3, B2' B3, B2 B3')
+//   point:   A_m, dA_m/dxhat_k    = sum_a (B1 | B1')(x1) H2[a][i2][i3][m][.]
+__global__ void geo_stage3_kernel(GeoDev G, double* __restrict__ H3) {
+  size_t total = (size_t)G.nc[0] * G.nc[1] * G.Q[2];
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int i3 = (int)(t % G.Q[2]);
+  size_t ab = t / G.Q[2];
+  const int p3 = G.pg[2];
+  int s3 = G.span[2][i3] - p3;
+  const double* V3 = G.V[2] + (size_t)i3 * (p3 + 1);
+  const double* D3 = G.D[2] + (size_t)i3 * (p3 + 1);
+  const double* C = G.ctrl + (ab * G.nc[2] + s3) * 4;
+  double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int c = 0; c <= p3; ++c)
+    for (int m = 0; m < 4; ++m) {
+      double cm = __ldg(C + c * 4 + m);
+      h[2 * m] += V3[c] * cm;
+      h[2 * m + 1] += D3[c] * cm;
+    }
+  double* o = H3 + t * 8;
+  for (int k = 0; k < 8; ++k) o[k] = h[k];
+}
+
+__global__ void geo_stage2_kernel(GeoDev G, const double* __restrict__ H3, double* __restrict__ H2) {
+  size_t total = (size_t)G.nc[0] * G.Q[1] * G.Q[2];
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int i3 = (int)(t % G.Q[2]);
+  size_t r = t / G.Q[2];
+  int i2 = (int)(r % G.Q[1]);
+  int A = (int)(r / G.Q[1]);
+  const int p2 = G.pg[1];
+  int s2 = G.span[1][i2] - p2;
+  const double* V2 = G.V[1] + (size_t)i2 * (p2 + 1);
+  const double* D2 = G.D[1] + (size_t)i2 * (p2 + 1);
+  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b <= p2; ++b) {
+    const double* h = H3 + (((size_t)A * G.nc[1] + s2 + b) * G.Q[2] + i3) * 8;
+    for (int m = 0; m < 4; ++m) {
+      double hv = h[2 * m], hd = h[2 * m + 1];
+      acc[3 * m + 0] += V2[b] * hv;
+      acc[3 * m + 1] += D2[b] * hv;
+      acc[3 * m + 2] += V2[b] * hd;
+    }
+  }
+  double* o = H2 + t * 12;
+  for (int k = 0; k < 12; ++k) o[k] = acc[k];
+}
+
+// One thread per tensor Gauss point: homogeneous map and derivatives from the
+// partial sums, quotient rule for the rational map, optional twist, then
+// omega, Q and the load density, all times g1 g2 g3.
 __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* __restrict__ flag) {
   size_t Q12 = (size_t)G.Q[1] * G.Q[2];
   size_t total = (size_t)G.Q[0] * Q12;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   int i1 = (int)(t / Q12);
-  int rem = (int)(t - (size_t)i1 * Q12);
-  int i2 = rem / G.Q[2];
-  int i3 = rem - i2 * G.Q[2];
-  const int p1 = G.pg[0], p2 = G.pg[1], p3 = G.pg[2];
+  size_t rem = t - (size_t)i1 * Q12;
+  const int p1 = G.pg[0];
   const double* V1 = G.V[0] + (size_t)i1 * (p1 + 1);
   const double* D1 = G.D[0] + (size_t)i1 * (p1 + 1);
-  const double* V2 = G.V[1] + (size_t)i2 * (p2 + 1);
-  const double* D2 = G.D[1] + (size_t)i2 * (p2 + 1);
-  const double* V3 = G.V[2] + (size_t)i3 * (p3 + 1);
-  const double* D3 = G.D[2] + (size_t)i3 * (p3 + 1);
-  int s1 = G.span[0][i1] - p1, s2 = G.span[1][i2] - p2, s3 = G.span[2][i3] - p3;
+  int s1 = G.span[0][i1] - p1;
   double A[4] = {0, 0, 0, 0}, dA[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
   for (int a = 0; a <= p1; ++a) {
-    for (int b = 0; b <= p2; ++b) {
-      double vv = V1[a] * V2[b], dv = D1[a] * V2[b], vd = V1[a] * D2[b];
-      const double* C = G.ctrl + (((size_t)(s1 + a) * G.nc[1] + (s2 + b)) * G.nc[2] + s3) * 4;
-      for (int c = 0; c <= p3; ++c) {
-        double w0 = vv * V3[c], w1 = dv * V3[c], w2 = vd * V3[c], w3 = vv * D3[c];
-        for (int m = 0; m < 4; ++m) {
-          double cm = __ldg(C + c * 4 + m);
-          A[m] += w0 * cm;
-          dA[0][m] += w1 * cm;
-          dA[1][m] += w2 * cm;
-          dA[2][m] += w3 * cm;
-        }
-      }
+    const double* h = G.H2 + ((size_t)(s1 + a) * Q12 + rem) * 12;
+    double v1 = V1[a], d1 = D1[a];
+    for (int m = 0; m < 4; ++m) {
+      double h0 = h[3 * m], h1 = h[3 * m + 1], h2 = h[3 * m + 2];
+      A[m] += v1 * h0;
+      dA[0][m] += d1 * h0;
+      dA[1][m] += v1 * h1;
+      dA[2][m] += v1 * h2;
     }
   }
+  int i2 = (int)(rem / G.Q[2]);
+  int i3 = (int)(rem - (size_t)i2 * G.Q[2]);
   double iw = 1.0 / A[3];
   double X[3] = {A[0] * iw, A[1] * iw, A[2] * iw};
   double J[3][3];                                    // J[a][k] = dG_a / dxhat_k
@@ -360,8 +406,15 @@ void sample_weights_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTable
   for (int i = 0; i < 4; ++i) G.tp[i] = target ? target->params[i] : 0.0;
   if (G.tkind == IGA_TARGET_GAUSS) IGA_REQUIRE(G.tp[3] > 0.0, "target width must be > 0");
   IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
-  size_t total = (size_t)G.Q[0] * G.Q[1] * G.Q[2];
   int threads = 256;
+  size_t n3 = (size_t)G.nc[0] * G.nc[1] * G.Q[2];
+  size_t n2 = (size_t)G.nc[0] * G.Q[1] * G.Q[2];
+  DevBuf<double> H3(n3 * 8), H2(n2 * 12);
+  G.H2 = H2.p;
+  IGA_LAUNCH(ctx, geo_stage3_kernel, (unsigned)((n3 + threads - 1) / threads), threads, 0, G, H3.p);
+  IGA_LAUNCH(ctx, geo_stage2_kernel, (unsigned)((n2 + threads - 1) / threads), threads, 0, G, H3.p,
+             H2.p);
+  size_t total = (size_t)G.Q[0] * G.Q[1] * G.Q[2];
   IGA_LAUNCH(ctx, sample_weights_kernel, (unsigned)((total + threads - 1) / threads), threads, 0,
              G, out, ctx->dflag);
   IGA_CUDA(cudaMemcpyAsync(ctx->hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost,

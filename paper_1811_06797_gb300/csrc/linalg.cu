@@ -315,7 +315,7 @@ static void gemm(iga_ctx* ctx, cublasOperation_t ta, cublasOperation_t tb, int m
 // col-major in Ctout.  Both outputs are (re)allocated here.
 static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, double delta,
                      int rmax, DevBuf<double>& Uout, DevBuf<double>& Ctout, uint64_t seed) {
-  int k = std::min(ns, 16);
+  int k = std::min(ns, 4);
   std::vector<double> lam;
   double* Q = nullptr;
   double* V = nullptr;
