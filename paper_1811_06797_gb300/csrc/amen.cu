@@ -382,15 +382,24 @@ __global__ void kkt_block_factor_kernel(
 // One warp per block, the working vector in shared memory.
 template <typename T>
 __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
-                                       const int* __restrict__ piv, T* __restrict__ v) {
+                                       const int* __restrict__ piv, T* __restrict__ v,
+                                       int lu_in_smem) {
   extern __shared__ unsigned char smraw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int blk = blockIdx.x * wpb + warp;
   if (blk >= L.NB) return;
   const int N = L.N, n = L.n, kl = L.kl, ku = L.ku;
-  T* s = reinterpret_cast<T*>(smraw) + (size_t)warp * N;
-  const T* A = Aall + (size_t)blk * N * L.W;
+  const size_t per = (size_t)N * L.W;
+  // per warp: [LU factor (optional)] [pivots] [vector]
+  T* base = reinterpret_cast<T*>(smraw) + (size_t)warp * ((lu_in_smem ? per : 0) + N);
+  T* s = base + (lu_in_smem ? per : 0);
+  const T* A = Aall + (size_t)blk * per;
+  if (lu_in_smem) {
+    T* As = base;
+    for (size_t e = lane; e < per; e += 32) As[e] = A[e];
+    A = As;
+  }
   const int* pv = piv + (size_t)blk * N;
   const int a = blk / L.r1, b = blk % L.r1;
   const size_t comp = (size_t)L.r0 * n * L.r1;
@@ -406,7 +415,7 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
     if (pr != k && lane == 0) { s[pr] = s[k]; s[k] = sk; }
     __syncwarp();
     const int last = min(N - 1, k + kl);
-    for (int t = 1 + lane; t <= last - k; t += 32) s[k + t] -= A[(size_t)(k + t) * L.W + (k - (k + t) + kl)] * sk;
+    for (int t = 1 + lane; t <= last - k; t += 32) s[k + t] -= A[(size_t)(k + t) * L.W + (kl - t)] * sk;
     __syncwarp();
   }
   for (int k = N - 1; k >= 0; --k) {
@@ -846,50 +855,64 @@ struct Solver {
   DevBuf<T> VLt, VRt;                    // transforms (col-major r x r)
   void precond_setup(const Local& c) {
     int r0 = c.r0, r1 = c.r1;
-    auto gen_eig = [&](const DevBuf<double>& PM, int SM, const DevBuf<double>& PK, int SK, int rr,
-                       int slotbase, DevBuf<T>& Vout, double* dM, double* dK) {
-      double* Tm = slot(slotbase + 0, (size_t)rr * rr);
-      double* Sm = slot(slotbase + 1, (size_t)rr * rr);
-      double* U = slot(slotbase + 2, (size_t)rr * rr);
-      double* w = slot(slotbase + 3, rr);
-      double* s = slot(slotbase + 4, rr);
-      double* B = slot(slotbase + 5, (size_t)rr * rr);
-      double* C = slot(slotbase + 6, (size_t)rr * rr);
-      double* V = slot(slotbase + 7, (size_t)rr * rr);
-      IGA_LAUNCH(ctx, sum_slices_kernel, nblk(rr * rr), 256, 0, PM.p, SM, rr, Tm);
-      IGA_LAUNCH(ctx, sum_slices_kernel, nblk(rr * rr), 256, 0, PK.p, SK, rr, Sm);
-      IGA_LAUNCH(ctx, symmetrize_kernel, nblk(rr * rr), 256, 0, Tm, rr);
-      IGA_LAUNCH(ctx, symmetrize_kernel, nblk(rr * rr), 256, 0, Sm, rr);
-      if (rr == 1) {
-        double one = 1.0;
-        IGA_CUDA(cudaMemcpyAsync(V, &one, 8, cudaMemcpyHostToDevice, ctx->stream));
-      } else {
-        jacobi_eig(ctx, Tm, U, w, rr);                                  // T = U diag(w) U^T
-        IGA_LAUNCH(ctx, inv_sqrt_abs_kernel, nblk(rr), 256, 0, w, rr, 1e-14, s);
-        IGA_LAUNCH(ctx, scale_cols_cm_kernel, nblk(rr * rr), 256, 0, U, s, rr, B);   // U s
-        // T^{-1/2} = (U s) U^T  (col-major) -> compute as row-major products of transposes
-        rm_gemm(ctx, true, false, rr, rr, rr, U, rr, B, rr, Tm, rr);   // Tm = U B^T ... symmetric
-        // C = Tm S Tm
-        rm_gemm(ctx, false, false, rr, rr, rr, Tm, rr, Sm, rr, B, rr);
-        rm_gemm(ctx, false, false, rr, rr, rr, B, rr, Tm, rr, C, rr);
-        IGA_LAUNCH(ctx, symmetrize_kernel, nblk(rr * rr), 256, 0, C, rr);
-        jacobi_eig(ctx, C, U, w, rr);                                   // C = W diag W^T
-        // V = Tm W (col-major): as row-major V^T = W^T Tm
-        rm_gemm(ctx, false, false, rr, rr, rr, U, rr, Tm, rr, V, rr);
-      }
-      IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(SM * rr), 256, 0, PM.p, V, SM, rr, dM);
-      IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(SK * rr), 256, 0, PK.p, V, SK, rr, dK);
-      Vout.ensure((size_t)rr * rr);
-      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(rr * rr), 256, 0, V, Vout.p, (size_t)rr * rr);
-    };
+    // generalised eigenvectors of (sum Phi^K, sum Phi^M) on both sides:
+    // Cholesky transform per side, then one batched Jacobi launch
     const CoreNZ& zM = nz[0][c.d];
     const CoreNZ& zK = nz[1][c.d];
     double* dLM = slot(40, (size_t)zM.R0 * r0);
     double* dLK = slot(41, (size_t)zK.R0 * r0);
     double* dRM = slot(42, (size_t)zM.R1 * r1);
     double* dRK = slot(43, (size_t)zK.R1 * r1);
-    gen_eig(PhiL[0][c.d], zM.R0, PhiL[1][c.d], zK.R0, r0, 50, VLt, dLM, dLK);
-    gen_eig(PhiR[0][c.d], zM.R1, PhiR[1][c.d], zK.R1, r1, 60, VRt, dRM, dRK);
+    const DevBuf<double>* PMs[2] = {&PhiL[0][c.d], &PhiR[0][c.d]};
+    const DevBuf<double>* PKs[2] = {&PhiL[1][c.d], &PhiR[1][c.d]};
+    int SMs[2] = {zM.R0, zM.R1}, SKs[2] = {zK.R0, zK.R1}, rrs[2] = {r0, r1};
+    double* Vs[2];
+    double* Lis[2];
+    double* As[2];
+    double* Ws[2];
+    double* ws[2];
+    int ks[2];
+    int cnt = 0;
+    for (int side = 0; side < 2; ++side) {
+      int rr = rrs[side];
+      int sb = side ? 60 : 50;
+      Vs[side] = slot(sb + 0, (size_t)rr * rr);
+      if (rr == 1) {
+        double one = 1.0;
+        IGA_CUDA(cudaMemcpyAsync(Vs[side], &one, 8, cudaMemcpyHostToDevice, ctx->stream));
+        continue;
+      }
+      double* work = slot(sb + 1, 3 * (size_t)rr * rr);
+      double* C = slot(sb + 2, (size_t)rr * rr);
+      Lis[side] = slot(sb + 3, (size_t)rr * rr);
+      gen_eig_prep(ctx, PMs[side]->p, SMs[side], PKs[side]->p, SKs[side], rr, work, C, Lis[side]);
+      As[cnt] = C;
+      Ws[cnt] = slot(sb + 4, (size_t)rr * rr);
+      ws[cnt] = slot(sb + 5, rr);
+      ks[cnt] = rr;
+      ++cnt;
+    }
+    if (cnt > 0) jacobi_eig_batched(ctx, As, Ws, ws, ks, cnt);
+    cnt = 0;
+    for (int side = 0; side < 2; ++side) {
+      int rr = rrs[side];
+      if (rr == 1) continue;
+      // V = Linv^T W (col-major); as row-major V^T = W^T Linv  (Linv row-major)
+      rm_gemm(ctx, false, false, rr, rr, rr, Ws[cnt], rr, Lis[side], rr, Vs[side], rr);
+      ++cnt;
+    }
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zM.R0 * r0), 256, 0, PhiL[0][c.d].p, Vs[0], zM.R0,
+               r0, dLM);
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zK.R0 * r0), 256, 0, PhiL[1][c.d].p, Vs[0], zK.R0,
+               r0, dLK);
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zM.R1 * r1), 256, 0, PhiR[0][c.d].p, Vs[1], zM.R1,
+               r1, dRM);
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zK.R1 * r1), 256, 0, PhiR[1][c.d].p, Vs[1], zK.R1,
+               r1, dRK);
+    VLt.ensure((size_t)r0 * r0);
+    VRt.ensure((size_t)r1 * r1);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r0 * r0), 256, 0, Vs[0], VLt.p, (size_t)r0 * r0);
+    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r1 * r1), 256, 0, Vs[1], VRt.p, (size_t)r1 * r1);
     T* tdLM = tslot(44, (size_t)zM.R0 * r0);
     T* tdLK = tslot(45, (size_t)zK.R0 * r0);
     T* tdRM = tslot(46, (size_t)zM.R1 * r1);
@@ -935,15 +958,20 @@ struct Solver {
     IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
     IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
     {
-      const int wpb = 4;
+      // keep each block's LU factor in shared memory when four of them fit
+      size_t per = (size_t)BL.N * BL.W;
+      size_t perw = (per + BL.N) * sizeof(T);
+      int lu_smem = perw <= 200 * 1024;
+      const int wpb = lu_smem ? (int)std::min<size_t>(4, (200 * 1024) / perw) : 4;
+      size_t smem = (size_t)wpb * ((lu_smem ? per : 0) + BL.N) * sizeof(T);
       static bool attr = false;
       if (!attr) {
         IGA_CUDA(cudaFuncSetAttribute(kkt_block_solve_kernel<T>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
         attr = true;
       }
-      IGA_LAUNCH(ctx, kkt_block_solve_kernel<T>, nblk(BL.NB, wpb), 32 * wpb,
-                 (size_t)wpb * BL.N * sizeof(T), BL, A, piv, z);
+      IGA_LAUNCH(ctx, kkt_block_solve_kernel<T>, nblk(BL.NB, wpb), 32 * wpb, smem, BL, A, piv, z,
+                 lu_smem);
     }
     // back: VL z VR^T
     IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, z, 1, 3, c.r0, c.nn, c.r1, 1, t);

@@ -189,10 +189,27 @@ void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
 // the Frobenius norm.  A is overwritten.  Storage: mode 2 keeps A and V in
 // shared memory, mode 1 keeps A in shared memory and V in global memory,
 // mode 0 keeps both in global memory.
-__global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ Vwork,
-                                  double* __restrict__ Vout, double* __restrict__ w, int k,
-                                  int mode) {
+struct JacobiProblem {
+  double* A;
+  double* Vwork;
+  double* Vout;
+  double* w;
+  int k;
+  int mode;
+};
+struct JacobiBatch {
+  JacobiProblem p[4];
+};
+
+__global__ void jacobi_eig_kernel(JacobiBatch batch) {
   extern __shared__ double sm[];
+  const JacobiProblem& P = batch.p[blockIdx.x];
+  double* __restrict__ Ag = P.A;
+  double* __restrict__ Vwork = P.Vwork;
+  double* __restrict__ Vout = P.Vout;
+  double* __restrict__ w = P.w;
+  const int k = P.k;
+  const int mode = P.mode;
   int kk = k + (k & 1);
   int npair = kk / 2;
   double* cs = sm;                 // npair
@@ -281,24 +298,131 @@ __global__ void jacobi_eig_kernel(double* __restrict__ Ag, double* __restrict__ 
   __syncthreads();
 }
 
-void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k) {
-  IGA_REQUIRE(k >= 1 && k <= 1024, "jacobi_eig: k out of range");
-  int kk = k + (k & 1);
-  size_t head = (size_t)(2 * (kk / 2) + (kk / 2) + 1 + 32) * sizeof(double);
-  size_t one = (size_t)k * k * sizeof(double);
+void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double* const* w,
+                        const int* k, int count) {
+  IGA_REQUIRE(count >= 1 && count <= 4, "jacobi_eig: batch of 1..4 problems");
   const size_t limit = 220 * 1024;
+  JacobiBatch batch{};
+  size_t smem = 0;
+  // modes from the largest problem so that one shared-memory size fits all
+  int kmax = 0;
+  for (int i = 0; i < count; ++i) kmax = std::max(kmax, k[i]);
+  IGA_REQUIRE(kmax >= 1 && kmax <= 1024, "jacobi_eig: k out of range");
+  int kkm = kmax + (kmax & 1);
+  size_t head = (size_t)(2 * (kkm / 2) + (kkm / 2) + 1 + 32) * sizeof(double);
+  size_t one = (size_t)kmax * kmax * sizeof(double);
   int mode = head + 2 * one <= limit ? 2 : (head + one <= limit ? 1 : 0);
-  size_t smem = head + (mode == 2 ? 2 * one : (mode == 1 ? one : 0));
-  // with V outside shared memory the rotations accumulate in a global work
-  // array and the sorted eigenvectors are scattered from there into V
-  double* Vw = mode == 2 ? nullptr : scratch<double>(ctx, SLOT_MISC1, (size_t)k * k);
+  smem = head + (mode == 2 ? 2 * one : (mode == 1 ? one : 0));
+  for (int i = 0; i < count; ++i) {
+    IGA_REQUIRE(k[i] >= 1, "jacobi_eig: empty problem");
+    batch.p[i].A = A[i];
+    batch.p[i].Vout = V[i];
+    batch.p[i].w = w[i];
+    batch.p[i].k = k[i];
+    batch.p[i].mode = mode;
+    // with V outside shared memory the rotations accumulate in a global work
+    // array and the sorted eigenvectors are scattered from there into V
+    batch.p[i].Vwork = mode == 2 ? nullptr
+                                 : scratch<double>(ctx, 220 + i, (size_t)k[i] * k[i]);
+  }
   static bool attr = false;
   if (!attr) {
     IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)limit));
     attr = true;
   }
-  IGA_LAUNCH(ctx, jacobi_eig_kernel, 1, 1024, smem, A, Vw, V, w, k, mode);
+  IGA_LAUNCH(ctx, jacobi_eig_kernel, count, 1024, smem, batch);
+}
+
+void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k) {
+  jacobi_eig_batched(ctx, &A, &V, &w, &k, 1);
+}
+
+// Generalised symmetric eigen-problem preparation in one block:
+//   T = sym(sum_s PM[s]), S = sym(sum_s PK[s]), T <- sign(trace T) T,
+//   T = L L^T (Cholesky), Linv = L^{-1}, C = Linv S Linv^T.
+// If T is not positive definite the transform falls back to C = S, Linv = I.
+// Work arrays in global memory (row-major k x k).
+__global__ void gen_eig_prep_kernel(const double* __restrict__ PM, int SM,
+                                    const double* __restrict__ PK, int SK, int k,
+                                    double* __restrict__ T, double* __restrict__ S,
+                                    double* __restrict__ X, double* __restrict__ C,
+                                    double* __restrict__ Linv) {
+  __shared__ double red[32];
+  __shared__ int fail;
+  const int kk = k * k;
+  for (int t = threadIdx.x; t < kk; t += blockDim.x) {
+    int i = t / k, j = t % k;
+    double a = 0.0, b = 0.0;
+    for (int s = 0; s < SM; ++s) a += PM[(size_t)s * kk + i * k + j] + PM[(size_t)s * kk + j * k + i];
+    for (int s = 0; s < SK; ++s) b += PK[(size_t)s * kk + i * k + j] + PK[(size_t)s * kk + j * k + i];
+    T[t] = 0.5 * a;
+    S[t] = 0.5 * b;
+  }
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) tr += T[i * k + i];
+  tr = block_sum(tr, red);
+  if (tr < 0.0)
+    for (int t = threadIdx.x; t < kk; t += blockDim.x) T[t] = -T[t];
+  __syncthreads();
+  // right-looking Cholesky in place (lower triangle of T becomes L)
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      double d = T[j * k + j];
+      if (!(d > 0.0)) fail = 1;
+      T[j * k + j] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    double ljj = T[j * k + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) T[i * k + j] /= ljj;
+    __syncthreads();
+    int m = k - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      int i = j + 1 + t / m, l = j + 1 + t % m;
+      if (l <= i) T[i * k + l] -= T[i * k + j] * T[l * k + j];
+    }
+    __syncthreads();
+  }
+  // Linv: column c solves L x = e_c by forward substitution
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int i = 0; i < k; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int m = c; m < i; ++m) v -= T[i * k + m] * Linv[m * k + c];
+      Linv[i * k + c] = i < c ? 0.0 : v / T[i * k + i];
+    }
+  }
+  __syncthreads();
+  if (fail) {
+    for (int t = threadIdx.x; t < kk; t += blockDim.x) {
+      Linv[t] = (t / k == t % k) ? 1.0 : 0.0;
+      C[t] = S[t];
+    }
+    return;
+  }
+  // X = Linv S, C = X Linv^T
+  for (int t = threadIdx.x; t < kk; t += blockDim.x) {
+    int i = t / k, j = t % k;
+    double v = 0.0;
+    for (int m = 0; m <= i; ++m) v += Linv[i * k + m] * S[m * k + j];
+    X[t] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kk; t += blockDim.x) {
+    int i = t / k, j = t % k;
+    double v = 0.0;
+    for (int m = 0; m <= j; ++m) v += X[i * k + m] * Linv[j * k + m];
+    C[t] = v;
+  }
+}
+
+void gen_eig_prep(iga_ctx* ctx, const double* PM, int SM, const double* PK, int SK, int k,
+                  double* work, double* C, double* Linv) {
+  double* T = work;
+  double* S = work + (size_t)k * k;
+  double* X = work + 2 * (size_t)k * k;
+  IGA_LAUNCH(ctx, gen_eig_prep_kernel, 1, 256, 0, PM, SM, PK, SK, k, T, S, X, C, Linv);
 }
 
 // ----------------------------------------------------------------- TT-SVD
