@@ -297,3 +297,33 @@ def sampled_rows(geo, disc, rows):
                                 Kr[s, o[0], o[1], o[2]] += np.sum(
                                     g * np.einsum("pkl,lp,kp->p", Q, gi, gj))
     return Mr, Kr
+
+
+def sampled_load(geo, disc, target, rows):
+    """Load entries b_i = int yhat(G) beta_i omega for sampled multi-indices (full space).
+
+    Integrates over the elements in the support of each basis function only,
+    with the same tensor Gauss rule as `assemble_band`.
+    """
+    p = disc.degree
+    rows = np.asarray(rows, dtype=np.int64)
+    out = np.zeros(len(rows))
+    hw = geo.homogeneous()
+    for s, r in enumerate(rows):
+        els = []
+        for d in range(3):
+            f = disc.first[d]
+            els.append(np.nonzero((f <= r[d]) & (r[d] <= f + p[d]))[0])
+        for e1 in els[0]:
+            for e2 in els[1]:
+                for e3 in els[2]:
+                    pts = grid_points([disc.x[0][e1], disc.x[1][e2], disc.x[2][e3]])
+                    g = np.einsum("a,b,c->abc", disc.g[0][e1], disc.g[1][e2], disc.g[2][e3]).ravel()
+                    Gp, J = map_and_jacobian(geo.kind, geo.degree, geo.knots, hw, geo.twist, pts)
+                    omega, _, _ = weights_from_jacobian(J)
+                    yh = evaluate_target(target, Gp)
+                    la = [r[0] - disc.first[0][e1], r[1] - disc.first[1][e2], r[2] - disc.first[2][e3]]
+                    vi = np.einsum("a,b,c->abc", disc.V[0][e1][:, la[0]], disc.V[1][e2][:, la[1]],
+                                   disc.V[2][e3][:, la[2]]).ravel()
+                    out[s] += np.sum(g * omega * yh * vi)
+    return out

@@ -135,6 +135,17 @@ def test_band_assembly_equals_bruteforce(name):
     assert np.abs(b.ravel() - bd).max() < 1e-14 * np.abs(bd).max() * 10
 
 
+def test_sampled_load_equals_band():
+    from oracle.assemble import sampled_load
+    geo = GEOS["twisted"]
+    disc = disc_of(wl.uniform_space(3, 4))
+    tgt = wl.Target(wl.TARGET_GAUSS, wl.ANNULUS_CENTROID, 0.1)
+    _, _, b = assemble_band(geo, disc, tgt)
+    rows = np.array([(0, 0, 0), (1, 2, 3), (6, 6, 6), (3, 0, 5)])
+    got = sampled_load(geo, disc, tgt, rows)
+    assert np.allclose(got, [b[tuple(r)] for r in rows], rtol=1e-13, atol=1e-17)
+
+
 def test_sampled_rows_equal_band():
     geo = GEOS["twisted"]
     disc = disc_of(wl.uniform_space(3, 5))
