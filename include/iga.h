@@ -197,8 +197,10 @@ void iga_op_destroy(iga_op* op);
 /* y = alpha * A x + beta * y with A = sum_blocks sum_{r1,r2}
  * A1[r1] (x) A2[r1,r2] (x) A3[r2] (Sec. 5, eqs. M_kron / K_kron; kron
  * ordering kron(A1, kron(A2, A3)) on C-ordered x).  x, y: device, length
- * n1 n2 n3, double (IGA_FP64) or float (IGA_FP32); x and y must not
- * overlap. */
+ * n1 n2 n3, double (IGA_FP64) or float (IGA_FP32, IGA_TF32); x and y must
+ * not overlap.  TT-matrix blocks (ranks above one) contract the rank index
+ * as one batched GEMM per i2 (M = R1, K = (2p+1) R2, N = n1 n3); IGA_TF32
+ * runs that GEMM on the tensor cores in TF32 with FP32 accumulation. */
 iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
                           double beta, void* y, iga_prec prec);
 

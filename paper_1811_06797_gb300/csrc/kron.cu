@@ -238,8 +238,125 @@ static void mode_product(iga_ctx* ctx, const T* band, int mode, const int* n, co
              band, mode, n[0], n[1], n[2], x, y, alpha, accumulate);
 }
 
+// ---- TT-matrix blocks (R1 R2 > 1): rank contraction as a batched GEMM
+//
+// For a block sum_{a,b} A1[a] (x) A2[a][b] (x) A3[b]:
+//   z3[j2][b][i1][i3] = (A3[b] x)(i1, j2, i3)          mode-3 products, j2 padded by P
+//   C[i2][a][(i1,i3)] = sum_{o,b} A2[a][b](i2, o) z3[i2+o][b][(i1,i3)]
+//                     = (W_{i2} Z_{i2})[a][(i1,i3)]   one GEMM per i2: M = R1, K = (2P+1) R2,
+//                                                      N = n1 n3 (Z_{i2} is a contiguous block)
+//   y += alpha sum_a (A1[a] (x) I (x) I) C[.][a]       mode-1 products, summed over a
+
 template <typename T, int P>
-static void kron_general(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y) {
+__global__ void ttm_mode3_kernel(const T* __restrict__ bands3, int R2, int n1, int n2, int n3,
+                                 const T* __restrict__ x, T* __restrict__ z3) {
+  // grid.y = (padded j2, b) pair, grid.x * blockDim.x covers (i1, i3)
+  constexpr int B = 2 * P + 1;
+  const size_t N13 = (size_t)n1 * n3;
+  const int jj = blockIdx.y / R2, b = blockIdx.y - (blockIdx.y / R2) * R2;
+  const int j2 = jj - P;
+  T* out = z3 + (size_t)blockIdx.y * N13;
+  const T* band = bands3 + (size_t)b * n3 * B;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < N13;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int i1 = (int)(t / n3), i3 = (int)(t - (size_t)i1 * n3);
+    T s = T(0);
+    if (j2 >= 0 && j2 < n2) {
+      const T* row = band + (size_t)i3 * B;
+      const T* xr = x + ((size_t)i1 * n2 + j2) * n3;
+#pragma unroll
+      for (int o = 0; o < B; ++o) {
+        int j3 = i3 + o - P;
+        if (j3 >= 0 && j3 < n3) s += row[o] * xr[j3];
+      }
+    }
+    out[t] = s;
+  }
+}
+
+template <typename T>
+__global__ void ttm_wpack_kernel(const T* __restrict__ bands2, int R1, int R2, int n2, int B,
+                                 T* __restrict__ W) {
+  // W[i2][a][o R2 + b] = A2[a][b](i2, o)
+  size_t total = (size_t)n2 * R1 * B * R2;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int b = (int)(idx % R2);
+  size_t r = idx / R2;
+  int o = (int)(r % B);
+  r /= B;
+  int a = (int)(r % R1);
+  int i2 = (int)(r / R1);
+  W[idx] = bands2[(((size_t)a * R2 + b) * n2 + i2) * B + o];
+}
+
+template <typename T, int P>
+__global__ void ttm_mode1_kernel(const T* __restrict__ bands1, int R1, int n1, int n2, int n3,
+                                 const T* __restrict__ C, T alpha, T* __restrict__ y) {
+  // grid.y = (i2, i1), threads over i3
+  constexpr int B = 2 * P + 1;
+  const size_t N13 = (size_t)n1 * n3;
+  const int i2 = blockIdx.y / n1, i1 = blockIdx.y - (blockIdx.y / n1) * n1;
+  for (int i3 = blockIdx.x * blockDim.x + threadIdx.x; i3 < n3; i3 += gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int a = 0; a < R1; ++a) {
+      const T* row = bands1 + ((size_t)a * n1 + i1) * B;
+      const T* c = C + ((size_t)i2 * R1 + a) * N13 + i3;
+#pragma unroll
+      for (int o = 0; o < B; ++o) {
+        int j1 = i1 + o - P;
+        if (j1 >= 0 && j1 < n1) s += row[o] * c[(size_t)j1 * n3];
+      }
+    }
+    y[((size_t)i1 * n2 + i2) * n3 + i3] += alpha * s;
+  }
+}
+
+template <typename T, int P>
+static void ttm_block_gemm(iga_ctx* ctx, const iga_op* A, const OpBlock& blk, T alpha, const T* x,
+                           T* y, bool tf32) {
+  const int n1 = A->n[0], n2 = A->n[1], n3 = A->n[2];
+  constexpr int B = 2 * P + 1;
+  const int R1 = blk.R1, R2 = blk.R2, Kd = B * R2;
+  const size_t N13 = (size_t)n1 * n3, N = (size_t)n1 * n2 * n3;
+  T* z3 = scratch<T>(ctx, SLOT_KRON_Z, (size_t)(n2 + 2 * P) * R2 * N13);
+  T* C = scratch<T>(ctx, SLOT_KRON_Z2, (size_t)n2 * R1 * N13);
+  T* W = scratch<T>(ctx, SLOT_MISC0 + 60, (size_t)n2 * R1 * Kd);
+  size_t t3 = (size_t)(n2 + 2 * P) * R2 * N13;
+  {
+    // algorithmic: mode 3 and mode 1 banded products plus the rank contraction
+    double fl = 2.0 * B * N * (R2 + (double)R1 * R2 + R1);
+    prof_count(ctx, (double)N * sizeof(T) * 3.0, fl);
+  }
+  {
+    dim3 grid((unsigned)std::min<size_t>((N13 + 255) / 256, 64), (unsigned)((n2 + 2 * P) * R2));
+    IGA_LAUNCH(ctx, (ttm_mode3_kernel<T, P>), grid, 256, 0, band_ptr<T>(A, 2, blk.off[2]), R2, n1,
+               n2, n3, x, z3);
+  }
+  (void)t3;
+  size_t tw = (size_t)n2 * R1 * Kd;
+  IGA_LAUNCH(ctx, ttm_wpack_kernel<T>, (unsigned)((tw + 255) / 256), 256, 0,
+             band_ptr<T>(A, 1, blk.off[1]), R1, R2, n2, B, W);
+  const T one = T(1), zero = T(0);
+  cudaDataType dt = sizeof(T) == 8 ? CUDA_R_64F : CUDA_R_32F;
+  cublasComputeType_t ct = sizeof(T) == 8 ? CUBLAS_COMPUTE_64F
+                                          : (tf32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F);
+  IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
+  IGA_BLAS(cublasGemmStridedBatchedEx(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N13, R1, Kd, &one,
+                                      z3, dt, (int)N13, (long long)R2 * N13, W, dt, Kd,
+                                      (long long)R1 * Kd, &zero, C, dt, (int)N13,
+                                      (long long)R1 * N13, n2, ct, CUBLAS_GEMM_DEFAULT));
+  {
+    int th = std::min(256, ((n3 + 31) / 32) * 32);
+    dim3 grid((unsigned)((n3 + th - 1) / th), (unsigned)((size_t)n2 * n1));
+    IGA_LAUNCH(ctx, (ttm_mode1_kernel<T, P>), grid, th, 0, band_ptr<T>(A, 0, blk.off[0]), R1, n1,
+               n2, n3, C, alpha, y);
+  }
+}
+
+template <typename T, int P>
+static void kron_general(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y,
+                         bool tf32) {
   const int* n = A->n;
   size_t N = (size_t)n[0] * n[1] * n[2];
   // y <- beta y first, then accumulate every block
@@ -255,22 +372,13 @@ static void kron_general(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T b
       mode_product<T, P>(ctx, band_ptr<T>(A, 0, blk.off[0]), 0, n, z2, y, alpha, 1);
       continue;
     }
-    T* z3 = scratch<T>(ctx, SLOT_KRON_Z, N * blk.R2);
-    T* z2 = scratch<T>(ctx, SLOT_KRON_Z2, N);
-    for (int b = 0; b < blk.R2; ++b)
-      mode_product<T, P>(ctx, band_ptr<T>(A, 2, blk.off[2] + b), 2, n, x, z3 + b * N, T(1), 0);
-    for (int a = 0; a < blk.R1; ++a) {
-      for (int b = 0; b < blk.R2; ++b)
-        mode_product<T, P>(ctx, band_ptr<T>(A, 1, blk.off[1] + (size_t)a * blk.R2 + b), 1, n,
-                           z3 + b * N, z2, T(1), b > 0);
-      mode_product<T, P>(ctx, band_ptr<T>(A, 0, blk.off[0] + a), 0, n, z2, y, alpha, 1);
-    }
+    ttm_block_gemm<T, P>(ctx, A, blk, alpha, x, y, tf32);
   }
 }
 
 template <typename T>
 static void kron_dispatch(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
-                          void* y) {
+                          void* y, bool tf32 = false) {
   int P = A->p[0];
   IGA_REQUIRE(A->p[1] == P && A->p[2] == P, "kron_apply: equal degrees per direction required");
   const T* xx = static_cast<const T*>(x);
@@ -280,7 +388,7 @@ static void kron_dispatch(iga_ctx* ctx, const iga_op* A, double alpha, const voi
 #define IGA_KRON_CASE(PP)                                                                   \
   case PP:                                                                                  \
     if (fused) kron_rank1<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy);                        \
-    else kron_general<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy);                            \
+    else kron_general<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy, tf32);                      \
     break;
     IGA_KRON_CASE(1)
     IGA_KRON_CASE(2)
@@ -298,7 +406,8 @@ void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
   IGA_REQUIRE(x != y, "kron_apply: x and y must not overlap");
   if (prec == IGA_FP64) kron_dispatch<double>(ctx, A, alpha, x, beta, y);
   else if (prec == IGA_FP32) kron_dispatch<float>(ctx, A, alpha, x, beta, y);
-  else throw Error(IGA_EINVAL, "kron_apply: precision must be IGA_FP64 or IGA_FP32");
+  else if (prec == IGA_TF32) kron_dispatch<float>(ctx, A, alpha, x, beta, y, true);
+  else throw Error(IGA_EINVAL, "kron_apply: unknown precision");
 }
 
 }  // namespace iga

@@ -418,11 +418,17 @@ def iga_weight_gradient(ctx, space, M, K, beta, y, u, lam, grad_w):
     return grad_w
 
 
-def iga_kron_apply(ctx, A, alpha, x, beta, y):
+def iga_kron_apply(ctx, A, alpha, x, beta, y, tf32=False):
+    """y = alpha A x + beta y; float32 tensors with tf32=True use the TF32 tensor-core path."""
     if x.dtype != y.dtype:
         raise IgaError(1, "x and y dtypes differ")
+    prec = _prec(x)
+    if tf32:
+        if prec != IGA_FP32:
+            raise IgaError(1, "tf32 needs float32 tensors")
+        prec = IGA_TF32
     _check(ctx, lib().iga_kron_apply(ctx.handle, A.handle, float(alpha), _ptr(x), float(beta),
-                                     _ptr(y), _prec(x)))
+                                     _ptr(y), prec))
     return y
 
 

@@ -53,6 +53,29 @@ def test_kron_apply(env, name, p, E, prec):
         assert np.linalg.norm(yt.double().cpu().numpy() - kron_apply(terms, x)) < tol * np.linalg.norm(ref) * 3
 
 
+@pytest.mark.parametrize("E,tol", [(5, 1e-6), (9, 1e-9)])
+def test_ttmatrix_apply_tf32(env, E, tol):
+    """Random volume (weight TT ranks > 1): the rank contraction as batched GEMMs,
+    FP64 exact, TF32 tensor cores within the TF32 rounding level."""
+    ctx, torch, iga = env
+    M, K, _ = _ops(env, "random", 2, E, tol)
+    assert max(K.info()["R"]) > 3
+    rng = np.random.default_rng(9)
+    for op in (M, K):
+        terms = op_terms(ctx, op)
+        N = int(np.prod(op.info()["n"]))
+        x = rng.standard_normal(N)
+        ref = kron_apply(terms, x)
+        y64 = torch.empty(N, dtype=torch.float64, device="cuda")
+        iga.iga_kron_apply(ctx, op, 1.0, torch.tensor(x, device="cuda"), 0.0, y64)
+        assert np.linalg.norm(y64.cpu().numpy() - ref) < 1e-12 * np.linalg.norm(ref)
+        y32 = torch.empty(N, dtype=torch.float32, device="cuda")
+        iga.iga_kron_apply(ctx, op, 1.0, torch.tensor(x, device="cuda", dtype=torch.float32), 0.0,
+                           y32, tf32=True)
+        err = np.linalg.norm(y32.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < 5e-3, err
+
+
 def test_kkt_apply_against_oracle_assembly(env):
     ctx, torch, iga = env
     work = wl.small(wl.quarter_annulus(twist=math.pi / 4), 2, 5, beta=1e-3)
