@@ -201,11 +201,46 @@ void kkt_apply_internal(iga_ctx* ctx, const iga_op* M, const iga_op* K, double b
 // Sample the eight weight tensors and TT-compress them (Sec. 3): omega g,
 // the six entries of Q g (truncated relative to ||Q||_F over all nine
 // entries), and the load density yhat(G) omega g.  Rank-0 tensors stay NULL.
+struct EachCtx {
+  iga_ctx* ctx;
+  int Q[3];
+  double tol;
+  double* qn2dev;
+  double qnorm;
+  iga_tt** tts;
+};
+
+static void weight_tt_cb(void* user, int c, const double* buf) {
+  EachCtx* e = static_cast<EachCtx*>(user);
+  if (c == 1) {
+    IGA_CUDA(cudaMemcpyAsync(&e->qnorm, e->qn2dev, 8, cudaMemcpyDeviceToHost, e->ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(e->ctx->stream));
+    e->qnorm = std::sqrt(e->qnorm);
+  }
+  double ref = (c >= 1 && c <= 6) ? e->qnorm : 0.0;
+  tt_svd3(e->ctx, buf, e->Q[0], e->Q[1], e->Q[2], e->tol, ref, 0, &e->tts[c]);
+}
+
 void weight_tts_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
                      const iga_target* target, double tol, iga_tt* tts[8]) {
   int Q[3];
   for (int d = 0; d < 3; ++d) Q[d] = st.dir[d].E * st.dir[d].q;
   size_t S = (size_t)Q[0] * Q[1] * Q[2];
+  size_t free_b = 0, tot_b = 0;
+  IGA_CUDA(cudaMemGetInfo(&free_b, &tot_b));
+  if (8 * S * sizeof(double) > free_b / 3) {
+    // large grids: one sample tensor at a time, each compressed before the next
+    double* buf = scratch<double>(ctx, SLOT_ASM_SAMPLES, S);
+    double* qn2 = scratch<double>(ctx, SLOT_MISC0 + 61, 1);
+    EachCtx e{ctx, {Q[0], Q[1], Q[2]}, tol, qn2, 0.0, tts};
+    try {
+      sample_weights_each(ctx, geo, st, target, buf, qn2, weight_tt_cb, &e);
+    } catch (...) {
+      for (int c = 0; c < 8; ++c) { delete tts[c]; tts[c] = nullptr; }
+      throw;
+    }
+    return;
+  }
   double* samples = scratch<double>(ctx, SLOT_ASM_SAMPLES, 8 * S);
   sample_weights_impl(ctx, geo, st, target, samples);
   double qn2 = 0.0;

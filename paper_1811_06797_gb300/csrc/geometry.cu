@@ -222,6 +222,8 @@ struct GeoDev {
   int Q[3];
   const double* ctrl;
   const double* H2;       // sum-factorised partial sums (stage 2 output)
+  int comp;               // -1: write all eight tensors; c >= 0: only tensor c
+  double* qn2;            // optional: accumulates ||Q g||_F^2 over all nine entries
   int kind;
   double twist;
   int tkind;
@@ -289,7 +291,10 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
   size_t Q12 = (size_t)G.Q[1] * G.Q[2];
   size_t total = (size_t)G.Q[0] * Q12;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
+  // lanes past the end evaluate point 0 and write nothing, so every warp stays
+  // converged for the reduction below
+  const bool valid = t < total;
+  if (!valid) t = 0;
   int i1 = (int)(t / Q12);
   size_t rem = t - (size_t)i1 * Q12;
   const int p1 = G.pg[0];
@@ -331,7 +336,7 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
   double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-  if (!(det != 0.0) || !isfinite(det)) atomicOr(flag, 1);
+  if (valid && (!(det != 0.0) || !isfinite(det))) atomicOr(flag, 1);
   double adet = fabs(det);
   // metric m = J^T J; Q = adj(m) / det(m) * |det J| = adj(m) / |det J|
   double m[3][3];
@@ -352,75 +357,119 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
     yh = exp(-(dx * dx + dy * dy + dz * dz) / G.tp[3]);
   }
   double g = G.g[0][i1] * G.g[1][i2] * G.g[2][i3];
-  out[t] = adet * g;
-  out[total + t] = q11 * g;
-  out[2 * total + t] = q12 * g;
-  out[3 * total + t] = q13 * g;
-  out[4 * total + t] = q22 * g;
-  out[5 * total + t] = q23 * g;
-  out[6 * total + t] = q33 * g;
-  out[7 * total + t] = yh * adet * g;
+  double v[8] = {adet, q11, q12, q13, q22, q23, q33, yh * adet};
+  if (valid) {
+    if (G.comp < 0) {
+      for (int c = 0; c < 8; ++c) out[c * total + t] = v[c] * g;
+    } else {
+      out[t] = v[G.comp] * g;
+    }
+  }
+  if (G.qn2) {
+    double q2 = valid ? (q11 * q11 + q22 * q22 + q33 * q33 +
+                         2.0 * (q12 * q12 + q13 * q13 + q23 * q23)) * g * g
+                      : 0.0;
+    for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(G.qn2, q2);
+  }
 }
+
+struct GeoSampler {
+  GeoDev G{};
+  DevBuf<double> gV[3], gD[3], gw[3], ctrl, H2;
+  DevBuf<int> gspan[3];
+  size_t total = 0;
+
+  void prepare(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+               const iga_target* target) {
+    IGA_REQUIRE(geo != nullptr, "null geometry");
+    IGA_REQUIRE(geo->kind == IGA_GEO_NURBS || geo->kind == IGA_GEO_NURBS_TWIST,
+                "unknown geometry kind");
+    IGA_REQUIRE(geo->ctrl_hw != nullptr, "null control net");
+    size_t nctrl = 1;
+    for (int d = 0; d < 3; ++d) {
+      check_knots(geo->knots[d], geo->nknots[d], geo->degree[d], "geometry");
+      IGA_REQUIRE(geo->nctrl[d] == geo->nknots[d] - geo->degree[d] - 1,
+                  "geometry: nctrl must equal nknots - degree - 1");
+      nctrl *= geo->nctrl[d];
+      const DirTables& T = st.dir[d];
+      int npts = T.E * T.q;
+      std::vector<double> k(geo->knots[d], geo->knots[d] + geo->nknots[d]);
+      gV[d].alloc((size_t)npts * (geo->degree[d] + 1));
+      gD[d].alloc((size_t)npts * (geo->degree[d] + 1));
+      gspan[d].alloc(npts);
+      gw[d].alloc(npts);
+      IGA_CUDA(cudaMemcpyAsync(gw[d].p, T.gq.data(), npts * 8, cudaMemcpyHostToDevice,
+                               ctx->stream));
+      basis_tables(ctx, k, geo->degree[d], T.dx.p, npts, gspan[d].p, gV[d].p, gD[d].p);
+      G.V[d] = gV[d].p;
+      G.D[d] = gD[d].p;
+      G.span[d] = gspan[d].p;
+      G.g[d] = gw[d].p;
+      G.pg[d] = geo->degree[d];
+      G.nc[d] = geo->nctrl[d];
+      G.Q[d] = npts;
+    }
+    ctrl.alloc(nctrl * 4);
+    IGA_CUDA(cudaMemcpyAsync(ctrl.p, geo->ctrl_hw, nctrl * 4 * 8, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    G.ctrl = ctrl.p;
+    G.kind = geo->kind;
+    G.twist = geo->twist;
+    G.tkind = target ? target->kind : IGA_TARGET_ZERO;
+    IGA_REQUIRE(G.tkind >= 0 && G.tkind <= 2, "unknown target kind");
+    for (int i = 0; i < 4; ++i) G.tp[i] = target ? target->params[i] : 0.0;
+    if (G.tkind == IGA_TARGET_GAUSS) IGA_REQUIRE(G.tp[3] > 0.0, "target width must be > 0");
+    int threads = 256;
+    size_t n3 = (size_t)G.nc[0] * G.nc[1] * G.Q[2];
+    size_t n2 = (size_t)G.nc[0] * G.Q[1] * G.Q[2];
+    DevBuf<double> H3(n3 * 8);
+    H2.alloc(n2 * 12);
+    G.H2 = H2.p;
+    IGA_LAUNCH(ctx, geo_stage3_kernel, (unsigned)((n3 + threads - 1) / threads), threads, 0, G,
+               H3.p);
+    IGA_LAUNCH(ctx, geo_stage2_kernel, (unsigned)((n2 + threads - 1) / threads), threads, 0, G,
+               H3.p, H2.p);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));    // H3 is released on return
+    total = (size_t)G.Q[0] * G.Q[1] * G.Q[2];
+  }
+
+  // comp = -1: all eight tensors into out (8 x total); comp >= 0: tensor comp
+  void run(iga_ctx* ctx, double* out, int comp, double* qn2) {
+    G.comp = comp;
+    G.qn2 = qn2;
+    IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
+    int threads = 256;
+    IGA_LAUNCH(ctx, sample_weights_kernel, (unsigned)((total + threads - 1) / threads), threads, 0,
+               G, out, ctx->dflag);
+    IGA_CUDA(cudaMemcpyAsync(ctx->hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    IGA_REQUIRE(*ctx->hflag == 0, "geometry: zero or non-finite Jacobian determinant");
+  }
+};
 
 void sample_weights_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
                          const iga_target* target, double* out) {
-  IGA_REQUIRE(geo != nullptr && out != nullptr, "null geometry or output");
-  IGA_REQUIRE(geo->kind == IGA_GEO_NURBS || geo->kind == IGA_GEO_NURBS_TWIST,
-              "unknown geometry kind");
-  IGA_REQUIRE(geo->ctrl_hw != nullptr, "null control net");
-  GeoDev G{};
-  std::vector<DevBuf<double>> keep;
-  DevBuf<double> gV[3], gD[3], gw[3];
-  DevBuf<int> gspan[3];
-  size_t nctrl = 1;
-  for (int d = 0; d < 3; ++d) {
-    check_knots(geo->knots[d], geo->nknots[d], geo->degree[d], "geometry");
-    IGA_REQUIRE(geo->nctrl[d] == geo->nknots[d] - geo->degree[d] - 1,
-                "geometry: nctrl must equal nknots - degree - 1");
-    nctrl *= geo->nctrl[d];
-    const DirTables& T = st.dir[d];
-    int npts = T.E * T.q;
-    std::vector<double> k(geo->knots[d], geo->knots[d] + geo->nknots[d]);
-    gV[d].alloc((size_t)npts * (geo->degree[d] + 1));
-    gD[d].alloc((size_t)npts * (geo->degree[d] + 1));
-    gspan[d].alloc(npts);
-    gw[d].alloc(npts);
-    IGA_CUDA(cudaMemcpyAsync(gw[d].p, T.gq.data(), npts * 8, cudaMemcpyHostToDevice, ctx->stream));
-    basis_tables(ctx, k, geo->degree[d], T.dx.p, npts, gspan[d].p, gV[d].p, gD[d].p);
-    G.V[d] = gV[d].p;
-    G.D[d] = gD[d].p;
-    G.span[d] = gspan[d].p;
-    G.g[d] = gw[d].p;
-    G.pg[d] = geo->degree[d];
-    G.nc[d] = geo->nctrl[d];
-    G.Q[d] = npts;
+  IGA_REQUIRE(out != nullptr, "null output");
+  GeoSampler S;
+  S.prepare(ctx, geo, st, target);
+  S.run(ctx, out, -1, nullptr);
+}
+
+// The weights one tensor at a time (for grids whose eight sample tensors do not
+// fit next to each other): calls back with each tensor in `buf`.
+void sample_weights_each(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+                         const iga_target* target, double* buf, double* qnorm2,
+                         void (*cb)(void*, int, const double*), void* user) {
+  GeoSampler S;
+  S.prepare(ctx, geo, st, target);
+  IGA_CUDA(cudaMemsetAsync(qnorm2, 0, sizeof(double), ctx->stream));
+  int last = (target && target->kind != IGA_TARGET_ZERO) ? 7 : 6;
+  for (int c = 0; c <= last; ++c) {
+    S.run(ctx, buf, c, c == 0 ? qnorm2 : nullptr);
+    cb(user, c, buf);
   }
-  DevBuf<double> ctrl(nctrl * 4);
-  IGA_CUDA(cudaMemcpyAsync(ctrl.p, geo->ctrl_hw, nctrl * 4 * 8, cudaMemcpyHostToDevice,
-                           ctx->stream));
-  G.ctrl = ctrl.p;
-  G.kind = geo->kind;
-  G.twist = geo->twist;
-  G.tkind = target ? target->kind : IGA_TARGET_ZERO;
-  IGA_REQUIRE(G.tkind >= 0 && G.tkind <= 2, "unknown target kind");
-  for (int i = 0; i < 4; ++i) G.tp[i] = target ? target->params[i] : 0.0;
-  if (G.tkind == IGA_TARGET_GAUSS) IGA_REQUIRE(G.tp[3] > 0.0, "target width must be > 0");
-  IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
-  int threads = 256;
-  size_t n3 = (size_t)G.nc[0] * G.nc[1] * G.Q[2];
-  size_t n2 = (size_t)G.nc[0] * G.Q[1] * G.Q[2];
-  DevBuf<double> H3(n3 * 8), H2(n2 * 12);
-  G.H2 = H2.p;
-  IGA_LAUNCH(ctx, geo_stage3_kernel, (unsigned)((n3 + threads - 1) / threads), threads, 0, G, H3.p);
-  IGA_LAUNCH(ctx, geo_stage2_kernel, (unsigned)((n2 + threads - 1) / threads), threads, 0, G, H3.p,
-             H2.p);
-  size_t total = (size_t)G.Q[0] * G.Q[1] * G.Q[2];
-  IGA_LAUNCH(ctx, sample_weights_kernel, (unsigned)((total + threads - 1) / threads), threads, 0,
-             G, out, ctx->dflag);
-  IGA_CUDA(cudaMemcpyAsync(ctx->hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost,
-                           ctx->stream));
-  IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-  IGA_REQUIRE(*ctx->hflag == 0, "geometry: zero or non-finite Jacobian determinant");
 }
 
 }  // namespace iga

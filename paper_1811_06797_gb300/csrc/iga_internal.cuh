@@ -196,6 +196,10 @@ enum {
 void build_space_tables(iga_ctx* ctx, const iga_space* sp, SpaceTables& t);
 void check_knots(const double* k, int nk, int p, const char* what);
 
+void sample_weights_each(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+                         const iga_target* target, double* buf, double* qnorm2,
+                         void (*cb)(void*, int, const double*), void* user);
+
 // assembly.cu
 void launch_assemble_bands(iga_ctx* ctx, const DirTables& t, const double* w, int T, int drow,
                            int dcol, int interior, double* band);

@@ -250,15 +250,15 @@ static void mode_product(iga_ctx* ctx, const T* band, int mode, const int* n, co
 template <typename T, int P>
 __global__ void ttm_mode3_kernel(const T* __restrict__ bands3, int R2, int n1, int n2, int n3,
                                  const T* __restrict__ x, T* __restrict__ z3) {
-  // grid.y = (padded j2, b) pair, grid.x * blockDim.x covers (i1, i3)
+  // grid.x = (padded j2, b) pair, grid.y * blockDim.x covers (i1, i3)
   constexpr int B = 2 * P + 1;
   const size_t N13 = (size_t)n1 * n3;
-  const int jj = blockIdx.y / R2, b = blockIdx.y - (blockIdx.y / R2) * R2;
+  const int jj = blockIdx.x / R2, b = blockIdx.x - (blockIdx.x / R2) * R2;
   const int j2 = jj - P;
-  T* out = z3 + (size_t)blockIdx.y * N13;
+  T* out = z3 + (size_t)blockIdx.x * N13;
   const T* band = bands3 + (size_t)b * n3 * B;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < N13;
-       t += (size_t)gridDim.x * blockDim.x) {
+  for (size_t t = (size_t)blockIdx.y * blockDim.x + threadIdx.x; t < N13;
+       t += (size_t)gridDim.y * blockDim.x) {
     int i1 = (int)(t / n3), i3 = (int)(t - (size_t)i1 * n3);
     T s = T(0);
     if (j2 >= 0 && j2 < n2) {
@@ -293,11 +293,11 @@ __global__ void ttm_wpack_kernel(const T* __restrict__ bands2, int R1, int R2, i
 template <typename T, int P>
 __global__ void ttm_mode1_kernel(const T* __restrict__ bands1, int R1, int n1, int n2, int n3,
                                  const T* __restrict__ C, T alpha, T* __restrict__ y) {
-  // grid.y = (i2, i1), threads over i3
+  // grid.x = (i2, i1), threads over i3
   constexpr int B = 2 * P + 1;
   const size_t N13 = (size_t)n1 * n3;
-  const int i2 = blockIdx.y / n1, i1 = blockIdx.y - (blockIdx.y / n1) * n1;
-  for (int i3 = blockIdx.x * blockDim.x + threadIdx.x; i3 < n3; i3 += gridDim.x * blockDim.x) {
+  const int i2 = blockIdx.x / n1, i1 = blockIdx.x - (blockIdx.x / n1) * n1;
+  for (int i3 = threadIdx.x; i3 < n3; i3 += blockDim.x) {
     T s = T(0);
     for (int a = 0; a < R1; ++a) {
       const T* row = bands1 + ((size_t)a * n1 + i1) * B;
@@ -329,7 +329,7 @@ static void ttm_block_gemm(iga_ctx* ctx, const iga_op* A, const OpBlock& blk, T 
     prof_count(ctx, (double)N * sizeof(T) * 3.0, fl);
   }
   {
-    dim3 grid((unsigned)std::min<size_t>((N13 + 255) / 256, 64), (unsigned)((n2 + 2 * P) * R2));
+    dim3 grid((unsigned)((n2 + 2 * P) * R2), (unsigned)std::min<size_t>((N13 + 255) / 256, 64));
     IGA_LAUNCH(ctx, (ttm_mode3_kernel<T, P>), grid, 256, 0, band_ptr<T>(A, 2, blk.off[2]), R2, n1,
                n2, n3, x, z3);
   }
@@ -348,7 +348,7 @@ static void ttm_block_gemm(iga_ctx* ctx, const iga_op* A, const OpBlock& blk, T 
                                       (long long)R1 * N13, n2, ct, CUBLAS_GEMM_DEFAULT));
   {
     int th = std::min(256, ((n3 + 31) / 32) * 32);
-    dim3 grid((unsigned)((n3 + th - 1) / th), (unsigned)((size_t)n2 * n1));
+    dim3 grid((unsigned)((size_t)n2 * n1), 1);
     IGA_LAUNCH(ctx, (ttm_mode1_kernel<T, P>), grid, th, 0, band_ptr<T>(A, 0, blk.off[0]), R1, n1,
                n2, n3, C, alpha, y);
   }
