@@ -32,6 +32,13 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_FMA_TFLOPS = 1.196      # measured FP64 FMA rate of this GB300 (CUDA cores)
 FP32_FMA_TFLOPS = 74.75      # measured FP32 FMA rate
+# kernels that can dominate a step, with the arithmetic they run in
+CANDIDATES = {
+    "jacobi_eig_kernel": "fp64", "sample_weights_kernel": "fp64",
+    "kkt_block_solve_kernel": "fp32", "kkt_block_factor_kernel": "fp32",
+    "kron_rank1_kernel": "fp64", "householder_qr_kernel": "fp64",
+    "pivoted_cholesky_kernel": "fp64", "rank1_residual_kernel": "fp64",
+}
 
 
 def parse():
@@ -45,7 +52,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--roofline-kernel", default="kron_rank1_kernel")
+    ap.add_argument("--roofline-kernel", default="auto",
+                    help="kernel name for the roofline entry, or auto (largest device time)")
     return ap.parse_args()
 
 
@@ -54,6 +62,17 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def aggregate_ms(ms, dist):
+    """Whole-job step time: the maximum over ranks (every rank solves its own replica)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def peaks():
@@ -209,7 +228,12 @@ def run_gpu(args, world, rank, local):
     state = {}
 
     def step():
+        ea = torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
         M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+        eb = torch.cuda.Event(enable_timing=True)
+        eb.record(stream)
+        state["split"] = (ea, eb)
         if "y" not in state:
             N = int(np.prod(M.info()["n"]))
             state["N"] = N
@@ -227,8 +251,19 @@ def run_gpu(args, world, rank, local):
     if not state["info"]["converged"]:
         raise RuntimeError(f"solve did not converge: {state['info']}")
 
+    # dominant kernel: device time of each candidate over one (untimed) step
+    shares = {}
+    for k in CANDIDATES:
+        ctx.profile_begin(k)
+        step()
+        p = ctx.profile_end()
+        shares[k] = p["ms"]
+    if args.roofline_kernel == "auto":
+        args.roofline_kernel = max(shares, key=shares.get)
+
     # timed region (device time with CUDA events on the context stream)
     times = []
+    asm_times = []
     launches0 = ctx.launches
     if dist is not None:
         dist.barrier()
@@ -244,16 +279,14 @@ def run_gpu(args, world, rank, local):
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
+            ea, eb = state["split"]
+            asm_times.append(ea.elapsed_time(eb))
     prof = ctx.profile_end()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     launches = ctx.launches - launches0
-    ms = sum(times) / len(times)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = aggregate_ms(sum(times) / len(times), dist)
     clocks = clk.summary()
     info = state["info"]
 
@@ -263,7 +296,11 @@ def run_gpu(args, world, rank, local):
     iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"], state["lam"],
                            tol=args.tol, precision=other)
     paths = {}
-    for pr in (prec, other):
+    # the two precisions with the default (pivoted) moves, and FP64 with the
+    # SVD moves of the paper
+    variants = [(prec, iga.IGA_TRUNC_PIVOTED), (other, iga.IGA_TRUNC_PIVOTED),
+                (iga.IGA_FP64, iga.IGA_TRUNC_SVD)]
+    for pr, tr in variants:
         ts = []
         for _ in range(max(2, args.steps)):
             torch.cuda.synchronize()
@@ -271,11 +308,11 @@ def run_gpu(args, world, rank, local):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             inf = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"],
-                                         state["lam"], tol=args.tol, precision=pr)
+                                         state["lam"], tol=args.tol, precision=pr, truncation=tr)
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
-        key = "fp64" if pr == iga.IGA_FP64 else "mixed"
+        key = ("fp64" if pr == iga.IGA_FP64 else "mixed") + ("_svd_moves" if tr else "")
         paths[key] = {"solve_s": statistics.median(ts) / 1e3, "sweeps": inf["sweeps"],
                       "max_rank": inf["max_rank"], "local_iters": inf["local_iters"],
                       "residual": inf["residual"], "converged": inf["converged"]}
@@ -308,18 +345,25 @@ def run_gpu(args, world, rank, local):
         avg_ms = prof["ms"] / prof["launches"]
         by = prof["bytes"] / prof["launches"]
         fl = prof["flops"] / prof["launches"]
-        if args.precision == "fp64":
+        arith = CANDIDATES.get(args.roofline_kernel, "fp64")
+        if arith == "prec":
+            arith = "fp64" if args.precision == "fp64" else "fp32"
+        alu_peak = FP64_FMA_TFLOPS if arith == "fp64" else FP32_FMA_TFLOPS
+        t_alu = fl / (alu_peak * 1e12)
+        t_hbm = by / (pk["hbm_gbs"] * 1e9)
+        if t_alu >= t_hbm:
             achieved = fl / (avg_ms * 1e-3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_FMA_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_FMA_TFLOPS, "traffic": None,
-                    "kernel": args.roofline_kernel, "launches": prof["launches"],
-                    "avg_us": avg_ms * 1e3, "peak_kind": "measured FP64 FMA"}
+            roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak,
+                    "peak_kind": f"measured {arith.upper()} FMA rate (CUDA cores)"}
         else:
             achieved = by / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                    "kernel": args.roofline_kernel, "launches": prof["launches"],
-                    "avg_us": avg_ms * 1e3, "peak_kind": pk_kind}
+                    "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind}
+        roof.update({"traffic": None, "kernel": args.roofline_kernel,
+                     "launches": prof["launches"], "avg_us": avg_ms * 1e3,
+                     "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": fl,
+                     "device_ms_per_step_by_kernel": {k: round(v, 3) for k, v in shares.items()}})
 
     line = {
         "metric": METRIC,
@@ -338,8 +382,12 @@ def run_gpu(args, world, rank, local):
                    "beta": work.beta, "tt_tol": work.tol, "residual_tol": args.tol,
                    "precision": args.precision, "l2": "flushed (256 MB write) before every step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "solve": {k: info[k] for k in ("sweeps", "refinements", "max_rank", "local_iters",
-                                       "residual")},
+        "solve": {**{k: info[k] for k in ("sweeps", "refinements", "max_rank", "local_iters",
+                                          "residual")},
+                  "device_s_by_phase": {k[2:]: round(info[k], 6) for k in
+                                        ("t_local", "t_residual", "t_move", "t_refine")}},
+        "step_split_ms": {"assembly": round(statistics.mean(asm_times), 3),
+                          "solve": round(statistics.mean(times) - statistics.mean(asm_times), 3)},
         "paths": paths,
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(3 * N * 8)},

@@ -288,6 +288,17 @@ iga_status iga_weight_gradient(iga_ctx* ctx, const iga_space* space, const iga_o
 
 /* ---- KKT solve (a6..a8) ---------------------------------------------- */
 
+/* Truncation of the block core when the block index moves to the next core
+ * (Sec. 5, eqs. svd1 and svd2).  IGA_TRUNC_SVD is the paper's truncated SVD,
+ * computed from the Gram matrix of the reshaped block core by a Jacobi
+ * eigen-decomposition.  IGA_TRUNC_PIVOTED keeps the columns chosen by a
+ * pivoted Cholesky factorisation of the same Gram matrix (QR with column
+ * pivoting): the projection error of each field obeys the same bound
+ * trunc_tol, the kept rank can be a little larger than the SVD's, and the
+ * work is about k^3 / 3 instead of a Jacobi method's tens of k^3 for k =
+ * three times the TT rank.  The default is IGA_TRUNC_PIVOTED. */
+typedef enum { IGA_TRUNC_PIVOTED = 0, IGA_TRUNC_SVD = 1 } iga_trunc;
+
 typedef struct {
   double tol;          /* stop when ||rhs - KKT z||_2 / ||rhs||_2 <= tol */
   double inner_tol;    /* tolerance of each AMEn correction (0: tol itself) */
@@ -298,8 +309,10 @@ typedef struct {
   int refine_max;      /* outer FP64 refinement steps */
   int precision;       /* IGA_FP64 or IGA_FP32 for the AMEn contractions */
   int verbose;         /* print one line per sweep to stderr */
-  double trunc_tol;    /* relative SVD truncation of each field in the block
-                          core when the block index moves (0: tol / 1000) */
+  double trunc_tol;    /* relative truncation of each field in the block core
+                          when the block index moves (0: tol / 1000) */
+  int truncation;      /* how the block index moves: IGA_TRUNC_PIVOTED or
+                          IGA_TRUNC_SVD (see iga_trunc) */
 } iga_solve_opts;
 
 typedef struct {
@@ -309,6 +322,12 @@ typedef struct {
   int local_iters;     /* Krylov iterations over all local solves */
   double residual;     /* final ||rhs - KKT z|| / ||rhs|| in FP64 */
   double seconds;      /* wall time of the solve */
+  double t_local;      /* device seconds: local systems (preconditioner + GMRES) */
+  double t_residual;   /* device seconds: full correction and FP64 residual after
+                          each local solve */
+  double t_move;       /* device seconds: truncation, orthogonalisation,
+                          enrichment and interface updates */
+  double t_refine;     /* device seconds: outer refinement residuals */
 } iga_solve_info;
 
 /* Fill opts with defaults. */

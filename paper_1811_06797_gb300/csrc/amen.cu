@@ -23,6 +23,8 @@
 //    (IGA_FP32) or FP64 (IGA_FP64); interfaces, SVD moves, residuals and the
 //    outer iterative refinement z <- z + delta run in FP64.
 #include <algorithm>
+#include <utility>
+#include <vector>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -170,6 +172,28 @@ __global__ void scale_rows_kernel(double* __restrict__ A, int rows, int cols,
   int r = (int)(idx / cols);
   double s = w[r];
   A[idx] = s > 0.0 ? A[idx] / sqrt(s) : 0.0;
+}
+
+// Y (m x rk col-major), column c = B(:, piv[c]) / ||B(:, piv[c])||, with
+// B(i, a) = B[i * si + a * sa]; one block (a multiple of 32 threads) per column
+__global__ void gather_unit_cols_kernel(const double* __restrict__ B, int m, int si, int sa,
+                                        const int* __restrict__ piv, double* __restrict__ Y) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const size_t a = (size_t)piv[c] * sa;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double v = B[(size_t)i * si + a];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    Y[(size_t)c * m + i] = B[(size_t)i * si + a] * inv;
 }
 
 __global__ void inv_sqrt_abs_kernel(const double* __restrict__ w, int k, double floor_rel,
@@ -379,10 +403,11 @@ __global__ void kkt_block_factor_kernel(
 
 // Solve every block system in place; the right-hand side of block (a, b) is
 // v[l](a, i, b) of a (3, r0, n, r1) tensor (node-interleaved as 3 i + l).
-// One warp per block, the working vector in shared memory.
-template <typename T>
+// One warp per block, the working vector in shared memory.  The factors and
+// the substitutions are in precision T, the vector v in precision V.
+template <typename T, typename V>
 __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
-                                       const int* __restrict__ piv, T* __restrict__ v,
+                                       const int* __restrict__ piv, V* __restrict__ v,
                                        int lu_in_smem) {
   extern __shared__ unsigned char smraw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -405,7 +430,7 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
   const size_t comp = (size_t)L.r0 * n * L.r1;
   for (int I = lane; I < N; I += 32) {
     int i = I / 3, l = I - 3 * i;
-    s[I] = v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b];
+    s[I] = (T)v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b];
   }
   __syncwarp();
   for (int k = 0; k < N; ++k) {
@@ -431,7 +456,7 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
   }
   for (int I = lane; I < N; I += 32) {
     int i = I / 3, l = I - 3 * i;
-    v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b] = s[I];
+    v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b] = (V)s[I];
   }
 }
 
@@ -517,6 +542,7 @@ static const T* bands_of(const iga_op* op, int d) {
 
 template <typename T>
 struct Solver {
+  using P = float;                     // precision of the block preconditioner
   iga_ctx* ctx;
   const iga_op* op[2];                 // 0: M, 1: K
   double beta;
@@ -526,6 +552,7 @@ struct Solver {
   int kick, rmax;
   double inner_tol;
   double trunc_tol;
+  bool svd_moves = false;        // Gram eigen-decomposition instead of pivoted Cholesky
   CoreNZ nz[2][3];
   DevBuf<double> X[3];                 // TT cores (FP64 master)
   DevBuf<double> Xh;                   // block core (3, r_d, n_d, r_{d+1})
@@ -709,6 +736,22 @@ struct Solver {
     return std::max(1, std::min(rk, rmax));
   }
 
+  int* piv_dev(int k) { return scratch<int>(ctx, SLOT_AMEN_BASE + 18, (size_t)k + 1); }
+
+  // rank-revealing column choice on the normalised Gram matrix G (k x k):
+  // the truncation keeps the chosen columns of the block core, with the
+  // projection error of each field bounded by trunc_tol as for the SVD
+  int pivot_columns(double* G, int k, int m) {
+    int* piv = piv_dev(k);
+    int* rkd = piv + k;
+    double* dsel = slot(9, k);
+    pivoted_cholesky(ctx, G, k, trunc_tol, std::min(rmax, m), piv, dsel, rkd);
+    int rk = 1;
+    IGA_CUDA(cudaMemcpyAsync(&rk, rkd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return std::max(1, std::min(rk, std::min(rmax, m)));
+  }
+
   // move the block index from core d to d+1 (forward) with enrichment
   void move_forward(int d, const double* res) {
     int r0 = r[d], nn = n[d], r1 = r[d + 1];
@@ -724,18 +767,26 @@ struct Solver {
     // coefficients below are exact projections of the unscaled core)
     double* sc = slot(17, 3);
     IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r1, sc);
-    jacobi_eig(ctx, G, V, w, c3);        // V col-major: columns = right singular vectors
-    IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r1, sc);
-    std::vector<double> lam(c3);
-    IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-    int rk = std::min(trunc_rank(lam, trunc_tol), m);
+    int rk;
+    double* Y;
+    if (svd_moves) {
+      jacobi_eig(ctx, G, V, w, c3);      // V col-major: columns = right singular vectors
+      IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r1, sc);
+      std::vector<double> lam(c3);
+      IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+      rk = std::min(trunc_rank(lam, trunc_tol), m);
+      Y = slot(10, (size_t)m * (rk + kick));         // col-major (m x nr): [U_k, E]
+      // U_k^T = Sigma^-1 V_k^T Mx^T  (row-major rk x m == col-major m x rk)
+      rm_gemm(ctx, false, true, rk, m, c3, V, c3, Mx, c3, Y, m);
+      IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
+    } else {
+      rk = pivot_columns(G, c3, m);
+      Y = slot(10, (size_t)m * (rk + kick));         // col-major (m x nr): [Mx(:, piv), E]
+      IGA_LAUNCH(ctx, gather_unit_cols_kernel, rk, 256, 0, Mx, m, c3, 1, piv_dev(c3), Y);
+    }
     int kk = std::max(0, std::min(kick, m - rk));
     int nr = rk + kk;
-    double* Y = slot(10, (size_t)m * nr);           // col-major (m x nr): [U_k, E]
-    // U_k^T = Sigma^-1 V_k^T Mx^T  (row-major rk x m == col-major m x rk)
-    rm_gemm(ctx, false, true, rk, m, c3, V, c3, Mx, c3, Y, m);
-    IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
     if (kk > 0) {
       int keep = kick;
       kick = kk;
@@ -769,18 +820,27 @@ struct Solver {
     rm_gemm(ctx, false, true, c3, c3, m, Mx, m, Mx, m, G, c3);
     double* sc = slot(17, 3);
     IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r0, sc);
-    jacobi_eig(ctx, G, V, w, c3);                   // columns: left singular vectors
-    IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r0, sc);
-    std::vector<double> lam(c3);
-    IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-    int rk = std::min(trunc_rank(lam, trunc_tol), m);
+    int rk;
+    double* Y;
+    if (svd_moves) {
+      jacobi_eig(ctx, G, V, w, c3);                 // columns: left singular vectors
+      IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r0, sc);
+      std::vector<double> lam(c3);
+      IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+      rk = std::min(trunc_rank(lam, trunc_tol), m);
+      Y = slot(10, (size_t)m * (rk + kick));
+      // W_k^T = Sigma^-1 U_k^T Mx (row-major rk x m == col-major m x rk)
+      rm_gemm(ctx, false, false, rk, m, c3, V, c3, Mx, m, Y, m);
+      IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
+    } else {
+      rk = pivot_columns(G, c3, m);
+      // candidate a is row a of Mx (row-major 3 r0 x m)
+      Y = slot(10, (size_t)m * (rk + kick));
+      IGA_LAUNCH(ctx, gather_unit_cols_kernel, rk, 256, 0, Mx, m, 1, m, piv_dev(c3), Y);
+    }
     int kk = std::max(0, std::min(kick, m - rk));
     int nr = rk + kk;
-    double* Y = slot(10, (size_t)m * nr);
-    // W_k^T = Sigma^-1 U_k^T Mx (row-major rk x m == col-major m x rk)
-    rm_gemm(ctx, false, false, rk, m, c3, V, c3, Mx, m, Y, m);
-    IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
     if (kk > 0) {
       int keep = kick;
       kick = kk;
@@ -892,7 +952,8 @@ struct Solver {
       ks[cnt] = rr;
       ++cnt;
     }
-    if (cnt > 0) jacobi_eig_batched(ctx, As, Ws, ws, ks, cnt);
+    // the eigenbases only shape the preconditioner: FP32 rotations suffice
+    if (cnt > 0) jacobi_eig_batched(ctx, As, Ws, ws, ks, cnt, true);
     cnt = 0;
     for (int side = 0; side < 2; ++side) {
       int rr = rrs[side];
@@ -913,14 +974,16 @@ struct Solver {
     VRt.ensure((size_t)r1 * r1);
     IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r0 * r0), 256, 0, Vs[0], VLt.p, (size_t)r0 * r0);
     IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r1 * r1), 256, 0, Vs[1], VRt.p, (size_t)r1 * r1);
-    T* tdLM = tslot(44, (size_t)zM.R0 * r0);
-    T* tdLK = tslot(45, (size_t)zK.R0 * r0);
-    T* tdRM = tslot(46, (size_t)zM.R1 * r1);
-    T* tdRK = tslot(47, (size_t)zK.R1 * r1);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zM.R0 * r0), 256, 0, dLM, tdLM, (size_t)zM.R0 * r0);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zK.R0 * r0), 256, 0, dLK, tdLK, (size_t)zK.R0 * r0);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zM.R1 * r1), 256, 0, dRM, tdRM, (size_t)zM.R1 * r1);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(zK.R1 * r1), 256, 0, dRK, tdRK, (size_t)zK.R1 * r1);
+    // the block factors are FP32 in both precisions: they only precondition
+    // GMRES, which keeps the preconditioned directions (flexible form)
+    P* tdLM = scratch<P>(ctx, SLOT_AMEN_BASE + 44, (size_t)zM.R0 * r0);
+    P* tdLK = scratch<P>(ctx, SLOT_AMEN_BASE + 45, (size_t)zK.R0 * r0);
+    P* tdRM = scratch<P>(ctx, SLOT_AMEN_BASE + 46, (size_t)zM.R1 * r1);
+    P* tdRK = scratch<P>(ctx, SLOT_AMEN_BASE + 47, (size_t)zK.R1 * r1);
+    IGA_LAUNCH(ctx, to_type_kernel<P>, nblk(zM.R0 * r0), 256, 0, dLM, tdLM, (size_t)zM.R0 * r0);
+    IGA_LAUNCH(ctx, to_type_kernel<P>, nblk(zK.R0 * r0), 256, 0, dLK, tdLK, (size_t)zK.R0 * r0);
+    IGA_LAUNCH(ctx, to_type_kernel<P>, nblk(zM.R1 * r1), 256, 0, dRM, tdRM, (size_t)zM.R1 * r1);
+    IGA_LAUNCH(ctx, to_type_kernel<P>, nblk(zK.R1 * r1), 256, 0, dRK, tdRK, (size_t)zK.R1 * r1);
     BL.n = c.nn;
     BL.p = op[0]->p[c.d];
     BL.kl = BL.ku = 3 * BL.p + 2;
@@ -929,30 +992,33 @@ struct Solver {
     BL.r0 = r0;
     BL.r1 = r1;
     BL.NB = r0 * r1;
-    T* A = tslot(48, (size_t)BL.N * BL.W * BL.NB);
+    P* A = scratch<P>(ctx, SLOT_AMEN_BASE + 48, (size_t)BL.N * BL.W * BL.NB);
     int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, (size_t)BL.N * BL.NB);
     IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
-    size_t perw = (size_t)BL.N * BL.W * sizeof(T);
+    size_t perw = (size_t)BL.N * BL.W * sizeof(P);
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perw));
     int use_smem = perw <= 200 * 1024;
     size_t smem = use_smem ? perw * wpb : 0;
     if (!use_smem) wpb = 4;
     static bool attr = false;
     if (!attr) {
-      IGA_CUDA(cudaFuncSetAttribute(kkt_block_factor_kernel<T>,
+      IGA_CUDA(cudaFuncSetAttribute(kkt_block_factor_kernel<P>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
       attr = true;
     }
-    IGA_LAUNCH(ctx, kkt_block_factor_kernel<T>, nblk(BL.NB, wpb), 32 * wpb, smem, BL, (T)beta,
-               bands_of<T>(op[0], c.d), zM.dl.p, zM.dr.p, zM.doff.p, (int)zM.l.size(),
-               bands_of<T>(op[1], c.d), zK.dl.p, zK.dr.p, zK.doff.p, (int)zK.l.size(), tdLM, tdRM,
+    // algorithmic: banded LU with partial pivoting, 2 N kl (kl + ku) flop per block
+    prof_count(ctx, (double)BL.NB * BL.N * BL.W * sizeof(P),
+               2.0 * BL.NB * BL.N * (double)BL.kl * (BL.kl + BL.ku));
+    IGA_LAUNCH(ctx, kkt_block_factor_kernel<P>, nblk(BL.NB, wpb), 32 * wpb, smem, BL, (P)beta,
+               bands_of<P>(op[0], c.d), zM.dl.p, zM.dr.p, zM.doff.p, (int)zM.l.size(),
+               bands_of<P>(op[1], c.d), zK.dl.p, zK.dr.p, zK.doff.p, (int)zK.l.size(), tdLM, tdRM,
                tdLK, tdRK, A, piv, ctx->dflag, use_smem);
   }
 
   void precond_apply(const Local& c, const T* v, T* z) {
     size_t per = (size_t)3 * c.L;
     T* t = tslot(24, per);
-    T* A = tslot(48, 1);
+    const P* A = scratch<P>(ctx, SLOT_AMEN_BASE + 48, 1);
     int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, 1);
     // w = VL^T v VR
     IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
@@ -960,18 +1026,21 @@ struct Solver {
     {
       // keep each block's LU factor in shared memory when four of them fit
       size_t per = (size_t)BL.N * BL.W;
-      size_t perw = (per + BL.N) * sizeof(T);
+      size_t perw = (per + BL.N) * sizeof(P);
       int lu_smem = perw <= 200 * 1024;
       const int wpb = lu_smem ? (int)std::min<size_t>(4, (200 * 1024) / perw) : 4;
-      size_t smem = (size_t)wpb * ((lu_smem ? per : 0) + BL.N) * sizeof(T);
+      size_t smem = (size_t)wpb * ((lu_smem ? per : 0) + BL.N) * sizeof(P);
       static bool attr = false;
       if (!attr) {
-        IGA_CUDA(cudaFuncSetAttribute(kkt_block_solve_kernel<T>,
+        IGA_CUDA(cudaFuncSetAttribute(kkt_block_solve_kernel<P, T>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
         attr = true;
       }
-      IGA_LAUNCH(ctx, kkt_block_solve_kernel<T>, nblk(BL.NB, wpb), 32 * wpb, smem, BL, A, piv, z,
-                 lu_smem);
+      // algorithmic: forward and back substitution, 2 N (2 kl + ku) flop per block
+      prof_count(ctx, (double)BL.NB * BL.N * (BL.W * sizeof(P) + 2 * sizeof(T)),
+                 2.0 * BL.NB * BL.N * (double)(2 * BL.kl + BL.ku));
+      IGA_LAUNCH(ctx, (kkt_block_solve_kernel<P, T>), nblk(BL.NB, wpb), 32 * wpb, smem, BL, A, piv,
+                 z, lu_smem);
     }
     // back: VL z VR^T
     IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, z, 1, 3, c.r0, c.nn, c.r1, 1, t);
@@ -1137,6 +1206,35 @@ struct Solver {
   }
 };
 
+// Device time of the solve's phases: an event on the context stream at every
+// phase boundary, the durations summed once the solve has synchronised.
+enum { PH_LOCAL = 0, PH_RESID, PH_MOVE, PH_REFINE, PH_COUNT };
+struct PhaseClock {
+  cudaStream_t stream = nullptr;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  void mark(int ph) {
+    cudaEvent_t e;
+    IGA_CUDA(cudaEventCreate(&e));
+    marks.push_back({ph, e});
+    IGA_CUDA(cudaEventRecord(e, stream));
+  }
+  // adds the phase durations (s) to t[PH_COUNT]; the stream is synchronised
+  void collect(double* t) {
+    for (size_t i = 0; i + 1 < marks.size(); ++i) {
+      float ms = 0.f;
+      if (marks[i].first >= 0 &&
+          cudaEventElapsedTime(&ms, marks[i].second, marks[i + 1].second) == cudaSuccess)
+        t[marks[i].first] += 1e-3 * ms;
+    }
+    release();
+  }
+  void release() {
+    for (auto& m : marks) cudaEventDestroy(m.second);
+    marks.clear();
+  }
+  ~PhaseClock() { release(); }
+};
+
 // full FP64 KKT residual res = F - KKT z, returns ||res||_2 (synchronises)
 static double kkt_residual(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
                            const double* F, const double* z, double* res, size_t N) {
@@ -1149,7 +1247,8 @@ static double kkt_residual(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
 template <typename T>
 static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
                            const double* F, double Fnorm, double tol, const iga_solve_opts* o,
-                           double* delta, int* sweeps_out, int* maxrank, int* liters, double* resid) {
+                           double* delta, int* sweeps_out, int* maxrank, int* liters, double* resid,
+                           PhaseClock* clk) {
   Solver<T> S;
   S.ctx = ctx;
   S.op[0] = M;
@@ -1163,6 +1262,7 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   // per-field truncation: the KKT residual amplifies the truncation error of
   // the solution, so truncate well below the residual target
   S.trunc_tol = o->trunc_tol > 0.0 ? o->trunc_tol : 1e-3 * tol;
+  S.svd_moves = o->truncation == IGA_TRUNC_SVD;
   S.verbose = o->verbose;
   size_t N = S.N;
   for (int op = 0; op < 2; ++op)
@@ -1212,11 +1312,14 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
       int d = order[s];
       if (sweep > 0 && s == 0) {
         // the first core of this sweep was solved last in the previous sweep
+        clk->mark(PH_MOVE);
         if (fwd) S.move_forward(d, res);
         else S.move_backward(d, res);
         continue;
       }
+      clk->mark(PH_LOCAL);
       S.local_solve(d, F, tol_abs, maxit);
+      clk->mark(PH_RESID);
       S.expand(d, delta);
       double rn = kkt_residual(ctx, M, K, beta, F, delta, res, N);
       rel = rn / Fnorm;
@@ -1225,6 +1328,7 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
                 d, S.r[1], S.r[2], S.local_iters, rel);
       if (rel <= tol) { ++sweep; goto done; }
       if (s < 2) {
+        clk->mark(PH_MOVE);
         if (fwd) S.move_forward(d, res);
         else S.move_backward(d, res);
       }
@@ -1254,6 +1358,7 @@ extern "C" void iga_solve_opts_default(iga_solve_opts* o) {
   o->precision = IGA_FP64;
   o->verbose = 0;
   o->trunc_tol = 0.0;
+  o->truncation = IGA_TRUNC_PIVOTED;
 }
 
 extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K,
@@ -1270,6 +1375,8 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     iga_solve_opts o;
     if (opts) o = *opts; else iga_solve_opts_default(&o);
     IGA_REQUIRE(o.tol > 0.0 && o.inner_tol >= 0.0, "kkt_solve_amen: bad tolerances");
+    IGA_REQUIRE(o.truncation == IGA_TRUNC_PIVOTED || o.truncation == IGA_TRUNC_SVD,
+                "kkt_solve_amen: unknown truncation");
     IGA_REQUIRE(o.precision == IGA_FP64 || o.precision == IGA_FP32,
                 "kkt_solve_amen: precision must be IGA_FP64 or IGA_FP32");
     IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
@@ -1288,6 +1395,8 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     }
     double Fn = device_norm2(ctx, F, 3 * N);
     iga_solve_info inf{};
+    PhaseClock clk;
+    clk.stream = ctx->stream;
     double rel = 0.0;
     bool ok = Fn == 0.0;
     if (!ok) {
@@ -1304,10 +1413,11 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
         double cres = 1.0;
         if (o.precision == IGA_FP64)
           amen_correction<double>(ctx, M, K, beta, r, rn, itol, &o, delta, &inf.sweeps,
-                                  &inf.max_rank, &inf.local_iters, &cres);
+                                  &inf.max_rank, &inf.local_iters, &cres, &clk);
         else
           amen_correction<float>(ctx, M, K, beta, r, rn, itol, &o, delta, &inf.sweeps,
-                                 &inf.max_rank, &inf.local_iters, &cres);
+                                 &inf.max_rank, &inf.local_iters, &cres, &clk);
+        clk.mark(PH_REFINE);
         IGA_LAUNCH(ctx, axpy_kernel, nblk(3 * N), 256, 0, z, delta, 1.0, 3 * N);
         rn = kkt_residual(ctx, M, K, beta, F, z, r, N);
         inf.refinements = it + 1;
@@ -1321,7 +1431,14 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     IGA_CUDA(cudaMemcpyAsync(y, z, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     IGA_CUDA(cudaMemcpyAsync(u, z + N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     IGA_CUDA(cudaMemcpyAsync(lam, z + 2 * N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    clk.mark(-1);
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    double ph[PH_COUNT] = {0.0, 0.0, 0.0, 0.0};
+    clk.collect(ph);
+    inf.t_local = ph[PH_LOCAL];
+    inf.t_residual = ph[PH_RESID];
+    inf.t_move = ph[PH_MOVE];
+    inf.t_refine = ph[PH_REFINE];
     inf.residual = rel;
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;

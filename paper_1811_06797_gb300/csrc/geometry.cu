@@ -440,6 +440,11 @@ struct GeoSampler {
     G.qn2 = qn2;
     IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
     int threads = 256;
+    // algorithmic per point: 16 (p1 + 1) FMA for the map and its derivatives,
+    // about 150 flop for the quotient rule, det, adjugate and target; one
+    // (comp >= 0) or eight FP64 outputs written
+    prof_count(ctx, (double)total * 8.0 * (comp < 0 ? 8 : 1),
+               (double)total * (32.0 * (G.pg[0] + 1) + 150.0));
     IGA_LAUNCH(ctx, sample_weights_kernel, (unsigned)((total + threads - 1) / threads), threads, 0,
                G, out, ctx->dflag);
     IGA_CUDA(cudaMemcpyAsync(ctx->hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost,

@@ -211,11 +211,18 @@ void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, 
              int rmax, iga_tt** out);
 double device_norm2(iga_ctx* ctx, const double* x, size_t n);   // synchronises
 void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k);  // device, col-major
+// fp32: run the rotations in FP32 (shared memory; falls back to FP64 when the
+// problem does not fit), for eigenbases that only feed a preconditioner
 void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double* const* w,
-                        const int* k, int count);
+                        const int* k, int count, bool fp32 = false);
 void gen_eig_prep(iga_ctx* ctx, const double* PM, int SM, const double* PK, int SK, int k,
                   double* work, double* C, double* Linv);
 void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k);  // Y overwritten
+// rank-revealing pivoted Cholesky of a PSD Gram matrix (col-major, lower
+// triangle overwritten): piv[0..rk) chosen indices, dsel their pivots, *rk
+// (device) the rank at which the Schur trace drops to rel^2 trace(G), <= jmax
+void pivoted_cholesky(iga_ctx* ctx, double* G, int k, double rel, int jmax, int* piv,
+                      double* dsel, int* rk);
 void fill_gaussian(iga_ctx* ctx, double* x, size_t n, uint64_t seed);
 void transpose_cm(iga_ctx* ctx, const double* A, int rows, int cols, double* B);
 

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "iga_internal.cuh"
 
 namespace iga {
@@ -174,9 +176,209 @@ __global__ void householder_qr_kernel(double* __restrict__ Y, double* __restrict
   }
 }
 
+// Householder QR with the rows of Y split over the CTAs of one thread-block
+// cluster: CTA c holds rows [c mc, (c + 1) mc) of Y and of Q in shared memory,
+// and the column norms and the reflector dot products of every step are
+// summed across the cluster through distributed shared memory.  The FP64
+// work is spread over up to 16 SMs; every CTA takes the same decisions from
+// the same sums, so all of them pass the same cluster barriers.
+namespace cgx = cooperative_groups;
+
+__device__ __forceinline__ double qr_block_sum(double v, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(256) householder_qr_cluster_kernel(
+    const double* __restrict__ Y, double* __restrict__ Q, int m, int k, int mc) {
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int C = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  extern __shared__ double sm[];
+  double* A = sm;                               // mc x k, leading dimension mc
+  double* Ql = A + (size_t)mc * k;              // mc x k
+  double* pw = Ql + (size_t)mc * k;             // 2 x k partial dot products
+  double* ps = pw + 2 * k;                      // [partial sum of squares, alpha]
+  double* tau = ps + 2;                         // k
+  double* wsum = tau + k;                       // k
+  double* red = wsum + k;                       // 32
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r0 = me * mc;
+  const int nloc = max(0, min(m, r0 + mc) - r0);
+  for (int t = threadIdx.x; t < mc * k; t += blockDim.x) {
+    int i = t % mc, c = t / mc;
+    A[t] = i < nloc ? Y[(size_t)c * m + r0 + i] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    // local rows i >= j of this CTA: [lo, nloc)
+    const int lo = min(nloc, max(0, j - r0));
+    const int own = j / mc;                     // CTA holding row j
+    double s = 0.0;
+    for (int i = lo + threadIdx.x; i < nloc; i += blockDim.x)
+      if (r0 + i > j) s += A[(size_t)j * mc + i] * A[(size_t)j * mc + i];
+    s = qr_block_sum(s, red);
+    if (threadIdx.x == 0) {
+      ps[0] = s;
+      ps[1] = (me == own) ? A[(size_t)j * mc + (j - r0)] : 0.0;
+    }
+    cl.sync();
+    double sig2 = 0.0;
+    for (int c = 0; c < C; ++c) sig2 += cl.map_shared_rank(ps, c)[0];
+    const double alpha = cl.map_shared_rank(ps, own)[1];
+    const double nrm = sqrt(alpha * alpha + sig2);
+    double tj = 0.0, inv = 0.0;
+    if (nrm > 0.0) {
+      const double beta = alpha >= 0.0 ? -nrm : nrm;
+      const double v0 = alpha - beta;
+      tj = -v0 / beta;
+      inv = 1.0 / v0;
+    }
+    if (threadIdx.x == 0) tau[j] = tj;
+    if (tj != 0.0) {
+      for (int i = lo + threadIdx.x; i < nloc; i += blockDim.x) {
+        if (r0 + i > j) A[(size_t)j * mc + i] *= inv;
+        else A[(size_t)j * mc + i] = 1.0;       // v_j = 1
+      }
+    }
+    __syncthreads();
+    // partial w_t = sum_i v_i A(i, t), t > j
+    double* pb = pw + (j & 1) * k;
+    for (int t = j + 1 + wid; t < k; t += nw) {
+      double d = 0.0;
+      if (tj != 0.0)
+        for (int i = lo + lane; i < nloc; i += 32) d += A[(size_t)j * mc + i] * A[(size_t)t * mc + i];
+      d = warp_sum(d);
+      if (lane == 0) pb[t] = d;
+    }
+    cl.sync();
+    for (int t = j + 1 + threadIdx.x; t < k; t += blockDim.x) {
+      double w = 0.0;
+      for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
+      wsum[t] = w;
+    }
+    __syncthreads();
+    if (tj != 0.0) {
+      const int w = k - j - 1;
+      for (int e = threadIdx.x; e < w * (nloc - lo); e += blockDim.x) {
+        int t = j + 1 + e / (nloc - lo), i = lo + e % (nloc - lo);
+        A[(size_t)t * mc + i] -= tj * A[(size_t)j * mc + i] * wsum[t];
+      }
+    }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{k-1} [I; 0], the last reflector first
+  for (int t = threadIdx.x; t < mc * k; t += blockDim.x) {
+    int i = t % mc, c = t / mc;
+    Ql[t] = (r0 + i == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int it = 0;                                   // applied reflectors: buffer parity
+  for (int j = k - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    if (tj == 0.0) continue;                    // the same in every CTA
+    const int lo = min(nloc, max(0, j - r0));
+    double* pb = pw + (it++ & 1) * k;
+    for (int t = j + wid; t < k; t += nw) {
+      double d = 0.0;
+      for (int i = lo + lane; i < nloc; i += 32) d += A[(size_t)j * mc + i] * Ql[(size_t)t * mc + i];
+      d = warp_sum(d);
+      if (lane == 0) pb[t] = d;
+    }
+    cl.sync();
+    for (int t = j + threadIdx.x; t < k; t += blockDim.x) {
+      double w = 0.0;
+      for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
+      wsum[t] = w;
+    }
+    __syncthreads();
+    const int w = k - j;
+    for (int e = threadIdx.x; e < w * (nloc - lo); e += blockDim.x) {
+      int t = j + e / (nloc - lo), i = lo + e % (nloc - lo);
+      Ql[(size_t)t * mc + i] -= tj * A[(size_t)j * mc + i] * wsum[t];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < mc * k; t += blockDim.x) {
+    int i = t % mc, c = t / mc;
+    if (i < nloc) Q[(size_t)c * m + r0 + i] = Ql[t];
+  }
+  // no CTA leaves while another may still read its shared memory
+  cl.sync();
+}
+
+static size_t qr_cluster_smem(int mc, int k) {
+  return ((size_t)2 * mc * k + 5 * (size_t)k + 2 + 32) * sizeof(double);
+}
+
 void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
   IGA_REQUIRE(k >= 1 && k <= 1024 && m >= k, "householder_qr: bad sizes");
+  // algorithmic: Householder QR 2 m k^2 - 2 k^3 / 3, forming Q the same again
+  const double by = 3.0 * 8.0 * m * k;
+  const double fl = 2.0 * (2.0 * m * k * k - 2.0 * k * k * k / 3.0);
+  // cluster of up to 16 CTAs with at least 64 rows each, when a slice fits
+  const size_t limit = 200 * 1024;
+  static int cmax = 0;                          // largest schedulable cluster
+  if (cmax == 0) {
+    IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+    IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
+                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cmax = 1;
+    for (int c : {16, 8}) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(c);
+      q.blockDim = dim3(256);
+      q.dynamicSmemBytes = limit;
+      cudaLaunchAttribute a[1];
+      a[0].id = cudaLaunchAttributeClusterDimension;
+      a[0].val.clusterDim.x = c;
+      a[0].val.clusterDim.y = 1;
+      a[0].val.clusterDim.z = 1;
+      q.attrs = a;
+      q.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, householder_qr_cluster_kernel, &q) == cudaSuccess &&
+          n >= 1) {
+        cmax = c;
+        break;
+      }
+      (void)cudaGetLastError();
+    }
+  }
+  int C = std::max(1, std::min(cmax, m / 64));
+  int mc = (m + C - 1) / C;
+  if (C >= 2 && qr_cluster_smem(mc, k) <= limit) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = qr_cluster_smem(mc, k);
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    prof_count(ctx, by, fl);
+    bool prof = prof_match(ctx, "householder_qr_cluster_kernel");
+    if (prof) prof_start(ctx);
+    IGA_CUDA(cudaLaunchKernelEx(&cfg, householder_qr_cluster_kernel, (const double*)Y, Q, m, k,
+                                mc));
+    if (prof) prof_stop(ctx);
+    ctx->launches++;
+    ctx->next_bytes = 0.0;
+    ctx->next_flops = 0.0;
+    return;
+  }
   size_t smem = (size_t)(k + 32) * sizeof(double);
+  prof_count(ctx, by, fl);
   IGA_LAUNCH(ctx, householder_qr_kernel, 1, 1024, smem, Y, Q, m, k);
 }
 
@@ -185,10 +387,11 @@ void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
 // Symmetric A (k x k, col-major) -> eigenvalues w (descending) and
 // eigenvectors V (columns).  Cyclic Jacobi with round-robin parallel
 // ordering: each round applies k/2 disjoint rotations (rows, then columns).
-// At most 40 sweeps; stops when the off-diagonal norm is below 1e-14 times
-// the Frobenius norm.  A is overwritten.  Storage: mode 2 keeps A and V in
+// At most 40 sweeps; stops when the off-diagonal norm is below 1e-14 (FP64)
+// or 1e-6 (FP32) times the Frobenius norm.  Storage: mode 2 keeps A and V in
 // shared memory, mode 1 keeps A in shared memory and V in global memory,
-// mode 0 keeps both in global memory.
+// mode 0 keeps both in global memory (A overwritten).  The FP32 variant
+// (T = float) always runs in mode 2; input and output stay FP64.
 struct JacobiProblem {
   double* A;
   double* Vwork;
@@ -201,55 +404,79 @@ struct JacobiBatch {
   JacobiProblem p[4];
 };
 
+template <typename T>
+struct JacobiTol;
+template <>
+struct JacobiTol<double> {
+  static constexpr double off2 = 1e-28, skip = 1e-17, tiny = 1e-300;
+};
+template <>
+struct JacobiTol<float> {
+  static constexpr float off2 = 1e-12f, skip = 1e-8f, tiny = 1e-30f;
+};
+
+template <typename T>
+__host__ __device__ inline size_t jacobi_head_bytes(int k) {
+  int kk = k + (k & 1);
+  size_t b = (size_t)(kk / 2) * (2 * sizeof(T) + 2 * sizeof(int));
+  b = (b + 7) / 8 * 8;
+  return b + 32 * sizeof(double);
+}
+
+template <typename T>
 __global__ void jacobi_eig_kernel(JacobiBatch batch) {
   extern __shared__ double sm[];
   const JacobiProblem& P = batch.p[blockIdx.x];
   double* __restrict__ Ag = P.A;
-  double* __restrict__ Vwork = P.Vwork;
   double* __restrict__ Vout = P.Vout;
   double* __restrict__ w = P.w;
   const int k = P.k;
   const int mode = P.mode;
   int kk = k + (k & 1);
   int npair = kk / 2;
-  double* cs = sm;                 // npair
-  double* sn = sm + npair;         // npair
-  int* pp = (int*)(sm + 2 * npair);
+  T* cs = (T*)sm;                  // npair
+  T* sn = cs + npair;              // npair
+  int* pp = (int*)(sn + npair);
   int* qq = pp + npair;
-  double* red = sm + 2 * npair + npair + 1;   // 32 doubles
-  double* A = Ag;
-  double* V = Vwork;
+  double* red = (double*)((char*)sm + (jacobi_head_bytes<T>(k) - 32 * sizeof(double)));
+  T* A;
+  T* V;
+  if constexpr (sizeof(T) == sizeof(double)) {
+    A = (T*)Ag;
+    V = (T*)P.Vwork;
+  }
   if (mode >= 1) {
-    A = red + 32;
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) A[t] = Ag[t];
+    A = (T*)(red + 32);
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) A[t] = (T)Ag[t];
   }
   if (mode == 2) V = A + (size_t)k * k;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) V[t] = ((t % k) == (t / k)) ? 1.0 : 0.0;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) V[t] = ((t % k) == (t / k)) ? T(1) : T(0);
   __syncthreads();
   double fro2 = 0.0;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) fro2 += A[t] * A[t];
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) fro2 += (double)A[t] * (double)A[t];
   fro2 = block_sum(fro2, red);
   for (int sweep = 0; sweep < 40 && k > 1; ++sweep) {
     double off2 = 0.0;
     for (int t = threadIdx.x; t < k * k; t += blockDim.x)
-      if ((t % k) != (t / k)) off2 += A[t] * A[t];
+      if ((t % k) != (t / k)) off2 += (double)A[t] * (double)A[t];
     off2 = block_sum(off2, red);
-    if (off2 <= 1e-28 * fro2 || off2 == 0.0) break;
+    if (off2 <= (double)JacobiTol<T>::off2 * fro2 || off2 == 0.0) break;
     for (int r = 0; r < kk - 1; ++r) {
       for (int i = threadIdx.x; i < npair; i += blockDim.x) {
         int p, q;
         if (i == 0) { p = kk - 1; q = r; }
         else { p = (r + i) % (kk - 1); q = (r - i + kk - 1) % (kk - 1); }
         if (p > q) { int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
+        T c = T(1), s = T(0);
         if (q < k) {
-          double apq = A[(size_t)q * k + p];
-          double app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
-          if (apq != 0.0 && fabs(apq) > 1e-300 + 1e-17 * sqrt(fabs(app * aqq))) {
-            double tau = (aqq - app) / (2.0 * apq);
-            double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                    : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+          T apq = A[(size_t)q * k + p];
+          T app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
+          if (apq != T(0) &&
+              fabs(apq) > JacobiTol<T>::tiny + JacobiTol<T>::skip * sqrt(fabs(app * aqq))) {
+            T tau = (aqq - app) / (T(2) * apq);
+            T t = (tau >= T(0)) ? T(1) / (tau + sqrt(T(1) + tau * tau))
+                                : T(-1) / (-tau + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
             s = t * c;
           }
         }
@@ -259,10 +486,10 @@ __global__ void jacobi_eig_kernel(JacobiBatch batch) {
       // rows p, q of A:  a_p <- c a_p - s a_q,  a_q <- s a_p + c a_q
       for (int t = threadIdx.x; t < npair * k; t += blockDim.x) {
         int i = t / k, col = t % k;
-        if (sn[i] == 0.0) continue;
+        if (sn[i] == T(0)) continue;
         int p = pp[i], q = qq[i];
-        double c = cs[i], s = sn[i];
-        double ap = A[(size_t)col * k + p], aq = A[(size_t)col * k + q];
+        T c = cs[i], s = sn[i];
+        T ap = A[(size_t)col * k + p], aq = A[(size_t)col * k + q];
         A[(size_t)col * k + p] = c * ap - s * aq;
         A[(size_t)col * k + q] = s * ap + c * aq;
       }
@@ -270,13 +497,13 @@ __global__ void jacobi_eig_kernel(JacobiBatch batch) {
       // columns p, q of A and V
       for (int t = threadIdx.x; t < npair * k; t += blockDim.x) {
         int i = t / k, row = t % k;
-        if (sn[i] == 0.0) continue;
+        if (sn[i] == T(0)) continue;
         int p = pp[i], q = qq[i];
-        double c = cs[i], s = sn[i];
-        double ap = A[(size_t)p * k + row], aq = A[(size_t)q * k + row];
+        T c = cs[i], s = sn[i];
+        T ap = A[(size_t)p * k + row], aq = A[(size_t)q * k + row];
         A[(size_t)p * k + row] = c * ap - s * aq;
         A[(size_t)q * k + row] = s * ap + c * aq;
-        double vp = V[(size_t)p * k + row], vq = V[(size_t)q * k + row];
+        T vp = V[(size_t)p * k + row], vq = V[(size_t)q * k + row];
         V[(size_t)p * k + row] = c * vp - s * vq;
         V[(size_t)q * k + row] = s * vp + c * vq;
       }
@@ -286,20 +513,20 @@ __global__ void jacobi_eig_kernel(JacobiBatch batch) {
   // sort descending: rank of each eigenvalue, then scatter columns
   __syncthreads();
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double wi = A[(size_t)i * k + i];
+    T wi = A[(size_t)i * k + i];
     int rank = 0;
     for (int j = 0; j < k; ++j) {
-      double wj = A[(size_t)j * k + j];
+      T wj = A[(size_t)j * k + j];
       if (wj > wi || (wj == wi && j < i)) ++rank;
     }
-    w[rank] = wi;
-    for (int row = 0; row < k; ++row) Vout[(size_t)rank * k + row] = V[(size_t)i * k + row];
+    w[rank] = (double)wi;
+    for (int row = 0; row < k; ++row) Vout[(size_t)rank * k + row] = (double)V[(size_t)i * k + row];
   }
   __syncthreads();
 }
 
 void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double* const* w,
-                        const int* k, int count) {
+                        const int* k, int count, bool fp32) {
   IGA_REQUIRE(count >= 1 && count <= 4, "jacobi_eig: batch of 1..4 problems");
   const size_t limit = 220 * 1024;
   JacobiBatch batch{};
@@ -308,9 +535,11 @@ void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double
   int kmax = 0;
   for (int i = 0; i < count; ++i) kmax = std::max(kmax, k[i]);
   IGA_REQUIRE(kmax >= 1 && kmax <= 1024, "jacobi_eig: k out of range");
-  int kkm = kmax + (kmax & 1);
-  size_t head = (size_t)(2 * (kkm / 2) + (kkm / 2) + 1 + 32) * sizeof(double);
-  size_t one = (size_t)kmax * kmax * sizeof(double);
+  // the FP32 variant needs A and V in shared memory; larger problems run in FP64
+  size_t head32 = jacobi_head_bytes<float>(kmax);
+  fp32 = fp32 && head32 + 2 * (size_t)kmax * kmax * sizeof(float) <= limit;
+  size_t head = fp32 ? head32 : jacobi_head_bytes<double>(kmax);
+  size_t one = (size_t)kmax * kmax * (fp32 ? sizeof(float) : sizeof(double));
   int mode = head + 2 * one <= limit ? 2 : (head + one <= limit ? 1 : 0);
   smem = head + (mode == 2 ? 2 * one : (mode == 1 ? one : 0));
   for (int i = 0; i < count; ++i) {
@@ -327,11 +556,143 @@ void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double
   }
   static bool attr = false;
   if (!attr) {
-    IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)limit));
+    IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<double>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+    IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
     attr = true;
   }
-  IGA_LAUNCH(ctx, jacobi_eig_kernel, count, 1024, smem, batch);
+  {
+    // algorithmic: a symmetric eigen-decomposition with eigenvectors, 9 k^3 flop
+    double fl = 0.0, by = 0.0;
+    for (int i = 0; i < count; ++i) {
+      fl += 9.0 * (double)k[i] * k[i] * k[i];
+      by += 3.0 * 8.0 * (double)k[i] * k[i];
+    }
+    prof_count(ctx, by, fl);
+  }
+  if (fp32)
+    IGA_LAUNCH(ctx, jacobi_eig_kernel<float>, count, 1024, smem, batch);
+  else
+    IGA_LAUNCH(ctx, jacobi_eig_kernel<double>, count, 1024, smem, batch);
+}
+
+// ----------------------------------------------------- pivoted Cholesky
+//
+// Rank-revealing pivoted Cholesky of a symmetric positive semidefinite k x k
+// Gram matrix G = B^T B: at each step the index with the largest Schur
+// complement diagonal is chosen and eliminated.  After j steps the trace of
+// the Schur complement equals || B - Q_j Q_j^T B ||_F^2, Q_j an orthonormal
+// basis of the chosen columns of B (this is QR with column pivoting of B done
+// on its Gram matrix).  The factorisation stops at the first j with that trace
+// <= rel^2 trace(G), or at j = jmax, so the truncation error of the chosen
+// columns is bounded exactly like an SVD truncation's.
+//
+// Only the lower triangle (row >= column, col-major) is read and updated.
+// Mode 1 keeps the matrix in shared memory, mode 0 works on G in place.
+
+__global__ void pivoted_cholesky_kernel(double* __restrict__ Gg, int k, double rel, int jmax,
+                                        int mode, int* __restrict__ piv,
+                                        double* __restrict__ dsel, int* __restrict__ rk_out) {
+  extern __shared__ double sm[];
+  double* red = sm;                      // 32 sums + 32 maxima
+  double* lv = sm + 64;                  // k
+  int* perm = (int*)(lv + k);            // k (+1 padding to 8 bytes)
+  int* ired = perm + k + (k & 1);        // 32 arg indices
+  double* S = Gg;
+  if (mode == 1) {
+    S = (double*)(ired + 32);
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) S[t] = Gg[t];
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) perm[i] = i;
+  __syncthreads();
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) tr += fmax(S[(size_t)i * k + i], 0.0);
+  tr = block_sum(tr, red);
+  const double thr2 = rel * rel * tr;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int j = 0;
+  for (; j < jmax; ++j) {
+    // remaining trace and the largest remaining diagonal
+    double sum = 0.0, mx = -1.0;
+    int arg = j;
+    for (int i = j + threadIdx.x; i < k; i += blockDim.x) {
+      int a = perm[i];
+      double d = S[(size_t)a * k + a];
+      sum += fmax(d, 0.0);
+      if (d > mx) { mx = d; arg = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      double om = __shfl_xor_sync(0xffffffffu, mx, o);
+      int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+      if (om > mx || (om == mx && oa < arg)) { mx = om; arg = oa; }
+    }
+    if (lane == 0) { red[wid] = sum; red[32 + wid] = mx; ired[wid] = arg; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ts = 0.0, tm = -1.0;
+      int ta = j;
+      for (int w = 0; w < nw; ++w) {
+        ts += red[w];
+        if (red[32 + w] > tm || (red[32 + w] == tm && ired[w] < ta)) { tm = red[32 + w]; ta = ired[w]; }
+      }
+      red[0] = ts; red[32] = tm; ired[0] = ta;
+      // the first step is always taken (a rank of at least one)
+      bool stop = j > 0 && (ts <= thr2 || !(tm > 0.0));
+      if (j == 0 && !(tm > 0.0)) ta = 0;
+      if (!stop) {
+        int t = perm[j]; perm[j] = perm[ta]; perm[ta] = t;
+        piv[j] = perm[j];
+        dsel[j] = tm;
+      }
+      ired[1] = stop ? 1 : 0;
+    }
+    __syncthreads();
+    if (ired[1]) break;
+    const int pj = perm[j];
+    const double dp = S[(size_t)pj * k + pj];
+    const double inv = dp > 0.0 ? 1.0 / sqrt(dp) : 0.0;
+    // column of the factor over the remaining indices (position i -> lv[i])
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+      int a = perm[i];
+      int hi = max(a, pj), lo = min(a, pj);
+      lv[i] = S[(size_t)lo * k + hi] * inv;
+    }
+    __syncthreads();
+    // Schur update of the lower triangle over the remaining indices
+    const int w = k - j - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      int i = j + 1 + t / w, i2 = j + 1 + t % w;
+      if (i2 > i) continue;
+      int a = perm[i], b = perm[i2];
+      int hi = max(a, b), lo = min(a, b);
+      S[(size_t)lo * k + hi] -= lv[i] * lv[i2];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *rk_out = j;
+}
+
+void pivoted_cholesky(iga_ctx* ctx, double* G, int k, double rel, int jmax, int* piv,
+                      double* dsel, int* rk) {
+  IGA_REQUIRE(k >= 1, "pivoted_cholesky: empty problem");
+  jmax = std::max(1, std::min(jmax, k));
+  const size_t limit = 220 * 1024;
+  size_t head = (size_t)(64 + k) * sizeof(double) + (size_t)(k + (k & 1) + 32) * sizeof(int);
+  size_t one = (size_t)k * k * sizeof(double);
+  int mode = head + one <= limit ? 1 : 0;
+  size_t smem = head + (mode == 1 ? one : 0);
+  IGA_REQUIRE(head <= limit, "pivoted_cholesky: k too large");
+  static bool attr = false;
+  if (!attr) {
+    IGA_CUDA(cudaFuncSetAttribute(pivoted_cholesky_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+    attr = true;
+  }
+  // algorithmic: k^3 / 3 flop for a full factorisation, the matrix read once
+  prof_count(ctx, 8.0 * (double)k * k, (double)k * k * k / 3.0);
+  IGA_LAUNCH(ctx, pivoted_cholesky_kernel, 1, 512, smem, G, k, rel, jmax, mode, piv, dsel, rk);
 }
 
 void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k) {
@@ -491,6 +852,119 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
   return r;
 }
 
+// ---- rank-1 cross test
+//
+// The cross approximation of Sec. 3 (TT-cross, named after eq.
+// weightEquationSolve as an alternative to TT-SVD) at rank one: through the
+// largest entry W(i0, j0, k0) = v take the three fibres a = W(:, j0, k0),
+// b = W(i0, :, k0), c = W(i0, j0, :); the candidate is a (x) b (x) c / v^2.
+// Its error is evaluated exactly over the whole tensor; when it is within the
+// per-unfolding TT-SVD threshold tol * ref / sqrt(2) every unfolding has a
+// rank-1 approximation that good, so TT-SVD would also stop at rank one, and
+// the rank-1 TT is returned without any sketch.
+
+__global__ void absmax_kernel(const double* __restrict__ x, size_t n,
+                              unsigned long long* __restrict__ best) {
+  // the bits of a non-negative double order like the values, so an integer
+  // atomicMax on them finds max |x|; the index is found in a second pass
+  double m = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(best, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void argmax_kernel(const double* __restrict__ x, size_t n,
+                              const unsigned long long* __restrict__ best,
+                              unsigned long long* __restrict__ idx) {
+  double m = __longlong_as_double((long long)*best);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (fabs(x[i]) == m) atomicMin(idx, (unsigned long long)i);
+}
+
+__global__ void fibres_kernel(const double* __restrict__ W, int n1, int n2, int n3,
+                              const unsigned long long* __restrict__ idx, double* __restrict__ f) {
+  // f = [a (n1) | b (n2) | c (n3) | v]
+  size_t id = *idx;
+  int k0 = (int)(id % n3);
+  int j0 = (int)((id / n3) % n2);
+  int i0 = (int)(id / ((size_t)n2 * n3));
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n1) f[t] = W[((size_t)t * n2 + j0) * n3 + k0];
+  else if (t < n1 + n2) f[t] = W[((size_t)i0 * n2 + (t - n1)) * n3 + k0];
+  else if (t < n1 + n2 + n3) f[t] = W[((size_t)i0 * n2 + j0) * n3 + (t - n1 - n2)];
+  else if (t == n1 + n2 + n3) f[t] = W[id];
+}
+
+__global__ void rank1_residual_kernel(const double* __restrict__ W, int n1, int n2, int n3,
+                                      const double* __restrict__ f, double* __restrict__ out) {
+  __shared__ double red[32];
+  const double* a = f;
+  const double* b = f + n1;
+  const double* c = f + n1 + n2;
+  double iv2 = 1.0 / (f[n1 + n2 + n3] * f[n1 + n2 + n3]);
+  size_t N = (size_t)n1 * n2 * n3;
+  double acc = 0.0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int k = (int)(t % n3);
+    size_t r = t / n3;
+    int j = (int)(r % n2), i = (int)(r / n2);
+    double e = W[t] - a[i] * b[j] * c[k] * iv2;
+    acc += e * e;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+__global__ void rank1_cores_kernel(const double* __restrict__ f, int n1, int n2, int n3,
+                                   double* __restrict__ c1, double* __restrict__ c2,
+                                   double* __restrict__ c3) {
+  double v = f[n1 + n2 + n3];
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n1) c1[t] = f[t];
+  else if (t < n1 + n2) c2[t - n1] = f[t] / v;
+  else if (t < n1 + n2 + n3) c3[t - n1 - n2] = f[t] / v;
+}
+
+// returns a rank-1 TT when the cross candidate meets err <= limit, else nullptr
+static iga_tt* rank1_cross(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double limit) {
+  size_t N = (size_t)n1 * n2 * n3;
+  unsigned long long* keys = scratch<unsigned long long>(ctx, SLOT_TTSVD_C, 2);
+  double* f = scratch<double>(ctx, SLOT_TTSVD_W, (size_t)n1 + n2 + n3 + 2);
+  double* err = f + n1 + n2 + n3 + 1;
+  unsigned long long init[2] = {0ull, ~0ull};
+  IGA_CUDA(cudaMemcpyAsync(keys, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+  IGA_CUDA(cudaMemsetAsync(err, 0, sizeof(double), ctx->stream));
+  int blocks = (int)std::min<size_t>((N + 255) / 256, 152 * 8);
+  IGA_LAUNCH(ctx, absmax_kernel, blocks, 256, 0, W, N, keys);
+  IGA_LAUNCH(ctx, argmax_kernel, blocks, 256, 0, W, N, keys, keys + 1);
+  int nf = n1 + n2 + n3 + 1;
+  IGA_LAUNCH(ctx, fibres_kernel, (nf + 255) / 256, 256, 0, W, n1, n2, n3, keys + 1, f);
+  prof_count(ctx, (double)N * 8.0, 4.0 * (double)N);
+  IGA_LAUNCH(ctx, rank1_residual_kernel, blocks, 256, 0, W, n1, n2, n3, f, err);
+  double h[2] = {0.0, 0.0};
+  IGA_CUDA(cudaMemcpyAsync(h, f + n1 + n2 + n3, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (h[0] == 0.0 || !(std::sqrt(std::max(h[1], 0.0)) <= limit)) return nullptr;
+  auto* tt = new iga_tt();
+  try {
+    tt->n[0] = n1; tt->n[1] = n2; tt->n[2] = n3;
+    tt->r[0] = 1; tt->r[1] = 1;
+    for (int d = 0; d < 3; ++d) tt->core[d].alloc(tt->n[d]);
+    IGA_LAUNCH(ctx, rank1_cores_kernel, (nf + 255) / 256, 256, 0, f, n1, n2, n3, tt->core[0].p,
+               tt->core[1].p, tt->core[2].p);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  } catch (...) {
+    delete tt;
+    throw;
+  }
+  return tt;
+}
+
 void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, double norm_ref,
              int rmax, iga_tt** out) {
   IGA_REQUIRE(W != nullptr && out != nullptr, "tt_svd: null pointer");
@@ -503,6 +977,11 @@ void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, 
   double ref = norm_ref > 0.0 ? norm_ref : nrm;
   if (nrm == 0.0 || nrm <= tol * ref) return;            // rank 0
   double delta = tol * ref / std::sqrt(2.0);
+  // rank-1 cross candidate within the per-unfolding threshold first
+  if (iga_tt* r1 = rank1_cross(ctx, W, n1, n2, n3, delta)) {
+    *out = r1;
+    return;
+  }
   IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
   // first unfolding (n1 x n2 n3): memory is X col-major (n2 n3 x n1)
   DevBuf<double> U1, C1, U2, C2;

@@ -18,6 +18,7 @@ _LIB_PATH = os.path.join(_HERE, "libiga.so")
 _lib = None
 
 IGA_FP64, IGA_FP32, IGA_TF32 = 0, 1, 2
+IGA_TRUNC_PIVOTED, IGA_TRUNC_SVD = 0, 1
 STATUS = {0: "IGA_OK", 1: "IGA_EINVAL", 2: "IGA_ENOMEM", 3: "IGA_ECUDA", 4: "IGA_ENOCONV",
           5: "IGA_ENONFINITE", 6: "IGA_ETIMEOUT"}
 
@@ -47,12 +48,14 @@ class SolveOpts_(C.Structure):
     _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("max_sweeps", C.c_int),
                 ("kick_rank", C.c_int), ("rmax", C.c_int), ("local_maxit", C.c_int),
                 ("refine_max", C.c_int), ("precision", C.c_int), ("verbose", C.c_int),
-                ("trunc_tol", C.c_double)]
+                ("trunc_tol", C.c_double), ("truncation", C.c_int)]
 
 
 class SolveInfo_(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("refinements", C.c_int), ("max_rank", C.c_int),
-                ("local_iters", C.c_int), ("residual", C.c_double), ("seconds", C.c_double)]
+                ("local_iters", C.c_int), ("residual", C.c_double), ("seconds", C.c_double),
+                ("t_local", C.c_double), ("t_residual", C.c_double), ("t_move", C.c_double),
+                ("t_refine", C.c_double)]
 
 
 def library_path() -> str:

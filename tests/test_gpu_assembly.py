@@ -173,3 +173,22 @@ def test_config2_sampled_rows(env):
                         idx[d] = o
                         want[tuple(idx)] = 0.0
             assert np.linalg.norm(got - want) < 1e-11 * np.linalg.norm(want), (s, r)
+
+
+@pytest.mark.parametrize("scale,rank_one", [(0.2, True), (5.0, False)])
+def test_tt_svd_rank_one_cross(env, scale, rank_one):
+    """Rank-1 tensor plus noise of norm scale * tol * |W|: the cross test accepts only
+    below the per-unfolding threshold, otherwise the sketch runs; the bound holds in both."""
+    ctx, torch, iga = env
+    tol = 1e-4
+    W0 = tt_full(_random_tt((40, 33, 57), (1, 1), 11))
+    noise = np.random.default_rng(12).standard_normal(W0.shape)
+    W = W0 + scale * tol * np.linalg.norm(W0) * noise / np.linalg.norm(noise)
+    tt = iga.iga_tt_svd(ctx, torch.tensor(W, device="cuda"), tol)
+    err = np.linalg.norm(tt_full(tt.cores(ctx)) - W) / np.linalg.norm(W)
+    assert err <= tol * 1.0001
+    if rank_one:
+        assert tt.info()[1] == (1, 1)
+    else:
+        assert all(a >= b for a, b in zip(tt.info()[1], tt_ranks(tt_svd(W, tol))))
+        assert max(tt.info()[1]) > 1

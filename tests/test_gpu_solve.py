@@ -52,8 +52,9 @@ CASES = [
 
 @pytest.mark.parametrize("name,work", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-def test_solve_matches_direct(env, name, work, prec):
-    info, y, u, lam = _solve(env, work, tol=1e-10, precision=prec)
+@pytest.mark.parametrize("trunc", [0, 1], ids=["pivoted", "svd"])
+def test_solve_matches_direct(env, name, work, prec, trunc):
+    info, y, u, lam = _solve(env, work, tol=1e-10, precision=prec, truncation=trunc)
     assert info["converged"], info
     M, K, b = _oracle_system(work)
     # residual of the GPU solution measured with the oracle's 3-D assembled matrices
