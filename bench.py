@@ -32,6 +32,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_FMA_TFLOPS = 1.196      # measured FP64 FMA rate of this GB300 (CUDA cores)
 FP32_FMA_TFLOPS = 74.75      # measured FP32 FMA rate
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel, as
+# summarised under profiles/; an entry is dropped whenever its kernel changes
+NCU_TRAFFIC = {"sample_weights_kernel": 1.0593e9}
 # kernels that can dominate a step, with the arithmetic they run in
 CANDIDATES = {
     "jacobi_eig_kernel": "fp64", "sample_weights_kernel": "fp64",
@@ -360,7 +363,7 @@ def run_gpu(args, world, rank, local):
             achieved = by / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind}
-        roof.update({"traffic": None, "kernel": args.roofline_kernel,
+        roof.update({"traffic": NCU_TRAFFIC.get(args.roofline_kernel), "kernel": args.roofline_kernel,
                      "launches": prof["launches"], "avg_us": avg_ms * 1e3,
                      "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": fl,
                      "device_ms_per_step_by_kernel": {k: round(v, 3) for k, v in shares.items()}})

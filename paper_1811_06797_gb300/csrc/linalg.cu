@@ -900,20 +900,23 @@ __global__ void fibres_kernel(const double* __restrict__ W, int n1, int n2, int 
 
 __global__ void rank1_residual_kernel(const double* __restrict__ W, int n1, int n2, int n3,
                                       const double* __restrict__ f, double* __restrict__ out) {
+  // one (i, j) fibre per block iteration, threads along k: e = W - (a_i b_j / v^2) c_k
   __shared__ double red[32];
   const double* a = f;
   const double* b = f + n1;
   const double* c = f + n1 + n2;
-  double iv2 = 1.0 / (f[n1 + n2 + n3] * f[n1 + n2 + n3]);
-  size_t N = (size_t)n1 * n2 * n3;
+  const double v = f[n1 + n2 + n3];
+  const double iv2 = 1.0 / (v * v);
+  const long long rows = (long long)n1 * n2;
   double acc = 0.0;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
-       t += (size_t)gridDim.x * blockDim.x) {
-    int k = (int)(t % n3);
-    size_t r = t / n3;
-    int j = (int)(r % n2), i = (int)(r / n2);
-    double e = W[t] - a[i] * b[j] * c[k] * iv2;
-    acc += e * e;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int i = (int)(row / n2), j = (int)(row - (long long)i * n2);
+    const double ab = a[i] * b[j] * iv2;
+    const double* w = W + (size_t)row * n3;
+    for (int k = threadIdx.x; k < n3; k += blockDim.x) {
+      double e = fma(-ab, c[k], w[k]);
+      acc = fma(e, e, acc);
+    }
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) atomicAdd(out, acc);
@@ -944,7 +947,8 @@ static iga_tt* rank1_cross(iga_ctx* ctx, const double* W, int n1, int n2, int n3
   int nf = n1 + n2 + n3 + 1;
   IGA_LAUNCH(ctx, fibres_kernel, (nf + 255) / 256, 256, 0, W, n1, n2, n3, keys + 1, f);
   prof_count(ctx, (double)N * 8.0, 4.0 * (double)N);
-  IGA_LAUNCH(ctx, rank1_residual_kernel, blocks, 256, 0, W, n1, n2, n3, f, err);
+  int rblocks = (int)std::min<long long>((long long)n1 * n2, 152 * 8);
+  IGA_LAUNCH(ctx, rank1_residual_kernel, rblocks, 256, 0, W, n1, n2, n3, f, err);
   double h[2] = {0.0, 0.0};
   IGA_CUDA(cudaMemcpyAsync(h, f + n1 + n2 + n3, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                            ctx->stream));
