@@ -291,12 +291,12 @@ iga_status iga_weight_gradient(iga_ctx* ctx, const iga_space* space, const iga_o
 /* Truncation of the block core when the block index moves to the next core
  * (Sec. 5, eqs. svd1 and svd2).  IGA_TRUNC_SVD is the paper's truncated SVD,
  * computed from the Gram matrix of the reshaped block core by a Jacobi
- * eigen-decomposition.  IGA_TRUNC_PIVOTED keeps the columns chosen by a
- * pivoted Cholesky factorisation of the same Gram matrix (QR with column
- * pivoting): the projection error of each field obeys the same bound
- * trunc_tol, the kept rank can be a little larger than the SVD's, and the
- * work is about k^3 / 3 instead of a Jacobi method's tens of k^3 for k =
- * three times the TT rank.  The default is IGA_TRUNC_PIVOTED. */
+ * eigen-decomposition.  IGA_TRUNC_PIVOTED (default) runs Householder QR with
+ * column pivoting on the reshaped block core itself and stops at the first
+ * rank whose remaining column norms meet trunc_tol, so the Frobenius error of
+ * each field obeys the same bound as the SVD's; the rank can be a little
+ * larger, and the work is one pass of pivoted QR instead of an
+ * eigen-decomposition of the Gram matrix. */
 typedef enum { IGA_TRUNC_PIVOTED = 0, IGA_TRUNC_SVD = 1 } iga_trunc;
 
 typedef struct {

@@ -174,28 +174,6 @@ __global__ void scale_rows_kernel(double* __restrict__ A, int rows, int cols,
   A[idx] = s > 0.0 ? A[idx] / sqrt(s) : 0.0;
 }
 
-// Y (m x rk col-major), column c = B(:, piv[c]) / ||B(:, piv[c])||, with
-// B(i, a) = B[i * si + a * sa]; one block (a multiple of 32 threads) per column
-__global__ void gather_unit_cols_kernel(const double* __restrict__ B, int m, int si, int sa,
-                                        const int* __restrict__ piv, double* __restrict__ Y) {
-  __shared__ double red[32];
-  const int c = blockIdx.x;
-  const size_t a = (size_t)piv[c] * sa;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double v = B[(size_t)i * si + a];
-    s += v * v;
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  s = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x)
-    Y[(size_t)c * m + i] = B[(size_t)i * si + a] * inv;
-}
-
 __global__ void inv_sqrt_abs_kernel(const double* __restrict__ w, int k, double floor_rel,
                                     double* __restrict__ out) {
   // out_i = 1/sqrt(|w_i|) with |w_i| floored at floor_rel * max|w|
@@ -285,11 +263,33 @@ __global__ void sub_kernel(const double* __restrict__ a, const double* __restric
   if (i < n) c[i] = a[i] - b[i];
 }
 
+// *out += sum x_i^2 accumulated in FP64 (one atomic per block; *out zeroed by
+// the caller)
 template <typename T>
-__global__ void scale_by_dev_kernel(T* __restrict__ x, const T* __restrict__ s, size_t n) {
+__global__ void sumsq_acc_kernel(const T* __restrict__ x, size_t n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double v = (double)x[i];
+    acc = fma(v, v, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
+// x /= sqrt(*s2) (x = 0 when *s2 = 0)
+template <typename T>
+__global__ void scale_rsqrt_kernel(T* __restrict__ x, const double* __restrict__ s2, size_t n) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  T v = *s;
-  if (i < n) x[i] = v > T(0) ? x[i] / v : T(0);
+  double s = *s2;
+  if (i < n) x[i] = s > 0.0 ? (T)((double)x[i] / sqrt(s)) : T(0);
 }
 
 // --------------------------------------------- banded LU of the local KKT blocks
@@ -359,39 +359,44 @@ __global__ void kkt_block_factor_kernel(
   __syncwarp();
   const int N = L.N, kl = L.kl, ku = L.ku;
   int* pv = piv + (size_t)blk * N;
+  // right-looking banded LU, one column per step: lanes take the rows of the
+  // pivot search and the columns of the rank-1 update
   for (int k = 0; k < N; ++k) {
     const int last = min(N - 1, k + kl);
     const int cnt = last - k + 1;
+    const int jend = min(N - 1, k + kl + ku);
     T v = T(-1);
     int idx = k;
-    if (lane < cnt) { v = fabs(bwin(A, L, k + lane, k)); idx = k + lane; }
+    for (int t = lane; t < cnt; t += 32) {
+      T a = fabs(bwin(A, L, k + t, k));
+      if (a > v) { v = a; idx = k + t; }
+    }
     for (int off = 16; off > 0; off >>= 1) {
       T ov = __shfl_xor_sync(0xffffffffu, v, off);
       int oi = __shfl_xor_sync(0xffffffffu, idx, off);
       if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
     }
     const int pr = idx;
-    const int jend = min(N - 1, k + kl + ku);
     if (lane == 0) pv[k] = pr;
-    if (pr != k) {
+    if (pr != k)
       for (int j = k + lane; j <= jend; j += 32) {
         T t = bwin(A, L, k, j);
         bwin(A, L, k, j) = bwin(A, L, pr, j);
         bwin(A, L, pr, j) = t;
       }
-    }
     __syncwarp();
     const T d = bwin(A, L, k, k);
     if (d == T(0)) {
       if (lane == 0) atomicOr(flag, 2);
       continue;
     }
-    for (int t = 1 + lane; t < cnt; t += 32) bwin(A, L, k + t, k) /= d;
+    const T rd = T(1) / d;
+    for (int t = 1 + lane; t < cnt; t += 32) bwin(A, L, k + t, k) *= rd;
     __syncwarp();
-    const int rows = cnt - 1, width = jend - k;
-    for (int e = lane; e < rows * width; e += 32) {
-      int i = k + 1 + e / width, j = k + 1 + e % width;
-      bwin(A, L, i, j) -= bwin(A, L, i, k) * bwin(A, L, k, j);
+    for (int j = k + 1 + lane; j <= jend; j += 32) {
+      const T u = bwin(A, L, k, j);
+#pragma unroll 4
+      for (int t = 1; t < cnt; ++t) bwin(A, L, k + t, j) -= bwin(A, L, k + t, k) * u;
     }
     __syncwarp();
   }
@@ -416,8 +421,9 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
   if (blk >= L.NB) return;
   const int N = L.N, n = L.n, kl = L.kl, ku = L.ku;
   const size_t per = (size_t)N * L.W;
-  // per warp: [LU factor (optional)] [pivots] [vector]
-  T* base = reinterpret_cast<T*>(smraw) + (size_t)warp * ((lu_in_smem ? per : 0) + N);
+  // per warp: [LU factor (optional)] [vector] [pivots]
+  const size_t pivT = ((size_t)N * sizeof(int) + sizeof(T) - 1) / sizeof(T);
+  T* base = reinterpret_cast<T*>(smraw) + (size_t)warp * ((lu_in_smem ? per : 0) + N + pivT);
   T* s = base + (lu_in_smem ? per : 0);
   const T* A = Aall + (size_t)blk * per;
   if (lu_in_smem) {
@@ -432,26 +438,28 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
     int i = I / 3, l = I - 3 * i;
     s[I] = (T)v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b];
   }
+  int* ps = reinterpret_cast<int*>(s + N);        // pivots of this block
+  for (int k = lane; k < N; k += 32) ps[k] = pv[k];
   __syncwarp();
+  // forward: L y = P b, one row per step, lanes over the kl rows below
   for (int k = 0; k < N; ++k) {
-    const int pr = pv[k];
-    T sk = s[pr];
+    const int pr = ps[k];
+    if (pr != k && lane == 0) { T t = s[pr]; s[pr] = s[k]; s[k] = t; }
     __syncwarp();
-    if (pr != k && lane == 0) { s[pr] = s[k]; s[k] = sk; }
-    __syncwarp();
-    const int last = min(N - 1, k + kl);
-    for (int t = 1 + lane; t <= last - k; t += 32) s[k + t] -= A[(size_t)(k + t) * L.W + (kl - t)] * sk;
+    const T sk = s[k];
+    const int cnt = min(N - 1, k + kl) - k;
+    for (int t = 1 + lane; t <= cnt; t += 32) s[k + t] -= A[(size_t)(k + t) * L.W + (kl - t)] * sk;
     __syncwarp();
   }
+  // backward, column by column: x_k = s_k / U(k, k), then the rows above
+  // within the band (kl + ku of them) drop U(k - t, k) x_k
   for (int k = N - 1; k >= 0; --k) {
-    const int jend = min(N - 1, k + kl + ku);
-    T part = T(0);
-    for (int j = k + 1 + lane; j <= jend; j += 32) part += A[(size_t)k * L.W + (j - k + kl)] * s[j];
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    if (lane == 0) {
-      T d = A[(size_t)k * L.W + kl];
-      s[k] = d != T(0) ? (s[k] - part) / d : T(0);
-    }
+    const T d = A[(size_t)k * L.W + kl];
+    const T x = d != T(0) ? s[k] / d : T(0);
+    __syncwarp();
+    const int cnt = min(k, kl + ku);
+    for (int t = 1 + lane; t <= cnt; t += 32) s[k - t] -= A[(size_t)(k - t) * L.W + (t + kl)] * x;
+    if (lane == 0) s[k] = x;
     __syncwarp();
   }
   for (int I = lane; I < N; I += 32) {
@@ -736,20 +744,26 @@ struct Solver {
     return std::max(1, std::min(rk, rmax));
   }
 
-  int* piv_dev(int k) { return scratch<int>(ctx, SLOT_AMEN_BASE + 18, (size_t)k + 1); }
-
-  // rank-revealing column choice on the normalised Gram matrix G (k x k):
-  // the truncation keeps the chosen columns of the block core, with the
-  // projection error of each field bounded by trunc_tol as for the SVD
-  int pivot_columns(double* G, int k, int m) {
-    int* piv = piv_dev(k);
-    int* rkd = piv + k;
-    double* dsel = slot(9, k);
-    pivoted_cholesky(ctx, G, k, trunc_tol, std::min(rmax, m), piv, dsel, rkd);
+  // basis of the moved core by truncated QR with column pivoting of the block
+  // core B (B(i, a) = B[i si + a sa], field groups of r columns), followed by
+  // the kick residual-sketch columns; returns Q (m x nr, col-major)
+  double* pivoted_basis(const double* B, int m, int c3, int si, int sa, int rg, const double* res,
+                        int d, bool forward, int& nr) {
+    const int ke = std::min(kick, m);
+    double* E = slot(33, (size_t)m * ke);
+    int keep = kick;
+    kick = ke;
+    sketch(res, d, forward, E, m);
+    kick = keep;
+    const int jm = std::min(rmax, m);
+    double* Q = slot(11, (size_t)m * std::min(jm + ke, m));
+    int* rkd = scratch<int>(ctx, SLOT_AMEN_BASE + 18, 1);
+    qrcp_truncate(ctx, B, m, c3, si, sa, rg, E, ke, trunc_tol, jm, Q, rkd);
     int rk = 1;
     IGA_CUDA(cudaMemcpyAsync(&rk, rkd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-    return std::max(1, std::min(rk, std::min(rmax, m)));
+    nr = std::min(rk + ke, m);
+    return Q;
   }
 
   // move the block index from core d to d+1 (forward) with enrichment
@@ -758,43 +772,41 @@ struct Solver {
     int m = r0 * nn, c3 = 3 * r1;
     double* Mx = slot(6, (size_t)m * c3);
     IGA_LAUNCH(ctx, permute_fwd_kernel, nblk((size_t)m * c3), 256, 0, Xh.p, r0, nn, r1, Mx);
-    double* G = slot(7, (size_t)c3 * c3);
-    double* V = slot(8, (size_t)c3 * c3);
-    double* w = slot(9, c3);
-    rm_gemm(ctx, true, false, c3, c3, m, Mx, c3, Mx, c3, G, c3);
-    // the rank decision treats y, u and lambda alike: each component of the
-    // block core is normalised before the eigen-decomposition (the kept
-    // coefficients below are exact projections of the unscaled core)
-    double* sc = slot(17, 3);
-    IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r1, sc);
-    int rk;
-    double* Y;
+    int nr;
+    double* Q;
     if (svd_moves) {
+      double* G = slot(7, (size_t)c3 * c3);
+      double* V = slot(8, (size_t)c3 * c3);
+      double* w = slot(9, c3);
+      rm_gemm(ctx, true, false, c3, c3, m, Mx, c3, Mx, c3, G, c3);
+      // the rank decision treats y, u and lambda alike: each component of the
+      // block core is normalised before the eigen-decomposition (the kept
+      // coefficients below are exact projections of the unscaled core)
+      double* sc = slot(17, 3);
+      IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r1, sc);
       jacobi_eig(ctx, G, V, w, c3);      // V col-major: columns = right singular vectors
       IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r1, sc);
       std::vector<double> lam(c3);
       IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
       IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-      rk = std::min(trunc_rank(lam, trunc_tol), m);
-      Y = slot(10, (size_t)m * (rk + kick));         // col-major (m x nr): [U_k, E]
+      int rk = std::min(trunc_rank(lam, trunc_tol), m);
+      int kk = std::max(0, std::min(kick, m - rk));
+      nr = rk + kk;
+      double* Y = slot(10, (size_t)m * nr);          // col-major (m x nr): [U_k, E]
       // U_k^T = Sigma^-1 V_k^T Mx^T  (row-major rk x m == col-major m x rk)
       rm_gemm(ctx, false, true, rk, m, c3, V, c3, Mx, c3, Y, m);
       IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
+      if (kk > 0) {
+        int keep = kick;
+        kick = kk;
+        sketch(res, d, true, Y + (size_t)rk * m, m);
+        kick = keep;
+      }
+      Q = slot(11, (size_t)m * nr);
+      householder_qr(ctx, Y, Q, m, nr);
     } else {
-      rk = pivot_columns(G, c3, m);
-      Y = slot(10, (size_t)m * (rk + kick));         // col-major (m x nr): [Mx(:, piv), E]
-      IGA_LAUNCH(ctx, gather_unit_cols_kernel, rk, 256, 0, Mx, m, c3, 1, piv_dev(c3), Y);
+      Q = pivoted_basis(Mx, m, c3, c3, 1, r1, res, d, true, nr);
     }
-    int kk = std::max(0, std::min(kick, m - rk));
-    int nr = rk + kk;
-    if (kk > 0) {
-      int keep = kick;
-      kick = kk;
-      sketch(res, d, true, Y + (size_t)rk * m, m);
-      kick = keep;
-    }
-    double* Q = slot(11, (size_t)m * nr);
-    householder_qr(ctx, Y, Q, m, nr);
     X[d].ensure((size_t)m * nr);
     transpose_cm(ctx, Q, m, nr, X[d].p);
     double* coef = slot(12, (size_t)nr * c3);
@@ -814,41 +826,39 @@ struct Solver {
     int r0 = r[d], nn = n[d], r1 = r[d + 1];
     int m = nn * r1, c3 = 3 * r0;
     const double* Mx = Xh.p;                         // row-major (3 r0 x n r1)
-    double* G = slot(7, (size_t)c3 * c3);
-    double* V = slot(8, (size_t)c3 * c3);
-    double* w = slot(9, c3);
-    rm_gemm(ctx, false, true, c3, c3, m, Mx, m, Mx, m, G, c3);
-    double* sc = slot(17, 3);
-    IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r0, sc);
-    int rk;
-    double* Y;
+    int nr;
+    double* Q;
     if (svd_moves) {
+      double* G = slot(7, (size_t)c3 * c3);
+      double* V = slot(8, (size_t)c3 * c3);
+      double* w = slot(9, c3);
+      rm_gemm(ctx, false, true, c3, c3, m, Mx, m, Mx, m, G, c3);
+      double* sc = slot(17, 3);
+      IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r0, sc);
       jacobi_eig(ctx, G, V, w, c3);                 // columns: left singular vectors
       IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r0, sc);
       std::vector<double> lam(c3);
       IGA_CUDA(cudaMemcpyAsync(lam.data(), w, c3 * 8, cudaMemcpyDeviceToHost, ctx->stream));
       IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-      rk = std::min(trunc_rank(lam, trunc_tol), m);
-      Y = slot(10, (size_t)m * (rk + kick));
+      int rk = std::min(trunc_rank(lam, trunc_tol), m);
+      int kk = std::max(0, std::min(kick, m - rk));
+      nr = rk + kk;
+      double* Y = slot(10, (size_t)m * nr);
       // W_k^T = Sigma^-1 U_k^T Mx (row-major rk x m == col-major m x rk)
       rm_gemm(ctx, false, false, rk, m, c3, V, c3, Mx, m, Y, m);
       IGA_LAUNCH(ctx, scale_rows_kernel, nblk((size_t)rk * m), 256, 0, Y, rk, m, w);
+      if (kk > 0) {
+        int keep = kick;
+        kick = kk;
+        sketch(res, d, false, Y + (size_t)rk * m, m);
+        kick = keep;
+      }
+      Q = slot(11, (size_t)m * nr);
+      householder_qr(ctx, Y, Q, m, nr);
     } else {
-      rk = pivot_columns(G, c3, m);
       // candidate a is row a of Mx (row-major 3 r0 x m)
-      Y = slot(10, (size_t)m * (rk + kick));
-      IGA_LAUNCH(ctx, gather_unit_cols_kernel, rk, 256, 0, Mx, m, 1, m, piv_dev(c3), Y);
+      Q = pivoted_basis(Mx, m, c3, 1, m, r0, res, d, false, nr);
     }
-    int kk = std::max(0, std::min(kick, m - rk));
-    int nr = rk + kk;
-    if (kk > 0) {
-      int keep = kick;
-      kick = kk;
-      sketch(res, d, false, Y + (size_t)rk * m, m);
-      kick = keep;
-    }
-    double* Q = slot(11, (size_t)m * nr);
-    householder_qr(ctx, Y, Q, m, nr);
     double* coef = slot(12, (size_t)c3 * nr);       // row-major (3 r0 x nr) = Mx Q
     rm_gemm(ctx, false, true, c3, nr, m, Mx, m, Q, m, coef, nr);
     X[d].ensure((size_t)m * nr);
@@ -1026,10 +1036,12 @@ struct Solver {
     {
       // keep each block's LU factor in shared memory when four of them fit
       size_t per = (size_t)BL.N * BL.W;
-      size_t perw = (per + BL.N) * sizeof(P);
+      // per warp: LU factor (when it fits), the vector and the pivots
+      const size_t pivT = ((size_t)BL.N * sizeof(int) + sizeof(P) - 1) / sizeof(P);
+      size_t perw = (per + BL.N + pivT) * sizeof(P);
       int lu_smem = perw <= 200 * 1024;
       const int wpb = lu_smem ? (int)std::min<size_t>(4, (200 * 1024) / perw) : 4;
-      size_t smem = (size_t)wpb * ((lu_smem ? per : 0) + BL.N) * sizeof(P);
+      size_t smem = (size_t)wpb * ((lu_smem ? per : 0) + BL.N + pivT) * sizeof(P);
       static bool attr = false;
       if (!attr) {
         IGA_CUDA(cudaFuncSetAttribute(kkt_block_solve_kernel<P, T>,
@@ -1069,9 +1081,12 @@ struct Solver {
       else
         IGA_BLAS(cublasSgemv(ctx->blas, t, rows, cols, al, A, rows, xx, 1, be, yy, 1));
     };
-    auto nrm2 = [&](const T* xx, T* out) {
-      if constexpr (sizeof(T) == 8) IGA_BLAS(cublasDnrm2(ctx->blas, (int)Lv, xx, 1, out));
-      else IGA_BLAS(cublasSnrm2(ctx->blas, (int)Lv, xx, 1, out));
+    // squared norms in FP64, one kernel each
+    double* nd = scratch<double>(ctx, SLOT_AMEN_BASE + 19, 2);
+    const unsigned nsb = std::min<unsigned>(nblk(Lv), 152 * 4);
+    auto sumsq = [&](const T* xx, double* out) {
+      IGA_CUDA(cudaMemsetAsync(out, 0, sizeof(double), ctx->stream));
+      IGA_LAUNCH(ctx, sumsq_acc_kernel<T>, nsb, 256, 0, xx, Lv, out);
     };
     int it = 0;
     std::vector<T> hh(3 * (m + 2));
@@ -1087,13 +1102,14 @@ struct Solver {
         else
           IGA_BLAS(cublasSgeam(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)Lv, 1, one, b, (int)Lv,
                                mone, w, (int)Lv, Vb, (int)Lv));
-        nrm2(Vb, hd);
-        IGA_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+        sumsq(Vb, nd);
+        double b2 = 0.0;
+        IGA_CUDA(cudaMemcpyAsync(&b2, nd, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-        double beta0 = (double)hh[0];
+        double beta0 = std::sqrt(b2);
         if (!std::isfinite(beta0)) throw Error(IGA_ENONFINITE, "local GMRES: non-finite residual");
         if (beta0 <= tol_abs) break;
-        IGA_LAUNCH(ctx, scale_by_dev_kernel<T>, nblk(Lv), 256, 0, Vb, hd, Lv);
+        IGA_LAUNCH(ctx, scale_rsqrt_kernel<T>, nblk(Lv), 256, 0, Vb, nd, Lv);
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta0;
         int k = 0;
@@ -1109,16 +1125,18 @@ struct Solver {
           gemv(CUBLAS_OP_N, (int)Lv, k + 1, mone, Vb, h1, one, w);
           gemv(CUBLAS_OP_T, (int)Lv, k + 1, one, Vb, w, zero, h2);
           gemv(CUBLAS_OP_N, (int)Lv, k + 1, mone, Vb, h2, one, w);
-          T* nr = hd + 2 * (m + 2);
-          nrm2(w, nr);
-          IGA_CUDA(cudaMemcpyAsync(hh.data(), hd, 3 * (m + 2) * sizeof(T), cudaMemcpyDeviceToHost,
+          sumsq(w, nd + 1);
+          IGA_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * (m + 2) * sizeof(T), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+          double h2n = 0.0;
+          IGA_CUDA(cudaMemcpyAsync(&h2n, nd + 1, sizeof(double), cudaMemcpyDeviceToHost,
                                    ctx->stream));
           T* vn = Vb + (size_t)(k + 1) * Lv;
           IGA_CUDA(cudaMemcpyAsync(vn, w, Lv * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
-          IGA_LAUNCH(ctx, scale_by_dev_kernel<T>, nblk(Lv), 256, 0, vn, nr, Lv);
+          IGA_LAUNCH(ctx, scale_rsqrt_kernel<T>, nblk(Lv), 256, 0, vn, nd + 1, Lv);
           IGA_CUDA(cudaStreamSynchronize(ctx->stream));
           for (int j = 0; j <= k; ++j) H[j * m + k] = (double)hh[j] + (double)hh[(m + 2) + j];
-          double hn = (double)hh[2 * (m + 2)];
+          double hn = std::sqrt(h2n);
           if (!std::isfinite(hn)) throw Error(IGA_ENONFINITE, "local GMRES: non-finite vector");
           for (int j = 0; j < k; ++j) {
             double t = cs[j] * H[j * m + k] + sn[j] * H[(j + 1) * m + k];

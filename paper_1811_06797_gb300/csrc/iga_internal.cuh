@@ -187,7 +187,7 @@ T* scratch(iga_ctx* ctx, int slot, size_t count) {
 // scratch slot numbers (kept apart so nested helpers do not collide)
 enum {
   SLOT_TTSVD_OMEGA = 0, SLOT_TTSVD_Y, SLOT_TTSVD_Q, SLOT_TTSVD_BT, SLOT_TTSVD_G, SLOT_TTSVD_V,
-  SLOT_TTSVD_W, SLOT_TTSVD_C, SLOT_TTSVD_NORM, SLOT_ASM_W, SLOT_ASM_SAMPLES, SLOT_KRON_Z,
+  SLOT_TTSVD_W, SLOT_TTSVD_C, SLOT_TTSVD_NORM, SLOT_QRCP_WORK, SLOT_ASM_W, SLOT_ASM_SAMPLES, SLOT_KRON_Z,
   SLOT_KRON_Z2, SLOT_LOCAL_T1, SLOT_LOCAL_T2, SLOT_KKT_TMP, SLOT_MISC0, SLOT_MISC1,
   SLOT_AMEN_BASE = 32
 };
@@ -218,11 +218,12 @@ void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double
 void gen_eig_prep(iga_ctx* ctx, const double* PM, int SM, const double* PK, int SK, int k,
                   double* work, double* C, double* Linv);
 void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k);  // Y overwritten
-// rank-revealing pivoted Cholesky of a PSD Gram matrix (col-major, lower
-// triangle overwritten): piv[0..rk) chosen indices, dsel their pivots, *rk
-// (device) the rank at which the Schur trace drops to rel^2 trace(G), <= jmax
-void pivoted_cholesky(iga_ctx* ctx, double* G, int k, double rel, int jmax, int* piv,
-                      double* dsel, int* rk);
+// truncated QR with column pivoting of B (m x c3, B(i, a) = B[i si + a sa],
+// field groups of r columns normalised), then kick extra columns E (m x kick
+// col-major) orthogonalised; Q (m x min(rk + kick, m), col-major) and *rk_dev
+// (device) receive the basis and the number of pivoted columns
+void qrcp_truncate(iga_ctx* ctx, const double* B, int m, int c3, int si, int sa, int r,
+                   const double* E, int kick, double rel, int jmax, double* Q, int* rk_dev);
 void fill_gaussian(iga_ctx* ctx, double* x, size_t n, uint64_t seed);
 void transpose_cm(iga_ctx* ctx, const double* A, int rows, int cols, double* B);
 

@@ -312,8 +312,354 @@ __global__ void __launch_bounds__(256) householder_qr_cluster_kernel(
   cl.sync();
 }
 
+// ------------------------------------------- truncated QR with column pivoting
+//
+// The block core B (m x c3, B(i, a) = B[i si + a sa]) is truncated by
+// Householder QR with column pivoting: each step takes the column with the
+// largest norm below the current row, and pivoting stops at the first step
+// whose remaining column norms sum to <= rel^2 * (sum of all), i.e. when the
+// Frobenius error of projecting B on the chosen columns is within rel.  The
+// columns of each field group (a / r, three groups) are first normalised to
+// unit Frobenius norm, so y, u and lambda are truncated alike.  Then `kick`
+// extra columns E (m x kick, col-major) are orthogonalised against the chosen
+// ones by unpivoted Householder steps, and the nr = min(rk + kick, m)
+// orthonormal columns Q are formed in place.  Working on B itself (not on
+// B^T B) resolves column residuals down to the FP64 rounding of B.
+//
+// Rows are split over the CTAs of a cluster as in the QR above; the slice of
+// each CTA lives in shared memory when it fits, else in a global workspace.
+struct QrcpArgs {
+  const double* B;
+  const double* E;
+  double* Q;
+  double* gwork;     // nullptr: slices in shared memory
+  int* rk;           // device: number of pivoted columns
+  double rel;
+  int m, c3, si, sa, r, kick, jmax, mc;
+};
+
+__global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int C = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  extern __shared__ double sm[];
+  const int ncol = a.c3 + a.kick;
+  const int mc = a.mc;
+  double* part = sm;                   // ncol: partial column norms
+  double* rowj = part + ncol;          // ncol: row j, published by its owner
+  double* pw = rowj + ncol;            // 2 ncol: partial dot products
+  double* nrm = pw + 2 * ncol;         // ncol: column norms below row j
+  double* tau = nrm + ncol;            // ncol
+  double* gpart = tau + ncol;          // 4: partial group sums
+  double* red = gpart + 4;             // 64
+  int* ired = (int*)(red + 64);        // 32
+  double* A = a.gwork ? a.gwork + (size_t)me * mc * ncol : (double*)(ired + 32);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int r0 = me * mc;
+  const int nloc = max(0, min(a.m, r0 + mc) - r0);
+
+  // load, with the sums of squares of the three field groups
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  for (int t = tid; t < mc * ncol; t += blockDim.x) {
+    const int i = t % mc, c = t / mc;
+    double v = 0.0;
+    if (i < nloc)
+      v = c < a.c3 ? a.B[(size_t)(r0 + i) * a.si + (size_t)c * a.sa]
+                   : a.E[(size_t)(c - a.c3) * a.m + r0 + i];
+    A[t] = v;
+    if (c < a.c3) {
+      const int g = c / a.r;
+      if (g == 0) g0 += v * v; else if (g == 1) g1 += v * v; else g2 += v * v;
+    }
+  }
+  g0 = qr_block_sum(g0, red);
+  g1 = qr_block_sum(g1, red);
+  g2 = qr_block_sum(g2, red);
+  if (tid == 0) { gpart[0] = g0; gpart[1] = g1; gpart[2] = g2; }
+  cl.sync();
+  double gsum[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < C; ++c) {
+    const double* q = cl.map_shared_rank(gpart, c);
+    gsum[0] += q[0]; gsum[1] += q[1]; gsum[2] += q[2];
+  }
+  double sc[3], tot = 0.0;
+  for (int g = 0; g < 3; ++g) {
+    sc[g] = gsum[g] > 0.0 ? 1.0 / sqrt(gsum[g]) : 0.0;
+    tot += gsum[g] > 0.0 ? 1.0 : 0.0;
+  }
+  for (int t = tid; t < mc * a.c3; t += blockDim.x) A[t] *= sc[(t / mc) / a.r];
+  __syncthreads();
+  const double thr2 = a.rel * a.rel * tot;
+  const int npiv = min(a.jmax, a.c3);
+  int par = 0;                                   // parity of the partial-product buffer
+
+  // one Householder step on column j (alpha = B(j, j), nrm2 = its squared
+  // norm over rows >= j), updating columns (j, jend)
+  auto house = [&](int j, double alpha, double nrm2, int jend) {
+    const int lo = min(nloc, max(0, j - r0));
+    double tj = 0.0, inv = 0.0;
+    const double nr_ = sqrt(fmax(nrm2, 0.0));
+    if (nr_ > 0.0) {
+      const double beta = alpha >= 0.0 ? -nr_ : nr_;
+      const double v0 = alpha - beta;
+      if (v0 != 0.0) {
+        tj = -v0 / beta;
+        inv = 1.0 / v0;
+      }
+    }
+    if (tid == 0) tau[j] = tj;
+    if (tj != 0.0)
+      for (int i = lo + tid; i < nloc; i += blockDim.x)
+        A[(size_t)j * mc + i] = (r0 + i > j) ? A[(size_t)j * mc + i] * inv : 1.0;
+    __syncthreads();
+    double* pb = pw + (par & 1) * ncol;
+    for (int t = j + 1 + wid; t < jend; t += nw) {
+      double d = 0.0;
+      if (tj != 0.0)
+        for (int i = lo + lane; i < nloc; i += 32) d += A[(size_t)j * mc + i] * A[(size_t)t * mc + i];
+      d = warp_sum(d);
+      if (lane == 0) pb[t] = d;
+    }
+    cl.sync();
+    ++par;
+    if (tj != 0.0) {
+      for (int t = j + 1 + tid; t < jend; t += blockDim.x) {
+        double w = 0.0;
+        for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
+        nrm[t] = w;                              // reused as the reduced products
+      }
+      __syncthreads();
+      const int w = jend - j - 1, h = nloc - lo;
+      for (int e = tid; e < w * h; e += blockDim.x) {
+        const int t = j + 1 + e / h, i = lo + e % h;
+        A[(size_t)t * mc + i] -= tj * A[(size_t)j * mc + i] * nrm[t];
+      }
+    }
+    __syncthreads();
+  };
+
+  // pivoted steps
+  int j = 0;
+  for (; j < npiv; ++j) {
+    const int lo = min(nloc, max(0, j - r0));
+    const int own = j / mc;
+    for (int t = j + wid; t < a.c3; t += nw) {
+      double sq = 0.0;
+      for (int i = lo + lane; i < nloc; i += 32) {
+        const double v = A[(size_t)t * mc + i];
+        sq += v * v;
+      }
+      sq = warp_sum(sq);
+      if (lane == 0) part[t] = sq;
+    }
+    if (me == own)
+      for (int t = j + tid; t < ncol; t += blockDim.x) rowj[t] = A[(size_t)t * mc + (j - r0)];
+    cl.sync();
+    double sum = 0.0, mx = -1.0;
+    int arg = j;
+    for (int t = j + tid; t < a.c3; t += blockDim.x) {
+      double sq = 0.0;
+      for (int c = 0; c < C; ++c) sq += cl.map_shared_rank(part, c)[t];
+      nrm[t] = sq;
+      sum += sq;
+      if (sq > mx) { mx = sq; arg = t; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      const double om = __shfl_xor_sync(0xffffffffu, mx, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+      if (om > mx || (om == mx && oa < arg)) { mx = om; arg = oa; }
+    }
+    if (lane == 0) { red[wid] = sum; red[32 + wid] = mx; ired[wid] = arg; }
+    __syncthreads();
+    double rem = 0.0, bm = -1.0;
+    int p = j;
+    for (int w = 0; w < nw; ++w) {
+      rem += red[w];
+      if (red[32 + w] > bm || (red[32 + w] == bm && ired[w] < p)) { bm = red[32 + w]; p = ired[w]; }
+    }
+    const double alpha = cl.map_shared_rank(rowj, own)[p];
+    const double nrm2 = nrm[p];
+    __syncthreads();
+    // the first column is always taken (a rank of at least one)
+    if (j > 0 && (rem <= thr2 || !(bm > 0.0))) break;
+    if (p != j)
+      for (int i = tid; i < nloc; i += blockDim.x) {
+        const double t0 = A[(size_t)j * mc + i];
+        A[(size_t)j * mc + i] = A[(size_t)p * mc + i];
+        A[(size_t)p * mc + i] = t0;
+      }
+    __syncthreads();
+    house(j, alpha, nrm2, ncol);
+  }
+  const int rk = j;
+  const int nr = min(rk + a.kick, a.m);
+  // the extra columns move next to the chosen ones (no CTA may still read
+  // this step's published norms when the next step writes them)
+  cl.sync();
+  for (int e = 0; e < nr - rk; ++e) {
+    const int t1 = rk + e, t2 = a.c3 + e;
+    if (t1 == t2) continue;
+    for (int i = tid; i < nloc; i += blockDim.x) {
+      const double t0 = A[(size_t)t1 * mc + i];
+      A[(size_t)t1 * mc + i] = A[(size_t)t2 * mc + i];
+      A[(size_t)t2 * mc + i] = t0;
+    }
+  }
+  __syncthreads();
+  // unpivoted steps on the extra columns
+  for (j = rk; j < nr; ++j) {
+    const int lo = min(nloc, max(0, j - r0));
+    const int own = j / mc;
+    double sq = 0.0;
+    for (int i = lo + tid; i < nloc; i += blockDim.x) {
+      const double v = A[(size_t)j * mc + i];
+      sq += v * v;
+    }
+    sq = qr_block_sum(sq, red);
+    if (tid == 0) part[0] = sq;
+    if (me == own && tid == 0) rowj[0] = A[(size_t)j * mc + (j - r0)];
+    cl.sync();
+    double nrm2 = 0.0;
+    for (int c = 0; c < C; ++c) nrm2 += cl.map_shared_rank(part, c)[0];
+    const double alpha = cl.map_shared_rank(rowj, own)[0];
+    house(j, alpha, nrm2, nr);
+  }
+  cl.sync();
+  // Q in place: Q(:, j) = H_0 ... H_{nr-1} e_j, the last reflector first
+  for (j = nr - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    const int lo = min(nloc, max(0, j - r0));
+    if (tj != 0.0 && j + 1 < nr) {
+      double* pb = pw + (par & 1) * ncol;
+      for (int t = j + 1 + wid; t < nr; t += nw) {
+        double d = 0.0;
+        for (int i = lo + lane; i < nloc; i += 32) d += A[(size_t)j * mc + i] * A[(size_t)t * mc + i];
+        d = warp_sum(d);
+        if (lane == 0) pb[t] = d;
+      }
+      cl.sync();
+      ++par;
+      for (int t = j + 1 + tid; t < nr; t += blockDim.x) {
+        double w = 0.0;
+        for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
+        nrm[t] = w;
+      }
+      __syncthreads();
+      const int w = nr - j - 1, h = nloc - lo;
+      for (int e = tid; e < w * h; e += blockDim.x) {
+        const int t = j + 1 + e / h, i = lo + e % h;
+        A[(size_t)t * mc + i] -= tj * A[(size_t)j * mc + i] * nrm[t];
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < nloc; i += blockDim.x) {
+      const int g = r0 + i;
+      double v;
+      if (g < j) v = 0.0;
+      else if (g == j) v = 1.0 - tj;
+      else v = -tj * A[(size_t)j * mc + i];
+      A[(size_t)j * mc + i] = v;
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < mc * nr; t += blockDim.x) {
+    const int i = t % mc, c = t / mc;
+    if (i < nloc) a.Q[(size_t)c * a.m + r0 + i] = A[t];
+  }
+  if (me == 0 && tid == 0) *a.rk = rk;
+  // no CTA leaves while another may still read its shared memory
+  cl.sync();
+}
+
+static int qr_cluster_max(iga_ctx* ctx);
+
+void qrcp_truncate(iga_ctx* ctx, const double* B, int m, int c3, int si, int sa, int r,
+                   const double* E, int kick, double rel, int jmax, double* Q, int* rk_dev) {
+  IGA_REQUIRE(m >= 1 && c3 >= 1 && r >= 1 && c3 <= 3 * r && kick >= 0, "qrcp: bad sizes");
+  const size_t limit = 200 * 1024;
+  const int cmax = qr_cluster_max(ctx);
+  const int C = std::max(1, std::min(cmax, m / 64));
+  const int mc = (m + C - 1) / C;
+  const int ncol = c3 + kick;
+  const size_t head = ((size_t)6 * ncol + 4 + 64) * sizeof(double) + 32 * sizeof(int);
+  const size_t slice = (size_t)mc * ncol * sizeof(double);
+  IGA_REQUIRE(head <= limit, "qrcp: too many columns");
+  QrcpArgs a;
+  a.B = B; a.E = E; a.Q = Q; a.rk = rk_dev; a.rel = rel;
+  a.m = m; a.c3 = c3; a.si = si; a.sa = sa; a.r = r; a.kick = kick;
+  a.jmax = std::max(1, std::min(jmax, m)); a.mc = mc;
+  a.gwork = head + slice <= limit ? nullptr : scratch<double>(ctx, SLOT_QRCP_WORK, (size_t)C * mc * ncol);
+  static bool attr = false;
+  if (!attr) {
+    IGA_CUDA(cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)limit));
+    IGA_CUDA(cudaFuncSetAttribute(qrcp_cluster_kernel,
+                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = a.gwork ? head : head + slice;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  // algorithmic: pivoted Householder on m x c3 up to rank jmax plus the
+  // extra columns, and forming Q: about 4 m c3 nr + 2 m nr^2 flop
+  const double nr = std::min(a.jmax + kick, m);
+  prof_count(ctx, 8.0 * m * (ncol + nr), 4.0 * m * c3 * nr + 2.0 * m * nr * nr);
+  bool prof = prof_match(ctx, "qrcp_cluster_kernel");
+  if (prof) prof_start(ctx);
+  IGA_CUDA(cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, a));
+  if (prof) prof_stop(ctx);
+  ctx->launches++;
+  ctx->next_bytes = 0.0;
+  ctx->next_flops = 0.0;
+}
+
 static size_t qr_cluster_smem(int mc, int k) {
   return ((size_t)2 * mc * k + 5 * (size_t)k + 2 + 32) * sizeof(double);
+}
+
+// largest cluster of 256-thread CTAs with 200 KB of shared memory each that
+// the GPU can schedule (16 with the non-portable size, else 8, else 1)
+static int qr_cluster_max(iga_ctx* ctx) {
+  static int cmax = 0;
+  if (cmax != 0) return cmax;
+  const size_t limit = 200 * 1024;
+  IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+  IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
+                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  int best = 1;
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(c);
+    q.blockDim = dim3(256);
+    q.dynamicSmemBytes = limit;
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeClusterDimension;
+    a[0].val.clusterDim.x = c;
+    a[0].val.clusterDim.y = 1;
+    a[0].val.clusterDim.z = 1;
+    q.attrs = a;
+    q.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, householder_qr_cluster_kernel, &q) == cudaSuccess &&
+        n >= 1) {
+      best = c;
+      break;
+    }
+    (void)cudaGetLastError();
+  }
+  (void)ctx;
+  cmax = best;
+  return cmax;
 }
 
 void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
@@ -321,39 +667,13 @@ void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
   // algorithmic: Householder QR 2 m k^2 - 2 k^3 / 3, forming Q the same again
   const double by = 3.0 * 8.0 * m * k;
   const double fl = 2.0 * (2.0 * m * k * k - 2.0 * k * k * k / 3.0);
-  // cluster of up to 16 CTAs with at least 64 rows each, when a slice fits
+  // cluster of up to 16 CTAs with at least 64 rows each (one CTA for small
+  // m) when a slice fits in shared memory, else the one-CTA global kernel
   const size_t limit = 200 * 1024;
-  static int cmax = 0;                          // largest schedulable cluster
-  if (cmax == 0) {
-    IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-    IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
-                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    cmax = 1;
-    for (int c : {16, 8}) {
-      cudaLaunchConfig_t q = {};
-      q.gridDim = dim3(c);
-      q.blockDim = dim3(256);
-      q.dynamicSmemBytes = limit;
-      cudaLaunchAttribute a[1];
-      a[0].id = cudaLaunchAttributeClusterDimension;
-      a[0].val.clusterDim.x = c;
-      a[0].val.clusterDim.y = 1;
-      a[0].val.clusterDim.z = 1;
-      q.attrs = a;
-      q.numAttrs = 1;
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, householder_qr_cluster_kernel, &q) == cudaSuccess &&
-          n >= 1) {
-        cmax = c;
-        break;
-      }
-      (void)cudaGetLastError();
-    }
-  }
+  const int cmax = qr_cluster_max(ctx);
   int C = std::max(1, std::min(cmax, m / 64));
   int mc = (m + C - 1) / C;
-  if (C >= 2 && qr_cluster_smem(mc, k) <= limit) {
+  if (qr_cluster_smem(mc, k) <= limit) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(256);
@@ -388,7 +708,7 @@ void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
 // eigenvectors V (columns).  Cyclic Jacobi with round-robin parallel
 // ordering: each round applies k/2 disjoint rotations (rows, then columns).
 // At most 40 sweeps; stops when the off-diagonal norm is below 1e-14 (FP64)
-// or 1e-6 (FP32) times the Frobenius norm.  Storage: mode 2 keeps A and V in
+// or 1e-4 (FP32) times the Frobenius norm.  Storage: mode 2 keeps A and V in
 // shared memory, mode 1 keeps A in shared memory and V in global memory,
 // mode 0 keeps both in global memory (A overwritten).  The FP32 variant
 // (T = float) always runs in mode 2; input and output stay FP64.
@@ -412,7 +732,9 @@ struct JacobiTol<double> {
 };
 template <>
 struct JacobiTol<float> {
-  static constexpr float off2 = 1e-12f, skip = 1e-8f, tiny = 1e-30f;
+  // the FP32 eigenbases only feed a preconditioner: a relative off-diagonal
+  // norm of 1e-4 is plenty
+  static constexpr float off2 = 1e-8f, skip = 1e-8f, tiny = 1e-30f;
 };
 
 template <typename T>
@@ -571,128 +893,13 @@ void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double
     }
     prof_count(ctx, by, fl);
   }
+  // one thread per rotation element of a round (k/2 pairs x k), at most 1024
+  int kkm2 = kmax + (kmax & 1);
+  int threads = std::min(1024, std::max(64, ((kkm2 / 2) * kmax + 31) / 32 * 32));
   if (fp32)
-    IGA_LAUNCH(ctx, jacobi_eig_kernel<float>, count, 1024, smem, batch);
+    IGA_LAUNCH(ctx, jacobi_eig_kernel<float>, count, threads, smem, batch);
   else
-    IGA_LAUNCH(ctx, jacobi_eig_kernel<double>, count, 1024, smem, batch);
-}
-
-// ----------------------------------------------------- pivoted Cholesky
-//
-// Rank-revealing pivoted Cholesky of a symmetric positive semidefinite k x k
-// Gram matrix G = B^T B: at each step the index with the largest Schur
-// complement diagonal is chosen and eliminated.  After j steps the trace of
-// the Schur complement equals || B - Q_j Q_j^T B ||_F^2, Q_j an orthonormal
-// basis of the chosen columns of B (this is QR with column pivoting of B done
-// on its Gram matrix).  The factorisation stops at the first j with that trace
-// <= rel^2 trace(G), or at j = jmax, so the truncation error of the chosen
-// columns is bounded exactly like an SVD truncation's.
-//
-// Only the lower triangle (row >= column, col-major) is read and updated.
-// Mode 1 keeps the matrix in shared memory, mode 0 works on G in place.
-
-__global__ void pivoted_cholesky_kernel(double* __restrict__ Gg, int k, double rel, int jmax,
-                                        int mode, int* __restrict__ piv,
-                                        double* __restrict__ dsel, int* __restrict__ rk_out) {
-  extern __shared__ double sm[];
-  double* red = sm;                      // 32 sums + 32 maxima
-  double* lv = sm + 64;                  // k
-  int* perm = (int*)(lv + k);            // k (+1 padding to 8 bytes)
-  int* ired = perm + k + (k & 1);        // 32 arg indices
-  double* S = Gg;
-  if (mode == 1) {
-    S = (double*)(ired + 32);
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) S[t] = Gg[t];
-  }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) perm[i] = i;
-  __syncthreads();
-  double tr = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) tr += fmax(S[(size_t)i * k + i], 0.0);
-  tr = block_sum(tr, red);
-  const double thr2 = rel * rel * tr;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  int j = 0;
-  for (; j < jmax; ++j) {
-    // remaining trace and the largest remaining diagonal
-    double sum = 0.0, mx = -1.0;
-    int arg = j;
-    for (int i = j + threadIdx.x; i < k; i += blockDim.x) {
-      int a = perm[i];
-      double d = S[(size_t)a * k + a];
-      sum += fmax(d, 0.0);
-      if (d > mx) { mx = d; arg = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      double om = __shfl_xor_sync(0xffffffffu, mx, o);
-      int oa = __shfl_xor_sync(0xffffffffu, arg, o);
-      if (om > mx || (om == mx && oa < arg)) { mx = om; arg = oa; }
-    }
-    if (lane == 0) { red[wid] = sum; red[32 + wid] = mx; ired[wid] = arg; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double ts = 0.0, tm = -1.0;
-      int ta = j;
-      for (int w = 0; w < nw; ++w) {
-        ts += red[w];
-        if (red[32 + w] > tm || (red[32 + w] == tm && ired[w] < ta)) { tm = red[32 + w]; ta = ired[w]; }
-      }
-      red[0] = ts; red[32] = tm; ired[0] = ta;
-      // the first step is always taken (a rank of at least one)
-      bool stop = j > 0 && (ts <= thr2 || !(tm > 0.0));
-      if (j == 0 && !(tm > 0.0)) ta = 0;
-      if (!stop) {
-        int t = perm[j]; perm[j] = perm[ta]; perm[ta] = t;
-        piv[j] = perm[j];
-        dsel[j] = tm;
-      }
-      ired[1] = stop ? 1 : 0;
-    }
-    __syncthreads();
-    if (ired[1]) break;
-    const int pj = perm[j];
-    const double dp = S[(size_t)pj * k + pj];
-    const double inv = dp > 0.0 ? 1.0 / sqrt(dp) : 0.0;
-    // column of the factor over the remaining indices (position i -> lv[i])
-    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
-      int a = perm[i];
-      int hi = max(a, pj), lo = min(a, pj);
-      lv[i] = S[(size_t)lo * k + hi] * inv;
-    }
-    __syncthreads();
-    // Schur update of the lower triangle over the remaining indices
-    const int w = k - j - 1;
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      int i = j + 1 + t / w, i2 = j + 1 + t % w;
-      if (i2 > i) continue;
-      int a = perm[i], b = perm[i2];
-      int hi = max(a, b), lo = min(a, b);
-      S[(size_t)lo * k + hi] -= lv[i] * lv[i2];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *rk_out = j;
-}
-
-void pivoted_cholesky(iga_ctx* ctx, double* G, int k, double rel, int jmax, int* piv,
-                      double* dsel, int* rk) {
-  IGA_REQUIRE(k >= 1, "pivoted_cholesky: empty problem");
-  jmax = std::max(1, std::min(jmax, k));
-  const size_t limit = 220 * 1024;
-  size_t head = (size_t)(64 + k) * sizeof(double) + (size_t)(k + (k & 1) + 32) * sizeof(int);
-  size_t one = (size_t)k * k * sizeof(double);
-  int mode = head + one <= limit ? 1 : 0;
-  size_t smem = head + (mode == 1 ? one : 0);
-  IGA_REQUIRE(head <= limit, "pivoted_cholesky: k too large");
-  static bool attr = false;
-  if (!attr) {
-    IGA_CUDA(cudaFuncSetAttribute(pivoted_cholesky_kernel,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-    attr = true;
-  }
-  // algorithmic: k^3 / 3 flop for a full factorisation, the matrix read once
-  prof_count(ctx, 8.0 * (double)k * k, (double)k * k * k / 3.0);
-  IGA_LAUNCH(ctx, pivoted_cholesky_kernel, 1, 512, smem, G, k, rel, jmax, mode, piv, dsel, rk);
+    IGA_LAUNCH(ctx, jacobi_eig_kernel<double>, count, threads, smem, batch);
 }
 
 void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k) {
