@@ -310,7 +310,9 @@ typedef struct {
   int precision;       /* IGA_FP64 or IGA_FP32 for the AMEn contractions */
   int verbose;         /* print one line per sweep to stderr */
   double trunc_tol;    /* relative truncation of each field in the block core
-                          when the block index moves (0: tol / 1000) */
+                          when the block index moves (0: tol / 1000, lowered
+                          100-fold down to tol * 1e-5 whenever a sweep reduces
+                          the residual by less than a factor 4) */
   int truncation;      /* how the block index moves: IGA_TRUNC_PIVOTED or
                           IGA_TRUNC_SVD (see iga_trunc) */
 } iga_solve_opts;

@@ -28,6 +28,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 
 #include "iga_internal.cuh"
 
@@ -481,6 +482,22 @@ static void rm_gemm(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const d
                        N, M, K, &alpha, B, ldb, A, lda, &beta, C, ldc));
 }
 
+// count products C_i = alpha op(A_i) op(B_i) + beta C_i of row-major matrices
+// with A_i = A + i sA (likewise B, C): one batched cuBLAS call
+static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const double* A,
+                            int lda, long long sA, const double* B, int ldb, long long sB,
+                            double* C, int ldc, long long sC, int count, double alpha = 1.0,
+                            double beta = 0.0) {
+  if (M == 0 || N == 0 || count == 0) return;
+  if (count == 1) {
+    rm_gemm(ctx, tA, tB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
+    return;
+  }
+  IGA_BLAS(cublasDgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,
+                                     tA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, B, ldb, sB,
+                                     A, lda, sA, &beta, C, ldc, sC, count));
+}
+
 // nonzero pattern of one TT-matrix core of an operator
 struct CoreNZ {
   int R0 = 1, R1 = 1;
@@ -585,15 +602,13 @@ struct Solver {
     double* u = slot(0, per * c.R0);
     double* w = slot(1, per * c.R1);
     // u[al] = PhiL[al] X  (r0 x n r1 each)
-    for (int al = 0; al < c.R0; ++al)
-      rm_gemm(ctx, false, false, r0, nn * r1, r0, PhiL[o][d].p + (size_t)al * r0 * r0, r0, X[d].p,
-              nn * r1, u + al * per, nn * r1);
+    rm_gemm_batched(ctx, false, false, r0, nn * r1, r0, PhiL[o][d].p, r0, (long long)r0 * r0,
+                    X[d].p, nn * r1, 0, u, nn * r1, (long long)per, c.R0);
     IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R1 * per), 256, 0, op[o]->band64[d].p,
                c.colptr.p, c.colsrc.p, c.coloff.p, u, c.R1, r0, nn, r1, op[o]->p[d], w);
     PhiL[o][d + 1].ensure((size_t)c.R1 * r1 * r1);
-    for (int be = 0; be < c.R1; ++be)
-      rm_gemm(ctx, true, false, r1, r1, r0 * nn, X[d].p, r1, w + be * per, r1,
-              PhiL[o][d + 1].p + (size_t)be * r1 * r1, r1);
+    rm_gemm_batched(ctx, true, false, r1, r1, r0 * nn, X[d].p, r1, 0, w, r1, (long long)per,
+                    PhiL[o][d + 1].p, r1, (long long)r1 * r1, c.R1);
   }
 
   void right_update(int o, int d) {         // PhiR[o][d-1] from PhiR[o][d] and X[d]
@@ -602,15 +617,13 @@ struct Solver {
     size_t per = (size_t)r0 * nn * r1;
     double* u = slot(0, per * c.R1);
     double* w = slot(1, per * c.R0);
-    for (int be = 0; be < c.R1; ++be)
-      rm_gemm(ctx, false, true, r0 * nn, r1, r1, X[d].p, r1, PhiR[o][d].p + (size_t)be * r1 * r1,
-              r1, u + be * per, r1);
+    rm_gemm_batched(ctx, false, true, r0 * nn, r1, r1, X[d].p, r1, 0, PhiR[o][d].p, r1,
+                    (long long)r1 * r1, u, r1, (long long)per, c.R1);
     IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R0 * per), 256, 0, op[o]->band64[d].p,
                c.rowptr.p, c.rowsrc.p, c.rowoff.p, u, c.R0, r0, nn, r1, op[o]->p[d], w);
     PhiR[o][d - 1].ensure((size_t)c.R0 * r0 * r0);
-    for (int al = 0; al < c.R0; ++al)
-      rm_gemm(ctx, false, true, r0, r0, nn * r1, X[d].p, nn * r1, w + al * per, nn * r1,
-              PhiR[o][d - 1].p + (size_t)al * r0 * r0, r0);
+    rm_gemm_batched(ctx, false, true, r0, r0, nn * r1, X[d].p, nn * r1, 0, w, nn * r1,
+                    (long long)per, PhiR[o][d - 1].p, r0, (long long)r0 * r0, c.R0);
   }
 
   void set_ones(DevBuf<double>& b) {
@@ -637,21 +650,22 @@ struct Solver {
     if (d == 0) {
       double* Xr = slot(2, (size_t)r[1] * n2 * n3);
       right_frame(Xr);
-      for (int l = 0; l < 3; ++l)
-        rm_gemm(ctx, false, true, n1, r[1], n2 * n3, F + l * N, n2 * n3, Xr, n2 * n3,
-                rhs + l * loc, r[1]);
+      rm_gemm_batched(ctx, false, true, n1, r[1], n2 * n3, F, n2 * n3, (long long)N, Xr, n2 * n3,
+                      0, rhs, r[1], (long long)loc, 3);
     } else if (d == 1) {
-      double* s = slot(2, (size_t)n1 * n2 * r[2]);
-      for (int l = 0; l < 3; ++l) {
-        rm_gemm(ctx, false, true, n1 * n2, r[2], n3, F + l * N, n3, X[2].p, n3, s, r[2]);
-        rm_gemm(ctx, true, false, r[1], n2 * r[2], n1, X[0].p, r[1], s, n2 * r[2], rhs + l * loc,
-                n2 * r[2]);
+      double* s = slot(2, (size_t)3 * n1 * n2 * r[2]);       // one slab per field
+      {
+        const long long ss = (long long)n1 * n2 * r[2];
+        rm_gemm_batched(ctx, false, true, n1 * n2, r[2], n3, F, n3, (long long)N, X[2].p, n3, 0, s,
+                        r[2], ss, 3);
+        rm_gemm_batched(ctx, true, false, r[1], n2 * r[2], n1, X[0].p, r[1], 0, s, n2 * r[2], ss,
+                        rhs, n2 * r[2], (long long)loc, 3);
       }
     } else {
       double* Xl = slot(2, (size_t)n1 * n2 * r[2]);
       left_frame(Xl);
-      for (int l = 0; l < 3; ++l)
-        rm_gemm(ctx, true, false, r[2], n3, n1 * n2, Xl, r[2], F + l * N, n3, rhs + l * loc, n3);
+      rm_gemm_batched(ctx, true, false, r[2], n3, n1 * n2, Xl, r[2], 0, F, n3, (long long)N, rhs,
+                      n3, (long long)loc, 3);
     }
   }
 
@@ -662,22 +676,22 @@ struct Solver {
     if (d == 0) {
       double* Xr = slot(2, (size_t)r[1] * n2 * n3);
       right_frame(Xr);
-      for (int l = 0; l < 3; ++l)
-        rm_gemm(ctx, false, false, n1, n2 * n3, r[1], Xh.p + l * loc, r[1], Xr, n2 * n3,
-                out + l * N, n2 * n3);
+      rm_gemm_batched(ctx, false, false, n1, n2 * n3, r[1], Xh.p, r[1], (long long)loc, Xr,
+                      n2 * n3, 0, out, n2 * n3, (long long)N, 3);
     } else if (d == 1) {
-      double* t = slot(2, (size_t)n1 * n2 * r[2]);
-      for (int l = 0; l < 3; ++l) {
-        rm_gemm(ctx, false, false, n1, n2 * r[2], r[1], X[0].p, r[1], Xh.p + l * loc, n2 * r[2],
-                t, n2 * r[2]);
-        rm_gemm(ctx, false, false, n1 * n2, n3, r[2], t, r[2], X[2].p, n3, out + l * N, n3);
+      double* t = slot(2, (size_t)3 * n1 * n2 * r[2]);       // one slab per field
+      {
+        const long long ts = (long long)n1 * n2 * r[2];
+        rm_gemm_batched(ctx, false, false, n1, n2 * r[2], r[1], X[0].p, r[1], 0, Xh.p, n2 * r[2],
+                        (long long)loc, t, n2 * r[2], ts, 3);
+        rm_gemm_batched(ctx, false, false, n1 * n2, n3, r[2], t, r[2], ts, X[2].p, n3, 0, out, n3,
+                        (long long)N, 3);
       }
     } else {
       double* Xl = slot(2, (size_t)n1 * n2 * r[2]);
       left_frame(Xl);
-      for (int l = 0; l < 3; ++l)
-        rm_gemm(ctx, false, false, n1 * n2, n3, r[2], Xl, r[2], Xh.p + l * loc, n3, out + l * N,
-                n3);
+      rm_gemm_batched(ctx, false, false, n1 * n2, n3, r[2], Xl, r[2], 0, Xh.p, n3, (long long)loc,
+                      out, n3, (long long)N, 3);
     }
   }
 
@@ -813,9 +827,8 @@ struct Solver {
     rm_gemm(ctx, false, false, nr, c3, m, Q, m, Mx, c3, coef, c3);
     int n2 = n[d + 1], r2 = r[d + 2];
     Xh.ensure((size_t)3 * nr * n2 * r2);
-    for (int l = 0; l < 3; ++l)
-      rm_gemm(ctx, false, false, nr, n2 * r2, r1, coef + l * r1, c3, X[d + 1].p, n2 * r2,
-              Xh.p + (size_t)l * nr * n2 * r2, n2 * r2);
+    rm_gemm_batched(ctx, false, false, nr, n2 * r2, r1, coef, c3, r1, X[d + 1].p, n2 * r2, 0,
+                    Xh.p, n2 * r2, (long long)nr * n2 * r2, 3);
     r[d + 1] = nr;
     left_update(0, d);
     left_update(1, d);
@@ -866,9 +879,8 @@ struct Solver {
                              ctx->stream));
     int rp = r[d - 1], np = n[d - 1];
     double* nXh = slot(13, (size_t)3 * rp * np * nr);
-    for (int l = 0; l < 3; ++l)
-      rm_gemm(ctx, false, false, rp * np, nr, r0, X[d - 1].p, r0, coef + (size_t)l * r0 * nr, nr,
-              nXh + (size_t)l * rp * np * nr, nr);
+    rm_gemm_batched(ctx, false, false, rp * np, nr, r0, X[d - 1].p, r0, 0, coef, nr,
+                    (long long)r0 * nr, nXh, nr, (long long)rp * np * nr, 3);
     Xh.ensure((size_t)3 * rp * np * nr);
     IGA_CUDA(cudaMemcpyAsync(Xh.p, nXh, (size_t)3 * rp * np * nr * 8, cudaMemcpyDeviceToDevice,
                              ctx->stream));
@@ -1322,6 +1334,13 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   int maxsw = std::max(1, o->max_sweeps);
   double tol_abs = 0.1 * tol * Fnorm;
   int maxit = std::max(1, o->local_maxit);
+  // default truncation: when a sweep reduces the residual by less than a
+  // factor 4, the truncation error (amplified by the KKT operator) is taken
+  // to limit the correction and the truncation tolerance drops 100-fold, down
+  // to 1e-5 tol
+  const bool adapt = !(o->trunc_tol > 0.0);
+  const double trunc_floor = 1e-5 * tol;
+  double rel_prev = std::numeric_limits<double>::infinity();
   for (sweep = 0; sweep < maxsw; ++sweep) {
     bool fwd = (sweep % 2) == 0;
     int order[3] = {0, 1, 2};
@@ -1351,6 +1370,11 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
         else S.move_backward(d, res);
       }
     }
+    if (adapt && sweep >= 1 && rel > 0.25 * rel_prev && S.trunc_tol > trunc_floor) {
+      S.trunc_tol = std::max(0.01 * S.trunc_tol, trunc_floor);
+      if (S.verbose) fprintf(stderr, "[amen] truncation tolerance -> %.1e\n", S.trunc_tol);
+    }
+    rel_prev = rel;
   }
 done:
   *sweeps_out += sweep;

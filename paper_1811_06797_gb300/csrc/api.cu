@@ -231,7 +231,7 @@ void weight_tts_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& s
   if (8 * S * sizeof(double) > free_b / 3) {
     // large grids: one sample tensor at a time, each compressed before the next
     double* buf = scratch<double>(ctx, SLOT_ASM_SAMPLES, S);
-    double* qn2 = scratch<double>(ctx, SLOT_MISC0 + 61, 1);
+    double* qn2 = scratch<double>(ctx, SLOT_QNORM, 1);
     EachCtx e{ctx, {Q[0], Q[1], Q[2]}, tol, qn2, 0.0, tts};
     try {
       sample_weights_each(ctx, geo, st, target, buf, qn2, weight_tt_cb, &e);

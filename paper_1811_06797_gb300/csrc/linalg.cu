@@ -1005,57 +1005,96 @@ static void gemm(iga_ctx* ctx, cublasOperation_t ta, cublasOperation_t tb, int m
 // (m x ns) when xT == false, A = Z with Z col-major (ns x m) when xT == true.
 // Returns the rank r, U (ns x r) col-major in Uout, Ct = A^T U (m x r)
 // col-major in Ctout.  Both outputs are (re)allocated here.
+//
+// Blocked adaptive randomized range finder: Gaussian blocks (8, 16, 32, ...
+// columns) are applied to A, projected off the basis found so far (twice)
+// and orthonormalised, until a fresh block's projected norm shows
+// ||(I - Q Q^T) A||_F <= delta / 10 (for Gaussian columns w,
+// E ||(I - QQ^T) A w||^2 = ||(I - QQ^T) A||_F^2).  Then Bt = A^T Q is formed
+// once, its SVD comes from a two-pass Gram/Jacobi (the second Gram matrix is
+// nearly diagonal, which gives relative accuracy to the small singular
+// values), and the rank is the smallest r whose sketched tail plus the
+// residual estimate is <= delta^2.  A is read once per block and once for Bt.
 static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, double delta,
                      int rmax, DevBuf<double>& Uout, DevBuf<double>& Ctout, uint64_t seed) {
-  int k = std::min(ns, 4);
-  std::vector<double> lam;
-  double* Q = nullptr;
-  double* V = nullptr;
-  int r = 1;
-  for (;;) {
-    double* Om = scratch<double>(ctx, SLOT_TTSVD_OMEGA, (size_t)m * k);
-    double* Y = scratch<double>(ctx, SLOT_TTSVD_Y, (size_t)ns * k);
-    Q = scratch<double>(ctx, SLOT_TTSVD_Q, (size_t)ns * k);
-    double* Bt = scratch<double>(ctx, SLOT_TTSVD_BT, (size_t)m * k * 2);
-    double* Bt2 = Bt + (size_t)m * k;
-    double* G = scratch<double>(ctx, SLOT_TTSVD_G, (size_t)k * k * 2 + k);
-    double* wv = G + (size_t)k * k * 2;
-    V = scratch<double>(ctx, SLOT_TTSVD_V, (size_t)k * k * 3);
-    double* V1 = V + (size_t)k * k;
-    double* V2 = V1 + (size_t)k * k;
-    fill_gaussian(ctx, Om, (size_t)m * k, seed + (uint64_t)k * 7919u);
-    if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, k, m, X, m, Om, m, Y, ns);
-    else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, k, m, X, ns, Om, m, Y, ns);
-    householder_qr(ctx, Y, Q, ns, k);
-    if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, ns, X, m, Q, ns, Bt, m);
-    else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, m, k, ns, X, ns, Q, ns, Bt, m);
-    // first Gram pass
-    gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt, m, Bt, m, G, k);
-    jacobi_eig(ctx, G, V1, wv, k);
-    // second pass on the rotated factor: nearly diagonal Gram matrix
-    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
-    gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
-    jacobi_eig(ctx, G, V2, wv, k);
-    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, V1, k, V2, k, V, k);
-    lam.resize(k);
-    IGA_CUDA(cudaMemcpyAsync(lam.data(), wv, k * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-    double smin = std::sqrt(std::max(lam[k - 1], 0.0));
-    if (k >= ns || smin <= 0.1 * delta || k >= 256) break;
-    k = std::min(ns, 2 * k);
+  const int kcap = std::min(ns, 256);
+  double* Q = scratch<double>(ctx, SLOT_TTSVD_Q, (size_t)ns * kcap);    // (swapped with Yq)
+  double* Om = scratch<double>(ctx, SLOT_TTSVD_OMEGA, (size_t)m * std::min(kcap, 128));
+  double* Y = scratch<double>(ctx, SLOT_TTSVD_Y, (size_t)ns * std::min(kcap, 128));
+  double* Yq = scratch<double>(ctx, SLOT_TTSVD_Y2, (size_t)ns * kcap);
+  double* T = scratch<double>(ctx, SLOT_TTSVD_C, (size_t)kcap * std::min(kcap, 128));
+  const double one = 1.0, mone = -1.0, zero = 0.0;
+  int kq = 0;
+  int b = std::min(ns, 8);
+  double est2 = 0.0;                           // squared residual estimate
+  for (int blk = 0;; ++blk) {
+    const int bt = std::min(b, kcap - kq);
+    if (bt <= 0) { est2 = 0.0; break; }
+    fill_gaussian(ctx, Om, (size_t)m * bt, seed + 7919u * (uint64_t)(blk + 1));
+    if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, bt, m, X, m, Om, m, Y, ns);
+    else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, bt, m, X, ns, Om, m, Y, ns);
+    for (int pass = 0; pass < 2 && kq > 0; ++pass) {
+      // Y -= Q (Q^T Y)
+      IGA_BLAS(cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, kq, bt, ns, &one, Q, ns, Y, ns,
+                           &zero, T, kq));
+      IGA_BLAS(cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, ns, bt, kq, &mone, Q, ns, T, kq,
+                           &one, Y, ns));
+    }
+    const double yn = device_norm2(ctx, Y, (size_t)ns * bt);
+    est2 = yn * yn / bt;
+    if (est2 <= 0.01 * delta * delta) break;
+    // orthonormalise [Q, Y] as a whole: the kept columns come back up to
+    // sign, and the new ones are orthogonal to them even when Y is
+    // numerically rank deficient (Householder completes the basis)
+    IGA_CUDA(cudaMemcpyAsync(Q + (size_t)kq * ns, Y, (size_t)ns * bt * sizeof(double),
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+    householder_qr(ctx, Q, Yq, ns, kq + bt);
+    std::swap(Q, Yq);
+    kq += bt;
+    if (kq >= kcap) { est2 = kq >= ns ? 0.0 : est2; break; }
+    b = std::min(2 * b, 128);
   }
-  // smallest r with the tail of the sketched spectrum below delta
+  const int k = std::max(kq, 1);
+  if (kq == 0) {
+    // A is below the threshold as a whole: one basis vector from a fresh sketch
+    fill_gaussian(ctx, Om, (size_t)m, seed + 104729u);
+    if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, 1, m, X, m, Om, m, Y, ns);
+    else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, 1, m, X, ns, Om, m, Y, ns);
+    householder_qr(ctx, Y, Q, ns, 1);
+  }
+  double* Bt = scratch<double>(ctx, SLOT_TTSVD_BT, (size_t)m * k * 2);
+  double* Bt2 = Bt + (size_t)m * k;
+  double* G = scratch<double>(ctx, SLOT_TTSVD_G, (size_t)k * k * 2 + k);
+  double* wv = G + (size_t)k * k * 2;
+  double* V = scratch<double>(ctx, SLOT_TTSVD_V, (size_t)k * k * 3);
+  double* V1 = V + (size_t)k * k;
+  double* V2 = V1 + (size_t)k * k;
+  if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, ns, X, m, Q, ns, Bt, m);
+  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, m, k, ns, X, ns, Q, ns, Bt, m);
+  // first Gram pass
+  gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt, m, Bt, m, G, k);
+  jacobi_eig(ctx, G, V1, wv, k);
+  // second pass on the rotated factor: nearly diagonal Gram matrix
+  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
+  gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
+  jacobi_eig(ctx, G, V2, wv, k);
+  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, V1, k, V2, k, V, k);
+  std::vector<double> lam(k);
+  IGA_CUDA(cudaMemcpyAsync(lam.data(), wv, k * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  // smallest r with the sketched tail plus the residual estimate below delta
   std::vector<double> tail(k + 1, 0.0);
+  tail[k] = est2;
   for (int i = k - 1; i >= 0; --i) tail[i] = tail[i + 1] + std::max(lam[i], 0.0);
-  r = k;
+  int r = k;
   for (int i = 1; i <= k; ++i)
     if (std::sqrt(tail[i]) <= delta) { r = i; break; }
   r = std::max(1, std::min(r, rmax));
   Uout.alloc((size_t)ns * r);
   gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, r, k, Q, ns, V, k, Uout.p, ns);
+  // Ct = A^T U = Bt V_r
   Ctout.alloc((size_t)m * r);
-  if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, r, ns, X, m, Uout.p, ns, Ctout.p, m);
-  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, m, r, ns, X, ns, Uout.p, ns, Ctout.p, m);
+  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, r, k, Bt, m, V, k, Ctout.p, m);
   return r;
 }
 
@@ -1070,31 +1109,30 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
 // rank-1 approximation that good, so TT-SVD would also stop at rank one, and
 // the rank-1 TT is returned without any sketch.
 
-__global__ void absmax_kernel(const double* __restrict__ x, size_t n,
-                              unsigned long long* __restrict__ best) {
-  // the bits of a non-negative double order like the values, so an integer
-  // atomicMax on them finds max |x|; the index is found in a second pass
-  double m = 0.0;
+__global__ void absmax_key_kernel(const double* __restrict__ x, size_t n,
+                                  unsigned long long* __restrict__ key) {
+  // key = (upper 32 bits of |x| as a double) << 32 | index: the upper bits of
+  // a non-negative double order like its value, so the largest key marks an
+  // entry within a factor 1 + 2^-20 of max |x| (any such entry is a good
+  // pivot); one integer atomicMax per warp
+  unsigned long long best = 0ull;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    m = fmax(m, fabs(x[i]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(best, (unsigned long long)__double_as_longlong(m));
-}
-
-__global__ void argmax_kernel(const double* __restrict__ x, size_t n,
-                              const unsigned long long* __restrict__ best,
-                              unsigned long long* __restrict__ idx) {
-  double m = __longlong_as_double((long long)*best);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    if (fabs(x[i]) == m) atomicMin(idx, (unsigned long long)i);
+       i += (size_t)gridDim.x * blockDim.x) {
+    unsigned long long hi = (unsigned long long)__double_as_longlong(fabs(x[i])) >> 32;
+    unsigned long long k = (hi << 32) | (unsigned long long)i;
+    best = k > best ? k : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+    best = other > best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(key, best);
 }
 
 __global__ void fibres_kernel(const double* __restrict__ W, int n1, int n2, int n3,
                               const unsigned long long* __restrict__ idx, double* __restrict__ f) {
-  // f = [a (n1) | b (n2) | c (n3) | v]
-  size_t id = *idx;
+  // f = [a (n1) | b (n2) | c (n3) | v]; the pivot index is the low half of the key
+  size_t id = (size_t)(*idx & 0xffffffffull);
   int k0 = (int)(id % n3);
   int j0 = (int)((id / n3) % n2);
   int i0 = (int)(id / ((size_t)n2 * n3));
@@ -1142,17 +1180,16 @@ __global__ void rank1_cores_kernel(const double* __restrict__ f, int n1, int n2,
 // returns a rank-1 TT when the cross candidate meets err <= limit, else nullptr
 static iga_tt* rank1_cross(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double limit) {
   size_t N = (size_t)n1 * n2 * n3;
+  if (N >= (1ull << 32)) return nullptr;            // the pivot key holds a 32-bit index
   unsigned long long* keys = scratch<unsigned long long>(ctx, SLOT_TTSVD_C, 2);
   double* f = scratch<double>(ctx, SLOT_TTSVD_W, (size_t)n1 + n2 + n3 + 2);
   double* err = f + n1 + n2 + n3 + 1;
-  unsigned long long init[2] = {0ull, ~0ull};
-  IGA_CUDA(cudaMemcpyAsync(keys, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+  IGA_CUDA(cudaMemsetAsync(keys, 0, 2 * sizeof(unsigned long long), ctx->stream));
   IGA_CUDA(cudaMemsetAsync(err, 0, sizeof(double), ctx->stream));
   int blocks = (int)std::min<size_t>((N + 255) / 256, 152 * 8);
-  IGA_LAUNCH(ctx, absmax_kernel, blocks, 256, 0, W, N, keys);
-  IGA_LAUNCH(ctx, argmax_kernel, blocks, 256, 0, W, N, keys, keys + 1);
+  IGA_LAUNCH(ctx, absmax_key_kernel, blocks, 256, 0, W, N, keys);
   int nf = n1 + n2 + n3 + 1;
-  IGA_LAUNCH(ctx, fibres_kernel, (nf + 255) / 256, 256, 0, W, n1, n2, n3, keys + 1, f);
+  IGA_LAUNCH(ctx, fibres_kernel, (nf + 255) / 256, 256, 0, W, n1, n2, n3, keys, f);
   prof_count(ctx, (double)N * 8.0, 4.0 * (double)N);
   int rblocks = (int)std::min<long long>((long long)n1 * n2, 152 * 8);
   IGA_LAUNCH(ctx, rank1_residual_kernel, rblocks, 256, 0, W, n1, n2, n3, f, err);
