@@ -489,8 +489,12 @@ static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K,
                             double* C, int ldc, long long sC, int count, double alpha = 1.0,
                             double beta = 0.0) {
   if (M == 0 || N == 0 || count == 0) return;
-  if (count == 1) {
-    rm_gemm(ctx, tA, tB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
+  // the library splits a long inner dimension over CTAs only for single
+  // GEMMs: long reductions with a small output run as a loop
+  if (count == 1 || (long long)K > 4LL * std::max(M, N)) {
+    for (int i = 0; i < count; ++i)
+      rm_gemm(ctx, tA, tB, M, N, K, A + i * sA, lda, B + i * sB, ldb, C + i * sC, ldc, alpha,
+              beta);
     return;
   }
   IGA_BLAS(cublasDgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,

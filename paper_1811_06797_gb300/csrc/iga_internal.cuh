@@ -189,7 +189,7 @@ enum {
   SLOT_TTSVD_OMEGA = 0, SLOT_TTSVD_Y, SLOT_TTSVD_Q, SLOT_TTSVD_BT, SLOT_TTSVD_G, SLOT_TTSVD_V,
   SLOT_TTSVD_W, SLOT_TTSVD_C, SLOT_TTSVD_NORM, SLOT_QRCP_WORK, SLOT_ASM_W, SLOT_ASM_SAMPLES, SLOT_KRON_Z,
   SLOT_KRON_Z2, SLOT_LOCAL_T1, SLOT_LOCAL_T2, SLOT_KKT_TMP, SLOT_MISC0, SLOT_MISC1,
-  SLOT_TTM_W, SLOT_QNORM, SLOT_TTSVD_Y2,
+  SLOT_TTM_W, SLOT_QNORM, SLOT_TTSVD_Y2, SLOT_TTSVD_PART,
   SLOT_AMEN_BASE = 32
 };
 

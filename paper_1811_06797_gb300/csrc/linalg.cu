@@ -1001,6 +1001,168 @@ static void gemm(iga_ctx* ctx, cublasOperation_t ta, cublasOperation_t tb, int m
   IGA_BLAS(cublasDgemm(ctx->blas, ta, tb, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc));
 }
 
+// ---- narrow products with a wide row-major A (ns x m, row length m >> ns)
+//
+// The randomized range finder multiplies the first unfolding (a few hundred
+// rows of length n2 n3) by 8..16 columns.  Library GEMM tiles are 32 or 64
+// columns wide and waste most of their FP64 work on such shapes; these
+// kernels do only the k needed products per element.
+
+constexpr int SKINNY_K = 16;        // widest block handled here
+constexpr int SKINNY_R = 32;        // rows of A per CTA in the sketch
+constexpr int SKINNY_T = 96;        // columns of A per shared-memory tile
+constexpr int SKINNY_C = 2016;      // columns of A per CTA in the sketch (21 tiles)
+
+// partial Y = A Om over this CTA's rows [i0, i0 + 32) and column chunk:
+// P[chunk][i][c].  Thread (r, q), r = t / 8, q = t % 8, accumulates row i0 + r
+// over the tile columns j = q, q + 8, ... in registers; A and Om tiles are
+// staged in shared memory with coalesced loads, and the eight partial sums
+// of a row (eight neighbouring lanes) meet by shuffles.
+__global__ void __launch_bounds__(256) skinny_sketch_kernel(
+    const double* __restrict__ A, int ns, long long m, const double* __restrict__ Om, int k,
+    double* __restrict__ P) {
+  __shared__ double As[SKINNY_R][SKINNY_T + 1];
+  __shared__ double Os[SKINNY_T][SKINNY_K];
+  const int i0 = blockIdx.y * SKINNY_R;
+  const long long c0 = (long long)blockIdx.x * SKINNY_C;
+  const long long cend = c0 + SKINNY_C < m ? c0 + SKINNY_C : m;
+  const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
+  double acc[SKINNY_K];
+#pragma unroll
+  for (int c = 0; c < SKINNY_K; ++c) acc[c] = 0.0;
+  for (long long j0 = c0; j0 < cend; j0 += SKINNY_T) {
+    for (int t = threadIdx.x; t < SKINNY_R * SKINNY_T; t += blockDim.x) {
+      const int rr = t / SKINNY_T, jj = t - rr * SKINNY_T;
+      const long long j = j0 + jj;
+      As[rr][jj] = (i0 + rr < ns && j < cend) ? A[(size_t)(i0 + rr) * m + j] : 0.0;
+    }
+    for (int t = threadIdx.x; t < SKINNY_T * SKINNY_K; t += blockDim.x) {
+      const int c = t / SKINNY_T, jj = t - c * SKINNY_T;
+      const long long j = j0 + jj;
+      Os[jj][c] = (c < k && j < cend) ? Om[(size_t)c * m + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = q; jj < SKINNY_T; jj += 8) {
+      const double a = As[r][jj];
+#pragma unroll
+      for (int c = 0; c < SKINNY_K; ++c)
+        if (c < k) acc[c] = fma(a, Os[jj][c], acc[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < SKINNY_K; ++c) {
+    double v = acc[c];
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    if (q == 0 && c < k && i0 + r < ns) P[((size_t)blockIdx.x * ns + i0 + r) * k + c] = v;
+  }
+}
+
+// Y (ns x k col-major) = sum over CTAs of the partials
+__global__ void skinny_reduce_kernel(const double* __restrict__ P, int nblk, int ns, int k,
+                                     double* __restrict__ Y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * k) return;
+  const int i = t / k, c = t - (t / k) * k;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += P[(size_t)b * ns * k + t];
+  Y[(size_t)c * ns + i] = s;
+}
+
+// Bt (m x k col-major) = A^T Q, Q (ns x k col-major): one thread per column j of A
+__global__ void __launch_bounds__(256) skinny_at_kernel(
+    const double* __restrict__ A, int ns, long long m, const double* __restrict__ Q, int k,
+    double* __restrict__ Bt) {
+  extern __shared__ double qs[];               // ns x k, row-major
+  for (int t = threadIdx.x; t < ns * k; t += blockDim.x) {
+    const int i = t / k, c = t - (t / k) * k;
+    qs[t] = Q[(size_t)c * ns + i];
+  }
+  __syncthreads();
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double acc[SKINNY_K];
+#pragma unroll
+  for (int c = 0; c < SKINNY_K; ++c) acc[c] = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    const double a = A[(size_t)i * m + j];
+#pragma unroll
+    for (int c = 0; c < SKINNY_K; ++c)
+      if (c < k) acc[c] = fma(a, qs[i * k + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < SKINNY_K; ++c)
+    if (c < k) Bt[(size_t)c * m + j] = acc[c];
+}
+
+// partial Gram matrices of Bt (m x k col-major): P[blk] (k x k), rows split
+// over the CTAs and threads; the reduce kernel above sums them
+__global__ void __launch_bounds__(256) skinny_gram_kernel(const double* __restrict__ Bt,
+                                                          long long m, int k,
+                                                          double* __restrict__ P) {
+  __shared__ double part[8][SKINNY_K * SKINNY_K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double g[SKINNY_K];
+  // thread (w, lane) accumulates column c0 = lane % k of the Gram for rows in its stride
+  for (int c0 = 0; c0 < k; ++c0) {
+#pragma unroll
+    for (int c = 0; c < SKINNY_K; ++c) g[c] = 0.0;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (long long)gridDim.x * blockDim.x) {
+      const double b0 = Bt[(size_t)c0 * m + j];
+#pragma unroll
+      for (int c = 0; c < SKINNY_K; ++c)
+        if (c < k) g[c] = fma(b0, Bt[(size_t)c * m + j], g[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < SKINNY_K; ++c) {
+      if (c >= k) break;
+      double v = g[c];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) part[w][c0 * k + c] = v;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += part[q][t];
+    P[(size_t)blockIdx.x * k * k + t] = s;
+  }
+}
+
+// Y (ns x k) = A Om for A = X^T, X col-major (m x ns)
+static void skinny_sketch(iga_ctx* ctx, const double* X, int ns, int m, const double* Om, int k,
+                          double* Y) {
+  const int nb = (int)(((long long)m + SKINNY_C - 1) / SKINNY_C);
+  double* P = scratch<double>(ctx, SLOT_TTSVD_PART, (size_t)nb * ns * k);
+  // algorithmic: 2 ns m k flop, A read once
+  prof_count(ctx, 8.0 * ns * (double)m, 2.0 * ns * (double)m * k);
+  IGA_LAUNCH(ctx, skinny_sketch_kernel, dim3(nb, (ns + SKINNY_R - 1) / SKINNY_R), 256, 0, X, ns,
+             (long long)m, Om, k, P);
+  IGA_LAUNCH(ctx, skinny_reduce_kernel, (ns * k + 255) / 256, 256, 0, P, nb, ns, k, Y);
+}
+
+// Bt (m x k) = A^T Q for A = X^T, X col-major (m x ns)
+static void skinny_at(iga_ctx* ctx, const double* X, int ns, int m, const double* Q, int k,
+                      double* Bt) {
+  const size_t smem = (size_t)ns * k * sizeof(double);
+  IGA_REQUIRE(smem <= 48 * 1024, "skinny_at: basis too large");
+  prof_count(ctx, 8.0 * ns * (double)m, 2.0 * ns * (double)m * k);
+  IGA_LAUNCH(ctx, skinny_at_kernel, (unsigned)((m + 255) / 256), 256, smem, X, ns, (long long)m, Q,
+             k, Bt);
+}
+
+// G (k x k) = Bt^T Bt for Bt col-major (m x k)
+static void skinny_gram(iga_ctx* ctx, const double* Bt, int m, int k, double* G) {
+  const int nb = std::max(1, std::min(152 * 2, (m + 255) / 256));
+  double* P = scratch<double>(ctx, SLOT_TTSVD_PART, (size_t)nb * k * k);
+  IGA_LAUNCH(ctx, skinny_gram_kernel, nb, 256, 0, Bt, (long long)m, k, P);
+  IGA_LAUNCH(ctx, skinny_reduce_kernel, (k * k + 255) / 256, 256, 0, P, nb, k, k, G);
+}
+
 // Truncated left singular factor of A (ns x m): A = X^T with X col-major
 // (m x ns) when xT == false, A = Z with Z col-major (ns x m) when xT == true.
 // Returns the rank r, U (ns x r) col-major in Uout, Ct = A^T U (m x r)
@@ -1031,7 +1193,8 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
     const int bt = std::min(b, kcap - kq);
     if (bt <= 0) { est2 = 0.0; break; }
     fill_gaussian(ctx, Om, (size_t)m * bt, seed + 7919u * (uint64_t)(blk + 1));
-    if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, bt, m, X, m, Om, m, Y, ns);
+    if (!xT && bt <= SKINNY_K) skinny_sketch(ctx, X, ns, m, Om, bt, Y);
+    else if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, bt, m, X, m, Om, m, Y, ns);
     else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, bt, m, X, ns, Om, m, Y, ns);
     for (int pass = 0; pass < 2 && kq > 0; ++pass) {
       // Y -= Q (Q^T Y)
@@ -1069,14 +1232,18 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
   double* V = scratch<double>(ctx, SLOT_TTSVD_V, (size_t)k * k * 3);
   double* V1 = V + (size_t)k * k;
   double* V2 = V1 + (size_t)k * k;
-  if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, ns, X, m, Q, ns, Bt, m);
+  const bool narrow = k <= SKINNY_K && (size_t)ns * k * sizeof(double) <= 48 * 1024;
+  if (!xT && narrow) skinny_at(ctx, X, ns, m, Q, k, Bt);
+  else if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, ns, X, m, Q, ns, Bt, m);
   else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, m, k, ns, X, ns, Q, ns, Bt, m);
   // first Gram pass
-  gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt, m, Bt, m, G, k);
+  if (k <= SKINNY_K) skinny_gram(ctx, Bt, m, k, G);
+  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt, m, Bt, m, G, k);
   jacobi_eig(ctx, G, V1, wv, k);
   // second pass on the rotated factor: nearly diagonal Gram matrix
   gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
-  gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
+  if (k <= SKINNY_K) skinny_gram(ctx, Bt2, m, k, G);
+  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
   jacobi_eig(ctx, G, V2, wv, k);
   gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, V1, k, V2, k, V, k);
   std::vector<double> lam(k);
