@@ -502,6 +502,88 @@ static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K,
                                      A, lda, sA, &beta, C, ldc, sC, count));
 }
 
+// ---- projections of full vectors onto the TT frames (long reductions)
+//
+// rowdot: C_b (M x N) = A_b B^T, A_b row-major (M x K) at A + b sA, B
+// row-major (N x K); block (i, column group of 16, b), threads stride over k
+// with 16 accumulators; tout stores C_b^T instead.
+// coldot: C_b (M x N) = A^T B_b, A row-major (K x M), B_b row-major (K x N);
+// block (chunk of 64 k, row group of 16, b), threads over j, partial sums
+// per chunk, then a reduction over the chunks.
+constexpr int PROJ_G = 16;
+constexpr int PROJ_KC = 64;
+
+__global__ void __launch_bounds__(256) rowdot_kernel(const double* __restrict__ A, int lda,
+                                                     long long sA, const double* __restrict__ B,
+                                                     int ldb, int K, int N, double* __restrict__ C,
+                                                     int ldc, long long sC, int tout) {
+  __shared__ double red[8][PROJ_G];
+  const int i = blockIdx.x, c0 = blockIdx.y * PROJ_G, b = blockIdx.z;
+  const int nc = min(PROJ_G, N - c0);
+  const double* a = A + b * sA + (size_t)i * lda;
+  double acc[PROJ_G];
+#pragma unroll
+  for (int c = 0; c < PROJ_G; ++c) acc[c] = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double av = a[k];
+#pragma unroll
+    for (int c = 0; c < PROJ_G; ++c)
+      if (c < nc) acc[c] = fma(av, B[(size_t)(c0 + c) * ldb + k], acc[c]);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < PROJ_G; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nc) {
+    double v = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
+    const int c = c0 + threadIdx.x;
+    C[b * sC + (tout ? (size_t)c * ldc + i : (size_t)i * ldc + c)] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) coldot_kernel(const double* __restrict__ A, int lda,
+                                                     const double* __restrict__ B, int ldb,
+                                                     long long sB, int K, int M, int N,
+                                                     double* __restrict__ P) {
+  // P[(chunk * nb + b) * M * N + i * N + j]
+  const int chunk = blockIdx.x, i0 = blockIdx.y * PROJ_G, b = blockIdx.z;
+  const int nchunk = gridDim.x, nb = gridDim.z;
+  const int mi = min(PROJ_G, M - i0);
+  const int k0 = chunk * PROJ_KC, k1 = min(K, k0 + PROJ_KC);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double acc[PROJ_G];
+#pragma unroll
+    for (int c = 0; c < PROJ_G; ++c) acc[c] = 0.0;
+    for (int k = k0; k < k1; ++k) {
+      const double bv = B[b * sB + (size_t)k * ldb + j];
+#pragma unroll
+      for (int c = 0; c < PROJ_G; ++c)
+        if (c < mi) acc[c] = fma(A[(size_t)k * lda + i0 + c], bv, acc[c]);
+    }
+    for (int c = 0; c < mi; ++c)
+      P[((size_t)chunk * nb + b) * M * N + (size_t)(i0 + c) * N + j] = acc[c];
+  }
+  (void)nchunk;
+}
+
+__global__ void coldot_reduce_kernel(const double* __restrict__ P, int nchunk, int nb, int M,
+                                     int N, double* __restrict__ C, int ldc, long long sC) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per = (size_t)M * N;
+  if (t >= per * nb) return;
+  const int b = (int)(t / per);
+  const size_t e = t - (size_t)b * per;
+  double v = 0.0;
+  for (int c = 0; c < nchunk; ++c) v += P[((size_t)c * nb + b) * per + e];
+  const int i = (int)(e / N), j = (int)(e - (size_t)i * N);
+  C[b * sC + (size_t)i * ldc + j] = v;
+}
+
 // nonzero pattern of one TT-matrix core of an operator
 struct CoreNZ {
   int R0 = 1, R1 = 1;
@@ -611,8 +693,15 @@ struct Solver {
     IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R1 * per), 256, 0, op[o]->band64[d].p,
                c.colptr.p, c.colsrc.p, c.coloff.p, u, c.R1, r0, nn, r1, op[o]->p[d], w);
     PhiL[o][d + 1].ensure((size_t)c.R1 * r1 * r1);
-    rm_gemm_batched(ctx, true, false, r1, r1, r0 * nn, X[d].p, r1, 0, w, r1, (long long)per,
-                    PhiL[o][d + 1].p, r1, (long long)r1 * r1, c.R1);
+    // PhiL[be] (r1 x r1) = X^T w[be], a reduction over r0 n
+    {
+      const int Kd = r0 * nn, nch = (Kd + PROJ_KC - 1) / PROJ_KC;
+      double* P = slot(35, (size_t)nch * c.R1 * r1 * r1);
+      IGA_LAUNCH(ctx, coldot_kernel, dim3(nch, (r1 + PROJ_G - 1) / PROJ_G, c.R1), 64, 0, X[d].p,
+                 r1, w, r1, (long long)per, Kd, r1, r1, P);
+      IGA_LAUNCH(ctx, coldot_reduce_kernel, nblk((size_t)c.R1 * r1 * r1), 256, 0, P, nch, c.R1,
+                 r1, r1, PhiL[o][d + 1].p, r1, (long long)r1 * r1);
+    }
   }
 
   void right_update(int o, int d) {         // PhiR[o][d-1] from PhiR[o][d] and X[d]
@@ -626,8 +715,10 @@ struct Solver {
     IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R0 * per), 256, 0, op[o]->band64[d].p,
                c.rowptr.p, c.rowsrc.p, c.rowoff.p, u, c.R0, r0, nn, r1, op[o]->p[d], w);
     PhiR[o][d - 1].ensure((size_t)c.R0 * r0 * r0);
-    rm_gemm_batched(ctx, false, true, r0, r0, nn * r1, X[d].p, nn * r1, 0, w, nn * r1,
-                    (long long)per, PhiR[o][d - 1].p, r0, (long long)r0 * r0, c.R0);
+    // PhiR[al] (r0 x r0) = X w[al]^T, a reduction over n r1 (rowdot gives its transpose)
+    IGA_LAUNCH(ctx, rowdot_kernel, dim3(r0, (r0 + PROJ_G - 1) / PROJ_G, c.R0), 256, 0, w, nn * r1,
+               (long long)per, X[d].p, nn * r1, nn * r1, r0, PhiR[o][d - 1].p, r0,
+               (long long)r0 * r0, 1);
   }
 
   void set_ones(DevBuf<double>& b) {
@@ -654,8 +745,10 @@ struct Solver {
     if (d == 0) {
       double* Xr = slot(2, (size_t)r[1] * n2 * n3);
       right_frame(Xr);
-      rm_gemm_batched(ctx, false, true, n1, r[1], n2 * n3, F, n2 * n3, (long long)N, Xr, n2 * n3,
-                      0, rhs, r[1], (long long)loc, 3);
+      // rhs_l (n1 x r1) = F_l Xr^T, K = n2 n3
+      prof_count(ctx, 8.0 * (3.0 * N + (double)r[1] * n2 * n3), 6.0 * N * r[1]);
+      IGA_LAUNCH(ctx, rowdot_kernel, dim3(n1, (r[1] + PROJ_G - 1) / PROJ_G, 3), 256, 0, F, n2 * n3,
+                 (long long)N, Xr, n2 * n3, n2 * n3, r[1], rhs, r[1], (long long)loc, 0);
     } else if (d == 1) {
       double* s = slot(2, (size_t)3 * n1 * n2 * r[2]);       // one slab per field
       {
@@ -668,8 +761,14 @@ struct Solver {
     } else {
       double* Xl = slot(2, (size_t)n1 * n2 * r[2]);
       left_frame(Xl);
-      rm_gemm_batched(ctx, true, false, r[2], n3, n1 * n2, Xl, r[2], 0, F, n3, (long long)N, rhs,
-                      n3, (long long)loc, 3);
+      // rhs_l (r2 x n3) = Xl^T F_l, K = n1 n2
+      const int Kd = n1 * n2, nch = (Kd + PROJ_KC - 1) / PROJ_KC;
+      double* P = slot(34, (size_t)nch * 3 * r[2] * n3);
+      prof_count(ctx, 8.0 * (3.0 * N + (double)Kd * r[2]), 6.0 * N * r[2]);
+      IGA_LAUNCH(ctx, coldot_kernel, dim3(nch, (r[2] + PROJ_G - 1) / PROJ_G, 3), 128, 0, Xl, r[2],
+                 F, n3, (long long)N, Kd, r[2], n3, P);
+      IGA_LAUNCH(ctx, coldot_reduce_kernel, nblk((size_t)3 * r[2] * n3), 256, 0, P, nch, 3, r[2],
+                 n3, rhs, n3, (long long)loc);
     }
   }
 

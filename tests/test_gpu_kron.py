@@ -27,8 +27,12 @@ def _ops(env, name, p, E, tol=1e-12):
     return iga.iga_lowrank_assemble(ctx, geo, space, wl.Target(wl.TARGET_SINPROD), tol)
 
 
+# n = E + p - 2 unknowns per direction; n = 33 (three 11 x 11 tiles per
+# direction) and n = 31 (a 16-wide tile and a ragged 15-wide one) span several
+# (i1, i2) tiles
 @pytest.mark.parametrize("name,p,E", [("cube", 2, 16), ("annulus", 3, 9), ("twisted", 1, 13),
-                                      ("random", 2, 5), ("annulus", 4, 7)])
+                                      ("random", 2, 5), ("annulus", 4, 7), ("cube", 2, 33),
+                                      ("annulus", 3, 30)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_kron_apply(env, name, p, E, prec):
     ctx, torch, iga = env
