@@ -220,18 +220,21 @@ __global__ void symmetrize_kernel(double* __restrict__ A, int r) {
 // diag entries d[s](a) = sum_{x,y} V(x,a) P[s](x,y) V(y,a)   (V col-major r x r)
 __global__ void diag_sandwich_kernel(const double* __restrict__ P, const double* __restrict__ V,
                                      int S, int r, double* __restrict__ d) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per (s, a): d = v_a^T P_s v_a, lanes over the rows x of P_s
+  const int lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (idx >= S * r) return;
-  int s = idx / r, a = idx % r;
+  const int s = idx / r, a = idx % r;
   const double* Ps = P + (size_t)s * r * r;
   const double* va = V + (size_t)a * r;
   double acc = 0.0;
-  for (int x = 0; x < r; ++x) {
+  for (int x = lane; x < r; x += 32) {
     double t = 0.0;
-    for (int y = 0; y < r; ++y) t += Ps[(size_t)x * r + y] * va[y];
-    acc += va[x] * t;
+    for (int y = 0; y < r; ++y) t = fma(Ps[(size_t)x * r + y], va[y], t);
+    acc = fma(va[x], t, acc);
   }
-  d[idx] = acc;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) d[idx] = acc;
 }
 
 template <typename T>
@@ -306,6 +309,10 @@ __global__ void scale_rsqrt_kernel(T* __restrict__ x, const double* __restrict__
 // lanes.  The factor is built in shared memory when it fits and written to
 // global memory as [block][row][w].
 
+// largest lower bandwidth + 1 of the node-interleaved KKT blocks the LU
+// kernel handles (kl = 3 p + 2: degrees up to 4)
+constexpr int KKT_MAXKL = 16;
+
 struct BandLayout {
   int n, p, kl, ku, W, N, NB, r0, r1;
 };
@@ -336,20 +343,38 @@ __global__ void kkt_block_factor_kernel(
   const int n = L.n, p = L.p, B = 2 * p + 1;
   for (size_t e = lane; e < per; e += 32) A[e] = T(0);
   __syncwarp();
-  // assemble the block: every (i, o) writes six distinct entries
-  for (int e = lane; e < n * B; e += 32) {
-    int i = e / B, o = e - i * B;
-    int j = i + o - p;
-    if (j < 0 || j >= n) continue;
+  // assemble the block: every (i, o) writes six distinct entries.  The
+  // interface products s_z = dL(z, a) dR(z, b) are computed once per lane
+  // (lane z) and broadcast by shuffles.
+  const int nzt = nnzM + nnzK;
+  for (int e0 = 0; e0 < n * B; e0 += 32) {
+    const int e = e0 + lane;
+    const bool ok = e < n * B;
+    const int i = ok ? e / B : 0, o = ok ? e - i * B : 0;
+    const int j = i + o - p;
+    const bool in = ok && j >= 0 && j < n;
     T m = T(0), k = T(0), kt = T(0);
-    for (int z = 0; z < nnzM; ++z)
-      m += dLM[(size_t)nzM_l[z] * L.r0 + a] * dRM[(size_t)nzM_r[z] * L.r1 + b] *
-           bandM[nzM_off[z] + (size_t)i * B + o];
-    for (int z = 0; z < nnzK; ++z) {
-      T s = dLK[(size_t)nzK_l[z] * L.r0 + a] * dRK[(size_t)nzK_r[z] * L.r1 + b];
-      k += s * bandK[nzK_off[z] + (size_t)i * B + o];
-      kt += s * bandK[nzK_off[z] + (size_t)j * B + (i - j + p)];    // K^T(i,j) = K(j,i)
+    for (int z0 = 0; z0 < nzt; z0 += 32) {
+      T sz = T(0);
+      const int z = z0 + lane;
+      if (z < nnzM) sz = dLM[(size_t)nzM_l[z] * L.r0 + a] * dRM[(size_t)nzM_r[z] * L.r1 + b];
+      else if (z < nzt)
+        sz = dLK[(size_t)nzK_l[z - nnzM] * L.r0 + a] * dRK[(size_t)nzK_r[z - nnzM] * L.r1 + b];
+      const int zn = min(32, nzt - z0);
+      for (int q = 0; q < zn; ++q) {
+        const T c = __shfl_sync(0xffffffffu, sz, q);
+        const int zz = z0 + q;
+        if (!in) continue;
+        if (zz < nnzM) {
+          m += c * bandM[nzM_off[zz] + (size_t)i * B + o];
+        } else {
+          const long long off = nzK_off[zz - nnzM];
+          k += c * bandK[off + (size_t)i * B + o];
+          kt += c * bandK[off + (size_t)j * B + (i - j + p)];    // K^T(i,j) = K(j,i)
+        }
+      }
     }
+    if (!in) continue;
     bwin(A, L, 3 * i + 0, 3 * j + 0) = m;
     bwin(A, L, 3 * i + 0, 3 * j + 2) = kt;
     bwin(A, L, 3 * i + 1, 3 * j + 1) = beta * m;
@@ -361,43 +386,72 @@ __global__ void kkt_block_factor_kernel(
   const int N = L.N, kl = L.kl, ku = L.ku;
   int* pv = piv + (size_t)blk * N;
   // right-looking banded LU, one column per step: lanes take the rows of the
-  // pivot search and the columns of the rank-1 update
+  // pivot search and the columns of the rank-1 update.  Element (r, c) of
+  // the band lives at r (W - 1) + kl + c (32-bit offsets within the block).
+  // The update loads a column's multipliers and entries into registers first
+  // (kl < KKT_MAXKL), so the loads issue back to back.
+  const int W1 = L.W - 1;
   for (int k = 0; k < N; ++k) {
     const int last = min(N - 1, k + kl);
     const int cnt = last - k + 1;
     const int jend = min(N - 1, k + kl + ku);
-    T v = T(-1);
-    int idx = k;
-    for (int t = lane; t < cnt; t += 32) {
-      T a = fabs(bwin(A, L, k + t, k));
-      if (a > v) { v = a; idx = k + t; }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      T ov = __shfl_xor_sync(0xffffffffu, v, off);
-      int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-    }
-    const int pr = idx;
-    if (lane == 0) pv[k] = pr;
-    if (pr != k)
-      for (int j = k + lane; j <= jend; j += 32) {
-        T t = bwin(A, L, k, j);
-        bwin(A, L, k, j) = bwin(A, L, pr, j);
-        bwin(A, L, pr, j) = t;
+    const int rk = k * W1 + kl;                   // row k: element (k, c) at rk + c
+    int pr;
+    if constexpr (sizeof(T) == 4) {
+      // partial pivoting by one warp-wide integer max: the key keeps the top
+      // 24 bits of |a| (a non-negative float orders like its bits) and the
+      // row offset in the low byte, smallest offset first on ties
+      unsigned key = 0u;
+      for (int t = lane; t < cnt; t += 32) {
+        const unsigned kb = (__float_as_uint(fabsf((float)A[rk + t * W1 + k])) & 0xFFFFFF00u) |
+                            (unsigned)(255 - t);
+        key = kb > key ? kb : key;
       }
+      key = __reduce_max_sync(0xffffffffu, key);
+      pr = k + (255 - (int)(key & 0xFFu));
+    } else {
+      T v = T(-1);
+      int idx = k;
+      for (int t = lane; t < cnt; t += 32) {
+        T a = fabs(A[rk + t * W1 + k]);
+        if (a > v) { v = a; idx = k + t; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, v, off);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      }
+      pr = idx;
+    }
+    if (lane == 0) pv[k] = pr;
+    if (pr != k) {
+      const int rp = pr * W1 + kl;
+      for (int j = k + lane; j <= jend; j += 32) {
+        T t = A[rk + j];
+        A[rk + j] = A[rp + j];
+        A[rp + j] = t;
+      }
+    }
     __syncwarp();
-    const T d = bwin(A, L, k, k);
+    const T d = A[rk + k];
     if (d == T(0)) {
       if (lane == 0) atomicOr(flag, 2);
       continue;
     }
     const T rd = T(1) / d;
-    for (int t = 1 + lane; t < cnt; t += 32) bwin(A, L, k + t, k) *= rd;
+    for (int t = 1 + lane; t < cnt; t += 32) A[rk + t * W1 + k] *= rd;
     __syncwarp();
+    T lm[KKT_MAXKL];
+#pragma unroll
+    for (int t = 1; t < KKT_MAXKL; ++t) lm[t] = t < cnt ? A[rk + t * W1 + k] : T(0);
     for (int j = k + 1 + lane; j <= jend; j += 32) {
-      const T u = bwin(A, L, k, j);
-#pragma unroll 4
-      for (int t = 1; t < cnt; ++t) bwin(A, L, k + t, j) -= bwin(A, L, k + t, k) * u;
+      const T u = A[rk + j];
+      T xv[KKT_MAXKL];
+#pragma unroll
+      for (int t = 1; t < KKT_MAXKL; ++t) xv[t] = t < cnt ? A[rk + t * W1 + j] : T(0);
+#pragma unroll
+      for (int t = 1; t < KKT_MAXKL; ++t)
+        if (t < cnt) A[rk + t * W1 + j] = xv[t] - lm[t] * u;
     }
     __syncwarp();
   }
@@ -442,6 +496,8 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
   int* ps = reinterpret_cast<int*>(s + N);        // pivots of this block
   for (int k = lane; k < N; k += 32) ps[k] = pv[k];
   __syncwarp();
+  // element (r, c) of the band at r (W - 1) + kl + c (32-bit offsets)
+  const int W1 = L.W - 1;
   // forward: L y = P b, one row per step, lanes over the kl rows below
   for (int k = 0; k < N; ++k) {
     const int pr = ps[k];
@@ -449,17 +505,19 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
     __syncwarp();
     const T sk = s[k];
     const int cnt = min(N - 1, k + kl) - k;
-    for (int t = 1 + lane; t <= cnt; t += 32) s[k + t] -= A[(size_t)(k + t) * L.W + (kl - t)] * sk;
+    const int ck = k * W1 + kl + k;               // element (k, k)
+    for (int t = 1 + lane; t <= cnt; t += 32) s[k + t] -= A[ck + t * W1] * sk;
     __syncwarp();
   }
   // backward, column by column: x_k = s_k / U(k, k), then the rows above
   // within the band (kl + ku of them) drop U(k - t, k) x_k
   for (int k = N - 1; k >= 0; --k) {
-    const T d = A[(size_t)k * L.W + kl];
+    const int ck = k * W1 + kl + k;
+    const T d = A[ck];
     const T x = d != T(0) ? s[k] / d : T(0);
     __syncwarp();
     const int cnt = min(k, kl + ku);
-    for (int t = 1 + lane; t <= cnt; t += 32) s[k - t] -= A[(size_t)(k - t) * L.W + (t + kl)] * x;
+    for (int t = 1 + lane; t <= cnt; t += 32) s[k - t] -= A[ck - t * W1] * x;
     if (lane == 0) s[k] = x;
     __syncwarp();
   }
@@ -508,10 +566,10 @@ static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K,
 // row-major (N x K); block (i, column group of 16, b), threads stride over k
 // with 16 accumulators; tout stores C_b^T instead.
 // coldot: C_b (M x N) = A^T B_b, A row-major (K x M), B_b row-major (K x N);
-// block (chunk of 64 k, row group of 16, b), threads over j, partial sums
+// block (chunk of 16 k, row group of 16, b), threads over j, partial sums
 // per chunk, then a reduction over the chunks.
 constexpr int PROJ_G = 16;
-constexpr int PROJ_KC = 64;
+constexpr int PROJ_KC = 16;
 
 __global__ void __launch_bounds__(256) rowdot_kernel(const double* __restrict__ A, int lda,
                                                      long long sA, const double* __restrict__ B,
@@ -559,6 +617,7 @@ __global__ void __launch_bounds__(256) coldot_kernel(const double* __restrict__ 
     double acc[PROJ_G];
 #pragma unroll
     for (int c = 0; c < PROJ_G; ++c) acc[c] = 0.0;
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
       const double bv = B[b * sB + (size_t)k * ldb + j];
 #pragma unroll
@@ -1087,13 +1146,13 @@ struct Solver {
       rm_gemm(ctx, false, false, rr, rr, rr, Ws[cnt], rr, Lis[side], rr, Vs[side], rr);
       ++cnt;
     }
-    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zM.R0 * r0), 256, 0, PhiL[0][c.d].p, Vs[0], zM.R0,
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zM.R0 * r0, 8), 256, 0, PhiL[0][c.d].p, Vs[0], zM.R0,
                r0, dLM);
-    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zK.R0 * r0), 256, 0, PhiL[1][c.d].p, Vs[0], zK.R0,
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zK.R0 * r0, 8), 256, 0, PhiL[1][c.d].p, Vs[0], zK.R0,
                r0, dLK);
-    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zM.R1 * r1), 256, 0, PhiR[0][c.d].p, Vs[1], zM.R1,
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zM.R1 * r1, 8), 256, 0, PhiR[0][c.d].p, Vs[1], zM.R1,
                r1, dRM);
-    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zK.R1 * r1), 256, 0, PhiR[1][c.d].p, Vs[1], zK.R1,
+    IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zK.R1 * r1, 8), 256, 0, PhiR[1][c.d].p, Vs[1], zK.R1,
                r1, dRK);
     VLt.ensure((size_t)r0 * r0);
     VRt.ensure((size_t)r1 * r1);
@@ -1112,6 +1171,7 @@ struct Solver {
     BL.n = c.nn;
     BL.p = op[0]->p[c.d];
     BL.kl = BL.ku = 3 * BL.p + 2;
+    IGA_REQUIRE(BL.kl < KKT_MAXKL, "kkt preconditioner: degree above 4");
     BL.W = 2 * BL.kl + BL.ku + 1;
     BL.N = 3 * c.nn;
     BL.r0 = r0;

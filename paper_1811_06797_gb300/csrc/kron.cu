@@ -33,7 +33,7 @@ struct KronTile {
   int nt2, nt3;     // tiles along 2 and 3
 };
 
-template <typename T, int P>
+template <typename T, int P, int MO>
 __global__ void __launch_bounds__(KRON_THREADS)
 kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __restrict__ x,
                   T* __restrict__ y) {
@@ -54,9 +54,9 @@ kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __re
   const int I1 = t1 * T1, I2 = t2 * T2, I3 = t3 * T3;
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
   const int nout = T1 * T2 * T3;
-  T acc[KRON_MAXOUT];
+  T acc[MO];
 #pragma unroll
-  for (int k = 0; k < KRON_MAXOUT; ++k) acc[k] = T(0);
+  for (int k = 0; k < MO; ++k) acc[k] = T(0);
 
   for (int t = 0; t < terms.nterms; ++t) {
     const T* A1 = terms.b[0][t];
@@ -101,7 +101,7 @@ kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __re
     __syncthreads();
     // mode 1 into the register accumulators
 #pragma unroll
-    for (int m = 0; m < KRON_MAXOUT; ++m) {
+    for (int m = 0; m < MO; ++m) {
       int idx = threadIdx.x + m * KRON_THREADS;
       if (idx < nout) {
         int k = idx % T3;
@@ -116,7 +116,7 @@ kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __re
     __syncthreads();
   }
 #pragma unroll
-  for (int m = 0; m < KRON_MAXOUT; ++m) {
+  for (int m = 0; m < MO; ++m) {
     int idx = threadIdx.x + m * KRON_THREADS;
     if (idx < nout) {
       int k = idx % T3;
@@ -204,9 +204,10 @@ static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T bet
   }
   int nchunks = (g.n3 + maxT3 - 1) / maxT3;
   {
-    // enough CTAs to cover every SM twice, down to i3 tiles of 16
+    // enough CTAs to cover every SM twice, down to i3 tiles of 4 (the i3
+    // halo of mode 3 is read through L1, not recomputed)
     int base = ((g.n1 + g.T1 - 1) / g.T1) * ((g.n2 + g.T2 - 1) / g.T2);
-    int maxchunks = std::max(1, (g.n3 + 15) / 16);
+    int maxchunks = std::max(1, g.n3 / 4);
     while (base * nchunks < 2 * 152 && nchunks < maxchunks) ++nchunks;
   }
   g.T3 = (g.n3 + nchunks - 1) / nchunks;
@@ -217,9 +218,14 @@ static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T bet
   size_t H1 = g.T1 + 2 * P, H2 = g.T2 + 2 * P;
   size_t smem = (H1 * H2 * g.T3 + H1 * g.T2 * g.T3 + (size_t)(g.T1 + g.T2 + g.T3) * B) * sizeof(T);
   IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: tile does not fit in shared memory");
+  // register accumulators: 8 outputs per thread when the tile allows, which
+  // leaves registers for more resident CTAs
+  const bool small = (size_t)g.T1 * g.T2 * g.T3 <= 8 * KRON_THREADS;
   static bool attr_set = false;
   if (!attr_set) {
-    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P>,
+    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P, 8>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P, KRON_MAXOUT>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr_set = true;
   }
@@ -238,8 +244,12 @@ static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T bet
       double N = (double)g.n1 * g.n2 * g.n3;
       prof_count(ctx, N * sizeof(T) * (bt != T(0) ? 3.0 : 2.0), 6.0 * (2 * P + 1) * N * cnt);
     }
-    IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P>), (unsigned)(nt1 * g.nt2 * g.nt3), KRON_THREADS, smem,
-               terms, g, alpha, bt, x, y);
+    if (small)
+      IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P, 8>), (unsigned)(nt1 * g.nt2 * g.nt3), KRON_THREADS,
+                 smem, terms, g, alpha, bt, x, y);
+    else
+      IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P, KRON_MAXOUT>), (unsigned)(nt1 * g.nt2 * g.nt3),
+                 KRON_THREADS, smem, terms, g, alpha, bt, x, y);
     if (nterm == 0) break;
   }
 }

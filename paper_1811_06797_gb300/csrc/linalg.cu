@@ -195,6 +195,27 @@ __device__ __forceinline__ double qr_block_sum(double v, double* red) {
   return t;
 }
 
+// out[t] = sum over the C CTAs of the cluster of buf[t] (distributed shared
+// memory), t in [t0, t1): a power-of-two segment of S >= C lanes per column,
+// one remote load per lane, then a segmented shuffle sum.  Every CTA runs the
+// same reduction tree on the same values, so all get identical sums.  Ends
+// with __syncthreads.
+__device__ void cluster_colsum(cgx::cluster_group& cl, int C, double* buf, int t0, int t1,
+                               double* out) {
+  int S = 1;
+  while (S < C) S <<= 1;                        // C <= 16, so S divides 32
+  const int per_warp = 32 / S;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int sub = lane / S, c = lane - (lane / S) * S;
+  for (int base = t0 + w * per_warp; base < t1; base += nw * per_warp) {
+    const int t = base + sub;
+    double v = (c < C && t < t1) ? cl.map_shared_rank(buf, c)[t] : 0.0;
+    for (int o = S >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (c == 0 && t < t1) out[t] = v;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) householder_qr_cluster_kernel(
     const double* __restrict__ Y, double* __restrict__ Q, int m, int k, int mc) {
   cgx::cluster_group cl = cgx::this_cluster();
@@ -257,12 +278,7 @@ __global__ void __launch_bounds__(256) householder_qr_cluster_kernel(
       if (lane == 0) pb[t] = d;
     }
     cl.sync();
-    for (int t = j + 1 + threadIdx.x; t < k; t += blockDim.x) {
-      double w = 0.0;
-      for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
-      wsum[t] = w;
-    }
-    __syncthreads();
+    cluster_colsum(cl, C, pb, j + 1, k, wsum);
     if (tj != 0.0) {
       const int w = k - j - 1;
       for (int e = threadIdx.x; e < w * (nloc - lo); e += blockDim.x) {
@@ -291,12 +307,7 @@ __global__ void __launch_bounds__(256) householder_qr_cluster_kernel(
       if (lane == 0) pb[t] = d;
     }
     cl.sync();
-    for (int t = j + threadIdx.x; t < k; t += blockDim.x) {
-      double w = 0.0;
-      for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
-      wsum[t] = w;
-    }
-    __syncthreads();
+    cluster_colsum(cl, C, pb, j, k, wsum);
     const int w = k - j;
     for (int e = threadIdx.x; e < w * (nloc - lo); e += blockDim.x) {
       int t = j + e / (nloc - lo), i = lo + e % (nloc - lo);
@@ -422,12 +433,7 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
     cl.sync();
     ++par;
     if (tj != 0.0) {
-      for (int t = j + 1 + tid; t < jend; t += blockDim.x) {
-        double w = 0.0;
-        for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
-        nrm[t] = w;                              // reused as the reduced products
-      }
-      __syncthreads();
+      cluster_colsum(cl, C, pb, j + 1, jend, nrm);   // nrm reused for the products
       const int w = jend - j - 1, h = nloc - lo;
       for (int e = tid; e < w * h; e += blockDim.x) {
         const int t = j + 1 + e / h, i = lo + e % h;
@@ -454,12 +460,11 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
     if (me == own)
       for (int t = j + tid; t < ncol; t += blockDim.x) rowj[t] = A[(size_t)t * mc + (j - r0)];
     cl.sync();
+    cluster_colsum(cl, C, part, j, a.c3, nrm);
     double sum = 0.0, mx = -1.0;
     int arg = j;
     for (int t = j + tid; t < a.c3; t += blockDim.x) {
-      double sq = 0.0;
-      for (int c = 0; c < C; ++c) sq += cl.map_shared_rank(part, c)[t];
-      nrm[t] = sq;
+      const double sq = nrm[t];
       sum += sq;
       if (sq > mx) { mx = sq; arg = t; }
     }
@@ -539,12 +544,7 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
       }
       cl.sync();
       ++par;
-      for (int t = j + 1 + tid; t < nr; t += blockDim.x) {
-        double w = 0.0;
-        for (int c = 0; c < C; ++c) w += cl.map_shared_rank(pb, c)[t];
-        nrm[t] = w;
-      }
-      __syncthreads();
+      cluster_colsum(cl, C, pb, j + 1, nr, nrm);
       const int w = nr - j - 1, h = nloc - lo;
       for (int e = tid; e < w * h; e += blockDim.x) {
         const int t = j + 1 + e / h, i = lo + e % h;
