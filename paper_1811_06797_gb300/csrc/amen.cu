@@ -562,9 +562,10 @@ static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K,
 
 // ---- projections of full vectors onto the TT frames (long reductions)
 //
-// rowdot: C_b (M x N) = A_b B^T, A_b row-major (M x K) at A + b sA, B
-// row-major (N x K); block (i, column group of 16, b), threads stride over k
-// with 16 accumulators; tout stores C_b^T instead.
+// rowdot: C_b (M x N) = sum_q A_{b,q} B_q^T, A_{b,q} row-major (M x K) at
+// A + (b nsum + q) sA, B_q row-major (N x K) at B + q sB; block (i, column
+// group of 16, b), threads stride over k with 16 accumulators; tout stores
+// C_b^T instead.
 // coldot: C_b (M x N) = A^T B_b, A row-major (K x M), B_b row-major (K x N);
 // block (chunk of 16 k, row group of 16, b), threads over j, partial sums
 // per chunk, then a reduction over the chunks.
@@ -573,20 +574,24 @@ constexpr int PROJ_KC = 16;
 
 __global__ void __launch_bounds__(256) rowdot_kernel(const double* __restrict__ A, int lda,
                                                      long long sA, const double* __restrict__ B,
-                                                     int ldb, int K, int N, double* __restrict__ C,
-                                                     int ldc, long long sC, int tout) {
+                                                     int ldb, long long sB, int nsum, int K, int N,
+                                                     double* __restrict__ C, int ldc, long long sC,
+                                                     int tout) {
   __shared__ double red[8][PROJ_G];
   const int i = blockIdx.x, c0 = blockIdx.y * PROJ_G, b = blockIdx.z;
   const int nc = min(PROJ_G, N - c0);
-  const double* a = A + b * sA + (size_t)i * lda;
   double acc[PROJ_G];
 #pragma unroll
   for (int c = 0; c < PROJ_G; ++c) acc[c] = 0.0;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const double av = a[k];
+  for (int q = 0; q < nsum; ++q) {
+    const double* a = A + (b * nsum + q) * sA + (size_t)i * lda;
+    const double* Bq = B + q * sB;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const double av = a[k];
 #pragma unroll
-    for (int c = 0; c < PROJ_G; ++c)
-      if (c < nc) acc[c] = fma(av, B[(size_t)(c0 + c) * ldb + k], acc[c]);
+      for (int c = 0; c < PROJ_G; ++c)
+        if (c < nc) acc[c] = fma(av, Bq[(size_t)(c0 + c) * ldb + k], acc[c]);
+    }
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -776,7 +781,7 @@ struct Solver {
     PhiR[o][d - 1].ensure((size_t)c.R0 * r0 * r0);
     // PhiR[al] (r0 x r0) = X w[al]^T, a reduction over n r1 (rowdot gives its transpose)
     IGA_LAUNCH(ctx, rowdot_kernel, dim3(r0, (r0 + PROJ_G - 1) / PROJ_G, c.R0), 256, 0, w, nn * r1,
-               (long long)per, X[d].p, nn * r1, nn * r1, r0, PhiR[o][d - 1].p, r0,
+               (long long)per, X[d].p, nn * r1, 0LL, 1, nn * r1, r0, PhiR[o][d - 1].p, r0,
                (long long)r0 * r0, 1);
   }
 
@@ -807,7 +812,7 @@ struct Solver {
       // rhs_l (n1 x r1) = F_l Xr^T, K = n2 n3
       prof_count(ctx, 8.0 * (3.0 * N + (double)r[1] * n2 * n3), 6.0 * N * r[1]);
       IGA_LAUNCH(ctx, rowdot_kernel, dim3(n1, (r[1] + PROJ_G - 1) / PROJ_G, 3), 256, 0, F, n2 * n3,
-                 (long long)N, Xr, n2 * n3, n2 * n3, r[1], rhs, r[1], (long long)loc, 0);
+                 (long long)N, Xr, n2 * n3, 0LL, 1, n2 * n3, r[1], rhs, r[1], (long long)loc, 0);
     } else if (d == 1) {
       double* s = slot(2, (size_t)3 * n1 * n2 * r[2]);       // one slab per field
       {
@@ -864,11 +869,12 @@ struct Solver {
     int k = kick;
     double* E = slot(3, (size_t)m * k);
     if (forward && d == 0) {
+      // E (n1 x k) = sum_l res_l Om_l^T with Om_l (k x n2 n3) Gaussian; stored
+      // transposed (k x n1)
       double* Om = slot(4, (size_t)3 * n2 * n3 * k);
       fill_gaussian(ctx, Om, (size_t)3 * n2 * n3 * k, seed++);
-      for (int l = 0; l < 3; ++l)
-        rm_gemm(ctx, true, true, k, n1, n2 * n3, Om + (size_t)l * n2 * n3 * k, k, res + l * N,
-                n2 * n3, Et, n1, 1.0, l ? 1.0 : 0.0);
+      IGA_LAUNCH(ctx, rowdot_kernel, dim3(n1, (k + PROJ_G - 1) / PROJ_G, 1), 256, 0, res, n2 * n3,
+                 (long long)N, Om, n2 * n3, (long long)n2 * n3 * k, 3, n2 * n3, k, Et, n1, 0LL, 1);
       return;
     }
     if (forward && d == 1) {

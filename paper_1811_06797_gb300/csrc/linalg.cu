@@ -578,7 +578,9 @@ void qrcp_truncate(iga_ctx* ctx, const double* B, int m, int c3, int si, int sa,
   IGA_REQUIRE(m >= 1 && c3 >= 1 && r >= 1 && c3 <= 3 * r && kick >= 0, "qrcp: bad sizes");
   const size_t limit = 200 * 1024;
   const int cmax = qr_cluster_max(ctx);
-  const int C = std::max(1, std::min(cmax, m / 64));
+  // at least 16 rows per CTA: one SM's FP64 rate (1/64 of FP32) makes even
+  // 65-row slices worth spreading
+  const int C = std::max(1, std::min(cmax, m / 16));
   const int mc = (m + C - 1) / C;
   const int ncol = c3 + kick;
   const size_t head = ((size_t)6 * ncol + 4 + 64) * sizeof(double) + 32 * sizeof(int);
