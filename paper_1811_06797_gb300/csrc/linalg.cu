@@ -405,6 +405,35 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
 
   // one Householder step on column j (alpha = B(j, j), nrm2 = its squared
   // norm over rows >= j), updating columns (j, jend)
+  // dst[t] = sum over this CTA's rows i >= lo of A(i, vc) A(i, t) (vc < 0:
+  // A(i, t)^2), t in [t0, t1).  Short slices take one thread per column
+  // (no shuffles on the critical path), tall ones a warp per column.
+  auto partial_dots = [&](int lo, int vc, int t0, int t1, double* dst) {
+    if (mc <= 96) {
+      for (int t = t0 + tid; t < t1; t += blockDim.x) {
+        const double* col = A + (size_t)t * mc;
+        const double* v = vc >= 0 ? A + (size_t)vc * mc : col;
+        double s0 = 0.0, s1 = 0.0;
+        int i = lo;
+        for (; i + 1 < nloc; i += 2) {
+          s0 = fma(v[i], col[i], s0);
+          s1 = fma(v[i + 1], col[i + 1], s1);
+        }
+        if (i < nloc) s0 = fma(v[i], col[i], s0);
+        dst[t] = s0 + s1;
+      }
+    } else {
+      for (int t = t0 + wid; t < t1; t += nw) {
+        const double* col = A + (size_t)t * mc;
+        const double* v = vc >= 0 ? A + (size_t)vc * mc : col;
+        double d = 0.0;
+        for (int i = lo + lane; i < nloc; i += 32) d = fma(v[i], col[i], d);
+        d = warp_sum(d);
+        if (lane == 0) dst[t] = d;
+      }
+    }
+  };
+
   auto house = [&](int j, double alpha, double nrm2, int jend) {
     const int lo = min(nloc, max(0, j - r0));
     double tj = 0.0, inv = 0.0;
@@ -423,13 +452,7 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
         A[(size_t)j * mc + i] = (r0 + i > j) ? A[(size_t)j * mc + i] * inv : 1.0;
     __syncthreads();
     double* pb = pw + (par & 1) * ncol;
-    for (int t = j + 1 + wid; t < jend; t += nw) {
-      double d = 0.0;
-      if (tj != 0.0)
-        for (int i = lo + lane; i < nloc; i += 32) d += A[(size_t)j * mc + i] * A[(size_t)t * mc + i];
-      d = warp_sum(d);
-      if (lane == 0) pb[t] = d;
-    }
+    if (tj != 0.0) partial_dots(lo, j, j + 1, jend, pb);
     cl.sync();
     ++par;
     if (tj != 0.0) {
@@ -448,15 +471,7 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
   for (; j < npiv; ++j) {
     const int lo = min(nloc, max(0, j - r0));
     const int own = j / mc;
-    for (int t = j + wid; t < a.c3; t += nw) {
-      double sq = 0.0;
-      for (int i = lo + lane; i < nloc; i += 32) {
-        const double v = A[(size_t)t * mc + i];
-        sq += v * v;
-      }
-      sq = warp_sum(sq);
-      if (lane == 0) part[t] = sq;
-    }
+    partial_dots(lo, -1, j, a.c3, part);
     if (me == own)
       for (int t = j + tid; t < ncol; t += blockDim.x) rowj[t] = A[(size_t)t * mc + (j - r0)];
     cl.sync();
@@ -536,12 +551,7 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
     const int lo = min(nloc, max(0, j - r0));
     if (tj != 0.0 && j + 1 < nr) {
       double* pb = pw + (par & 1) * ncol;
-      for (int t = j + 1 + wid; t < nr; t += nw) {
-        double d = 0.0;
-        for (int i = lo + lane; i < nloc; i += 32) d += A[(size_t)j * mc + i] * A[(size_t)t * mc + i];
-        d = warp_sum(d);
-        if (lane == 0) pb[t] = d;
-      }
+      partial_dots(lo, j, j + 1, nr, pb);
       cl.sync();
       ++par;
       cluster_colsum(cl, C, pb, j + 1, nr, nrm);
@@ -731,12 +741,14 @@ struct JacobiTol;
 template <>
 struct JacobiTol<double> {
   static constexpr double off2 = 1e-28, skip = 1e-17, tiny = 1e-300;
+  static constexpr int sweeps = 40;
 };
 template <>
 struct JacobiTol<float> {
   // the FP32 eigenbases only feed a preconditioner: a relative off-diagonal
-  // norm of 1e-4 is plenty
+  // norm of 1e-4 is plenty (fewer sweeps cost more GMRES iterations)
   static constexpr float off2 = 1e-8f, skip = 1e-8f, tiny = 1e-30f;
+  static constexpr int sweeps = 40;
 };
 
 template <typename T>
@@ -779,7 +791,7 @@ __global__ void jacobi_eig_kernel(JacobiBatch batch) {
   double fro2 = 0.0;
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) fro2 += (double)A[t] * (double)A[t];
   fro2 = block_sum(fro2, red);
-  for (int sweep = 0; sweep < 40 && k > 1; ++sweep) {
+  for (int sweep = 0; sweep < JacobiTol<T>::sweeps && k > 1; ++sweep) {
     double off2 = 0.0;
     for (int t = threadIdx.x; t < k * k; t += blockDim.x)
       if ((t % k) != (t / k)) off2 += (double)A[t] * (double)A[t];
