@@ -243,18 +243,19 @@ void weight_tts_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& s
   }
   double* samples = scratch<double>(ctx, SLOT_ASM_SAMPLES, 8 * S);
   sample_weights_impl(ctx, geo, st, target, samples);
+  // the eight Frobenius norms in one pass
+  double nrm[8];
+  device_norms(ctx, samples, S, 8, nrm);
   double qn2 = 0.0;
-  for (int c = 1; c <= 6; ++c) {
-    double v = device_norm2(ctx, samples + c * S, S);
-    qn2 += (c == 2 || c == 3 || c == 5) ? 2 * v * v : v * v;
-  }
+  for (int c = 1; c <= 6; ++c)
+    qn2 += (c == 2 || c == 3 || c == 5) ? 2 * nrm[c] * nrm[c] : nrm[c] * nrm[c];
   double qnorm = std::sqrt(qn2);
   try {
-    tt_svd3(ctx, samples, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[0]);
+    tt_svd3(ctx, samples, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[0], nrm[0]);
     for (int c = 1; c <= 6; ++c)
-      tt_svd3(ctx, samples + c * S, Q[0], Q[1], Q[2], tol, qnorm, 0, &tts[c]);
+      tt_svd3(ctx, samples + c * S, Q[0], Q[1], Q[2], tol, qnorm, 0, &tts[c], nrm[c]);
     if (target && target->kind != IGA_TARGET_ZERO)
-      tt_svd3(ctx, samples + 7 * S, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[7]);
+      tt_svd3(ctx, samples + 7 * S, Q[0], Q[1], Q[2], tol, 0.0, 0, &tts[7], nrm[7]);
   } catch (...) {
     for (int c = 0; c < 8; ++c) { delete tts[c]; tts[c] = nullptr; }
     throw;

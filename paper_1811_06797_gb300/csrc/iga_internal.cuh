@@ -209,8 +209,10 @@ void launch_load_vectors(iga_ctx* ctx, const DirTables& t, const double* w, int 
 
 // linalg.cu
 void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, double norm_ref,
-             int rmax, iga_tt** out);
+             int rmax, iga_tt** out, double norm_w = -1.0);   // norm_w >= 0: ||W||_F known
 double device_norm2(iga_ctx* ctx, const double* x, size_t n);   // synchronises
+// Frobenius norms of `count` consecutive tensors of n elements (host array)
+void device_norms(iga_ctx* ctx, const double* x, size_t n, int count, double* norms);
 void jacobi_eig(iga_ctx* ctx, double* A, double* V, double* w, int k);  // device, col-major
 // fp32: run the rotations in FP32 (shared memory; falls back to FP64 when the
 // problem does not fit), for eigenbases that only feed a preconditioner

@@ -69,6 +69,31 @@ double device_norm2(iga_ctx* ctx, const double* x, size_t n) {
   return std::sqrt(h);
 }
 
+// sums of squares of `count` tensors of n elements each (x + t n), one launch
+__global__ void sumsq_multi_kernel(const double* __restrict__ x, size_t n,
+                                   double* __restrict__ out) {
+  __shared__ double red[32];
+  const double* xt = x + (size_t)blockIdx.y * n;
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    acc = fma(xt[i], xt[i], acc);
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(out + blockIdx.y, acc);
+}
+
+void device_norms(iga_ctx* ctx, const double* x, size_t n, int count, double* norms) {
+  double* acc = scratch<double>(ctx, SLOT_TTSVD_NORM, (size_t)count);
+  IGA_CUDA(cudaMemsetAsync(acc, 0, (size_t)count * 8, ctx->stream));
+  if (n > 0) {
+    int blocks = (int)std::min<size_t>((n + 255) / 256, (152 * 8 + count - 1) / count);
+    IGA_LAUNCH(ctx, sumsq_multi_kernel, dim3(blocks, count), 256, 0, x, n, acc);
+  }
+  IGA_CUDA(cudaMemcpyAsync(norms, acc, (size_t)count * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int t = 0; t < count; ++t) norms[t] = std::sqrt(norms[t]);
+}
+
 // counter-based Gaussian numbers: splitmix64 hash -> two uniforms -> Box-Muller
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   z += 0x9e3779b97f4a7c15ull;
@@ -1032,25 +1057,26 @@ constexpr int SKINNY_C = 2016;      // columns of A per CTA in the sketch (21 ti
 // over the tile columns j = q, q + 8, ... in registers; A and Om tiles are
 // staged in shared memory with coalesced loads, and the eight partial sums
 // of a row (eight neighbouring lanes) meet by shuffles.
+template <int KK>
 __global__ void __launch_bounds__(256) skinny_sketch_kernel(
     const double* __restrict__ A, int ns, long long m, const double* __restrict__ Om, int k,
     double* __restrict__ P) {
   __shared__ double As[SKINNY_R][SKINNY_T + 1];
-  __shared__ double Os[SKINNY_T][SKINNY_K];
+  __shared__ double Os[SKINNY_T][KK];
   const int i0 = blockIdx.y * SKINNY_R;
   const long long c0 = (long long)blockIdx.x * SKINNY_C;
   const long long cend = c0 + SKINNY_C < m ? c0 + SKINNY_C : m;
   const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
-  double acc[SKINNY_K];
+  double acc[KK];
 #pragma unroll
-  for (int c = 0; c < SKINNY_K; ++c) acc[c] = 0.0;
+  for (int c = 0; c < KK; ++c) acc[c] = 0.0;
   for (long long j0 = c0; j0 < cend; j0 += SKINNY_T) {
     for (int t = threadIdx.x; t < SKINNY_R * SKINNY_T; t += blockDim.x) {
       const int rr = t / SKINNY_T, jj = t - rr * SKINNY_T;
       const long long j = j0 + jj;
       As[rr][jj] = (i0 + rr < ns && j < cend) ? A[(size_t)(i0 + rr) * m + j] : 0.0;
     }
-    for (int t = threadIdx.x; t < SKINNY_T * SKINNY_K; t += blockDim.x) {
+    for (int t = threadIdx.x; t < SKINNY_T * KK; t += blockDim.x) {
       const int c = t / SKINNY_T, jj = t - c * SKINNY_T;
       const long long j = j0 + jj;
       Os[jj][c] = (c < k && j < cend) ? Om[(size_t)c * m + j] : 0.0;
@@ -1060,13 +1086,13 @@ __global__ void __launch_bounds__(256) skinny_sketch_kernel(
     for (int jj = q; jj < SKINNY_T; jj += 8) {
       const double a = As[r][jj];
 #pragma unroll
-      for (int c = 0; c < SKINNY_K; ++c)
+      for (int c = 0; c < KK; ++c)
         if (c < k) acc[c] = fma(a, Os[jj][c], acc[c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int c = 0; c < SKINNY_K; ++c) {
+  for (int c = 0; c < KK; ++c) {
     double v = acc[c];
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     v += __shfl_xor_sync(0xffffffffu, v, 2);
@@ -1087,6 +1113,7 @@ __global__ void skinny_reduce_kernel(const double* __restrict__ P, int nblk, int
 }
 
 // Bt (m x k col-major) = A^T Q, Q (ns x k col-major): one thread per column j of A
+template <int KK>
 __global__ void __launch_bounds__(256) skinny_at_kernel(
     const double* __restrict__ A, int ns, long long m, const double* __restrict__ Q, int k,
     double* __restrict__ Bt) {
@@ -1098,17 +1125,17 @@ __global__ void __launch_bounds__(256) skinny_at_kernel(
   __syncthreads();
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  double acc[SKINNY_K];
+  double acc[KK];
 #pragma unroll
-  for (int c = 0; c < SKINNY_K; ++c) acc[c] = 0.0;
+  for (int c = 0; c < KK; ++c) acc[c] = 0.0;
   for (int i = 0; i < ns; ++i) {
     const double a = A[(size_t)i * m + j];
 #pragma unroll
-    for (int c = 0; c < SKINNY_K; ++c)
+    for (int c = 0; c < KK; ++c)
       if (c < k) acc[c] = fma(a, qs[i * k + c], acc[c]);
   }
 #pragma unroll
-  for (int c = 0; c < SKINNY_K; ++c)
+  for (int c = 0; c < KK; ++c)
     if (c < k) Bt[(size_t)c * m + j] = acc[c];
 }
 
@@ -1147,6 +1174,52 @@ __global__ void __launch_bounds__(256) skinny_gram_kernel(const double* __restri
   }
 }
 
+// T (kq x bt, col-major) = Q^T Y for Q (ns x kq), Y (ns x bt) col-major: one
+// warp per entry
+__global__ void qt_y_kernel(const double* __restrict__ Q, const double* __restrict__ Y, int ns,
+                            int kq, int bt, double* __restrict__ T) {
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= kq * bt) return;
+  const int a = e % kq, c = e / kq;
+  double d = 0.0;
+  for (int i = lane; i < ns; i += 32) d = fma(Q[(size_t)a * ns + i], Y[(size_t)c * ns + i], d);
+  d = warp_sum(d);
+  if (lane == 0) T[e] = d;
+}
+
+// Y -= Q T (Y ns x bt, Q ns x kq, T kq x bt; col-major): one thread per entry
+__global__ void y_minus_qt_kernel(double* __restrict__ Y, const double* __restrict__ Q,
+                                  const double* __restrict__ T, int ns, int kq, int bt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ns * bt) return;
+  const int i = e % ns, c = e / ns;
+  double s = Y[e];
+  for (int a = 0; a < kq; ++a) s = fma(-Q[(size_t)a * ns + i], T[(size_t)c * kq + a], s);
+  Y[e] = s;
+}
+
+// C (m x r, col-major) = B (m x k, col-major) V(:, 0:r) with V (k x k col-major),
+// k <= SKINNY_K: one thread per row of B
+__global__ void rows_small_kernel(const double* __restrict__ B, long long m, int k,
+                                  const double* __restrict__ V, int r, double* __restrict__ C) {
+  __shared__ double vs[SKINNY_K * SKINNY_K];
+  for (int t = threadIdx.x; t < k * r; t += blockDim.x) vs[t] = V[t];
+  __syncthreads();
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double b[SKINNY_K];
+#pragma unroll
+  for (int a = 0; a < SKINNY_K; ++a) b[a] = a < k ? B[(size_t)a * m + j] : 0.0;
+  for (int c = 0; c < r; ++c) {
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < SKINNY_K; ++a)
+      if (a < k) s = fma(b[a], vs[c * k + a], s);
+    C[(size_t)c * m + j] = s;
+  }
+}
+
 // Y (ns x k) = A Om for A = X^T, X col-major (m x ns)
 static void skinny_sketch(iga_ctx* ctx, const double* X, int ns, int m, const double* Om, int k,
                           double* Y) {
@@ -1154,8 +1227,11 @@ static void skinny_sketch(iga_ctx* ctx, const double* X, int ns, int m, const do
   double* P = scratch<double>(ctx, SLOT_TTSVD_PART, (size_t)nb * ns * k);
   // algorithmic: 2 ns m k flop, A read once
   prof_count(ctx, 8.0 * ns * (double)m, 2.0 * ns * (double)m * k);
-  IGA_LAUNCH(ctx, skinny_sketch_kernel, dim3(nb, (ns + SKINNY_R - 1) / SKINNY_R), 256, 0, X, ns,
-             (long long)m, Om, k, P);
+  const dim3 grid(nb, (ns + SKINNY_R - 1) / SKINNY_R);
+  if (k <= 8)
+    IGA_LAUNCH(ctx, skinny_sketch_kernel<8>, grid, 256, 0, X, ns, (long long)m, Om, k, P);
+  else
+    IGA_LAUNCH(ctx, skinny_sketch_kernel<SKINNY_K>, grid, 256, 0, X, ns, (long long)m, Om, k, P);
   IGA_LAUNCH(ctx, skinny_reduce_kernel, (ns * k + 255) / 256, 256, 0, P, nb, ns, k, Y);
 }
 
@@ -1165,8 +1241,12 @@ static void skinny_at(iga_ctx* ctx, const double* X, int ns, int m, const double
   const size_t smem = (size_t)ns * k * sizeof(double);
   IGA_REQUIRE(smem <= 48 * 1024, "skinny_at: basis too large");
   prof_count(ctx, 8.0 * ns * (double)m, 2.0 * ns * (double)m * k);
-  IGA_LAUNCH(ctx, skinny_at_kernel, (unsigned)((m + 255) / 256), 256, smem, X, ns, (long long)m, Q,
-             k, Bt);
+  if (k <= 8)
+    IGA_LAUNCH(ctx, skinny_at_kernel<8>, (unsigned)((m + 255) / 256), 256, smem, X, ns,
+               (long long)m, Q, k, Bt);
+  else
+    IGA_LAUNCH(ctx, skinny_at_kernel<SKINNY_K>, (unsigned)((m + 255) / 256), 256, smem, X, ns,
+               (long long)m, Q, k, Bt);
 }
 
 // G (k x k) = Bt^T Bt for Bt col-major (m x k)
@@ -1199,7 +1279,6 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
   double* Y = scratch<double>(ctx, SLOT_TTSVD_Y, (size_t)ns * std::min(kcap, 128));
   double* Yq = scratch<double>(ctx, SLOT_TTSVD_Y2, (size_t)ns * kcap);
   double* T = scratch<double>(ctx, SLOT_TTSVD_C, (size_t)kcap * std::min(kcap, 128));
-  const double one = 1.0, mone = -1.0, zero = 0.0;
   int kq = 0;
   int b = std::min(ns, 8);
   double est2 = 0.0;                           // squared residual estimate
@@ -1212,10 +1291,9 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
     else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, bt, m, X, ns, Om, m, Y, ns);
     for (int pass = 0; pass < 2 && kq > 0; ++pass) {
       // Y -= Q (Q^T Y)
-      IGA_BLAS(cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, kq, bt, ns, &one, Q, ns, Y, ns,
-                           &zero, T, kq));
-      IGA_BLAS(cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, ns, bt, kq, &mone, Q, ns, T, kq,
-                           &one, Y, ns));
+      IGA_LAUNCH(ctx, qt_y_kernel, (unsigned)((kq * bt + 7) / 8), 256, 0, Q, Y, ns, kq, bt, T);
+      IGA_LAUNCH(ctx, y_minus_qt_kernel, (unsigned)((ns * bt + 255) / 256), 256, 0, Y, Q, T, ns,
+                 kq, bt);
     }
     const double yn = device_norm2(ctx, Y, (size_t)ns * bt);
     est2 = yn * yn / bt;
@@ -1255,7 +1333,11 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
   else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt, m, Bt, m, G, k);
   jacobi_eig(ctx, G, V1, wv, k);
   // second pass on the rotated factor: nearly diagonal Gram matrix
-  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
+  if (k <= SKINNY_K)
+    IGA_LAUNCH(ctx, rows_small_kernel, (unsigned)((m + 255) / 256), 256, 0, Bt, (long long)m, k,
+               V1, k, Bt2);
+  else
+    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
   if (k <= SKINNY_K) skinny_gram(ctx, Bt2, m, k, G);
   else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
   jacobi_eig(ctx, G, V2, wv, k);
@@ -1275,7 +1357,11 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
   gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, r, k, Q, ns, V, k, Uout.p, ns);
   // Ct = A^T U = Bt V_r
   Ctout.alloc((size_t)m * r);
-  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, r, k, Bt, m, V, k, Ctout.p, m);
+  if (k <= SKINNY_K)
+    IGA_LAUNCH(ctx, rows_small_kernel, (unsigned)((m + 255) / 256), 256, 0, Bt, (long long)m, k,
+               V, r, Ctout.p);
+  else
+    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, r, k, Bt, m, V, k, Ctout.p, m);
   return r;
 }
 
@@ -1326,7 +1412,8 @@ __global__ void fibres_kernel(const double* __restrict__ W, int n1, int n2, int 
 
 __global__ void rank1_residual_kernel(const double* __restrict__ W, int n1, int n2, int n3,
                                       const double* __restrict__ f, double* __restrict__ out) {
-  // one (i, j) fibre per block iteration, threads along k: e = W - (a_i b_j / v^2) c_k
+  // (i, j) fibres per block iteration (four in flight), threads along k:
+  // e = W - (a_i b_j / v^2) c_k
   __shared__ double red[32];
   const double* a = f;
   const double* b = f + n1;
@@ -1334,17 +1421,33 @@ __global__ void rank1_residual_kernel(const double* __restrict__ W, int n1, int 
   const double v = f[n1 + n2 + n3];
   const double iv2 = 1.0 / (v * v);
   const long long rows = (long long)n1 * n2;
-  double acc = 0.0;
-  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int i = (int)(row / n2), j = (int)(row - (long long)i * n2);
-    const double ab = a[i] * b[j] * iv2;
-    const double* w = W + (size_t)row * n3;
+  const long long G = gridDim.x;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (long long row = blockIdx.x; row < rows; row += 4 * G) {
+    double ab[4];
+    const double* w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long rq = row + q * G;
+      const long long rr = rq < rows ? rq : row;
+      const int i = (int)(rr / n2), j = (int)(rr - (long long)i * n2);
+      ab[q] = rq < rows ? a[i] * b[j] * iv2 : 0.0;
+      w[q] = W + (size_t)rr * n3;
+    }
     for (int k = threadIdx.x; k < n3; k += blockDim.x) {
-      double e = fma(-ab, c[k], w[k]);
-      acc = fma(e, e, acc);
+      const double ck = c[k];
+      double x[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] = w[q][k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (row + q * G >= rows) continue;        // (a valid row stands in; skipped)
+        const double e = fma(-ab[q], ck, x[q]);
+        if (q & 1) acc1 = fma(e, e, acc1); else acc0 = fma(e, e, acc0);
+      }
     }
   }
-  acc = block_sum(acc, red);
+  double acc = block_sum(acc0 + acc1, red);
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 
@@ -1395,14 +1498,14 @@ static iga_tt* rank1_cross(iga_ctx* ctx, const double* W, int n1, int n2, int n3
 }
 
 void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, double norm_ref,
-             int rmax, iga_tt** out) {
+             int rmax, iga_tt** out, double norm_w) {
   IGA_REQUIRE(W != nullptr && out != nullptr, "tt_svd: null pointer");
   IGA_REQUIRE(n1 > 0 && n2 > 0 && n3 > 0, "tt_svd: empty tensor");
   IGA_REQUIRE(tol >= 0.0, "tt_svd: negative tolerance");
   if (rmax <= 0) rmax = 1 << 30;
   *out = nullptr;
   size_t N = (size_t)n1 * n2 * n3;
-  double nrm = device_norm2(ctx, W, N);
+  double nrm = norm_w >= 0.0 ? norm_w : device_norm2(ctx, W, N);
   double ref = norm_ref > 0.0 ? norm_ref : nrm;
   if (nrm == 0.0 || nrm <= tol * ref) return;            // rank 0
   double delta = tol * ref / std::sqrt(2.0);
