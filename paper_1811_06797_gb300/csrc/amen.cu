@@ -540,6 +540,30 @@ static void rm_gemm(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const d
                        N, M, K, &alpha, B, ldb, A, lda, &beta, C, ldc));
 }
 
+// strided batch of row-major products in FP64 (DGEMM) or FP32 (SGEMM, no
+// TF32): C_i = alpha op(A_i) op(B_i) + beta C_i; runs in host pointer mode
+// whatever mode the caller has set
+template <typename U>
+static void rm_gemm_strided(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const U* A,
+                            int lda, long long sA, const U* B, int ldb, long long sB, U* C,
+                            int ldc, long long sC, int count, U alpha, U beta) {
+  if (M == 0 || N == 0 || count == 0) return;
+  cublasPointerMode_t pm;
+  IGA_BLAS(cublasGetPointerMode(ctx->blas, &pm));
+  if (pm != CUBLAS_POINTER_MODE_HOST) IGA_BLAS(cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST));
+  cublasStatus_t st;
+  if constexpr (sizeof(U) == 8)
+    st = cublasDgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,
+                                   tA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, B, ldb, sB, A,
+                                   lda, sA, &beta, C, ldc, sC, count);
+  else
+    st = cublasSgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,
+                                   tA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, B, ldb, sB, A,
+                                   lda, sA, &beta, C, ldc, sC, count);
+  if (pm != CUBLAS_POINTER_MODE_HOST) IGA_BLAS(cublasSetPointerMode(ctx->blas, pm));
+  IGA_BLAS(st);
+}
+
 // count products C_i = alpha op(A_i) op(B_i) + beta C_i of row-major matrices
 // with A_i = A + i sA (likewise B, C): one batched cuBLAS call
 static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const double* A,
@@ -1063,6 +1087,38 @@ struct Solver {
     size_t L;                            // per component
   };
 
+  // interface products of the local matvec (Sec. 5, the local operator as
+  // Phi_L (x) A_d (x) Phi_R): element kernels for small local systems, where
+  // launch latency dominates, library GEMMs once a product has 2^24 FMA
+  //   right: t[s][v](a, i, :) = x[v](a, i, :) R_s^T   (R_s^T when transR)
+  //   left:  y[v] = sum_s L_s t[s][v]                  (L_s^T when transL)
+  template <typename U>
+  void right_mult(const U* R, const U* x, int S, int nv, int r0, int nn, int r1, int transR,
+                  U* t) {
+    const size_t per = (size_t)nv * r0 * nn * r1;
+    if ((double)per * S * r1 < 16777216.0) {
+      IGA_LAUNCH(ctx, right_mult_kernel<U>, nblk(per * S), 256, 0, R, x, S, nv, r0, nn, r1,
+                 transR, t);
+      return;
+    }
+    rm_gemm_strided<U>(ctx, false, !transR, nv * r0 * nn, r1, r1, x, r1, 0, R, r1,
+                       (long long)r1 * r1, t, r1, (long long)per, S, U(1), U(0));
+  }
+  template <typename U>
+  void left_mult(const U* L, const U* t, int S, int nv, int r0, int nn, int r1, int transL, U* y) {
+    const size_t per = (size_t)nv * r0 * nn * r1;
+    if ((double)per * S * r0 < 16777216.0) {
+      IGA_LAUNCH(ctx, left_mult_kernel<U>, nblk(per), 256, 0, L, t, S, nv, r0, nn, r1, transL, y);
+      return;
+    }
+    const int nr = nn * r1;
+    for (int q = 0; q < S; ++q) {
+      rm_gemm_strided<U>(ctx, transL != 0, false, r0, nr, r0, L + (size_t)q * r0 * r0, r0, 0,
+                         t + (size_t)q * per, nr, (long long)r0 * nr, y, nr, (long long)r0 * nr,
+                         nv, U(1), q ? U(1) : U(0));
+    }
+  }
+
   // local KKT operator applied with interfaces PL/PR and bands of type U:
   // out = [M y + K lam, beta M u - M lam, K y - M u]
   template <typename U>
@@ -1076,13 +1132,11 @@ struct Solver {
       U* t1 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 2, per * z.R1);
       U* t2 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 3, per * z.R0);
       U* out = o ? Kv : Mv;
-      IGA_LAUNCH(ctx, right_mult_kernel<U>, nblk(per * z.R1), 256, 0, PR[o], x, z.R1, 3, c.r0,
-                 c.nn, c.r1, 0, t1);
+      right_mult<U>(PR[o], x, z.R1, 3, c.r0, c.nn, c.r1, 0, t1);
       IGA_LAUNCH(ctx, band_group_kernel<U>, nblk(per * z.R0), 256, 0, bands_of<U>(op[o], c.d),
                  z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, 3 * c.r0, c.nn, c.r1,
                  op[o]->p[c.d], t2);
-      IGA_LAUNCH(ctx, left_mult_kernel<U>, nblk(per), 256, 0, PL[o], t2, z.R0, 3, c.r0, c.nn,
-                 c.r1, 0, out);
+      left_mult<U>(PL[o], t2, z.R0, 3, c.r0, c.nn, c.r1, 0, out);
     }
     IGA_LAUNCH(ctx, kkt_combine_kernel<U>, nblk(c.L), 256, 0, Mv, Kv, c.L, (U)beta, y);
   }
@@ -1212,8 +1266,8 @@ struct Solver {
     const P* A = scratch<P>(ctx, SLOT_AMEN_BASE + 48, 1);
     int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, 1);
     // w = VL^T v VR
-    IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
-    IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
+    right_mult<T>(VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
+    left_mult<T>(VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
     {
       // keep each block's LU factor in shared memory when four of them fit
       size_t per = (size_t)BL.N * BL.W;
@@ -1236,8 +1290,8 @@ struct Solver {
                  z, lu_smem);
     }
     // back: VL z VR^T
-    IGA_LAUNCH(ctx, right_mult_kernel<T>, nblk(per), 256, 0, VRt.p, z, 1, 3, c.r0, c.nn, c.r1, 1, t);
-    IGA_LAUNCH(ctx, left_mult_kernel<T>, nblk(per), 256, 0, VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 1, z);
+    right_mult<T>(VRt.p, z, 1, 3, c.r0, c.nn, c.r1, 1, t);
+    left_mult<T>(VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 1, z);
   }
 
   // ---- restarted right-preconditioned GMRES in precision T; returns iterations
