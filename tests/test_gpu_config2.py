@@ -1,0 +1,85 @@
+"""The timed workload at full size (quarter annulus, degree 3, 64 elements per
+direction, beta 1e-4): the KKT solve as the benchmark runs it, checked against
+the definition at sampled rows.
+
+Each sampled row of the three KKT equations is evaluated with the oracle's own
+row integrals of M and K (`sampled_rows`) and load entries (`sampled_load`),
+applied to the GPU solution; a row's residual can never exceed the residual's
+2-norm, so every sampled entry must be within the solve tolerance times the
+load norm, up to the TT truncation of the weights (tol 1e-6 here).
+"""
+import numpy as np
+import pytest
+
+from oracle.assemble import Discretisation, sampled_load, sampled_rows
+from paper_1811_06797_gb300 import workloads as wl
+from gpu_util import ctx_and_torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    ctx, torch, iga = ctx_and_torch()
+    work = wl.config(2)
+    M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    disc = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+    rng = np.random.default_rng(2020)
+    n = disc.n
+    rows = np.stack([rng.integers(1, n[d] - 1, 10) for d in range(3)], axis=1)
+    rows[0] = (1, 1, 1)
+    rows[1] = tuple(x - 2 for x in n)
+    Mr, Kr = sampled_rows(work.geometry, disc, rows)
+    br = sampled_load(work.geometry, disc, work.target, rows)
+    return ctx, torch, iga, work, M, K, load, n, rows, Mr, Kr, br
+
+
+def _apply_row(stencil, field, r, n, p=3):
+    """sum_o stencil[o] field[r + o - p] over interior neighbours (field on the
+    interior grid, index = full index - 1)."""
+    acc = 0.0
+    for a in range(7):
+        i = r[0] + a - p
+        if i < 1 or i > n[0] - 2:
+            continue
+        for b in range(7):
+            j = r[1] + b - p
+            if j < 1 or j > n[1] - 2:
+                continue
+            for c in range(7):
+                k = r[2] + c - p
+                if k < 1 or k > n[2] - 2:
+                    continue
+                acc += stencil[a, b, c] * field[i - 1, j - 1, k - 1]
+    return acc
+
+
+@pytest.mark.parametrize("prec,trunc", [(0, 0), (1, 0), (0, 1)],
+                         ids=["fp64-pivoted", "mixed-pivoted", "fp64-svd"])
+def test_config2_solve_rows(setup, prec, trunc):
+    ctx, torch, iga, work, M, K, load, n, rows, Mr, Kr, br = setup
+    ni = M.info()["n"]
+    N = int(np.prod(ni))
+    y, u, lam = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+    info = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, y, u, lam, tol=1e-6,
+                                  precision=prec, truncation=trunc)
+    assert info["converged"] and info["residual"] <= 1e-6, info
+    # the full residual with the library's operator apply
+    z = torch.cat([y, u, lam])
+    out = torch.empty_like(z)
+    iga.iga_kkt_apply(ctx, M, K, work.beta, z, out)
+    bfull = torch.empty(ni, dtype=torch.float64, device="cuda")
+    load.full(ctx, bfull)
+    b = torch.zeros_like(z)
+    b[:N] = bfull.reshape(-1)
+    assert float((b - out).norm() / b.norm()) <= 1e-6
+    # sampled rows of the three equations against the definition
+    Y, U, L = (t.cpu().numpy().reshape(ni) for t in (y, u, lam))
+    bnorm = float(b.norm())
+    bound = (1e-6 + 10 * work.tol) * bnorm
+    for s, r in enumerate(rows):
+        my, ky = _apply_row(Mr[s], Y, r, n), _apply_row(Kr[s], Y, r, n)
+        mu, ml, kl = _apply_row(Mr[s], U, r, n), _apply_row(Mr[s], L, r, n), _apply_row(Kr[s], L, r, n)
+        assert abs(my + kl - br[s]) <= bound, (s, r, my + kl - br[s])
+        assert abs(work.beta * mu - ml) <= bound, (s, r)
+        assert abs(ky - mu) <= bound, (s, r)
