@@ -312,6 +312,8 @@ __global__ void scale_rsqrt_kernel(T* __restrict__ x, const double* __restrict__
 // largest lower bandwidth + 1 of the node-interleaved KKT blocks the LU
 // kernel handles (kl = 3 p + 2: degrees up to 4)
 constexpr int KKT_MAXKL = 16;
+// most K terms per core the quasi-definite form takes (else the LU form)
+constexpr int KKT_QD_MAXK = 64;
 
 struct BandLayout {
   int n, p, kl, ku, W, N, NB, r0, r1;
@@ -524,6 +526,184 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
   for (int I = lane; I < N; I += 32) {
     int i = I / 3, l = I - 3 * i;
     v[(size_t)l * comp + ((size_t)a * n + i) * L.r1 + b] = (V)s[I];
+  }
+}
+
+// ---- quasi-definite form of the local KKT blocks
+//
+// When the mass operator of the core is one Kronecker term, every block's
+// M_ab is symmetric positive definite (a positive multiple of the univariate
+// mass band in the transformed basis).  The control then eliminates: the
+// second row gives u = (lambda + M^-1 f2) / beta, and (y, lambda) solve
+//   S = [[M, K^T], [K, -M / beta]],  [y; lambda] = [f1; f3 + f2 / beta],
+// a symmetric quasi-definite matrix, which has an LDL^T factorisation without
+// pivoting.  Node-interleaved (2 i + l), S has half-bandwidth w = 2 p + 1;
+// M is factorised by banded Cholesky (half-bandwidth p).  Storage per block:
+// S lower band (2n x (w + 1)), entry (r, r - c) at r (w + 1) + c, then the
+// Cholesky band of M (n x (p + 1)).  One warp per block.
+template <typename T>
+__global__ void kkt_qd_factor_kernel(
+    BandLayout L, T beta, const T* __restrict__ bandM, const int* __restrict__ nzM_l,
+    const int* __restrict__ nzM_r, const long long* __restrict__ nzM_off,
+    const T* __restrict__ bandK, const int* __restrict__ nzK_l, const int* __restrict__ nzK_r,
+    const long long* __restrict__ nzK_off, int nnzK, const T* __restrict__ dLM,
+    const T* __restrict__ dRM, const T* __restrict__ dLK, const T* __restrict__ dRK,
+    T* __restrict__ out, int* __restrict__ flag) {
+  extern __shared__ unsigned char smraw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int blk = blockIdx.x * wpb + warp;
+  if (blk >= L.NB) return;
+  const int n = L.n, p = L.p, B = 2 * p + 1, w = 2 * p + 1, w1 = w + 1;
+  const int n2 = 2 * n;
+  const size_t per = (size_t)n2 * w1 + (size_t)n * (p + 1);
+  T* S = reinterpret_cast<T*>(smraw) + (size_t)warp * (per + KKT_QD_MAXK + 1);
+  T* Mc = S + (size_t)n2 * w1;
+  T* cf = Mc + (size_t)n * (p + 1);            // [M coefficient, K coefficients]
+  const int a = blk / L.r1, b = blk % L.r1;
+  for (size_t e = lane; e < per; e += 32) S[e] = T(0);
+  if (lane == 0) cf[0] = dLM[(size_t)nzM_l[0] * L.r0 + a] * dRM[(size_t)nzM_r[0] * L.r1 + b];
+  for (int z = lane; z < nnzK; z += 32)
+    cf[1 + z] = dLK[(size_t)nzK_l[z] * L.r0 + a] * dRK[(size_t)nzK_r[z] * L.r1 + b];
+  __syncwarp();
+  const T sm = cf[0];
+  for (int e = lane; e < n * B; e += 32) {
+    const int i = e / B, o = e - i * B;
+    const int j = i + o - p;                    // column node
+    if (j < 0 || j >= n || j > i) continue;     // lower part: j <= i
+    const T m = sm * bandM[nzM_off[0] + (size_t)i * B + o];
+    T k = T(0), kt = T(0);
+    for (int z = 0; z < nnzK; ++z) {
+      const T c = cf[1 + z];
+      k += c * bandK[nzK_off[z] + (size_t)i * B + o];                 // K(i, j)
+      kt += c * bandK[nzK_off[z] + (size_t)j * B + (i - j + p)];      // K(j, i)
+    }
+    // rows 2i (y) and 2i+1 (lambda), columns 2j, 2j+1, lower part only
+    S[(size_t)(2 * i) * w1 + (2 * i - 2 * j)] = m;                     // (2i, 2j)
+    if (j < i) S[(size_t)(2 * i) * w1 + (2 * i - 2 * j - 1)] = kt;      // (2i, 2j+1) = K^T(i,j)
+    S[(size_t)(2 * i + 1) * w1 + (2 * i + 1 - 2 * j)] = k;             // (2i+1, 2j) = K(i,j)
+    S[(size_t)(2 * i + 1) * w1 + (2 * i - 2 * j)] = -m / beta;         // (2i+1, 2j+1)
+    Mc[(size_t)i * (p + 1) + (i - j)] = m;
+  }
+  __syncwarp();
+  // LDL^T: with c_t = S(k + t, k), S(k + t2, k + t1) -= c_t2 c_t1 / d_k, then
+  // the column becomes l_t = c_t / d_k
+  for (int k = 0; k < n2; ++k) {
+    const T d = S[(size_t)k * w1];
+    if (d == T(0)) {
+      if (lane == 0) atomicOr(flag, 2);
+      continue;
+    }
+    const int cnt = min(w, n2 - 1 - k);
+    for (int e = lane; e < cnt * (cnt + 1) / 2; e += 32) {
+      int t2 = 1;
+      while (t2 * (t2 + 1) / 2 <= e) ++t2;
+      const int t1 = e - (t2 - 1) * t2 / 2 + 1;
+      const T c2 = S[(size_t)(k + t2) * w1 + t2];
+      const T c1 = S[(size_t)(k + t1) * w1 + t1];
+      S[(size_t)(k + t2) * w1 + (t2 - t1)] -= c2 * c1 / d;
+    }
+    __syncwarp();
+    for (int t = 1 + lane; t <= cnt; t += 32) S[(size_t)(k + t) * w1 + t] /= d;
+    __syncwarp();
+  }
+  // banded Cholesky of M: with c_t = Mc(k + t, k) and s = sqrt(Mc(k, k)),
+  // Mc(k + t2, k + t1) -= c_t2 c_t1 / s^2, then the column becomes c_t / s
+  for (int k = 0; k < n; ++k) {
+    T d = Mc[(size_t)k * (p + 1)];
+    if (!(d > T(0))) {
+      if (lane == 0) atomicOr(flag, 2);
+      d = T(1);
+    }
+    const int cnt = min(p, n - 1 - k);
+    for (int e = lane; e < cnt * (cnt + 1) / 2; e += 32) {
+      int t2 = 1;
+      while (t2 * (t2 + 1) / 2 <= e) ++t2;
+      const int t1 = e - (t2 - 1) * t2 / 2 + 1;
+      const T c2 = Mc[(size_t)(k + t2) * (p + 1) + t2];
+      const T c1 = Mc[(size_t)(k + t1) * (p + 1) + t1];
+      Mc[(size_t)(k + t2) * (p + 1) + (t2 - t1)] -= c2 * c1 / d;
+    }
+    __syncwarp();
+    const T sq = sqrt(d);
+    for (int t = 1 + lane; t <= cnt; t += 32) Mc[(size_t)(k + t) * (p + 1) + t] /= sq;
+    if (lane == 0) Mc[(size_t)k * (p + 1)] = sq;
+    __syncwarp();
+  }
+  T* g = out + (size_t)blk * per;
+  for (size_t e = lane; e < per; e += 32) g[e] = S[e];
+}
+
+// apply: f (y, u, lambda rows of block (a, b)) -> solution, in place in v
+template <typename T, typename V>
+__global__ void kkt_qd_solve_kernel(BandLayout L, T beta, const T* __restrict__ fac,
+                                    V* __restrict__ v) {
+  extern __shared__ unsigned char smraw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int blk = blockIdx.x * wpb + warp;
+  if (blk >= L.NB) return;
+  const int n = L.n, p = L.p, w = 2 * p + 1, w1 = w + 1, n2 = 2 * n;
+  const size_t per = (size_t)n2 * w1 + (size_t)n * (p + 1);
+  T* S = reinterpret_cast<T*>(smraw) + (size_t)warp * (per + 3 * n);
+  T* Mc = S + (size_t)n2 * w1;
+  T* h = Mc + (size_t)n * (p + 1);            // 2n: (y, lambda) interleaved
+  T* g = h + n2;                              // n: M^-1 f2
+  const T* src = fac + (size_t)blk * per;
+  for (size_t e = lane; e < per; e += 32) S[e] = src[e];
+  const int a = blk / L.r1, b = blk % L.r1;
+  const size_t comp = (size_t)L.r0 * n * L.r1;
+  for (int i = lane; i < n; i += 32) {
+    const size_t o = ((size_t)a * n + i) * L.r1 + b;
+    const T f1 = (T)v[o], f2 = (T)v[comp + o], f3 = (T)v[2 * comp + o];
+    h[2 * i] = f1;
+    h[2 * i + 1] = f3 + f2 / beta;
+    g[i] = f2;
+  }
+  __syncwarp();
+  // g = M^-1 f2 (Cholesky, column-oriented sweeps)
+  for (int k = 0; k < n; ++k) {
+    const T x = g[k] / Mc[(size_t)k * (p + 1)];
+    __syncwarp();
+    const int cnt = min(p, n - 1 - k);
+    for (int t = 1 + lane; t <= cnt; t += 32) g[k + t] -= Mc[(size_t)(k + t) * (p + 1) + t] * x;
+    if (lane == 0) g[k] = x;
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const T x = g[k] / Mc[(size_t)k * (p + 1)];
+    __syncwarp();
+    const int cnt = min(p, k);
+    for (int t = 1 + lane; t <= cnt; t += 32) g[k - t] -= Mc[(size_t)k * (p + 1) + t] * x;
+    if (lane == 0) g[k] = x;
+    __syncwarp();
+  }
+  // (y, lambda) = S^-1 h with S = L D L^T
+  for (int k = 0; k < n2; ++k) {
+    const T x = h[k];
+    __syncwarp();
+    const int cnt = min(w, n2 - 1 - k);
+    for (int t = 1 + lane; t <= cnt; t += 32) h[k + t] -= S[(size_t)(k + t) * w1 + t] * x;
+    __syncwarp();
+  }
+  for (int k = lane; k < n2; k += 32) {
+    const T d = S[(size_t)k * w1];
+    h[k] = d != T(0) ? h[k] / d : T(0);
+  }
+  __syncwarp();
+  for (int k = n2 - 1; k >= 0; --k) {
+    const T x = h[k];
+    __syncwarp();
+    const int cnt = min(w, k);
+    for (int t = 1 + lane; t <= cnt; t += 32) h[k - t] -= S[(size_t)k * w1 + t] * x;
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) {
+    const size_t o = ((size_t)a * n + i) * L.r1 + b;
+    const T y = h[2 * i], lam = h[2 * i + 1];
+    v[o] = (V)y;
+    v[comp + o] = (V)((lam + g[i]) / beta);
+    v[2 * comp + o] = (V)lam;
   }
 }
 
@@ -1156,6 +1336,7 @@ struct Solver {
 
   // ---- preconditioner
   BandLayout BL{};
+  bool qd = false;                     // quasi-definite block form (one M term)
   DevBuf<T> VLt, VRt;                    // transforms (col-major r x r)
   void precond_setup(const Local& c) {
     int r0 = c.r0, r1 = c.r1;
@@ -1237,6 +1418,33 @@ struct Solver {
     BL.r0 = r0;
     BL.r1 = r1;
     BL.NB = r0 * r1;
+    qd = zM.l.size() == 1 && (int)zK.l.size() <= KKT_QD_MAXK;
+    if (qd) {
+      // one M term: eliminate u, LDL^T of the quasi-definite (y, lambda) blocks
+      const int w1 = 2 * BL.p + 2;
+      const size_t per = (size_t)2 * BL.n * w1 + (size_t)BL.n * (BL.p + 1);
+      P* F = scratch<P>(ctx, SLOT_AMEN_BASE + 48, per * BL.NB);
+      IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
+      const size_t perw = (per + KKT_QD_MAXK + 1) * sizeof(P);
+      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perw));
+      IGA_REQUIRE(perw <= 200 * 1024, "kkt preconditioner: block too large");
+      static bool qattr = false;
+      if (!qattr) {
+        IGA_CUDA(cudaFuncSetAttribute(kkt_qd_factor_kernel<P>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+        qattr = true;
+      }
+      // algorithmic: LDL^T of 2n rows with half-bandwidth w and Cholesky of n
+      // rows with half-bandwidth p
+      prof_count(ctx, (double)BL.NB * per * sizeof(P),
+                 (double)BL.NB * (2.0 * BL.n * (2 * BL.p + 1) * (2 * BL.p + 2) +
+                                  (double)BL.n * BL.p * (BL.p + 1)));
+      IGA_LAUNCH(ctx, kkt_qd_factor_kernel<P>, nblk(BL.NB, wpb), 32 * wpb, wpb * perw, BL,
+                 (P)beta, bands_of<P>(op[0], c.d), zM.dl.p, zM.dr.p, zM.doff.p,
+                 bands_of<P>(op[1], c.d), zK.dl.p, zK.dr.p, zK.doff.p, (int)zK.l.size(), tdLM,
+                 tdRM, tdLK, tdRK, F, ctx->dflag);
+      return;
+    }
     P* A = scratch<P>(ctx, SLOT_AMEN_BASE + 48, (size_t)BL.N * BL.W * BL.NB);
     int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, (size_t)BL.N * BL.NB);
     IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
@@ -1268,7 +1476,23 @@ struct Solver {
     // w = VL^T v VR
     right_mult<T>(VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
     left_mult<T>(VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
-    {
+    if (qd) {
+      const int w1 = 2 * BL.p + 2;
+      const size_t per = (size_t)2 * BL.n * w1 + (size_t)BL.n * (BL.p + 1);
+      const size_t perw = (per + 3 * (size_t)BL.n) * sizeof(P);
+      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perw));
+      static bool qattr = false;
+      if (!qattr) {
+        IGA_CUDA(cudaFuncSetAttribute(kkt_qd_solve_kernel<P, T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+        qattr = true;
+      }
+      // algorithmic: two band sweeps of 2n rows (half-bandwidth 2p+1) and two of n rows
+      prof_count(ctx, (double)BL.NB * (per * sizeof(P) + 6.0 * BL.n * sizeof(T)),
+                 (double)BL.NB * (8.0 * BL.n * (2 * BL.p + 1) + 4.0 * BL.n * BL.p));
+      IGA_LAUNCH(ctx, (kkt_qd_solve_kernel<P, T>), nblk(BL.NB, wpb), 32 * wpb, wpb * perw, BL,
+                 (P)beta, A, z);
+    } else {
       // keep each block's LU factor in shared memory when four of them fit
       size_t per = (size_t)BL.N * BL.W;
       // per warp: LU factor (when it fits), the vector and the pivots
