@@ -586,48 +586,68 @@ __global__ void kkt_qd_factor_kernel(
     Mc[(size_t)i * (p + 1) + (i - j)] = m;
   }
   __syncwarp();
-  // LDL^T: with c_t = S(k + t, k), S(k + t2, k + t1) -= c_t2 c_t1 / d_k, then
-  // the column becomes l_t = c_t / d_k
+  // Each lane owns one pair t1 <= t2 of the column update (w (w + 1) / 2 <= 45
+  // pairs for p <= 4, so at most two per lane), decoded once.
+  int pt2[2], pt1[2];
+  for (int q = 0; q < 2; ++q) {
+    const int e = lane + 32 * q;
+    int t2 = 1;
+    while (t2 * (t2 + 1) / 2 <= e) ++t2;
+    pt2[q] = t2;
+    pt1[q] = e - (t2 - 1) * t2 / 2 + 1;
+  }
+  // LDL^T: with c_t = S(k + t, k), S(k + t2, k + t1) -= c_t2 c_t1 / d_k and the
+  // column becomes l_t = c_t / d_k; every lane reads its c values before the
+  // shared update
   for (int k = 0; k < n2; ++k) {
     const T d = S[(size_t)k * w1];
     if (d == T(0)) {
       if (lane == 0) atomicOr(flag, 2);
       continue;
     }
+    const T rd = T(1) / d;
     const int cnt = min(w, n2 - 1 - k);
-    for (int e = lane; e < cnt * (cnt + 1) / 2; e += 32) {
-      int t2 = 1;
-      while (t2 * (t2 + 1) / 2 <= e) ++t2;
-      const int t1 = e - (t2 - 1) * t2 / 2 + 1;
-      const T c2 = S[(size_t)(k + t2) * w1 + t2];
-      const T c1 = S[(size_t)(k + t1) * w1 + t1];
-      S[(size_t)(k + t2) * w1 + (t2 - t1)] -= c2 * c1 / d;
+    T c2[2], c1[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const bool on = pt2[q] <= cnt;
+      c2[q] = on ? S[(size_t)(k + pt2[q]) * w1 + pt2[q]] : T(0);
+      c1[q] = on ? S[(size_t)(k + pt1[q]) * w1 + pt1[q]] : T(0);
     }
+    const T ct = (lane >= 1 && lane <= cnt) ? S[(size_t)(k + lane) * w1 + lane] : T(0);
     __syncwarp();
-    for (int t = 1 + lane; t <= cnt; t += 32) S[(size_t)(k + t) * w1 + t] /= d;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (pt2[q] <= cnt) S[(size_t)(k + pt2[q]) * w1 + (pt2[q] - pt1[q])] -= c2[q] * c1[q] * rd;
+    if (lane >= 1 && lane <= cnt) S[(size_t)(k + lane) * w1 + lane] = ct * rd;
     __syncwarp();
   }
   // banded Cholesky of M: with c_t = Mc(k + t, k) and s = sqrt(Mc(k, k)),
-  // Mc(k + t2, k + t1) -= c_t2 c_t1 / s^2, then the column becomes c_t / s
+  // Mc(k + t2, k + t1) -= c_t2 c_t1 / s^2 and the column becomes c_t / s
   for (int k = 0; k < n; ++k) {
     T d = Mc[(size_t)k * (p + 1)];
     if (!(d > T(0))) {
       if (lane == 0) atomicOr(flag, 2);
       d = T(1);
     }
+    const T rd = T(1) / d;
+    const T rs = T(1) / sqrt(d);
     const int cnt = min(p, n - 1 - k);
-    for (int e = lane; e < cnt * (cnt + 1) / 2; e += 32) {
-      int t2 = 1;
-      while (t2 * (t2 + 1) / 2 <= e) ++t2;
-      const int t1 = e - (t2 - 1) * t2 / 2 + 1;
-      const T c2 = Mc[(size_t)(k + t2) * (p + 1) + t2];
-      const T c1 = Mc[(size_t)(k + t1) * (p + 1) + t1];
-      Mc[(size_t)(k + t2) * (p + 1) + (t2 - t1)] -= c2 * c1 / d;
+    T c2[2], c1[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const bool on = pt2[q] <= cnt;
+      c2[q] = on ? Mc[(size_t)(k + pt2[q]) * (p + 1) + pt2[q]] : T(0);
+      c1[q] = on ? Mc[(size_t)(k + pt1[q]) * (p + 1) + pt1[q]] : T(0);
     }
+    const T ct = (lane >= 1 && lane <= cnt) ? Mc[(size_t)(k + lane) * (p + 1) + lane] : T(0);
     __syncwarp();
-    const T sq = sqrt(d);
-    for (int t = 1 + lane; t <= cnt; t += 32) Mc[(size_t)(k + t) * (p + 1) + t] /= sq;
-    if (lane == 0) Mc[(size_t)k * (p + 1)] = sq;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (pt2[q] <= cnt)
+        Mc[(size_t)(k + pt2[q]) * (p + 1) + (pt2[q] - pt1[q])] -= c2[q] * c1[q] * rd;
+    if (lane >= 1 && lane <= cnt) Mc[(size_t)(k + lane) * (p + 1) + lane] = ct * rs;
+    if (lane == 0) Mc[(size_t)k * (p + 1)] = sqrt(d);
     __syncwarp();
   }
   T* g = out + (size_t)blk * per;
@@ -661,43 +681,75 @@ __global__ void kkt_qd_solve_kernel(BandLayout L, T beta, const T* __restrict__ 
     g[i] = f2;
   }
   __syncwarp();
-  // g = M^-1 f2 (Cholesky, column-oriented sweeps)
-  for (int k = 0; k < n; ++k) {
-    const T x = g[k] / Mc[(size_t)k * (p + 1)];
-    __syncwarp();
-    const int cnt = min(p, n - 1 - k);
-    for (int t = 1 + lane; t <= cnt; t += 32) g[k + t] -= Mc[(size_t)(k + t) * (p + 1) + t] * x;
-    if (lane == 0) g[k] = x;
-    __syncwarp();
+  // The four triangular sweeps run on a register window: in a forward sweep
+  // lane t holds entry k + t of the vector (k + t in a backward one), the
+  // settled entry k comes from lane 0 by a shuffle, lanes 1..band subtract
+  // their band coefficient times it, and the window shifts by one lane (lane
+  // 31 reads the next untouched entry from shared memory).  The dependency
+  // chain per row is two shuffles and one FMA.
+  const int pw = p + 1;
+  // g = M^-1 f2: forward with the Cholesky factor ...
+  {
+    T hv = lane < n ? g[lane] : T(0);
+    for (int k = 0; k < n; ++k) {
+      const T c = (lane >= 1 && lane <= p && k + lane < n) ? Mc[(size_t)(k + lane) * pw + lane]
+                                                           : T(0);
+      const T x = __shfl_sync(0xffffffffu, hv, 0) / Mc[(size_t)k * pw];
+      if (lane == 0) g[k] = x;
+      hv -= c * x;
+      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+      if (lane == 31) nx = k + 32 < n ? g[k + 32] : T(0);
+      hv = nx;
+    }
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const T x = g[k] / Mc[(size_t)k * (p + 1)];
-    __syncwarp();
-    const int cnt = min(p, k);
-    for (int t = 1 + lane; t <= cnt; t += 32) g[k - t] -= Mc[(size_t)k * (p + 1) + t] * x;
-    if (lane == 0) g[k] = x;
-    __syncwarp();
+  __syncwarp();
+  // ... and backward with its transpose
+  {
+    T hv = n - 1 - lane >= 0 ? g[n - 1 - lane] : T(0);
+    for (int k = n - 1; k >= 0; --k) {
+      const T c = (lane >= 1 && lane <= p && k - lane >= 0) ? Mc[(size_t)k * pw + lane] : T(0);
+      const T x = __shfl_sync(0xffffffffu, hv, 0) / Mc[(size_t)k * pw];
+      if (lane == 0) g[k] = x;
+      hv -= c * x;
+      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+      if (lane == 31) nx = k - 32 >= 0 ? g[k - 32] : T(0);
+      hv = nx;
+    }
   }
-  // (y, lambda) = S^-1 h with S = L D L^T
-  for (int k = 0; k < n2; ++k) {
-    const T x = h[k];
-    __syncwarp();
-    const int cnt = min(w, n2 - 1 - k);
-    for (int t = 1 + lane; t <= cnt; t += 32) h[k + t] -= S[(size_t)(k + t) * w1 + t] * x;
-    __syncwarp();
+  __syncwarp();
+  // (y, lambda) = S^-1 h with S = L D L^T: unit lower sweep, D, unit upper sweep
+  {
+    T hv = lane < n2 ? h[lane] : T(0);
+    for (int k = 0; k < n2; ++k) {
+      const T c = (lane >= 1 && lane <= w && k + lane < n2) ? S[(size_t)(k + lane) * w1 + lane]
+                                                            : T(0);
+      const T x = __shfl_sync(0xffffffffu, hv, 0);
+      if (lane == 0) h[k] = x;
+      hv -= c * x;
+      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+      if (lane == 31) nx = k + 32 < n2 ? h[k + 32] : T(0);
+      hv = nx;
+    }
   }
+  __syncwarp();
   for (int k = lane; k < n2; k += 32) {
     const T d = S[(size_t)k * w1];
     h[k] = d != T(0) ? h[k] / d : T(0);
   }
   __syncwarp();
-  for (int k = n2 - 1; k >= 0; --k) {
-    const T x = h[k];
-    __syncwarp();
-    const int cnt = min(w, k);
-    for (int t = 1 + lane; t <= cnt; t += 32) h[k - t] -= S[(size_t)k * w1 + t] * x;
-    __syncwarp();
+  {
+    T hv = n2 - 1 - lane >= 0 ? h[n2 - 1 - lane] : T(0);
+    for (int k = n2 - 1; k >= 0; --k) {
+      const T c = (lane >= 1 && lane <= w && k - lane >= 0) ? S[(size_t)k * w1 + lane] : T(0);
+      const T x = __shfl_sync(0xffffffffu, hv, 0);
+      if (lane == 0) h[k] = x;
+      hv -= c * x;
+      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+      if (lane == 31) nx = k - 32 >= 0 ? h[k - 32] : T(0);
+      hv = nx;
+    }
   }
+  __syncwarp();
   for (int i = lane; i < n; i += 32) {
     const size_t o = ((size_t)a * n + i) * L.r1 + b;
     const T y = h[2 * i], lam = h[2 * i + 1];
