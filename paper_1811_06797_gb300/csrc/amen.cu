@@ -296,6 +296,63 @@ __global__ void scale_rsqrt_kernel(T* __restrict__ x, const double* __restrict__
   if (i < n) x[i] = s > 0.0 ? (T)((double)x[i] / sqrt(s)) : T(0);
 }
 
+// Gram-Schmidt steps of the local GMRES against the basis V (nb vectors of n
+// entries, vector j at V + j n).  h (nb entries, zeroed by the caller) gets
+// V^T w by per-block partial sums and atomics; then w -= V h.
+template <typename T>
+__global__ void cgs_dots_kernel(const T* __restrict__ V, const T* __restrict__ w, size_t n,
+                                int nb, T* __restrict__ h) {
+  __shared__ double red[32];
+  const int j = blockIdx.y;
+  const T* vj = V + (size_t)j * n;
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    acc = fma((double)vj[i], (double)w[i], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    atomicAdd(h + j, (T)t);
+  }
+  (void)nb;
+}
+
+// w -= V h; with nrm != nullptr also *nrm += ||w||^2 (FP64)
+template <typename T>
+__global__ void cgs_update_kernel(const T* __restrict__ V, const T* __restrict__ h, size_t n,
+                                  int nb, T* __restrict__ w, double* __restrict__ nrm) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    T s = w[i];
+    for (int j = 0; j < nb; ++j) s -= V[(size_t)j * n + i] * h[j];
+    w[i] = s;
+    acc = fma((double)s, (double)s, acc);
+  }
+  if (nrm == nullptr) return;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    atomicAdd(nrm, t);
+  }
+}
+
+// y = x / sqrt(*s2) (y = 0 when *s2 = 0)
+template <typename T>
+__global__ void scale_copy_kernel(const T* __restrict__ x, const double* __restrict__ s2, size_t n,
+                                  T* __restrict__ y) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s = *s2;
+  if (i < n) y[i] = s > 0.0 ? (T)((double)x[i] / sqrt(s)) : T(0);
+}
+
 // --------------------------------------------- banded LU of the local KKT blocks
 //
 // For every rank pair (a, b) the 3n x 3n local KKT block
@@ -1629,22 +1686,24 @@ struct Solver {
           T* zk = Zb + (size_t)k * Lv;
           precond_apply(c, vk, zk);
           local_op(c, zk, w);
-          // classical Gram-Schmidt, twice
+          // classical Gram-Schmidt, twice: h1 = V^T w, w -= V h1, h2 = V^T w,
+          // w -= V h2 with ||w||^2, then v_{k+1} = w / ||w||
           T* h1 = hd;
           T* h2 = hd + (m + 2);
-          gemv(CUBLAS_OP_T, (int)Lv, k + 1, one, Vb, w, zero, h1);
-          gemv(CUBLAS_OP_N, (int)Lv, k + 1, mone, Vb, h1, one, w);
-          gemv(CUBLAS_OP_T, (int)Lv, k + 1, one, Vb, w, zero, h2);
-          gemv(CUBLAS_OP_N, (int)Lv, k + 1, mone, Vb, h2, one, w);
-          sumsq(w, nd + 1);
+          const unsigned db = std::max(1u, std::min<unsigned>(nblk(Lv), 304u / (unsigned)(k + 1)));
+          IGA_CUDA(cudaMemsetAsync(hd, 0, 2 * (m + 2) * sizeof(T), ctx->stream));
+          IGA_CUDA(cudaMemsetAsync(nd + 1, 0, sizeof(double), ctx->stream));
+          IGA_LAUNCH(ctx, cgs_dots_kernel<T>, dim3(db, k + 1), 256, 0, Vb, w, Lv, k + 1, h1);
+          IGA_LAUNCH(ctx, cgs_update_kernel<T>, nsb, 256, 0, Vb, h1, Lv, k + 1, w, (double*)nullptr);
+          IGA_LAUNCH(ctx, cgs_dots_kernel<T>, dim3(db, k + 1), 256, 0, Vb, w, Lv, k + 1, h2);
+          IGA_LAUNCH(ctx, cgs_update_kernel<T>, nsb, 256, 0, Vb, h2, Lv, k + 1, w, nd + 1);
           IGA_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * (m + 2) * sizeof(T), cudaMemcpyDeviceToHost,
                                    ctx->stream));
           double h2n = 0.0;
           IGA_CUDA(cudaMemcpyAsync(&h2n, nd + 1, sizeof(double), cudaMemcpyDeviceToHost,
                                    ctx->stream));
           T* vn = Vb + (size_t)(k + 1) * Lv;
-          IGA_CUDA(cudaMemcpyAsync(vn, w, Lv * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
-          IGA_LAUNCH(ctx, scale_rsqrt_kernel<T>, nblk(Lv), 256, 0, vn, nd + 1, Lv);
+          IGA_LAUNCH(ctx, scale_copy_kernel<T>, nblk(Lv), 256, 0, w, nd + 1, Lv, vn);
           IGA_CUDA(cudaStreamSynchronize(ctx->stream));
           for (int j = 0; j <= k; ++j) H[j * m + k] = (double)hh[j] + (double)hh[(m + 2) + j];
           double hn = std::sqrt(h2n);

@@ -1412,38 +1412,35 @@ __global__ void fibres_kernel(const double* __restrict__ W, int n1, int n2, int 
 
 __global__ void rank1_residual_kernel(const double* __restrict__ W, int n1, int n2, int n3,
                                       const double* __restrict__ f, double* __restrict__ out) {
-  // (i, j) fibres per block iteration (four in flight), threads along k:
-  // e = W - (a_i b_j / v^2) c_k
+  // each block takes a contiguous range of (i, j) fibres, their factors
+  // a_i b_j / v^2 staged in shared memory (one division per fibre), threads
+  // along k: e = W - (a_i b_j / v^2) c_k
+  constexpr int RB = 64;
   __shared__ double red[32];
+  __shared__ double abs_[RB];
   const double* a = f;
   const double* b = f + n1;
   const double* c = f + n1 + n2;
   const double v = f[n1 + n2 + n3];
   const double iv2 = 1.0 / (v * v);
   const long long rows = (long long)n1 * n2;
-  const long long G = gridDim.x;
   double acc0 = 0.0, acc1 = 0.0;
-  for (long long row = blockIdx.x; row < rows; row += 4 * G) {
-    double ab[4];
-    const double* w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long rq = row + q * G;
-      const long long rr = rq < rows ? rq : row;
+  for (long long r0 = (long long)blockIdx.x * RB; r0 < rows; r0 += (long long)gridDim.x * RB) {
+    const int nr = (int)min((long long)RB, rows - r0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const long long rr = r0 + t;
       const int i = (int)(rr / n2), j = (int)(rr - (long long)i * n2);
-      ab[q] = rq < rows ? a[i] * b[j] * iv2 : 0.0;
-      w[q] = W + (size_t)rr * n3;
+      abs_[t] = a[i] * b[j] * iv2;
     }
+    __syncthreads();
+    const double* w = W + (size_t)r0 * n3;
     for (int k = threadIdx.x; k < n3; k += blockDim.x) {
       const double ck = c[k];
-      double x[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) x[q] = w[q][k];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (row + q * G >= rows) continue;        // (a valid row stands in; skipped)
-        const double e = fma(-ab[q], ck, x[q]);
-        if (q & 1) acc1 = fma(e, e, acc1); else acc0 = fma(e, e, acc0);
+#pragma unroll 8
+      for (int r = 0; r < nr; ++r) {
+        const double e0 = fma(-abs_[r], ck, w[(size_t)r * n3 + k]);
+        if (r & 1) acc1 = fma(e0, e0, acc1); else acc0 = fma(e0, e0, acc0);
       }
     }
   }
@@ -1475,7 +1472,7 @@ static iga_tt* rank1_cross(iga_ctx* ctx, const double* W, int n1, int n2, int n3
   int nf = n1 + n2 + n3 + 1;
   IGA_LAUNCH(ctx, fibres_kernel, (nf + 255) / 256, 256, 0, W, n1, n2, n3, keys, f);
   prof_count(ctx, (double)N * 8.0, 4.0 * (double)N);
-  int rblocks = (int)std::min<long long>((long long)n1 * n2, 152 * 8);
+  int rblocks = (int)std::min<long long>(((long long)n1 * n2 + 63) / 64, 152 * 8);
   IGA_LAUNCH(ctx, rank1_residual_kernel, rblocks, 256, 0, W, n1, n2, n3, f, err);
   double h[2] = {0.0, 0.0};
   IGA_CUDA(cudaMemcpyAsync(h, f + n1 + n2 + n3, 2 * sizeof(double), cudaMemcpyDeviceToHost,
