@@ -39,6 +39,7 @@ NCU_TRAFFIC = {"sample_weights_kernel": 1.0593e9}
 CANDIDATES = {
     "jacobi_eig_kernel": "fp64", "sample_weights_kernel": "fp64",
     "kkt_block_solve_kernel": "fp32", "kkt_block_factor_kernel": "fp32",
+    "kkt_qd_solve_kernel": "fp32", "kkt_qd_factor_kernel": "fp32",
     "kron_rank1_kernel": "fp64",
     "qrcp_cluster_kernel": "fp64", "householder_qr_cluster_kernel": "fp64",
     "rank1_residual_kernel": "fp64",
