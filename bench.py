@@ -34,7 +34,7 @@ FP64_FMA_TFLOPS = 1.196      # measured FP64 FMA rate of this GB300 (CUDA cores)
 FP32_FMA_TFLOPS = 74.75      # measured FP32 FMA rate
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel, as
 # summarised under profiles/; an entry is dropped whenever its kernel changes
-NCU_TRAFFIC = {"sample_weights_kernel": 1.0593e9}
+NCU_TRAFFIC = {"sample_weights_kernel": 1.0692e9}
 # kernels that can dominate a step, with the arithmetic they run in
 CANDIDATES = {
     "jacobi_eig_kernel": "fp64", "sample_weights_kernel": "fp64",

@@ -322,7 +322,8 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
     for (int k = 0; k < 3; ++k) J[a][k] = (dA[k][a] - X[a] * dA[k][3]) * iw;
   if (G.kind == IGA_GEO_NURBS_TWIST) {
     double th = G.twist * X[2];
-    double c = cos(th), s = sin(th);
+    double s, c;
+    sincos(th, &s, &c);
     double x = X[0], y = X[1];
     double J0[3], J1[3];
     for (int k = 0; k < 3; ++k) {
@@ -339,16 +340,22 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
   if (valid && (!(det != 0.0) || !isfinite(det))) atomicOr(flag, 1);
   double adet = fabs(det);
   // metric m = J^T J; Q = adj(m) / det(m) * |det J| = adj(m) / |det J|
-  double m[3][3];
-  for (int k = 0; k < 3; ++k)
-    for (int l = 0; l < 3; ++l) m[k][l] = J[0][k] * J[0][l] + J[1][k] * J[1][l] + J[2][k] * J[2][l];
-  double inv = 1.0 / adet;
-  double q11 = (m[1][1] * m[2][2] - m[1][2] * m[2][1]) * inv;
-  double q12 = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) * inv;
-  double q13 = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) * inv;
-  double q22 = (m[0][0] * m[2][2] - m[0][2] * m[2][0]) * inv;
-  double q23 = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) * inv;
-  double q33 = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) * inv;
+  // symmetric metric m = J^T J (six entries)
+  double m00 = J[0][0] * J[0][0] + J[1][0] * J[1][0] + J[2][0] * J[2][0];
+  double m01 = J[0][0] * J[0][1] + J[1][0] * J[1][1] + J[2][0] * J[2][1];
+  double m02 = J[0][0] * J[0][2] + J[1][0] * J[1][2] + J[2][0] * J[2][2];
+  double m11 = J[0][1] * J[0][1] + J[1][1] * J[1][1] + J[2][1] * J[2][1];
+  double m12 = J[0][1] * J[0][2] + J[1][1] * J[1][2] + J[2][1] * J[2][2];
+  double m22 = J[0][2] * J[0][2] + J[1][2] * J[1][2] + J[2][2] * J[2][2];
+  double g = G.g[0][i1] * G.g[1][i2] * G.g[2][i3];
+  // the Gauss weight folded into the scale of the adjugate
+  double inv = g / adet;
+  double q11 = (m11 * m22 - m12 * m12) * inv;
+  double q12 = (m02 * m12 - m01 * m22) * inv;
+  double q13 = (m01 * m12 - m02 * m11) * inv;
+  double q22 = (m00 * m22 - m02 * m02) * inv;
+  double q23 = (m02 * m01 - m00 * m12) * inv;
+  double q33 = (m00 * m11 - m01 * m01) * inv;
   double yh = 0.0;
   if (G.tkind == IGA_TARGET_SINPROD) {
     yh = sin(M_PI * X[0]) * sin(M_PI * X[1]) * sin(M_PI * X[2]);
@@ -356,18 +363,18 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
     double dx = X[0] - G.tp[0], dy = X[1] - G.tp[1], dz = X[2] - G.tp[2];
     yh = exp(-(dx * dx + dy * dy + dz * dz) / G.tp[3]);
   }
-  double g = G.g[0][i1] * G.g[1][i2] * G.g[2][i3];
-  double v[8] = {adet, q11, q12, q13, q22, q23, q33, yh * adet};
+  const double wg = adet * g;
+  double v[8] = {wg, q11, q12, q13, q22, q23, q33, yh * wg};
   if (valid) {
     if (G.comp < 0) {
-      for (int c = 0; c < 8; ++c) out[c * total + t] = v[c] * g;
+      for (int c = 0; c < 8; ++c) out[c * total + t] = v[c];
     } else {
-      out[t] = v[G.comp] * g;
+      out[t] = v[G.comp];
     }
   }
   if (G.qn2) {
     double q2 = valid ? (q11 * q11 + q22 * q22 + q33 * q33 +
-                         2.0 * (q12 * q12 + q13 * q13 + q23 * q23)) * g * g
+                         2.0 * (q12 * q12 + q13 * q13 + q23 * q23))
                       : 0.0;
     for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(G.qn2, q2);
@@ -441,10 +448,11 @@ struct GeoSampler {
     IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
     int threads = 256;
     // algorithmic per point: 16 (p1 + 1) FMA for the map and its derivatives,
-    // about 150 flop for the quotient rule, det, adjugate and target; one
-    // (comp >= 0) or eight FP64 outputs written
+    // about 128 flop for the quotient rule (30), det (14), the symmetric
+    // metric (30), the adjugate with the Gauss weight (26), the target (about
+    // 24 with exp) and the products; one (comp >= 0) or eight FP64 outputs
     prof_count(ctx, (double)total * 8.0 * (comp < 0 ? 8 : 1),
-               (double)total * (32.0 * (G.pg[0] + 1) + 150.0));
+               (double)total * (32.0 * (G.pg[0] + 1) + 128.0));
     IGA_LAUNCH(ctx, sample_weights_kernel, (unsigned)((total + threads - 1) / threads), threads, 0,
                G, out, ctx->dflag);
     IGA_CUDA(cudaMemcpyAsync(ctx->hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost,
