@@ -175,15 +175,16 @@ template <typename T, int P>
 static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y) {
   KronTile g{};
   g.n1 = A->n[0]; g.n2 = A->n[1]; g.n3 = A->n[2];
-  // (i1, i2) tile edge from 8..16 minimising the mode-product work per term:
+  // (i1, i2) tile edge from 8..40 minimising the mode-product work per term:
   // tiles^2 x ((T + 2P)^2 halo points of mode 3 + (T + 2P) T of mode 2 + T^2 of
   // mode 1), so that the halo share and the empty part of the last tile stay
-  // small (n = 65 takes 13 x 13 tiles, 35 % less work than 8 x 8)
+  // small (n = 65 takes 33 x 33 tiles: 1.19 times the work of an unbounded
+  // tile, against 1.94 for 8 x 8)
   auto pick = [](int n) {
     if (n <= 8) return n;
     int best = 8;
     double bestw = 1e300;
-    for (int t = 8; t <= 16; ++t) {
+    for (int t = 8; t <= 40; ++t) {
       double nt = (double)((n + t - 1) / t);
       double h = t + 2 * P;
       double w = nt * nt * (h * h + h * t + (double)t * t);    // both directions tiled alike
@@ -204,11 +205,14 @@ static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T bet
   }
   int nchunks = (g.n3 + maxT3 - 1) / maxT3;
   {
-    // enough CTAs to cover every SM twice, down to i3 tiles of 4 (the i3
-    // halo of mode 3 is read through L1, not recomputed)
+    // enough CTAs to cover every SM twice and tiles small enough for the
+    // 8-output register variant, down to i3 tiles of one (the i3 halo of
+    // mode 3 is read through L1, not recomputed)
     int base = ((g.n1 + g.T1 - 1) / g.T1) * ((g.n2 + g.T2 - 1) / g.T2);
-    int maxchunks = std::max(1, g.n3 / 4);
-    while (base * nchunks < 2 * 152 && nchunks < maxchunks) ++nchunks;
+    auto t3 = [&](int c) { return (g.n3 + c - 1) / c; };
+    while (nchunks < g.n3 &&
+           (base * nchunks < 2 * 152 || (size_t)g.T1 * g.T2 * t3(nchunks) > 8 * KRON_THREADS))
+      ++nchunks;
   }
   g.T3 = (g.n3 + nchunks - 1) / nchunks;
   g.nt2 = (g.n2 + g.T2 - 1) / g.T2;
