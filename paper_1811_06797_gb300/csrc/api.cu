@@ -185,6 +185,12 @@ static void kkt_apply_impl(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   void* o3 = oc + 2 * N * es;
   // K is symmetric by construction (the (k,l) and (l,k) blocks share the
   // weight q_kl = q_lk and have transposed factors), so K^T = K.
+  {
+    const char* ze = zc + 3 * N * es;
+    const char* oe = oc + 3 * N * es;
+    IGA_REQUIRE(ze <= oc || oe <= zc, "kkt_apply: z and out must not overlap");
+  }
+  if (kkt_apply_fused(ctx, M, K, beta, z, out, prec)) return;
   kron_apply_impl(ctx, M, 1.0, y, 0.0, o1, prec);
   kron_apply_impl(ctx, K, 1.0, l, 1.0, o1, prec);
   kron_apply_impl(ctx, M, beta, u, 0.0, o2, prec);
@@ -324,6 +330,7 @@ iga_status iga_create(iga_ctx** out, void* stream) {
     ctx = new iga_ctx();
     ctx->stream = static_cast<cudaStream_t>(stream);
     IGA_CUDA(cudaGetDevice(&ctx->device));
+    IGA_CUDA(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     IGA_BLAS(cublasCreate(&ctx->blas));
     IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
     IGA_CUDA(cudaMalloc((void**)&ctx->dflag, 64 * sizeof(int)));

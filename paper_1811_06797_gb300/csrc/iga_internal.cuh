@@ -118,6 +118,7 @@ struct OpBlock {
 struct iga_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
+  int nsm = 1;                              // SMs of the device
   std::string err;
   uint64_t launches = 0;
   cublasHandle_t blas = nullptr;
@@ -248,6 +249,10 @@ void kkt_apply_internal(iga_ctx* ctx, const iga_op* M, const iga_op* K, double b
                         void* out, iga_prec prec);
 
 // kron.cu
+// the KKT operator on (y, u, lambda) in one fused launch when M and K are
+// rank-1 Kronecker sums (false: not applicable, nothing launched)
+bool kkt_apply_fused(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta, const void* z,
+                     void* out, iga_prec prec);
 void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
                      void* y, iga_prec prec);
 

@@ -12,6 +12,9 @@
 // once.  TT-matrix blocks (ranks > 1) use staged single-mode products with
 // full-size intermediates.
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "iga_internal.cuh"
 
@@ -19,24 +22,34 @@ namespace iga {
 
 constexpr int KRON_MAXTERMS = 32;
 constexpr int KRON_THREADS = 256;
-constexpr int KRON_MAXOUT = 32;    // outputs per thread held in registers
+constexpr int KRON_MO = 8;         // outputs per thread and output field held in registers
 
+// One launch of the fused rank-1 apply.  Term t reads input x[xin[t]], forms
+// its three banded mode products on the tile and adds coef[t][o] times the
+// result to output o (o < NY); finally y[o] = acc_o + beta[o] y[o].  One
+// operator is NY = 1 with one input; the KKT operator is NY = 3 with the
+// three fields as inputs, so that each product feeds every block row that
+// uses it (M u enters rows two and three).
 template <typename T>
-struct KronTerms {
+struct KronJob {
   const T* b[3][KRON_MAXTERMS];
+  T coef[KRON_MAXTERMS][3];
+  unsigned char xin[KRON_MAXTERMS];
   int nterms;
+  const T* x[3];
+  T* y[3];
+  T beta[3];
 };
 
 struct KronTile {
   int n1, n2, n3;
   int T1, T2, T3;
-  int nt2, nt3;     // tiles along 2 and 3
+  int nt1, nt2, nt3;     // tiles along 1, 2 and 3
 };
 
-template <typename T, int P, int MO>
+template <typename T, int P, int NY>
 __global__ void __launch_bounds__(KRON_THREADS)
-kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __restrict__ x,
-                  T* __restrict__ y) {
+kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
   constexpr int B = 2 * P + 1;
   extern __shared__ unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -54,14 +67,18 @@ kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __re
   const int I1 = t1 * T1, I2 = t2 * T2, I3 = t3 * T3;
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
   const int nout = T1 * T2 * T3;
-  T acc[MO];
+  T acc[NY][KRON_MO];
 #pragma unroll
-  for (int k = 0; k < MO; ++k) acc[k] = T(0);
+  for (int o = 0; o < NY; ++o)
+#pragma unroll
+    for (int k = 0; k < KRON_MO; ++k) acc[o][k] = T(0);
 
-  for (int t = 0; t < terms.nterms; ++t) {
-    const T* A1 = terms.b[0][t];
-    const T* A2 = terms.b[1][t];
-    const T* A3 = terms.b[2][t];
+  for (int t = 0; t < job.nterms; ++t) {
+    const T* A1 = job.b[0][t];
+    const T* A2 = job.b[1][t];
+    const T* A3 = job.b[2][t];
+    const int xi = job.xin[t];
+    const T* __restrict__ x = xi == 0 ? job.x[0] : (xi == 1 ? job.x[1] : job.x[2]);
     for (int idx = threadIdx.x; idx < (T1 + T2 + T3) * B; idx += blockDim.x) {
       int r = idx / B, o = idx - r * B;
       T v = T(0);
@@ -88,20 +105,27 @@ kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __re
       z3[idx] = s;
     }
     __syncthreads();
-    // mode 2: z2[a][c][k] = sum_o A2(I2+c, I2+c+o-P) z3[a][c+o][k]
+    // mode 2: z2[a][c][k] = sum_o A2(I2+c, I2+c+o-P) z3[a][c+o][k]; rows a
+    // outside the domain and columns past n2 stay zero without arithmetic
     for (int idx = threadIdx.x; idx < H1 * T2 * T3; idx += blockDim.x) {
       int k = idx % T3;
       int ac = idx / T3;
       int c = ac % T2, a = ac / T2;
+      int j1 = I1 + a - P;
       T s = T(0);
+      if (j1 >= 0 && j1 < n1 && I2 + c < n2) {
 #pragma unroll
-      for (int o = 0; o < B; ++o) s += a2[c * B + o] * z3[((size_t)a * H2 + c + o) * T3 + k];
+        for (int o = 0; o < B; ++o) s += a2[c * B + o] * z3[((size_t)a * H2 + c + o) * T3 + k];
+      }
       z2[idx] = s;
     }
     __syncthreads();
-    // mode 1 into the register accumulators
+    // mode 1 into the register accumulators of every output the term feeds
+    T cf[NY];
 #pragma unroll
-    for (int m = 0; m < MO; ++m) {
+    for (int o = 0; o < NY; ++o) cf[o] = job.coef[t][o];
+#pragma unroll
+    for (int m = 0; m < KRON_MO; ++m) {
       int idx = threadIdx.x + m * KRON_THREADS;
       if (idx < nout) {
         int k = idx % T3;
@@ -110,13 +134,15 @@ kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __re
         T s = T(0);
 #pragma unroll
         for (int o = 0; o < B; ++o) s += a1[a * B + o] * z2[((size_t)(a + o) * T2 + c) * T3 + k];
-        acc[m] += s;
+#pragma unroll
+        for (int o = 0; o < NY; ++o)
+          if (cf[o] != T(0)) acc[o][m] += cf[o] * s;
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int m = 0; m < MO; ++m) {
+  for (int m = 0; m < KRON_MO; ++m) {
     int idx = threadIdx.x + m * KRON_THREADS;
     if (idx < nout) {
       int k = idx % T3;
@@ -124,10 +150,13 @@ kron_rank1_kernel(KronTerms<T> terms, KronTile g, T alpha, T beta, const T* __re
       int c = ac % T2, a = ac / T2;
       int i1 = I1 + a, i2 = I2 + c, i3 = I3 + k;
       if (i1 < n1 && i2 < n2 && i3 < n3) {
-        size_t o = ((size_t)i1 * n2 + i2) * n3 + i3;
-        T v = alpha * acc[m];
-        if (beta != T(0)) v += beta * y[o];
-        y[o] = v;
+        size_t off = ((size_t)i1 * n2 + i2) * n3 + i3;
+#pragma unroll
+        for (int o = 0; o < NY; ++o) {
+          T v = acc[o][m];
+          if (job.beta[o] != T(0)) v += job.beta[o] * job.y[o][off];
+          job.y[o][off] = v;
+        }
       }
     }
   }
@@ -164,6 +193,90 @@ __global__ void mode_product_kernel(const T* __restrict__ A, int mode, int n1, i
   y[idx] = accumulate ? y[idx] + alpha * s : alpha * s;
 }
 
+// Tile of the fused apply: edges T1, T2 in 8..40 and T3 >= 1 with at most
+// KRON_MO x KRON_THREADS outputs, minimising the busiest SM's work, i.e.
+// ceil(CTAs / SMs) times the mode-product points of an interior tile.  Halo
+// rows outside the domain cost nothing (the kernel skips them), so a
+// direction covered by one or two tiles pays little halo.  Ties go to the
+// thicker i3 slab, which re-reads less of the x halo.
+static KronTile choose_tile(int n1, int n2, int n3, int P, int nsm) {
+  struct Key { int n1, n2, n3, P, nsm; };
+  static std::mutex mu;
+  static std::vector<std::pair<Key, KronTile>> cache;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : cache)
+      if (e.first.n1 == n1 && e.first.n2 == n2 && e.first.n3 == n3 && e.first.P == P &&
+          e.first.nsm == nsm)
+        return e.second;
+  }
+  auto span = [](int n, int T, int P) {
+    // rows of the halo slab [I - P, I + T + P) inside [0, n) for the most
+    // expensive tile (an interior one when there are three or more)
+    int nt = (n + T - 1) / T;
+    if (nt == 1) return std::min(n, T);
+    if (nt == 2) return std::min(n, T + P);
+    return T + 2 * P;
+  };
+  KronTile best{};
+  double bestc = 1e300;
+  for (int t1 = std::min(n1, 8); t1 <= std::min(n1, 40); ++t1)
+    for (int t2 = std::min(n2, 8); t2 <= std::min(n2, 40); ++t2) {
+      int h1 = span(n1, t1, P), h2 = span(n2, t2, P);
+      int nt12 = ((n1 + t1 - 1) / t1) * ((n2 + t2 - 1) / t2);
+      int max3 = std::min(n3, KRON_MO * KRON_THREADS / (t1 * t2));
+      for (int t3 = 1; t3 <= max3; ++t3) {
+        int nt3 = (n3 + t3 - 1) / t3;
+        if (nt3 > 1 && (n3 + nt3 - 1) / nt3 != t3) continue;    // balanced slabs only
+        double w = (double)t3 * ((double)h1 * h2 + (double)h1 * t2 + (double)t1 * t2);
+        double waves = std::ceil((double)nt12 * nt3 / nsm);
+        double c = waves * w;
+        if (c < bestc * (1.0 - 1e-9) || (c <= bestc * (1.0 + 1e-9) && t3 > best.T3)) {
+          bestc = c;
+          best.T1 = t1; best.T2 = t2; best.T3 = t3;
+        }
+      }
+    }
+  best.n1 = n1; best.n2 = n2; best.n3 = n3;
+  best.nt1 = (n1 + best.T1 - 1) / best.T1;
+  best.nt2 = (n2 + best.T2 - 1) / best.T2;
+  best.nt3 = (n3 + best.T3 - 1) / best.T3;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache.size() > 64) cache.clear();
+  cache.push_back({Key{n1, n2, n3, P, nsm}, best});
+  return best;
+}
+
+template <typename T, int P, int NY>
+static void launch_kron_job(iga_ctx* ctx, const KronJob<T>& job, const KronTile& g) {
+  constexpr int B = 2 * P + 1;
+  size_t H1 = g.T1 + 2 * P, H2 = g.T2 + 2 * P;
+  size_t smem = (H1 * H2 * g.T3 + H1 * g.T2 * g.T3 + (size_t)(g.T1 + g.T2 + g.T3) * B) * sizeof(T);
+  IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: tile does not fit in shared memory");
+  static bool attr_set = false;
+  if (!attr_set) {
+    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P, NY>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set = true;
+  }
+  {
+    // algorithmic: read every input, write every output (and read it when
+    // accumulating); 3 banded mode products of 2(2P+1) flop per point and term
+    double N = (double)g.n1 * g.n2 * g.n3;
+    int nin = 0;
+    for (int i = 0; i < 3; ++i) {
+      bool used = false;
+      for (int t = 0; t < job.nterms; ++t) used |= job.xin[t] == i;
+      nin += used;
+    }
+    double outs = 0.0;
+    for (int o = 0; o < NY; ++o) outs += job.beta[o] != T(0) ? 2.0 : 1.0;
+    prof_count(ctx, N * sizeof(T) * (nin + outs), 6.0 * B * N * job.nterms);
+  }
+  IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P, NY>), (unsigned)(g.nt1 * g.nt2 * g.nt3), KRON_THREADS,
+             smem, job, g);
+}
+
 template <typename T>
 static const T* band_ptr(const iga_op* A, int d, size_t k) {
   size_t len = (size_t)A->n[d] * (2 * A->p[d] + 1);
@@ -173,89 +286,60 @@ static const T* band_ptr(const iga_op* A, int d, size_t k) {
 
 template <typename T, int P>
 static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y) {
-  KronTile g{};
-  g.n1 = A->n[0]; g.n2 = A->n[1]; g.n3 = A->n[2];
-  // (i1, i2) tile edge from 8..40 minimising the mode-product work per term:
-  // tiles^2 x ((T + 2P)^2 halo points of mode 3 + (T + 2P) T of mode 2 + T^2 of
-  // mode 1), so that the halo share and the empty part of the last tile stay
-  // small (n = 65 takes 33 x 33 tiles: 1.19 times the work of an unbounded
-  // tile, against 1.94 for 8 x 8)
-  auto pick = [](int n) {
-    if (n <= 8) return n;
-    int best = 8;
-    double bestw = 1e300;
-    for (int t = 8; t <= 40; ++t) {
-      double nt = (double)((n + t - 1) / t);
-      double h = t + 2 * P;
-      double w = nt * nt * (h * h + h * t + (double)t * t);    // both directions tiled alike
-      if (w < bestw - 1e-9) { bestw = w; best = t; }
-    }
-    return best;
-  };
-  g.T1 = pick(g.n1);
-  g.T2 = pick(g.n2);
-  constexpr int Bw = 2 * P + 1;
-  int maxT3 = KRON_MAXOUT * KRON_THREADS / (g.T1 * g.T2);
-  {
-    // shared memory: (H1 H2 + H1 T2 + B) T3 + (T1 + T2) B elements of T
-    size_t budget = 220 * 1024 / sizeof(T);
-    size_t per3 = (size_t)(g.T1 + 2 * P) * (g.T2 + 2 * P) + (size_t)(g.T1 + 2 * P) * g.T2 + Bw;
-    int m3 = (int)((budget - (size_t)(g.T1 + g.T2) * Bw) / per3);
-    maxT3 = std::min(maxT3, m3);
-  }
-  int nchunks = (g.n3 + maxT3 - 1) / maxT3;
-  {
-    // enough CTAs to cover every SM twice and tiles small enough for the
-    // 8-output register variant, down to i3 tiles of one (the i3 halo of
-    // mode 3 is read through L1, not recomputed)
-    int base = ((g.n1 + g.T1 - 1) / g.T1) * ((g.n2 + g.T2 - 1) / g.T2);
-    auto t3 = [&](int c) { return (g.n3 + c - 1) / c; };
-    while (nchunks < g.n3 &&
-           (base * nchunks < 2 * 152 || (size_t)g.T1 * g.T2 * t3(nchunks) > 8 * KRON_THREADS))
-      ++nchunks;
-  }
-  g.T3 = (g.n3 + nchunks - 1) / nchunks;
-  g.nt2 = (g.n2 + g.T2 - 1) / g.T2;
-  g.nt3 = (g.n3 + g.T3 - 1) / g.T3;
-  int nt1 = (g.n1 + g.T1 - 1) / g.T1;
-  constexpr int B = 2 * P + 1;
-  size_t H1 = g.T1 + 2 * P, H2 = g.T2 + 2 * P;
-  size_t smem = (H1 * H2 * g.T3 + H1 * g.T2 * g.T3 + (size_t)(g.T1 + g.T2 + g.T3) * B) * sizeof(T);
-  IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: tile does not fit in shared memory");
-  // register accumulators: 8 outputs per thread when the tile allows, which
-  // leaves registers for more resident CTAs
-  const bool small = (size_t)g.T1 * g.T2 * g.T3 <= 8 * KRON_THREADS;
-  static bool attr_set = false;
-  if (!attr_set) {
-    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P, 8>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P, KRON_MAXOUT>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set = true;
-  }
+  KronTile g = choose_tile(A->n[0], A->n[1], A->n[2], P, ctx->nsm);
   // terms in chunks of KRON_MAXTERMS (beta applies to the first chunk only)
   size_t nterm = A->blocks.size();
   for (size_t c0 = 0; c0 < nterm || c0 == 0; c0 += KRON_MAXTERMS) {
-    KronTerms<T> terms{};
+    KronJob<T> job{};
     int cnt = 0;
-    for (size_t t = c0; t < std::min(nterm, c0 + KRON_MAXTERMS); ++t, ++cnt)
-      for (int d = 0; d < 3; ++d) terms.b[d][cnt] = band_ptr<T>(A, d, A->blocks[t].off[d]);
-    terms.nterms = cnt;
-    T bt = (c0 == 0) ? beta : T(1);
-    {
-      // algorithmic: read x, write y (read y too when accumulating); 3 banded
-      // mode products of 2(2P+1) flop per point and term
-      double N = (double)g.n1 * g.n2 * g.n3;
-      prof_count(ctx, N * sizeof(T) * (bt != T(0) ? 3.0 : 2.0), 6.0 * (2 * P + 1) * N * cnt);
+    for (size_t t = c0; t < std::min(nterm, c0 + KRON_MAXTERMS); ++t, ++cnt) {
+      for (int d = 0; d < 3; ++d) job.b[d][cnt] = band_ptr<T>(A, d, A->blocks[t].off[d]);
+      job.coef[cnt][0] = alpha;
+      job.xin[cnt] = 0;
     }
-    if (small)
-      IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P, 8>), (unsigned)(nt1 * g.nt2 * g.nt3), KRON_THREADS,
-                 smem, terms, g, alpha, bt, x, y);
-    else
-      IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P, KRON_MAXOUT>), (unsigned)(nt1 * g.nt2 * g.nt3),
-                 KRON_THREADS, smem, terms, g, alpha, bt, x, y);
+    job.nterms = cnt;
+    job.x[0] = job.x[1] = job.x[2] = x;
+    job.y[0] = job.y[1] = job.y[2] = y;
+    job.beta[0] = (c0 == 0) ? beta : T(1);
+    launch_kron_job<T, P, 1>(ctx, job, g);
     if (nterm == 0) break;
   }
+}
+
+// The KKT operator [[M, 0, K^T], [0, beta M, -M], [K, -M, 0]] on z = (y, u,
+// lambda) in one launch when M and K are rank-1 Kronecker sums: the products
+// M y, M u, M lambda, K y and K lambda (K^T = K) are each formed once and
+// added to the block rows that use them.
+template <typename T, int P>
+static void kkt_rank1(iga_ctx* ctx, const iga_op* M, const iga_op* K, T beta, const T* z,
+                      T* out) {
+  KronTile g = choose_tile(M->n[0], M->n[1], M->n[2], P, ctx->nsm);
+  size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
+  KronJob<T> job{};
+  int cnt = 0;
+  auto add = [&](const iga_op* A, int xin, T c0, T c1, T c2) {
+    for (const OpBlock& blk : A->blocks) {
+      for (int d = 0; d < 3; ++d) job.b[d][cnt] = band_ptr<T>(A, d, blk.off[d]);
+      job.xin[cnt] = (unsigned char)xin;
+      job.coef[cnt][0] = c0;
+      job.coef[cnt][1] = c1;
+      job.coef[cnt][2] = c2;
+      ++cnt;
+    }
+  };
+  // terms grouped by input so that the x halo of one input stays in L1
+  add(M, 0, T(1), T(0), T(0));       // M y      -> row 1
+  add(K, 0, T(0), T(0), T(1));       // K y      -> row 3
+  add(M, 1, T(0), beta, T(-1));      // M u      -> rows 2 and 3
+  add(M, 2, T(0), T(-1), T(0));      // M lambda -> row 2
+  add(K, 2, T(1), T(0), T(0));       // K lambda -> row 1
+  job.nterms = cnt;
+  for (int i = 0; i < 3; ++i) {
+    job.x[i] = z + i * N;
+    job.y[i] = out + i * N;
+    job.beta[i] = T(0);
+  }
+  launch_kron_job<T, P, 3>(ctx, job, g);
 }
 
 template <typename T, int P>
@@ -427,6 +511,33 @@ static void kron_dispatch(iga_ctx* ctx, const iga_op* A, double alpha, const voi
     default:
       throw Error(IGA_EINVAL, "kron_apply: degree must be 1..4");
   }
+}
+
+template <typename T>
+static bool kkt_dispatch(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                         const void* z, void* out) {
+  int P = M->p[0];
+  for (int d = 0; d < 3; ++d)
+    if (M->p[d] != P || K->p[d] != P || M->n[d] != K->n[d]) return false;
+  if (!M->rank1 || !K->rank1 || M->blocks.empty() || K->blocks.empty() ||
+      3 * M->blocks.size() + 2 * K->blocks.size() > (size_t)KRON_MAXTERMS)
+    return false;
+  const T* zz = static_cast<const T*>(z);
+  T* oo = static_cast<T*>(out);
+  switch (P) {
+    case 1: kkt_rank1<T, 1>(ctx, M, K, (T)beta, zz, oo); return true;
+    case 2: kkt_rank1<T, 2>(ctx, M, K, (T)beta, zz, oo); return true;
+    case 3: kkt_rank1<T, 3>(ctx, M, K, (T)beta, zz, oo); return true;
+    case 4: kkt_rank1<T, 4>(ctx, M, K, (T)beta, zz, oo); return true;
+    default: return false;
+  }
+}
+
+bool kkt_apply_fused(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta, const void* z,
+                     void* out, iga_prec prec) {
+  if (prec == IGA_FP64) return kkt_dispatch<double>(ctx, M, K, beta, z, out);
+  if (prec == IGA_FP32) return kkt_dispatch<float>(ctx, M, K, beta, z, out);
+  return false;
 }
 
 void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,

@@ -94,6 +94,28 @@ def test_kkt_apply_against_oracle_assembly(env):
     assert np.linalg.norm(out.cpu().numpy() - ref) < 1e-11 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("p,E", [(3, 14), (2, 19)])
+def test_kkt_apply_fused_rank1(env, p, E):
+    """Rank-1 M and K (quarter annulus): the whole KKT operator is one fused
+    launch over ragged multi-tile grids, in FP64 and FP32."""
+    ctx, torch, iga = env
+    work = wl.small(wl.quarter_annulus(), p, E, beta=1e-3)
+    M, K, _ = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, 1e-12)
+    disc = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+    Mb, Kb, _ = assemble_band(work.geometry, disc)
+    A = kkt_matrix(band_to_csr(Mb, True), band_to_csr(Kb, True), work.beta)
+    z = np.random.default_rng(5).standard_normal(A.shape[0])
+    ref = A @ z
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 5e-6)):
+        out = torch.empty(A.shape[0], dtype=dt, device="cuda")
+        ctx.profile_begin("kron_rank1_kernel")
+        iga.iga_kkt_apply(ctx, M, K, work.beta, torch.tensor(z, device="cuda", dtype=dt), out)
+        prof = ctx.profile_end()
+        assert prof["launches"] == 1, prof
+        err = np.linalg.norm(out.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < tol, (dt, err)
+
+
 @pytest.mark.parametrize("r0,n,r1,R0,R1,p,nvec", [(1, 17, 5, 1, 3, 2, 3), (6, 11, 7, 3, 2, 3, 2),
                                                  (9, 20, 1, 4, 1, 1, 1), (16, 33, 12, 2, 2, 3, 3)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
