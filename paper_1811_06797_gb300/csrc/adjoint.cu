@@ -345,6 +345,7 @@ using namespace iga;
 
 #define IGA_TRY2(ctx, ...)                                                        \
   try {                                                                           \
+    ::iga::AllocScope scope__((ctx)->stream);                                     \
     __VA_ARGS__;                                                                  \
     return IGA_OK;                                                                \
   } catch (const ::iga::Error& e) {                                               \

@@ -970,7 +970,7 @@ struct CoreNZ {
   DevBuf<long long> doff, rowoff, coloff;
 };
 
-static void build_core_nz(const iga_op* op, int d, CoreNZ& c) {
+static void build_core_nz(iga_ctx* ctx, const iga_op* op, int d, CoreNZ& c) {
   c.l.clear(); c.r.clear(); c.off.clear();
   size_t len = (size_t)op->n[d] * (2 * op->p[d] + 1);
   int a0 = 0, b0 = 0;
@@ -1011,11 +1011,12 @@ static void build_core_nz(const iga_op* op, int d, CoreNZ& c) {
     int pc = cf[c.r[z]]++;
     cs[pc] = c.l[z]; co[pc] = c.off[z];
   }
-  auto up = [](auto& buf, const auto& v) {
+  auto up = [ctx](auto& buf, const auto& v) {
     using E = typename std::decay_t<decltype(v)>::value_type;
     buf.alloc(std::max<size_t>(1, v.size()));
     if (!v.empty())
-      IGA_CUDA(cudaMemcpy(buf.p, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice));
+      IGA_CUDA(cudaMemcpyAsync(buf.p, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice,
+                               ctx->stream));
   };
   up(c.dl, c.l); up(c.dr, c.r); up(c.doff, c.off);
   up(c.rowptr, rp); up(c.rowsrc, rs); up(c.rowoff, ro);
@@ -1854,7 +1855,7 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   S.verbose = o->verbose;
   size_t N = S.N;
   for (int op = 0; op < 2; ++op)
-    for (int d = 0; d < 3; ++d) build_core_nz(S.op[op], d, S.nz[op][d]);
+    for (int d = 0; d < 3; ++d) build_core_nz(ctx, S.op[op], d, S.nz[op][d]);
   // initial TT: rank kick Gaussian cores, right-orthogonalised by QR; block index at core 0
   int r0 = std::min({S.kick, S.n[0], S.n[1] * S.n[2]});
   int r1 = std::min({S.kick, S.n[2], S.n[0] * S.n[1]});
@@ -1968,6 +1969,7 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
   if (!ctx) return IGA_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
   try {
+    AllocScope scope(ctx->stream);
     IGA_REQUIRE(M && K && y && u && lam, "kkt_solve_amen: null argument");
     IGA_REQUIRE(beta > 0.0, "kkt_solve_amen: beta must be positive");
     for (int d = 0; d < 3; ++d)

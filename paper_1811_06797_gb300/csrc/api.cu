@@ -7,6 +7,8 @@
 // K = sum_{k,l} sum (x)_d K_kl^(d) with the core slices of eq. TTranks.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "iga_internal.cuh"
@@ -303,10 +305,77 @@ void ops_from_weights_impl(iga_ctx* ctx, const SpaceTables& st, const iga_tt* co
 
 }  // namespace iga
 
+namespace iga {
+
+namespace {
+thread_local cudaStream_t t_alloc_stream = nullptr;
+thread_local bool t_alloc_active = false;
+
+// one stream-ordered pool per device, keeping up to 4 GB of released memory
+// cached across synchronisations
+cudaMemPool_t device_pool() {
+  int dev = 0;
+  IGA_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  IGA_CUDA(cudaMemPoolCreate(&pool, &props));
+  uint64_t keep = 4ull << 30;
+  IGA_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  pools[dev] = pool;
+  return pool;
+}
+}  // namespace
+
+AllocScope::AllocScope(cudaStream_t s) : prev_stream(t_alloc_stream), prev_active(t_alloc_active) {
+  t_alloc_stream = s;
+  t_alloc_active = true;
+}
+
+AllocScope::~AllocScope() {
+  t_alloc_stream = prev_stream;
+  t_alloc_active = prev_active;
+}
+
+void* dev_alloc(size_t bytes, bool* pooled) {
+  void* p = nullptr;
+  if (t_alloc_active) {
+    IGA_CUDA(cudaMallocFromPoolAsync(&p, bytes, device_pool(), t_alloc_stream));
+    *pooled = true;
+  } else {
+    IGA_CUDA(cudaMalloc(&p, bytes));
+    *pooled = false;
+  }
+  return p;
+}
+
+void dev_free(void* p, bool pooled) noexcept {
+  if (!p) return;
+  if (!pooled) {
+    cudaFree(p);
+  } else if (t_alloc_active) {
+    cudaFreeAsync(p, t_alloc_stream);
+  } else {
+    // released outside any entry: the stream that used it is unknown
+    cudaDeviceSynchronize();
+    cudaFree(p);
+  }
+}
+
+}  // namespace iga
+
 using namespace iga;
 
 #define IGA_TRY(ctx, ...)                                                         \
   try {                                                                           \
+    ::iga::AllocScope scope__((ctx)->stream);                                     \
     __VA_ARGS__;                                                                  \
     return IGA_OK;                                                                \
   } catch (const ::iga::Error& e) {                                               \
@@ -405,7 +474,10 @@ iga_status iga_sample_weights(iga_ctx* ctx, const iga_geometry* geo, const iga_s
 iga_status iga_tt_svd(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol,
                       double norm_ref, int rmax, iga_tt** out) {
   if (!ctx) return IGA_EINVAL;
-  IGA_TRY(ctx, tt_svd3(ctx, W, n1, n2, n3, tol, norm_ref, rmax, out))
+  IGA_TRY(ctx, {
+    tt_svd3(ctx, W, n1, n2, n3, tol, norm_ref, rmax, out);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));   // the handle is usable on any stream
+  })
 }
 
 iga_status iga_tt_info(const iga_tt* tt, int n[3], int r[2]) {
@@ -455,6 +527,7 @@ iga_status iga_weight_tts(iga_ctx* ctx, const iga_geometry* geo, const iga_space
     SpaceTables st;
     build_space_tables(ctx, space, st);
     weight_tts_impl(ctx, geo, st, target, tol, out);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
   })
 }
 
@@ -503,6 +576,7 @@ iga_status iga_ops_from_weights(iga_ctx* ctx, const iga_space* space,
           IGA_REQUIRE(weights[c]->n[d] == st.dir[d].E * st.dir[d].q,
                       "ops_from_weights: weight TT is not on the Gauss grid of the space");
     ops_from_weights_impl(ctx, st, weights, M, K);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
   })
 }
 
@@ -514,6 +588,7 @@ iga_status iga_load_from_density(iga_ctx* ctx, const iga_space* space, const iga
     SpaceTables st;
     build_space_tables(ctx, space, st);
     *load = load_tt(ctx, st, density);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
   })
 }
 
@@ -549,6 +624,7 @@ iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga
         throw;
       }
     }
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));   // the handles are usable on any stream
   })
 }
 

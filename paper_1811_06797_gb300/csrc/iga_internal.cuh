@@ -60,29 +60,53 @@ struct Error : public std::runtime_error {
     IGA_CUDA(cudaGetLastError());                                                \
   } while (0)
 
+// Device memory of the library.  While a C-ABI entry runs (an AllocScope on
+// its context stream is active on the calling thread), buffers come from a
+// per-device stream-ordered pool: allocation and release are queued on that
+// stream, so freeing a temporary does not wait for the device to drain (a
+// plain cudaFree synchronises the whole device).  Every use of such a buffer
+// is on the same stream, and an entry that returns a handle synchronises its
+// stream first.  Outside an entry (a handle destroyed by the caller) a pooled
+// buffer is freed after a device synchronisation.
+struct AllocScope {
+  explicit AllocScope(cudaStream_t s);
+  ~AllocScope();
+  AllocScope(const AllocScope&) = delete;
+  AllocScope& operator=(const AllocScope&) = delete;
+  cudaStream_t prev_stream;
+  bool prev_active;
+};
+void* dev_alloc(size_t bytes, bool* pooled);
+void dev_free(void* p, bool pooled) noexcept;
+
 // Device buffer owned by RAII (library-internal allocations only).
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  bool pooled = false;
   DevBuf() = default;
   explicit DevBuf(size_t count) { alloc(count); }
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), pooled(o.pooled) { o.p = nullptr; o.n = 0; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) {
+      release();
+      p = o.p; n = o.n; pooled = o.pooled;
+      o.p = nullptr; o.n = 0;
+    }
     return *this;
   }
   void alloc(size_t count) {
     release();
     if (count == 0) return;
-    IGA_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+    p = static_cast<T*>(dev_alloc(count * sizeof(T), &pooled));
     n = count;
   }
   void ensure(size_t count) { if (count > n) alloc(count); }
-  void release() {
-    if (p) cudaFree(p);
+  void release() noexcept {
+    if (p) dev_free(p, pooled);
     p = nullptr;
     n = 0;
   }

@@ -140,6 +140,7 @@ extern "C" iga_status iga_amen_local_matvec(iga_ctx* ctx, int r0, int n, int r1,
                                             int nvec, const void* x, void* y, iga_prec prec) {
   if (!ctx) return IGA_EINVAL;
   try {
+    AllocScope scope(ctx->stream);
     IGA_REQUIRE(r0 > 0 && n > 0 && r1 > 0 && R0 > 0 && R1 > 0 && p >= 0 && nvec > 0,
                 "local_matvec: sizes must be positive");
     IGA_REQUIRE(PhiL && bands && PhiR && x && y, "local_matvec: null pointer");
