@@ -880,8 +880,9 @@ static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K,
 // group of 16, b), threads stride over k with 16 accumulators; tout stores
 // C_b^T instead.
 // coldot: C_b (M x N) = A^T B_b, A row-major (K x M), B_b row-major (K x N);
-// block (chunk of 16 k, row group of 16, b), threads over j, partial sums
-// per chunk, then a reduction over the chunks.
+// block (chunk of k, row group of 16, b), threads over j, partial sums per
+// chunk, then a reduction over the chunks (chunk length chosen at launch so
+// that every SM gets a few blocks).
 constexpr int PROJ_G = 16;
 constexpr int PROJ_KC = 16;
 
@@ -922,15 +923,54 @@ __global__ void __launch_bounds__(256) rowdot_kernel(const double* __restrict__ 
   }
 }
 
+// rowdot for short K: one warp per row i (lanes over k), 16 columns per
+// block y; the 16 sums are reduced over the warp and lane c writes column c
+__global__ void __launch_bounds__(256) rowdot_warp_kernel(const double* __restrict__ A, int lda,
+                                                          long long sA,
+                                                          const double* __restrict__ B, int ldb,
+                                                          long long sB, int nsum, int K, int M,
+                                                          int N, double* __restrict__ C, int ldc,
+                                                          long long sC, int tout) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int c0 = blockIdx.y * PROJ_G, b = blockIdx.z;
+  if (i >= M) return;                         // whole warps only
+  const int nc = min(PROJ_G, N - c0);
+  double acc[PROJ_G];
+#pragma unroll
+  for (int c = 0; c < PROJ_G; ++c) acc[c] = 0.0;
+  for (int q = 0; q < nsum; ++q) {
+    const double* a = A + (b * nsum + q) * sA + (size_t)i * lda;
+    const double* Bq = B + q * sB + (size_t)c0 * ldb;
+    for (int k = lane; k < K; k += 32) {
+      const double av = a[k];
+#pragma unroll
+      for (int c = 0; c < PROJ_G; ++c)
+        if (c < nc) acc[c] = fma(av, Bq[(size_t)c * ldb + k], acc[c]);
+    }
+  }
+  double mine = 0.0;
+#pragma unroll
+  for (int c = 0; c < PROJ_G; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == c) mine = v;
+  }
+  if (lane < nc) {
+    const int c = c0 + lane;
+    C[b * sC + (tout ? (size_t)c * ldc + i : (size_t)i * ldc + c)] = mine;
+  }
+}
+
 __global__ void __launch_bounds__(256) coldot_kernel(const double* __restrict__ A, int lda,
                                                      const double* __restrict__ B, int ldb,
-                                                     long long sB, int K, int M, int N,
+                                                     long long sB, int K, int M, int N, int kc,
                                                      double* __restrict__ P) {
   // P[(chunk * nb + b) * M * N + i * N + j]
   const int chunk = blockIdx.x, i0 = blockIdx.y * PROJ_G, b = blockIdx.z;
   const int nchunk = gridDim.x, nb = gridDim.z;
   const int mi = min(PROJ_G, M - i0);
-  const int k0 = chunk * PROJ_KC, k1 = min(K, k0 + PROJ_KC);
+  const int k0 = chunk * kc, k1 = min(K, k0 + kc);
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     double acc[PROJ_G];
 #pragma unroll
@@ -948,17 +988,86 @@ __global__ void __launch_bounds__(256) coldot_kernel(const double* __restrict__ 
   (void)nchunk;
 }
 
-__global__ void coldot_reduce_kernel(const double* __restrict__ P, int nchunk, int nb, int M,
-                                     int N, double* __restrict__ C, int ldc, long long sC) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+// sum of the chunk partials: one warp per output, lanes over the chunks
+__global__ void __launch_bounds__(256) coldot_reduce_kernel(const double* __restrict__ P,
+                                                            int nchunk, int nb, int M, int N,
+                                                            double* __restrict__ C, int ldc,
+                                                            long long sC) {
+  const size_t t = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   const size_t per = (size_t)M * N;
-  if (t >= per * nb) return;
+  if (t >= per * nb) return;                  // whole warps only
   const int b = (int)(t / per);
   const size_t e = t - (size_t)b * per;
   double v = 0.0;
-  for (int c = 0; c < nchunk; ++c) v += P[((size_t)c * nb + b) * per + e];
-  const int i = (int)(e / N), j = (int)(e - (size_t)i * N);
-  C[b * sC + (size_t)i * ldc + j] = v;
+  for (int c = lane; c < nchunk; c += 32) v += P[((size_t)c * nb + b) * per + e];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    const int i = (int)(e / N), j = (int)(e - (size_t)i * N);
+    C[b * sC + (size_t)i * ldc + j] = v;
+  }
+}
+
+// C_b (M x N) = A^T B_b over K rows in chunks (coldot, then the chunk sum);
+// the chunk length keeps the partials within a few blocks per SM.  P is a
+// scratch of nchunk * nb * M * N doubles.
+static void coldot(iga_ctx* ctx, const double* A, int lda, const double* B, int ldb, long long sB,
+                   int K, int M, int N, int nb, double* C, int ldc, long long sC, int pslot) {
+  const int groups = (M + PROJ_G - 1) / PROJ_G;
+  const int want = std::max(1, 4 * ctx->nsm / std::max(1, groups * nb));
+  const int kc = std::max(PROJ_KC, (K + want - 1) / want);
+  const int nch = (K + kc - 1) / kc;
+  double* P = scratch<double>(ctx, pslot, (size_t)nch * nb * M * N);
+  const int th = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
+  prof_count(ctx, 8.0 * ((double)K * M + (double)K * N * nb), 2.0 * K * M * N * nb);
+  IGA_LAUNCH(ctx, coldot_kernel, dim3(nch, groups, nb), th, 0, A, lda, B, ldb, sB, K, M, N, kc, P);
+  const size_t outs = (size_t)nb * M * N;
+  IGA_LAUNCH(ctx, coldot_reduce_kernel, (unsigned)((outs + 7) / 8), 256, 0, P, nch, nb, M, N, C,
+             ldc, sC);
+}
+
+// C_b (M x N) = A_b B_b for a short inner dimension K (a TT rank): one
+// thread per output, B rows read coalesced along j, A entries broadcast
+__global__ void __launch_bounds__(256) gemm_smallk_kernel(const double* __restrict__ A, int lda,
+                                                          long long sA,
+                                                          const double* __restrict__ B, int ldb,
+                                                          long long sB, int M, int N, int K,
+                                                          double* __restrict__ C, int ldc,
+                                                          long long sC) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)M * N) return;
+  const int i = (int)(t / N), j = (int)(t - (size_t)i * N);
+  const int b = blockIdx.y;
+  const double* a = A + b * sA + (size_t)i * lda;
+  const double* bb = B + b * sB + j;
+  double acc0 = 0.0, acc1 = 0.0;
+  int c = 0;
+  for (; c + 1 < K; c += 2) {
+    acc0 = fma(a[c], bb[(size_t)c * ldb], acc0);
+    acc1 = fma(a[c + 1], bb[(size_t)(c + 1) * ldb], acc1);
+  }
+  if (c < K) acc0 = fma(a[c], bb[(size_t)c * ldb], acc0);
+  C[b * sC + (size_t)i * ldc + j] = acc0 + acc1;
+}
+
+static void gemm_smallk(iga_ctx* ctx, const double* A, int lda, long long sA, const double* B,
+                        int ldb, long long sB, int M, int N, int K, double* C, int ldc,
+                        long long sC, int nb) {
+  const size_t outs = (size_t)M * N;
+  prof_count(ctx, 8.0 * (double)nb * ((double)M * K + (double)K * N + (double)outs),
+             2.0 * (double)nb * outs * K);
+  IGA_LAUNCH(ctx, gemm_smallk_kernel, dim3((unsigned)((outs + 255) / 256), nb), 256, 0, A, lda, sA,
+             B, ldb, sB, M, N, K, C, ldc, sC);
+}
+
+// C_b (M x N) = sum_q A_{b,q} B_q^T with short K (rowdot_warp_kernel)
+static void rowdot_short(iga_ctx* ctx, const double* A, int lda, long long sA, const double* B,
+                         int ldb, long long sB, int nsum, int K, int M, int N, int nb, double* C,
+                         int ldc, long long sC, int tout) {
+  prof_count(ctx, 8.0 * ((double)M * K * nb * nsum + (double)N * K * nsum),
+             2.0 * K * M * N * (double)nb * nsum);
+  IGA_LAUNCH(ctx, rowdot_warp_kernel, dim3((M + 7) / 8, (N + PROJ_G - 1) / PROJ_G, nb), 256, 0, A,
+             lda, sA, B, ldb, sB, nsum, K, M, N, C, ldc, sC, tout);
 }
 
 // nonzero pattern of one TT-matrix core of an operator
@@ -1072,14 +1181,8 @@ struct Solver {
                c.colptr.p, c.colsrc.p, c.coloff.p, u, c.R1, r0, nn, r1, op[o]->p[d], w);
     PhiL[o][d + 1].ensure((size_t)c.R1 * r1 * r1);
     // PhiL[be] (r1 x r1) = X^T w[be], a reduction over r0 n
-    {
-      const int Kd = r0 * nn, nch = (Kd + PROJ_KC - 1) / PROJ_KC;
-      double* P = slot(35, (size_t)nch * c.R1 * r1 * r1);
-      IGA_LAUNCH(ctx, coldot_kernel, dim3(nch, (r1 + PROJ_G - 1) / PROJ_G, c.R1), 64, 0, X[d].p,
-                 r1, w, r1, (long long)per, Kd, r1, r1, P);
-      IGA_LAUNCH(ctx, coldot_reduce_kernel, nblk((size_t)c.R1 * r1 * r1), 256, 0, P, nch, c.R1,
-                 r1, r1, PhiL[o][d + 1].p, r1, (long long)r1 * r1);
-    }
+    coldot(ctx, X[d].p, r1, w, r1, (long long)per, r0 * nn, r1, r1, c.R1, PhiL[o][d + 1].p, r1,
+           (long long)r1 * r1, SLOT_AMEN_BASE + 35);
   }
 
   void right_update(int o, int d) {         // PhiR[o][d-1] from PhiR[o][d] and X[d]
@@ -1109,11 +1212,12 @@ struct Solver {
   // full tensors ----------------------------------------------------------
   // frame pieces: Xr = X_{>0} (r1 x n2 n3), Xl = X_{<2} (n1 n2 x r2)
   void right_frame(double* Xr) {
-    rm_gemm(ctx, false, false, r[1] * n[1], n[2], r[2], X[1].p, r[2], X[2].p, n[2], Xr, n[2]);
+    gemm_smallk(ctx, X[1].p, r[2], 0LL, X[2].p, n[2], 0LL, r[1] * n[1], n[2], r[2], Xr, n[2], 0LL,
+                1);
   }
   void left_frame(double* Xl) {
-    rm_gemm(ctx, false, false, n[0], n[1] * r[2], r[1], X[0].p, r[1], X[1].p, n[1] * r[2], Xl,
-            n[1] * r[2]);
+    gemm_smallk(ctx, X[0].p, r[1], 0LL, X[1].p, n[1] * r[2], 0LL, n[0], n[1] * r[2], r[1], Xl,
+                n[1] * r[2], 0LL, 1);
   }
 
   // local rhs F_{!=d}^T f_l for the three components of a full (3, N) tensor
@@ -1128,25 +1232,19 @@ struct Solver {
       IGA_LAUNCH(ctx, rowdot_kernel, dim3(n1, (r[1] + PROJ_G - 1) / PROJ_G, 3), 256, 0, F, n2 * n3,
                  (long long)N, Xr, n2 * n3, 0LL, 1, n2 * n3, r[1], rhs, r[1], (long long)loc, 0);
     } else if (d == 1) {
+      // s_l (n1 n2 x r2) = F_l X2^T (K = n3), then rhs_l = X0^T s_l (K = n1)
       double* s = slot(2, (size_t)3 * n1 * n2 * r[2]);       // one slab per field
-      {
-        const long long ss = (long long)n1 * n2 * r[2];
-        rm_gemm_batched(ctx, false, true, n1 * n2, r[2], n3, F, n3, (long long)N, X[2].p, n3, 0, s,
-                        r[2], ss, 3);
-        rm_gemm_batched(ctx, true, false, r[1], n2 * r[2], n1, X[0].p, r[1], 0, s, n2 * r[2], ss,
-                        rhs, n2 * r[2], (long long)loc, 3);
-      }
+      const long long ss = (long long)n1 * n2 * r[2];
+      rm_gemm_batched(ctx, false, true, n1 * n2, r[2], n3, F, n3, (long long)N, X[2].p, n3, 0, s,
+                      r[2], ss, 3);
+      rm_gemm_batched(ctx, true, false, r[1], n2 * r[2], n1, X[0].p, r[1], 0, s, n2 * r[2], ss,
+                      rhs, n2 * r[2], (long long)loc, 3);
     } else {
       double* Xl = slot(2, (size_t)n1 * n2 * r[2]);
       left_frame(Xl);
       // rhs_l (r2 x n3) = Xl^T F_l, K = n1 n2
-      const int Kd = n1 * n2, nch = (Kd + PROJ_KC - 1) / PROJ_KC;
-      double* P = slot(34, (size_t)nch * 3 * r[2] * n3);
-      prof_count(ctx, 8.0 * (3.0 * N + (double)Kd * r[2]), 6.0 * N * r[2]);
-      IGA_LAUNCH(ctx, coldot_kernel, dim3(nch, (r[2] + PROJ_G - 1) / PROJ_G, 3), 128, 0, Xl, r[2],
-                 F, n3, (long long)N, Kd, r[2], n3, P);
-      IGA_LAUNCH(ctx, coldot_reduce_kernel, nblk((size_t)3 * r[2] * n3), 256, 0, P, nch, 3, r[2],
-                 n3, rhs, n3, (long long)loc);
+      coldot(ctx, Xl, r[2], F, n3, (long long)N, n1 * n2, r[2], n3, 3, rhs, n3, (long long)loc,
+             SLOT_AMEN_BASE + 34);
     }
   }
 
@@ -1157,22 +1255,19 @@ struct Solver {
     if (d == 0) {
       double* Xr = slot(2, (size_t)r[1] * n2 * n3);
       right_frame(Xr);
-      rm_gemm_batched(ctx, false, false, n1, n2 * n3, r[1], Xh.p, r[1], (long long)loc, Xr,
-                      n2 * n3, 0, out, n2 * n3, (long long)N, 3);
+      gemm_smallk(ctx, Xh.p, r[1], (long long)loc, Xr, n2 * n3, 0LL, n1, n2 * n3, r[1], out,
+                  n2 * n3, (long long)N, 3);
     } else if (d == 1) {
       double* t = slot(2, (size_t)3 * n1 * n2 * r[2]);       // one slab per field
-      {
-        const long long ts = (long long)n1 * n2 * r[2];
-        rm_gemm_batched(ctx, false, false, n1, n2 * r[2], r[1], X[0].p, r[1], 0, Xh.p, n2 * r[2],
-                        (long long)loc, t, n2 * r[2], ts, 3);
-        rm_gemm_batched(ctx, false, false, n1 * n2, n3, r[2], t, r[2], ts, X[2].p, n3, 0, out, n3,
-                        (long long)N, 3);
-      }
+      const long long ts = (long long)n1 * n2 * r[2];
+      gemm_smallk(ctx, X[0].p, r[1], 0LL, Xh.p, n2 * r[2], (long long)loc, n1, n2 * r[2], r[1], t,
+                  n2 * r[2], ts, 3);
+      gemm_smallk(ctx, t, r[2], ts, X[2].p, n3, 0LL, n1 * n2, n3, r[2], out, n3, (long long)N, 3);
     } else {
       double* Xl = slot(2, (size_t)n1 * n2 * r[2]);
       left_frame(Xl);
-      rm_gemm_batched(ctx, false, false, n1 * n2, n3, r[2], Xl, r[2], 0, Xh.p, n3, (long long)loc,
-                      out, n3, (long long)N, 3);
+      gemm_smallk(ctx, Xl, r[2], 0LL, Xh.p, n3, (long long)loc, n1 * n2, n3, r[2], out, n3,
+                  (long long)N, 3);
     }
   }
 
@@ -1181,7 +1276,6 @@ struct Solver {
   void sketch(const double* res, int d, bool forward, double* Et, int m) {
     int n1 = n[0], n2 = n[1], n3 = n[2];
     int k = kick;
-    double* E = slot(3, (size_t)m * k);
     if (forward && d == 0) {
       // E (n1 x k) = sum_l res_l Om_l^T with Om_l (k x n2 n3) Gaussian; stored
       // transposed (k x n1)
@@ -1192,36 +1286,34 @@ struct Solver {
       return;
     }
     if (forward && d == 1) {
-      double* Om = slot(4, (size_t)3 * n3 * k);
-      double* t = slot(5, (size_t)n1 * n2 * k);
-      fill_gaussian(ctx, Om, (size_t)3 * n3 * k, seed++);
-      for (int l = 0; l < 3; ++l) {
-        rm_gemm(ctx, false, false, n1 * n2, k, n3, res + l * N, n3, Om + (size_t)l * n3 * k, k, t, k);
-        rm_gemm(ctx, true, false, r[1], n2 * k, n1, X[0].p, r[1], t, n2 * k, E, n2 * k, 1.0,
-                l ? 1.0 : 0.0);
-      }
-      transpose_cm(ctx, E, k, m, Et);   // E row-major (m x k) == col-major (k x m) -> (m x k) cm
+      // t^T (k x n1 n2) = sum_l Om_l res_l^T over i3 (Om_l: k x n3), then
+      // E^T[j] (r1 x n2) = X0^T t^T[j] over i1
+      double* Om = slot(4, (size_t)3 * k * n3);
+      double* tT = slot(5, (size_t)k * n1 * n2);
+      fill_gaussian(ctx, Om, (size_t)3 * k * n3, seed++);
+      rowdot_short(ctx, res, n3, (long long)N, Om, n3, (long long)k * n3, 3, n3, n1 * n2, k, 1, tT,
+                   n1 * n2, 0LL, 1);
+      coldot(ctx, X[0].p, r[1], tT, n2, (long long)n1 * n2, n1, r[1], n2, k, Et, n2,
+             (long long)r[1] * n2, SLOT_AMEN_BASE + 36);
       return;
     }
     if (!forward && d == 2) {
+      // E^T (k x n3) = Om^T res over all rows of the three fields (K = 3 n1 n2)
       double* Om = slot(4, (size_t)3 * n1 * n2 * k);
       fill_gaussian(ctx, Om, (size_t)3 * n1 * n2 * k, seed++);
-      for (int l = 0; l < 3; ++l)
-        rm_gemm(ctx, true, false, n3, k, n1 * n2, res + l * N, n3, Om + (size_t)l * n1 * n2 * k, k,
-                E, k, 1.0, l ? 1.0 : 0.0);
-      transpose_cm(ctx, E, k, m, Et);
+      coldot(ctx, Om, k, res, n3, 0LL, 3 * n1 * n2, k, n3, 1, Et, n3, 0LL, SLOT_AMEN_BASE + 36);
       return;
     }
-    // backward, d == 1: basis in (n2 r2)
+    // backward, d == 1: basis in (n2 r2); s_l (n1 n2 x r2) = res_l X2^T, then
+    // E^T (k x n2 r2) = sum_l Om_l^T s_l over i1 (K = 3 n1)
     double* Om = slot(4, (size_t)3 * n1 * k);
-    double* s = slot(5, (size_t)n1 * n2 * r[2]);
+    double* s = slot(5, (size_t)3 * n1 * n2 * r[2]);
     fill_gaussian(ctx, Om, (size_t)3 * n1 * k, seed++);
-    for (int l = 0; l < 3; ++l) {
-      rm_gemm(ctx, false, true, n1 * n2, r[2], n3, res + l * N, n3, X[2].p, n3, s, r[2]);
-      rm_gemm(ctx, true, false, n2 * r[2], k, n1, s, n2 * r[2], Om + (size_t)l * n1 * k, k, E, k,
-              1.0, l ? 1.0 : 0.0);
-    }
-    transpose_cm(ctx, E, k, m, Et);
+    rm_gemm_batched(ctx, false, true, n1 * n2, r[2], n3, res, n3, (long long)N, X[2].p, n3, 0, s,
+                    r[2], (long long)n1 * n2 * r[2], 3);
+    coldot(ctx, Om, k, s, n2 * r[2], 0LL, 3 * n1, k, n2 * r[2], 1, Et, n2 * r[2], 0LL,
+           SLOT_AMEN_BASE + 36);
+    (void)m;
   }
 
   // truncation rank from descending eigenvalues of a Gram matrix
