@@ -1156,6 +1156,8 @@ struct Solver {
   DevBuf<double> Xh;                   // block core (3, r_d, n_d, r_{d+1})
   DevBuf<double> PhiL[2][4], PhiR[2][4];   // PhiL[o][d]: (R_{d-1}, r_d, r_d) left of core d
   DevBuf<T> PLt[2], PRt[2];            // precision-T copies for the current core
+  const T* PLp[2] = {nullptr, nullptr};   // interfaces of the local operator (the FP64
+  const T* PRp[2] = {nullptr, nullptr};   // interfaces themselves, or the copies)
   int local_iters = 0;
   uint64_t seed = 0x51ed2701ull;
   int verbose = 0;
@@ -1524,8 +1526,8 @@ struct Solver {
   }
 
   void local_op(const Local& c, const T* x, T* y) {
-    const T* PL[2] = {PLt[0].p, PLt[1].p};
-    const T* PR[2] = {PRt[0].p, PRt[1].p};
+    const T* PL[2] = {PLp[0], PLp[1]};
+    const T* PR[2] = {PRp[0], PRp[1]};
     local_op_u<T>(c, PL, PR, x, y, 20);
   }
 
@@ -1540,6 +1542,8 @@ struct Solver {
   BandLayout BL{};
   bool qd = false;                     // quasi-definite block form (one M term)
   DevBuf<T> VLt, VRt;                    // transforms (col-major r x r)
+  const T* VLp = nullptr;                // the transforms in precision T
+  const T* VRp = nullptr;
   void precond_setup(const Local& c) {
     int r0 = c.r0, r1 = c.r1;
     // generalised eigenvectors of (sum Phi^K, sum Phi^M) on both sides:
@@ -1597,10 +1601,18 @@ struct Solver {
                r1, dRM);
     IGA_LAUNCH(ctx, diag_sandwich_kernel, nblk(zK.R1 * r1, 8), 256, 0, PhiR[1][c.d].p, Vs[1], zK.R1,
                r1, dRK);
-    VLt.ensure((size_t)r0 * r0);
-    VRt.ensure((size_t)r1 * r1);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r0 * r0), 256, 0, Vs[0], VLt.p, (size_t)r0 * r0);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r1 * r1), 256, 0, Vs[1], VRt.p, (size_t)r1 * r1);
+    if constexpr (sizeof(T) == 8) {
+      // the transforms stay in their slots until the next setup
+      VLp = reinterpret_cast<const T*>(Vs[0]);
+      VRp = reinterpret_cast<const T*>(Vs[1]);
+    } else {
+      VLt.ensure((size_t)r0 * r0);
+      VRt.ensure((size_t)r1 * r1);
+      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r0 * r0), 256, 0, Vs[0], VLt.p, (size_t)r0 * r0);
+      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(r1 * r1), 256, 0, Vs[1], VRt.p, (size_t)r1 * r1);
+      VLp = VLt.p;
+      VRp = VRt.p;
+    }
     // the block factors are FP32 in both precisions: they only precondition
     // GMRES, which keeps the preconditioned directions (flexible form)
     P* tdLM = scratch<P>(ctx, SLOT_AMEN_BASE + 44, (size_t)zM.R0 * r0);
@@ -1676,8 +1688,8 @@ struct Solver {
     const P* A = scratch<P>(ctx, SLOT_AMEN_BASE + 48, 1);
     int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, 1);
     // w = VL^T v VR
-    right_mult<T>(VRt.p, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
-    left_mult<T>(VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
+    right_mult<T>(VRp, v, 1, 3, c.r0, c.nn, c.r1, 0, t);
+    left_mult<T>(VLp, t, 1, 3, c.r0, c.nn, c.r1, 0, z);
     if (qd) {
       const int w1 = 2 * BL.p + 2;
       const size_t per = (size_t)2 * BL.n * w1 + (size_t)BL.n * (BL.p + 1);
@@ -1716,8 +1728,8 @@ struct Solver {
                  z, lu_smem);
     }
     // back: VL z VR^T
-    right_mult<T>(VRt.p, z, 1, 3, c.r0, c.nn, c.r1, 1, t);
-    left_mult<T>(VLt.p, t, 1, 3, c.r0, c.nn, c.r1, 1, z);
+    right_mult<T>(VRp, z, 1, 3, c.r0, c.nn, c.r1, 1, t);
+    left_mult<T>(VLp, t, 1, 3, c.r0, c.nn, c.r1, 1, z);
   }
 
   // ---- restarted right-preconditioned GMRES in precision T; returns iterations
@@ -1843,24 +1855,32 @@ struct Solver {
     double* rhs = slot(14, per);
     project(F, d, rhs);
     for (int o = 0; o < 2; ++o) {
-      size_t nl = (size_t)nz[o][d].R0 * r[d] * r[d];
-      size_t nr = (size_t)nz[o][d].R1 * r[d + 1] * r[d + 1];
-      PLt[o].ensure(nl);
-      PRt[o].ensure(nr);
-      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(nl), 256, 0, PhiL[o][d].p, PLt[o].p, nl);
-      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(nr), 256, 0, PhiR[o][d].p, PRt[o].p, nr);
+      if constexpr (sizeof(T) == 8) {
+        // FP64: the local operator reads the interfaces themselves
+        PLp[o] = reinterpret_cast<const T*>(PhiL[o][d].p);
+        PRp[o] = reinterpret_cast<const T*>(PhiR[o][d].p);
+      } else {
+        size_t nl = (size_t)nz[o][d].R0 * r[d] * r[d];
+        size_t nr = (size_t)nz[o][d].R1 * r[d + 1] * r[d + 1];
+        PLt[o].ensure(nl);
+        PRt[o].ensure(nr);
+        IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(nl), 256, 0, PhiL[o][d].p, PLt[o].p, nl);
+        IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(nr), 256, 0, PhiR[o][d].p, PRt[o].p, nr);
+        PLp[o] = PLt[o].p;
+        PRp[o] = PRt[o].p;
+      }
     }
     precond_setup(c);
-    T* bt = tslot(30, per);
-    T* xt = tslot(31, per);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, rhs, bt, per);
     // warm start from the current block core
     Xh.ensure(per);
-    IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, Xh.p, xt, per);
     if constexpr (sizeof(T) == 8) {
-      local_iters += gmres(c, bt, xt, tol_abs, maxit);
-      IGA_LAUNCH(ctx, from_type_kernel<T>, nblk(per), 256, 0, xt, Xh.p, per);
+      local_iters += gmres(c, reinterpret_cast<const T*>(rhs), reinterpret_cast<T*>(Xh.p),
+                           tol_abs, maxit);
     } else {
+      T* bt = tslot(30, per);
+      T* xt = tslot(31, per);
+      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, rhs, bt, per);
+      IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, Xh.p, xt, per);
       // FP32 Krylov solves with FP64 local iterative refinement: the local
       // residual is formed with the FP64 interfaces and bands, and FP32
       // corrections are added to the FP64 block core until it meets tol_abs
