@@ -1050,10 +1050,15 @@ __global__ void __launch_bounds__(256) gemm_smallk_kernel(const double* __restri
   C[b * sC + (size_t)i * ldc + j] = acc0 + acc1;
 }
 
+// above 2^26 FMA (the 256-element workloads) the library DGEMM is used
 static void gemm_smallk(iga_ctx* ctx, const double* A, int lda, long long sA, const double* B,
                         int ldb, long long sB, int M, int N, int K, double* C, int ldc,
                         long long sC, int nb) {
   const size_t outs = (size_t)M * N;
+  if ((double)outs * K * nb > 67108864.0) {
+    rm_gemm_batched(ctx, false, false, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nb, 1.0, 0.0);
+    return;
+  }
   prof_count(ctx, 8.0 * (double)nb * ((double)M * K + (double)K * N + (double)outs),
              2.0 * (double)nb * outs * K);
   IGA_LAUNCH(ctx, gemm_smallk_kernel, dim3((unsigned)((outs + 255) / 256), nb), 256, 0, A, lda, sA,
