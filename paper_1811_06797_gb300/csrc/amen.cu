@@ -715,105 +715,113 @@ __global__ void kkt_qd_factor_kernel(
 template <typename T, typename V>
 __global__ void kkt_qd_solve_kernel(BandLayout L, T beta, const T* __restrict__ fac,
                                     V* __restrict__ v) {
+  // two warps per rank pair: the M solve (g = M^-1 f2) and the (y, lambda)
+  // solve are independent chains and run side by side
   extern __shared__ unsigned char smraw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
-  const int blk = blockIdx.x * wpb + warp;
-  if (blk >= L.NB) return;
+  const int pair = warp >> 1, role = warp & 1;
+  const int ppb = blockDim.x >> 6;
+  const int blk = blockIdx.x * ppb + pair;
+  const bool active = blk < L.NB;
   const int n = L.n, p = L.p, w = 2 * p + 1, w1 = w + 1, n2 = 2 * n;
   const size_t per = (size_t)n2 * w1 + (size_t)n * (p + 1);
-  T* S = reinterpret_cast<T*>(smraw) + (size_t)warp * (per + 3 * n);
+  T* S = reinterpret_cast<T*>(smraw) + (size_t)pair * (per + 3 * n);
   T* Mc = S + (size_t)n2 * w1;
   T* h = Mc + (size_t)n * (p + 1);            // 2n: (y, lambda) interleaved
   T* g = h + n2;                              // n: M^-1 f2
-  const T* src = fac + (size_t)blk * per;
-  for (size_t e = lane; e < per; e += 32) S[e] = src[e];
   const int a = blk / L.r1, b = blk % L.r1;
   const size_t comp = (size_t)L.r0 * n * L.r1;
-  for (int i = lane; i < n; i += 32) {
-    const size_t o = ((size_t)a * n + i) * L.r1 + b;
-    const T f1 = (T)v[o], f2 = (T)v[comp + o], f3 = (T)v[2 * comp + o];
-    h[2 * i] = f1;
-    h[2 * i + 1] = f3 + f2 / beta;
-    g[i] = f2;
-  }
-  __syncwarp();
-  // The four triangular sweeps run on a register window: in a forward sweep
-  // lane t holds entry k + t of the vector (k + t in a backward one), the
-  // settled entry k comes from lane 0 by a shuffle, lanes 1..band subtract
-  // their band coefficient times it, and the window shifts by one lane (lane
-  // 31 reads the next untouched entry from shared memory).  The dependency
-  // chain per row is two shuffles and one FMA.
-  const int pw = p + 1;
-  // g = M^-1 f2: forward with the Cholesky factor ...
-  {
-    T hv = lane < n ? g[lane] : T(0);
-    for (int k = 0; k < n; ++k) {
-      const T c = (lane >= 1 && lane <= p && k + lane < n) ? Mc[(size_t)(k + lane) * pw + lane]
-                                                           : T(0);
-      const T x = __shfl_sync(0xffffffffu, hv, 0) / Mc[(size_t)k * pw];
-      if (lane == 0) g[k] = x;
-      hv -= c * x;
-      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
-      if (lane == 31) nx = k + 32 < n ? g[k + 32] : T(0);
-      hv = nx;
+  if (active) {
+    const T* src = fac + (size_t)blk * per;
+    for (size_t e = lane + 32 * role; e < per; e += 64) S[e] = src[e];
+    for (int i = lane + 32 * role; i < n; i += 64) {
+      const size_t o = ((size_t)a * n + i) * L.r1 + b;
+      const T f1 = (T)v[o], f2 = (T)v[comp + o], f3 = (T)v[2 * comp + o];
+      h[2 * i] = f1;
+      h[2 * i + 1] = f3 + f2 / beta;
+      g[i] = f2;
     }
   }
-  __syncwarp();
-  // ... and backward with its transpose
-  {
-    T hv = n - 1 - lane >= 0 ? g[n - 1 - lane] : T(0);
-    for (int k = n - 1; k >= 0; --k) {
-      const T c = (lane >= 1 && lane <= p && k - lane >= 0) ? Mc[(size_t)k * pw + lane] : T(0);
-      const T x = __shfl_sync(0xffffffffu, hv, 0) / Mc[(size_t)k * pw];
-      if (lane == 0) g[k] = x;
-      hv -= c * x;
-      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
-      if (lane == 31) nx = k - 32 >= 0 ? g[k - 32] : T(0);
-      hv = nx;
+  __syncthreads();
+  // The triangular sweeps run on a register window: in a forward sweep lane
+  // t holds entry k + t of the vector (k + t in a backward one), the settled
+  // entry k comes from lane 0 by a shuffle, lanes 1..band subtract their band
+  // coefficient times it, and the window shifts by one lane (lane 31 reads
+  // the next untouched entry from shared memory).  The dependency chain per
+  // row is two shuffles and one FMA.
+  if (active && role == 0) {
+    const int pw = p + 1;
+    // g = M^-1 f2: forward with the Cholesky factor ...
+    {
+      T hv = lane < n ? g[lane] : T(0);
+      for (int k = 0; k < n; ++k) {
+        const T c = (lane >= 1 && lane <= p && k + lane < n) ? Mc[(size_t)(k + lane) * pw + lane]
+                                                             : T(0);
+        const T x = __shfl_sync(0xffffffffu, hv, 0) / Mc[(size_t)k * pw];
+        if (lane == 0) g[k] = x;
+        hv -= c * x;
+        T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+        if (lane == 31) nx = k + 32 < n ? g[k + 32] : T(0);
+        hv = nx;
+      }
+    }
+    __syncwarp();
+    // ... and backward with its transpose
+    {
+      T hv = n - 1 - lane >= 0 ? g[n - 1 - lane] : T(0);
+      for (int k = n - 1; k >= 0; --k) {
+        const T c = (lane >= 1 && lane <= p && k - lane >= 0) ? Mc[(size_t)k * pw + lane] : T(0);
+        const T x = __shfl_sync(0xffffffffu, hv, 0) / Mc[(size_t)k * pw];
+        if (lane == 0) g[k] = x;
+        hv -= c * x;
+        T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+        if (lane == 31) nx = k - 32 >= 0 ? g[k - 32] : T(0);
+        hv = nx;
+      }
+    }
+  } else if (active) {
+    // (y, lambda) = S^-1 h with S = L D L^T: unit lower sweep, D, unit upper sweep
+    {
+      T hv = lane < n2 ? h[lane] : T(0);
+      for (int k = 0; k < n2; ++k) {
+        const T c = (lane >= 1 && lane <= w && k + lane < n2) ? S[(size_t)(k + lane) * w1 + lane]
+                                                              : T(0);
+        const T x = __shfl_sync(0xffffffffu, hv, 0);
+        if (lane == 0) h[k] = x;
+        hv -= c * x;
+        T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+        if (lane == 31) nx = k + 32 < n2 ? h[k + 32] : T(0);
+        hv = nx;
+      }
+    }
+    __syncwarp();
+    for (int k = lane; k < n2; k += 32) {
+      const T d = S[(size_t)k * w1];
+      h[k] = d != T(0) ? h[k] / d : T(0);
+    }
+    __syncwarp();
+    {
+      T hv = n2 - 1 - lane >= 0 ? h[n2 - 1 - lane] : T(0);
+      for (int k = n2 - 1; k >= 0; --k) {
+        const T c = (lane >= 1 && lane <= w && k - lane >= 0) ? S[(size_t)k * w1 + lane] : T(0);
+        const T x = __shfl_sync(0xffffffffu, hv, 0);
+        if (lane == 0) h[k] = x;
+        hv -= c * x;
+        T nx = __shfl_down_sync(0xffffffffu, hv, 1);
+        if (lane == 31) nx = k - 32 >= 0 ? h[k - 32] : T(0);
+        hv = nx;
+      }
     }
   }
-  __syncwarp();
-  // (y, lambda) = S^-1 h with S = L D L^T: unit lower sweep, D, unit upper sweep
-  {
-    T hv = lane < n2 ? h[lane] : T(0);
-    for (int k = 0; k < n2; ++k) {
-      const T c = (lane >= 1 && lane <= w && k + lane < n2) ? S[(size_t)(k + lane) * w1 + lane]
-                                                            : T(0);
-      const T x = __shfl_sync(0xffffffffu, hv, 0);
-      if (lane == 0) h[k] = x;
-      hv -= c * x;
-      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
-      if (lane == 31) nx = k + 32 < n2 ? h[k + 32] : T(0);
-      hv = nx;
+  __syncthreads();
+  if (active)
+    for (int i = lane + 32 * role; i < n; i += 64) {
+      const size_t o = ((size_t)a * n + i) * L.r1 + b;
+      const T y = h[2 * i], lam = h[2 * i + 1];
+      v[o] = (V)y;
+      v[comp + o] = (V)((lam + g[i]) / beta);
+      v[2 * comp + o] = (V)lam;
     }
-  }
-  __syncwarp();
-  for (int k = lane; k < n2; k += 32) {
-    const T d = S[(size_t)k * w1];
-    h[k] = d != T(0) ? h[k] / d : T(0);
-  }
-  __syncwarp();
-  {
-    T hv = n2 - 1 - lane >= 0 ? h[n2 - 1 - lane] : T(0);
-    for (int k = n2 - 1; k >= 0; --k) {
-      const T c = (lane >= 1 && lane <= w && k - lane >= 0) ? S[(size_t)k * w1 + lane] : T(0);
-      const T x = __shfl_sync(0xffffffffu, hv, 0);
-      if (lane == 0) h[k] = x;
-      hv -= c * x;
-      T nx = __shfl_down_sync(0xffffffffu, hv, 1);
-      if (lane == 31) nx = k - 32 >= 0 ? h[k - 32] : T(0);
-      hv = nx;
-    }
-  }
-  __syncwarp();
-  for (int i = lane; i < n; i += 32) {
-    const size_t o = ((size_t)a * n + i) * L.r1 + b;
-    const T y = h[2 * i], lam = h[2 * i + 1];
-    v[o] = (V)y;
-    v[comp + o] = (V)((lam + g[i]) / beta);
-    v[2 * comp + o] = (V)lam;
-  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -1699,7 +1707,8 @@ struct Solver {
       const int w1 = 2 * BL.p + 2;
       const size_t per = (size_t)2 * BL.n * w1 + (size_t)BL.n * (BL.p + 1);
       const size_t perw = (per + 3 * (size_t)BL.n) * sizeof(P);
-      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perw));
+      // two warps per rank pair, up to four pairs per block
+      const int ppb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / perw));
       static bool qattr = false;
       if (!qattr) {
         IGA_CUDA(cudaFuncSetAttribute(kkt_qd_solve_kernel<P, T>,
@@ -1709,7 +1718,7 @@ struct Solver {
       // algorithmic: two band sweeps of 2n rows (half-bandwidth 2p+1) and two of n rows
       prof_count(ctx, (double)BL.NB * (per * sizeof(P) + 6.0 * BL.n * sizeof(T)),
                  (double)BL.NB * (8.0 * BL.n * (2 * BL.p + 1) + 4.0 * BL.n * BL.p));
-      IGA_LAUNCH(ctx, (kkt_qd_solve_kernel<P, T>), nblk(BL.NB, wpb), 32 * wpb, wpb * perw, BL,
+      IGA_LAUNCH(ctx, (kkt_qd_solve_kernel<P, T>), nblk(BL.NB, ppb), 64 * ppb, ppb * perw, BL,
                  (P)beta, A, z);
     } else {
       // keep each block's LU factor in shared memory when four of them fit
