@@ -102,13 +102,17 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+// Gaussian test matrices for the randomized sketches (Box-Muller on two
+// 24-bit uniforms from one splitmix64 hash).  The transform runs in FP32:
+// the sketches need independent normal samples, not FP64 ones, and the FP64
+// logarithm and cosine cost some 60 FP64 operations per sample on this GPU.
 __global__ void gaussian_kernel(double* __restrict__ x, size_t n, uint64_t seed) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    uint64_t h1 = splitmix64(seed ^ (2 * i)), h2 = splitmix64(seed ^ (2 * i + 1) ^ 0x5bd1e995ull);
-    double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);   // (0, 1]
-    double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);           // [0, 1)
-    x[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    const uint64_t h = splitmix64(seed ^ (0x9e3779b97f4a7c15ull * (i + 1)));
+    const float u1 = (float)((h >> 40) + 1) * (1.0f / 16777216.0f);          // (0, 1]
+    const float u2 = (float)((h >> 16) & 0xffffffull) * (1.0f / 16777216.0f);  // [0, 1)
+    x[i] = (double)(sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2));
   }
 }
 
