@@ -206,7 +206,9 @@ iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, double alpha, const voi
 
 /* out = KKT z for the stationary KKT matrix (Sec. 4 eq. KKTSystem with one
  * time step and tau = 1):  [[M, 0, K^T], [0, beta M, -M], [K, -M, 0]].
- * z, out: device, 3N (y, u, lambda stacked), precision as above. */
+ * z, out: device, 3N (y, u, lambda stacked), precision as above; z and out
+ * must not overlap (IGA_EINVAL).  When M and K are rank-1 Kronecker sums the
+ * five operator products run as one fused launch. */
 iga_status iga_kkt_apply(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
                          const void* z, void* out, iga_prec prec);
 
