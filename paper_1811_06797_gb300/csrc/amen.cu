@@ -597,7 +597,8 @@ __global__ void kkt_block_solve_kernel(BandLayout L, const T* __restrict__ Aall,
 // pivoting.  Node-interleaved (2 i + l), S has half-bandwidth w = 2 p + 1;
 // M is factorised by banded Cholesky (half-bandwidth p).  Storage per block:
 // S lower band (2n x (w + 1)), entry (r, r - c) at r (w + 1) + c, then the
-// Cholesky band of M (n x (p + 1)).  One warp per block.
+// Cholesky band of M (n x (p + 1)).  Two warps per block: the LDL^T of S and
+// the Cholesky of M are independent and run side by side.
 template <typename T>
 __global__ void kkt_qd_factor_kernel(
     BandLayout L, T beta, const T* __restrict__ bandM, const int* __restrict__ nzM_l,
@@ -606,43 +607,51 @@ __global__ void kkt_qd_factor_kernel(
     const long long* __restrict__ nzK_off, int nnzK, const T* __restrict__ dLM,
     const T* __restrict__ dRM, const T* __restrict__ dLK, const T* __restrict__ dRK,
     T* __restrict__ out, int* __restrict__ flag) {
+  // two warps per rank pair: both assemble the block, then one factorises
+  // the quasi-definite (y, lambda) matrix and the other the mass block, side
+  // by side (the two factorisations are independent)
   extern __shared__ unsigned char smraw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
-  const int blk = blockIdx.x * wpb + warp;
-  if (blk >= L.NB) return;
+  const int pair = warp >> 1, role = warp & 1, tid = threadIdx.x & 63;
+  const int ppb = blockDim.x >> 6;
+  const int blk = blockIdx.x * ppb + pair;
+  const bool active = blk < L.NB;
   const int n = L.n, p = L.p, B = 2 * p + 1, w = 2 * p + 1, w1 = w + 1;
   const int n2 = 2 * n;
   const size_t per = (size_t)n2 * w1 + (size_t)n * (p + 1);
-  T* S = reinterpret_cast<T*>(smraw) + (size_t)warp * (per + KKT_QD_MAXK + 1);
+  T* S = reinterpret_cast<T*>(smraw) + (size_t)pair * (per + KKT_QD_MAXK + 1);
   T* Mc = S + (size_t)n2 * w1;
   T* cf = Mc + (size_t)n * (p + 1);            // [M coefficient, K coefficients]
   const int a = blk / L.r1, b = blk % L.r1;
-  for (size_t e = lane; e < per; e += 32) S[e] = T(0);
-  if (lane == 0) cf[0] = dLM[(size_t)nzM_l[0] * L.r0 + a] * dRM[(size_t)nzM_r[0] * L.r1 + b];
-  for (int z = lane; z < nnzK; z += 32)
-    cf[1 + z] = dLK[(size_t)nzK_l[z] * L.r0 + a] * dRK[(size_t)nzK_r[z] * L.r1 + b];
-  __syncwarp();
-  const T sm = cf[0];
-  for (int e = lane; e < n * B; e += 32) {
-    const int i = e / B, o = e - i * B;
-    const int j = i + o - p;                    // column node
-    if (j < 0 || j >= n || j > i) continue;     // lower part: j <= i
-    const T m = sm * bandM[nzM_off[0] + (size_t)i * B + o];
-    T k = T(0), kt = T(0);
-    for (int z = 0; z < nnzK; ++z) {
-      const T c = cf[1 + z];
-      k += c * bandK[nzK_off[z] + (size_t)i * B + o];                 // K(i, j)
-      kt += c * bandK[nzK_off[z] + (size_t)j * B + (i - j + p)];      // K(j, i)
-    }
-    // rows 2i (y) and 2i+1 (lambda), columns 2j, 2j+1, lower part only
-    S[(size_t)(2 * i) * w1 + (2 * i - 2 * j)] = m;                     // (2i, 2j)
-    if (j < i) S[(size_t)(2 * i) * w1 + (2 * i - 2 * j - 1)] = kt;      // (2i, 2j+1) = K^T(i,j)
-    S[(size_t)(2 * i + 1) * w1 + (2 * i + 1 - 2 * j)] = k;             // (2i+1, 2j) = K(i,j)
-    S[(size_t)(2 * i + 1) * w1 + (2 * i - 2 * j)] = -m / beta;         // (2i+1, 2j+1)
-    Mc[(size_t)i * (p + 1) + (i - j)] = m;
+  if (active) {
+    for (size_t e = tid; e < per; e += 64) S[e] = T(0);
+    if (tid == 0) cf[0] = dLM[(size_t)nzM_l[0] * L.r0 + a] * dRM[(size_t)nzM_r[0] * L.r1 + b];
+    for (int z = tid; z < nnzK; z += 64)
+      cf[1 + z] = dLK[(size_t)nzK_l[z] * L.r0 + a] * dRK[(size_t)nzK_r[z] * L.r1 + b];
   }
-  __syncwarp();
+  __syncthreads();
+  if (active) {
+    const T sm = cf[0];
+    for (int e = tid; e < n * B; e += 64) {
+      const int i = e / B, o = e - i * B;
+      const int j = i + o - p;                    // column node
+      if (j < 0 || j >= n || j > i) continue;     // lower part: j <= i
+      const T m = sm * bandM[nzM_off[0] + (size_t)i * B + o];
+      T k = T(0), kt = T(0);
+      for (int z = 0; z < nnzK; ++z) {
+        const T c = cf[1 + z];
+        k += c * bandK[nzK_off[z] + (size_t)i * B + o];                 // K(i, j)
+        kt += c * bandK[nzK_off[z] + (size_t)j * B + (i - j + p)];      // K(j, i)
+      }
+      // rows 2i (y) and 2i+1 (lambda), columns 2j, 2j+1, lower part only
+      S[(size_t)(2 * i) * w1 + (2 * i - 2 * j)] = m;                     // (2i, 2j)
+      if (j < i) S[(size_t)(2 * i) * w1 + (2 * i - 2 * j - 1)] = kt;      // (2i, 2j+1) = K^T(i,j)
+      S[(size_t)(2 * i + 1) * w1 + (2 * i + 1 - 2 * j)] = k;             // (2i+1, 2j) = K(i,j)
+      S[(size_t)(2 * i + 1) * w1 + (2 * i - 2 * j)] = -m / beta;         // (2i+1, 2j+1)
+      Mc[(size_t)i * (p + 1) + (i - j)] = m;
+    }
+  }
+  __syncthreads();
   // Each lane owns one pair t1 <= t2 of the column update (w (w + 1) / 2 <= 45
   // pairs for p <= 4, so at most two per lane), decoded once.
   int pt2[2], pt1[2];
@@ -653,62 +662,68 @@ __global__ void kkt_qd_factor_kernel(
     pt2[q] = t2;
     pt1[q] = e - (t2 - 1) * t2 / 2 + 1;
   }
-  // LDL^T: with c_t = S(k + t, k), S(k + t2, k + t1) -= c_t2 c_t1 / d_k and the
-  // column becomes l_t = c_t / d_k; every lane reads its c values before the
-  // shared update
-  for (int k = 0; k < n2; ++k) {
-    const T d = S[(size_t)k * w1];
-    if (d == T(0)) {
-      if (lane == 0) atomicOr(flag, 2);
-      continue;
-    }
-    const T rd = T(1) / d;
-    const int cnt = min(w, n2 - 1 - k);
-    T c2[2], c1[2];
+  if (active && role == 0) {
+    // LDL^T: with c_t = S(k + t, k), S(k + t2, k + t1) -= c_t2 c_t1 / d_k and
+    // the column becomes l_t = c_t / d_k; every lane reads its c values
+    // before the shared update
+    for (int k = 0; k < n2; ++k) {
+      const T d = S[(size_t)k * w1];
+      if (d == T(0)) {
+        if (lane == 0) atomicOr(flag, 2);
+        continue;
+      }
+      const T rd = T(1) / d;
+      const int cnt = min(w, n2 - 1 - k);
+      T c2[2], c1[2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const bool on = pt2[q] <= cnt;
-      c2[q] = on ? S[(size_t)(k + pt2[q]) * w1 + pt2[q]] : T(0);
-      c1[q] = on ? S[(size_t)(k + pt1[q]) * w1 + pt1[q]] : T(0);
-    }
-    const T ct = (lane >= 1 && lane <= cnt) ? S[(size_t)(k + lane) * w1 + lane] : T(0);
-    __syncwarp();
+      for (int q = 0; q < 2; ++q) {
+        const bool on = pt2[q] <= cnt;
+        c2[q] = on ? S[(size_t)(k + pt2[q]) * w1 + pt2[q]] : T(0);
+        c1[q] = on ? S[(size_t)(k + pt1[q]) * w1 + pt1[q]] : T(0);
+      }
+      const T ct = (lane >= 1 && lane <= cnt) ? S[(size_t)(k + lane) * w1 + lane] : T(0);
+      __syncwarp();
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
-      if (pt2[q] <= cnt) S[(size_t)(k + pt2[q]) * w1 + (pt2[q] - pt1[q])] -= c2[q] * c1[q] * rd;
-    if (lane >= 1 && lane <= cnt) S[(size_t)(k + lane) * w1 + lane] = ct * rd;
-    __syncwarp();
+      for (int q = 0; q < 2; ++q)
+        if (pt2[q] <= cnt) S[(size_t)(k + pt2[q]) * w1 + (pt2[q] - pt1[q])] -= c2[q] * c1[q] * rd;
+      if (lane >= 1 && lane <= cnt) S[(size_t)(k + lane) * w1 + lane] = ct * rd;
+      __syncwarp();
+    }
+  } else if (active) {
+    // banded Cholesky of M: with c_t = Mc(k + t, k) and s = sqrt(Mc(k, k)),
+    // Mc(k + t2, k + t1) -= c_t2 c_t1 / s^2 and the column becomes c_t / s
+    for (int k = 0; k < n; ++k) {
+      T d = Mc[(size_t)k * (p + 1)];
+      if (!(d > T(0))) {
+        if (lane == 0) atomicOr(flag, 2);
+        d = T(1);
+      }
+      const T rd = T(1) / d;
+      const T rs = T(1) / sqrt(d);
+      const int cnt = min(p, n - 1 - k);
+      T c2[2], c1[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const bool on = pt2[q] <= cnt;
+        c2[q] = on ? Mc[(size_t)(k + pt2[q]) * (p + 1) + pt2[q]] : T(0);
+        c1[q] = on ? Mc[(size_t)(k + pt1[q]) * (p + 1) + pt1[q]] : T(0);
+      }
+      const T ct = (lane >= 1 && lane <= cnt) ? Mc[(size_t)(k + lane) * (p + 1) + lane] : T(0);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (pt2[q] <= cnt)
+          Mc[(size_t)(k + pt2[q]) * (p + 1) + (pt2[q] - pt1[q])] -= c2[q] * c1[q] * rd;
+      if (lane >= 1 && lane <= cnt) Mc[(size_t)(k + lane) * (p + 1) + lane] = ct * rs;
+      if (lane == 0) Mc[(size_t)k * (p + 1)] = sqrt(d);
+      __syncwarp();
+    }
   }
-  // banded Cholesky of M: with c_t = Mc(k + t, k) and s = sqrt(Mc(k, k)),
-  // Mc(k + t2, k + t1) -= c_t2 c_t1 / s^2 and the column becomes c_t / s
-  for (int k = 0; k < n; ++k) {
-    T d = Mc[(size_t)k * (p + 1)];
-    if (!(d > T(0))) {
-      if (lane == 0) atomicOr(flag, 2);
-      d = T(1);
-    }
-    const T rd = T(1) / d;
-    const T rs = T(1) / sqrt(d);
-    const int cnt = min(p, n - 1 - k);
-    T c2[2], c1[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const bool on = pt2[q] <= cnt;
-      c2[q] = on ? Mc[(size_t)(k + pt2[q]) * (p + 1) + pt2[q]] : T(0);
-      c1[q] = on ? Mc[(size_t)(k + pt1[q]) * (p + 1) + pt1[q]] : T(0);
-    }
-    const T ct = (lane >= 1 && lane <= cnt) ? Mc[(size_t)(k + lane) * (p + 1) + lane] : T(0);
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-      if (pt2[q] <= cnt)
-        Mc[(size_t)(k + pt2[q]) * (p + 1) + (pt2[q] - pt1[q])] -= c2[q] * c1[q] * rd;
-    if (lane >= 1 && lane <= cnt) Mc[(size_t)(k + lane) * (p + 1) + lane] = ct * rs;
-    if (lane == 0) Mc[(size_t)k * (p + 1)] = sqrt(d);
-    __syncwarp();
+  __syncthreads();
+  if (active) {
+    T* g = out + (size_t)blk * per;
+    for (size_t e = tid; e < per; e += 64) g[e] = S[e];
   }
-  T* g = out + (size_t)blk * per;
-  for (size_t e = lane; e < per; e += 32) g[e] = S[e];
 }
 
 // apply: f (y, u, lambda rows of block (a, b)) -> solution, in place in v
@@ -1653,7 +1668,8 @@ struct Solver {
       P* F = scratch<P>(ctx, SLOT_AMEN_BASE + 48, per * BL.NB);
       IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
       const size_t perw = (per + KKT_QD_MAXK + 1) * sizeof(P);
-      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perw));
+      // two warps per rank pair, up to four pairs per block
+      const int ppb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / perw));
       IGA_REQUIRE(perw <= 200 * 1024, "kkt preconditioner: block too large");
       static bool qattr = false;
       if (!qattr) {
@@ -1666,7 +1682,7 @@ struct Solver {
       prof_count(ctx, (double)BL.NB * per * sizeof(P),
                  (double)BL.NB * (2.0 * BL.n * (2 * BL.p + 1) * (2 * BL.p + 2) +
                                   (double)BL.n * BL.p * (BL.p + 1)));
-      IGA_LAUNCH(ctx, kkt_qd_factor_kernel<P>, nblk(BL.NB, wpb), 32 * wpb, wpb * perw, BL,
+      IGA_LAUNCH(ctx, kkt_qd_factor_kernel<P>, nblk(BL.NB, ppb), 64 * ppb, ppb * perw, BL,
                  (P)beta, bands_of<P>(op[0], c.d), zM.dl.p, zM.dr.p, zM.doff.p,
                  bands_of<P>(op[1], c.d), zK.dl.p, zK.dr.p, zK.doff.p, (int)zK.l.size(), tdLM,
                  tdRM, tdLK, tdRK, F, ctx->dflag);
