@@ -312,7 +312,8 @@ thread_local cudaStream_t t_alloc_stream = nullptr;
 thread_local bool t_alloc_active = false;
 
 // one stream-ordered pool per device, keeping up to 4 GB of released memory
-// cached across synchronisations
+// cached across synchronisations; nullptr on a device without memory pools
+// (allocations then go through cudaMalloc)
 cudaMemPool_t device_pool() {
   int dev = 0;
   IGA_CUDA(cudaGetDevice(&dev));
@@ -321,6 +322,12 @@ cudaMemPool_t device_pool() {
   std::lock_guard<std::mutex> lk(mu);
   auto it = pools.find(dev);
   if (it != pools.end()) return it->second;
+  int supported = 0;
+  IGA_CUDA(cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev));
+  if (!supported) {
+    pools[dev] = nullptr;
+    return nullptr;
+  }
   cudaMemPoolProps props{};
   props.allocType = cudaMemAllocationTypePinned;
   props.location.type = cudaMemLocationTypeDevice;
@@ -346,8 +353,9 @@ AllocScope::~AllocScope() {
 
 void* dev_alloc(size_t bytes, bool* pooled) {
   void* p = nullptr;
-  if (t_alloc_active) {
-    IGA_CUDA(cudaMallocFromPoolAsync(&p, bytes, device_pool(), t_alloc_stream));
+  cudaMemPool_t pool = t_alloc_active ? device_pool() : nullptr;
+  if (pool) {
+    IGA_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool, t_alloc_stream));
     *pooled = true;
   } else {
     IGA_CUDA(cudaMalloc(&p, bytes));
