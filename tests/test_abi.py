@@ -3,6 +3,8 @@ entry point declared in include/iga.h (no GPU calls)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -46,3 +48,41 @@ def test_header_cites_the_paper():
     hdr = open(os.path.join(ROOT, "include", "iga.h")).read()
     for needle in ("KKT_red", "KKTSystem", "massMatrix1D", "eq. tt", "geometryMapping"):
         assert needle in hdr, needle
+
+
+# public structs of include/iga.h and their ctypes mirrors in the binding
+_STRUCTS = {"iga_geometry": "Geometry_", "iga_space": "Space_", "iga_target": "Target_",
+            "iga_solve_opts": "SolveOpts_", "iga_solve_info": "SolveInfo_"}
+
+
+def _c_layouts(tmp_path):
+    """sizeof and every field offset of the public structs, as a C compiler
+    lays them out from the header (host gcc, no CUDA)."""
+    from paper_1811_06797_gb300 import iga
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "iga.h"', "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in getattr(iga, pyname)._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="no host C compiler")
+def test_binding_struct_layouts_match_header(tmp_path):
+    """Every ctypes structure of the binding has the C layout of the header:
+    same size and the same offset for every field (a field added on one side
+    only shifts the ones after it)."""
+    from paper_1811_06797_gb300 import iga
+    c = _c_layouts(tmp_path)
+    for cname, pyname in _STRUCTS.items():
+        py = getattr(iga, pyname)
+        assert ctypes.sizeof(py) == c[(cname, "size")], cname
+        for field, _ in py._fields_:
+            assert getattr(py, field).offset == c[(cname, field)], (cname, field)
