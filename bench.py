@@ -258,11 +258,13 @@ def run_gpu(args, world, rank, local):
 
     # dominant kernel: device time of each candidate over one (untimed) step
     shares = {}
+    per_kernel = {}
     for k in CANDIDATES:
         ctx.profile_begin(k)
         step()
         p = ctx.profile_end()
         shares[k] = p["ms"]
+        per_kernel[k] = p
     if args.roofline_kernel == "auto":
         args.roofline_kernel = max(shares, key=shares.get)
 
@@ -370,6 +372,24 @@ def run_gpu(args, world, rank, local):
                      "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": fl,
                      "device_ms_per_step_by_kernel": {k: round(v, 3) for k, v in shares.items()}})
 
+    # the Kronecker apply (KKT residuals) against the FP64 rate: the metric's
+    # second part, from the same untimed per-kernel step
+    kron_roof = None
+    try:
+        kp = per_kernel.get("kron_rank1_kernel")
+        if kp and kp["launches"] > 0 and kp["ms"] > 0:
+            kavg = kp["ms"] / kp["launches"]
+            kfl = kp["flops"] / kp["launches"]
+            kach = kfl / (kavg * 1e-3) / 1e12
+            kron_roof = {"kernel": "kron_rank1_kernel", "bound": "alu", "achieved": kach,
+                         "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s", "frac": kach / FP64_FMA_TFLOPS,
+                         "peak_kind": "measured FP64 FMA rate (CUDA cores)",
+                         "launches_per_step": kp["launches"], "avg_us": kavg * 1e3,
+                         "algorithmic_flops_per_launch": kfl,
+                         "algorithmic_bytes_per_launch": kp["bytes"] / kp["launches"]}
+    except (KeyError, TypeError, ZeroDivisionError):
+        kron_roof = None
+
     line = {
         "metric": METRIC,
         "value": ms / 1e3,
@@ -398,6 +418,7 @@ def run_gpu(args, world, rank, local):
                 "d2h_bytes_per_step": int(3 * N * 8)},
         "gpu_launches": int(launches / max(1, args.steps)),
         "roofline": roof,
+        "kron_roofline": kron_roof,
         "clocks": clocks,
     }
     return line, work
