@@ -1,0 +1,61 @@
+"""Host-side pieces of bench.py that need no GPU: the clock and throttle
+summary taken from nvidia-smi's CSV during the timed region, and the peak
+table's fallback."""
+import json
+
+import bench
+
+
+def _sampler_with(tmp_path, rows):
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    with open(s.path, "w") as f:
+        for r in rows:
+            f.write(", ".join(r) + "\n")
+    return s
+
+
+def test_clock_summary_median_max_and_reasons(tmp_path):
+    # index, sm, max sm, power, active mask, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    rows = [["0", "2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+            ["0", "1980", "2070", "1390.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+            ["0", "2055", "2070", "1200.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    out = _sampler_with(tmp_path, rows).summary()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2055.0
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_flags_thermal_slowdown(tmp_path):
+    rows = [["0", "1500", "2070", "1000", "0x40", "Not Active", "Active", "Not Active", "Not Active"]]
+    out = _sampler_with(tmp_path, rows).summary()
+    assert out["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_clock_summary_without_samples(tmp_path):
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "missing.csv")
+    out = s.summary()
+    assert out == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_clock_summary_skips_malformed_rows(tmp_path):
+    rows = [["0", "[N/A]", "2070"], ["0", "2070", "2070", "1", "0x0", "Not Active", "Not Active",
+                                     "Not Active", "Not Active"]]
+    out = _sampler_with(tmp_path, rows).summary()
+    assert out["samples"] == 1 and out["sm_mhz"] == 2070.0
+
+
+def test_peaks_fallback_when_file_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "none.json"))
+    p, kind = bench.peaks()
+    assert kind == "fallback" and p["hbm_gbs"] == 6800.0
+
+
+def test_peaks_measured_file(monkeypatch, tmp_path):
+    f = tmp_path / "peaks.json"
+    f.write_text(json.dumps({"hbm_gbs": 6794.0, "bf16_tflops": 1968.0}))
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(f))
+    p, kind = bench.peaks()
+    assert kind == "measured" and p["hbm_gbs"] == 6794.0
