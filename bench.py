@@ -89,6 +89,25 @@ def peaks():
         return FALLBACK_PEAKS, "fallback"
 
 
+def alu_roofline(kernel, p, peak_tflops, peak_kind):
+    """Roofline object of one kernel against an arithmetic peak, from the
+    library's live profile of one step (launches, ms, algorithmic bytes and
+    flops summed over the launches); None when the kernel did not run."""
+    try:
+        if not p or p["launches"] <= 0 or p["ms"] <= 0:
+            return None
+        avg = p["ms"] / p["launches"]
+        fl = p["flops"] / p["launches"]
+        ach = fl / (avg * 1e-3) / 1e12
+        return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": ach / peak_tflops, "peak_kind": peak_kind,
+                "launches_per_step": p["launches"], "avg_us": avg * 1e3,
+                "algorithmic_flops_per_launch": fl,
+                "algorithmic_bytes_per_launch": p["bytes"] / p["launches"]}
+    except (KeyError, TypeError, ZeroDivisionError):
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -374,21 +393,8 @@ def run_gpu(args, world, rank, local):
 
     # the Kronecker apply (KKT residuals) against the FP64 rate: the metric's
     # second part, from the same untimed per-kernel step
-    kron_roof = None
-    try:
-        kp = per_kernel.get("kron_rank1_kernel")
-        if kp and kp["launches"] > 0 and kp["ms"] > 0:
-            kavg = kp["ms"] / kp["launches"]
-            kfl = kp["flops"] / kp["launches"]
-            kach = kfl / (kavg * 1e-3) / 1e12
-            kron_roof = {"kernel": "kron_rank1_kernel", "bound": "alu", "achieved": kach,
-                         "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s", "frac": kach / FP64_FMA_TFLOPS,
-                         "peak_kind": "measured FP64 FMA rate (CUDA cores)",
-                         "launches_per_step": kp["launches"], "avg_us": kavg * 1e3,
-                         "algorithmic_flops_per_launch": kfl,
-                         "algorithmic_bytes_per_launch": kp["bytes"] / kp["launches"]}
-    except (KeyError, TypeError, ZeroDivisionError):
-        kron_roof = None
+    kron_roof = alu_roofline("kron_rank1_kernel", per_kernel.get("kron_rank1_kernel"),
+                             FP64_FMA_TFLOPS, "measured FP64 FMA rate (CUDA cores)")
 
     line = {
         "metric": METRIC,

@@ -59,3 +59,20 @@ def test_peaks_measured_file(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "PEAKS_FILE", str(f))
     p, kind = bench.peaks()
     assert kind == "measured" and p["hbm_gbs"] == 6794.0
+
+
+def test_alu_roofline_of_a_profile():
+    # seven KKT applies of 103.8 MFLOP in 1.42 ms at 1.196 TFLOP/s
+    p = {"launches": 7, "ms": 1.42, "bytes": 7 * 13.2e6, "flops": 7 * 103.8e6}
+    r = bench.alu_roofline("kron_rank1_kernel", p, 1.196, "measured")
+    assert r["launches_per_step"] == 7
+    assert abs(r["avg_us"] - 1420.0 / 7) < 1e-9
+    assert abs(r["achieved"] - 103.8e6 / (1.42e-3 / 7) / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / 1.196) < 1e-12
+    assert r["algorithmic_bytes_per_launch"] == 13.2e6
+
+
+def test_alu_roofline_absent_kernel():
+    assert bench.alu_roofline("k", None, 1.0, "x") is None
+    assert bench.alu_roofline("k", {"launches": 0, "ms": 0.0, "bytes": 0, "flops": 0}, 1.0, "x") is None
+    assert bench.alu_roofline("k", {"launches": 1}, 1.0, "x") is None
