@@ -1,0 +1,85 @@
+"""Planted mistakes: each test plants one plausible error in the oracle (on
+the CPU, through monkeypatch) and checks that the pin written for that part
+of the oracle fails.  Together they show that the pins are not vacuous: a
+transposed operand, a dropped weight, a flipped sign or a swapped Kronecker
+order does not pass them."""
+import numpy as np
+import pytest
+
+import oracle.assemble as oassemble
+import oracle.kkt as okkt
+import oracle.lowrank as olowrank
+import scipy.sparse as sp
+import test_oracle_assembly as pins_assembly
+import test_oracle_bspline as pins_bspline
+import test_oracle_kkt as pins_kkt
+import test_oracle_lowrank as pins_lowrank
+
+
+def test_transposed_metric_fails_the_manufactured_solution(monkeypatch):
+    # Q = (J J^T)^{-1} omega instead of (J^T J)^{-1} omega (Sec. 3)
+    def wrong(J):
+        det = np.linalg.det(J)
+        omega = np.abs(det)
+        JJt = np.einsum("pab,pcb->pac", J, J)
+        return omega, np.linalg.inv(JJt) * omega[:, None, None], det
+    monkeypatch.setattr(oassemble, "weights_from_jacobian", wrong)
+    with pytest.raises(AssertionError):
+        pins_assembly.test_manufactured_poisson_converges("annulus")
+
+
+def test_dropped_jacobian_determinant_fails_the_volume(monkeypatch):
+    # omega = 1 in the mass matrix (the |det J| factor dropped)
+    right = oassemble.weights_from_jacobian
+
+    def wrong(J):
+        omega, Q, det = right(J)
+        return np.ones_like(omega), Q, det
+    monkeypatch.setattr(oassemble, "weights_from_jacobian", wrong)
+    with pytest.raises(AssertionError):
+        pins_assembly.test_volume_and_neumann_kernel("annulus")
+
+
+def test_flipped_kkt_sign_fails_optimality(monkeypatch):
+    # +M instead of -M in the second block row of eq. KKTSystem
+    def wrong(M, K, beta):
+        return sp.bmat([[M, None, K.T], [None, beta * M, M], [K, -M, None]], format="csc")
+    monkeypatch.setattr(okkt, "kkt_matrix", wrong)
+    with pytest.raises(AssertionError):
+        pins_kkt.test_kkt_solution_is_optimal()
+
+
+def test_flipped_gradient_sign_fails_finite_differences(monkeypatch):
+    # beta M u + M lambda instead of beta M u - M lambda
+    def wrong(M, K, b, beta, u):
+        y = okkt.state_solve(M, K, u)
+        lam = okkt.adjoint_solve(M, K, b, y)
+        return beta * (M @ u) + M @ lam, y, lam
+    monkeypatch.setattr(pins_kkt, "reduced_gradient", wrong)
+    with pytest.raises(AssertionError):
+        pins_kkt.test_reduced_gradient_matches_finite_differences()
+
+
+def test_swapped_kronecker_order_fails_the_definition(monkeypatch):
+    # kron(A3, kron(A2, A1)) instead of kron(A1, kron(A2, A3)) on C-ordered x
+    def wrong(terms):
+        out = None
+        for A1, A2, A3 in terms:
+            T = sp.kron(sp.csr_matrix(A3), sp.kron(sp.csr_matrix(A2), sp.csr_matrix(A1)))
+            out = T if out is None else out + T
+        return out.tocsr()
+    monkeypatch.setattr(olowrank, "kron_matrix", wrong)
+    with pytest.raises(AssertionError):
+        pins_lowrank.test_kron_apply_definition_tiny()
+
+
+def test_negated_derivative_fails_finite_differences(monkeypatch):
+    right = pins_bspline.basis_all
+
+    def wrong(knots, p, x, nderiv=1):
+        v, dv = right(knots, p, x, nderiv)
+        return v, (None if dv is None else -dv)
+    monkeypatch.setattr(pins_bspline, "basis_all", wrong)
+    p, knots = pins_bspline.KNOTS[1]
+    with pytest.raises(AssertionError):
+        pins_bspline.test_partition_of_unity_and_fd(p, knots)
