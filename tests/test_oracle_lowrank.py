@@ -41,6 +41,28 @@ def test_tt_svd_error_bound(tol):
         assert np.linalg.norm(tt_full(worse) - W) / np.linalg.norm(W) > tol / math.sqrt(2) * 0.999
 
 
+def test_tt_svd_threshold_splits_the_budget():
+    """The tolerance is split over the D - 1 = 2 unfoldings (threshold
+    tol ||W|| / sqrt(2) each, Sec. 3).  W = a b c + e a' b' c + e a b'' c'
+    with orthonormal a, a' and b, b', b'' and c, c' has one singular value e
+    in the tail of each unfolding.  With e = 0.9 tol both must be kept
+    (0.9 > 1/sqrt(2)); a threshold of tol per unfolding would drop both and
+    leave an error of 1.27 tol."""
+    rng = np.random.default_rng(5)
+    qa, _ = np.linalg.qr(rng.standard_normal((6, 2)))
+    qb, _ = np.linalg.qr(rng.standard_normal((4, 3)))
+    qc, _ = np.linalg.qr(rng.standard_normal((5, 2)))
+    tol = 1e-3
+    e = 0.9 * tol
+    outer = lambda x, y, z: np.einsum("i,j,k->ijk", x, y, z)
+    W = (outer(qa[:, 0], qb[:, 0], qc[:, 0]) + e * outer(qa[:, 1], qb[:, 1], qc[:, 0])
+         + e * outer(qa[:, 0], qb[:, 2], qc[:, 1]))
+    out = tt_svd(W, tol)
+    err = np.linalg.norm(tt_full(out) - W) / np.linalg.norm(W)
+    assert err <= tol
+    assert tt_ranks(out) == (2, 2)
+
+
 def test_tt_svd_separable_and_zero():
     a, b, c = (np.random.default_rng(2).standard_normal(m) for m in (5, 6, 7))
     W = np.einsum("i,j,k->ijk", a, b, c)

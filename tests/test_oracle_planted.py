@@ -83,3 +83,26 @@ def test_negated_derivative_fails_finite_differences(monkeypatch):
     p, knots = pins_bspline.KNOTS[1]
     with pytest.raises(AssertionError):
         pins_bspline.test_partition_of_unity_and_fd(p, knots)
+
+
+def test_threshold_without_sqrt_d_minus_1_fails_the_error_bound(monkeypatch):
+    # per-unfolding threshold tol ||W|| instead of tol ||W|| / sqrt(D - 1)
+    right = olowrank.tt_svd
+
+    def wrong(W, tol, rmax=None, norm=None):
+        return right(W, tol * np.sqrt(np.ndim(W) - 1), rmax, norm)
+    monkeypatch.setattr(pins_lowrank, "tt_svd", wrong)
+    with pytest.raises(AssertionError):
+        pins_lowrank.test_tt_svd_threshold_splits_the_budget()
+
+
+def test_values_for_derivatives_fail_the_univariate_route(monkeypatch):
+    # the row factor always takes basis values, never derivatives
+    right = olowrank.univariate_band
+
+    def wrong(V, D, first, n, w, du_row, du_col):
+        return right(V, D, first, n, w, False, du_col)
+    monkeypatch.setattr(olowrank, "univariate_band", wrong)
+    with pytest.raises(AssertionError):
+        pins_lowrank.test_univariate_route_exact_on_rank_one_geometry("annulus",
+                                                                       pins_lowrank.wl.quarter_annulus())
