@@ -106,3 +106,29 @@ def test_values_for_derivatives_fail_the_univariate_route(monkeypatch):
     with pytest.raises(AssertionError):
         pins_lowrank.test_univariate_route_exact_on_rank_one_geometry("annulus",
                                                                        pins_lowrank.wl.quarter_annulus())
+
+
+def test_transposed_jacobian_fails_finite_differences(monkeypatch):
+    # J[a][k] = dG_k / dxhat_a instead of dG_a / dxhat_k
+    import test_oracle_geometry as pins_geometry
+    right = pins_geometry.map_and_jacobian
+
+    def wrong(*args):
+        G, J = right(*args)
+        return G, np.swapaxes(J, 1, 2)
+    monkeypatch.setattr(pins_geometry, "map_and_jacobian", wrong)
+    with pytest.raises(AssertionError):
+        pins_geometry.test_jacobian_matches_finite_differences(pins_geometry.wl.quarter_annulus())
+
+
+def test_transposed_left_interface_fails_the_frame_projection(monkeypatch):
+    # Phi_L[a]^T instead of Phi_L[a] in the local matvec (Sec. 5, eq. KKT_red)
+    import oracle.amen as oamen
+    import test_oracle_amen as pins_amen
+    right = oamen.local_matvec
+
+    def wrong(PhiL, Ad, PhiR, x):
+        return right(np.swapaxes(PhiL, 1, 2), Ad, PhiR, x)
+    monkeypatch.setattr(pins_amen, "local_matvec", wrong)
+    with pytest.raises(AssertionError):
+        pins_amen.test_interfaces_equal_frame_projection(1)
