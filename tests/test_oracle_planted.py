@@ -132,3 +132,28 @@ def test_transposed_left_interface_fails_the_frame_projection(monkeypatch):
     monkeypatch.setattr(pins_amen, "local_matvec", wrong)
     with pytest.raises(AssertionError):
         pins_amen.test_interfaces_equal_frame_projection(1)
+
+
+def test_unmapped_gauss_weights_fail_the_span_integrals(monkeypatch):
+    # weights not scaled by half the element length (the interval map dropped)
+    right = pins_bspline.element_quadrature
+
+    def wrong(knots, q):
+        x, g = right(knots, q)
+        el = np.diff(np.unique(knots))[:, None]
+        return x, g * 2.0 / el
+    monkeypatch.setattr(pins_bspline, "element_quadrature", wrong)
+    with pytest.raises(AssertionError):
+        pins_bspline.test_element_quadrature_integrates_on_spans()
+
+
+def test_mirrored_row_stencil_fails_the_sampled_rows(monkeypatch):
+    # the row stencil read as columns: M(r, r - o) in place of M(r, r + o)
+    right = pins_assembly.sampled_rows
+
+    def wrong(geo, disc, rows):
+        Mr, Kr = right(geo, disc, rows)
+        return Mr[:, ::-1, ::-1, ::-1], Kr[:, ::-1, ::-1, ::-1]
+    monkeypatch.setattr(pins_assembly, "sampled_rows", wrong)
+    with pytest.raises(AssertionError):
+        pins_assembly.test_sampled_rows_equal_band()
