@@ -76,3 +76,26 @@ def test_alu_roofline_absent_kernel():
     assert bench.alu_roofline("k", None, 1.0, "x") is None
     assert bench.alu_roofline("k", {"launches": 0, "ms": 0.0, "bytes": 0, "flops": 0}, 1.0, "x") is None
     assert bench.alu_roofline("k", {"launches": 1}, 1.0, "x") is None
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` (the oracle on a bounded sample, host cores
+    only) prints one JSON line with the contract's keys."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                         check=True, timeout=300, cwd=root)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["higher_is_better"] is False and line["value"] > 0
+    assert line["config"]["workload"] == "quarter_annulus_p3_e64"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
