@@ -21,6 +21,12 @@
  *     (Sec. 4, discrete quadratic problem).
  *   - Banded univariate matrices are stored row-major as band[i][o] with
  *     A(i, i + o - p), o = 0..2p, entries outside the matrix are zero.
+ *   - Device memory the library needs during a call comes from a per-device
+ *     stream-ordered pool on the context stream, which keeps up to 4 GB of
+ *     released memory cached for later calls (so free memory reported by
+ *     the driver can stay lower after a call).  Calls that return handles
+ *     synchronise their stream first, so a handle is usable on any stream;
+ *     destroying a handle synchronises the device.
  */
 #ifndef IGA_H
 #define IGA_H
