@@ -30,8 +30,23 @@ if ROOT not in sys.path:
 METRIC = "KKT solve s to 1e-6 rel. residual; Kron/TT apply % of roofline, mixed vs FP64"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-FP64_FMA_TFLOPS = 1.196      # measured FP64 FMA rate of this GB300 (CUDA cores)
-FP32_FMA_TFLOPS = 74.75      # measured FP32 FMA rate
+# ALU peaks derived from unit counts and the maximum SM clock: 152 SMs, 2 FP64
+# FMA and 128 FP32 FMA per SM per clock (2 flop per FMA); at 2070 MHz that is
+# 1.26 and 80.6 TFLOP/s.  The library's own FMA micro-kernel
+# (iga_measure_fma) is run in the same job and reported beside them.
+SMS = 152
+FP64_FMA_PER_SM_CLK = 2
+FP32_FMA_PER_SM_CLK = 128
+
+
+def alu_peak_tflops(arith, pk):
+    mhz = float(pk.get("sm_max_mhz") or 2070.0)
+    per = FP64_FMA_PER_SM_CLK if arith == "fp64" else FP32_FMA_PER_SM_CLK
+    return SMS * per * 2.0 * mhz * 1e6 / 1e12
+
+
+FP64_FMA_TFLOPS = alu_peak_tflops("fp64", {})
+FP32_FMA_TFLOPS = alu_peak_tflops("fp32", {})
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel, as
 # summarised under profiles/; an entry is dropped whenever its kernel changes
 NCU_TRAFFIC = {"sample_weights_kernel": 1.0692e9}

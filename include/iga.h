@@ -110,6 +110,12 @@ size_t iga_scratch_bytes(const iga_ctx* ctx);
 iga_status iga_profile_begin(iga_ctx* ctx, const char* kernel);
 iga_status iga_profile_end(iga_ctx* ctx, uint64_t* launches, double* ms, double* bytes,
                            double* flops);
+/* Instrumentation (no counterpart in the paper): the FMA rate of the CUDA
+ * cores in TFLOP/s (2 flop per FMA) for prec IGA_FP64 or IGA_FP32, measured
+ * by a kernel of independent FMA chains over every SM, timed with CUDA
+ * events on the context stream (best of three launches after one warm-up).
+ * Synchronises. */
+iga_status iga_measure_fma(iga_ctx* ctx, iga_prec prec, double* tflops);
 
 /* ---- (a1, a2) geometry sampling ------------------------------------- */
 
@@ -239,7 +245,14 @@ iga_status iga_amen_local_matvec(iga_ctx* ctx, int r0, int n, int r1, int R0, in
  * which therefore can call neither cudaMalloc nor iga_create, which
  * allocates).  Same arguments and results as iga_amen_local_matvec, except:
  *   - `stream` is the cudaStream_t to launch on (NULL: legacy default
- *     stream); no iga_ctx is used and no error text is kept;
+ *     stream); the calling thread's current device must be the device of
+ *     that stream and of every pointer; no iga_ctx is used and no error
+ *     text is kept;
+ *   - a CUDA error already pending on the calling thread is reported as
+ *     IGA_ECUDA before any launch and left pending for its owner;
+ *   - with a bandmask the call waits for the stream to reach it before
+ *     returning (the mask is host memory borrowed for the call); without
+ *     one it returns as soon as the work is queued;
  *   - the intermediates live in a fixed 16 MiB file-scope device array, so
  *     (R0 + R1) * nvec * r0 * n * r1 * sizeof(element) must not exceed
  *     16 MiB and R0 * R1 must not exceed 4096 when a bandmask is given;

@@ -19,7 +19,10 @@ Pins: unit cube M and K equal Kronecker products of closed-form 1-D
 matrices; 1^T M 1 is the domain volume; K 1 = 0 without Dirichlet
 reduction; symmetry and definiteness; agreement with `dense_bruteforce`
 (a separately written per-point loop over full basis vectors) on 4^3
-elements; manufactured Poisson solutions converge at rate p+1.
+elements; manufactured Poisson solutions converge at rate p+1; the desired
+state yhat at points where its definition gives the value outright, and the
+load vector summed over the full space against int_Omega yhat dx in closed
+form (unit cube) or by library quadrature (annulus, twisted annulus).
 """
 from __future__ import annotations
 

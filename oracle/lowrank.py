@@ -177,19 +177,6 @@ def kron_apply(terms, x):
     return kron_matrix(terms) @ np.asarray(x).ravel()
 
 
-def kron_rows(terms, rows, x):
-    """(A x)_i for sampled multi-indices i, one row at a time (large grids)."""
-    n = tuple(t.shape[0] for t in terms[0])
-    X = np.asarray(x).reshape(n)
-    out = np.zeros(len(rows))
-    for s, (i1, i2, i3) in enumerate(rows):
-        acc = 0.0
-        for A1, A2, A3 in terms:
-            acc += np.einsum("a,b,c,abc->", A1[i1], A2[i2], A3[i3], X)
-        out[s] = acc
-    return out
-
-
 def weight_tts(geo, disc, tol, target=None):
     """TT cores of omega*g, q_kl*g (k <= l) and, with a target, yhat*omega*g.
 

@@ -1671,12 +1671,7 @@ struct Solver {
       // two warps per rank pair, up to four pairs per block
       const int ppb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / perw));
       IGA_REQUIRE(perw <= 200 * 1024, "kkt preconditioner: block too large");
-      static bool qattr = false;
-      if (!qattr) {
-        IGA_CUDA(cudaFuncSetAttribute(kkt_qd_factor_kernel<P>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-        qattr = true;
-      }
+      func_attr(kkt_qd_factor_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
       // algorithmic: LDL^T of 2n rows with half-bandwidth w and Cholesky of n
       // rows with half-bandwidth p
       prof_count(ctx, (double)BL.NB * per * sizeof(P),
@@ -1696,12 +1691,7 @@ struct Solver {
     int use_smem = perw <= 200 * 1024;
     size_t smem = use_smem ? perw * wpb : 0;
     if (!use_smem) wpb = 4;
-    static bool attr = false;
-    if (!attr) {
-      IGA_CUDA(cudaFuncSetAttribute(kkt_block_factor_kernel<P>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-      attr = true;
-    }
+    func_attr(kkt_block_factor_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     // algorithmic: banded LU with partial pivoting, 2 N kl (kl + ku) flop per block
     prof_count(ctx, (double)BL.NB * BL.N * BL.W * sizeof(P),
                2.0 * BL.NB * BL.N * (double)BL.kl * (BL.kl + BL.ku));
@@ -1725,12 +1715,7 @@ struct Solver {
       const size_t perw = (per + 3 * (size_t)BL.n) * sizeof(P);
       // two warps per rank pair, up to four pairs per block
       const int ppb = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / perw));
-      static bool qattr = false;
-      if (!qattr) {
-        IGA_CUDA(cudaFuncSetAttribute(kkt_qd_solve_kernel<P, T>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-        qattr = true;
-      }
+      func_attr(kkt_qd_solve_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
       // algorithmic: two band sweeps of 2n rows (half-bandwidth 2p+1) and two of n rows
       prof_count(ctx, (double)BL.NB * (per * sizeof(P) + 6.0 * BL.n * sizeof(T)),
                  (double)BL.NB * (8.0 * BL.n * (2 * BL.p + 1) + 4.0 * BL.n * BL.p));
@@ -1745,12 +1730,7 @@ struct Solver {
       int lu_smem = perw <= 200 * 1024;
       const int wpb = lu_smem ? (int)std::min<size_t>(4, (200 * 1024) / perw) : 4;
       size_t smem = (size_t)wpb * ((lu_smem ? per : 0) + BL.N + pivT) * sizeof(P);
-      static bool attr = false;
-      if (!attr) {
-        IGA_CUDA(cudaFuncSetAttribute(kkt_block_solve_kernel<P, T>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-        attr = true;
-      }
+      func_attr(kkt_block_solve_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
       // algorithmic: forward and back substitution, 2 N (2 kl + ku) flop per block
       prof_count(ctx, (double)BL.NB * BL.N * (BL.W * sizeof(P) + 2 * sizeof(T)),
                  2.0 * BL.NB * BL.N * (double)(2 * BL.kl + BL.ku));

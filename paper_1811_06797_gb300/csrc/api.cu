@@ -19,6 +19,28 @@ void set_error(iga_ctx* ctx, const std::string& m) {
   if (ctx) ctx->err = m;
 }
 
+void func_attr(const void* fn, cudaFuncAttribute attr, int value) {
+  struct Key {
+    const void* fn;
+    int attr, value, dev;
+    bool operator<(const Key& o) const {
+      if (fn != o.fn) return fn < o.fn;
+      if (attr != o.attr) return attr < o.attr;
+      if (value != o.value) return value < o.value;
+      return dev < o.dev;
+    }
+  };
+  static std::mutex mu;
+  static std::map<Key, bool> done;
+  int dev = 0;
+  IGA_CUDA(cudaGetDevice(&dev));
+  Key k{fn, (int)attr, value, dev};
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(k)) return;
+  IGA_CUDA(cudaFuncSetAttribute(fn, attr, value));
+  done[k] = true;
+}
+
 void prof_start(iga_ctx* ctx) {
   if (ctx->prof_used + 2 > ctx->prof_ev.size()) {
     for (int i = 0; i < 64; ++i) {

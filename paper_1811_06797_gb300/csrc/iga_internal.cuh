@@ -282,4 +282,14 @@ void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
 
 void set_error(iga_ctx* ctx, const std::string& m);
 
+// cudaFuncSetAttribute(fn, attr, value) once per (function, attribute,
+// value, device): a function attribute belongs to the device that was
+// current when it was set, so a second device needs its own call.  Thread
+// safe.
+void func_attr(const void* fn, cudaFuncAttribute attr, int value);
+template <typename F>
+inline void func_attr(F* fn, cudaFuncAttribute attr, int value) {
+  func_attr(reinterpret_cast<const void*>(fn), attr, value);
+}
+
 }  // namespace iga

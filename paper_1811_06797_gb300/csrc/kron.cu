@@ -253,12 +253,7 @@ static void launch_kron_job(iga_ctx* ctx, const KronJob<T>& job, const KronTile&
   size_t H1 = g.T1 + 2 * P, H2 = g.T2 + 2 * P;
   size_t smem = (H1 * H2 * g.T3 + H1 * g.T2 * g.T3 + (size_t)(g.T1 + g.T2 + g.T3) * B) * sizeof(T);
   IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: tile does not fit in shared memory");
-  static bool attr_set = false;
-  if (!attr_set) {
-    IGA_CUDA(cudaFuncSetAttribute(kron_rank1_kernel<T, P, NY>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set = true;
-  }
+  func_attr(kron_rank1_kernel<T, P, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   {
     // algorithmic: read every input, write every output (and read it when
     // accumulating); 3 banded mode products of 2(2P+1) flop per point and term

@@ -15,6 +15,8 @@
 #include <cmath>
 
 #include <cooperative_groups.h>
+#include <map>
+#include <mutex>
 
 #include "iga_internal.cuh"
 
@@ -630,14 +632,8 @@ void qrcp_truncate(iga_ctx* ctx, const double* B, int m, int c3, int si, int sa,
   a.m = m; a.c3 = c3; a.si = si; a.sa = sa; a.r = r; a.kick = kick;
   a.jmax = std::max(1, std::min(jmax, m)); a.mc = mc;
   a.gwork = head + slice <= limit ? nullptr : scratch<double>(ctx, SLOT_QRCP_WORK, (size_t)C * mc * ncol);
-  static bool attr = false;
-  if (!attr) {
-    IGA_CUDA(cudaFuncSetAttribute(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)limit));
-    IGA_CUDA(cudaFuncSetAttribute(qrcp_cluster_kernel,
-                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    attr = true;
-  }
+  func_attr(qrcp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  func_attr(qrcp_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(256);
@@ -670,13 +666,17 @@ static size_t qr_cluster_smem(int mc, int k) {
 // largest cluster of 256-thread CTAs with 200 KB of shared memory each that
 // the GPU can schedule (16 with the non-portable size, else 8, else 1)
 static int qr_cluster_max(iga_ctx* ctx) {
-  static int cmax = 0;
-  if (cmax != 0) return cmax;
   const size_t limit = 200 * 1024;
-  IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-  IGA_CUDA(cudaFuncSetAttribute(householder_qr_cluster_kernel,
-                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  func_attr(householder_qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)limit);
+  func_attr(householder_qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  static std::mutex mu;
+  static std::map<int, int> cmax_of;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cmax_of.find(ctx->device);
+    if (it != cmax_of.end()) return it->second;
+  }
   int best = 1;
   for (int c : {16, 8}) {
     cudaLaunchConfig_t q = {};
@@ -698,9 +698,11 @@ static int qr_cluster_max(iga_ctx* ctx) {
     }
     (void)cudaGetLastError();
   }
-  (void)ctx;
-  cmax = best;
-  return cmax;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cmax_of[ctx->device] = best;
+  }
+  return best;
 }
 
 void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k) {
@@ -919,14 +921,8 @@ void jacobi_eig_batched(iga_ctx* ctx, double* const* A, double* const* V, double
     batch.p[i].Vwork = mode == 2 ? nullptr
                                  : scratch<double>(ctx, 220 + i, (size_t)k[i] * k[i]);
   }
-  static bool attr = false;
-  if (!attr) {
-    IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<double>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-    IGA_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<float>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-    attr = true;
-  }
+  func_attr(jacobi_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  func_attr(jacobi_eig_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
   {
     // algorithmic: a symmetric eigen-decomposition with eigenvectors, 9 k^3 flop
     double fl = 0.0, by = 0.0;

@@ -246,6 +246,9 @@ extern "C" iga_status iga_amen_local_matvec_noalloc(void* stream, int r0, int n,
   size_t per = (size_t)nvec * r0 * n * r1;
   if (per * (size_t)(R0 + R1) * es > NOALLOC_SCRATCH_BYTES) return IGA_EINVAL;
   if (bandmask && (size_t)R0 * R1 > NOALLOC_MASK_BYTES) return IGA_EINVAL;
+  // an error left pending by earlier work on this thread is not this call's:
+  // report it without consuming it, before any launch
+  if (cudaPeekAtLastError() != cudaSuccess) return IGA_ECUDA;
   void* scratch = nullptr;
   void* mask = nullptr;
   iga_status s = noalloc_addresses(&scratch, &mask);
@@ -258,9 +261,14 @@ extern "C" iga_status iga_amen_local_matvec_noalloc(void* stream, int r0, int n,
     dmask = static_cast<const unsigned char*>(mask);
   }
   if (prec == IGA_FP64)
-    return noalloc_run<double>(st, r0, n, r1, R0, R1, p, (const double*)PhiL, (const double*)bands,
-                               (const double*)PhiR, dmask, nvec, (const double*)x, (double*)y,
-                               scratch);
-  return noalloc_run<float>(st, r0, n, r1, R0, R1, p, (const float*)PhiL, (const float*)bands,
-                            (const float*)PhiR, dmask, nvec, (const float*)x, (float*)y, scratch);
+    s = noalloc_run<double>(st, r0, n, r1, R0, R1, p, (const double*)PhiL, (const double*)bands,
+                            (const double*)PhiR, dmask, nvec, (const double*)x, (double*)y,
+                            scratch);
+  else
+    s = noalloc_run<float>(st, r0, n, r1, R0, R1, p, (const float*)PhiL, (const float*)bands,
+                           (const float*)PhiR, dmask, nvec, (const float*)x, (float*)y, scratch);
+  // the host mask is only borrowed for the call: wait until the stream has
+  // copied it (this allocates nothing)
+  if (s == IGA_OK && bandmask && cudaStreamSynchronize(st) != cudaSuccess) return IGA_ECUDA;
+  return s;
 }

@@ -1,0 +1,74 @@
+// Instrumentation (no counterpart in the paper): the FMA issue rate of the
+// CUDA cores, measured with CUDA events on the context stream, so that the
+// roofline denominators of the FP64 and FP32 kernels come from this library
+// and not from a constant.  Each thread runs FMA_CHAINS independent
+// dependency chains of fma(a, b, c) for `iters` steps; the chains are folded
+// into one store per thread so that nothing is optimised away.
+#include <algorithm>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+constexpr int FMA_CHAINS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_rate_kernel(int iters, T b, T c, T* __restrict__ out) {
+  T a[FMA_CHAINS];
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; ++k) a[k] = fma(a[k], b, c);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) s += a[k];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+static double fma_rate(iga_ctx* ctx) {
+  // 8 CTAs of 256 threads per SM: enough resident warps to cover the FMA
+  // latency; b < 1 keeps the chains finite
+  const int blocks = ctx->nsm * 8, threads = 256, iters = 1 << 14;
+  DevBuf<T> out((size_t)blocks * threads);
+  cudaEvent_t e0, e1;
+  IGA_CUDA(cudaEventCreate(&e0));
+  IGA_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up
+    IGA_CUDA(cudaEventRecord(e0, ctx->stream));
+    IGA_LAUNCH(ctx, fma_rate_kernel<T>, blocks, threads, 0, iters, (T)0.999, (T)1e-4, out.p);
+    IGA_CUDA(cudaEventRecord(e1, ctx->stream));
+    IGA_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    IGA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  double flops = 2.0 * FMA_CHAINS * (double)iters * blocks * threads;
+  return flops / (best * 1e-3) / 1e12;
+}
+
+}  // namespace iga
+
+using namespace iga;
+
+extern "C" iga_status iga_measure_fma(iga_ctx* ctx, iga_prec prec, double* tflops) {
+  if (!ctx || !tflops) return IGA_EINVAL;
+  try {
+    AllocScope scope(ctx->stream);
+    if (prec == IGA_FP64) *tflops = fma_rate<double>(ctx);
+    else if (prec == IGA_FP32) *tflops = fma_rate<float>(ctx);
+    else throw Error(IGA_EINVAL, "measure_fma: precision must be IGA_FP64 or IGA_FP32");
+    return IGA_OK;
+  } catch (const Error& e) {
+    set_error(ctx, e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    set_error(ctx, e.what());
+    return IGA_ECUDA;
+  }
+}

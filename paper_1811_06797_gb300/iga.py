@@ -80,6 +80,7 @@ def lib():
         "iga_scratch_bytes": (C.c_size_t, [vp]),
         "iga_profile_begin": (st, [vp, C.c_char_p]),
         "iga_profile_end": (st, [vp, P(C.c_uint64), P(d), P(d), P(d)]),
+        "iga_measure_fma": (st, [vp, i, P(d)]),
         "iga_sample_weights": (st, [vp, P(Geometry_), P(Space_), P(Target_), vp]),
         "iga_tt_svd": (st, [vp, vp, i, i, i, d, d, i, P(vp)]),
         "iga_tt_info": (st, [vp, P(C.c_int), P(C.c_int)]),
@@ -196,6 +197,13 @@ class Context:
         _check(self, lib().iga_profile_end(self.handle, C.byref(n), C.byref(ms), C.byref(by),
                                           C.byref(fl)))
         return {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
+
+
+def iga_measure_fma(ctx, prec):
+    """Measured FMA rate of the CUDA cores in TFLOP/s (IGA_FP64 or IGA_FP32)."""
+    r = C.c_double()
+    _check(ctx, lib().iga_measure_fma(ctx.handle, int(prec), C.byref(r)))
+    return r.value
 
 
 class _Keep:
@@ -443,42 +451,79 @@ def iga_kkt_apply(ctx, M, K, beta, z, out):
     return out
 
 
+def _local_matvec_args(PhiL, bands, PhiR, x, y, bandmask):
+    """Check the operands of a local matvec before any launch.
+
+    All five tensors must be contiguous CUDA tensors of one dtype (float64 or
+    float32) on one device, with PhiL (R0, r0, r0), bands (R0, R1, n, 2p+1),
+    PhiR (R1, r1, r1) and x, y (nvec, r0, n, r1); a band mask has R0 * R1
+    entries.  Returns the sizes and the host mask pointer (or None).
+    """
+    ts = {"PhiL": PhiL, "bands": bands, "PhiR": PhiR, "x": x, "y": y}
+    for name, t in ts.items():
+        if t is None or not t.is_cuda:
+            raise IgaError(1, f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise IgaError(1, f"{name} must be contiguous")
+        if t.dtype != x.dtype:
+            raise IgaError(1, f"{name} has dtype {t.dtype}, x has {x.dtype}")
+        if t.device != x.device:
+            raise IgaError(1, f"{name} is on {t.device}, x is on {x.device}")
+    _prec(x)
+    if PhiL.dim() != 3 or PhiR.dim() != 3 or bands.dim() != 4 or x.dim() != 4:
+        raise IgaError(1, "expected PhiL (R0,r0,r0), bands (R0,R1,n,2p+1), PhiR (R1,r1,r1), "
+                          "x (nvec,r0,n,r1)")
+    R0, r0, r0b = PhiL.shape
+    R1, r1, r1b = PhiR.shape
+    nvec, xr0, n, xr1 = x.shape
+    if r0b != r0 or r1b != r1:
+        raise IgaError(1, "PhiL and PhiR must be square in their last two dimensions")
+    if tuple(bands.shape[:3]) != (R0, R1, n) or bands.shape[3] % 2 != 1:
+        raise IgaError(1, f"bands must be ({R0}, {R1}, {n}, 2p+1), got {tuple(bands.shape)}")
+    if (xr0, xr1) != (r0, r1) or tuple(y.shape) != tuple(x.shape):
+        raise IgaError(1, f"x and y must be (nvec, {r0}, {n}, {r1})")
+    if x.data_ptr() == y.data_ptr():
+        raise IgaError(1, "x and y must not overlap")
+    mask = keep = None
+    if bandmask is not None:
+        keep = np.ascontiguousarray(bandmask, dtype=np.uint8)
+        if keep.size != R0 * R1:
+            raise IgaError(1, f"bandmask must have R0 * R1 = {R0 * R1} entries")
+        mask = keep.ctypes.data_as(C.POINTER(C.c_ubyte))
+    p = (bands.shape[3] - 1) // 2
+    return (r0, n, r1, R0, R1, p, nvec), mask, keep
+
+
 def iga_amen_local_matvec(ctx, PhiL, bands, PhiR, x, y, bandmask=None):
     """PhiL (R0,r0,r0), bands (R0,R1,n,2p+1), PhiR (R1,r1,r1), x/y (nvec,r0,n,r1)."""
-    R0, r0, _ = PhiL.shape
-    R1, r1, _ = PhiR.shape
-    n, b = bands.shape[2], bands.shape[3]
-    nvec = x.shape[0]
-    mask = None
-    if bandmask is not None:
-        m = np.ascontiguousarray(bandmask, dtype=np.uint8)
-        mask = m.ctypes.data_as(C.POINTER(C.c_ubyte))
-    _check(ctx, lib().iga_amen_local_matvec(ctx.handle, r0, n, r1, R0, R1, (b - 1) // 2,
-                                            _ptr(PhiL), _ptr(bands), _ptr(PhiR), mask, nvec,
-                                            _ptr(x), _ptr(y), _prec(x)))
+    (r0, n, r1, R0, R1, p, nvec), mask, keep = _local_matvec_args(PhiL, bands, PhiR, x, y,
+                                                                  bandmask)
+    _check(ctx, lib().iga_amen_local_matvec(ctx.handle, r0, n, r1, R0, R1, p, _ptr(PhiL),
+                                            _ptr(bands), _ptr(PhiR), mask, nvec, _ptr(x),
+                                            _ptr(y), _prec(x)))
+    del keep
     return y
 
 
 def iga_amen_local_matvec_noalloc(PhiL, bands, PhiR, x, y, bandmask=None, stream=None):
-    """Allocation-free local matvec on `stream` (default: torch's current stream).
+    """Allocation-free local matvec on `stream` (default: the current stream of x's device).
 
     Same contraction as iga_amen_local_matvec, using the library's fixed
     device scratch instead of allocating; raises IgaError (IGA_EINVAL) for
-    sizes beyond that fixed scratch.
+    sizes beyond that fixed scratch.  The call runs with x's device current,
+    so the library picks that device's scratch.
     """
     import torch
-    R0, r0, _ = PhiL.shape
-    R1, r1, _ = PhiR.shape
-    n, b = bands.shape[2], bands.shape[3]
-    nvec = x.shape[0]
-    mask = None
-    if bandmask is not None:
-        m = np.ascontiguousarray(bandmask, dtype=np.uint8)
-        mask = m.ctypes.data_as(C.POINTER(C.c_ubyte))
-    s = stream if stream is not None else torch.cuda.current_stream()
-    st = lib().iga_amen_local_matvec_noalloc(C.c_void_p(s.cuda_stream), r0, n, r1, R0, R1,
-                                             (b - 1) // 2, _ptr(PhiL), _ptr(bands), _ptr(PhiR),
-                                             mask, nvec, _ptr(x), _ptr(y), _prec(x))
+    (r0, n, r1, R0, R1, p, nvec), mask, keep = _local_matvec_args(PhiL, bands, PhiR, x, y,
+                                                                  bandmask)
+    with torch.cuda.device(x.device):
+        s = stream if stream is not None else torch.cuda.current_stream(x.device)
+        if s.device != x.device:
+            raise IgaError(1, f"stream is on {s.device}, the tensors on {x.device}")
+        st = lib().iga_amen_local_matvec_noalloc(C.c_void_p(s.cuda_stream), r0, n, r1, R0, R1,
+                                                 p, _ptr(PhiL), _ptr(bands), _ptr(PhiR), mask,
+                                                 nvec, _ptr(x), _ptr(y), _prec(x))
+    del keep
     if st != 0:
         raise IgaError(st, "iga_amen_local_matvec_noalloc failed (sizes beyond the fixed "
                            "16 MiB scratch, invalid arguments or a CUDA error)")

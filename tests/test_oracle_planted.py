@@ -157,3 +157,47 @@ def test_mirrored_row_stencil_fails_the_sampled_rows(monkeypatch):
     monkeypatch.setattr(pins_assembly, "sampled_rows", wrong)
     with pytest.raises(AssertionError):
         pins_assembly.test_sampled_rows_equal_band()
+
+
+def _gauss_variant(width_factor, sign):
+    right = oassemble.target_values
+
+    def wrong(kind, params, x):
+        if kind != oassemble.TARGET_GAUSS:
+            return right(kind, params, x)
+        c = np.asarray(params[:3])
+        return np.exp(sign * np.sum((x - c) ** 2, axis=1) / (width_factor * params[3]))
+    return wrong
+
+
+@pytest.mark.parametrize("width_factor,sign", [(2.0, -1.0), (1.0, 1.0)])
+def test_wrong_gaussian_target_fails_its_pins(monkeypatch, width_factor, sign):
+    # exp(-|x - c|^2 / (2 w)) (a variance-style width) or exp(+|x - c|^2 / w)
+    # (a dropped minus sign) in the desired state of Sec. 4
+    import test_oracle_target as pins_target
+    wrong = _gauss_variant(width_factor, sign)
+    monkeypatch.setattr(pins_target, "target_values", wrong)
+    with pytest.raises(AssertionError):
+        pins_target.test_gaussian_target_at_its_centre_and_one_width_away()
+    monkeypatch.setattr(oassemble, "target_values", wrong)
+    with pytest.raises(AssertionError):
+        pins_target.test_load_of_the_gaussian_on_the_unit_cube()
+    with pytest.raises(AssertionError):
+        pins_target.test_load_of_the_gaussian_on_the_annulus_matches_library_quadrature(0.0)
+
+
+def test_sine_target_with_a_shifted_phase_fails_its_pins(monkeypatch):
+    # prod cos(pi x_k) in place of prod sin(pi x_k)
+    import test_oracle_target as pins_target
+    right = oassemble.target_values
+
+    def wrong(kind, params, x):
+        if kind == oassemble.TARGET_SINPROD:
+            return np.prod(np.cos(np.pi * x), axis=1)
+        return right(kind, params, x)
+    monkeypatch.setattr(pins_target, "target_values", wrong)
+    with pytest.raises(AssertionError):
+        pins_target.test_sine_product_target_vanishes_on_the_faces_and_peaks_in_the_middle()
+    monkeypatch.setattr(oassemble, "target_values", wrong)
+    with pytest.raises(AssertionError):
+        pins_target.test_load_of_the_sine_product_on_the_unit_cube()

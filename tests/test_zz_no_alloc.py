@@ -77,3 +77,31 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     with pytest.raises(iga.IgaError) as e:
         iga.iga_amen_local_matvec_noalloc(PhiL, bands, PhiR, x, y)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_on_a_side_stream_with_two_different_masks(env, prec):
+    # the shared mask buffer is safe only through stream order: two masked
+    # calls in a row on one non-default stream, each with its own mask
+    ctx, torch, iga = env
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = 1e-13 if prec == "fp64" else 1e-5
+    rng = np.random.default_rng(12)
+    cases = [_case(rng, 5, 19, 6, 3, 4, 2, 2, dt, torch, True),
+             _case(rng, 5, 19, 6, 3, 4, 2, 2, dt, torch, True)]
+    assert not np.array_equal(cases[0][4], cases[1][4])
+    refs = [torch.empty(c[3].shape, dtype=dt, device="cuda") for c in cases]
+    for (PhiL, bands, PhiR, x, mask), ref in zip(cases, refs):
+        iga.iga_amen_local_matvec(ctx, PhiL, bands, PhiR, x, ref, bandmask=mask)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    outs = [torch.full(c[3].shape, float("nan"), dtype=dt, device="cuda") for c in cases]
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for (PhiL, bands, PhiR, x, mask), out in zip(cases, outs):
+            iga.iga_amen_local_matvec_noalloc(PhiL, bands, PhiR, x, out, bandmask=mask,
+                                              stream=side)
+    side.synchronize()
+    for out, ref in zip(outs, refs):
+        err = (out.double() - ref.double()).norm() / ref.double().norm()
+        assert float(err) < tol, float(err)
