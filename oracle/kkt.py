@@ -16,9 +16,15 @@ J(y, u) = 1/2 y^T M y - b^T y + 1/2 c + beta/2 u^T M u  (c = int yhat^2 omega),
 and along the state equation the reduced gradient is beta M u - M lam with
 lam the adjoint K^T lam = b - M y.
 
+For grids too large for the direct solve, `reduced_solve` runs conjugate
+gradients on the reduced system (M + beta K M^{-1} K) y = b obtained by
+eliminating u and lam (rows 2 and 3), optionally preconditioned by the
+Kronecker approximation `kron_schur_preconditioner`.
+
 Pins: the unit-cube fast-diagonalisation solve (independent of SuperLU),
-the gradient against central finite differences, and first-order
-optimality of the KKT solution (tests/test_oracle_kkt.py).
+the gradient against central finite differences, first-order optimality of
+the KKT solution, and the reduced CG solve against the direct solve on
+small curved grids (tests/test_oracle_kkt.py).
 """
 from __future__ import annotations
 
@@ -100,3 +106,66 @@ def fast_diag_solve(M1s, K1s, beta, b):
     ut = lt / beta
     back = lambda T: np.einsum("ia,jb,kc,abc->ijk", Vs[0], Vs[1], Vs[2], T).ravel()
     return back(yt), back(ut), back(lt)
+
+
+def reduced_solve(M_apply, K_apply, Minv_apply, beta, b, tol=1e-12, precond=None, maxit=10000):
+    """Stationary KKT solve through the reduced (Schur) system, by conjugate gradients.
+
+    Rows 2 and 3 of eq. KKTSystem (one time step) give lam = beta u and
+    M u = K y, so u = M^{-1} K y; row 1, M y + K^T lam = b with K = K^T, then
+    reads
+
+        S y = (M + beta K M^{-1} K) y = b,
+
+    with S symmetric positive definite.  CG on S (preconditioned by `precond`,
+    a callable approximating S^{-1}; None for plain CG) until
+    ||b - S y|| <= tol ||b||, then u = M^{-1} K y and lam = beta u.  The
+    operators are callables on flat vectors.  Returns (y, u, lam, iterations).
+    """
+    b = np.asarray(b, dtype=np.float64)
+    S = lambda v: M_apply(v) + beta * K_apply(Minv_apply(K_apply(v)))
+    P = precond if precond is not None else (lambda v: v)
+    y = np.zeros_like(b)
+    r = b.copy()
+    z = P(r)
+    d = z.copy()
+    rz = r @ z
+    nb = np.linalg.norm(b)
+    it = 0
+    while np.linalg.norm(r) > tol * nb and it < maxit:
+        Sd = S(d)
+        alpha = rz / (d @ Sd)
+        y += alpha * d
+        r -= alpha * Sd
+        z = P(r)
+        rz_new = r @ z
+        d = z + (rz_new / rz) * d
+        rz = rz_new
+        it += 1
+    u = Minv_apply(K_apply(y))
+    return y, u, beta * u, it
+
+
+def kron_schur_preconditioner(M1s, G1s, beta):
+    """Approximate inverse of S = M + beta K M^{-1} K for CG (changes the
+    iteration count, not the solution of `reduced_solve`).
+
+    With M ~ M_1 (x) M_2 (x) M_3 and K ~ sum_d G_d (x) M_e (x) M_f the
+    generalised eigenvectors V_d of (G_d, M_d) diagonalise both, and
+    S ~ V (I + beta Kappa^2) V^T with Kappa = Lambda_1 (+) Lambda_2 (+)
+    Lambda_3 (the same algebra as `fast_diag_solve`; exact on the unit cube).
+    """
+    Vs, lams = [], []
+    for M1, G1 in zip(M1s, G1s):
+        lam, V = sla.eigh(G1, M1)
+        Vs.append(V)
+        lams.append(lam)
+    n = [V.shape[0] for V in Vs]
+    kap = lams[0][:, None, None] + lams[1][None, :, None] + lams[2][None, None, :]
+    dinv = 1.0 / (1.0 + beta * kap ** 2)
+
+    def apply(r):
+        R = r.reshape(n)
+        T = np.einsum("ia,jb,kc,ijk->abc", Vs[0], Vs[1], Vs[2], R, optimize=True) * dinv
+        return np.einsum("ia,jb,kc,abc->ijk", Vs[0], Vs[1], Vs[2], T, optimize=True).ravel()
+    return apply

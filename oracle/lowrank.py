@@ -16,11 +16,13 @@ Test infrastructure only (see the package header).
                       cores of eq. TTranks as the canonical terms.
   kron_apply       -- y = sum_a (A_1^a (x) A_2^a (x) A_3^a) x, written out with
                       scipy.sparse.kron (the definition).
+  kron_apply_modes -- the same product as three mode products (the Kronecker
+                      identity), for large grids.
 
 Pins: TT-SVD reproduces random exact-rank tensors and respects its error
 bound, separable tensors come out at rank 1; the univariate route equals the
 3-D assembly on exact-rank geometry; kron_apply equals an explicit dense
-Kronecker product on tiny sizes.
+Kronecker product on tiny sizes, and kron_apply_modes equals kron_apply.
 """
 from __future__ import annotations
 
@@ -175,6 +177,19 @@ def kron_matrix(terms):
 def kron_apply(terms, x):
     """y = sum_a (A_1^a (x) A_2^a (x) A_3^a) x for x flattened in C order."""
     return kron_matrix(terms) @ np.asarray(x).ravel()
+
+
+def kron_apply_modes(terms, x):
+    """The same y = sum_a (A_1^a (x) A_2^a (x) A_3^a) x through the identity
+    (A_1 (x) A_2 (x) A_3) vec(X) = vec(X x_1 A_1 x_2 A_2 x_3 A_3) (three mode
+    products on the C-ordered tensor), for grids where the explicit sparse
+    Kronecker matrix would be too large."""
+    n = tuple(t.shape[1] for t in terms[0])
+    X = np.asarray(x, dtype=np.float64).reshape(n)
+    out = np.zeros(tuple(t.shape[0] for t in terms[0]))
+    for A1, A2, A3 in terms:
+        out += np.einsum("ia,jb,kc,abc->ijk", A1, A2, A3, X, optimize=True)
+    return out.ravel()
 
 
 def weight_tts(geo, disc, tol, target=None):

@@ -88,3 +88,42 @@ def test_objective_definition():
     b = M @ yh
     c = yh @ b
     assert abs(objective(M, b, c, 0.3, yh, np.zeros_like(yh))) < 1e-14
+
+
+@pytest.mark.parametrize("geo,beta", [(wl.quarter_annulus(), 1e-3),
+                                      (wl.quarter_annulus(twist=math.pi / 4), 1e-5),
+                                      (wl.random_volume(), 1e-4)])
+def test_reduced_cg_equals_direct_solve(geo, beta):
+    # eliminating u and lam (rows 2 and 3 of eq. KKTSystem) and solving the
+    # Schur system by CG must reproduce SuperLU on the full KKT matrix
+    import scipy.sparse.linalg as spla
+    from oracle.kkt import reduced_solve
+    work = wl.small(geo, 2, 4, wl.Target(wl.TARGET_GAUSS, wl.ANNULUS_CENTROID, 0.1), beta=beta)
+    M, K, b = _system(work)
+    y, u, lam = kkt_solve(M, K, beta, b)
+    lu = spla.splu(M.tocsc())
+    yr, ur, lr, it = reduced_solve(lambda v: M @ v, lambda v: K @ v, lu.solve, beta, b, tol=1e-13)
+    assert it > 3
+    for a, c in ((yr, y), (ur, u), (lr, lam)):
+        assert np.linalg.norm(a - c) < 1e-9 * np.linalg.norm(c)
+
+
+def test_reduced_cg_with_kronecker_preconditioner_on_the_unit_cube():
+    # on the unit cube the Kronecker preconditioner is the exact inverse of S,
+    # so preconditioned CG stops after one step at the fast-diagonalisation
+    # solution
+    from oracle.kkt import kron_schur_preconditioner, reduced_solve
+    E, beta = 6, 1e-6
+    work = wl.small(wl.unit_cube(), 2, E, beta=beta)
+    M, K, b = _system(work)
+    M1, K1 = _exact_1d_interior(work.space.knots[0], 2)
+    P = kron_schur_preconditioner([M1] * 3, [K1] * 3, beta)
+    n1 = M1.shape[0]
+    M1i = np.linalg.inv(M1)
+    Mi = lambda v: np.einsum("ia,jb,kc,abc->ijk", M1i, M1i, M1i, v.reshape((n1,) * 3)).ravel()
+    y, u, lam, it = reduced_solve(lambda v: M @ v, lambda v: K @ v, Mi, beta, b, tol=1e-12,
+                                  precond=P)
+    yf, uf, lf = fast_diag_solve([M1] * 3, [K1] * 3, beta, b)
+    assert it <= 2
+    for a, c in ((y, yf), (u, uf), (lam, lf)):
+        assert np.linalg.norm(a - c) < 1e-8 * np.linalg.norm(c)

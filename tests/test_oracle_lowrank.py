@@ -142,3 +142,13 @@ def test_random_volume_high_rank_within_tolerance():
         assert _fro_rel(kron_matrix(Mt), band_to_csr(Mb)) < 10 * tol
         assert _fro_rel(kron_matrix(Kt), band_to_csr(Kb)) < 10 * tol
     assert min(tt_ranks(tts["omega"])) > 3
+
+
+def test_kron_apply_modes_equals_the_sparse_definition():
+    from oracle.lowrank import kron_apply_modes
+    rng = np.random.default_rng(4)
+    terms = [[rng.standard_normal((m, m)) for m in (5, 3, 4)] for _ in range(3)]
+    x = rng.standard_normal(60)
+    assert np.allclose(kron_apply_modes(terms, x), kron_apply(terms, x), rtol=0, atol=1e-12)
+    dense = sum(np.kron(t[0], np.kron(t[1], t[2])) for t in terms)
+    assert np.allclose(kron_apply_modes(terms, x), dense @ x, atol=1e-12)

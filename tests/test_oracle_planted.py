@@ -201,3 +201,23 @@ def test_sine_target_with_a_shifted_phase_fails_its_pins(monkeypatch):
     monkeypatch.setattr(oassemble, "target_values", wrong)
     with pytest.raises(AssertionError):
         pins_target.test_load_of_the_sine_product_on_the_unit_cube()
+
+
+@pytest.mark.parametrize("mistake", ["minus", "no_minv"])
+def test_wrong_schur_operator_fails_the_reduced_solve_pin(monkeypatch, mistake):
+    # (M - beta K M^{-1} K) or (M + beta K K) in place of the Schur operator
+    # of eq. KKTSystem after eliminating u and lambda
+    right = okkt.reduced_solve
+
+    def wrong(M_apply, K_apply, Minv_apply, beta, b, **kw):
+        if mistake == "minus":
+            return right(M_apply, K_apply, Minv_apply, -beta, b, **kw)
+        return right(M_apply, K_apply, lambda v: v, beta, b, **kw)
+    monkeypatch.setattr(okkt, "reduced_solve", wrong)
+    with pytest.raises(AssertionError):
+        pins_kkt.test_reduced_cg_equals_direct_solve(oassemble_geo(), 1e-3)
+
+
+def oassemble_geo():
+    from paper_1811_06797_gb300 import workloads as wl
+    return wl.quarter_annulus()
