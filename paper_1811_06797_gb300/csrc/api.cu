@@ -19,6 +19,19 @@ void set_error(iga_ctx* ctx, const std::string& m) {
   if (ctx) ctx->err = m;
 }
 
+void tc_flag_reset(iga_ctx* ctx) {
+  IGA_CUDA(cudaMemsetAsync(ctx->dflag + 1, 0, sizeof(int), ctx->stream));
+}
+
+void tc_flag_check(iga_ctx* ctx, const char* what) {
+  IGA_CUDA(cudaMemcpyAsync(ctx->hflag + 1, ctx->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->hflag[1] != 0)
+    throw Error(IGA_ETIMEOUT, std::string(what) + ": a bounded wait of the tensor-core pipeline "
+                                                  "gave up");
+}
+
 void func_attr(const void* fn, cudaFuncAttribute attr, int value) {
   struct Key {
     const void* fn;
@@ -434,6 +447,7 @@ iga_status iga_create(iga_ctx** out, void* stream) {
     IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
     IGA_CUDA(cudaMalloc((void**)&ctx->dflag, 64 * sizeof(int)));
     IGA_CUDA(cudaMallocHost((void**)&ctx->hflag, 64 * sizeof(int)));
+    IGA_CUDA(cudaMemset(ctx->dflag, 0, 64 * sizeof(int)));
     *out = ctx;
     return IGA_OK;
   } catch (const ::iga::Error& e) {
@@ -701,13 +715,21 @@ void iga_op_destroy(iga_op* op) { delete op; }
 iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
                           double beta, void* y, iga_prec prec) {
   if (!ctx) return IGA_EINVAL;
-  IGA_TRY(ctx, kron_apply_impl(ctx, A, alpha, x, beta, y, prec))
+  IGA_TRY(ctx, {
+    if (prec == IGA_TF32) tc_flag_reset(ctx);
+    kron_apply_impl(ctx, A, alpha, x, beta, y, prec);
+    if (prec == IGA_TF32) tc_flag_check(ctx, "kron_apply");
+  })
 }
 
 iga_status iga_kkt_apply(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
                          const void* z, void* out, iga_prec prec) {
   if (!ctx) return IGA_EINVAL;
-  IGA_TRY(ctx, kkt_apply_impl(ctx, M, K, beta, z, out, prec))
+  IGA_TRY(ctx, {
+    if (prec == IGA_TF32) tc_flag_reset(ctx);
+    kkt_apply_impl(ctx, M, K, beta, z, out, prec);
+    if (prec == IGA_TF32) tc_flag_check(ctx, "kkt_apply");
+  })
 }
 
 }  // extern "C"

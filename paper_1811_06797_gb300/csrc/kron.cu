@@ -9,8 +9,10 @@
 // directions 1 and 2 (reading x through L1), then the mode-2 and mode-1
 // products in shared memory, for every term in turn, and writes y once.
 // x is read from HBM once per tile (halo re-reads hit L1/L2) and y written
-// once.  TT-matrix blocks (ranks > 1) use staged single-mode products with
-// full-size intermediates.
+// once.  TT-matrix blocks (ranks > 1) in TF32 go through the fused tcgen05
+// kernel of ttm_tc.cu; in FP64 and plain FP32 they use staged single-mode
+// products with full-size intermediates and a batched GEMM for the rank
+// contraction.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -423,6 +425,13 @@ __global__ void ttm_mode1_kernel(const T* __restrict__ bands1, int R1, int n1, i
 template <typename T, int P>
 static void ttm_block_gemm(iga_ctx* ctx, const iga_op* A, const OpBlock& blk, T alpha, const T* x,
                            T* y, bool tf32) {
+  if constexpr (sizeof(T) == 4) {
+    // TF32: the fused tcgen05 kernel (one launch per block, O(tile) scratch)
+    if (tf32 && ttm_tc_block(ctx, band_ptr<float>(A, 0, blk.off[0]),
+                             band_ptr<float>(A, 1, blk.off[1]), band_ptr<float>(A, 2, blk.off[2]),
+                             blk.R1, blk.R2, A->n, P, (float)alpha, x, y))
+      return;
+  }
   const int n1 = A->n[0], n2 = A->n[1], n3 = A->n[2];
   constexpr int B = 2 * P + 1;
   const int R1 = blk.R1, R2 = blk.R2, Kd = B * R2;

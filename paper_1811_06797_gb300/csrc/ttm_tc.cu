@@ -1,0 +1,593 @@
+// TT-matrix Kronecker apply on the 5th-generation tensor cores (step a5,
+// blocks with TT ranks above one):
+//
+//   y += alpha sum_{a,b} (A1[a] (x) A2[a,b] (x) A3[b]) x        (Sec. 5, eq. K_kron)
+//
+// with banded univariate factors of half-bandwidth P.  Written as three
+// contractions,
+//   Z[j2][b](j1, i3)  = sum_o3 A3[b](i3, o3) x(j1, j2, i3 + o3 - P)       mode 3
+//   C[i2][a](j1, i3)  = sum_{j2, b} A2[a,b](i2, j2 - i2 + P) Z[j2][b](j1, i3)
+//   y(i1, i2, i3)    += alpha sum_{a, o1} A1[a](i1, o1) C[i2][a](i1 + o1 - P, i3)
+// the middle one is the dense rank contraction and runs as tcgen05.mma
+// (TF32 operands, FP32 accumulation in tensor memory); modes 1 and 3 run on
+// the CUDA cores in FP32.
+//
+// One CTA owns a tile of PTS = 128 H points (j1, i3): T3 consecutive i3 and
+// T1 + 2P consecutive j1 (the mode-1 halo), T1 outputs along i1.  Each point
+// is one tensor-memory lane.  The CTA streams over j2 = 0 .. n2-1:
+//   * producer warps (one thread per point) form the slab Z[j2] in shared
+//     memory in the canonical K-major layout of the MMA (rows = points,
+//     K = b), and one of them starts a bulk copy (TMA, cp.async.bulk) of
+//     column j2 of the A2 bands, pre-packed in global memory as the B operand
+//     (rows (t, a), K = b, t = target offset) of the MMA;
+//   * one thread issues the MMAs: slab j2 contributes to the 2P+1 outputs
+//     i2 = j2 - P + t, whose FP32 accumulators form a ring of 2P+1 tensor-
+//     memory column blocks (per half of the tile); contiguous targets are
+//     one MMA with N = (targets) x R1p columns;
+//   * epilogue warps drain an accumulator as soon as its last slab is in
+//     (tcgen05.ld), zero it for its next use (tcgen05.st), apply the banded
+//     mode-1 product across the lanes through shared memory and add the
+//     result into y.
+// Z and the A2 column are double buffered, so the mode-3 product and the copy
+// of slab j2+1 overlap the MMAs of slab j2, and the epilogue of i2 overlaps
+// them too.  Every wait on an mbarrier is bounded: a wait that gives up sets
+// the context's error flag, the CTA stops issuing work, waits (bounded) for
+// its outstanding copies and MMAs, frees its tensor memory and exits; the
+// host reports IGA_ETIMEOUT.
+#include <algorithm>
+#include <cmath>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+namespace {
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor, K-major, no swizzle: core matrices of
+// 8 rows x 16 bytes; lbo = byte distance of neighbouring core matrices along
+// K, sbo = along M/N (8-row groups)
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor cores
+  return d;
+}
+
+// instruction descriptor of kind::tf32 (A, B TF32, D FP32, both K-major)
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+constexpr unsigned long long WAIT_POLLS = 1ull << 22;   // about a second with the back-off
+
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase of the given parity; false after WAIT_POLLS
+// polls or once another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort) {
+  for (unsigned long long i = 0; i < WAIT_POLLS; ++i) {
+    if (mbar_try(addr, parity)) return true;
+    if (*abort) return false;
+    if (i > 16) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(addr),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// named barrier over the epilogue warps with an OR of `pred` handed to all
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred q, p;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, %2, %3, q;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return out != 0;
+}
+
+}  // namespace
+
+}  // namespace iga
+
+namespace iga {
+
+struct TtmTcArgs {
+  const float* x;
+  float* y;
+  float alpha;
+  const float* A1;     // (R1, n1, 2P+1) bands of direction 1
+  const float* A3;     // (R2, n3, 2P+1) bands of direction 3
+  const float* V;      // packed A2 columns: (n2, 2P+1, R1p x R2p MMA image)
+  int n1, n2, n3;
+  int R1, R2, R1p, R2p;
+  int T1, T3, nt3;
+  int tcols;           // tensor-memory columns allocated (power of two >= 32)
+  int* err;            // set to IGA_ETIMEOUT when a bounded wait gives up
+};
+
+// Row strides (floats) of the A1 and A3 tiles in shared memory: threads of a
+// warp read rows of different i1 (A1) or i3 (A3) at once, so each stride is
+// an odd multiple of four floats (16 bytes) modulo 128 bytes and the rows
+// fall into distinct 16-byte bank groups.
+__host__ __device__ inline int ttm_tc_s1(int R1p) { return R1p + ((R1p / 4) % 2 == 0 ? 4 : 0); }
+__host__ __device__ inline int ttm_tc_s3(int P, int R2p) {
+  const int w = (2 * P + 1) * R2p;
+  return w + ((w / 4) % 2 == 0 ? 4 : 0);
+}
+
+// shared-memory footprint of one CTA (bytes, without the alignment slack)
+__host__ __device__ inline size_t ttm_tc_smem(int P, int H, int R1p, int R2p, int T1, int T3) {
+  const size_t B = 2 * P + 1, PTS = 128 * (size_t)H;
+  size_t z = 2 * (size_t)H * 512 * R2p;                 // Z slabs, double buffered
+  size_t v = 2 * B * 4 * (size_t)R1p * R2p;             // A2 columns, double buffered
+  size_t a1 = (size_t)T1 * B * ttm_tc_s1(R1p) * 4, a3 = (size_t)T3 * ttm_tc_s3(P, R2p) * 4;
+  size_t part = 2 * PTS * B * 4;
+  size_t bars = 8 * (7 + 2 * B) + 16;
+  return z + v + a1 + a3 + part + bars;
+}
+
+template <int P, int H>
+__global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTcArgs g) {
+  constexpr int B = 2 * P + 1;
+  constexpr int PTS = 128 * H;
+  constexpr int NPW = 4 * H;             // producer warps = epilogue warps
+  constexpr int MMA_WARP = 8 * H;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = smem_raw;
+  const int R1p = g.R1p, R2p = g.R2p, T1 = g.T1, T3 = g.T3;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  const uint32_t ZH = 512u * R2p, VT = 4u * R1p * R2p, SBO = 32u * R2p;
+  unsigned char* zbuf = sm;
+  unsigned char* vbuf = zbuf + 2 * H * ZH;
+  const int S1 = ttm_tc_s1(R1p), S3 = ttm_tc_s3(P, R2p);
+  float* a1s = reinterpret_cast<float*>(vbuf + 2 * B * VT);   // [(ii B + o) S1 + a]
+  float* a3s = a1s + T1 * B * S1;                               // [k S3 + o R2p + b]
+  float* part = a3s + T3 * S3;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(part + 2 * PTS * B);
+  const uint32_t z_full = su32(bars), v_full = z_full + 16, slab_free = z_full + 32;
+  const uint32_t acc_full = z_full + 48, acc_empty = acc_full + 8 * B,
+                 mma_done = acc_empty + 8 * B;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 7 + 2 * B);
+  volatile int* abort_ = reinterpret_cast<volatile int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t3 = blockIdx.x % g.nt3, t1 = blockIdx.x / g.nt3;
+  const int I1 = t1 * T1, I3 = t3 * T3;
+  auto fail = [&]() {
+    *abort_ = 1;
+    atomicExch(g.err, (int)IGA_ETIMEOUT);
+  };
+
+  // ---- prologue: factor tiles, barriers, tensor memory
+  for (int idx = threadIdx.x; idx < T1 * B * R1p; idx += blockDim.x) {
+    const int a = idx % R1p, r = idx / R1p, o = r % B, i1 = I1 + r / B;
+    a1s[r * S1 + a] = (a < g.R1 && i1 < n1) ? g.A1[((size_t)a * n1 + i1) * B + o] : 0.f;
+  }
+  for (int idx = threadIdx.x; idx < T3 * B * R2p; idx += blockDim.x) {
+    const int b = idx % R2p, r = idx / R2p, o = r % B, k = r / B, i3 = I3 + k;
+    a3s[k * S3 + o * R2p + b] = (b < g.R2 && i3 < n3) ? g.A3[((size_t)b * n3 + i3) * B + o] : 0.f;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(z_full + 8 * s, NPW);
+      mbar_init(v_full + 8 * s, 1);
+      mbar_init(slab_free + 8 * s, 1);
+    }
+    for (int c = 0; c < B; ++c) {
+      mbar_init(acc_full + 8 * c, 1);
+      mbar_init(acc_empty + 8 * c, NPW);
+    }
+    mbar_init(mma_done, 1);
+    *abort_ = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(g.tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  // accumulators start at zero (every MMA accumulates; the epilogue zeroes an
+  // accumulator again after draining it)
+  if (warp >= NPW && warp < 2 * NPW) {
+    const int e = warp - NPW, h = e >> 2, q = e & 3;
+    const uint32_t la = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * B * R1p);
+    for (int c = 0; c < B * R1p; c += 16) tc_st16_zero(la + c);
+    tc_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (warp < NPW) {
+    // ---- producers: mode-3 slabs and the bulk copies of the A2 columns
+    const int pt = threadIdx.x;
+    const int jj = pt / T3, k = pt - jj * T3, h = pt >> 7, m = pt & 127;
+    const int j1 = I1 - P + jj, i3 = I3 + k;
+    const bool valid = j1 >= 0 && j1 < n1 && i3 < n3;
+    unsigned char* zrow = zbuf + h * ZH + (m >> 3) * SBO + (m & 7) * 16;
+    const float4* a3r = reinterpret_cast<const float4*>(a3s + k * S3);
+    const int R2q = R2p >> 2;
+    int issued[2] = {-1, -1};
+    // x of the next slab is loaded one iteration ahead (its latency hides
+    // behind the wait and the arithmetic of the current slab)
+    float xn[B];
+    auto load_x = [&](int j2, float* xv) {
+#pragma unroll
+      for (int o = 0; o < B; ++o) {
+        const int j3 = i3 + o - P;
+        xv[o] = (valid && j3 >= 0 && j3 < n3) ? __ldg(g.x + ((size_t)j1 * n2 + j2) * n3 + j3)
+                                              : 0.f;
+      }
+    };
+    load_x(0, xn);
+    for (int j2 = 0; j2 < n2; ++j2) {
+      const int s = j2 & 1;
+      const uint32_t use = (uint32_t)(j2 >> 1);
+      float xw[B];
+#pragma unroll
+      for (int o = 0; o < B; ++o) xw[o] = xn[o];
+      if (j2 + 1 < n2) load_x(j2 + 1, xn);
+      if (j2 >= 2) {
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(slab_free + 8 * s, (use - 1) & 1, abort_);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) fail();
+          break;
+        }
+      }
+      if (pt == 0) {
+        mbar_expect_tx(v_full + 8 * s, (uint32_t)B * VT);
+        bulk_g2s(su32(vbuf + s * B * VT), g.V + (size_t)j2 * B * (VT / 4), (uint32_t)B * VT,
+                 v_full + 8 * s);
+        issued[s] = j2;
+      }
+      unsigned char* zr = zrow + s * H * ZH;
+      for (int b4 = 0; b4 < R2q; ++b4) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int o = 0; o < B; ++o) {
+          const float4 a = a3r[o * R2q + b4];
+          acc.x = fmaf(a.x, xw[o], acc.x);
+          acc.y = fmaf(a.y, xw[o], acc.y);
+          acc.z = fmaf(a.z, xw[o], acc.z);
+          acc.w = fmaf(a.w, xw[o], acc.w);
+        }
+        *reinterpret_cast<float4*>(zr + b4 * 128) = acc;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(z_full + 8 * s);
+    }
+    // copies still in flight must land before the CTA exits
+    if (pt == 0) {
+      for (int s = 0; s < 2; ++s)
+        if (issued[s] >= 0) {
+          volatile int never = 0;
+          if (!mbar_wait(v_full + 8 * s, ((uint32_t)issued[s] >> 1) & 1, &never)) fail();
+        }
+    }
+  } else if (warp < 2 * NPW) {
+    // ---- epilogue: drain accumulators, mode-1 product, y update
+    const int e = warp - NPW, h = e >> 2, q = e & 3;
+    const int pt = h * 128 + q * 32 + lane;
+    const int jj = pt / T3, k = pt - jj * T3;
+    const uint32_t la = tbase + ((uint32_t)(q * 32) << 16);
+    // this thread's output column (i1, ., i3), if any; y of the next i2 is
+    // loaded one iteration ahead
+    const int oi1 = I1 + jj - P, oi3 = I3 + k;
+    const bool outp = jj >= P && jj < P + T1 && oi1 < n1 && oi3 < n3;
+    float* ycol = outp ? g.y + (size_t)oi1 * n2 * n3 + oi3 : nullptr;
+    float ynext = outp ? ycol[0] : 0.f;
+    for (int i2 = 0; i2 < n2; ++i2) {
+      const int acc = i2 % B;
+      const float ycur = ynext;
+      if (outp && i2 + 1 < n2) ynext = ycol[(size_t)(i2 + 1) * n3];
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(acc_full + 8 * acc, (uint32_t)(i2 / B) & 1, abort_);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      float c[B];
+#pragma unroll
+      for (int o = 0; o < B; ++o) c[o] = 0.f;
+      if (ok) {
+        tc_fence_after();
+        const uint32_t col0 = (uint32_t)((h * B + acc) * R1p);
+        for (int ch = 0; ch < R1p; ch += 16) {
+          float d[16];
+          tc_ld16(la + col0 + ch, d);
+#pragma unroll
+          for (int o = 0; o < B; ++o) {
+            const int ii = jj - o;
+            if (ii >= 0 && ii < T1) {
+              const float4* ar = reinterpret_cast<const float4*>(a1s + (ii * B + o) * S1 + ch);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float4 av = ar[u];
+                c[o] = fmaf(av.x, d[4 * u], c[o]);
+                c[o] = fmaf(av.y, d[4 * u + 1], c[o]);
+                c[o] = fmaf(av.z, d[4 * u + 2], c[o]);
+                c[o] = fmaf(av.w, d[4 * u + 3], c[o]);
+              }
+            }
+          }
+          tc_st16_zero(la + col0 + ch);
+        }
+        tc_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty + 8 * acc);
+      }
+      float* pb = part + (i2 & 1) * PTS * B;
+#pragma unroll
+      for (int o = 0; o < B; ++o) pb[pt * B + o] = c[o];
+      const bool bad = bar_or(1, NPW * 32, !ok || *abort_ != 0);
+      if (bad) {
+        if (!ok && lane == 0) fail();
+        break;
+      }
+      if (outp) {
+        const int ii = jj - P;
+        float v = 0.f;
+#pragma unroll
+        for (int o = 0; o < B; ++o) v += pb[((ii + o) * T3 + k) * B + o];
+        ycol[(size_t)i2 * n3] = fmaf(g.alpha, v, ycur);
+      }
+    }
+  } else if (lane == 0) {
+    // ---- MMA issuer
+    const int maxrun = 256 / R1p;
+    auto issue = [&](int j2, int s, int ta, int tb) {
+      int t = ta;
+      while (t <= tb) {
+        const int c0 = (j2 - P + t) % B;
+        const int len = min(min(tb - t + 1, B - c0), maxrun);
+        const uint32_t idesc = idesc_tf32(128, len * R1p);
+        for (int kb = 0; kb < (R2p >> 3); ++kb) {
+          const uint64_t bd = umma_desc(su32(vbuf + s * B * VT + t * VT) + kb * 256, 128, SBO);
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            const uint64_t ad = umma_desc(su32(zbuf + (s * H + h) * ZH) + kb * 256, 128, SBO);
+            tc_mma_tf32(tbase + (uint32_t)((h * B + c0) * R1p), ad, bd, idesc, 1u);
+          }
+        }
+        t += len;
+      }
+    };
+    for (int j2 = 0; j2 < n2; ++j2) {
+      const int s = j2 & 1;
+      const uint32_t use = (uint32_t)(j2 >> 1);
+      if (!mbar_wait(z_full + 8 * s, use & 1, abort_) || !mbar_wait(v_full + 8 * s, use & 1, abort_)) {
+        fail();
+        break;
+      }
+      tc_fence_after();
+      const int tlo = max(0, P - j2), thi = min(B - 1, n2 - 1 - j2 + P);
+      const bool fresh = (j2 + P < n2) && (j2 + P >= B);   // target i2 = j2 + P reuses a ring slot
+      issue(j2, s, tlo, fresh ? B - 2 : thi);
+      if (fresh) {
+        const int i2n = j2 + P;
+        if (!mbar_wait(acc_empty + 8 * (i2n % B), (uint32_t)(i2n / B - 1) & 1, abort_)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        issue(j2, s, B - 1, B - 1);
+      }
+      tc_commit(slab_free + 8 * s);
+      if (j2 - P >= 0) tc_commit(acc_full + 8 * ((j2 - P) % B));
+      if (j2 == n2 - 1)
+        for (int i2 = max(0, j2 - P + 1); i2 < n2; ++i2) tc_commit(acc_full + 8 * (i2 % B));
+    }
+    // every MMA issued must finish before the tensor memory is released
+    tc_commit(mma_done);
+    volatile int never = 0;
+    if (!mbar_wait(mma_done, 0, &never)) fail();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(g.tcols)
+                 : "memory");
+  }
+}
+
+}  // namespace iga
+
+namespace iga {
+
+// Column j2 of the A2 bands of one block as the B operand of the MMAs of slab
+// j2: V[j2][t] is an R1p x R2p K-major image (8-row x 4-column core
+// matrices) of A2[a][b](i2, 2P - t), i2 = j2 - P + t, zero outside the ranks
+// and the matrix.
+__global__ void ttm_tc_pack_kernel(const float* __restrict__ A2, int R1, int R2, int n2, int P,
+                                   int R1p, int R2p, float* __restrict__ V) {
+  const int B = 2 * P + 1;
+  const size_t img = (size_t)R1p * R2p;
+  const size_t total = (size_t)n2 * B * img;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t jt = idx / img;
+    const int e = (int)(idx - jt * img);
+    const int t = (int)(jt % B), j2 = (int)(jt / B);
+    // e = (a/8) 8 R2p + (b/4) 32 + (a%8) 4 + b%4
+    const int g8 = e / (8 * R2p), r8 = e - g8 * 8 * R2p;
+    const int b4 = r8 / 32, r32 = r8 - b4 * 32;
+    const int a = g8 * 8 + r32 / 4, b = b4 * 4 + (r32 & 3);
+    const int i2 = j2 - P + t;
+    float v = 0.f;
+    if (a < R1 && b < R2 && i2 >= 0 && i2 < n2)
+      v = A2[(((size_t)a * R2 + b) * n2 + i2) * B + (2 * P - t)];
+    V[idx] = v;
+  }
+}
+
+struct TtmTcPlan {
+  bool ok = false;
+  int H = 1, T1 = 0, T3 = 0, R1p = 0, R2p = 0, tcols = 0;
+  size_t smem = 0;
+};
+
+static constexpr size_t TTM_TC_SMEM_MAX = 227 * 1024;
+
+// Tile of the fused tensor-core apply: two halves (256 lanes) when tensor
+// memory and shared memory allow, T3 in {16, 8, 4} consecutive i3 with
+// T1 = 128 H / T3 - 2P outputs along i1; the plan with the fewest waves of
+// CTAs over the SMs, weighted by the per-CTA work (proportional to H), wins.
+static TtmTcPlan ttm_tc_plan(int n1, int n3, int R1, int R2, int P, int nsm) {
+  TtmTcPlan best;
+  const int B = 2 * P + 1;
+  const int R1p = (R1 + 15) / 16 * 16, R2p = (R2 + 7) / 8 * 8;
+  if (R1p > 256 || R2p > 256 || P < 1 || P > 3) return best;
+  double bestc = 1e300;
+  for (int H = 2; H >= 1; --H) {
+    if (H * B * R1p > 512) continue;
+    for (int T3 : {16, 8, 4}) {
+      const int T1 = 128 * H / T3 - 2 * P;
+      if (T1 < 1) continue;
+      const size_t smem = ttm_tc_smem(P, H, R1p, R2p, T1, T3) + 1024;
+      if (smem > TTM_TC_SMEM_MAX) continue;
+      const long nt = (long)((n1 + T1 - 1) / T1) * ((n3 + T3 - 1) / T3);
+      const double c = std::ceil((double)nt / nsm) * H;
+      if (c < bestc * (1 - 1e-9)) {
+        bestc = c;
+        best.ok = true;
+        best.H = H; best.T1 = T1; best.T3 = T3; best.R1p = R1p; best.R2p = R2p;
+        best.smem = smem;
+        int tc = 32;
+        while (tc < H * B * R1p) tc *= 2;
+        best.tcols = tc;
+      }
+    }
+  }
+  return best;
+}
+
+bool ttm_tc_supported(int n1, int n3, int R1, int R2, int P, int nsm) {
+  return ttm_tc_plan(n1, n3, R1, R2, P, nsm).ok;
+}
+
+template <int P, int H>
+static void ttm_tc_launch(iga_ctx* ctx, const TtmTcArgs& a, const TtmTcPlan& pl, unsigned grid) {
+  func_attr(ttm_tc_kernel<P, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  IGA_LAUNCH(ctx, (ttm_tc_kernel<P, H>), grid, (8 * H + 1) * 32, pl.smem, a);
+}
+
+// y += alpha (sum_{a,b} A1[a] (x) A2[a,b] (x) A3[b]) x for one TT-matrix block
+// in FP32 storage with TF32 tensor-core rank contraction.  Returns false (and
+// launches nothing) when the block's shape has no plan.
+bool ttm_tc_block(iga_ctx* ctx, const float* A1, const float* A2, const float* A3, int R1, int R2,
+                  const int* n, int P, float alpha, const float* x, float* y) {
+  const TtmTcPlan pl = ttm_tc_plan(n[0], n[2], R1, R2, P, ctx->nsm);
+  if (!pl.ok) return false;
+  const int B = 2 * P + 1;
+  const size_t vcount = (size_t)n[1] * B * pl.R1p * pl.R2p;
+  float* V = scratch<float>(ctx, SLOT_TTM_W, vcount);
+  IGA_LAUNCH(ctx, ttm_tc_pack_kernel, (unsigned)std::min<size_t>((vcount + 255) / 256, 4096), 256,
+             0, A2, R1, R2, n[1], P, pl.R1p, pl.R2p, V);
+  TtmTcArgs a{};
+  a.x = x; a.y = y; a.alpha = alpha;
+  a.A1 = A1; a.A3 = A3; a.V = V;
+  a.n1 = n[0]; a.n2 = n[1]; a.n3 = n[2];
+  a.R1 = R1; a.R2 = R2; a.R1p = pl.R1p; a.R2p = pl.R2p;
+  a.T1 = pl.T1; a.T3 = pl.T3; a.nt3 = (n[2] + pl.T3 - 1) / pl.T3;
+  a.tcols = pl.tcols;
+  a.err = ctx->dflag + 1;
+  const unsigned grid = (unsigned)(((n[0] + pl.T1 - 1) / pl.T1) * a.nt3);
+  {
+    // algorithmic: mode 3 and mode 1 banded products and the rank
+    // contraction; x read once, y read and written once
+    const double N = (double)n[0] * n[1] * n[2];
+    prof_count(ctx, N * 4.0 * 3.0, 2.0 * B * N * (R2 + (double)R1 * R2 + R1));
+  }
+  switch (P * 2 + (pl.H - 1)) {
+    case 2: ttm_tc_launch<1, 1>(ctx, a, pl, grid); break;
+    case 3: ttm_tc_launch<1, 2>(ctx, a, pl, grid); break;
+    case 4: ttm_tc_launch<2, 1>(ctx, a, pl, grid); break;
+    case 5: ttm_tc_launch<2, 2>(ctx, a, pl, grid); break;
+    case 6: ttm_tc_launch<3, 1>(ctx, a, pl, grid); break;
+    case 7: ttm_tc_launch<3, 2>(ctx, a, pl, grid); break;
+    default: return false;
+  }
+  return true;
+}
+
+}  // namespace iga
