@@ -48,7 +48,12 @@ typedef enum {
   IGA_ETIMEOUT = 6     /* a bounded device wait gave up */
 } iga_status;
 
-typedef enum { IGA_FP64 = 0, IGA_FP32 = 1, IGA_TF32 = 2 } iga_prec;
+/* Arithmetic of an operator apply or a solve.  IGA_FP64 and IGA_FP32: CUDA
+ * cores in that precision on double / float vectors.  IGA_TF32 and IGA_BF16:
+ * float vectors; the dense rank contraction of TT-matrix blocks runs on the
+ * tensor cores with TF32 or BF16 operands and FP32 accumulation (rank-1
+ * blocks, which have no dense contraction, run in FP32). */
+typedef enum { IGA_FP64 = 0, IGA_FP32 = 1, IGA_TF32 = 2, IGA_BF16 = 3 } iga_prec;
 
 enum { IGA_GEO_NURBS = 0, IGA_GEO_NURBS_TWIST = 1 };
 enum { IGA_TARGET_ZERO = 0, IGA_TARGET_SINPROD = 1, IGA_TARGET_GAUSS = 2 };
@@ -126,8 +131,11 @@ iga_status iga_measure_fma(iga_ctx* ctx, iga_prec prec, double* tflops);
  * out: device, 8 consecutive tensors of shape (Q1, Q2, Q3), Q_d = E_d * nquad:
  *   [0] omega g, [1] q11 g, [2] q12 g, [3] q13 g, [4] q22 g, [5] q23 g,
  *   [6] q33 g, [7] yhat(G) omega g.
- * Fails with IGA_EINVAL on invalid knots or a non-positive Jacobian
- * determinant (detected on the device, reported after the call). */
+ * Fails with IGA_EINVAL on invalid knots, a Jacobian determinant that is
+ * zero or not finite at a Gauss point, or one that changes sign between
+ * Gauss points (a map folding over itself); a map of constant negative
+ * orientation is accepted (omega = |det J|).  Detected on the device and
+ * reported after the call (the call synchronises). */
 iga_status iga_sample_weights(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
                               const iga_target* target, double* out);
 
@@ -147,6 +155,14 @@ iga_status iga_tt_core(iga_ctx* ctx, const iga_tt* tt, int d, double* core);
 /* Expand to a full device tensor (n1, n2, n3), FP64. */
 iga_status iga_tt_full(iga_ctx* ctx, const iga_tt* tt, double* out);
 void iga_tt_destroy(iga_tt* tt);
+/* Save a TT to a host file / load it back (no counterpart in the paper;
+ * it stores the TT of eq. tt).  Format: the 8 bytes "IGATT" 1 0 0, int32
+ * n1 n2 n3 r1 r2, then the three cores (r_{d-1}, n_d, r_d) in C order as
+ * float64, little-endian.  iga_tt_load checks the magic, the sizes and the
+ * file length (IGA_EINVAL on a mismatch or an unreadable file) and returns a
+ * library-owned TT.  Both synchronise the context stream. */
+iga_status iga_tt_save(iga_ctx* ctx, const iga_tt* tt, const char* path);
+iga_status iga_tt_load(iga_ctx* ctx, const char* path, iga_tt** out);
 
 /* ---- (a4) batched univariate assembly ------------------------------- */
 
@@ -192,6 +208,19 @@ iga_status iga_ops_from_weights(iga_ctx* ctx, const iga_space* space,
 iga_status iga_load_from_density(iga_ctx* ctx, const iga_space* space, const iga_tt* density,
                                  iga_tt** load);
 
+/* A Kronecker / TT-matrix operator from its banded univariate factors
+ * (Sec. 5, eqs. M_kron / K_kron):
+ *   A = sum_k sum_{a,b} A1_k[a] (x) A2_k[a,b] (x) A3_k[b],
+ * acting on C-ordered tensors of size n[0] x n[1] x n[2] with half-bandwidth
+ * p[d] in direction d (the apply needs p[0] = p[1] = p[2] in 1..4).  Block k
+ * has ranks (R[2k], R[2k+1]); bands[3k + d] is a device FP64 array of block
+ * k, direction d: d=0 (R1, n1, 2p+1), d=1 (R1, R2, n2, 2p+1), d=2
+ * (R2, n3, 2p+1), band[i][o] = A(i, i + o - p); entries outside the matrix
+ * are ignored.  The bands are copied (an FP32 copy is made for the FP32 and
+ * tensor-core applies); *out is library-owned.  Synchronises. */
+iga_status iga_op_from_bands(iga_ctx* ctx, const int n[3], const int p[3], int nblocks,
+                             const int* R, const double* const* bands, iga_op** out);
+
 /* Operator structure: interior sizes n[3], degrees p[3], number of blocks
  * (one per TT weight term group), summed TT-matrix ranks R[2] and device
  * bytes of its factors. */
@@ -206,15 +235,21 @@ void iga_op_destroy(iga_op* op);
 
 /* ---- (a5) Kronecker-sum apply --------------------------------------- */
 
-/* y = alpha * A x + beta * y with A = sum_blocks sum_{r1,r2}
+/* y = alpha * op(A) x + beta * y with A = sum_blocks sum_{r1,r2}
  * A1[r1] (x) A2[r1,r2] (x) A3[r2] (Sec. 5, eqs. M_kron / K_kron; kron
- * ordering kron(A1, kron(A2, A3)) on C-ordered x).  x, y: device, length
- * n1 n2 n3, double (IGA_FP64) or float (IGA_FP32, IGA_TF32); x and y must
- * not overlap.  TT-matrix blocks (ranks above one) contract the rank index
- * as one batched GEMM per i2 (M = R1, K = (2p+1) R2, N = n1 n3); IGA_TF32
- * runs that GEMM on the tensor cores in TF32 with FP32 accumulation. */
-iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
-                          double beta, void* y, iga_prec prec);
+ * ordering kron(A1, kron(A2, A3)) on C-ordered x), op(A) = A (transpose = 0)
+ * or A^T = sum A1^T (x) A2^T (x) A3^T (transpose != 0, the bands transposed
+ * into a temporary on the context stream).  x, y: device, length n1 n2 n3,
+ * double (IGA_FP64) or float (IGA_FP32, IGA_TF32, IGA_BF16); x and y must
+ * not overlap (IGA_EINVAL).  Rank-1 blocks run as one fused launch of banded
+ * mode products.  TT-matrix blocks (ranks above one): IGA_TF32 / IGA_BF16
+ * run the rank contraction as tcgen05 tensor-core MMAs (TF32 or BF16
+ * operands, FP32 accumulation) in one fused launch per block; IGA_FP64 /
+ * IGA_FP32 use staged mode products and a batched GEMM per i2.  With
+ * IGA_TF32 / IGA_BF16 the call synchronises the stream and returns
+ * IGA_ETIMEOUT if a bounded wait of the tensor-core pipeline gave up. */
+iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, int transpose, double alpha,
+                          const void* x, double beta, void* y, iga_prec prec);
 
 /* out = KKT z for the stationary KKT matrix (Sec. 4 eq. KKTSystem with one
  * time step and tau = 1):  [[M, 0, K^T], [0, beta M, -M], [K, -M, 0]].
@@ -365,6 +400,17 @@ void iga_solve_opts_default(iga_solve_opts* opts);
 iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K, const iga_tt* load,
                               double beta, const iga_solve_opts* opts, double* y, double* u,
                               double* lam, iga_solve_info* info);
+
+/* The same solve with the solution returned as TT tensors (Sec. 5: the
+ * block-AMEn solution is the block TT of eq. btt; here one TT per field).
+ * The solve runs into full device vectors owned by the call, each field is
+ * compressed by TT-SVD to a relative Frobenius error of opts->tol / 10, and
+ * *y, *u, *lam receive library-owned TTs (NULL for a field that is exactly
+ * zero); iga_tt_full expands them.  Returns what the solve returns
+ * (IGA_ENOCONV with the best iterate compressed). */
+iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                                 const iga_tt* load, double beta, const iga_solve_opts* opts,
+                                 iga_tt** y, iga_tt** u, iga_tt** lam, iga_solve_info* info);
 
 #ifdef __cplusplus
 }

@@ -192,7 +192,7 @@ def kron_apply_modes(terms, x):
     return out.ravel()
 
 
-def weight_tts(geo, disc, tol, target=None):
+def weight_tts(geo, disc, tol, target=None, samples=None):
     """TT cores of omega*g, q_kl*g (k <= l) and, with a target, yhat*omega*g.
 
     The weights are sampled on the tensor Gauss grid of the discretisation
@@ -200,9 +200,11 @@ def weight_tts(geo, disc, tol, target=None):
     relative to the Frobenius norm of all of Q, so entries that vanish
     analytically (off-diagonal q_kl of the annulus) drop to rank 0.
     Returns {'omega': cores, (k, l): cores or None, 'load': cores or None}.
+    `samples` may pass the output of assemble.sample_weights for this grid
+    (to compress one sample at several tolerances).
     """
     from .assemble import sample_weights, evaluate_target
-    G, omega, Q, _ = sample_weights(geo, disc)
+    G, omega, Q, _ = samples if samples is not None else sample_weights(geo, disc)
     _, gs = disc.gauss_grid()
     g = np.einsum("a,b,c->abc", gs[0], gs[1], gs[2])
     out = {"omega": tt_svd(omega * g, tol)}

@@ -62,11 +62,12 @@ def _cg(apply, b, precond, tol):
     return x
 
 
-def interior_operators(space, geometry, target, tol):
+def interior_operators(space, geometry, target, tol, samples=None):
     """Interior Kronecker terms of M and K, the interior load vector and the
-    diagonal stiffness terms, from the oracle's low-rank route."""
+    diagonal stiffness terms, from the oracle's low-rank route (`samples`: an
+    earlier assemble.sample_weights output of this grid, or None)."""
     disc = Discretisation(space.degree, space.knots, space.nquad)
-    tts = weight_tts(geometry, disc, tol, target)
+    tts = weight_tts(geometry, disc, tol, target, samples=samples)
     Mt = restrict_interior(lowrank_operator(disc, tts["omega"], "M"))
     kl = {}
     for k in range(3):
@@ -111,10 +112,12 @@ def solve_kkt(Mt, Kt, diag, b, beta, tol=1e-12, max_iter=None):
     return reduced_solve(M_apply, K_apply, Minv, beta, b, tol=tol, precond=P, **kw)
 
 
-def timed_solve(work, tol=1e-12):
-    """Oracle pipeline on a workload with wall times of its two parts."""
+def timed_solve(work, tol=1e-12, tt_tol=None, samples=None):
+    """Oracle pipeline on a workload with wall times of its two parts (TT
+    truncation at tt_tol, default the workload's)."""
     t0 = time.perf_counter()
-    Mt, Kt, diag, b = interior_operators(work.space, work.geometry, work.target, work.tol)
+    Mt, Kt, diag, b = interior_operators(work.space, work.geometry, work.target,
+                                         work.tol if tt_tol is None else tt_tol, samples)
     t1 = time.perf_counter()
     y, u, lam, it = solve_kkt(Mt, Kt, diag, b, work.beta, tol)
     t2 = time.perf_counter()

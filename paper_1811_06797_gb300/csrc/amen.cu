@@ -2181,3 +2181,44 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     return IGA_ECUDA;
   }
 }
+
+// The same solve with the solution returned as TT tensors (Sec. 5: the
+// block-AMEn solution is a block TT, eq. btt).  The solve runs into full
+// device vectors owned by the call; each field is then compressed by TT-SVD
+// to a relative Frobenius error of tol / 10, and the full vectors are freed.
+extern "C" iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                                            const iga_tt* load, double beta,
+                                            const iga_solve_opts* opts, iga_tt** y, iga_tt** u,
+                                            iga_tt** lam, iga_solve_info* info) {
+  if (!ctx || !y || !u || !lam || !M) return IGA_EINVAL;
+  *y = *u = *lam = nullptr;
+  try {
+    AllocScope scope(ctx->stream);
+    const size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
+    DevBuf<double> Z(3 * N);
+    iga_status st = iga_kkt_solve_amen(ctx, M, K, load, beta, opts, Z.p, Z.p + N, Z.p + 2 * N,
+                                       info);
+    if (st != IGA_OK && st != IGA_ENOCONV) return st;
+    iga_solve_opts o;
+    if (opts) o = *opts; else iga_solve_opts_default(&o);
+    iga_tt* out[3] = {nullptr, nullptr, nullptr};
+    try {
+      for (int f = 0; f < 3; ++f)
+        tt_svd3(ctx, Z.p + f * N, M->n[0], M->n[1], M->n[2], 0.1 * o.tol, 0.0, 0, &out[f]);
+      IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+      for (int f = 0; f < 3; ++f) delete out[f];
+      throw;
+    }
+    *y = out[0];
+    *u = out[1];
+    *lam = out[2];
+    return st;
+  } catch (const Error& e) {
+    set_error(ctx, e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    set_error(ctx, e.what());
+    return IGA_ECUDA;
+  }
+}

@@ -6,8 +6,10 @@
 // massMatrix1D, stiffnessFinal), so that M = sum (x)_d M_d and
 // K = sum_{k,l} sum (x)_d K_kl^(d) with the core slices of eq. TTranks.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 
@@ -145,12 +147,12 @@ static void add_block(iga_ctx* ctx, const SpaceTables& st, const iga_tt* tt, con
   B.blocks.push_back(blk);
 }
 
-static iga_op* finish_op(iga_ctx* ctx, const SpaceTables& st, OpBuilder& B) {
+static iga_op* finish_op(iga_ctx* ctx, const int* n_int, const int* p_deg, OpBuilder& B) {
   auto* op = new iga_op();
   try {
     for (int d = 0; d < 3; ++d) {
-      op->n[d] = st.dir[d].n - 2;
-      op->p[d] = st.dir[d].p;
+      op->n[d] = n_int[d];
+      op->p[d] = p_deg[d];
       size_t len = (size_t)op->n[d] * (2 * op->p[d] + 1);
       op->nbands[d] = B.count[d];
       op->band64[d].alloc(std::max<size_t>(1, B.count[d] * len));
@@ -326,16 +328,63 @@ void ops_from_weights_impl(iga_ctx* ctx, const SpaceTables& st, const iga_tt* co
       }
       add_block(ctx, st, t, dk, bk);
     }
-  iga_op* m = finish_op(ctx, st, bm);
+  int ni[3], pd[3];
+  for (int d = 0; d < 3; ++d) {
+    ni[d] = st.dir[d].n - 2;
+    pd[d] = st.dir[d].p;
+  }
+  iga_op* m = finish_op(ctx, ni, pd, bm);
   iga_op* kk = nullptr;
   try {
-    kk = finish_op(ctx, st, bk);
+    kk = finish_op(ctx, ni, pd, bk);
   } catch (...) {
     delete m;
     throw;
   }
   *M = m;
   *K = kk;
+}
+
+// copy of a band array with the entries outside the matrix set to zero
+__global__ void band_clean_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                  size_t total, int n, int P) {
+  const int B = 2 * P + 1;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(idx % B);
+    const int i = (int)((idx / B) % n);
+    const int j = i + o - P;
+    out[idx] = (j >= 0 && j < n) ? in[idx] : 0.0;
+  }
+}
+
+iga_op* op_from_bands_impl(iga_ctx* ctx, const int n[3], const int p[3], int nblocks,
+                           const int* R, const double* const* bands) {
+  IGA_REQUIRE(nblocks >= 1 && R && bands, "op_from_bands: no blocks");
+  for (int d = 0; d < 3; ++d)
+    IGA_REQUIRE(n[d] >= 1 && p[d] >= 0 && p[d] <= 8, "op_from_bands: invalid size or degree");
+  OpBuilder b;
+  for (int k = 0; k < nblocks; ++k) {
+    const int R1 = R[2 * k], R2 = R[2 * k + 1];
+    IGA_REQUIRE(R1 >= 1 && R2 >= 1, "op_from_bands: ranks must be positive");
+    OpBlock blk;
+    blk.R1 = R1;
+    blk.R2 = R2;
+    const size_t cnt[3] = {(size_t)R1, (size_t)R1 * R2, (size_t)R2};
+    for (int d = 0; d < 3; ++d) {
+      const double* src = bands[3 * k + d];
+      IGA_REQUIRE(src != nullptr, "op_from_bands: null band array");
+      const size_t total = cnt[d] * n[d] * (2 * p[d] + 1);
+      DevBuf<double> band(total);
+      IGA_LAUNCH(ctx, band_clean_kernel, (unsigned)std::min<size_t>((total + 255) / 256, 4096),
+                 256, 0, src, band.p, total, n[d], p[d]);
+      blk.off[d] = b.count[d];
+      b.count[d] += cnt[d];
+      b.parts[d].push_back(std::move(band));
+    }
+    b.blocks.push_back(blk);
+  }
+  return finish_op(ctx, n, p, b);
 }
 
 }  // namespace iga
@@ -548,6 +597,76 @@ iga_status iga_tt_full(iga_ctx* ctx, const iga_tt* tt, double* out) {
 
 void iga_tt_destroy(iga_tt* tt) { delete tt; }
 
+// File format of a TT tensor: the 8 bytes "IGATT" 0x01 0x00 0x00, the int32
+// sizes n1 n2 n3 and ranks r1 r2, then the cores (r_{d-1}, n_d, r_d) in C
+// order as float64, all little-endian (the byte order of every host this
+// library builds for).
+static const unsigned char TT_MAGIC[8] = {'I', 'G', 'A', 'T', 'T', 1, 0, 0};
+
+iga_status iga_tt_save(iga_ctx* ctx, const iga_tt* tt, const char* path) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(tt && path, "tt_save: null argument");
+    std::vector<double> host[3];
+    for (int d = 0; d < 3; ++d) {
+      host[d].resize(tt->core[d].n);
+      if (!host[d].empty())
+        IGA_CUDA(cudaMemcpyAsync(host[d].data(), tt->core[d].p, host[d].size() * 8,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    FILE* f = std::fopen(path, "wb");
+    IGA_REQUIRE(f != nullptr, std::string("tt_save: cannot open ") + path);
+    int32_t hdr[5] = {tt->n[0], tt->n[1], tt->n[2], tt->r[0], tt->r[1]};
+    bool ok = std::fwrite(TT_MAGIC, 1, 8, f) == 8 && std::fwrite(hdr, 4, 5, f) == 5;
+    for (int d = 0; d < 3 && ok; ++d)
+      ok = std::fwrite(host[d].data(), 8, host[d].size(), f) == host[d].size();
+    ok = (std::fclose(f) == 0) && ok;
+    IGA_REQUIRE(ok, std::string("tt_save: write failed for ") + path);
+  })
+}
+
+iga_status iga_tt_load(iga_ctx* ctx, const char* path, iga_tt** out) {
+  if (!ctx || !out) return IGA_EINVAL;
+  *out = nullptr;
+  IGA_TRY(ctx, {
+    IGA_REQUIRE(path != nullptr, "tt_load: null path");
+    FILE* f = std::fopen(path, "rb");
+    IGA_REQUIRE(f != nullptr, std::string("tt_load: cannot open ") + path);
+    unsigned char magic[8];
+    int32_t hdr[5];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, TT_MAGIC, 8) == 0 &&
+              std::fread(hdr, 4, 5, f) == 5;
+    for (int k = 0; k < 5 && ok; ++k) ok = hdr[k] >= 1 && hdr[k] <= (1 << 24);
+    std::vector<double> host[3];
+    if (ok) {
+      const int rl[4] = {1, hdr[3], hdr[4], 1};
+      for (int d = 0; d < 3 && ok; ++d) {
+        const size_t cnt = (size_t)rl[d] * hdr[d] * rl[d + 1];
+        ok = cnt <= ((size_t)1 << 34);
+        if (ok) {
+          host[d].resize(cnt);
+          ok = std::fread(host[d].data(), 8, cnt, f) == cnt;
+        }
+      }
+      ok = ok && std::fgetc(f) == EOF;     // nothing after the cores
+    }
+    std::fclose(f);
+    IGA_REQUIRE(ok, std::string("tt_load: not a TT file of this library: ") + path);
+    std::unique_ptr<iga_tt> tt(new iga_tt());
+    for (int d = 0; d < 3; ++d) tt->n[d] = hdr[d];
+    tt->r[0] = hdr[3];
+    tt->r[1] = hdr[4];
+    for (int d = 0; d < 3; ++d) {
+      tt->core[d].alloc(host[d].size());
+      IGA_CUDA(cudaMemcpyAsync(tt->core[d].p, host[d].data(), host[d].size() * 8,
+                               cudaMemcpyHostToDevice, ctx->stream));
+    }
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = tt.release();
+  })
+}
+
 iga_status iga_assemble_bands(iga_ctx* ctx, const iga_space* space, int d, const double* w, int T,
                               int deriv_row, int deriv_col, int interior, double* band) {
   if (!ctx) return IGA_EINVAL;
@@ -712,13 +831,21 @@ iga_status iga_op_bands(iga_ctx* ctx, const iga_op* op, int k, int d, double* ho
 
 void iga_op_destroy(iga_op* op) { delete op; }
 
-iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, double alpha, const void* x,
-                          double beta, void* y, iga_prec prec) {
+iga_status iga_op_from_bands(iga_ctx* ctx, const int n[3], const int p[3], int nblocks,
+                             const int* R, const double* const* bands, iga_op** out) {
+  if (!ctx || !out || !n || !p) return IGA_EINVAL;
+  *out = nullptr;
+  IGA_TRY(ctx, *out = op_from_bands_impl(ctx, n, p, nblocks, R, bands))
+}
+
+iga_status iga_kron_apply(iga_ctx* ctx, const iga_op* A, int transpose, double alpha,
+                          const void* x, double beta, void* y, iga_prec prec) {
   if (!ctx) return IGA_EINVAL;
   IGA_TRY(ctx, {
-    if (prec == IGA_TF32) tc_flag_reset(ctx);
-    kron_apply_impl(ctx, A, alpha, x, beta, y, prec);
-    if (prec == IGA_TF32) tc_flag_check(ctx, "kron_apply");
+    if (prec == IGA_TF32 || prec == IGA_BF16) tc_flag_reset(ctx);
+    if (transpose) kron_apply_transposed(ctx, A, alpha, x, beta, y, prec);
+    else kron_apply_impl(ctx, A, alpha, x, beta, y, prec);
+    if (prec == IGA_TF32 || prec == IGA_BF16) tc_flag_check(ctx, "kron_apply");
   })
 }
 
@@ -726,9 +853,9 @@ iga_status iga_kkt_apply(iga_ctx* ctx, const iga_op* M, const iga_op* K, double 
                          const void* z, void* out, iga_prec prec) {
   if (!ctx) return IGA_EINVAL;
   IGA_TRY(ctx, {
-    if (prec == IGA_TF32) tc_flag_reset(ctx);
+    if (prec == IGA_TF32 || prec == IGA_BF16) tc_flag_reset(ctx);
     kkt_apply_impl(ctx, M, K, beta, z, out, prec);
-    if (prec == IGA_TF32) tc_flag_check(ctx, "kkt_apply");
+    if (prec == IGA_TF32 || prec == IGA_BF16) tc_flag_check(ctx, "kkt_apply");
   })
 }
 

@@ -337,7 +337,14 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
   double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-  if (valid && (!(det != 0.0) || !isfinite(det))) atomicOr(flag, 1);
+  {
+    // orientation record: 1 = some det < 0, 2 = some det > 0, 4 = det zero or
+    // not finite; one OR per warp, an atomic only when it adds a bit
+    const int code = !valid ? 0 : ((!(det != 0.0) || !isfinite(det)) ? 4 : (det > 0.0 ? 2 : 1));
+    const int wcode = __reduce_or_sync(0xffffffffu, code);
+    if ((threadIdx.x & 31) == 0 && wcode != 0 && (wcode & ~*(volatile int*)flag) != 0)
+      atomicOr(flag, wcode);
+  }
   double adet = fabs(det);
   // metric m = J^T J; Q = adj(m) / det(m) * |det J| = adj(m) / |det J|
   // symmetric metric m = J^T J (six entries)
@@ -458,7 +465,11 @@ struct GeoSampler {
     IGA_CUDA(cudaMemcpyAsync(ctx->hflag, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost,
                              ctx->stream));
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
-    IGA_REQUIRE(*ctx->hflag == 0, "geometry: zero or non-finite Jacobian determinant");
+    // omega = |det J| admits a map of either orientation, but not a vanishing
+    // determinant or one that changes sign (a map that folds over itself)
+    IGA_REQUIRE((*ctx->hflag & 4) == 0, "geometry: zero or non-finite Jacobian determinant");
+    IGA_REQUIRE((*ctx->hflag & 3) != 3,
+                "geometry: the Jacobian determinant changes sign (the map folds over itself)");
   }
 };
 

@@ -279,13 +279,17 @@ bool kkt_apply_fused(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta
                      void* out, iga_prec prec);
 void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
                      void* y, iga_prec prec);
+// the same with A^T (every band transposed)
+void kron_apply_transposed(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
+                           void* y, iga_prec prec);
 
 // ttm_tc.cu: one TT-matrix block y += alpha (A1 (x) A2 (x) A3) x in FP32
-// storage with the rank contraction on the tensor cores (TF32, FP32
-// accumulation); false when the shape has no tile plan (nothing launched).
+// storage with the rank contraction on the tensor cores (TF32 or BF16
+// operands, FP32 accumulation); false when the shape has no tile plan
+// (nothing launched).
 // A bounded wait that gives up sets ctx->dflag[1] to IGA_ETIMEOUT.
 bool ttm_tc_block(iga_ctx* ctx, const float* A1, const float* A2, const float* A3, int R1, int R2,
-                  const int* n, int P, float alpha, const float* x, float* y);
+                  const int* n, int P, float alpha, const float* x, float* y, bool bf16);
 bool ttm_tc_supported(int n1, int n3, int R1, int R2, int P, int nsm);
 // zero / check the tensor-core timeout flag around a TF32 entry (the check
 // synchronises the context stream)

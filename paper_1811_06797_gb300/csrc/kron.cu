@@ -422,16 +422,21 @@ __global__ void ttm_mode1_kernel(const T* __restrict__ bands1, int R1, int n1, i
   }
 }
 
+// tensor-core mode of an FP32 apply
+enum { TC_NONE = 0, TC_TF32 = 1, TC_BF16 = 2 };
+
 template <typename T, int P>
 static void ttm_block_gemm(iga_ctx* ctx, const iga_op* A, const OpBlock& blk, T alpha, const T* x,
-                           T* y, bool tf32) {
+                           T* y, int tc) {
   if constexpr (sizeof(T) == 4) {
-    // TF32: the fused tcgen05 kernel (one launch per block, O(tile) scratch)
-    if (tf32 && ttm_tc_block(ctx, band_ptr<float>(A, 0, blk.off[0]),
-                             band_ptr<float>(A, 1, blk.off[1]), band_ptr<float>(A, 2, blk.off[2]),
-                             blk.R1, blk.R2, A->n, P, (float)alpha, x, y))
+    // TF32 / BF16: the fused tcgen05 kernel (one launch per block, O(tile) scratch)
+    if (tc != TC_NONE && ttm_tc_block(ctx, band_ptr<float>(A, 0, blk.off[0]),
+                                      band_ptr<float>(A, 1, blk.off[1]),
+                                      band_ptr<float>(A, 2, blk.off[2]), blk.R1, blk.R2, A->n, P,
+                                      (float)alpha, x, y, tc == TC_BF16))
       return;
   }
+  const bool tf32 = tc != TC_NONE;
   const int n1 = A->n[0], n2 = A->n[1], n3 = A->n[2];
   constexpr int B = 2 * P + 1;
   const int R1 = blk.R1, R2 = blk.R2, Kd = B * R2;
@@ -473,7 +478,7 @@ static void ttm_block_gemm(iga_ctx* ctx, const iga_op* A, const OpBlock& blk, T 
 
 template <typename T, int P>
 static void kron_general(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y,
-                         bool tf32) {
+                         int tc) {
   const int* n = A->n;
   size_t N = (size_t)n[0] * n[1] * n[2];
   // y <- beta y first, then accumulate every block
@@ -489,13 +494,13 @@ static void kron_general(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T b
       mode_product<T, P>(ctx, band_ptr<T>(A, 0, blk.off[0]), 0, n, z2, y, alpha, 1);
       continue;
     }
-    ttm_block_gemm<T, P>(ctx, A, blk, alpha, x, y, tf32);
+    ttm_block_gemm<T, P>(ctx, A, blk, alpha, x, y, tc);
   }
 }
 
 template <typename T>
 static void kron_dispatch(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
-                          void* y, bool tf32 = false) {
+                          void* y, int tc = TC_NONE) {
   int P = A->p[0];
   IGA_REQUIRE(A->p[1] == P && A->p[2] == P, "kron_apply: equal degrees per direction required");
   const T* xx = static_cast<const T*>(x);
@@ -505,7 +510,7 @@ static void kron_dispatch(iga_ctx* ctx, const iga_op* A, double alpha, const voi
 #define IGA_KRON_CASE(PP)                                                                   \
   case PP:                                                                                  \
     if (fused) kron_rank1<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy);                        \
-    else kron_general<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy, tf32);                      \
+    else kron_general<T, PP>(ctx, A, (T)alpha, xx, (T)beta, yy, tc);                        \
     break;
     IGA_KRON_CASE(1)
     IGA_KRON_CASE(2)
@@ -544,13 +549,58 @@ bool kkt_apply_fused(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta
   return false;
 }
 
+// band of the transposed univariate matrix: A^T(i, i + o - p) = A(i + o - p, i)
+template <typename T>
+__global__ void band_transpose_kernel(const T* __restrict__ in, T* __restrict__ out, size_t nb,
+                                      int n, int P) {
+  const int B = 2 * P + 1;
+  const size_t total = nb * n * B;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(idx % B);
+    const size_t r = idx / B;
+    const int i = (int)(r % n);
+    const size_t k = r / n;
+    const int j = i + o - P;
+    out[idx] = (j >= 0 && j < n) ? in[(k * n + j) * B + (2 * P - o)] : T(0);
+  }
+}
+
+void kron_apply_transposed(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
+                           void* y, iga_prec prec) {
+  // (sum A1 (x) A2 (x) A3)^T = sum A1^T (x) A2^T (x) A3^T: the same blocks with
+  // every band transposed, in a temporary operator on the context stream
+  IGA_REQUIRE(A != nullptr, "kron_apply: null operator");
+  iga_op At;
+  for (int d = 0; d < 3; ++d) {
+    At.n[d] = A->n[d];
+    At.p[d] = A->p[d];
+    At.nbands[d] = A->nbands[d];
+  }
+  At.blocks = A->blocks;
+  At.rank1 = A->rank1;
+  for (int d = 0; d < 3; ++d) {
+    const size_t len = A->band64[d].n;
+    if (len == 0) continue;
+    const unsigned g = (unsigned)std::min<size_t>((len + 255) / 256, 4096);
+    At.band64[d].alloc(len);
+    IGA_LAUNCH(ctx, band_transpose_kernel<double>, g, 256, 0, A->band64[d].p, At.band64[d].p,
+               A->nbands[d], A->n[d], A->p[d]);
+    At.band32[d].alloc(A->band32[d].n);
+    IGA_LAUNCH(ctx, band_transpose_kernel<float>, g, 256, 0, A->band32[d].p, At.band32[d].p,
+               A->nbands[d], A->n[d], A->p[d]);
+  }
+  kron_apply_impl(ctx, &At, alpha, x, beta, y, prec);
+}
+
 void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
                      void* y, iga_prec prec) {
   IGA_REQUIRE(A != nullptr && x != nullptr && y != nullptr, "kron_apply: null argument");
   IGA_REQUIRE(x != y, "kron_apply: x and y must not overlap");
   if (prec == IGA_FP64) kron_dispatch<double>(ctx, A, alpha, x, beta, y);
   else if (prec == IGA_FP32) kron_dispatch<float>(ctx, A, alpha, x, beta, y);
-  else if (prec == IGA_TF32) kron_dispatch<float>(ctx, A, alpha, x, beta, y, true);
+  else if (prec == IGA_TF32) kron_dispatch<float>(ctx, A, alpha, x, beta, y, TC_TF32);
+  else if (prec == IGA_BF16) kron_dispatch<float>(ctx, A, alpha, x, beta, y, TC_BF16);
   else throw Error(IGA_EINVAL, "kron_apply: unknown precision");
 }
 

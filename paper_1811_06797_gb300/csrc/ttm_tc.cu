@@ -37,6 +37,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "iga_internal.cuh"
 
 namespace iga {
@@ -58,9 +60,10 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// instruction descriptor of kind::tf32 (A, B TF32, D FP32, both K-major)
-__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+// instruction descriptor of kind::tf32 (fmt 2) or kind::f16 with BF16
+// operands (fmt 1): D FP32, A and B K-major
+__device__ __forceinline__ uint32_t idesc_mma(int fmt, int M, int N) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
@@ -124,6 +127,13 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t a, uint64_t
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
+__device__ __forceinline__ void tc_mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -170,10 +180,11 @@ struct TtmTcArgs {
   float alpha;
   const float* A1;     // (R1, n1, 2P+1) bands of direction 1
   const float* A3;     // (R2, n3, 2P+1) bands of direction 3
-  const float* V;      // packed A2 columns: (n2, 2P+1, R1p x R2p MMA image)
+  const void* V;       // packed A2 columns: (n2, 2P+1, R1p x R2p MMA image), TF32 or BF16
   int n1, n2, n3;
   int R1, R2, R1p, R2p;
   int T1, T3, nt3;
+  int NV;              // stages of the A2-column ring (2..4)
   int tcols;           // tensor-memory columns allocated (power of two >= 32)
   int* err;            // set to IGA_ETIMEOUT when a bounded wait gives up
 };
@@ -188,39 +199,64 @@ __host__ __device__ inline int ttm_tc_s3(int P, int R2p) {
   return w + ((w / 4) % 2 == 0 ? 4 : 0);
 }
 
-// shared-memory footprint of one CTA (bytes, without the alignment slack)
-__host__ __device__ inline size_t ttm_tc_smem(int P, int H, int R1p, int R2p, int T1, int T3) {
+// shared-memory footprint of one CTA in bytes (es = operand element size)
+__host__ __device__ inline size_t ttm_tc_smem(int P, int H, int es, int NV, int R1p, int R2p,
+                                              int T1, int T3) {
   const size_t B = 2 * P + 1, PTS = 128 * (size_t)H;
-  size_t z = 2 * (size_t)H * 512 * R2p;                 // Z slabs, double buffered
-  size_t v = 2 * B * 4 * (size_t)R1p * R2p;             // A2 columns, double buffered
+  size_t z = 2 * (size_t)H * 128 * R2p * es;             // Z slabs, two stages
+  size_t v = (size_t)NV * B * (size_t)R1p * R2p * es;    // A2-column ring
   size_t a1 = (size_t)T1 * B * ttm_tc_s1(R1p) * 4, a3 = (size_t)T3 * ttm_tc_s3(P, R2p) * 4;
   size_t part = 2 * PTS * B * 4;
-  size_t bars = 8 * (7 + 2 * B) + 16;
-  return z + v + a1 + a3 + part + bars;
+  return z + v + a1 + a3 + part + 256 + 16;
 }
 
-template <int P, int H>
-__global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTcArgs g) {
+template <bool BF>
+__device__ __forceinline__ void store_z_chunk(unsigned char* dst, const float* acc);
+template <>
+__device__ __forceinline__ void store_z_chunk<false>(unsigned char* dst, const float* acc) {
+  *reinterpret_cast<float4*>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+template <>
+__device__ __forceinline__ void store_z_chunk<true>(unsigned char* dst, const float* acc) {
+  __nv_bfloat162 h[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) h[u] = __floats2bfloat162_rn(acc[2 * u], acc[2 * u + 1]);
+  *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+}
+
+}  // namespace iga
+
+namespace iga {
+
+// Warp roles: [0, 4H) producers (one thread per point), [4H, 8H) epilogue
+// (warp w reads tensor-memory lanes 32 (w % 4) ..), 8H the MMA issuer, 8H+1
+// the loader of the A2-column ring.
+template <int P, int H, bool BF>
+__global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTcArgs g) {
   constexpr int B = 2 * P + 1;
   constexpr int PTS = 128 * H;
   constexpr int NPW = 4 * H;             // producer warps = epilogue warps
-  constexpr int MMA_WARP = 8 * H;
+  constexpr int MMA_WARP = 8 * H, LOAD_WARP = 8 * H + 1;
+  constexpr int ES = BF ? 2 : 4;         // operand element size
+  constexpr int EPC = 16 / ES;           // elements per 16-byte core-matrix row
+  constexpr int KSTEP = 32 / ES;         // K of one MMA (two core matrices)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw;
-  const int R1p = g.R1p, R2p = g.R2p, T1 = g.T1, T3 = g.T3;
+  const int R1p = g.R1p, R2p = g.R2p, T1 = g.T1, T3 = g.T3, NV = g.NV;
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
-  const uint32_t ZH = 512u * R2p, VT = 4u * R1p * R2p, SBO = 32u * R2p;
+  const uint32_t ZH = 128u * R2p * ES, VT = (uint32_t)R1p * R2p * ES;
+  const uint32_t SBO = (uint32_t)(R2p / EPC) * 128u;   // 8-row group stride of both operands
+  const int S1 = ttm_tc_s1(R1p), S3 = ttm_tc_s3(P, R2p);
   unsigned char* zbuf = sm;
   unsigned char* vbuf = zbuf + 2 * H * ZH;
-  const int S1 = ttm_tc_s1(R1p), S3 = ttm_tc_s3(P, R2p);
-  float* a1s = reinterpret_cast<float*>(vbuf + 2 * B * VT);   // [(ii B + o) S1 + a]
-  float* a3s = a1s + T1 * B * S1;                               // [k S3 + o R2p + b]
+  float* a1s = reinterpret_cast<float*>(vbuf + (size_t)NV * B * VT);   // [(ii B + o) S1 + a]
+  float* a3s = a1s + T1 * B * S1;                                       // [k S3 + o R2p + b]
   float* part = a3s + T3 * S3;
   uint64_t* bars = reinterpret_cast<uint64_t*>(part + 2 * PTS * B);
-  const uint32_t z_full = su32(bars), v_full = z_full + 16, slab_free = z_full + 32;
-  const uint32_t acc_full = z_full + 48, acc_empty = acc_full + 8 * B,
+  const uint32_t z_full = su32(bars), z_free = z_full + 16, v_full = z_full + 32,
+                 v_free = v_full + 32, acc_full = v_free + 32, acc_empty = acc_full + 8 * B,
                  mma_done = acc_empty + 8 * B;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 7 + 2 * B);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 32);
   volatile int* abort_ = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t3 = blockIdx.x % g.nt3, t1 = blockIdx.x / g.nt3;
@@ -242,8 +278,11 @@ __global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTc
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(z_full + 8 * s, NPW);
+      mbar_init(z_free + 8 * s, 1);
+    }
+    for (int s = 0; s < NV; ++s) {
       mbar_init(v_full + 8 * s, 1);
-      mbar_init(slab_free + 8 * s, 1);
+      mbar_init(v_free + 8 * s, 1);
     }
     for (int c = 0; c < B; ++c) {
       mbar_init(acc_full + 8 * c, 1);
@@ -276,7 +315,7 @@ __global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTc
   tc_fence_after();
 
   if (warp < NPW) {
-    // ---- producers: mode-3 slabs and the bulk copies of the A2 columns
+    // ---- producers: mode-3 slabs
     const int pt = threadIdx.x;
     const int jj = pt / T3, k = pt - jj * T3, h = pt >> 7, m = pt & 127;
     const int j1 = I1 - P + jj, i3 = I3 + k;
@@ -284,7 +323,6 @@ __global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTc
     unsigned char* zrow = zbuf + h * ZH + (m >> 3) * SBO + (m & 7) * 16;
     const float4* a3r = reinterpret_cast<const float4*>(a3s + k * S3);
     const int R2q = R2p >> 2;
-    int issued[2] = {-1, -1};
     // x of the next slab is loaded one iteration ahead (its latency hides
     // behind the wait and the arithmetic of the current slab)
     float xn[B];
@@ -299,50 +337,40 @@ __global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTc
     load_x(0, xn);
     for (int j2 = 0; j2 < n2; ++j2) {
       const int s = j2 & 1;
-      const uint32_t use = (uint32_t)(j2 >> 1);
       float xw[B];
 #pragma unroll
       for (int o = 0; o < B; ++o) xw[o] = xn[o];
       if (j2 + 1 < n2) load_x(j2 + 1, xn);
       if (j2 >= 2) {
         bool ok = true;
-        if (lane == 0) ok = mbar_wait(slab_free + 8 * s, (use - 1) & 1, abort_);
+        if (lane == 0) ok = mbar_wait(z_free + 8 * s, (uint32_t)((j2 >> 1) - 1) & 1, abort_);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           if (lane == 0) fail();
           break;
         }
       }
-      if (pt == 0) {
-        mbar_expect_tx(v_full + 8 * s, (uint32_t)B * VT);
-        bulk_g2s(su32(vbuf + s * B * VT), g.V + (size_t)j2 * B * (VT / 4), (uint32_t)B * VT,
-                 v_full + 8 * s);
-        issued[s] = j2;
-      }
       unsigned char* zr = zrow + s * H * ZH;
-      for (int b4 = 0; b4 < R2q; ++b4) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c = 0; c < R2p / EPC; ++c) {
+        float acc[EPC];
+#pragma unroll
+        for (int u = 0; u < EPC; ++u) acc[u] = 0.f;
 #pragma unroll
         for (int o = 0; o < B; ++o) {
-          const float4 a = a3r[o * R2q + b4];
-          acc.x = fmaf(a.x, xw[o], acc.x);
-          acc.y = fmaf(a.y, xw[o], acc.y);
-          acc.z = fmaf(a.z, xw[o], acc.z);
-          acc.w = fmaf(a.w, xw[o], acc.w);
+#pragma unroll
+          for (int u4 = 0; u4 < EPC / 4; ++u4) {
+            const float4 a = a3r[o * R2q + c * (EPC / 4) + u4];
+            acc[4 * u4 + 0] = fmaf(a.x, xw[o], acc[4 * u4 + 0]);
+            acc[4 * u4 + 1] = fmaf(a.y, xw[o], acc[4 * u4 + 1]);
+            acc[4 * u4 + 2] = fmaf(a.z, xw[o], acc[4 * u4 + 2]);
+            acc[4 * u4 + 3] = fmaf(a.w, xw[o], acc[4 * u4 + 3]);
+          }
         }
-        *reinterpret_cast<float4*>(zr + b4 * 128) = acc;
+        store_z_chunk<BF>(zr + c * 128, acc);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(z_full + 8 * s);
-    }
-    // copies still in flight must land before the CTA exits
-    if (pt == 0) {
-      for (int s = 0; s < 2; ++s)
-        if (issued[s] >= 0) {
-          volatile int never = 0;
-          if (!mbar_wait(v_full + 8 * s, ((uint32_t)issued[s] >> 1) & 1, &never)) fail();
-        }
     }
   } else if (warp < 2 * NPW) {
     // ---- epilogue: drain accumulators, mode-1 product, y update
@@ -410,55 +438,84 @@ __global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTc
         ycol[(size_t)i2 * n3] = fmaf(g.alpha, v, ycur);
       }
     }
-  } else if (lane == 0) {
-    // ---- MMA issuer
-    const int maxrun = 256 / R1p;
-    auto issue = [&](int j2, int s, int ta, int tb) {
-      int t = ta;
-      while (t <= tb) {
-        const int c0 = (j2 - P + t) % B;
-        const int len = min(min(tb - t + 1, B - c0), maxrun);
-        const uint32_t idesc = idesc_tf32(128, len * R1p);
-        for (int kb = 0; kb < (R2p >> 3); ++kb) {
-          const uint64_t bd = umma_desc(su32(vbuf + s * B * VT + t * VT) + kb * 256, 128, SBO);
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const int maxrun = 256 / R1p;
+      auto issue = [&](int j2, int s, int sv, int ta, int tb) {
+        int t = ta;
+        while (t <= tb) {
+          const int c0 = (j2 - P + t) % B;
+          const int len = min(min(tb - t + 1, B - c0), maxrun);
+          const uint32_t idesc = idesc_mma(BF ? 1 : 2, 128, len * R1p);
+          for (int kb = 0; kb < R2p / KSTEP; ++kb) {
+            const uint64_t bd =
+                umma_desc(su32(vbuf + ((size_t)sv * B + t) * VT) + kb * 256, 128, SBO);
 #pragma unroll
-          for (int h = 0; h < H; ++h) {
-            const uint64_t ad = umma_desc(su32(zbuf + (s * H + h) * ZH) + kb * 256, 128, SBO);
-            tc_mma_tf32(tbase + (uint32_t)((h * B + c0) * R1p), ad, bd, idesc, 1u);
+            for (int h = 0; h < H; ++h) {
+              const uint64_t ad = umma_desc(su32(zbuf + (s * H + h) * ZH) + kb * 256, 128, SBO);
+              if (BF) tc_mma_bf16(tbase + (uint32_t)((h * B + c0) * R1p), ad, bd, idesc, 1u);
+              else tc_mma_tf32(tbase + (uint32_t)((h * B + c0) * R1p), ad, bd, idesc, 1u);
+            }
           }
+          t += len;
         }
-        t += len;
-      }
-    };
-    for (int j2 = 0; j2 < n2; ++j2) {
-      const int s = j2 & 1;
-      const uint32_t use = (uint32_t)(j2 >> 1);
-      if (!mbar_wait(z_full + 8 * s, use & 1, abort_) || !mbar_wait(v_full + 8 * s, use & 1, abort_)) {
-        fail();
-        break;
-      }
-      tc_fence_after();
-      const int tlo = max(0, P - j2), thi = min(B - 1, n2 - 1 - j2 + P);
-      const bool fresh = (j2 + P < n2) && (j2 + P >= B);   // target i2 = j2 + P reuses a ring slot
-      issue(j2, s, tlo, fresh ? B - 2 : thi);
-      if (fresh) {
-        const int i2n = j2 + P;
-        if (!mbar_wait(acc_empty + 8 * (i2n % B), (uint32_t)(i2n / B - 1) & 1, abort_)) {
+      };
+      for (int j2 = 0; j2 < n2; ++j2) {
+        const int s = j2 & 1, sv = j2 % NV;
+        if (!mbar_wait(z_full + 8 * s, (uint32_t)(j2 >> 1) & 1, abort_) ||
+            !mbar_wait(v_full + 8 * sv, (uint32_t)(j2 / NV) & 1, abort_)) {
           fail();
           break;
         }
         tc_fence_after();
-        issue(j2, s, B - 1, B - 1);
+        const int tlo = max(0, P - j2), thi = min(B - 1, n2 - 1 - j2 + P);
+        const bool fresh = (j2 + P < n2) && (j2 + P >= B);   // target i2 = j2 + P reuses a slot
+        issue(j2, s, sv, tlo, fresh ? B - 2 : thi);
+        // accumulator i2 = j2 - P is complete with these MMAs: hand it to the
+        // epilogue before waiting for the slot of the fresh target, so that the
+        // epilogue of i2 runs under the MMAs of the next slab
+        if (j2 - P >= 0) tc_commit(acc_full + 8 * ((j2 - P) % B));
+        if (fresh) {
+          const int i2n = j2 + P;
+          if (!mbar_wait(acc_empty + 8 * (i2n % B), (uint32_t)(i2n / B - 1) & 1, abort_)) {
+            fail();
+            break;
+          }
+          tc_fence_after();
+          issue(j2, s, sv, B - 1, B - 1);
+        }
+        tc_commit(z_free + 8 * s);
+        tc_commit(v_free + 8 * sv);
+        if (j2 == n2 - 1)
+          for (int i2 = max(0, j2 - P + 1); i2 < n2; ++i2) tc_commit(acc_full + 8 * (i2 % B));
       }
-      tc_commit(slab_free + 8 * s);
-      if (j2 - P >= 0) tc_commit(acc_full + 8 * ((j2 - P) % B));
-      if (j2 == n2 - 1)
-        for (int i2 = max(0, j2 - P + 1); i2 < n2; ++i2) tc_commit(acc_full + 8 * (i2 % B));
+      // every MMA issued must finish before the tensor memory is released
+      tc_commit(mma_done);
+      volatile int never = 0;
+      if (!mbar_wait(mma_done, 0, &never)) fail();
     }
-    // every MMA issued must finish before the tensor memory is released
-    tc_commit(mma_done);
-    volatile int never = 0;
-    if (!mbar_wait(mma_done, 0, &never)) fail();
+  } else if (warp == LOAD_WARP && lane == 0) {
+    // ---- loader: bulk copies of the A2 columns into the NV-stage ring
+    int last[4] = {-1, -1, -1, -1};
+    const unsigned char* V = static_cast<const unsigned char*>(g.V);
+    for (int j2 = 0; j2 < n2; ++j2) {
+      const int sv = j2 % NV;
+      if (j2 >= NV && !mbar_wait(v_free + 8 * sv, (uint32_t)(j2 / NV - 1) & 1, abort_)) {
+        fail();
+        break;
+      }
+      mbar_expect_tx(v_full + 8 * sv, (uint32_t)B * VT);
+      bulk_g2s(su32(vbuf + (size_t)sv * B * VT), V + (size_t)j2 * B * VT, (uint32_t)B * VT,
+               v_full + 8 * sv);
+      last[sv] = j2;
+    }
+    // copies still in flight must land before the CTA exits
+    for (int sv = 0; sv < NV; ++sv)
+      if (last[sv] >= 0) {
+        volatile int never = 0;
+        if (!mbar_wait(v_full + 8 * sv, (uint32_t)(last[sv] / NV) & 1, &never)) fail();
+      }
   }
 
   tc_fence_before();
@@ -475,11 +532,13 @@ __global__ void __launch_bounds__((8 * H + 1) * 32, 1) ttm_tc_kernel(const TtmTc
 namespace iga {
 
 // Column j2 of the A2 bands of one block as the B operand of the MMAs of slab
-// j2: V[j2][t] is an R1p x R2p K-major image (8-row x 4-column core
-// matrices) of A2[a][b](i2, 2P - t), i2 = j2 - P + t, zero outside the ranks
-// and the matrix.
+// j2: V[j2][t] is an R1p x R2p K-major image (core matrices of 8 rows x 16
+// bytes) of A2[a][b](i2, 2P - t), i2 = j2 - P + t, zero outside the ranks
+// and the matrix; TF32 keeps the FP32 bits, BF16 rounds to nearest.
+template <typename E>
 __global__ void ttm_tc_pack_kernel(const float* __restrict__ A2, int R1, int R2, int n2, int P,
-                                   int R1p, int R2p, float* __restrict__ V) {
+                                   int R1p, int R2p, E* __restrict__ V) {
+  constexpr int EPC = 16 / (int)sizeof(E);
   const int B = 2 * P + 1;
   const size_t img = (size_t)R1p * R2p;
   const size_t total = (size_t)n2 * B * img;
@@ -488,87 +547,117 @@ __global__ void ttm_tc_pack_kernel(const float* __restrict__ A2, int R1, int R2,
     const size_t jt = idx / img;
     const int e = (int)(idx - jt * img);
     const int t = (int)(jt % B), j2 = (int)(jt / B);
-    // e = (a/8) 8 R2p + (b/4) 32 + (a%8) 4 + b%4
+    // e = (a/8) 8 R2p + (b/EPC) 8 EPC + (a%8) EPC + b%EPC
     const int g8 = e / (8 * R2p), r8 = e - g8 * 8 * R2p;
-    const int b4 = r8 / 32, r32 = r8 - b4 * 32;
-    const int a = g8 * 8 + r32 / 4, b = b4 * 4 + (r32 & 3);
+    const int c = r8 / (8 * EPC), r = r8 - c * 8 * EPC;
+    const int a = g8 * 8 + r / EPC, b = c * EPC + r % EPC;
     const int i2 = j2 - P + t;
     float v = 0.f;
     if (a < R1 && b < R2 && i2 >= 0 && i2 < n2)
       v = A2[(((size_t)a * R2 + b) * n2 + i2) * B + (2 * P - t)];
-    V[idx] = v;
+    if constexpr (sizeof(E) == 2) V[idx] = __float2bfloat16_rn(v);
+    else V[idx] = v;
   }
 }
 
 struct TtmTcPlan {
   bool ok = false;
-  int H = 1, T1 = 0, T3 = 0, R1p = 0, R2p = 0, tcols = 0;
+  int H = 1, T1 = 0, T3 = 0, R1p = 0, R2p = 0, NV = 2, tcols = 0;
   size_t smem = 0;
 };
 
 static constexpr size_t TTM_TC_SMEM_MAX = 227 * 1024;
 
-// Tile of the fused tensor-core apply: two halves (256 lanes) when tensor
-// memory and shared memory allow, T3 in {16, 8, 4} consecutive i3 with
-// T1 = 128 H / T3 - 2P outputs along i1; the plan with the fewest waves of
-// CTAs over the SMs, weighted by the per-CTA work (proportional to H), wins.
-static TtmTcPlan ttm_tc_plan(int n1, int n3, int R1, int R2, int P, int nsm) {
+// Tile plan.  Per slab a CTA spends about H * 128 * B * R1p * R2p / rate
+// cycles in MMAs (rate: TF32 ~1500, BF16 ~3000 multiply-adds per SM and
+// cycle) plus about 1500 H cycles of CUDA-core work (the mode-3 and mode-1
+// products of 128 H points), and waits up to ~2500 cycles for one A2-column
+// copy, which an NV-stage ring spreads over NV - 1 slabs; the plan with the
+// least (waves of CTAs) x (cycles per slab) that fits tensor memory
+// (H B R1p <= 512 columns) and shared memory wins.
+static TtmTcPlan ttm_tc_plan(int n1, int n3, int R1, int R2, int P, bool bf16, int nsm) {
   TtmTcPlan best;
-  const int B = 2 * P + 1;
-  const int R1p = (R1 + 15) / 16 * 16, R2p = (R2 + 7) / 8 * 8;
+  const int B = 2 * P + 1, es = bf16 ? 2 : 4, kstep = bf16 ? 16 : 8;
+  const int R1p = (R1 + 15) / 16 * 16, R2p = (R2 + kstep - 1) / kstep * kstep;
   if (R1p > 256 || R2p > 256 || P < 1 || P > 3) return best;
+  const double rate = bf16 ? 3000.0 : 1500.0, vlat = 2500.0;
   double bestc = 1e300;
   for (int H = 2; H >= 1; --H) {
     if (H * B * R1p > 512) continue;
-    for (int T3 : {16, 8, 4}) {
-      const int T1 = 128 * H / T3 - 2 * P;
-      if (T1 < 1) continue;
-      const size_t smem = ttm_tc_smem(P, H, R1p, R2p, T1, T3) + 1024;
-      if (smem > TTM_TC_SMEM_MAX) continue;
-      const long nt = (long)((n1 + T1 - 1) / T1) * ((n3 + T3 - 1) / T3);
-      const double c = std::ceil((double)nt / nsm) * H;
-      if (c < bestc * (1 - 1e-9)) {
-        bestc = c;
-        best.ok = true;
-        best.H = H; best.T1 = T1; best.T3 = T3; best.R1p = R1p; best.R2p = R2p;
-        best.smem = smem;
-        int tc = 32;
-        while (tc < H * B * R1p) tc *= 2;
-        best.tcols = tc;
+    for (int NV = 4; NV >= 2; --NV)
+      for (int T3 : {16, 8, 4}) {
+        const int T1 = 128 * H / T3 - 2 * P;
+        if (T1 < 1) continue;
+        const size_t smem = ttm_tc_smem(P, H, es, NV, R1p, R2p, T1, T3) + 1024;
+        if (smem > TTM_TC_SMEM_MAX) continue;
+        const long nt = (long)((n1 + T1 - 1) / T1) * ((n3 + T3 - 1) / T3);
+        // per-slab cost: a fixed part (barrier hand-offs, the copy latency
+        // spread over NV - 1 slabs) and a part proportional to the points
+        const double slab = vlat / (NV - 1) + H * (128.0 * B * R1p * R2p / rate + 1500.0);
+        const double c = std::ceil((double)nt / nsm) * slab;
+        if (c < bestc * (1 - 1e-9)) {
+          bestc = c;
+          best.ok = true;
+          best.H = H; best.T1 = T1; best.T3 = T3; best.R1p = R1p; best.R2p = R2p; best.NV = NV;
+          best.smem = smem;
+          int tc = 32;
+          while (tc < H * B * R1p) tc *= 2;
+          best.tcols = tc;
+        }
       }
-    }
   }
   return best;
 }
 
 bool ttm_tc_supported(int n1, int n3, int R1, int R2, int P, int nsm) {
-  return ttm_tc_plan(n1, n3, R1, R2, P, nsm).ok;
+  return ttm_tc_plan(n1, n3, R1, R2, P, false, nsm).ok;
 }
 
-template <int P, int H>
+template <int P, int H, bool BF>
 static void ttm_tc_launch(iga_ctx* ctx, const TtmTcArgs& a, const TtmTcPlan& pl, unsigned grid) {
-  func_attr(ttm_tc_kernel<P, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-  IGA_LAUNCH(ctx, (ttm_tc_kernel<P, H>), grid, (8 * H + 1) * 32, pl.smem, a);
+  func_attr(ttm_tc_kernel<P, H, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  IGA_LAUNCH(ctx, (ttm_tc_kernel<P, H, BF>), grid, (8 * H + 2) * 32, pl.smem, a);
+}
+
+template <bool BF>
+static bool ttm_tc_dispatch(iga_ctx* ctx, const TtmTcArgs& a, const TtmTcPlan& pl, int P,
+                            unsigned grid) {
+  switch (P * 2 + (pl.H - 1)) {
+    case 2: ttm_tc_launch<1, 1, BF>(ctx, a, pl, grid); return true;
+    case 3: ttm_tc_launch<1, 2, BF>(ctx, a, pl, grid); return true;
+    case 4: ttm_tc_launch<2, 1, BF>(ctx, a, pl, grid); return true;
+    case 5: ttm_tc_launch<2, 2, BF>(ctx, a, pl, grid); return true;
+    case 6: ttm_tc_launch<3, 1, BF>(ctx, a, pl, grid); return true;
+    case 7: ttm_tc_launch<3, 2, BF>(ctx, a, pl, grid); return true;
+    default: return false;
+  }
 }
 
 // y += alpha (sum_{a,b} A1[a] (x) A2[a,b] (x) A3[b]) x for one TT-matrix block
-// in FP32 storage with TF32 tensor-core rank contraction.  Returns false (and
-// launches nothing) when the block's shape has no plan.
+// in FP32 storage with the rank contraction on the tensor cores (TF32, or
+// BF16 operands when bf16), FP32 accumulation.  Returns false (and launches
+// nothing) when the block's shape has no plan.
 bool ttm_tc_block(iga_ctx* ctx, const float* A1, const float* A2, const float* A3, int R1, int R2,
-                  const int* n, int P, float alpha, const float* x, float* y) {
-  const TtmTcPlan pl = ttm_tc_plan(n[0], n[2], R1, R2, P, ctx->nsm);
+                  const int* n, int P, float alpha, const float* x, float* y, bool bf16) {
+  const TtmTcPlan pl = ttm_tc_plan(n[0], n[2], R1, R2, P, bf16, ctx->nsm);
   if (!pl.ok) return false;
   const int B = 2 * P + 1;
   const size_t vcount = (size_t)n[1] * B * pl.R1p * pl.R2p;
-  float* V = scratch<float>(ctx, SLOT_TTM_W, vcount);
-  IGA_LAUNCH(ctx, ttm_tc_pack_kernel, (unsigned)std::min<size_t>((vcount + 255) / 256, 4096), 256,
-             0, A2, R1, R2, n[1], P, pl.R1p, pl.R2p, V);
+  void* V = scratch<char>(ctx, SLOT_TTM_W, vcount * (bf16 ? 2 : 4));
+  const unsigned pg = (unsigned)std::min<size_t>((vcount + 255) / 256, 4096);
+  if (bf16)
+    IGA_LAUNCH(ctx, ttm_tc_pack_kernel<__nv_bfloat16>, pg, 256, 0, A2, R1, R2, n[1], P, pl.R1p,
+               pl.R2p, static_cast<__nv_bfloat16*>(V));
+  else
+    IGA_LAUNCH(ctx, ttm_tc_pack_kernel<float>, pg, 256, 0, A2, R1, R2, n[1], P, pl.R1p, pl.R2p,
+               static_cast<float*>(V));
   TtmTcArgs a{};
   a.x = x; a.y = y; a.alpha = alpha;
   a.A1 = A1; a.A3 = A3; a.V = V;
   a.n1 = n[0]; a.n2 = n[1]; a.n3 = n[2];
   a.R1 = R1; a.R2 = R2; a.R1p = pl.R1p; a.R2p = pl.R2p;
   a.T1 = pl.T1; a.T3 = pl.T3; a.nt3 = (n[2] + pl.T3 - 1) / pl.T3;
+  a.NV = pl.NV;
   a.tcols = pl.tcols;
   a.err = ctx->dflag + 1;
   const unsigned grid = (unsigned)(((n[0] + pl.T1 - 1) / pl.T1) * a.nt3);
@@ -578,16 +667,8 @@ bool ttm_tc_block(iga_ctx* ctx, const float* A1, const float* A2, const float* A
     const double N = (double)n[0] * n[1] * n[2];
     prof_count(ctx, N * 4.0 * 3.0, 2.0 * B * N * (R2 + (double)R1 * R2 + R1));
   }
-  switch (P * 2 + (pl.H - 1)) {
-    case 2: ttm_tc_launch<1, 1>(ctx, a, pl, grid); break;
-    case 3: ttm_tc_launch<1, 2>(ctx, a, pl, grid); break;
-    case 4: ttm_tc_launch<2, 1>(ctx, a, pl, grid); break;
-    case 5: ttm_tc_launch<2, 2>(ctx, a, pl, grid); break;
-    case 6: ttm_tc_launch<3, 1>(ctx, a, pl, grid); break;
-    case 7: ttm_tc_launch<3, 2>(ctx, a, pl, grid); break;
-    default: return false;
-  }
-  return true;
+  return bf16 ? ttm_tc_dispatch<true>(ctx, a, pl, P, grid)
+              : ttm_tc_dispatch<false>(ctx, a, pl, P, grid);
 }
 
 }  // namespace iga

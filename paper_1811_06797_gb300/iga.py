@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libiga.so")
 _lib = None
 
-IGA_FP64, IGA_FP32, IGA_TF32 = 0, 1, 2
+IGA_FP64, IGA_FP32, IGA_TF32, IGA_BF16 = 0, 1, 2, 3
 IGA_TRUNC_PIVOTED, IGA_TRUNC_SVD = 0, 1
 STATUS = {0: "IGA_OK", 1: "IGA_EINVAL", 2: "IGA_ENOMEM", 3: "IGA_ECUDA", 4: "IGA_ENOCONV",
           5: "IGA_ENONFINITE", 6: "IGA_ETIMEOUT"}
@@ -87,6 +87,8 @@ def lib():
         "iga_tt_core": (st, [vp, vp, i, vp]),
         "iga_tt_full": (st, [vp, vp, vp]),
         "iga_tt_destroy": (None, [vp]),
+        "iga_tt_save": (st, [vp, vp, C.c_char_p]),
+        "iga_tt_load": (st, [vp, C.c_char_p, P(vp)]),
         "iga_assemble_bands": (st, [vp, P(Space_), i, vp, i, i, i, i, vp]),
         "iga_lowrank_assemble": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, P(vp), P(vp),
                                       P(vp)]),
@@ -97,12 +99,13 @@ def lib():
         "iga_spd_solve": (st, [vp, vp, vp, vp, vp, vp, d, i, P(C.c_int), P(d)]),
         "iga_reduced_gradient": (st, [vp, vp, vp, vp, d, i, vp, d, vp, vp, vp, P(d)]),
         "iga_weight_gradient": (st, [vp, P(Space_), vp, vp, d, vp, vp, vp, vp]),
+        "iga_op_from_bands": (st, [vp, P(C.c_int), P(C.c_int), i, P(C.c_int), P(vp), P(vp)]),
         "iga_op_info": (st, [vp, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int),
                              P(C.c_size_t)]),
         "iga_op_block": (st, [vp, i, P(C.c_int)]),
         "iga_op_bands": (st, [vp, vp, i, i, vp]),
         "iga_op_destroy": (None, [vp]),
-        "iga_kron_apply": (st, [vp, vp, d, vp, d, vp, i]),
+        "iga_kron_apply": (st, [vp, vp, i, d, vp, d, vp, i]),
         "iga_kkt_apply": (st, [vp, vp, vp, d, vp, vp, i]),
         "iga_amen_local_matvec": (st, [vp, i, i, i, i, i, i, vp, vp, vp, vp, i, vp, vp, i]),
         "iga_amen_local_matvec_noalloc": (st, [vp, i, i, i, i, i, i, vp, vp, vp, vp, i, vp, vp,
@@ -110,6 +113,8 @@ def lib():
         "iga_solve_opts_default": (None, [P(SolveOpts_)]),
         "iga_kkt_solve_amen": (st, [vp, vp, vp, vp, d, P(SolveOpts_), vp, vp, vp,
                                     P(SolveInfo_)]),
+        "iga_kkt_solve_amen_tt": (st, [vp, vp, vp, vp, d, P(SolveOpts_), P(vp), P(vp), P(vp),
+                                       P(SolveInfo_)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -278,6 +283,9 @@ class TT:
         _check(ctx, lib().iga_tt_full(ctx.handle, self.handle, _ptr(out)))
         return out
 
+    def save(self, ctx, path):
+        _check(ctx, lib().iga_tt_save(ctx.handle, self.handle, os.fsencode(path)))
+
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.iga_tt_destroy(self.handle)
@@ -329,6 +337,12 @@ def iga_sample_weights(ctx, geometry, space, target, out):
     t = target_struct(target)
     _check(ctx, lib().iga_sample_weights(ctx.handle, C.byref(g), C.byref(s), C.byref(t), _ptr(out)))
     return out
+
+
+def iga_tt_load(ctx, path):
+    h = C.c_void_p()
+    _check(ctx, lib().iga_tt_load(ctx.handle, os.fsencode(path), C.byref(h)))
+    return TT(h)
 
 
 def iga_tt_svd(ctx, W, tol, norm_ref=0.0, rmax=0):
@@ -393,6 +407,30 @@ def iga_ops_from_weights(ctx, space, weights):
     return Op(hm), Op(hk)
 
 
+def iga_op_from_bands(ctx, blocks):
+    """Operator from banded factors: blocks = [(A1, A2, A3), ...] FP64 CUDA
+    tensors of shapes (R1, n1, 2p+1), (R1, R2, n2, 2p+1), (R2, n3, 2p+1)."""
+    nb = len(blocks)
+    if nb == 0:
+        raise IgaError(1, "no blocks")
+    A1, A2, A3 = blocks[0]
+    n = (C.c_int * 3)(A1.shape[1], A2.shape[2], A3.shape[1])
+    p = (C.c_int * 3)(*[(t.shape[-1] - 1) // 2 for t in (A1, A2, A3)])
+    R = (C.c_int * (2 * nb))()
+    ptrs = (C.c_void_p * (3 * nb))()
+    for k, (a1, a2, a3) in enumerate(blocks):
+        R[2 * k], R[2 * k + 1] = a1.shape[0], a3.shape[0]
+        if tuple(a2.shape[:2]) != (a1.shape[0], a3.shape[0]):
+            raise IgaError(1, "A2 must be (R1, R2, n2, 2p+1)")
+        for d, t in enumerate((a1, a2, a3)):
+            ptrs[3 * k + d] = _ptr(t).value
+            if t.dtype.itemsize != 8:
+                raise IgaError(1, "bands must be float64")
+    h = C.c_void_p()
+    _check(ctx, lib().iga_op_from_bands(ctx.handle, n, p, nb, R, ptrs, C.byref(h)))
+    return Op(h)
+
+
 def iga_load_from_density(ctx, space, density):
     keep = _Keep()
     s = space_struct(space, keep)
@@ -429,17 +467,19 @@ def iga_weight_gradient(ctx, space, M, K, beta, y, u, lam, grad_w):
     return grad_w
 
 
-def iga_kron_apply(ctx, A, alpha, x, beta, y, tf32=False):
-    """y = alpha A x + beta y; float32 tensors with tf32=True use the TF32 tensor-core path."""
+def iga_kron_apply(ctx, A, alpha, x, beta, y, tf32=False, bf16=False, transpose=False):
+    """y = alpha op(A) x + beta y (op(A) = A^T with transpose=True); float32
+    tensors with tf32=True (bf16=True) run the rank contraction of TT-matrix
+    blocks on the tensor cores with TF32 (BF16) operands."""
     if x.dtype != y.dtype:
         raise IgaError(1, "x and y dtypes differ")
     prec = _prec(x)
-    if tf32:
-        if prec != IGA_FP32:
-            raise IgaError(1, "tf32 needs float32 tensors")
-        prec = IGA_TF32
-    _check(ctx, lib().iga_kron_apply(ctx.handle, A.handle, float(alpha), _ptr(x), float(beta),
-                                     _ptr(y), prec))
+    if tf32 or bf16:
+        if prec != IGA_FP32 or (tf32 and bf16):
+            raise IgaError(1, "tf32 / bf16 need float32 tensors (one of the two)")
+        prec = IGA_TF32 if tf32 else IGA_BF16
+    _check(ctx, lib().iga_kron_apply(ctx.handle, A.handle, int(bool(transpose)), float(alpha),
+                                     _ptr(x), float(beta), _ptr(y), prec))
     return y
 
 
@@ -551,3 +591,19 @@ def iga_kkt_solve_amen(ctx, M, K, load, beta, y, u, lam, **opts):
         _check(ctx, st)
     res["converged"] = st == 0
     return res
+
+
+def iga_kkt_solve_amen_tt(ctx, M, K, load, beta, **opts):
+    """The KKT solve with the solution as TT handles: (y, u, lam, info)."""
+    o = solve_opts(**opts)
+    info = SolveInfo_()
+    hs = [C.c_void_p() for _ in range(3)]
+    st = lib().iga_kkt_solve_amen_tt(ctx.handle, M.handle, K.handle,
+                                     load.handle if load is not None else None, float(beta),
+                                     C.byref(o), C.byref(hs[0]), C.byref(hs[1]), C.byref(hs[2]),
+                                     C.byref(info))
+    res = {f: getattr(info, f) for f, _ in SolveInfo_._fields_}
+    if st not in (0, 4):
+        _check(ctx, st)
+    res["converged"] = st == 0
+    return tuple(TT(h) if h.value else None for h in hs) + (res,)

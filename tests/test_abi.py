@@ -39,7 +39,7 @@ def test_binding_covers_header(libpath):
 def test_null_context_is_rejected(libpath):
     from paper_1811_06797_gb300 import iga
     L = iga.lib()
-    assert L.iga_kron_apply(None, None, 1.0, None, 0.0, None, 0) == 1
+    assert L.iga_kron_apply(None, None, 0, 1.0, None, 0.0, None, 0) == 1
     assert L.iga_last_error(None) == b"null context"
     assert L.iga_launch_count(None) == 0
 

@@ -83,3 +83,50 @@ def test_config2_solve_rows(setup, prec, trunc):
         assert abs(my + kl - br[s]) <= bound, (s, r, my + kl - br[s])
         assert abs(work.beta * mu - ml) <= bound, (s, r)
         assert abs(ky - mu) <= bound, (s, r)
+
+
+@pytest.fixture(scope="module")
+def oracle_solutions():
+    # the oracle's own route at full size: sampled weights (once), TT-SVD at the
+    # workload's tolerance and at 1e-10, univariate factors, reduced-system CG
+    # to 1e-12 (oracle/solve.py)
+    from oracle.assemble import sample_weights
+    from oracle.solve import timed_solve
+    work = wl.config(2)
+    disc = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+    samples = sample_weights(work.geometry, disc)
+    return {tol: timed_solve(work, tol=1e-12, tt_tol=tol, samples=samples)
+            for tol in (work.tol, 1e-10)}
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("tt_tol", [1e-6, 1e-10], ids=["tt1e-6", "tt1e-10"])
+def test_config2_solution_matches_oracle_elementwise(setup, oracle_solutions, prec, tt_tol):
+    """y, u and lambda of the GPU solve against the oracle's solution, element by
+    element.  With both sides' weights and load truncated at 1e-10 the two
+    operators agree to rounding, and the refined solve (run to a residual of
+    1e-9) must agree within 1e-6 relative in every field, the accuracy target
+    of the mixed-precision refined solve.  At the workload's own truncation
+    (1e-6) the two independent TT-SVDs of the load density differ at that
+    level, so the bound is 10 x the truncation tolerance."""
+    ctx, torch, iga, work, M, K, load, n, rows, Mr, Kr, br = setup
+    ref_sol = oracle_solutions[tt_tol if tt_tol != 1e-6 else work.tol]
+    if tt_tol != work.tol:
+        M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, tt_tol)
+    bound = 1e-6 if tt_tol < 1e-8 else 1e-6 + 10 * tt_tol
+    ni = M.info()["n"]
+    N = int(np.prod(ni))
+    bfull = torch.empty(ni, dtype=torch.float64, device="cuda")
+    load.full(ctx, bfull)
+    bo = ref_sol["b"]
+    assert np.linalg.norm(bfull.cpu().numpy().ravel() - bo) <= 10 * tt_tol * np.linalg.norm(bo)
+    y, u, lam = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+    info = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, y, u, lam, tol=1e-9,
+                                  precision=prec)
+    assert info["converged"], info
+    for g, name in ((y, "y"), (u, "u"), (lam, "lam")):
+        ref = ref_sol[name]
+        got = g.cpu().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= bound, (name, err)
+        assert np.abs(got - ref).max() <= 10 * bound * np.abs(ref).max(), name

@@ -156,3 +156,44 @@ def test_errors_are_reported(env):
     with pytest.raises(iga.IgaError) as e:
         iga.iga_lowrank_assemble(ctx, bad.geometry, bad.space, bad.target, 1e-8)
     assert e.value.status == 1 and "end knots" in str(e.value)
+
+
+def _random_band_op(env, n, p, ranks, seed):
+    """Operator from random, non-symmetric banded factors (iga_op_from_bands)
+    and its oracle Kronecker terms."""
+    ctx, torch, iga = env
+    rng = np.random.default_rng(seed)
+    b = 2 * p + 1
+    blocks, terms = [], []
+    for R1, R2 in ranks:
+        A1 = rng.standard_normal((R1, n[0], b))
+        A2 = rng.standard_normal((R1, R2, n[1], b))
+        A3 = rng.standard_normal((R2, n[2], b))
+        blocks.append(tuple(torch.tensor(a, device="cuda") for a in (A1, A2, A3)))
+        for a in range(R1):
+            for c in range(R2):
+                terms.append([band_dense(A1[a]), band_dense(A2[a, c]), band_dense(A3[c])])
+    return iga.iga_op_from_bands(ctx, blocks), terms
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_operator_from_bands_and_its_transpose(env, prec, transpose):
+    """op(A) x for an operator built from random non-symmetric banded factors
+    (one rank-1 block and one TT-matrix block), with op(A) = A or A^T (every
+    factor transposed, Sec. 5 eq. K_kron), against the oracle's Kronecker
+    product of the same (transposed) factors."""
+    ctx, torch, iga = env
+    n = (23, 19, 21)
+    op, terms = _random_band_op(env, n, 2, [(1, 1), (6, 5)], seed=31)
+    if transpose:
+        terms = [[A.T.copy() for A in t] for t in terms]
+    N = int(np.prod(n))
+    x = np.random.default_rng(32).standard_normal(N)
+    ref = kron_apply(terms, x)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    y = torch.zeros(N, dtype=dt, device="cuda")
+    iga.iga_kron_apply(ctx, op, 1.0, torch.tensor(x, device="cuda", dtype=dt), 0.0, y,
+                       tf32=prec == "tf32", bf16=prec == "bf16", transpose=transpose)
+    err = np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < {"fp64": 1e-13, "fp32": 1e-5, "tf32": 5e-3, "bf16": 2.5e-2}[prec], err

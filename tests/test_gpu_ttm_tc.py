@@ -35,10 +35,17 @@ def random_op(env, p, E, R1, R2, seed):
     return M
 
 
-@pytest.mark.parametrize("p,E,R1,R2", [(2, 13, 7, 5), (1, 22, 17, 9), (3, 9, 12, 20),
-                                       (2, 30, 35, 33), (2, 21, 48, 48), (2, 2, 4, 3),
-                                       (3, 5, 40, 8), (2, 41, 16, 24)])
-def test_tensor_core_apply_matches_the_kronecker_definition(env, p, E, R1, R2):
+CASES = [(2, 13, 7, 5), (1, 22, 17, 9), (3, 9, 12, 20), (2, 30, 35, 33), (2, 21, 48, 48),
+         (2, 2, 4, 3), (3, 5, 40, 8), (2, 41, 16, 24)]
+# operand rounding: TF32 keeps 10 fraction bits, BF16 7 (relative 2^-11 and
+# 2^-8 per operand, round to nearest); the bounds leave room for a sum of a
+# few hundred such products
+TOL = {"tf32": (5e-3, 2e-2), "bf16": (2.5e-2, 8e-2)}
+
+
+@pytest.mark.parametrize("kind", ["tf32", "bf16"])
+@pytest.mark.parametrize("p,E,R1,R2", CASES)
+def test_tensor_core_apply_matches_the_kronecker_definition(env, p, E, R1, R2, kind):
     ctx, torch, iga = env
     M = random_op(env, p, E, R1, R2, seed=R1 * 100 + R2)
     assert M.block_ranks(0) == (R1, R2)
@@ -51,28 +58,31 @@ def test_tensor_core_apply_matches_the_kronecker_definition(env, p, E, R1, R2):
     xt = torch.tensor(x, device="cuda", dtype=torch.float32)
     yt = torch.tensor(y0, device="cuda", dtype=torch.float32)
     ctx.profile_begin("ttm_tc_kernel")
-    iga.iga_kron_apply(ctx, M, 0.75, xt, 0.5, yt, tf32=True)
+    iga.iga_kron_apply(ctx, M, 0.75, xt, 0.5, yt, tf32=kind == "tf32", bf16=kind == "bf16")
     prof = ctx.profile_end()
     assert prof["launches"] == 1                      # the fused tensor-core kernel ran
     want = 0.75 * ref + 0.5 * y0
     got = yt.double().cpu().numpy()
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
-    assert err < 5e-3, err
-    assert np.abs(got - want).max() < 2e-2 * np.abs(want).max()
+    tn, tm = TOL[kind]
+    assert err < tn, err
+    assert np.abs(got - want).max() < tm * np.abs(want).max()
 
 
-def test_tensor_core_apply_is_deterministic_and_accumulates(env):
+@pytest.mark.parametrize("kind", ["tf32", "bf16"])
+def test_tensor_core_apply_is_deterministic_and_accumulates(env, kind):
     ctx, torch, iga = env
     M = random_op(env, 2, 17, 20, 20, seed=5)
     N = int(np.prod(M.info()["n"]))
     x = torch.randn(N, device="cuda", dtype=torch.float32)
     y1 = torch.zeros(N, device="cuda", dtype=torch.float32)
     y2 = torch.zeros(N, device="cuda", dtype=torch.float32)
-    iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y1, tf32=True)
-    iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y2, tf32=True)
+    kw = {kind: True}
+    iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y1, **kw)
+    iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y2, **kw)
     assert torch.equal(y1, y2)
     # y = 2 A x from two accumulating calls equals one call with alpha = 2
-    iga.iga_kron_apply(ctx, M, 1.0, x, 1.0, y2, tf32=True)
+    iga.iga_kron_apply(ctx, M, 1.0, x, 1.0, y2, **kw)
     y3 = torch.zeros(N, device="cuda", dtype=torch.float32)
-    iga.iga_kron_apply(ctx, M, 2.0, x, 0.0, y3, tf32=True)
+    iga.iga_kron_apply(ctx, M, 2.0, x, 0.0, y3, **kw)
     assert float((y2 - y3).abs().max()) <= 1e-5 * float(y3.abs().max())
