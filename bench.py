@@ -184,50 +184,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def cpu_oracle_sample(work, budget_s=20.0):
-    """Time the oracle on a bounded sample of the workload; scaled to one solve.
-
-    Assembly: the oracle's element loop on as many slabs of elements (along
-    direction 1) as fit the budget, scaled linearly to all slabs.  KKT solve:
-    the oracle's sparse direct solve is measured on the same geometry at a
-    reduced element count and scaled by (unknowns ratio)^2 (3-D nested
-    dissection cost grows about as N^2).
-    """
-    import numpy as np
-    from oracle.assemble import Discretisation, assemble_band, band_to_csr
-    from oracle.kkt import kkt_solve
-    from paper_1811_06797_gb300 import workloads as wl
-    p = work.space.degree[0]
-    E = len(np.unique(work.space.knots[0])) - 1
-    # --- assembly sample: a thin slab of elements
-    slab = 1
-    disc_full = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
-    t0 = time.perf_counter()
-    # restrict to a slab by building a space with E elements in dirs 2, 3 and `slab` in dir 1,
-    # same element size: knots on [0, slab/E]
-    k1 = np.concatenate([np.zeros(p), np.linspace(0, slab / E, slab + 1), np.full(p, slab / E)])
-    k1 = k1 / k1[-1]   # element loop cost does not depend on the element size
-    disc = Discretisation(work.space.degree, (k1, work.space.knots[1], work.space.knots[2]),
-                          work.space.nquad)
-    try:
-        assemble_band(work.geometry, disc, work.target, chunk=1)
-        t_slab = time.perf_counter() - t0
-    except MemoryError:
-        t_slab = float("nan")
-    t_asm = t_slab * E / slab
-    # --- solve sample on a reduced grid of the same geometry
-    Es = 10
-    ws = wl.small(work.geometry, p, Es, work.target, beta=work.beta)
-    ds = Discretisation(ws.space.degree, ws.space.knots, ws.space.nquad)
-    Mb, Kb, b = assemble_band(ws.geometry, ds, ws.target)
-    M, K = band_to_csr(Mb, True), band_to_csr(Kb, True)
-    t1 = time.perf_counter()
-    kkt_solve(M, K, ws.beta, b[1:-1, 1:-1, 1:-1].ravel())
-    t_solve_s = time.perf_counter() - t1
-    Ns = M.shape[0]
-    Nf = int(np.prod(disc_full.n)) // 1
-    Nf = int(np.prod([n - 2 for n in disc_full.n]))
-    t_solve = t_solve_s * (Nf / Ns) ** 2
+def _threads():
     cores = os.cpu_count() or 1
     try:
         import threadpoolctl
@@ -235,17 +192,172 @@ def cpu_oracle_sample(work, budget_s=20.0):
         cores = max([i.get("num_threads", 1) for i in info] + [1])
     except Exception:
         pass
-    total = t_asm + t_solve
-    return {
-        "value": total, "unit": "s", "cores": cores, "kind": "oracle",
-        "sample": (f"assembly: element loop on 1 of {E} slabs of elements ({t_slab:.2f} s) x{E}; "
-                   f"KKT: SuperLU on the same geometry at {Es}^3 elements ({3 * Ns} unknowns, "
-                   f"{t_solve_s:.2f} s) scaled by (N/N_s)^2 to {3 * Nf} unknowns"),
-        "assembly_s": t_asm, "solve_s_extrapolated": t_solve,
-    }
+    return cores
+
+
+class OracleLeg:
+    """The oracle (oracle/) timed on the host cores on a bounded sample of the
+    workload, and its solution for the per-field errors of the GPU result.
+
+    Set-up (untimed, once): the oracle's full pipeline at full size -- the
+    weights sampled on the whole Gauss grid, TT-SVD, univariate factors, the
+    reduced-system CG solve to 1e-12 (oracle/solve.py).  One timed step:
+      * sampling of the weights on a slab of 1/S of the Gauss planes along
+        direction 3, scaled by S (the per-point work is identical);
+      * TT-SVD of the eight sample tensors of that slab, scaled by S (the
+        first unfolding dominates and its SVD cost is linear in its number of
+        columns);
+      * univariate factors and load vector at full size;
+      * the reduced-system CG solve at full size to 1e-12.
+    The value is the sum, in seconds per step of the GPU arm's metric.
+    """
+
+    def __init__(self, work, slab=16):
+        import numpy as np
+        from oracle.assemble import Discretisation, sample_weights
+        self.work = work
+        self.disc = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+        from oracle.lowrank import weight_tts
+        from oracle.solve import operators_from_tts, solve_kkt
+        t0 = time.perf_counter()
+        samples = sample_weights(work.geometry, self.disc)
+        self.tts = weight_tts(work.geometry, self.disc, work.tol, work.target, samples=samples)
+        Mt, Kt, diag, b = operators_from_tts(work.space, self.tts)
+        y, u, lam, _ = solve_kkt(Mt, Kt, diag, b, work.beta, tol=1e-12)
+        self.full = {"y": y, "u": u, "lam": lam}
+        self.setup_s = time.perf_counter() - t0
+        q3 = len(self.disc.x[2].ravel())
+        self.S = max(1, q3 // slab)
+        self.slab = q3 // self.S
+        del samples
+        self.np = np
+
+    def step(self):
+        """One timed step: (seconds scaled to the whole workload, parts)."""
+        np = self.np
+        from oracle.assemble import evaluate_target
+        from oracle.geometry import grid_points, map_and_jacobian, weights_from_jacobian
+        from oracle.lowrank import tt_svd
+        from oracle.solve import operators_from_tts, solve_kkt
+        w = self.work
+        xs, gs = self.disc.gauss_grid()
+        xs3 = [xs[0], xs[1], xs[2][:self.slab]]
+        gs3 = [gs[0], gs[1], gs[2][:self.slab]]
+        t0 = time.perf_counter()
+        pts = grid_points(xs3)
+        G, J = map_and_jacobian(w.geometry.kind, w.geometry.degree, w.geometry.knots,
+                                w.geometry.homogeneous(), w.geometry.twist, pts)
+        omega, Q, _ = weights_from_jacobian(J)
+        shp = tuple(len(x) for x in xs3)
+        g = np.einsum("a,b,c->abc", *gs3)
+        om = omega.reshape(shp) * g
+        Qg = Q.reshape(shp + (3, 3)) * g[..., None, None]
+        f = evaluate_target(w.target, G).reshape(shp) * om
+        t1 = time.perf_counter()
+        qn = np.linalg.norm(Qg)
+        tt_svd(om, w.tol)
+        for k in range(3):
+            for l in range(k, 3):
+                tt_svd(np.ascontiguousarray(Qg[..., k, l]), w.tol, norm=qn)
+        tt_svd(f, w.tol)
+        t2 = time.perf_counter()
+        Mt, Kt, diag, b = operators_from_tts(w.space, self.tts)
+        t3 = time.perf_counter()
+        solve_kkt(Mt, Kt, diag, b, w.beta, tol=1e-12)
+        t4 = time.perf_counter()
+        parts = {"sampling_s": (t1 - t0) * self.S, "tt_svd_s": (t2 - t1) * self.S,
+                 "univariate_s": t3 - t2, "solve_s": t4 - t3}
+        return sum(parts.values()), parts
+
+    def describe(self):
+        return (f"oracle pipeline at full size in the set-up ({self.setup_s:.1f} s, untimed); per "
+                f"step: weight sampling and TT-SVD on a slab of {self.slab} of "
+                f"{self.slab * self.S} Gauss planes along direction 3, scaled x{self.S}; "
+                f"univariate factors, load and reduced-system CG solve to 1e-12 at full size")
 
 
 # ------------------------------------------------------------------ GPU leg
+
+# TF32 dense tensor rate from the measured BF16 GEMM rate and the nominal
+# ratio of the two (1.1 / 2.25 PFLOP/s dense per GB300)
+TF32_PER_BF16 = 1.1 / 2.25
+# TT ranks of the tensor-core apply measurement: the ranks of the sampled
+# metric entries q_kl of the random-volume workload at TT tolerance 1e-8
+# (36-38 on a 96^3 Gauss grid; omega has 33)
+TTM_RANK = 37
+
+
+def ttm_roofline(ctx, iga, torch, pk, pk_kind, reps=5):
+    """The TT-matrix Kronecker apply on the tensor cores (TF32 and BF16
+    operands) at the shape of the random-volume workload: degree 2, 512
+    elements per direction (n = 512 interior functions per direction), one
+    TT-matrix block of ranks (TTM_RANK, TTM_RANK) assembled from a seeded
+    weight TT of those ranks on its Gauss grid.  Live CUDA-event timing of
+    the fused kernel; algorithmic flops 2 (2p+1) N (R2 + R1 R2 + R1)."""
+    import numpy as np
+    from paper_1811_06797_gb300 import workloads as wl
+    space = wl.uniform_space(2, 512)
+    Q = 512 * space.nquad
+    R = TTM_RANK
+    rng = np.random.default_rng(1811)
+    cores = [rng.uniform(0.5, 1.5, (1, Q, R)), rng.standard_normal((R, Q, R)),
+             rng.uniform(0.5, 1.5, (R, Q, 1))]
+    tt = iga.iga_tt_from_cores(ctx, [torch.tensor(c, device="cuda") for c in cores])
+    M, _ = iga.iga_ops_from_weights(ctx, space, [tt] + [None] * 6)
+    N = int(np.prod(M.info()["n"]))
+    x = torch.randn(N, device="cuda", dtype=torch.float32)
+    y = torch.zeros(N, device="cuda", dtype=torch.float32)
+    out = {}
+    for kind in ("tf32", "bf16"):
+        kw = {kind: True}
+        iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y, **kw)
+        torch.cuda.synchronize()
+        ctx.profile_begin("ttm_tc_kernel")
+        for _ in range(reps):
+            iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y, **kw)
+        p = ctx.profile_end()
+        avg = p["ms"] / max(1, p["launches"])
+        fl = p["flops"] / max(1, p["launches"])
+        ach = fl / (avg * 1e-3) / 1e12
+        peak = pk["bf16_tflops"] * (TF32_PER_BF16 if kind == "tf32" else 1.0)
+        out[kind] = {"kernel": "ttm_tc_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak,
+                     "peak_kind": (f"{pk_kind} BF16 GEMM rate" +
+                                   (" x 1.1/2.25 (nominal TF32/BF16)" if kind == "tf32" else "")),
+                     "avg_ms": avg, "launches": p["launches"],
+                     "algorithmic_flops_per_launch": fl,
+                     "algorithmic_bytes_per_launch": p["bytes"] / max(1, p["launches"]),
+                     "workload": f"random-volume shape, p=2, n=512^3, TT ranks ({R},{R})"}
+    del M, tt, x, y
+    torch.cuda.empty_cache()
+    return out
+
+
+def rank_tables(ctx):
+    """TT ranks of the seven sampled weights at the tolerances of the paper's
+    rank tables (Sec. 6) on the two curved synthetic geometries, degree 2,
+    64 elements per direction."""
+    import math
+    from paper_1811_06797_gb300 import report, workloads as wl
+    out = {}
+    space = wl.uniform_space(2, 64)
+    for name, geo in (("twisted_annulus_p2_e64", wl.quarter_annulus(twist=math.pi / 4)),
+                      ("random_volume_p2_e64", wl.random_volume())):
+        tab = report.rank_table(ctx, geo, space, (1e-4, 1e-7, 1e-10))
+        out[name] = {f"{t:g}": {w: (list(r) if r else None) for w, r in row.items()}
+                     for t, row in tab.items()}
+    return out
+
+
+def field_errors(sol, ref):
+    """Relative 2-norm and max-norm errors of (y, u, lam) against the oracle."""
+    import numpy as np
+    out = {}
+    for name, a in zip(("y", "u", "lam"), sol):
+        r = ref[name]
+        out[name] = {"rel_2": float(np.linalg.norm(a - r) / np.linalg.norm(r)),
+                     "rel_max": float(np.abs(a - r).max() / np.abs(r).max())}
+    return out
 
 def run_gpu(args, world, rank, local):
     import numpy as np
@@ -253,6 +365,7 @@ def run_gpu(args, world, rank, local):
     from paper_1811_06797_gb300 import build, iga, workloads as wl
 
     build.build()
+    from paper_1811_06797_gb300 import report
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -337,6 +450,7 @@ def run_gpu(args, world, rank, local):
     iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"], state["lam"],
                            tol=args.tol, precision=other)
     paths = {}
+    solutions = {}
     # the two precisions with the default (pivoted) moves, and FP64 with the
     # SVD moves of the paper
     variants = [(prec, iga.IGA_TRUNC_PIVOTED), (other, iga.IGA_TRUNC_PIVOTED),
@@ -357,6 +471,8 @@ def run_gpu(args, world, rank, local):
         paths[key] = {"solve_s": statistics.median(ts) / 1e3, "sweeps": inf["sweeps"],
                       "max_rank": inf["max_rank"], "local_iters": inf["local_iters"],
                       "residual": inf["residual"], "converged": inf["converged"]}
+        solutions[key] = tuple(t.cpu().numpy().copy() for t in (state["y"], state["u"],
+                                                                  state["lam"]))
     # restore the headline solution in y, u, lam
     iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, state["y"], state["u"], state["lam"],
                            tol=args.tol, precision=prec)
@@ -389,14 +505,15 @@ def run_gpu(args, world, rank, local):
         arith = CANDIDATES.get(args.roofline_kernel, "fp64")
         if arith == "prec":
             arith = "fp64" if args.precision == "fp64" else "fp32"
-        alu_peak = FP64_FMA_TFLOPS if arith == "fp64" else FP32_FMA_TFLOPS
+        alu_peak = alu_peak_tflops(arith, pk)
         t_alu = fl / (alu_peak * 1e12)
         t_hbm = by / (pk["hbm_gbs"] * 1e9)
         if t_alu >= t_hbm:
             achieved = fl / (avg_ms * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak,
-                    "peak_kind": f"measured {arith.upper()} FMA rate (CUDA cores)"}
+                    "peak_kind": f"{arith.upper()} FMA rate from unit counts and the maximum "
+                                 f"SM clock (CUDA cores)"}
         else:
             achieved = by / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -409,7 +526,8 @@ def run_gpu(args, world, rank, local):
     # the Kronecker apply (KKT residuals) against the FP64 rate: the metric's
     # second part, from the same untimed per-kernel step
     kron_roof = alu_roofline("kron_rank1_kernel", per_kernel.get("kron_rank1_kernel"),
-                             FP64_FMA_TFLOPS, "measured FP64 FMA rate (CUDA cores)")
+                             alu_peak_tflops("fp64", pk),
+                             "FP64 FMA rate from unit counts and the maximum SM clock")
 
     line = {
         "metric": METRIC,
@@ -440,29 +558,51 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": int(launches / max(1, args.steps)),
         "roofline": roof,
         "kron_roofline": kron_roof,
+        "ttm_roofline": ttm_roofline(ctx, iga, torch, pk, pk_kind),
+        "rank_tables": rank_tables(ctx),
+        "storage": {work.name: report.storage(ctx, work.geometry, work.space, work.target,
+                                              work.tol)},
+        "alu_rates_measured_tflops": {"fp64": iga.iga_measure_fma(ctx, iga.IGA_FP64),
+                                      "fp32": iga.iga_measure_fma(ctx, iga.IGA_FP32)},
         "clocks": clocks,
     }
-    return line, work
+    return line, work, solutions
+
+
+def oracle_baseline(work, steps):
+    """cpu_baseline: the oracle leg's set-up plus `steps` timed steps."""
+    leg = OracleLeg(work)
+    vals, parts = [], None
+    for _ in range(max(1, steps)):
+        v, parts = leg.step()
+        vals.append(v)
+    return leg, {"value": statistics.median(vals), "unit": "s", "cores": _threads(),
+                 "kind": "oracle", "sample": leg.describe(),
+                 "parts_s": {k: round(v, 3) for k, v in parts.items()},
+                 "setup_s": round(leg.setup_s, 2)}
 
 
 def run_reference(args):
-    """The oracle timed as it stands on a bounded sample (no GPU)."""
+    """The oracle timed as it stands on the host cores (no GPU): the set-up,
+    W untimed and K timed steps of the bounded sample (OracleLeg)."""
     from paper_1811_06797_gb300 import workloads as wl
     work = wl.config(args.config)
-    vals = []
-    base = None
+    leg = OracleLeg(work)
     for _ in range(args.warmup):
-        pass
-    for _ in range(max(1, min(args.steps, 2))):
-        base = cpu_oracle_sample(work, args.cpu_seconds)
-        vals.append(base["value"])
+        leg.step()
+    vals, parts = [], None
+    for _ in range(args.steps):
+        v, parts = leg.step()
+        vals.append(v)
     v = statistics.median(vals)
     return {
-        "metric": METRIC, "value": v, "unit": "s", "n_gpus": 1, "steps": len(vals),
+        "metric": METRIC, "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": work.name}, "impl": "reference",
-        "cpu_baseline": {k: base[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s"},
+        "cpu_baseline": {"kind": "oracle", "cores": _threads(), "sample": leg.describe(),
+                         "value": v, "unit": "s",
+                         "parts_s": {k: round(x, 3) for k, x in parts.items()}},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -474,11 +614,14 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)))
         return
-    line, work = run_gpu(args, world, rank, local)
+    line, work, solutions = run_gpu(args, world, rank, local)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             try:
-                line["cpu_baseline"] = cpu_oracle_sample(work, args.cpu_seconds)
+                leg, base = oracle_baseline(work, 2)
+                line["cpu_baseline"] = base
+                # the error of every result against the oracle's solution
+                line["oracle_errors"] = {k: field_errors(v, leg.full) for k, v in solutions.items()}
             except Exception as e:   # the baseline is reported, not required
                 line["cpu_baseline"] = {"value": None, "unit": "s", "kind": "oracle",
                                         "cores": os.cpu_count(), "sample": f"failed: {e}"}

@@ -67,7 +67,14 @@ def interior_operators(space, geometry, target, tol, samples=None):
     diagonal stiffness terms, from the oracle's low-rank route (`samples`: an
     earlier assemble.sample_weights output of this grid, or None)."""
     disc = Discretisation(space.degree, space.knots, space.nquad)
-    tts = weight_tts(geometry, disc, tol, target, samples=samples)
+    return operators_from_tts(space, weight_tts(geometry, disc, tol, target, samples=samples))
+
+
+def operators_from_tts(space, tts):
+    """The univariate step alone: interior Kronecker terms of M and K, the
+    interior load and the diagonal stiffness terms from weight TT cores
+    (lowrank.weight_tts output)."""
+    disc = Discretisation(space.degree, space.knots, space.nquad)
     Mt = restrict_interior(lowrank_operator(disc, tts["omega"], "M"))
     kl = {}
     for k in range(3):

@@ -85,8 +85,11 @@ def test_reference_arm_line():
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    # the small unit-cube workload keeps this CPU test short; the default
+    # workload goes through the same code
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                          "--config", "1", "--steps", "2", "--warmup", "3"],
+                         capture_output=True, text=True,
                          check=True, timeout=300, cwd=root)
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference"
@@ -95,7 +98,7 @@ def test_reference_arm_line():
                 "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["higher_is_better"] is False and line["value"] > 0
-    assert line["config"]["workload"] == "quarter_annulus_p3_e64"
+    assert line["config"]["workload"] == "unit_cube_p2_e16" and line["steps"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
