@@ -22,6 +22,11 @@ blocking or fusion beyond the definition):
                fast-diagonalisation solve on the unit cube
   amen      -- frame matrix (Sec. 5 eq. frame), projected local KKT
                operator (Sec. 5 eq. KKT_red) and its interface form
+  interp    -- the weights interpolated in a spline space of degree 2p+1 by
+               per-direction collocation (Sec. 3 eqs. weightEquationSystem /
+               weightEquationSolve), mapped to the Gauss points
+  solve     -- the KKT solve at sizes beyond the direct solve: low-rank
+               operators and CG on the reduced system
 
 Parity status per function is stated in each module header; every function
 listed above is pinned by a ``-m "not gpu"`` test against a closed form,

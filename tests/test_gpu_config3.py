@@ -64,12 +64,19 @@ def test_config3_operators_and_load_at_sampled_rows(setup):
             assert np.linalg.norm(got - want) < 1e-7 * np.linalg.norm(want)
 
 
-@pytest.mark.parametrize("beta", [1e-2, 1e-4, 1e-6])
-def test_config3_kkt_solve(setup, beta):
+@pytest.mark.parametrize("beta,prec", [(1e-2, 0), (1e-4, 0), (1e-6, 0), (1e-4, 2), (1e-6, 2)],
+                         ids=["1e-2", "1e-4", "1e-6", "1e-4-tf32", "1e-6-tf32"])
+def test_config3_kkt_solve(setup, beta, prec):
+    """FP64 solves, and solves whose large local interface products run on the
+    tensor cores in TF32 (IGA_TF32) inside the FP64 refinement."""
     ctx, torch, iga, work, M, K, load = setup
     N = int(np.prod(M.info()["n"]))
     y, u, lam = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
-    info = iga.iga_kkt_solve_amen(ctx, M, K, load, beta, y, u, lam, tol=1e-6)
+    if prec == 2:
+        ctx.profile_begin("tc_gemm_tf32_kernel")
+    info = iga.iga_kkt_solve_amen(ctx, M, K, load, beta, y, u, lam, tol=1e-6, precision=prec)
+    if prec == 2:
+        assert ctx.profile_end()["launches"] > 0          # the tensor-core products ran
     assert info["converged"], info
     # independent residual check with the (row-verified) operator apply
     z = torch.cat([y, u, lam])

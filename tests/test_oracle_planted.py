@@ -221,3 +221,20 @@ def test_wrong_schur_operator_fails_the_reduced_solve_pin(monkeypatch, mistake):
 def oassemble_geo():
     from paper_1811_06797_gb300 import workloads as wl
     return wl.quarter_annulus()
+
+
+def test_interpolation_without_the_collocation_solve_fails_its_pin(monkeypatch):
+    # node values taken as the spline coefficients (no solve with Bt, eq.
+    # weightEquationSolve): exact only up to degree 1, so the quadratic
+    # |det J| of the cubic stretch is no longer reproduced
+    import oracle.interp as ointerp
+    import test_oracle_interp as pins_interp
+    from oracle.bspline import basis_all as ba
+
+    def wrong(knots, pt, xg):
+        kt = ointerp.interp_knots(knots, pt)
+        E, _ = ba(kt, pt, xg, nderiv=0)
+        return E
+    monkeypatch.setattr(ointerp, "node_to_gauss", wrong)
+    with pytest.raises(AssertionError):
+        pins_interp.test_polynomial_weights_are_reproduced_exactly("cubic")
