@@ -333,6 +333,31 @@ def ttm_roofline(ctx, iga, torch, pk, pk_kind, reps=5):
     return out
 
 
+def config5_assembly(ctx, iga, torch):
+    """The random-volume workload (degree 2, 512 elements per direction, TT
+    tolerance 1e-8) assembled through the paper's weight interpolation: wall
+    time of iga_lowrank_assemble_interp (the weights at the 517^3 Greville
+    nodes of the degree-5 interpolation space, TT-SVD, collocation solves,
+    univariate assembly) and the ranks and bytes of the operators."""
+    from paper_1811_06797_gb300 import workloads as wl
+    work = wl.config(5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    M, K, load = iga.iga_lowrank_assemble_interp(ctx, work.geometry, work.space, work.target,
+                                                 work.tol)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out = {"workload": work.name, "route": "weights interpolated in degree 5 (Sec. 3)",
+           "seconds": t}
+    for name, op in (("M", M), ("K", K)):
+        inf = op.info()
+        out[name] = {"blocks": inf["nblocks"], "R_sum": list(inf["R"]), "bytes": inf["bytes"],
+                     "block_ranks": [list(op.block_ranks(k)) for k in range(inf["nblocks"])]}
+    del M, K, load
+    torch.cuda.empty_cache()
+    return out
+
+
 def rank_tables(ctx):
     """TT ranks of the seven sampled weights at the tolerances of the paper's
     rank tables (Sec. 6) on the two curved synthetic geometries, degree 2,
@@ -560,6 +585,7 @@ def run_gpu(args, world, rank, local):
         "kron_roofline": kron_roof,
         "ttm_roofline": ttm_roofline(ctx, iga, torch, pk, pk_kind),
         "rank_tables": rank_tables(ctx),
+        "config5_assembly": config5_assembly(ctx, iga, torch),
         "storage": {work.name: report.storage(ctx, work.geometry, work.space, work.target,
                                               work.tol)},
         "alu_rates_measured_tflops": {"fp64": iga.iga_measure_fma(ctx, iga.IGA_FP64),

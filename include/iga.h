@@ -42,7 +42,7 @@ typedef enum {
   IGA_OK = 0,
   IGA_EINVAL = 1,      /* invalid argument (sizes, knots, null pointers) */
   IGA_ENOMEM = 2,      /* device or host allocation failed */
-  IGA_ECUDA = 3,       /* CUDA runtime / cuBLAS error */
+  IGA_ECUDA = 3,       /* CUDA runtime error */
   IGA_ENOCONV = 4,     /* iteration limit reached before the tolerance */
   IGA_ENONFINITE = 5,  /* NaN or Inf detected in a reduction */
   IGA_ETIMEOUT = 6     /* a bounded device wait gave up */
@@ -186,6 +186,27 @@ iga_status iga_assemble_bands(iga_ctx* ctx, const iga_space* space, int d, const
 iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
                                 const iga_target* target, double tol, iga_op** M, iga_op** K,
                                 iga_tt** load);
+
+/* The same assembly with the paper's weight interpolation (Sec. 3, eqs.
+ * weightEquationSystem and weightEquationSolve) in place of sampling on the
+ * Gauss grid: each weight is interpolated in the tensor spline space of
+ * degree `degree` (0: 2p + 1, p the largest degree of `space`) on the break
+ * points of `space`, from its values at the Greville abscissae of that space
+ * ((E + degree)^3 points instead of (E nquad)^3); the node values are
+ * compressed by TT-SVD at tol, every core is mapped by the per-direction
+ * collocation solve and the evaluation of the interpolant at the Gauss points
+ * (times the Gauss weights), and the univariate assembly proceeds as above.
+ * The operators then carry the interpolation error of the weights (of order
+ * h^(degree+1) for a smooth map) besides the truncation. */
+iga_status iga_lowrank_assemble_interp(iga_ctx* ctx, const iga_geometry* geo,
+                                       const iga_space* space, const iga_target* target,
+                                       double tol, int degree, iga_op** M, iga_op** K,
+                                       iga_tt** load);
+/* The eight weight TTs of that route at the Gauss points (the layout of
+ * iga_weight_tts). */
+iga_status iga_weight_tts_interp(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                                 const iga_target* target, double tol, int degree,
+                                 iga_tt* out[8]);
 
 /* The eight sampled weights of the composite assembly as TT tensors on the
  * Gauss grid (Sec. 3: omega g, q11 g, q12 g, q13 g, q22 g, q23 g, q33 g and
@@ -363,7 +384,10 @@ typedef struct {
   int rmax;            /* TT rank cap */
   int local_maxit;     /* Krylov iterations per local system */
   int refine_max;      /* outer FP64 refinement steps */
-  int precision;       /* IGA_FP64 or IGA_FP32 for the AMEn contractions */
+  int precision;       /* arithmetic of the AMEn local systems: IGA_FP64,
+                          IGA_FP32, or IGA_TF32 (FP32 with the large
+                          interface products on the tensor cores, TF32
+                          operands and FP32 accumulation) */
   int verbose;         /* print one line per sweep to stderr */
   double trunc_tol;    /* relative truncation of each field in the block core
                           when the block index moves (0: tol / 1000, lowered

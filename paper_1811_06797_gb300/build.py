@@ -1,7 +1,8 @@
 """Build libiga.so in-tree with nvcc for sm_103a.
 
 Every translation unit under csrc/ is compiled in parallel into _build/ and
-linked into paper_1811_06797_gb300/libiga.so together with cuBLAS.  The
+linked into paper_1811_06797_gb300/libiga.so (CUDA runtime only; the library
+calls no BLAS).  The
 build is skipped when the library is newer than every source and header.
 """
 from __future__ import annotations
@@ -65,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -31,18 +31,14 @@ static inline unsigned nb(size_t n, int th = 256) { return (unsigned)((n + th - 
 // row-major C (M x N) = op(A) op(B) (+ beta C)
 static void rgemm(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const double* A, int lda,
                   const double* B, int ldb, double* C, int ldc, double beta = 0.0) {
-  const double one = 1.0;
-  IGA_BLAS(cublasDgemm(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N, tA ? CUBLAS_OP_T : CUBLAS_OP_N,
-                       N, M, K, &one, B, ldb, A, lda, &beta, C, ldc));
+  gemm_rm_batched<double>(ctx, tA, tB, M, N, K, 1.0, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);
 }
 
 static void rgemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const double* A,
                           int lda, long long sA, const double* B, int ldb, long long sB, double* C,
                           int ldc, long long sC, int batch) {
-  const double one = 1.0, zero = 0.0;
-  IGA_BLAS(cublasDgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,
-                                     tA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &one, B, ldb, sB, A,
-                                     lda, sA, &zero, C, ldc, sC, batch));
+  gemm_rm_batched<double>(ctx, tA, tB, M, N, K, 1.0, A, lda, sA, B, ldb, sB, 0.0, C, ldc, sC,
+                          batch);
 }
 
 __global__ void band_to_dense_kernel(const double* __restrict__ band, int n, int p, double sign,
@@ -291,9 +287,7 @@ struct FDPrecond {
 };
 
 static double dot(iga_ctx* ctx, const double* a, const double* b, size_t n) {
-  double r = 0.0;
-  IGA_BLAS(cublasDdot(ctx->blas, (int)n, a, 1, b, 1, &r));
-  return r;
+  return device_dot(ctx, a, b, n);
 }
 
 // preconditioned CG for A x = b (A = M or K, SPD); x holds the initial guess
@@ -304,7 +298,6 @@ static int pcg(iga_ctx* ctx, const iga_op* A, FDPrecond& P, bool stiffness, cons
   double* z = scratch<double>(ctx, SLOT_AMEN_BASE + 121, N);
   double* pv = scratch<double>(ctx, SLOT_AMEN_BASE + 122, N);
   double* q = scratch<double>(ctx, SLOT_AMEN_BASE + 123, N);
-  IGA_BLAS(cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST));
   double bn = std::sqrt(dot(ctx, b, b, N));
   if (bn == 0.0) {
     IGA_CUDA(cudaMemsetAsync(x, 0, N * 8, ctx->stream));
@@ -349,7 +342,6 @@ using namespace iga;
     __VA_ARGS__;                                                                  \
     return IGA_OK;                                                                \
   } catch (const ::iga::Error& e) {                                               \
-    cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST);                    \
     set_error(ctx, e.what());                                                     \
     return e.status;                                                              \
   } catch (const std::exception& e) {                                             \
@@ -366,7 +358,6 @@ iga_status iga_spd_solve(iga_ctx* ctx, const iga_op* A, const iga_op* M, const i
   IGA_TRY2(ctx, {
     IGA_REQUIRE(A && M && b && x && (A == M || A == K), "spd_solve: A must be M or K");
     IGA_REQUIRE(tol > 0.0 && maxit > 0, "spd_solve: bad tolerance or iteration limit");
-    IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
     FDPrecond P;
     P.setup(ctx, M, K);
     double rr = 0.0;
@@ -386,7 +377,6 @@ iga_status iga_reduced_gradient(iga_ctx* ctx, const iga_op* M, const iga_op* K,
                 "reduced_gradient: null argument");
     IGA_REQUIRE(tol > 0.0, "reduced_gradient: tolerance must be positive");
     for (int d = 0; d < 3; ++d) IGA_REQUIRE(M->n[d] == K->n[d], "reduced_gradient: M, K mismatch");
-    IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
     size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
     double* bvec = scratch<double>(ctx, SLOT_AMEN_BASE + 130, N);
     double* Mu = scratch<double>(ctx, SLOT_AMEN_BASE + 131, N);

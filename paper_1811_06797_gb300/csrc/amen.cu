@@ -847,53 +847,27 @@ static inline unsigned nblk(size_t n, int th = 256) { return (unsigned)((n + th 
 static void rm_gemm(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const double* A, int lda,
                     const double* B, int ldb, double* C, int ldc, double alpha = 1.0,
                     double beta = 0.0) {
-  if (M == 0 || N == 0) return;
-  IGA_BLAS(cublasDgemm(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N, tA ? CUBLAS_OP_T : CUBLAS_OP_N,
-                       N, M, K, &alpha, B, ldb, A, lda, &beta, C, ldc));
+  gemm_rm_batched<double>(ctx, tA, tB, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);
 }
 
-// strided batch of row-major products in FP64 (DGEMM) or FP32 (SGEMM, no
-// TF32): C_i = alpha op(A_i) op(B_i) + beta C_i; runs in host pointer mode
-// whatever mode the caller has set
+// strided batch of row-major products in FP64 or FP32:
+// C_i = alpha op(A_i) op(B_i) + beta C_i
 template <typename U>
 static void rm_gemm_strided(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const U* A,
                             int lda, long long sA, const U* B, int ldb, long long sB, U* C,
                             int ldc, long long sC, int count, U alpha, U beta) {
-  if (M == 0 || N == 0 || count == 0) return;
-  cublasPointerMode_t pm;
-  IGA_BLAS(cublasGetPointerMode(ctx->blas, &pm));
-  if (pm != CUBLAS_POINTER_MODE_HOST) IGA_BLAS(cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST));
-  cublasStatus_t st;
-  if constexpr (sizeof(U) == 8)
-    st = cublasDgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,
-                                   tA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, B, ldb, sB, A,
-                                   lda, sA, &beta, C, ldc, sC, count);
-  else
-    st = cublasSgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,
-                                   tA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, B, ldb, sB, A,
-                                   lda, sA, &beta, C, ldc, sC, count);
-  if (pm != CUBLAS_POINTER_MODE_HOST) IGA_BLAS(cublasSetPointerMode(ctx->blas, pm));
-  IGA_BLAS(st);
+  gemm_rm_batched<U>(ctx, tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, count);
 }
 
 // count products C_i = alpha op(A_i) op(B_i) + beta C_i of row-major matrices
-// with A_i = A + i sA (likewise B, C): one batched cuBLAS call
+// with A_i = A + i sA (likewise B, C); long reductions with a small output
+// are split over K inside gemm_rm_batched
 static void rm_gemm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, const double* A,
                             int lda, long long sA, const double* B, int ldb, long long sB,
                             double* C, int ldc, long long sC, int count, double alpha = 1.0,
                             double beta = 0.0) {
-  if (M == 0 || N == 0 || count == 0) return;
-  // the library splits a long inner dimension over CTAs only for single
-  // GEMMs: long reductions with a small output run as a loop
-  if (count == 1 || (long long)K > 4LL * std::max(M, N)) {
-    for (int i = 0; i < count; ++i)
-      rm_gemm(ctx, tA, tB, M, N, K, A + i * sA, lda, B + i * sB, ldb, C + i * sC, ldc, alpha,
-              beta);
-    return;
-  }
-  IGA_BLAS(cublasDgemmStridedBatched(ctx->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N,
-                                     tA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, B, ldb, sB,
-                                     A, lda, sA, &beta, C, ldc, sC, count));
+  gemm_rm_batched<double>(ctx, tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                          count);
 }
 
 // ---- projections of full vectors onto the TT frames (long reductions)
@@ -1179,6 +1153,7 @@ struct Solver {
   double inner_tol;
   double trunc_tol;
   bool svd_moves = false;        // Gram eigen-decomposition instead of pivoted Cholesky
+  bool tc_local = false;         // FP32 solve: large interface products on the tensor cores (TF32)
   CoreNZ nz[2][3];
   DevBuf<double> X[3];                 // TT cores (FP64 master)
   DevBuf<double> Xh;                   // block core (3, r_d, n_d, r_{d+1})
@@ -1513,6 +1488,15 @@ struct Solver {
                  transR, t);
       return;
     }
+    if constexpr (sizeof(U) == 4) {
+      if (tc_local) {
+        // t_s (rows (v, a, i), r1) = x (rows, r1) op(R_s): K-major x, one product per s
+        for (int q = 0; q < S; ++q)
+          tc_gemm_tf32(ctx, false, !transR, false, nv * r0 * nn, r1, r1, 1.f, x, r1, 0,
+                       R + (size_t)q * r1 * r1, r1, 0, 0.f, t + (size_t)q * per, r1, 0, 1);
+        return;
+      }
+    }
     rm_gemm_strided<U>(ctx, false, !transR, nv * r0 * nn, r1, r1, x, r1, 0, R, r1,
                        (long long)r1 * r1, t, r1, (long long)per, S, U(1), U(0));
   }
@@ -1525,6 +1509,16 @@ struct Solver {
     }
     const int nr = nn * r1;
     for (int q = 0; q < S; ++q) {
+      if constexpr (sizeof(U) == 4) {
+        if (tc_local) {
+          // y_v^T (nr x r0) += t_{q,v}^T op(L_q)^T: the long dimension nr as the
+          // MMA rows, t and y read and written transposed
+          tc_gemm_tf32(ctx, true, transL == 0, true, nr, r0, r0, 1.f, t + (size_t)q * per, nr,
+                       (long long)r0 * nr, L + (size_t)q * r0 * r0, r0, 0, q ? 1.f : 0.f, y, nr,
+                       (long long)r0 * nr, nv);
+          continue;
+        }
+      }
       rm_gemm_strided<U>(ctx, transL != 0, false, r0, nr, r0, L + (size_t)q * r0 * r0, r0, 0,
                          t + (size_t)q * per, nr, (long long)r0 * nr, y, nr, (long long)r0 * nr,
                          nv, U(1), q ? U(1) : U(0));
@@ -1750,20 +1744,6 @@ struct Solver {
     T* Zb = tslot(26, Lv * m);
     T* w = tslot(27, Lv);
     T* hd = tslot(28, 3 * (m + 2));
-    T* cst = tslot(29, 8);
-    T hc[4] = {T(1), T(0), T(-1), T(0)};
-    IGA_CUDA(cudaMemcpyAsync(cst, hc, sizeof(hc), cudaMemcpyHostToDevice, ctx->stream));
-    const T* one = cst;
-    const T* zero = cst + 1;
-    const T* mone = cst + 2;
-    IGA_BLAS(cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_DEVICE));
-    auto gemv = [&](cublasOperation_t t, int rows, int cols, const T* al, const T* A, const T* xx,
-                    const T* be, T* yy) {
-      if constexpr (sizeof(T) == 8)
-        IGA_BLAS(cublasDgemv(ctx->blas, t, rows, cols, al, A, rows, xx, 1, be, yy, 1));
-      else
-        IGA_BLAS(cublasSgemv(ctx->blas, t, rows, cols, al, A, rows, xx, 1, be, yy, 1));
-    };
     // squared norms in FP64, one kernel each
     double* nd = scratch<double>(ctx, SLOT_AMEN_BASE + 19, 2);
     const unsigned nsb = std::min<unsigned>(nblk(Lv), 152 * 4);
@@ -1779,12 +1759,7 @@ struct Solver {
       while (!done && it < maxit) {
         // r = b - A x
         local_op(c, x, w);
-        if constexpr (sizeof(T) == 8)
-          IGA_BLAS(cublasDgeam(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)Lv, 1, one, b, (int)Lv,
-                               mone, w, (int)Lv, Vb, (int)Lv));
-        else
-          IGA_BLAS(cublasSgeam(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)Lv, 1, one, b, (int)Lv,
-                               mone, w, (int)Lv, Vb, (int)Lv));
+        vec_sub<T>(ctx, Lv, b, w, Vb);
         sumsq(Vb, nd);
         double b2 = 0.0;
         IGA_CUDA(cudaMemcpyAsync(&b2, nd, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1847,14 +1822,12 @@ struct Solver {
         std::vector<T> yt(kk);
         for (int i = 0; i < kk; ++i) yt[i] = (T)y[i];
         IGA_CUDA(cudaMemcpyAsync(hd, yt.data(), kk * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
-        if (kk > 0) gemv(CUBLAS_OP_N, (int)Lv, kk, one, Zb, hd, one, x);
+        if (kk > 0) gemv_cm_add<T>(ctx, (int)Lv, kk, Zb, hd, x);
         IGA_CUDA(cudaStreamSynchronize(ctx->stream));
       }
     } catch (...) {
-      cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST);
       throw;
     }
-    IGA_BLAS(cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST));
     return it;
   }
 
@@ -1974,6 +1947,7 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   // the solution, so truncate well below the residual target
   S.trunc_tol = o->trunc_tol > 0.0 ? o->trunc_tol : 1e-3 * tol;
   S.svd_moves = o->truncation == IGA_TRUNC_SVD;
+  S.tc_local = o->precision == IGA_TF32;
   S.verbose = o->verbose;
   size_t N = S.N;
   for (int op = 0; op < 2; ++op)
@@ -2101,9 +2075,8 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     IGA_REQUIRE(o.tol > 0.0 && o.inner_tol >= 0.0, "kkt_solve_amen: bad tolerances");
     IGA_REQUIRE(o.truncation == IGA_TRUNC_PIVOTED || o.truncation == IGA_TRUNC_SVD,
                 "kkt_solve_amen: unknown truncation");
-    IGA_REQUIRE(o.precision == IGA_FP64 || o.precision == IGA_FP32,
-                "kkt_solve_amen: precision must be IGA_FP64 or IGA_FP32");
-    IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
+    IGA_REQUIRE(o.precision == IGA_FP64 || o.precision == IGA_FP32 || o.precision == IGA_TF32,
+                "kkt_solve_amen: precision must be IGA_FP64, IGA_FP32 or IGA_TF32");
     size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
     // rhs F = [b; 0; 0] (full FP64); z = 0
     double* F = scratch<double>(ctx, SLOT_AMEN_BASE - 4, 3 * N);
@@ -2172,11 +2145,9 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     }
     return IGA_OK;
   } catch (const Error& e) {
-    cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST);
     set_error(ctx, e.what());
     return e.status;
   } catch (const std::exception& e) {
-    cublasSetPointerMode(ctx->blas, CUBLAS_POINTER_MODE_HOST);
     set_error(ctx, e.what());
     return IGA_ECUDA;
   }

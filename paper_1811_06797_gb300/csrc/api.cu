@@ -5,6 +5,7 @@
 // assemble one banded univariate matrix per TT core slice (eqs.
 // massMatrix1D, stiffnessFinal), so that M = sum (x)_d M_d and
 // K = sum_{k,l} sum (x)_d K_kl^(d) with the core slices of eq. TTranks.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,25 +36,28 @@ void tc_flag_check(iga_ctx* ctx, const char* what) {
 }
 
 void func_attr(const void* fn, cudaFuncAttribute attr, int value) {
+  // one value per (function, attribute, device), raised monotonically: a
+  // launch needs at least the value it asks for, so a later request for a
+  // smaller value keeps the larger one that is already set
   struct Key {
     const void* fn;
-    int attr, value, dev;
+    int attr, dev;
     bool operator<(const Key& o) const {
       if (fn != o.fn) return fn < o.fn;
       if (attr != o.attr) return attr < o.attr;
-      if (value != o.value) return value < o.value;
       return dev < o.dev;
     }
   };
   static std::mutex mu;
-  static std::map<Key, bool> done;
+  static std::map<Key, int> cur;
   int dev = 0;
   IGA_CUDA(cudaGetDevice(&dev));
-  Key k{fn, (int)attr, value, dev};
+  Key k{fn, (int)attr, dev};
   std::lock_guard<std::mutex> lk(mu);
-  if (done.count(k)) return;
+  auto it = cur.find(k);
+  if (it != cur.end() && it->second >= value) return;
   IGA_CUDA(cudaFuncSetAttribute(fn, attr, value));
-  done[k] = true;
+  cur[k] = value;
 }
 
 void prof_start(iga_ctx* ctx) {
@@ -438,12 +442,21 @@ AllocScope::~AllocScope() {
 void* dev_alloc(size_t bytes, bool* pooled) {
   void* p = nullptr;
   cudaMemPool_t pool = t_alloc_active ? device_pool() : nullptr;
+  cudaError_t e;
   if (pool) {
-    IGA_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool, t_alloc_stream));
+    e = cudaMallocFromPoolAsync(&p, bytes, pool, t_alloc_stream);
     *pooled = true;
   } else {
-    IGA_CUDA(cudaMalloc(&p, bytes));
+    e = cudaMalloc(&p, bytes);
     *pooled = false;
+  }
+  if (e != cudaSuccess) {
+    // a refused allocation is not a sticky error: clear the thread's last
+    // error so that the next launch check does not report it again
+    (void)cudaGetLastError();
+    throw Error(e == cudaErrorMemoryAllocation ? IGA_ENOMEM : IGA_ECUDA,
+                std::string("device allocation of ") + std::to_string(bytes) +
+                    " bytes failed: " + cudaGetErrorString(e));
   }
   return p;
 }
@@ -492,8 +505,6 @@ iga_status iga_create(iga_ctx** out, void* stream) {
     ctx->stream = static_cast<cudaStream_t>(stream);
     IGA_CUDA(cudaGetDevice(&ctx->device));
     IGA_CUDA(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-    IGA_BLAS(cublasCreate(&ctx->blas));
-    IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
     IGA_CUDA(cudaMalloc((void**)&ctx->dflag, 64 * sizeof(int)));
     IGA_CUDA(cudaMallocHost((void**)&ctx->hflag, 64 * sizeof(int)));
     IGA_CUDA(cudaMemset(ctx->dflag, 0, 64 * sizeof(int)));
@@ -513,7 +524,6 @@ void iga_destroy(iga_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   ctx->scratch.clear();
-  if (ctx->blas) cublasDestroy(ctx->blas);
   if (ctx->dflag) cudaFree(ctx->dflag);
   if (ctx->hflag) cudaFreeHost(ctx->hflag);
   delete ctx;
@@ -755,39 +765,73 @@ iga_status iga_load_from_density(iga_ctx* ctx, const iga_space* space, const iga
   })
 }
 
+// the composite assembly with the weights sampled on the Gauss grid (pt = 0)
+// or interpolated in the spline space of degree pt (pt > 0)
+static void lowrank_assemble_impl(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                                  const iga_target* target, double tol, int pt, iga_op** M,
+                                  iga_op** K, iga_tt** load) {
+  IGA_REQUIRE(M && K, "lowrank_assemble: null output");
+  IGA_REQUIRE(tol >= 0.0, "lowrank_assemble: negative tolerance");
+  *M = nullptr;
+  *K = nullptr;
+  if (load) *load = nullptr;
+  SpaceTables st;
+  build_space_tables(ctx, space, st);
+  iga_tt* tts[8] = {nullptr};
+  struct Guard {
+    iga_tt** t;
+    ~Guard() { for (int i = 0; i < 8; ++i) delete t[i]; }
+  } guard{tts};
+  if (pt > 0) weight_tts_interp_impl(ctx, geo, st, target, tol, pt, tts);
+  else weight_tts_impl(ctx, geo, st, target, tol, tts);
+  IGA_REQUIRE(tts[0] != nullptr, "lowrank_assemble: omega is zero");
+  const iga_tt* w[7] = {tts[0], tts[1], tts[2], tts[3], tts[4], tts[5], tts[6]};
+  ops_from_weights_impl(ctx, st, w, M, K);
+  if (load && tts[7]) {
+    try {
+      *load = load_tt(ctx, st, tts[7]);
+    } catch (...) {
+      delete *M;
+      delete *K;
+      *M = nullptr;
+      *K = nullptr;
+      throw;
+    }
+  }
+  IGA_CUDA(cudaStreamSynchronize(ctx->stream));   // the handles are usable on any stream
+}
+
+static int interp_degree(const iga_space* space, int degree) {
+  IGA_REQUIRE(space != nullptr, "null space");
+  int p = std::max({space->degree[0], space->degree[1], space->degree[2]});
+  return degree > 0 ? degree : 2 * p + 1;
+}
+
 iga_status iga_lowrank_assemble(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
                                 const iga_target* target, double tol, iga_op** M, iga_op** K,
                                 iga_tt** load) {
   if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, lowrank_assemble_impl(ctx, geo, space, target, tol, 0, M, K, load))
+}
+
+iga_status iga_lowrank_assemble_interp(iga_ctx* ctx, const iga_geometry* geo,
+                                       const iga_space* space, const iga_target* target,
+                                       double tol, int degree, iga_op** M, iga_op** K,
+                                       iga_tt** load) {
+  if (!ctx) return IGA_EINVAL;
+  IGA_TRY(ctx, lowrank_assemble_impl(ctx, geo, space, target, tol, interp_degree(space, degree),
+                                     M, K, load))
+}
+
+iga_status iga_weight_tts_interp(iga_ctx* ctx, const iga_geometry* geo, const iga_space* space,
+                                 const iga_target* target, double tol, int degree,
+                                 iga_tt* out[8]) {
+  if (!ctx || !out) return IGA_EINVAL;
+  for (int c = 0; c < 8; ++c) out[c] = nullptr;
   IGA_TRY(ctx, {
-    IGA_REQUIRE(M && K, "lowrank_assemble: null output");
-    IGA_REQUIRE(tol >= 0.0, "lowrank_assemble: negative tolerance");
-    *M = nullptr;
-    *K = nullptr;
-    if (load) *load = nullptr;
     SpaceTables st;
     build_space_tables(ctx, space, st);
-    iga_tt* tts[8] = {nullptr};
-    struct Guard {
-      iga_tt** t;
-      ~Guard() { for (int i = 0; i < 8; ++i) delete t[i]; }
-    } guard{tts};
-    weight_tts_impl(ctx, geo, st, target, tol, tts);
-    IGA_REQUIRE(tts[0] != nullptr, "lowrank_assemble: omega is zero");
-    const iga_tt* w[7] = {tts[0], tts[1], tts[2], tts[3], tts[4], tts[5], tts[6]};
-    ops_from_weights_impl(ctx, st, w, M, K);
-    if (load && tts[7]) {
-      try {
-        *load = load_tt(ctx, st, tts[7]);
-      } catch (...) {
-        delete *M;
-        delete *K;
-        *M = nullptr;
-        *K = nullptr;
-        throw;
-      }
-    }
-    IGA_CUDA(cudaStreamSynchronize(ctx->stream));   // the handles are usable on any stream
+    weight_tts_interp_impl(ctx, geo, st, target, tol, interp_degree(space, degree), out);
   })
 }
 

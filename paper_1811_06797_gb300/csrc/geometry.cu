@@ -284,19 +284,15 @@ __global__ void geo_stage2_kernel(GeoDev G, const double* __restrict__ H3, doubl
   for (int k = 0; k < 12; ++k) o[k] = acc[k];
 }
 
-// One thread per tensor Gauss point: homogeneous map and derivatives from the
-// partial sums, quotient rule for the rational map, optional twist, then
-// omega, Q and the load density, all times g1 g2 g3.
-__global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* __restrict__ flag) {
-  size_t Q12 = (size_t)G.Q[1] * G.Q[2];
-  size_t total = (size_t)G.Q[0] * Q12;
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // lanes past the end evaluate point 0 and write nothing, so every warp stays
-  // converged for the reduction below
-  const bool valid = t < total;
-  if (!valid) t = 0;
-  int i1 = (int)(t / Q12);
-  size_t rem = t - (size_t)i1 * Q12;
+// The eight weights of one tensor Gauss point (i1, i2, i3): homogeneous map
+// and derivatives from the partial sums, quotient rule for the rational map,
+// optional twist, then omega, Q and the load density, all times g1 g2 g3.
+// Returns the orientation code of the point: 1 det < 0, 2 det > 0, 4 det zero
+// or not finite.
+__device__ __forceinline__ int point_weights(const GeoDev& G, int i1, int i2, int i3,
+                                             double v[8]) {
+  const size_t rem = (size_t)i2 * G.Q[2] + i3;
+  const size_t Q12 = (size_t)G.Q[1] * G.Q[2];
   const int p1 = G.pg[0];
   const double* V1 = G.V[0] + (size_t)i1 * (p1 + 1);
   const double* D1 = G.D[0] + (size_t)i1 * (p1 + 1);
@@ -313,8 +309,6 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
       dA[2][m] += v1 * h2;
     }
   }
-  int i2 = (int)(rem / G.Q[2]);
-  int i3 = (int)(rem - (size_t)i2 * G.Q[2]);
   double iw = 1.0 / A[3];
   double X[3] = {A[0] * iw, A[1] * iw, A[2] * iw};
   double J[3][3];                                    // J[a][k] = dG_a / dxhat_k
@@ -337,14 +331,7 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
   double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-  {
-    // orientation record: 1 = some det < 0, 2 = some det > 0, 4 = det zero or
-    // not finite; one OR per warp, an atomic only when it adds a bit
-    const int code = !valid ? 0 : ((!(det != 0.0) || !isfinite(det)) ? 4 : (det > 0.0 ? 2 : 1));
-    const int wcode = __reduce_or_sync(0xffffffffu, code);
-    if ((threadIdx.x & 31) == 0 && wcode != 0 && (wcode & ~*(volatile int*)flag) != 0)
-      atomicOr(flag, wcode);
-  }
+  const int code = (!(det != 0.0) || !isfinite(det)) ? 4 : (det > 0.0 ? 2 : 1);
   double adet = fabs(det);
   // metric m = J^T J; Q = adj(m) / det(m) * |det J| = adj(m) / |det J|
   // symmetric metric m = J^T J (six entries)
@@ -357,12 +344,12 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
   double g = G.g[0][i1] * G.g[1][i2] * G.g[2][i3];
   // the Gauss weight folded into the scale of the adjugate
   double inv = g / adet;
-  double q11 = (m11 * m22 - m12 * m12) * inv;
-  double q12 = (m02 * m12 - m01 * m22) * inv;
-  double q13 = (m01 * m12 - m02 * m11) * inv;
-  double q22 = (m00 * m22 - m02 * m02) * inv;
-  double q23 = (m02 * m01 - m00 * m12) * inv;
-  double q33 = (m00 * m11 - m01 * m01) * inv;
+  v[1] = (m11 * m22 - m12 * m12) * inv;
+  v[2] = (m02 * m12 - m01 * m22) * inv;
+  v[3] = (m01 * m12 - m02 * m11) * inv;
+  v[4] = (m00 * m22 - m02 * m02) * inv;
+  v[5] = (m02 * m01 - m00 * m12) * inv;
+  v[6] = (m00 * m11 - m01 * m01) * inv;
   double yh = 0.0;
   if (G.tkind == IGA_TARGET_SINPROD) {
     yh = sin(M_PI * X[0]) * sin(M_PI * X[1]) * sin(M_PI * X[2]);
@@ -371,7 +358,34 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
     yh = exp(-(dx * dx + dy * dy + dz * dz) / G.tp[3]);
   }
   const double wg = adet * g;
-  double v[8] = {wg, q11, q12, q13, q22, q23, q33, yh * wg};
+  v[0] = wg;
+  v[7] = yh * wg;
+  return code;
+}
+
+// one OR of the orientation codes per warp, an atomic only when it adds a bit
+__device__ __forceinline__ void record_orientation(int code, int* flag) {
+  const int wcode = __reduce_or_sync(0xffffffffu, code);
+  if ((threadIdx.x & 31) == 0 && wcode != 0 && (wcode & ~*(volatile int*)flag) != 0)
+    atomicOr(flag, wcode);
+}
+
+// One thread per tensor Gauss point of the whole grid.
+__global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* __restrict__ flag) {
+  size_t Q12 = (size_t)G.Q[1] * G.Q[2];
+  size_t total = (size_t)G.Q[0] * Q12;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // lanes past the end evaluate point 0 and write nothing, so every warp stays
+  // converged for the reductions below
+  const bool valid = t < total;
+  if (!valid) t = 0;
+  int i1 = (int)(t / Q12);
+  size_t rem = t - (size_t)i1 * Q12;
+  int i2 = (int)(rem / G.Q[2]);
+  int i3 = (int)(rem - (size_t)i2 * G.Q[2]);
+  double v[8];
+  const int code = point_weights(G, i1, i2, i3, v);
+  record_orientation(valid ? code : 0, flag);
   if (valid) {
     if (G.comp < 0) {
       for (int c = 0; c < 8; ++c) out[c * total + t] = v[c];
@@ -380,12 +394,26 @@ __global__ void sample_weights_kernel(GeoDev G, double* __restrict__ out, int* _
     }
   }
   if (G.qn2) {
-    double q2 = valid ? (q11 * q11 + q22 * q22 + q33 * q33 +
-                         2.0 * (q12 * q12 + q13 * q13 + q23 * q23))
+    double q2 = valid ? (v[1] * v[1] + v[4] * v[4] + v[6] * v[6] +
+                         2.0 * (v[2] * v[2] + v[3] * v[3] + v[5] * v[5]))
                       : 0.0;
     for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(G.qn2, q2);
   }
+}
+
+// The weights at P listed points (i1, i2, i3) = idx[3p .. 3p+2]: all eight
+// channels, out[c P + p] (the fibres and test points of the TT-cross).
+__global__ void sample_points_kernel(GeoDev G, const int* __restrict__ idx, int P,
+                                     double* __restrict__ out, int* __restrict__ flag) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = p < P;
+  const int q = valid ? p : 0;
+  double v[8];
+  const int code = point_weights(G, idx[3 * q], idx[3 * q + 1], idx[3 * q + 2], v);
+  record_orientation(valid ? code : 0, flag);
+  if (valid)
+    for (int c = 0; c < 8; ++c) out[(size_t)c * P + p] = v[c];
 }
 
 struct GeoSampler {
@@ -396,6 +424,40 @@ struct GeoSampler {
 
   void prepare(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
                const iga_target* target) {
+    const double* pts[3];
+    const double* wts[3];
+    int np[3];
+    for (int d = 0; d < 3; ++d) {
+      pts[d] = st.dir[d].dx.p;
+      wts[d] = st.dir[d].gq.data();
+      np[d] = st.dir[d].E * st.dir[d].q;
+    }
+    prepare_grid(ctx, geo, pts, wts, np, target);
+  }
+
+  // the tensor grid of arbitrary 1-D point sets (device arrays) with the given
+  // host weights per point (folded into every sample as on the Gauss grid)
+  DevBuf<double> own_pts[3];
+  void prepare_points(iga_ctx* ctx, const iga_geometry* geo, const std::vector<double> hp[3],
+                      const iga_target* target) {
+    const double* pts[3];
+    std::vector<double> ones[3];
+    const double* wts[3];
+    int np[3];
+    for (int d = 0; d < 3; ++d) {
+      own_pts[d].alloc(hp[d].size());
+      IGA_CUDA(cudaMemcpyAsync(own_pts[d].p, hp[d].data(), hp[d].size() * 8,
+                               cudaMemcpyHostToDevice, ctx->stream));
+      pts[d] = own_pts[d].p;
+      ones[d].assign(hp[d].size(), 1.0);
+      wts[d] = ones[d].data();
+      np[d] = (int)hp[d].size();
+    }
+    prepare_grid(ctx, geo, pts, wts, np, target);
+  }
+
+  void prepare_grid(iga_ctx* ctx, const iga_geometry* geo, const double* const dpts[3],
+                    const double* const hwts[3], const int npts_d[3], const iga_target* target) {
     IGA_REQUIRE(geo != nullptr, "null geometry");
     IGA_REQUIRE(geo->kind == IGA_GEO_NURBS || geo->kind == IGA_GEO_NURBS_TWIST,
                 "unknown geometry kind");
@@ -406,16 +468,14 @@ struct GeoSampler {
       IGA_REQUIRE(geo->nctrl[d] == geo->nknots[d] - geo->degree[d] - 1,
                   "geometry: nctrl must equal nknots - degree - 1");
       nctrl *= geo->nctrl[d];
-      const DirTables& T = st.dir[d];
-      int npts = T.E * T.q;
+      const int npts = npts_d[d];
       std::vector<double> k(geo->knots[d], geo->knots[d] + geo->nknots[d]);
       gV[d].alloc((size_t)npts * (geo->degree[d] + 1));
       gD[d].alloc((size_t)npts * (geo->degree[d] + 1));
       gspan[d].alloc(npts);
       gw[d].alloc(npts);
-      IGA_CUDA(cudaMemcpyAsync(gw[d].p, T.gq.data(), npts * 8, cudaMemcpyHostToDevice,
-                               ctx->stream));
-      basis_tables(ctx, k, geo->degree[d], T.dx.p, npts, gspan[d].p, gV[d].p, gD[d].p);
+      IGA_CUDA(cudaMemcpyAsync(gw[d].p, hwts[d], npts * 8, cudaMemcpyHostToDevice, ctx->stream));
+      basis_tables(ctx, k, geo->degree[d], dpts[d], npts, gspan[d].p, gV[d].p, gD[d].p);
       G.V[d] = gV[d].p;
       G.D[d] = gD[d].p;
       G.span[d] = gspan[d].p;
@@ -478,6 +538,16 @@ void sample_weights_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTable
   IGA_REQUIRE(out != nullptr, "null output");
   GeoSampler S;
   S.prepare(ctx, geo, st, target);
+  S.run(ctx, out, -1, nullptr);
+}
+
+// The eight weights on the tensor grid of the 1-D point sets hp (no
+// quadrature weights): out holds 8 consecutive tensors (n1, n2, n3).
+void sample_weights_points(iga_ctx* ctx, const iga_geometry* geo, const std::vector<double> hp[3],
+                           const iga_target* target, double* out) {
+  IGA_REQUIRE(out != nullptr, "null output");
+  GeoSampler S;
+  S.prepare_points(ctx, geo, hp, target);
   S.run(ctx, out, -1, nullptr);
 }
 

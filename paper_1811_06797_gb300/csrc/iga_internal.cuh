@@ -2,7 +2,6 @@
 #pragma once
 
 #include <cuda_runtime.h>
-#include <cublas_v2.h>
 
 #include <cstdint>
 #include <cstdio>
@@ -35,14 +34,6 @@ struct Error : public std::runtime_error {
       throw ::iga::Error(IGA_ECUDA, std::string(#call) + ": " +                  \
                                         cudaGetErrorString(e__));                \
     }                                                                            \
-  } while (0)
-
-#define IGA_BLAS(call)                                                           \
-  do {                                                                           \
-    cublasStatus_t s__ = (call);                                                 \
-    if (s__ != CUBLAS_STATUS_SUCCESS)                                            \
-      throw ::iga::Error(IGA_ECUDA, std::string(#call) + ": cublas status " +    \
-                                        std::to_string((int)s__));               \
   } while (0)
 
 // Launch on the context stream, count it, and surface launch errors.  When
@@ -145,7 +136,6 @@ struct iga_ctx {
   int nsm = 1;                              // SMs of the device
   std::string err;
   uint64_t launches = 0;
-  cublasHandle_t blas = nullptr;
   std::vector<iga::DevBuf<char>> scratch;   // reusable scratch slots
   int* dflag = nullptr;                     // device status flags (zeroed per use)
   int* hflag = nullptr;                     // pinned host mirror
@@ -214,7 +204,7 @@ enum {
   SLOT_TTSVD_OMEGA = 0, SLOT_TTSVD_Y, SLOT_TTSVD_Q, SLOT_TTSVD_BT, SLOT_TTSVD_G, SLOT_TTSVD_V,
   SLOT_TTSVD_W, SLOT_TTSVD_C, SLOT_TTSVD_NORM, SLOT_QRCP_WORK, SLOT_ASM_W, SLOT_ASM_SAMPLES, SLOT_KRON_Z,
   SLOT_KRON_Z2, SLOT_LOCAL_T1, SLOT_LOCAL_T2, SLOT_KKT_TMP, SLOT_MISC0, SLOT_MISC1,
-  SLOT_TTM_W, SLOT_QNORM, SLOT_TTSVD_Y2, SLOT_TTSVD_PART,
+  SLOT_TTM_W, SLOT_QNORM, SLOT_TTSVD_Y2, SLOT_TTSVD_PART, SLOT_GEMM_PART, SLOT_GEMM_DOT,
   SLOT_AMEN_BASE = 32
 };
 
@@ -222,6 +212,8 @@ enum {
 void build_space_tables(iga_ctx* ctx, const iga_space* sp, SpaceTables& t);
 void check_knots(const double* k, int nk, int p, const char* what);
 
+void sample_weights_points(iga_ctx* ctx, const iga_geometry* geo, const std::vector<double> hp[3],
+                           const iga_target* target, double* out);
 void sample_weights_each(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
                          const iga_target* target, double* buf, double* qnorm2,
                          void (*cb)(void*, int, const double*), void* user);
@@ -267,6 +259,10 @@ void local_matvec_t(iga_ctx* ctx, int r0, int n, int r1, int R0, int R1, int p, 
 // api.cu
 void weight_tts_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
                      const iga_target* target, double tol, iga_tt* tts[8]);
+// interp.cu: the eight weight TTs at the Gauss points from the interpolant
+// of degree pt (Sec. 3, weightEquationSystem / weightEquationSolve)
+void weight_tts_interp_impl(iga_ctx* ctx, const iga_geometry* geo, const SpaceTables& st,
+                            const iga_target* target, double tol, int pt, iga_tt* tts[8]);
 void ops_from_weights_impl(iga_ctx* ctx, const SpaceTables& st, const iga_tt* const w[7],
                            iga_op** M, iga_op** K);
 void kkt_apply_internal(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta, const void* z,
@@ -298,8 +294,27 @@ void tc_flag_check(iga_ctx* ctx, const char* what);
 
 void set_error(iga_ctx* ctx, const std::string& m);
 
-// cudaFuncSetAttribute(fn, attr, value) once per (function, attribute,
-// value, device): a function attribute belongs to the device that was
+// gemm.cu: row-major strided batch C_i = alpha op(A_i) op(B_i) + beta C_i
+// (op(A) is M x K: A[m lda + k], or A[k lda + m] when tA), the local GMRES's
+// vector kernels and a deterministic FP64 dot product (synchronises)
+template <typename T>
+void gemm_rm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, T alpha, const T* A,
+                     int lda, long long sA, const T* B, int ldb, long long sB, T beta, T* C,
+                     int ldc, long long sC, int count);
+template <typename T>
+void gemv_cm_add(iga_ctx* ctx, int rows, int cols, const T* A, const T* x, T* y);
+template <typename T>
+void vec_sub(iga_ctx* ctx, size_t n, const T* a, const T* b, T* out);
+double device_dot(iga_ctx* ctx, const double* a, const double* b, size_t n);
+// tc_gemm.cu: the same product in FP32 storage on the tensor cores (TF32
+// operands, FP32 accumulation); tC stores C transposed (C[n ldc + m])
+void tc_gemm_tf32(iga_ctx* ctx, bool tA, bool tB, bool tC, int M, int N, int K, float alpha,
+                  const float* A, int lda, long long sA, const float* B, int ldb, long long sB,
+                  float beta, float* C, int ldc, long long sC, int count);
+
+// cudaFuncSetAttribute(fn, attr, value) per (function, attribute, device),
+// raising the value monotonically (a smaller later request keeps the larger
+// value already set): a function attribute belongs to the device that was
 // current when it was set, so a second device needs its own call.  Thread
 // safe.
 void func_attr(const void* fn, cudaFuncAttribute attr, int value);

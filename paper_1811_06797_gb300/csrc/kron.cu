@@ -9,10 +9,10 @@
 // directions 1 and 2 (reading x through L1), then the mode-2 and mode-1
 // products in shared memory, for every term in turn, and writes y once.
 // x is read from HBM once per tile (halo re-reads hit L1/L2) and y written
-// once.  TT-matrix blocks (ranks > 1) in TF32 go through the fused tcgen05
-// kernel of ttm_tc.cu; in FP64 and plain FP32 they use staged single-mode
-// products with full-size intermediates and a batched GEMM for the rank
-// contraction.
+// once.  TT-matrix blocks (ranks > 1) in TF32 / BF16 go through the fused
+// tcgen05 kernel of ttm_tc.cu; in FP64 and plain FP32 they use staged
+// single-mode products with full-size intermediates and the library's batched
+// GEMM (gemm.cu) for the rank contraction.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -459,15 +459,11 @@ static void ttm_block_gemm(iga_ctx* ctx, const iga_op* A, const OpBlock& blk, T 
   size_t tw = (size_t)n2 * R1 * Kd;
   IGA_LAUNCH(ctx, ttm_wpack_kernel<T>, (unsigned)((tw + 255) / 256), 256, 0,
              band_ptr<T>(A, 1, blk.off[1]), R1, R2, n2, B, W);
-  const T one = T(1), zero = T(0);
-  cudaDataType dt = sizeof(T) == 8 ? CUDA_R_64F : CUDA_R_32F;
-  cublasComputeType_t ct = sizeof(T) == 8 ? CUBLAS_COMPUTE_64F
-                                          : (tf32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F);
-  IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
-  IGA_BLAS(cublasGemmStridedBatchedEx(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N13, R1, Kd, &one,
-                                      z3, dt, (int)N13, (long long)R2 * N13, W, dt, Kd,
-                                      (long long)R1 * Kd, &zero, C, dt, (int)N13,
-                                      (long long)R1 * N13, n2, ct, CUBLAS_GEMM_DEFAULT));
+  // C_{i2} (R1 x n1 n3) = W_{i2} (R1 x (2P+1) R2) Z_{i2}, Z_{i2} = the window of
+  // z3 starting at slab i2 (stride R2 n1 n3 between consecutive i2)
+  (void)tf32;
+  gemm_rm_batched<T>(ctx, false, false, R1, (int)N13, Kd, T(1), W, Kd, (long long)R1 * Kd, z3,
+                     (int)N13, (long long)R2 * N13, T(0), C, (int)N13, (long long)R1 * N13, n2);
   {
     int th = std::min(256, ((n3 + 31) / 32) * 32);
     dim3 grid((unsigned)((size_t)n2 * n1), 1);

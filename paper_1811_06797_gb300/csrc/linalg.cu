@@ -10,7 +10,8 @@
 //   taken twice (the second Gram matrix is nearly diagonal, which gives
 //   the small singular values to relative accuracy),
 // and the kept factor is recomputed exactly as U^T A.  Large products go to
-// cuBLAS DGEMM; the QR, Jacobi and helper kernels are below.
+// the library's tiled GEMM (gemm.cu); the QR, Jacobi and helper kernels are
+// below.
 #include <algorithm>
 #include <cmath>
 
@@ -1034,10 +1035,13 @@ void gen_eig_prep(iga_ctx* ctx, const double* PM, int SM, const double* PK, int 
 
 // ----------------------------------------------------------------- TT-SVD
 
-static void gemm(iga_ctx* ctx, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-                 const double* A, int lda, const double* B, int ldb, double* C, int ldc) {
-  const double one = 1.0, zero = 0.0;
-  IGA_BLAS(cublasDgemm(ctx->blas, ta, tb, m, n, k, &one, A, lda, B, ldb, &zero, C, ldc));
+// column-major C (m x n, ldc) = op(A) op(B): the same storage as the
+// row-major product C^T = op(B)^T op(A)^T
+enum GemmOp { OP_N = 0, OP_T = 1 };
+static void gemm(iga_ctx* ctx, GemmOp ta, GemmOp tb, int m, int n, int k, const double* A, int lda,
+                 const double* B, int ldb, double* C, int ldc) {
+  gemm_rm_batched<double>(ctx, tb == OP_T, ta == OP_T, n, m, k, 1.0, B, ldb, 0, A, lda, 0, 0.0, C,
+                          ldc, 0, 1);
 }
 
 // ---- narrow products with a wide row-major A (ns x m, row length m >> ns)
@@ -1287,8 +1291,8 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
     if (bt <= 0) { est2 = 0.0; break; }
     fill_gaussian(ctx, Om, (size_t)m * bt, seed + 7919u * (uint64_t)(blk + 1));
     if (!xT && bt <= SKINNY_K) skinny_sketch(ctx, X, ns, m, Om, bt, Y);
-    else if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, bt, m, X, m, Om, m, Y, ns);
-    else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, bt, m, X, ns, Om, m, Y, ns);
+    else if (!xT) gemm(ctx, OP_T, OP_N, ns, bt, m, X, m, Om, m, Y, ns);
+    else gemm(ctx, OP_N, OP_N, ns, bt, m, X, ns, Om, m, Y, ns);
     for (int pass = 0; pass < 2 && kq > 0; ++pass) {
       // Y -= Q (Q^T Y)
       IGA_LAUNCH(ctx, qt_y_kernel, (unsigned)((kq * bt + 7) / 8), 256, 0, Q, Y, ns, kq, bt, T);
@@ -1313,8 +1317,8 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
   if (kq == 0) {
     // A is below the threshold as a whole: one basis vector from a fresh sketch
     fill_gaussian(ctx, Om, (size_t)m, seed + 104729u);
-    if (!xT) gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, ns, 1, m, X, m, Om, m, Y, ns);
-    else gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, 1, m, X, ns, Om, m, Y, ns);
+    if (!xT) gemm(ctx, OP_T, OP_N, ns, 1, m, X, m, Om, m, Y, ns);
+    else gemm(ctx, OP_N, OP_N, ns, 1, m, X, ns, Om, m, Y, ns);
     householder_qr(ctx, Y, Q, ns, 1);
   }
   double* Bt = scratch<double>(ctx, SLOT_TTSVD_BT, (size_t)m * k * 2);
@@ -1326,22 +1330,22 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
   double* V2 = V1 + (size_t)k * k;
   const bool narrow = k <= SKINNY_K && (size_t)ns * k * sizeof(double) <= 48 * 1024;
   if (!xT && narrow) skinny_at(ctx, X, ns, m, Q, k, Bt);
-  else if (!xT) gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, ns, X, m, Q, ns, Bt, m);
-  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, m, k, ns, X, ns, Q, ns, Bt, m);
+  else if (!xT) gemm(ctx, OP_N, OP_N, m, k, ns, X, m, Q, ns, Bt, m);
+  else gemm(ctx, OP_T, OP_N, m, k, ns, X, ns, Q, ns, Bt, m);
   // first Gram pass
   if (k <= SKINNY_K) skinny_gram(ctx, Bt, m, k, G);
-  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt, m, Bt, m, G, k);
+  else gemm(ctx, OP_T, OP_N, k, k, m, Bt, m, Bt, m, G, k);
   jacobi_eig(ctx, G, V1, wv, k);
   // second pass on the rotated factor: nearly diagonal Gram matrix
   if (k <= SKINNY_K)
     IGA_LAUNCH(ctx, rows_small_kernel, (unsigned)((m + 255) / 256), 256, 0, Bt, (long long)m, k,
                V1, k, Bt2);
   else
-    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
+    gemm(ctx, OP_N, OP_N, m, k, k, Bt, m, V1, k, Bt2, m);
   if (k <= SKINNY_K) skinny_gram(ctx, Bt2, m, k, G);
-  else gemm(ctx, CUBLAS_OP_T, CUBLAS_OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
+  else gemm(ctx, OP_T, OP_N, k, k, m, Bt2, m, Bt2, m, G, k);
   jacobi_eig(ctx, G, V2, wv, k);
-  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, V1, k, V2, k, V, k);
+  gemm(ctx, OP_N, OP_N, k, k, k, V1, k, V2, k, V, k);
   std::vector<double> lam(k);
   IGA_CUDA(cudaMemcpyAsync(lam.data(), wv, k * 8, cudaMemcpyDeviceToHost, ctx->stream));
   IGA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1354,14 +1358,14 @@ static int rsvd_left(iga_ctx* ctx, const double* X, bool xT, int ns, int m, doub
     if (std::sqrt(tail[i]) <= delta) { r = i; break; }
   r = std::max(1, std::min(r, rmax));
   Uout.alloc((size_t)ns * r);
-  gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, ns, r, k, Q, ns, V, k, Uout.p, ns);
+  gemm(ctx, OP_N, OP_N, ns, r, k, Q, ns, V, k, Uout.p, ns);
   // Ct = A^T U = Bt V_r
   Ctout.alloc((size_t)m * r);
   if (k <= SKINNY_K)
     IGA_LAUNCH(ctx, rows_small_kernel, (unsigned)((m + 255) / 256), 256, 0, Bt, (long long)m, k,
                V, r, Ctout.p);
   else
-    gemm(ctx, CUBLAS_OP_N, CUBLAS_OP_N, m, r, k, Bt, m, V, k, Ctout.p, m);
+    gemm(ctx, OP_N, OP_N, m, r, k, Bt, m, V, k, Ctout.p, m);
   return r;
 }
 
@@ -1511,7 +1515,6 @@ void tt_svd3(iga_ctx* ctx, const double* W, int n1, int n2, int n3, double tol, 
     *out = r1;
     return;
   }
-  IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
   // first unfolding (n1 x n2 n3): memory is X col-major (n2 n3 x n1)
   DevBuf<double> U1, C1, U2, C2;
   int m1 = n2 * n3;

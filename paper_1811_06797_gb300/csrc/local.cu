@@ -116,14 +116,11 @@ template void local_matvec_t<float>(iga_ctx*, int, int, int, int, int, int, cons
 // row-major C (M x N) = A (M x K) B (K x N)
 void gemm_rm(iga_ctx* ctx, int M, int N, int K, const double* A, const double* B, double* C,
              double beta) {
-  const double one = 1.0;
-  IGA_BLAS(cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, N, M, K, &one, B, N, A, K, &beta, C,
-                       N));
+  gemm_rm_batched<double>(ctx, false, false, M, N, K, 1.0, A, K, 0, B, N, 0, beta, C, N, 0, 1);
 }
 
 void tt_full_impl(iga_ctx* ctx, const iga_tt* tt, double* out) {
   IGA_REQUIRE(tt && out, "tt_full: null argument");
-  IGA_BLAS(cublasSetStream(ctx->blas, ctx->stream));
   int n1 = tt->n[0], n2 = tt->n[1], n3 = tt->n[2], r1 = tt->r[0], r2 = tt->r[1];
   double* t12 = scratch<double>(ctx, SLOT_MISC0, (size_t)n1 * n2 * r2);
   gemm_rm(ctx, n1, n2 * r2, r1, tt->core[0].p, tt->core[1].p, t12);

@@ -93,6 +93,9 @@ def lib():
         "iga_lowrank_assemble": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, P(vp), P(vp),
                                       P(vp)]),
         "iga_weight_tts": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, P(vp)]),
+        "iga_lowrank_assemble_interp": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, i,
+                                             P(vp), P(vp), P(vp)]),
+        "iga_weight_tts_interp": (st, [vp, P(Geometry_), P(Space_), P(Target_), d, i, P(vp)]),
         "iga_tt_from_cores": (st, [vp, P(C.c_int), P(C.c_int), P(vp), P(vp)]),
         "iga_ops_from_weights": (st, [vp, P(Space_), P(vp), P(vp), P(vp)]),
         "iga_load_from_density": (st, [vp, P(Space_), vp, P(vp)]),
@@ -371,6 +374,31 @@ def iga_lowrank_assemble(ctx, geometry, space, target, tol):
     _check(ctx, lib().iga_lowrank_assemble(ctx.handle, C.byref(g), C.byref(s), C.byref(t),
                                            float(tol), C.byref(hm), C.byref(hk), C.byref(hl)))
     return Op(hm), Op(hk), (TT(hl) if hl.value else None)
+
+
+def iga_lowrank_assemble_interp(ctx, geometry, space, target, tol, degree=0):
+    """Low-rank assembly with the weights interpolated in a spline space of the
+    given degree (0: 2p + 1)."""
+    keep = _Keep()
+    g = geometry_struct(geometry, keep)
+    s = space_struct(space, keep)
+    t = target_struct(target)
+    hm, hk, hl = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(ctx, lib().iga_lowrank_assemble_interp(ctx.handle, C.byref(g), C.byref(s), C.byref(t),
+                                                  float(tol), int(degree), C.byref(hm),
+                                                  C.byref(hk), C.byref(hl)))
+    return Op(hm), Op(hk), (TT(hl) if hl.value else None)
+
+
+def iga_weight_tts_interp(ctx, geometry, space, target, tol, degree=0):
+    keep = _Keep()
+    g = geometry_struct(geometry, keep)
+    s = space_struct(space, keep)
+    t = target_struct(target)
+    hs = (C.c_void_p * 8)()
+    _check(ctx, lib().iga_weight_tts_interp(ctx.handle, C.byref(g), C.byref(s), C.byref(t),
+                                            float(tol), int(degree), hs))
+    return [TT(C.c_void_p(h)) if h else None for h in hs]
 
 
 def iga_weight_tts(ctx, geometry, space, target, tol):
