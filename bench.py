@@ -49,7 +49,7 @@ FP64_FMA_TFLOPS = alu_peak_tflops("fp64", {})
 FP32_FMA_TFLOPS = alu_peak_tflops("fp32", {})
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel, as
 # summarised under profiles/; an entry is dropped whenever its kernel changes
-NCU_TRAFFIC = {"sample_weights_kernel": 1.0692e9}
+NCU_TRAFFIC = {}
 # kernels that can dominate a step, with the arithmetic they run in
 CANDIDATES = {
     "jacobi_eig_kernel": "fp64", "sample_weights_kernel": "fp64",
@@ -57,7 +57,7 @@ CANDIDATES = {
     "kkt_qd_solve_kernel": "fp32", "kkt_qd_factor_kernel": "fp32",
     "kron_rank1_kernel": "fp64",
     "qrcp_cluster_kernel": "fp64", "householder_qr_cluster_kernel": "fp64",
-    "rank1_residual_kernel": "fp64",
+    "rank1_residual_kernel": "fp64", "gemm_tile_kernel": "fp64",
 }
 
 
@@ -69,11 +69,19 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--weights", default="interp", choices=["interp", "sampled"],
+                    help="weights interpolated in degree 2p+1 (the paper's route, Sec. 3) or "
+                         "sampled on the Gauss grid")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--roofline-kernel", default="auto",
                     help="kernel name for the roofline entry, or auto (largest device time)")
+    ap.add_argument("--only", default=None, choices=["ttm"],
+                    help="ttm: only the tensor-core TT apply measurement (a profiling case)")
+    ap.add_argument("--ttm-elements", type=int, default=512,
+                    help="elements per direction of the --only ttm grid")
+    ap.add_argument("--ttm-kinds", default="tf32,bf16", help="operand types of --only ttm")
     return ap.parse_args()
 
 
@@ -212,7 +220,16 @@ class OracleLeg:
     The value is the sum, in seconds per step of the GPU arm's metric.
     """
 
-    def __init__(self, work, slab=16):
+    def __init__(self, work, slab=16, route="sampled"):
+        self.route = route
+        if route == "interp":
+            # the interpolation route is cheap enough to run in full every step
+            self.work = work
+            t0 = time.perf_counter()
+            v, parts, sol = self._interp_pipeline()
+            self.full = sol
+            self.setup_s = time.perf_counter() - t0
+            return
         import numpy as np
         from oracle.assemble import Discretisation, sample_weights
         self.work = work
@@ -232,8 +249,29 @@ class OracleLeg:
         del samples
         self.np = np
 
+    def _interp_pipeline(self):
+        """The oracle's whole interpolated-weight pipeline at full size:
+        (seconds, parts, solution)."""
+        from oracle.assemble import Discretisation
+        from oracle.interp import weight_tts_interp
+        from oracle.solve import operators_from_tts, solve_kkt
+        w = self.work
+        t0 = time.perf_counter()
+        disc = Discretisation(w.space.degree, w.space.knots, w.space.nquad)
+        tts = weight_tts_interp(w.geometry, disc, w.tol, w.target)
+        t1 = time.perf_counter()
+        Mt, Kt, diag, b = operators_from_tts(w.space, tts)
+        t2 = time.perf_counter()
+        y, u, lam, _ = solve_kkt(Mt, Kt, diag, b, w.beta, tol=1e-12)
+        t3 = time.perf_counter()
+        parts = {"weights_s": t1 - t0, "univariate_s": t2 - t1, "solve_s": t3 - t2}
+        return t3 - t0, parts, {"y": y, "u": u, "lam": lam}
+
     def step(self):
         """One timed step: (seconds scaled to the whole workload, parts)."""
+        if self.route == "interp":
+            v, parts, _ = self._interp_pipeline()
+            return v, parts
         np = self.np
         from oracle.assemble import evaluate_target
         from oracle.geometry import grid_points, map_and_jacobian, weights_from_jacobian
@@ -270,6 +308,10 @@ class OracleLeg:
         return sum(parts.values()), parts
 
     def describe(self):
+        if self.route == "interp":
+            return ("the oracle's whole pipeline at full size every step, no sampling or "
+                    "scaling: weights at the Greville nodes of the degree-2p+1 space, TT-SVD, "
+                    "collocation maps, univariate factors, load, reduced-system CG to 1e-12")
         return (f"oracle pipeline at full size in the set-up ({self.setup_s:.1f} s, untimed); per "
                 f"step: weight sampling and TT-SVD on a slab of {self.slab} of "
                 f"{self.slab * self.S} Gauss planes along direction 3, scaled x{self.S}; "
@@ -287,17 +329,18 @@ TF32_PER_BF16 = 1.1 / 2.25
 TTM_RANK = 37
 
 
-def ttm_roofline(ctx, iga, torch, pk, pk_kind, reps=5):
+def ttm_roofline(ctx, iga, torch, pk, pk_kind, reps=5, elements=512, kinds=("tf32", "bf16")):
     """The TT-matrix Kronecker apply on the tensor cores (TF32 and BF16
     operands) at the shape of the random-volume workload: degree 2, 512
-    elements per direction (n = 512 interior functions per direction), one
+    elements per direction (n = 512 interior functions per direction; a
+    smaller `elements` gives the same shape on a smaller grid), one
     TT-matrix block of ranks (TTM_RANK, TTM_RANK) assembled from a seeded
     weight TT of those ranks on its Gauss grid.  Live CUDA-event timing of
     the fused kernel; algorithmic flops 2 (2p+1) N (R2 + R1 R2 + R1)."""
     import numpy as np
     from paper_1811_06797_gb300 import workloads as wl
-    space = wl.uniform_space(2, 512)
-    Q = 512 * space.nquad
+    space = wl.uniform_space(2, elements)
+    Q = elements * space.nquad
     R = TTM_RANK
     rng = np.random.default_rng(1811)
     cores = [rng.uniform(0.5, 1.5, (1, Q, R)), rng.standard_normal((R, Q, R)),
@@ -308,7 +351,7 @@ def ttm_roofline(ctx, iga, torch, pk, pk_kind, reps=5):
     x = torch.randn(N, device="cuda", dtype=torch.float32)
     y = torch.zeros(N, device="cuda", dtype=torch.float32)
     out = {}
-    for kind in ("tf32", "bf16"):
+    for kind in kinds:
         kw = {kind: True}
         iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y, **kw)
         torch.cuda.synchronize()
@@ -327,9 +370,26 @@ def ttm_roofline(ctx, iga, torch, pk, pk_kind, reps=5):
                      "avg_ms": avg, "launches": p["launches"],
                      "algorithmic_flops_per_launch": fl,
                      "algorithmic_bytes_per_launch": p["bytes"] / max(1, p["launches"]),
-                     "workload": f"random-volume shape, p=2, n=512^3, TT ranks ({R},{R})"}
+                     "workload": f"random-volume shape, p=2, n={elements}^3, TT ranks ({R},{R})"}
     del M, tt, x, y
     torch.cuda.empty_cache()
+    return out
+
+
+def assembly_routes(assemble, work, torch, reps=3):
+    """Median wall time of the low-rank assembly of the workload through both
+    weight routes (interpolated in degree 2p+1, sampled on the Gauss grid)."""
+    out = {}
+    for route in ("interp", "sampled"):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ops = assemble(work, route)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+            del ops
+        out[route] = round(statistics.median(ts), 3)
     return out
 
 
@@ -404,10 +464,16 @@ def run_gpu(args, world, rank, local):
 
     state = {}
 
+    def assemble(w, route=None):
+        route = route or args.weights
+        if route == "interp":
+            return iga.iga_lowrank_assemble_interp(ctx, w.geometry, w.space, w.target, w.tol)
+        return iga.iga_lowrank_assemble(ctx, w.geometry, w.space, w.target, w.tol)
+
     def step():
         ea = torch.cuda.Event(enable_timing=True)
         ea.record(stream)
-        M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+        M, K, load = assemble(work)
         eb = torch.cuda.Event(enable_timing=True)
         eb.record(stream)
         state["split"] = (ea, eb)
@@ -569,7 +635,10 @@ def run_gpu(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": work.name, "unknowns_per_field": N, "kkt_unknowns": 3 * N,
                    "beta": work.beta, "tt_tol": work.tol, "residual_tol": args.tol,
-                   "precision": args.precision, "l2": "flushed (256 MB write) before every step",
+                   "precision": args.precision,
+                   "weights": ("interpolated in degree 2p+1 at the Greville nodes"
+                               if args.weights == "interp" else "sampled on the Gauss grid"),
+                   "l2": "flushed (256 MB write) before every step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "solve": {**{k: info[k] for k in ("sweeps", "refinements", "max_rank", "local_iters",
                                           "residual")},
@@ -584,6 +653,7 @@ def run_gpu(args, world, rank, local):
         "roofline": roof,
         "kron_roofline": kron_roof,
         "ttm_roofline": ttm_roofline(ctx, iga, torch, pk, pk_kind),
+        "assembly_routes_ms": assembly_routes(assemble, work, torch),
         "rank_tables": rank_tables(ctx),
         "config5_assembly": config5_assembly(ctx, iga, torch),
         "storage": {work.name: report.storage(ctx, work.geometry, work.space, work.target,
@@ -595,9 +665,9 @@ def run_gpu(args, world, rank, local):
     return line, work, solutions
 
 
-def oracle_baseline(work, steps):
+def oracle_baseline(work, steps, route):
     """cpu_baseline: the oracle leg's set-up plus `steps` timed steps."""
-    leg = OracleLeg(work)
+    leg = OracleLeg(work, route=route)
     vals, parts = [], None
     for _ in range(max(1, steps)):
         v, parts = leg.step()
@@ -613,7 +683,7 @@ def run_reference(args):
     W untimed and K timed steps of the bounded sample (OracleLeg)."""
     from paper_1811_06797_gb300 import workloads as wl
     work = wl.config(args.config)
-    leg = OracleLeg(work)
+    leg = OracleLeg(work, route=args.weights)
     for _ in range(args.warmup):
         leg.step()
     vals, parts = [], None
@@ -625,7 +695,9 @@ def run_reference(args):
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": work.name}, "impl": "reference",
+        "config": {"workload": work.name,
+                   "weights": "interpolated" if args.weights == "interp" else "sampled"},
+        "impl": "reference",
         "cpu_baseline": {"kind": "oracle", "cores": _threads(), "sample": leg.describe(),
                          "value": v, "unit": "s",
                          "parts_s": {k: round(x, 3) for k, x in parts.items()}},
@@ -640,11 +712,22 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)))
         return
+    if args.only == "ttm":
+        import torch
+        from paper_1811_06797_gb300 import build, iga
+        build.build()
+        torch.cuda.set_device(local)
+        pk, pk_kind = peaks()
+        out = ttm_roofline(iga.Context(), iga, torch, pk, pk_kind, reps=args.steps,
+                           elements=args.ttm_elements, kinds=tuple(args.ttm_kinds.split(",")))
+        if rank == 0:
+            print(json.dumps({"ttm_roofline": out}))
+        return
     line, work, solutions = run_gpu(args, world, rank, local)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             try:
-                leg, base = oracle_baseline(work, 2)
+                leg, base = oracle_baseline(work, 2, args.weights)
                 line["cpu_baseline"] = base
                 # the error of every result against the oracle's solution
                 line["oracle_errors"] = {k: field_errors(v, leg.full) for k, v in solutions.items()}

@@ -121,6 +121,20 @@ iga_status iga_profile_end(iga_ctx* ctx, uint64_t* launches, double* ms, double*
  * events on the context stream (best of three launches after one warm-up).
  * Synchronises. */
 iga_status iga_measure_fma(iga_ctx* ctx, iga_prec prec, double* tflops);
+/* Utility (no counterpart in the paper): the library's own dense product,
+ * the one its contractions use, for count row-major matrices
+ *   C_i = alpha op(A_i) op(B_i) + beta C_i,   i < count,
+ * op(A_i) M x K, op(B_i) K x N, A_i = A + i sA (elements; likewise B, C),
+ * op = transpose when tA / tB is nonzero (A_i then K x M with leading
+ * dimension lda).  Device pointers in FP64 (prec IGA_FP64) or FP32
+ * (IGA_FP32); the caller owns them.  Deterministic: a reduction split over K
+ * is summed in a fixed order.  Queued on the context stream (no
+ * synchronisation).  IGA_EINVAL for a null pointer, a negative size or a
+ * leading dimension shorter than a row. */
+iga_status iga_gemm_batched(iga_ctx* ctx, iga_prec prec, int tA, int tB, int M, int N, int K,
+                            double alpha, const void* A, int lda, long long sA, const void* B,
+                            int ldb, long long sB, double beta, void* C, int ldc, long long sC,
+                            int count);
 
 /* ---- (a1, a2) geometry sampling ------------------------------------- */
 

@@ -20,7 +20,8 @@ the iteration count, never the solution.
 
 Pins: tests/test_oracle_solve.py checks this route against the sparse direct
 solve of the 3-D assembled system on small grids (annulus, twisted annulus,
-random volume).
+random volume); the interpolated-weight variant reuses the same solve on the
+operators of oracle/interp.py (pinned there).
 """
 from __future__ import annotations
 
@@ -68,6 +69,14 @@ def interior_operators(space, geometry, target, tol, samples=None):
     earlier assemble.sample_weights output of this grid, or None)."""
     disc = Discretisation(space.degree, space.knots, space.nquad)
     return operators_from_tts(space, weight_tts(geometry, disc, tol, target, samples=samples))
+
+
+def interior_operators_interp(space, geometry, target, tol, pt=None):
+    """interior_operators with the weights interpolated in a spline space of
+    degree pt (interp.weight_tts_interp) instead of sampled."""
+    from .interp import weight_tts_interp
+    disc = Discretisation(space.degree, space.knots, space.nquad)
+    return operators_from_tts(space, weight_tts_interp(geometry, disc, tol, target, pt))
 
 
 def operators_from_tts(space, tts):

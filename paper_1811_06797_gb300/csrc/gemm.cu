@@ -8,8 +8,10 @@
 // batch.  One CTA computes a BM x BN tile with 256 threads, each a TM x TN
 // block of outputs in registers; the A and B panels of depth BK are staged
 // in shared memory (transposed on the way in when an operand is transposed),
-// so every shared-memory load feeds TM (or TN) FMAs.  FP64 uses 64 x 64 tiles
-// (4 x 4 per thread; the FP64 pipe is the bound), FP32 128 x 128 (8 x 8).
+// so every shared-memory load feeds TM (or TN) FMAs.  FP64 uses 64 x 64,
+// 64 x 16, 16 x 64 or 16 x 16 tiles (4 x 4 down to 1 x 1 per thread, the
+// shape with the least padding: the FP64 pipe is the bound), FP32 128 x 128
+// (8 x 8).
 // A long reduction with few output tiles is split over the K dimension into
 // partial products and summed by a second kernel in a fixed order, so that
 // every result is deterministic.
@@ -113,15 +115,14 @@ __global__ void gemm_splitk_reduce_kernel(int M, int N, int ksplit, int count, T
   }
 }
 
-template <typename T>
-void gemm_rm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, T alpha, const T* A,
-                     int lda, long long sA, const T* B, int ldb, long long sB, T beta, T* C,
-                     int ldc, long long sC, int count) {
-  if (M <= 0 || N <= 0 || count <= 0) return;
-  constexpr int TM = sizeof(T) == 8 ? 4 : 8, TN = TM, BK = sizeof(T) == 8 ? 16 : 8;
+// one tile shape: split the reduction when the output tiles cannot fill the
+// GPU, then the tile kernel (and the ordered sum of the partial products)
+template <typename T, int TM, int TN, int BK>
+static void gemm_launch(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, T alpha, const T* A,
+                        int lda, long long sA, const T* B, int ldb, long long sB, T beta, T* C,
+                        int ldc, long long sC, int count) {
   constexpr int BM = 16 * TM, BN = 16 * TN;
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  // split the reduction when the output tiles cannot fill the GPU
   const long long tiles = (long long)tm * tn * count;
   int ksplit = 1;
   if (K > 4 * BK && tiles < 2LL * ctx->nsm) {
@@ -153,6 +154,51 @@ void gemm_rm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, T alph
                  (unsigned)std::min<size_t>((tot + 255) / 256, 4096), 256, 0, M, N, ksplit, nb,
                  alpha, part, beta, C + b0 * sC, ldc, sC);
     }
+  }
+}
+
+// FP64 tile shape: the FP64 pipe (two FMA per clock and SM) computes the
+// padding of a partly filled tile at full cost, so the shape is the one with
+// the fewest padded FMAs among 64 x 64, 64 x 16, 16 x 64 and 16 x 16 (the
+// larger tile unless the smaller one saves a tenth: fewer blocks, more reuse
+// of each staged element)
+static int gemm_fp64_shape(int M, int N) {
+  static const int bm[4] = {64, 64, 16, 16}, bn[4] = {64, 16, 64, 16};
+  int best = 0;
+  double cbest = 0.0;
+  for (int v = 0; v < 4; ++v) {
+    const double c = (double)((M + bm[v] - 1) / bm[v]) * bm[v] * ((N + bn[v] - 1) / bn[v]) * bn[v];
+    if (v == 0 || c < 0.9 * cbest) { best = v; cbest = c; }
+  }
+  return best;
+}
+
+template <typename T>
+void gemm_rm_batched(iga_ctx* ctx, bool tA, bool tB, int M, int N, int K, T alpha, const T* A,
+                     int lda, long long sA, const T* B, int ldb, long long sB, T beta, T* C,
+                     int ldc, long long sC, int count) {
+  if (M <= 0 || N <= 0 || count <= 0) return;
+  if constexpr (sizeof(T) == 8) {
+    switch (gemm_fp64_shape(M, N)) {
+      case 0:
+        gemm_launch<T, 4, 4, 16>(ctx, tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                                 ldc, sC, count);
+        break;
+      case 1:
+        gemm_launch<T, 4, 1, 16>(ctx, tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                                 ldc, sC, count);
+        break;
+      case 2:
+        gemm_launch<T, 1, 4, 16>(ctx, tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                                 ldc, sC, count);
+        break;
+      default:
+        gemm_launch<T, 1, 1, 16>(ctx, tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                                 ldc, sC, count);
+    }
+  } else {
+    gemm_launch<T, 8, 8, 8>(ctx, tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                            sC, count);
   }
 }
 

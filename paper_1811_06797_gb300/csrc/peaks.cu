@@ -72,3 +72,34 @@ extern "C" iga_status iga_measure_fma(iga_ctx* ctx, iga_prec prec, double* tflop
     return IGA_ECUDA;
   }
 }
+
+extern "C" iga_status iga_gemm_batched(iga_ctx* ctx, iga_prec prec, int tA, int tB, int M, int N,
+                                       int K, double alpha, const void* A, int lda, long long sA,
+                                       const void* B, int ldb, long long sB, double beta, void* C,
+                                       int ldc, long long sC, int count) {
+  if (!ctx) return IGA_EINVAL;
+  try {
+    IGA_REQUIRE(M >= 0 && N >= 0 && K >= 0 && count >= 0, "gemm_batched: negative size");
+    if (M == 0 || N == 0 || count == 0) return IGA_OK;
+    IGA_REQUIRE(A && B && C, "gemm_batched: null pointer");
+    IGA_REQUIRE(lda >= (tA ? M : K) && ldb >= (tB ? K : N) && ldc >= N && lda > 0 && ldb > 0,
+                "gemm_batched: leading dimension shorter than a row");
+    AllocScope scope(ctx->stream);
+    if (prec == IGA_FP64)
+      gemm_rm_batched<double>(ctx, tA != 0, tB != 0, M, N, K, alpha, (const double*)A, lda, sA,
+                              (const double*)B, ldb, sB, beta, (double*)C, ldc, sC, count);
+    else if (prec == IGA_FP32)
+      gemm_rm_batched<float>(ctx, tA != 0, tB != 0, M, N, K, (float)alpha, (const float*)A, lda,
+                             sA, (const float*)B, ldb, sB, (float)beta, (float*)C, ldc, sC,
+                             count);
+    else
+      throw Error(IGA_EINVAL, "gemm_batched: precision must be IGA_FP64 or IGA_FP32");
+    return IGA_OK;
+  } catch (const Error& e) {
+    set_error(ctx, e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    set_error(ctx, e.what());
+    return IGA_ECUDA;
+  }
+}

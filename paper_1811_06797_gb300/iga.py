@@ -81,6 +81,8 @@ def lib():
         "iga_profile_begin": (st, [vp, C.c_char_p]),
         "iga_profile_end": (st, [vp, P(C.c_uint64), P(d), P(d), P(d)]),
         "iga_measure_fma": (st, [vp, i, P(d)]),
+        "iga_gemm_batched": (st, [vp, i, i, i, i, i, i, d, vp, i, C.c_longlong, vp, i,
+                                  C.c_longlong, d, vp, i, C.c_longlong, i]),
         "iga_sample_weights": (st, [vp, P(Geometry_), P(Space_), P(Target_), vp]),
         "iga_tt_svd": (st, [vp, vp, i, i, i, d, d, i, P(vp)]),
         "iga_tt_info": (st, [vp, P(C.c_int), P(C.c_int)]),
@@ -212,6 +214,30 @@ def iga_measure_fma(ctx, prec):
     r = C.c_double()
     _check(ctx, lib().iga_measure_fma(ctx.handle, int(prec), C.byref(r)))
     return r.value
+
+
+def iga_gemm_batched(ctx, A, B, C, alpha=1.0, beta=0.0, tA=False, tB=False):
+    """C[i] = alpha op(A[i]) op(B[i]) + beta C[i] for contiguous CUDA tensors
+    of shape (count, rows, cols), all FP64 or all FP32, through the library's
+    own dense product."""
+    import torch
+    for t in (A, B, C):
+        if not (t.is_cuda and t.is_contiguous() and t.dim() == 3):
+            raise IgaError(1, "gemm_batched: contiguous 3-d CUDA tensors expected")
+        if t.dtype != A.dtype or t.device != A.device:
+            raise IgaError(1, "gemm_batched: mixed dtypes or devices")
+    if A.dtype not in (torch.float64, torch.float32):
+        raise IgaError(1, "gemm_batched: FP64 or FP32 tensors expected")
+    count = A.shape[0]
+    M, K = (A.shape[2], A.shape[1]) if tA else (A.shape[1], A.shape[2])
+    Kb, N = (B.shape[2], B.shape[1]) if tB else (B.shape[1], B.shape[2])
+    if Kb != K or tuple(C.shape) != (count, M, N) or B.shape[0] != count:
+        raise IgaError(1, "gemm_batched: shape mismatch")
+    prec = IGA_FP64 if A.dtype == torch.float64 else IGA_FP32
+    _check(ctx, lib().iga_gemm_batched(
+        ctx.handle, prec, int(tA), int(tB), M, N, K, float(alpha), _ptr(A), A.shape[2],
+        A.shape[1] * A.shape[2], _ptr(B), B.shape[2], B.shape[1] * B.shape[2], float(beta),
+        _ptr(C), N, M * N, count))
 
 
 class _Keep:

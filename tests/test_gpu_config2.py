@@ -130,3 +130,23 @@ def test_config2_solution_matches_oracle_elementwise(setup, oracle_solutions, pr
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= bound, (name, err)
         assert np.abs(got - ref).max() <= 10 * bound * np.abs(ref).max(), name
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_config2_interpolated_weights_solution_matches_oracle(setup, prec):
+    """The same workload assembled through the paper's weight interpolation
+    (degree 2p+1 = 7) on both sides -- iga_lowrank_assemble_interp against
+    oracle/interp.py -- and solved to a residual of 1e-9: y, u and lambda agree
+    element by element within 1e-6 (both TT-SVDs at 1e-10)."""
+    from oracle.solve import interior_operators_interp, solve_kkt
+    ctx, torch, iga, work, *_ = setup
+    Mt, Kt, diag, b = interior_operators_interp(work.space, work.geometry, work.target, 1e-10)
+    yo, uo, lo, _ = solve_kkt(Mt, Kt, diag, b, work.beta, tol=1e-12)
+    M, K, load = iga.iga_lowrank_assemble_interp(ctx, work.geometry, work.space, work.target, 1e-10)
+    N = int(np.prod(M.info()["n"]))
+    y, u, lam = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+    info = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, y, u, lam, tol=1e-9, precision=prec)
+    assert info["converged"], info
+    for g, ref, name in ((y, yo, "y"), (u, uo, "u"), (lam, lo, "lam")):
+        err = np.linalg.norm(g.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= 1e-6, (name, err)
