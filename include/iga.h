@@ -390,8 +390,27 @@ iga_status iga_weight_gradient(iga_ctx* ctx, const iga_space* space, const iga_o
  * eigen-decomposition of the Gram matrix. */
 typedef enum { IGA_TRUNC_PIVOTED = 0, IGA_TRUNC_SVD = 1 } iga_trunc;
 
+/* How the solve measures its residual.  IGA_RESID_FULL (default): after
+ * every local solve the exact FP64 residual of the full KKT system is formed
+ * with the Kronecker apply; it drives the enrichment, the stopping test and
+ * an outer iterative refinement z <- z + delta.  Its cost grows with the
+ * operators' TT-matrix ranks (a KKT apply is about 2 (2p+1) N sum_blocks
+ * (R1 + R1 R2 + R2) flop per operator application).
+ * IGA_RESID_LOCAL: the method of the paper's Sec. 5 without any full-size
+ * operator apply.  The stopping test is the local residual: before each
+ * local solve, ||F_{!=d}^T (rhs - KKT z)||_2, the projection of the residual
+ * onto the current frame, computed with the FP64 interfaces; the solve stops
+ * after the sweep whose largest such value is <= tol ||rhs||_2.  The
+ * enrichment takes the residual sketched by Khatri-Rao products of Gaussian
+ * vectors (a rank-one test tensor per sketch column) through interfaces of
+ * the same kind as the local operator's.  There is no outer refinement; the
+ * full solution is expanded once at the end.  info->residual then reports
+ * that largest projected residual, a lower bound of the true one. */
+typedef enum { IGA_RESID_FULL = 0, IGA_RESID_LOCAL = 1 } iga_residual;
+
 typedef struct {
-  double tol;          /* stop when ||rhs - KKT z||_2 / ||rhs||_2 <= tol */
+  double tol;          /* stop when ||rhs - KKT z||_2 / ||rhs||_2 <= tol (the
+                          projected residual with IGA_RESID_LOCAL) */
   double inner_tol;    /* tolerance of each AMEn correction (0: tol itself) */
   int max_sweeps;      /* AMEn sweeps per correction */
   int kick_rank;       /* AMEn enrichment rank */
@@ -409,6 +428,7 @@ typedef struct {
                           the residual by less than a factor 4) */
   int truncation;      /* how the block index moves: IGA_TRUNC_PIVOTED or
                           IGA_TRUNC_SVD (see iga_trunc) */
+  int residual;        /* IGA_RESID_FULL or IGA_RESID_LOCAL (see iga_residual) */
 } iga_solve_opts;
 
 typedef struct {
@@ -444,8 +464,11 @@ iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K, co
  * The solve runs into full device vectors owned by the call, each field is
  * compressed by TT-SVD to a relative Frobenius error of opts->tol / 10, and
  * *y, *u, *lam receive library-owned TTs (NULL for a field that is exactly
- * zero); iga_tt_full expands them.  Returns what the solve returns
- * (IGA_ENOCONV with the best iterate compressed). */
+ * zero); iga_tt_full expands them.  With opts->residual IGA_RESID_LOCAL no
+ * full vector is formed: the fields are the solve's own block TT split by
+ * field (the frame cores shared, the block core's slice per field; a zero
+ * right-hand side gives rank-one zero TTs).  Returns what the solve returns
+ * (IGA_ENOCONV with the best iterate). */
 iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const iga_op* K,
                                  const iga_tt* load, double beta, const iga_solve_opts* opts,
                                  iga_tt** y, iga_tt** u, iga_tt** lam, iga_solve_info* info);

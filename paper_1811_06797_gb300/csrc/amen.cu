@@ -29,6 +29,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <memory>
 
 #include "iga_internal.cuh"
 
@@ -121,6 +122,96 @@ __global__ void kkt_combine_kernel(const T* __restrict__ Mv, const T* __restrict
   out[2 * L + i] = Kv[i] - Mv[L + i];
 }
 
+// ---- Khatri-Rao residual sketches (IGA_RESID_LOCAL)
+//
+// A sketch column kk tests the residual with the rank-one tensor
+// s_{l,kk} (x) om_1(:,kk) (x) om_2(:,kk) (x) om_3(:,kk) (field weight s and
+// one Gaussian vector per direction), so its products with the operator and
+// the TT reduce to interfaces of the same kind as the local operator's.
+
+// out[g][kk][c] = sum_j om[j k + kk] w[g sg + kk sk + j sj + c sc]
+__global__ void kr_reduce_kernel(const double* __restrict__ w, const double* __restrict__ om,
+                                 int G, int k, int C, int n, long long sg, long long sk,
+                                 long long sj, long long sc, double* __restrict__ out) {
+  const long long total = (long long)G * k * C;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % C);
+    const long long q = idx / C;
+    const int kk = (int)(q % k);
+    const int g = (int)(q / k);
+    const double* p = w + g * sg + kk * sk + c * sc;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc = fma(om[(size_t)j * k + kk], p[j * sj], acc);
+    out[idx] = acc;
+  }
+}
+
+// forward sketch: Et[kk][q] = sum_l s[l][kk] (Fw - O)[l][q][kk], q < m
+__global__ void kr_combine_fwd_kernel(const double* __restrict__ Fw, const double* __restrict__ O,
+                                      const double* __restrict__ sw, int m, int k,
+                                      double* __restrict__ Et) {
+  const long long total = (long long)k * m;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % m);
+    const int kk = (int)(idx / m);
+    double acc = 0.0;
+    for (int l = 0; l < 3; ++l) {
+      const size_t e = ((size_t)l * m + q) * k + kk;
+      acc = fma(sw[l * k + kk], Fw[e] - O[e], acc);
+    }
+    Et[idx] = acc;
+  }
+}
+
+// backward sketch: Et[kk][q] = sum_l s[l][kk] (Fw - O)[l][kk][q], q < m
+__global__ void kr_combine_bwd_kernel(const double* __restrict__ Fw, const double* __restrict__ O,
+                                      const double* __restrict__ sw, int m, int k,
+                                      double* __restrict__ Et) {
+  const long long total = (long long)k * m;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % m);
+    const int kk = (int)(idx / m);
+    double acc = 0.0;
+    for (int l = 0; l < 3; ++l) {
+      const size_t e = ((size_t)l * k + kk) * m + q;
+      acc = fma(sw[l * k + kk], Fw[e] - O[e], acc);
+    }
+    Et[idx] = acc;
+  }
+}
+
+// O[v][kk][q] = sum_{al < G} sum_{a < r0} Psi[al][kk][a] t[al][v][a][q] for
+// the three fields v, q < m; every thread keeps the k (<= 16) sums of one
+// (v, q) and reads t once
+__global__ void kr_left_apply_kernel(const double* __restrict__ Psi, const double* __restrict__ t,
+                                     int G, int k, int r0, int m, double* __restrict__ O) {
+  const long long total = 3LL * m;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % m);
+    const int v = (int)(idx / m);
+    double acc[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc[kk] = 0.0;
+    for (int al = 0; al < G; ++al) {
+      const double* ps = Psi + (size_t)al * k * r0;
+      const double* tp = t + (((size_t)al * 3 + v) * r0) * m + q;
+      for (int a = 0; a < r0; ++a) {
+        const double x = tp[(size_t)a * m];
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk)
+          if (kk < k) acc[kk] = fma(ps[kk * r0 + a], x, acc[kk]);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk)
+      if (kk < k) O[((size_t)v * k + kk) * m + q] = acc[kk];
+  }
+}
+
 // (3, r, n, r1) block core -> row-major ((a,i) x (l,b)) matrix
 __global__ void permute_fwd_kernel(const double* __restrict__ Xh, int r, int n, int r1,
                                    double* __restrict__ Mx) {
@@ -201,8 +292,6 @@ __global__ void sum_slices_kernel(const double* __restrict__ P, int S, int r,
   if (idx >= r * r) return;
   double acc = 0.0;
   for (int s = 0; s < S; ++s) acc += P[(size_t)s * r * r + idx];
-  int a = idx / r, b = idx % r;
-  (void)a; (void)b;
   out[idx] = acc;
 }
 
@@ -1164,6 +1253,12 @@ struct Solver {
   int local_iters = 0;
   uint64_t seed = 0x51ed2701ull;
   int verbose = 0;
+  // IGA_RESID_LOCAL: Khatri-Rao sketch interfaces and the local residual
+  bool kr_mode = false;
+  int kr_k = 0;                        // sketch columns of the current draw
+  DevBuf<double> Om[3], Sw;            // om_d (n_d x k, row-major), s (3 x k)
+  DevBuf<double> PsiR[2][3], PsiL[2][3];   // (R, k, r) sketch interfaces at core d
+  double last_local_res = 0.0;         // ||F_{!=d}^T (F - KKT z)|| before the last local solve
 
   // ---- small helpers
   double* slot(int k, size_t n) { return scratch<double>(ctx, SLOT_AMEN_BASE + k, n); }
@@ -1279,6 +1374,10 @@ struct Solver {
   // Gaussian sketch of the residual projected on the left frame (forward) or
   // right frame (backward) of core d; returns E^T row-major (kick x m)
   void sketch(const double* res, int d, bool forward, double* Et, int m) {
+    if (kr_mode) {
+      kr_sketch(d, forward, Et, m);
+      return;
+    }
     int n1 = n[0], n2 = n[1], n3 = n[2];
     int k = kick;
     if (forward && d == 0) {
@@ -1319,6 +1418,155 @@ struct Solver {
     coldot(ctx, Om, k, s, n2 * r[2], 0LL, 3 * n1, k, n2 * r[2], 1, Et, n2 * r[2], 0LL,
            SLOT_AMEN_BASE + 36);
     (void)m;
+  }
+
+  // ---- Khatri-Rao sketches of the residual (IGA_RESID_LOCAL) -------------
+  const double* Fsk = nullptr;         // the right-hand side (3, N), full
+
+  // new Gaussian vectors om_d and field weights s, kr_k = kick columns
+  void kr_draw() {
+    kr_k = std::min(kick, 16);
+    for (int d = 0; d < 3; ++d) {
+      Om[d].ensure((size_t)n[d] * kr_k);
+      fill_gaussian(ctx, Om[d].p, (size_t)n[d] * kr_k, seed++);
+    }
+    Sw.ensure((size_t)3 * kr_k);
+    fill_gaussian(ctx, Sw.p, (size_t)3 * kr_k, seed++);
+  }
+  void kr_ones(DevBuf<double>& b) {
+    b.ensure(kr_k);
+    std::vector<double> one(kr_k, 1.0);
+    IGA_CUDA(cudaMemcpyAsync(b.p, one.data(), kr_k * 8, cudaMemcpyHostToDevice, ctx->stream));
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  void kr_reduce(const double* w, const double* om, int G, int C, int nn, long long sg,
+                 long long sk, long long sj, long long sc, double* out) {
+    const long long tot = (long long)G * kr_k * C;
+    IGA_LAUNCH(ctx, kr_reduce_kernel, (unsigned)std::min<long long>((tot + 255) / 256, 8 * 152),
+               256, 0, w, om, G, kr_k, C, nn, sg, sk, sj, sc, out);
+  }
+  // PsiR[o][d-1] (R0, k, r0) from PsiR[o][d] (R1, k, r1) and X[d]:
+  // PsiR[al](kk, a) = sum_{i,j,b} om_d(i,kk) A_d^{al,be}(i,j) X_d(a,j,b) PsiR[be](kk,b)
+  void kr_right_update(int o, int d) {
+    const CoreNZ& c = nz[o][d];
+    const int r0 = r[d], nn = n[d], r1 = r[d + 1], k = kr_k;
+    const size_t per = (size_t)r0 * nn * k;
+    double* u = slot(90, per * c.R1);
+    double* w = slot(91, per * c.R0);
+    rm_gemm_batched(ctx, false, true, r0 * nn, k, r1, X[d].p, r1, 0, PsiR[o][d].p, r1,
+                    (long long)k * r1, u, k, (long long)per, c.R1);
+    IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R0 * per), 256, 0, op[o]->band64[d].p,
+               c.rowptr.p, c.rowsrc.p, c.rowoff.p, u, c.R0, r0, nn, k, op[o]->p[d], w);
+    PsiR[o][d - 1].ensure((size_t)c.R0 * k * r0);
+    kr_reduce(w, Om[d].p, c.R0, r0, nn, (long long)per, 1, k, (long long)nn * k,
+              PsiR[o][d - 1].p);
+  }
+  // PsiL[o][d+1] (R1, k, r1) from PsiL[o][d] (R0, k, r0) and X[d]:
+  // PsiL[be](kk, b) = sum_{i,j,a} PsiL[al](kk,a) om_d(i,kk) A_d^{al,be}(i,j) X_d(a,j,b)
+  void kr_left_update(int o, int d) {
+    const CoreNZ& c = nz[o][d];
+    const int r0 = r[d], nn = n[d], r1 = r[d + 1], k = kr_k;
+    const size_t per = (size_t)k * nn * r1;
+    double* u = slot(90, per * c.R0);
+    double* w = slot(91, per * c.R1);
+    rm_gemm_batched(ctx, false, false, k, nn * r1, r0, PsiL[o][d].p, r0, (long long)k * r0,
+                    X[d].p, nn * r1, 0, u, nn * r1, (long long)per, c.R0);
+    IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(c.R1 * per), 256, 0, op[o]->band64[d].p,
+               c.colptr.p, c.colsrc.p, c.coloff.p, u, c.R1, k, nn, r1, op[o]->p[d], w);
+    PsiL[o][d + 1].ensure((size_t)c.R1 * k * r1);
+    kr_reduce(w, Om[d].p, c.R1, r1, nn, (long long)per, (long long)nn * r1, r1, 1,
+              PsiL[o][d + 1].p);
+  }
+  // a new draw and the right sketch interfaces of every core (forward sweep;
+  // cores 1 and 2 right-orthogonal, the block index at core 0)
+  void kr_right_all() {
+    kr_draw();
+    for (int o = 0; o < 2; ++o) {
+      kr_ones(PsiR[o][2]);
+      kr_right_update(o, 2);
+      kr_right_update(o, 1);
+    }
+  }
+  // a new draw and the left sketch interfaces (backward sweep; cores 0 and 1
+  // left-orthogonal, the block index at core 2)
+  void kr_left_all() {
+    kr_draw();
+    for (int o = 0; o < 2; ++o) {
+      kr_ones(PsiL[o][0]);
+      kr_left_update(o, 0);
+      kr_left_update(o, 1);
+    }
+  }
+  // the sketch E^T (kick x m, row-major) of the residual F - KKT z projected
+  // on the left frame of core d (forward, m = r_d n_d) or its right frame
+  // (backward, m = n_d r_{d+1}); the first `kick` of the kr_k columns
+  void kr_sketch(int d, bool forward, double* Et, int m) {
+    const int r0 = r[d], nn = n[d], r1 = r[d + 1], k = kr_k;
+    const int n1 = n[0], n2 = n[1], n3 = n[2];
+    IGA_REQUIRE(kick <= k, "amen: sketch width");
+    const size_t L = (size_t)r0 * nn * r1;
+    double* Mv = slot(92, 3 * (size_t)m * k);
+    double* Kv = slot(93, 3 * (size_t)m * k);
+    double* O = slot(94, 3 * (size_t)m * k);
+    double* Fw = slot(95, 3 * (size_t)m * k);
+    double* E = slot(96, (size_t)m * k);
+    if (forward) {
+      // O[v](a, i, kk) = sum PhiL[al](a,a') A^{al,be}(i,j) Xh[v](a',j,b) PsiR[be](kk,b)
+      for (int o = 0; o < 2; ++o) {
+        const CoreNZ& z = nz[o][d];
+        const size_t per = (size_t)3 * r0 * nn * k;
+        double* t1 = slot(97, per * z.R1);
+        double* t2 = slot(98, per * z.R0);
+        rm_gemm_batched(ctx, false, true, 3 * r0 * nn, k, r1, Xh.p, r1, 0, PsiR[o][d].p, r1,
+                        (long long)k * r1, t1, k, (long long)per, z.R1);
+        IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(per * z.R0), 256, 0, op[o]->band64[d].p,
+                   z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, 3 * r0, nn, k, op[o]->p[d], t2);
+        left_mult<double>(PhiL[o][d].p, t2, z.R0, 3, r0, nn, k, 0, o ? Kv : Mv);
+      }
+      IGA_LAUNCH(ctx, kkt_combine_kernel<double>, nblk((size_t)m * k), 256, 0, Mv, Kv,
+                 (size_t)m * k, beta, O);
+      // Fw[l](a, i, kk) = (X_{<d}^T (x) I (x) om_{>d}(kk)^T) F_l
+      double* T1 = slot(99, (size_t)3 * n1 * n2 * k);
+      rm_gemm_batched(ctx, false, false, n1 * n2, k, n3, Fsk, n3, (long long)N, Om[2].p, k, 0, T1,
+                      k, (long long)n1 * n2 * k, 3);
+      if (d == 0) {
+        kr_reduce(T1, Om[1].p, 3 * n1, 1, n2, (long long)n2 * k, 1, k, 0, Fw);
+      } else {
+        rm_gemm_batched(ctx, true, false, r[1], n2 * k, n1, X[0].p, r[1], 0, T1, n2 * k,
+                        (long long)n1 * n2 * k, Fw, n2 * k, (long long)r[1] * n2 * k, 3);
+      }
+      IGA_LAUNCH(ctx, kr_combine_fwd_kernel, nblk((size_t)m * k), 256, 0, Fw, O, Sw.p, m, k, E);
+    } else {
+      // O[v](kk, i, b) = sum PsiL[al](kk,a) A^{al,be}(i,j) Xh[v](a,j,b') PhiR[be](b,b')
+      for (int o = 0; o < 2; ++o) {
+        const CoreNZ& z = nz[o][d];
+        const size_t per = 3 * L;
+        double* t1 = slot(97, per * z.R1);
+        double* t2 = slot(98, per * z.R0);
+        right_mult<double>(PhiR[o][d].p, Xh.p, z.R1, 3, r0, nn, r1, 0, t1);
+        IGA_LAUNCH(ctx, band_group_kernel<double>, nblk(per * z.R0), 256, 0, op[o]->band64[d].p,
+                   z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, 3 * r0, nn, r1, op[o]->p[d], t2);
+        IGA_LAUNCH(ctx, kr_left_apply_kernel, nblk(3 * (size_t)m), 256, 0, PsiL[o][d].p, t2,
+                   z.R0, k, r0, m, o ? Kv : Mv);
+      }
+      IGA_LAUNCH(ctx, kkt_combine_kernel<double>, nblk((size_t)m * k), 256, 0, Mv, Kv,
+                 (size_t)m * k, beta, O);
+      // Fw[l](kk, i, b) = (om_{<d}(kk)^T (x) I (x) X_{>d}^T) F_l
+      if (d == 2) {
+        double* T1 = slot(99, (size_t)3 * k * n2 * n3);
+        rm_gemm_batched(ctx, true, false, k, n2 * n3, n1, Om[0].p, k, 0, Fsk, n2 * n3,
+                        (long long)N, T1, n2 * n3, (long long)k * n2 * n3, 3);
+        kr_reduce(T1, Om[1].p, 3, n3, n2, (long long)k * n2 * n3, (long long)n2 * n3, n3, 1, Fw);
+      } else {
+        double* S1 = slot(99, (size_t)3 * n1 * n2 * r[2]);
+        rm_gemm_batched(ctx, false, true, n1 * n2, r[2], n3, Fsk, n3, (long long)N, X[2].p, n3,
+                        0, S1, r[2], (long long)n1 * n2 * r[2], 3);
+        rm_gemm_batched(ctx, true, false, k, n2 * r[2], n1, Om[0].p, k, 0, S1, n2 * r[2],
+                        (long long)n1 * n2 * r[2], Fw, n2 * r[2], (long long)k * n2 * r[2], 3);
+      }
+      IGA_LAUNCH(ctx, kr_combine_bwd_kernel, nblk((size_t)m * k), 256, 0, Fw, O, Sw.p, m, k, E);
+    }
+    IGA_CUDA(cudaMemcpyAsync(Et, E, (size_t)kick * m * 8, cudaMemcpyDeviceToDevice, ctx->stream));
   }
 
   // truncation rank from descending eigenvalues of a Gram matrix
@@ -1853,6 +2101,14 @@ struct Solver {
         PRp[o] = PRt[o].p;
       }
     }
+    if (kr_mode) {
+      // projected residual of the current iterate, FP64 interfaces and bands
+      double* r64 = slot(15 + 60, per);
+      double* ax = slot(16 + 60, per);
+      local_op64(c, Xh.p, ax);
+      IGA_LAUNCH(ctx, sub_kernel, nblk(per), 256, 0, rhs, ax, r64, per);
+      last_local_res = device_norm2(ctx, r64, per);
+    }
     precond_setup(c);
     // warm start from the current block core
     Xh.ensure(per);
@@ -1928,12 +2184,12 @@ static double kkt_residual(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   return device_norm2(ctx, res, 3 * N);
 }
 
+// A solver on (M, K, beta) with a random initial TT of rank kick_rank,
+// right-orthogonal, the block index at core 0 (zero block core), and the
+// right interfaces of both operators
 template <typename T>
-static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
-                           const double* F, double Fnorm, double tol, const iga_solve_opts* o,
-                           double* delta, int* sweeps_out, int* maxrank, int* liters, double* resid,
-                           PhaseClock* clk) {
-  Solver<T> S;
+static void solver_init(Solver<T>& S, iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                        double beta, double tol, const iga_solve_opts* o) {
   S.ctx = ctx;
   S.op[0] = M;
   S.op[1] = K;
@@ -1949,7 +2205,6 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   S.svd_moves = o->truncation == IGA_TRUNC_SVD;
   S.tc_local = o->precision == IGA_TF32;
   S.verbose = o->verbose;
-  size_t N = S.N;
   for (int op = 0; op < 2; ++op)
     for (int d = 0; d < 3; ++d) build_core_nz(ctx, S.op[op], d, S.nz[op][d]);
   // initial TT: rank kick Gaussian cores, right-orthogonalised by QR; block index at core 0
@@ -1983,6 +2238,16 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
     S.right_update(op, 2);
     S.right_update(op, 1);
   }
+}
+
+template <typename T>
+static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                           const double* F, double Fnorm, double tol, const iga_solve_opts* o,
+                           double* delta, int* sweeps_out, int* maxrank, int* liters, double* resid,
+                           PhaseClock* clk) {
+  Solver<T> S;
+  solver_init(S, ctx, M, K, beta, tol, o);
+  const size_t N = S.N;
   double* res = S.slot(15, 3 * N);
   double rel = 1.0;
   int sweep = 0;
@@ -2039,6 +2304,94 @@ done:
   return rel <= tol;
 }
 
+// IGA_RESID_LOCAL: block AMEn on KKT z = F without any full-size operator
+// apply.  Every sweep draws new Khatri-Rao sketch vectors and builds their
+// interfaces on the side the sweep moves into; before each local solve the
+// projected residual is measured (FP64); the solve stops after the sweep
+// whose largest projected residual is <= tol ||F||.  On return z (3N, may be
+// null) holds the expanded solution and out[l] (may be null) the TT of field
+// l (y, u, lambda), the block core split by field.
+template <typename T>
+static bool amen_local(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                       const double* F, double Fnorm, const iga_solve_opts* o, double* z,
+                       iga_tt* out[3], iga_solve_info* inf, PhaseClock* clk) {
+  Solver<T> S;
+  const double tol = o->tol;
+  solver_init(S, ctx, M, K, beta, tol, o);
+  S.kr_mode = true;
+  S.Fsk = F;
+  const int maxsw = std::max(1, o->max_sweeps);
+  const double tol_abs = 0.1 * tol * Fnorm;
+  const int maxit = std::max(1, o->local_maxit);
+  const bool adapt = !(o->trunc_tol > 0.0);
+  const double trunc_floor = 1e-5 * tol;
+  double rel = std::numeric_limits<double>::infinity();
+  double rel_prev = rel;
+  int sweep = 0, last = 0;
+  for (sweep = 0; sweep < maxsw; ++sweep) {
+    const bool fwd = (sweep % 2) == 0;
+    int order[3] = {0, 1, 2};
+    if (!fwd) { order[0] = 2; order[2] = 0; }
+    clk->mark(PH_MOVE);
+    if (fwd) S.kr_right_all();
+    else S.kr_left_all();
+    double worst = 0.0;
+    for (int s = 0; s < 3; ++s) {
+      const int d = order[s];
+      if (sweep > 0 && s == 0) {
+        // the first core of this sweep was solved last in the previous sweep
+        clk->mark(PH_MOVE);
+        if (fwd) S.move_forward(d, nullptr);
+        else S.move_backward(d, nullptr);
+        continue;
+      }
+      clk->mark(PH_LOCAL);
+      S.local_solve(d, F, tol_abs, maxit);
+      worst = std::max(worst, S.last_local_res);
+      last = d;
+      if (S.verbose)
+        fprintf(stderr, "[amen-local] sweep %d core %d ranks (%d,%d) local_it %d proj. resid %.3e\n",
+                sweep, d, S.r[1], S.r[2], S.local_iters, S.last_local_res / Fnorm);
+      if (s < 2) {
+        clk->mark(PH_MOVE);
+        if (fwd) S.move_forward(d, nullptr);
+        else S.move_backward(d, nullptr);
+      }
+    }
+    rel = worst / Fnorm;
+    if (rel <= tol) { ++sweep; break; }
+    if (adapt && sweep >= 1 && rel > 0.25 * rel_prev && S.trunc_tol > trunc_floor) {
+      S.trunc_tol = std::max(0.01 * S.trunc_tol, trunc_floor);
+      if (S.verbose) fprintf(stderr, "[amen-local] truncation tolerance -> %.1e\n", S.trunc_tol);
+    }
+    rel_prev = rel;
+  }
+  clk->mark(PH_REFINE);
+  if (z) S.expand(last, z);
+  if (out) {
+    const size_t L = (size_t)S.r[last] * S.n[last] * S.r[last + 1];
+    for (int l = 0; l < 3; ++l) {
+      std::unique_ptr<iga_tt> t(new iga_tt());
+      for (int d = 0; d < 3; ++d) t->n[d] = S.n[d];
+      t->r[0] = S.r[1];
+      t->r[1] = S.r[2];
+      for (int d = 0; d < 3; ++d) {
+        const size_t cnt = (size_t)S.r[d] * S.n[d] * S.r[d + 1];
+        t->core[d].alloc(cnt);
+        const double* src = d == last ? S.Xh.p + l * L : S.X[d].p;
+        IGA_CUDA(cudaMemcpyAsync(t->core[d].p, src, cnt * 8, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+      }
+      out[l] = t.release();
+    }
+  }
+  inf->sweeps += sweep;
+  inf->max_rank = std::max(inf->max_rank, std::max(S.r[1], S.r[2]));
+  inf->local_iters += S.local_iters;
+  inf->residual = rel;
+  return rel <= tol;
+}
+
 }  // namespace iga
 
 using namespace iga;
@@ -2058,15 +2411,17 @@ extern "C" void iga_solve_opts_default(iga_solve_opts* o) {
   o->truncation = IGA_TRUNC_PIVOTED;
 }
 
-extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K,
-                                         const iga_tt* load, double beta,
-                                         const iga_solve_opts* opts, double* y, double* u,
-                                         double* lam, iga_solve_info* info) {
+// The solve behind both entry points: the fields into y, u, lam (full
+// vectors, device) or, with tt_out (IGA_RESID_LOCAL only), as TT handles.
+static iga_status kkt_solve_impl(iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                                 const iga_tt* load, double beta, const iga_solve_opts* opts,
+                                 double* y, double* u, double* lam, iga_tt** tt_out,
+                                 iga_solve_info* info) {
   if (!ctx) return IGA_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
   try {
     AllocScope scope(ctx->stream);
-    IGA_REQUIRE(M && K && y && u && lam, "kkt_solve_amen: null argument");
+    IGA_REQUIRE(M && K && ((y && u && lam) || tt_out), "kkt_solve_amen: null argument");
     IGA_REQUIRE(beta > 0.0, "kkt_solve_amen: beta must be positive");
     for (int d = 0; d < 3; ++d)
       IGA_REQUIRE(M->n[d] == K->n[d] && M->p[d] == K->p[d], "kkt_solve_amen: M, K mismatch");
@@ -2077,14 +2432,21 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
                 "kkt_solve_amen: unknown truncation");
     IGA_REQUIRE(o.precision == IGA_FP64 || o.precision == IGA_FP32 || o.precision == IGA_TF32,
                 "kkt_solve_amen: precision must be IGA_FP64, IGA_FP32 or IGA_TF32");
+    IGA_REQUIRE(o.residual == IGA_RESID_FULL || o.residual == IGA_RESID_LOCAL,
+                "kkt_solve_amen: residual must be IGA_RESID_FULL or IGA_RESID_LOCAL");
+    IGA_REQUIRE(!tt_out || o.residual == IGA_RESID_LOCAL, "kkt_solve_amen: TT output mode");
+    IGA_REQUIRE(o.residual != IGA_RESID_LOCAL || o.kick_rank <= 16,
+                "kkt_solve_amen: kick_rank above 16 with IGA_RESID_LOCAL");
+    const bool local = o.residual == IGA_RESID_LOCAL;
     size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
-    // rhs F = [b; 0; 0] (full FP64); z = 0
+    // rhs F = [b; 0; 0] (full FP64); z = 0 (the full-residual mode also keeps
+    // a correction and a residual; the TT output needs no full solution)
     double* F = scratch<double>(ctx, SLOT_AMEN_BASE - 4, 3 * N);
-    double* z = scratch<double>(ctx, SLOT_AMEN_BASE - 3, 3 * N);
-    double* delta = scratch<double>(ctx, SLOT_AMEN_BASE - 2, 3 * N);
-    double* r = scratch<double>(ctx, SLOT_AMEN_BASE - 1, 3 * N);
+    double* z = tt_out ? nullptr : scratch<double>(ctx, SLOT_AMEN_BASE - 3, 3 * N);
+    double* delta = local ? nullptr : scratch<double>(ctx, SLOT_AMEN_BASE - 2, 3 * N);
+    double* r = local ? nullptr : scratch<double>(ctx, SLOT_AMEN_BASE - 1, 3 * N);
     IGA_CUDA(cudaMemsetAsync(F, 0, 3 * N * 8, ctx->stream));
-    IGA_CUDA(cudaMemsetAsync(z, 0, 3 * N * 8, ctx->stream));
+    if (z) IGA_CUDA(cudaMemsetAsync(z, 0, 3 * N * 8, ctx->stream));
     if (load) {
       for (int d = 0; d < 3; ++d)
         IGA_REQUIRE(load->n[d] == M->n[d], "kkt_solve_amen: load size mismatch");
@@ -2096,7 +2458,25 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
     clk.stream = ctx->stream;
     double rel = 0.0;
     bool ok = Fn == 0.0;
-    if (!ok) {
+    if (ok && tt_out) {
+      // zero right-hand side: the zero solution as rank-one TTs
+      for (int l = 0; l < 3; ++l) {
+        std::unique_ptr<iga_tt> t(new iga_tt());
+        for (int d = 0; d < 3; ++d) {
+          t->n[d] = M->n[d];
+          t->core[d].alloc(M->n[d]);
+          IGA_CUDA(cudaMemsetAsync(t->core[d].p, 0, (size_t)M->n[d] * 8, ctx->stream));
+        }
+        tt_out[l] = t.release();
+      }
+    }
+    if (!ok && o.residual == IGA_RESID_LOCAL) {
+      if (o.precision == IGA_FP64)
+        ok = amen_local<double>(ctx, M, K, beta, F, Fn, &o, z, tt_out, &inf, &clk);
+      else
+        ok = amen_local<float>(ctx, M, K, beta, F, Fn, &o, z, tt_out, &inf, &clk);
+      rel = inf.residual;
+    } else if (!ok) {
       double rn = Fn;
       IGA_CUDA(cudaMemcpyAsync(r, F, 3 * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
       double inner = std::max(o.inner_tol, o.tol);
@@ -2125,9 +2505,11 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
       rel = rn / Fn;
       ok = rel <= o.tol;
     }
-    IGA_CUDA(cudaMemcpyAsync(y, z, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-    IGA_CUDA(cudaMemcpyAsync(u, z + N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-    IGA_CUDA(cudaMemcpyAsync(lam, z + 2 * N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (z) {
+      IGA_CUDA(cudaMemcpyAsync(y, z, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+      IGA_CUDA(cudaMemcpyAsync(u, z + N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+      IGA_CUDA(cudaMemcpyAsync(lam, z + 2 * N, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     clk.mark(-1);
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
     double ph[PH_COUNT] = {0.0, 0.0, 0.0, 0.0};
@@ -2153,6 +2535,13 @@ extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const ig
   }
 }
 
+extern "C" iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                                         const iga_tt* load, double beta,
+                                         const iga_solve_opts* opts, double* y, double* u,
+                                         double* lam, iga_solve_info* info) {
+  return kkt_solve_impl(ctx, M, K, load, beta, opts, y, u, lam, nullptr, info);
+}
+
 // The same solve with the solution returned as TT tensors (Sec. 5: the
 // block-AMEn solution is a block TT, eq. btt).  The solve runs into full
 // device vectors owned by the call; each field is then compressed by TT-SVD
@@ -2163,6 +2552,20 @@ extern "C" iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const
                                             iga_tt** lam, iga_solve_info* info) {
   if (!ctx || !y || !u || !lam || !M) return IGA_EINVAL;
   *y = *u = *lam = nullptr;
+  if (opts && opts->residual == IGA_RESID_LOCAL) {
+    // the block TT of the solve itself, split by field
+    iga_tt* out[3] = {nullptr, nullptr, nullptr};
+    iga_status st = kkt_solve_impl(ctx, M, K, load, beta, opts, nullptr, nullptr, nullptr, out,
+                                   info);
+    if (st != IGA_OK && st != IGA_ENOCONV) {
+      for (int f = 0; f < 3; ++f) delete out[f];
+      return st;
+    }
+    *y = out[0];
+    *u = out[1];
+    *lam = out[2];
+    return st;
+  }
   try {
     AllocScope scope(ctx->stream);
     const size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];

@@ -19,6 +19,7 @@ _lib = None
 
 IGA_FP64, IGA_FP32, IGA_TF32, IGA_BF16 = 0, 1, 2, 3
 IGA_TRUNC_PIVOTED, IGA_TRUNC_SVD = 0, 1
+IGA_RESID_FULL, IGA_RESID_LOCAL = 0, 1
 STATUS = {0: "IGA_OK", 1: "IGA_EINVAL", 2: "IGA_ENOMEM", 3: "IGA_ECUDA", 4: "IGA_ENOCONV",
           5: "IGA_ENONFINITE", 6: "IGA_ETIMEOUT"}
 
@@ -48,7 +49,7 @@ class SolveOpts_(C.Structure):
     _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("max_sweeps", C.c_int),
                 ("kick_rank", C.c_int), ("rmax", C.c_int), ("local_maxit", C.c_int),
                 ("refine_max", C.c_int), ("precision", C.c_int), ("verbose", C.c_int),
-                ("trunc_tol", C.c_double), ("truncation", C.c_int)]
+                ("trunc_tol", C.c_double), ("truncation", C.c_int), ("residual", C.c_int)]
 
 
 class SolveInfo_(C.Structure):
