@@ -77,8 +77,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--roofline-kernel", default="auto",
                     help="kernel name for the roofline entry, or auto (largest device time)")
-    ap.add_argument("--only", default=None, choices=["ttm"],
-                    help="ttm: only the tensor-core TT apply measurement (a profiling case)")
+    ap.add_argument("--only", default=None, choices=["ttm", "c5solve"],
+                    help="ttm: only the tensor-core TT apply measurement (a profiling case); "
+                         "c5solve: only the random-volume solve without full-size applies")
+    ap.add_argument("--c5-tol", type=float, default=1e-4)
+    ap.add_argument("--c5-trunc", type=float, default=1e-6)
+    ap.add_argument("--c5-sweeps", type=int, default=4)
     ap.add_argument("--ttm-elements", type=int, default=512,
                     help="elements per direction of the --only ttm grid")
     ap.add_argument("--ttm-kinds", default="tf32,bf16", help="operand types of --only ttm")
@@ -418,6 +422,50 @@ def config5_assembly(ctx, iga, torch):
     return out
 
 
+def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, rows=512):
+    """The random-volume KKT solve (degree 2, 512 elements per direction,
+    beta 1e-6, 1.34e8 unknowns per field) without any full-size operator
+    apply (IGA_RESID_LOCAL, the solution as the block TT), mixed precision:
+    wall time of the solve, its sweeps, ranks and projected residual, and the
+    true relative residual estimated from `rows` uniformly sampled rows of
+    the three KKT equations (iga_kkt_residual_rows)."""
+    import numpy as np
+    from paper_1811_06797_gb300 import workloads as wl
+    work = wl.config(5)
+    M, K, load = iga.iga_lowrank_assemble_interp(ctx, work.geometry, work.space, work.target,
+                                                 work.tol)
+    ni = M.info()["n"]
+    N = int(np.prod(ni))
+    bfull = torch.empty(ni, dtype=torch.float64, device="cuda")
+    load.full(ctx, bfull)
+    bnorm = float(bfull.norm())
+    del bfull
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(5120)
+    pts = np.stack([rng.integers(0, ni[d], rows) for d in range(3)], axis=1)
+    out = {"workload": work.name, "unknowns_per_field": N, "beta": work.beta,
+           "residual_mode": "projected residuals, Khatri-Rao sketches (IGA_RESID_LOCAL)",
+           "tol_projected": tol, "trunc_tol": trunc_tol}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ty, tu, tl, info = iga.iga_kkt_solve_amen_tt(ctx, M, K, load, work.beta, tol=tol,
+                                                 precision=iga.IGA_FP32,
+                                                 residual=iga.IGA_RESID_LOCAL,
+                                                 max_sweeps=max_sweeps, trunc_tol=trunc_tol)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    res = iga.iga_kkt_residual_rows(ctx, M, K, work.beta, load, ty, tu, tl, pts)
+    est = float(np.sqrt(N / rows * np.sum(res ** 2)) / bnorm)
+    out["mixed"] = {"solve_s": t, "sweeps": info["sweeps"], "max_rank": info["max_rank"],
+                    "local_iters": info["local_iters"],
+                    "projected_residual": info["residual"], "converged": info["converged"],
+                    "residual_estimate": est, "rows_sampled": rows,
+                    "device_s_by_phase": {"local": info["t_local"], "move": info["t_move"]}}
+    del M, K, load, ty, tu, tl
+    torch.cuda.empty_cache()
+    return out
+
+
 def rank_tables(ctx):
     """TT ranks of the seven sampled weights at the tolerances of the paper's
     rank tables (Sec. 6) on the two curved synthetic geometries, degree 2,
@@ -722,6 +770,15 @@ def main():
                            elements=args.ttm_elements, kinds=tuple(args.ttm_kinds.split(",")))
         if rank == 0:
             print(json.dumps({"ttm_roofline": out}))
+        return
+    if args.only == "c5solve":
+        import torch
+        from paper_1811_06797_gb300 import build, iga
+        build.build()
+        torch.cuda.set_device(local)
+        out = config5_solve(iga.Context(), iga, torch, args.c5_tol, args.c5_trunc, args.c5_sweeps)
+        if rank == 0:
+            print(json.dumps({"config5_solve": out}))
         return
     line, work, solutions = run_gpu(args, world, rank, local)
     if rank == 0:

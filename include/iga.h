@@ -405,7 +405,9 @@ typedef enum { IGA_TRUNC_PIVOTED = 0, IGA_TRUNC_SVD = 1 } iga_trunc;
  * vectors (a rank-one test tensor per sketch column) through interfaces of
  * the same kind as the local operator's.  There is no outer refinement; the
  * full solution is expanded once at the end.  info->residual then reports
- * that largest projected residual, a lower bound of the true one. */
+ * the largest projected residual of the last sweep (each measured before its
+ * local solve, and each a lower bound of the true residual of the iterate
+ * at that moment). */
 typedef enum { IGA_RESID_FULL = 0, IGA_RESID_LOCAL = 1 } iga_residual;
 
 typedef struct {
@@ -423,9 +425,10 @@ typedef struct {
                           operands and FP32 accumulation) */
   int verbose;         /* print one line per sweep to stderr */
   double trunc_tol;    /* relative truncation of each field in the block core
-                          when the block index moves (0: tol / 1000, lowered
-                          100-fold down to tol * 1e-5 whenever a sweep reduces
-                          the residual by less than a factor 4) */
+                          when the block index moves (0: tol / 1000; with
+                          IGA_RESID_FULL lowered 100-fold down to tol * 1e-5
+                          whenever a sweep reduces the residual by less than a
+                          factor 4, with IGA_RESID_LOCAL kept fixed) */
   int truncation;      /* how the block index moves: IGA_TRUNC_PIVOTED or
                           IGA_TRUNC_SVD (see iga_trunc) */
   int residual;        /* IGA_RESID_FULL or IGA_RESID_LOCAL (see iga_residual) */
@@ -458,6 +461,23 @@ void iga_solve_opts_default(iga_solve_opts* opts);
 iga_status iga_kkt_solve_amen(iga_ctx* ctx, const iga_op* M, const iga_op* K, const iga_tt* load,
                               double beta, const iga_solve_opts* opts, double* y, double* u,
                               double* lam, iga_solve_info* info);
+
+/* Rows of the KKT residual (Sec. 4, eq. KKTSystem, one time step) for a
+ * solution held as TTs, without forming anything of full size: for each of
+ * the nrows interior multi-indices rows[3s .. 3s+2] (0-based, i_d < n_d;
+ * host int32) res[3s + e] (host) receives equation e's residual,
+ *   e = 0: b_i - (M y)_i - (K lambda)_i,
+ *   e = 1: -(beta (M u)_i - (M lambda)_i),
+ *   e = 2: -((K y)_i - (M u)_i),
+ * with every operator entry formed from the univariate bands over the row's
+ * (2p+1)^3 stencil and every solution value from the TT cores (FP64).  load
+ * may be NULL (b = 0).  Uniformly sampled rows estimate ||rhs - KKT z||_2^2
+ * without bias as (N / S) sum_s sum_e res[3s+e]^2.  IGA_EINVAL for a row
+ * outside the interior grid, mismatched sizes or a degree above 4.
+ * Synchronises. */
+iga_status iga_kkt_residual_rows(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
+                                 const iga_tt* load, const iga_tt* y, const iga_tt* u,
+                                 const iga_tt* lam, int nrows, const int* rows, double* res);
 
 /* The same solve with the solution returned as TT tensors (Sec. 5: the
  * block-AMEn solution is the block TT of eq. btt; here one TT per field).

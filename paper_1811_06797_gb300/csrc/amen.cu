@@ -2323,11 +2323,11 @@ static bool amen_local(iga_ctx* ctx, const iga_op* M, const iga_op* K, double be
   const int maxsw = std::max(1, o->max_sweeps);
   const double tol_abs = 0.1 * tol * Fnorm;
   const int maxit = std::max(1, o->local_maxit);
-  const bool adapt = !(o->trunc_tol > 0.0);
-  const double trunc_floor = 1e-5 * tol;
+  // the truncation tolerance stays fixed: the projected residuals of early
+  // sweeps are measured in different frames and are no measure of progress
   double rel = std::numeric_limits<double>::infinity();
-  double rel_prev = rel;
   int sweep = 0, last = 0;
+  const auto t_start = std::chrono::steady_clock::now();
   for (sweep = 0; sweep < maxsw; ++sweep) {
     const bool fwd = (sweep % 2) == 0;
     int order[3] = {0, 1, 2};
@@ -2350,7 +2350,9 @@ static bool amen_local(iga_ctx* ctx, const iga_op* M, const iga_op* K, double be
       worst = std::max(worst, S.last_local_res);
       last = d;
       if (S.verbose)
-        fprintf(stderr, "[amen-local] sweep %d core %d ranks (%d,%d) local_it %d proj. resid %.3e\n",
+        fprintf(stderr,
+                "[amen-local] %.2f s sweep %d core %d ranks (%d,%d) local_it %d proj. resid %.3e\n",
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(),
                 sweep, d, S.r[1], S.r[2], S.local_iters, S.last_local_res / Fnorm);
       if (s < 2) {
         clk->mark(PH_MOVE);
@@ -2360,11 +2362,6 @@ static bool amen_local(iga_ctx* ctx, const iga_op* M, const iga_op* K, double be
     }
     rel = worst / Fnorm;
     if (rel <= tol) { ++sweep; break; }
-    if (adapt && sweep >= 1 && rel > 0.25 * rel_prev && S.trunc_tol > trunc_floor) {
-      S.trunc_tol = std::max(0.01 * S.trunc_tol, trunc_floor);
-      if (S.verbose) fprintf(stderr, "[amen-local] truncation tolerance -> %.1e\n", S.trunc_tol);
-    }
-    rel_prev = rel;
   }
   clk->mark(PH_REFINE);
   if (z) S.expand(last, z);

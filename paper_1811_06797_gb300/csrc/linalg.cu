@@ -1064,12 +1064,12 @@ constexpr int SKINNY_C = 2016;      // columns of A per CTA in the sketch (21 ti
 template <int KK>
 __global__ void __launch_bounds__(256) skinny_sketch_kernel(
     const double* __restrict__ A, int ns, long long m, const double* __restrict__ Om, int k,
-    double* __restrict__ P) {
+    long long clen, double* __restrict__ P) {
   __shared__ double As[SKINNY_R][SKINNY_T + 1];
   __shared__ double Os[SKINNY_T][KK];
   const int i0 = blockIdx.y * SKINNY_R;
-  const long long c0 = (long long)blockIdx.x * SKINNY_C;
-  const long long cend = c0 + SKINNY_C < m ? c0 + SKINNY_C : m;
+  const long long c0 = (long long)blockIdx.x * clen;
+  const long long cend = c0 + clen < m ? c0 + clen : m;
   const int r = threadIdx.x >> 3, q = threadIdx.x & 7;
   double acc[KK];
 #pragma unroll
@@ -1227,15 +1227,23 @@ __global__ void rows_small_kernel(const double* __restrict__ B, long long m, int
 // Y (ns x k) = A Om for A = X^T, X col-major (m x ns)
 static void skinny_sketch(iga_ctx* ctx, const double* X, int ns, int m, const double* Om, int k,
                           double* Y) {
-  const int nb = (int)(((long long)m + SKINNY_C - 1) / SKINNY_C);
+  // column chunks of at most SKINNY_C, and short enough (whole shared-memory
+  // tiles) that the grid has about two CTAs per SM when A is small
+  const int rb = (ns + SKINNY_R - 1) / SKINNY_R;
+  const long long want = std::max<long long>(((long long)m + SKINNY_C - 1) / SKINNY_C,
+                                             (2LL * ctx->nsm + rb - 1) / rb);
+  long long clen = ((long long)m + want - 1) / want;
+  clen = std::min<long long>(SKINNY_C, (clen + SKINNY_T - 1) / SKINNY_T * SKINNY_T);
+  const int nb = (int)(((long long)m + clen - 1) / clen);
   double* P = scratch<double>(ctx, SLOT_TTSVD_PART, (size_t)nb * ns * k);
   // algorithmic: 2 ns m k flop, A read once
   prof_count(ctx, 8.0 * ns * (double)m, 2.0 * ns * (double)m * k);
-  const dim3 grid(nb, (ns + SKINNY_R - 1) / SKINNY_R);
+  const dim3 grid(nb, rb);
   if (k <= 8)
-    IGA_LAUNCH(ctx, skinny_sketch_kernel<8>, grid, 256, 0, X, ns, (long long)m, Om, k, P);
+    IGA_LAUNCH(ctx, skinny_sketch_kernel<8>, grid, 256, 0, X, ns, (long long)m, Om, k, clen, P);
   else
-    IGA_LAUNCH(ctx, skinny_sketch_kernel<SKINNY_K>, grid, 256, 0, X, ns, (long long)m, Om, k, P);
+    IGA_LAUNCH(ctx, skinny_sketch_kernel<SKINNY_K>, grid, 256, 0, X, ns, (long long)m, Om, k,
+               clen, P);
   IGA_LAUNCH(ctx, skinny_reduce_kernel, (ns * k + 255) / 256, 256, 0, P, nb, ns, k, Y);
 }
 

@@ -186,6 +186,7 @@ struct TtmTcArgs {
   int T1, T3, nt3;
   int NV;              // stages of the A2-column ring (2..4)
   int tcols;           // tensor-memory columns allocated (power of two >= 32)
+  int nacc;            // accumulator slots per half (2P+1 .. TTM_MAXACC)
   int* err;            // set to IGA_ETIMEOUT when a bounded wait gives up
 };
 
@@ -253,9 +254,10 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
   float* a3s = a1s + T1 * B * S1;                                       // [k S3 + o R2p + b]
   float* part = a3s + T3 * S3;
   uint64_t* bars = reinterpret_cast<uint64_t*>(part + 2 * PTS * B);
+  const int NA = g.nacc;                 // accumulator ring depth (>= B)
   const uint32_t z_full = su32(bars), z_free = z_full + 16, v_full = z_full + 32,
-                 v_free = v_full + 32, acc_full = v_free + 32, acc_empty = acc_full + 8 * B,
-                 mma_done = acc_empty + 8 * B;
+                 v_free = v_full + 32, acc_full = v_free + 32, acc_empty = acc_full + 8 * NA,
+                 mma_done = acc_empty + 8 * NA;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 32);
   volatile int* abort_ = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
       mbar_init(v_full + 8 * s, 1);
       mbar_init(v_free + 8 * s, 1);
     }
-    for (int c = 0; c < B; ++c) {
+    for (int c = 0; c < NA; ++c) {
       mbar_init(acc_full + 8 * c, 1);
       mbar_init(acc_empty + 8 * c, NPW);
     }
@@ -306,8 +308,8 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
   // accumulator again after draining it)
   if (warp >= NPW && warp < 2 * NPW) {
     const int e = warp - NPW, h = e >> 2, q = e & 3;
-    const uint32_t la = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * B * R1p);
-    for (int c = 0; c < B * R1p; c += 16) tc_st16_zero(la + c);
+    const uint32_t la = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * NA * R1p);
+    for (int c = 0; c < NA * R1p; c += 16) tc_st16_zero(la + c);
     tc_wait_st();
   }
   tc_fence_before();
@@ -385,18 +387,18 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
     float* ycol = outp ? g.y + (size_t)oi1 * n2 * n3 + oi3 : nullptr;
     float ynext = outp ? ycol[0] : 0.f;
     for (int i2 = 0; i2 < n2; ++i2) {
-      const int acc = i2 % B;
+      const int acc = i2 % NA;
       const float ycur = ynext;
       if (outp && i2 + 1 < n2) ynext = ycol[(size_t)(i2 + 1) * n3];
       bool ok = true;
-      if (lane == 0) ok = mbar_wait(acc_full + 8 * acc, (uint32_t)(i2 / B) & 1, abort_);
+      if (lane == 0) ok = mbar_wait(acc_full + 8 * acc, (uint32_t)(i2 / NA) & 1, abort_);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       float c[B];
 #pragma unroll
       for (int o = 0; o < B; ++o) c[o] = 0.f;
       if (ok) {
         tc_fence_after();
-        const uint32_t col0 = (uint32_t)((h * B + acc) * R1p);
+        const uint32_t col0 = (uint32_t)((h * NA + acc) * R1p);
         for (int ch = 0; ch < R1p; ch += 16) {
           float d[16];
           tc_ld16(la + col0 + ch, d);
@@ -445,8 +447,8 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
       auto issue = [&](int j2, int s, int sv, int ta, int tb) {
         int t = ta;
         while (t <= tb) {
-          const int c0 = (j2 - P + t) % B;
-          const int len = min(min(tb - t + 1, B - c0), maxrun);
+          const int c0 = (j2 - P + t) % NA;
+          const int len = min(min(tb - t + 1, NA - c0), maxrun);
           const uint32_t idesc = idesc_mma(BF ? 1 : 2, 128, len * R1p);
           for (int kb = 0; kb < R2p / KSTEP; ++kb) {
             const uint64_t bd =
@@ -454,8 +456,8 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
 #pragma unroll
             for (int h = 0; h < H; ++h) {
               const uint64_t ad = umma_desc(su32(zbuf + (s * H + h) * ZH) + kb * 256, 128, SBO);
-              if (BF) tc_mma_bf16(tbase + (uint32_t)((h * B + c0) * R1p), ad, bd, idesc, 1u);
-              else tc_mma_tf32(tbase + (uint32_t)((h * B + c0) * R1p), ad, bd, idesc, 1u);
+              if (BF) tc_mma_bf16(tbase + (uint32_t)((h * NA + c0) * R1p), ad, bd, idesc, 1u);
+              else tc_mma_tf32(tbase + (uint32_t)((h * NA + c0) * R1p), ad, bd, idesc, 1u);
             }
           }
           t += len;
@@ -470,15 +472,15 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
         }
         tc_fence_after();
         const int tlo = max(0, P - j2), thi = min(B - 1, n2 - 1 - j2 + P);
-        const bool fresh = (j2 + P < n2) && (j2 + P >= B);   // target i2 = j2 + P reuses a slot
+        const bool fresh = (j2 + P < n2) && (j2 + P >= NA);  // target i2 = j2 + P reuses a slot
         issue(j2, s, sv, tlo, fresh ? B - 2 : thi);
         // accumulator i2 = j2 - P is complete with these MMAs: hand it to the
         // epilogue before waiting for the slot of the fresh target, so that the
         // epilogue of i2 runs under the MMAs of the next slab
-        if (j2 - P >= 0) tc_commit(acc_full + 8 * ((j2 - P) % B));
+        if (j2 - P >= 0) tc_commit(acc_full + 8 * ((j2 - P) % NA));
         if (fresh) {
           const int i2n = j2 + P;
-          if (!mbar_wait(acc_empty + 8 * (i2n % B), (uint32_t)(i2n / B - 1) & 1, abort_)) {
+          if (!mbar_wait(acc_empty + 8 * (i2n % NA), (uint32_t)(i2n / NA - 1) & 1, abort_)) {
             fail();
             break;
           }
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
         tc_commit(z_free + 8 * s);
         tc_commit(v_free + 8 * sv);
         if (j2 == n2 - 1)
-          for (int i2 = max(0, j2 - P + 1); i2 < n2; ++i2) tc_commit(acc_full + 8 * (i2 % B));
+          for (int i2 = max(0, j2 - P + 1); i2 < n2; ++i2) tc_commit(acc_full + 8 * (i2 % NA));
       }
       // every MMA issued must finish before the tensor memory is released
       tc_commit(mma_done);
@@ -562,19 +564,24 @@ __global__ void ttm_tc_pack_kernel(const float* __restrict__ A2, int R1, int R2,
 
 struct TtmTcPlan {
   bool ok = false;
-  int H = 1, T1 = 0, T3 = 0, R1p = 0, R2p = 0, NV = 2, tcols = 0;
+  int H = 1, T1 = 0, T3 = 0, R1p = 0, R2p = 0, NV = 2, tcols = 0, nacc = 0;
   size_t smem = 0;
 };
 
 static constexpr size_t TTM_TC_SMEM_MAX = 227 * 1024;
+// deepest accumulator ring (the CTA's mbarrier block holds 2 x 9 ring barriers)
+static constexpr int TTM_MAXACC = 9;
 
 // Tile plan.  Per slab a CTA spends about H * 128 * B * R1p * R2p / rate
 // cycles in MMAs (rate: TF32 ~1500, BF16 ~3000 multiply-adds per SM and
 // cycle) plus about 1500 H cycles of CUDA-core work (the mode-3 and mode-1
 // products of 128 H points), and waits up to ~2500 cycles for one A2-column
-// copy, which an NV-stage ring spreads over NV - 1 slabs; the plan with the
-// least (waves of CTAs) x (cycles per slab) that fits tensor memory
-// (H B R1p <= 512 columns) and shared memory wins.
+// copy, which an NV-stage ring spreads over NV - 1 slabs.  The accumulator
+// ring takes as many slots as tensor memory allows (H nacc R1p <= 512
+// columns, nacc <= 9); with only the 2P+1 slots that are in use at once, the
+// MMAs of every slab wait for the epilogue of the plane completed one slab
+// earlier, which costs about 1000 cycles per slab more.  The plan with the
+// least (waves of CTAs) x (cycles per slab) that fits shared memory wins.
 static TtmTcPlan ttm_tc_plan(int n1, int n3, int R1, int R2, int P, bool bf16, int nsm) {
   TtmTcPlan best;
   const int B = 2 * P + 1, es = bf16 ? 2 : 4, kstep = bf16 ? 16 : 8;
@@ -593,15 +600,18 @@ static TtmTcPlan ttm_tc_plan(int n1, int n3, int R1, int R2, int P, bool bf16, i
         const long nt = (long)((n1 + T1 - 1) / T1) * ((n3 + T3 - 1) / T3);
         // per-slab cost: a fixed part (barrier hand-offs, the copy latency
         // spread over NV - 1 slabs) and a part proportional to the points
-        const double slab = vlat / (NV - 1) + H * (128.0 * B * R1p * R2p / rate + 1500.0);
+        const int nacc = std::min(TTM_MAXACC, 512 / (H * R1p));
+        const double slab = vlat / (NV - 1) + H * (128.0 * B * R1p * R2p / rate + 1500.0) +
+                            (nacc == B ? 1000.0 : 0.0);
         const double c = std::ceil((double)nt / nsm) * slab;
         if (c < bestc * (1 - 1e-9)) {
           bestc = c;
           best.ok = true;
           best.H = H; best.T1 = T1; best.T3 = T3; best.R1p = R1p; best.R2p = R2p; best.NV = NV;
           best.smem = smem;
+          best.nacc = nacc;
           int tc = 32;
-          while (tc < H * B * R1p) tc *= 2;
+          while (tc < H * nacc * R1p) tc *= 2;
           best.tcols = tc;
         }
       }
@@ -659,6 +669,7 @@ bool ttm_tc_block(iga_ctx* ctx, const float* A1, const float* A2, const float* A
   a.T1 = pl.T1; a.T3 = pl.T3; a.nt3 = (n[2] + pl.T3 - 1) / pl.T3;
   a.NV = pl.NV;
   a.tcols = pl.tcols;
+  a.nacc = pl.nacc;
   a.err = ctx->dflag + 1;
   const unsigned grid = (unsigned)(((n[0] + pl.T1 - 1) / pl.T1) * a.nt3);
   {

@@ -82,6 +82,7 @@ def lib():
         "iga_profile_begin": (st, [vp, C.c_char_p]),
         "iga_profile_end": (st, [vp, P(C.c_uint64), P(d), P(d), P(d)]),
         "iga_measure_fma": (st, [vp, i, P(d)]),
+        "iga_kkt_residual_rows": (st, [vp, vp, vp, d, vp, vp, vp, vp, i, P(C.c_int), P(d)]),
         "iga_gemm_batched": (st, [vp, i, i, i, i, i, i, d, vp, i, C.c_longlong, vp, i,
                                   C.c_longlong, d, vp, i, C.c_longlong, i]),
         "iga_sample_weights": (st, [vp, P(Geometry_), P(Space_), P(Target_), vp]),
@@ -646,6 +647,20 @@ def iga_kkt_solve_amen(ctx, M, K, load, beta, y, u, lam, **opts):
         _check(ctx, st)
     res["converged"] = st == 0
     return res
+
+
+def iga_kkt_residual_rows(ctx, M, K, beta, load, y, u, lam, rows):
+    """Residuals of the three KKT equations at the interior multi-indices
+    `rows` ((S, 3) integers, 0-based) for a solution given as TT handles:
+    a numpy array (S, 3)."""
+    import numpy as np
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((r.shape[0], 3), dtype=np.float64)
+    _check(ctx, lib().iga_kkt_residual_rows(
+        ctx.handle, M.handle, K.handle, float(beta), load.handle if load is not None else None,
+        y.handle, u.handle, lam.handle, r.shape[0],
+        r.ctypes.data_as(C.POINTER(C.c_int)), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
 
 
 def iga_kkt_solve_amen_tt(ctx, M, K, load, beta, **opts):

@@ -145,3 +145,39 @@ def test_local_mode_config2_matches_oracle(env, prec):
     for g, ref, name in ((y, yo, "y"), (u, uo, "u"), (lam, lo, "lam")):
         err = np.linalg.norm(g.cpu().numpy() - ref) / np.linalg.norm(ref)
         assert err <= 1e-6, (name, err)
+
+
+def test_residual_rows_match_the_full_residual(env):
+    """iga_kkt_residual_rows (operator entries from the bands, solution values
+    from the TT cores, nothing of full size) against the full FP64 KKT
+    residual of the expanded solution, row by row, including rows on the
+    boundary layer of the interior grid."""
+    ctx, torch, iga = env
+    work = CASES[3][1]
+    M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    ni = M.info()["n"]
+    N = int(np.prod(ni))
+    ty, tu, tl, info = iga.iga_kkt_solve_amen_tt(ctx, M, K, load, work.beta, tol=1e-4,
+                                                 residual=iga.IGA_RESID_LOCAL)
+    z = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    for f, t in enumerate((ty, tu, tl)):
+        t.full(ctx, z[f * N:(f + 1) * N].view(ni))
+    out = torch.empty_like(z)
+    iga.iga_kkt_apply(ctx, M, K, work.beta, z, out)
+    bfull = torch.empty(ni, dtype=torch.float64, device="cuda")
+    load.full(ctx, bfull)
+    b = torch.zeros_like(z)
+    b[:N] = bfull.reshape(-1)
+    res = (b - out).cpu().numpy().reshape(3, *ni)
+    rng = np.random.default_rng(7)
+    rows = np.stack([rng.integers(0, ni[d], 40) for d in range(3)], axis=1)
+    rows[0] = (0, 0, 0)
+    rows[1] = tuple(x - 1 for x in ni)
+    got = iga.iga_kkt_residual_rows(ctx, M, K, work.beta, load, ty, tu, tl, rows)
+    ref = np.stack([res[e][tuple(rows.T)] for e in range(3)], axis=1)
+    scale = float(b.norm())
+    assert np.abs(got - ref).max() <= 1e-12 * scale, np.abs(got - ref).max() / scale
+    # the residual is not negligible at this tolerance, so the comparison is not vacuous
+    assert np.abs(ref).max() > 1e-9 * scale
+    with pytest.raises(iga.IgaError):
+        iga.iga_kkt_residual_rows(ctx, M, K, work.beta, load, ty, tu, tl, [[ni[0], 0, 0]])

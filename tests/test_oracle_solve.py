@@ -27,3 +27,24 @@ def test_low_rank_reduced_route_equals_direct_solve(geo, p, E, beta):
     y, u, lam, it = solve_kkt(Mt, Kt, diag, bl, beta, tol=1e-13)
     for a, c in ((y, yd), (u, ud), (lam, ld)):
         assert np.linalg.norm(a - c) < 1e-8 * np.linalg.norm(c)
+
+
+def test_interpolated_route_operators_equal_sampled_route_on_an_affine_box():
+    """With a constant Jacobian every weight is a constant, which the spline
+    interpolation reproduces exactly: the interpolated route's interior
+    operators and load must equal the sampled route's (the Kronecker matrices
+    compared densely on a 3-element grid)."""
+    from oracle.lowrank import kron_matrix
+    from oracle.solve import interior_operators_interp
+    geo = wl.affine_box(np.array([[1.0, 0.2, 0.0], [0.1, 0.9, 0.3], [0.0, 0.2, 1.3]]))
+    space = wl.uniform_space(2, 3)
+    target = wl.Target(wl.TARGET_SINPROD)
+    Ms, Ks, _, bs = interior_operators(space, geo, target, 1e-14)
+    Mi, Ki, _, bi = interior_operators_interp(space, geo, target, 1e-14)
+    for A, B in ((Ms, Mi), (Ks, Ki)):
+        As, Ai = kron_matrix(A).toarray(), kron_matrix(B).toarray()
+        assert np.linalg.norm(As - Ai) < 1e-12 * np.linalg.norm(As)
+    # the load density sin(pi x) sin(pi y) sin(pi z) o G is not polynomial:
+    # only the interpolation error of degree 5 on 3 elements separates the loads
+    assert np.linalg.norm(bs - bi) < 1e-3 * np.linalg.norm(bs)
+    assert np.linalg.norm(bs - bi) > 0.0
