@@ -36,6 +36,7 @@ template <typename T>
 struct KronJob {
   const T* b[3][KRON_MAXTERMS];
   T coef[KRON_MAXTERMS][3];
+  unsigned char cmask[KRON_MAXTERMS];   // bit o set when coef[t][o] != 0
   unsigned char xin[KRON_MAXTERMS];
   int nterms;
   const T* x[3];
@@ -123,9 +124,12 @@ kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
     }
     __syncthreads();
     // mode 1 into the register accumulators of every output the term feeds
+    // (which outputs from an integer mask: an FP64 comparison per output and
+    // point would occupy the narrow FP64 pipe)
     T cf[NY];
 #pragma unroll
     for (int o = 0; o < NY; ++o) cf[o] = job.coef[t][o];
+    const unsigned cm = job.cmask[t];
 #pragma unroll
     for (int m = 0; m < KRON_MO; ++m) {
       int idx = threadIdx.x + m * KRON_THREADS;
@@ -138,7 +142,7 @@ kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
         for (int o = 0; o < B; ++o) s += a1[a * B + o] * z2[((size_t)(a + o) * T2 + c) * T3 + k];
 #pragma unroll
         for (int o = 0; o < NY; ++o)
-          if (cf[o] != T(0)) acc[o][m] += cf[o] * s;
+          if (cm & (1u << o)) acc[o][m] = fma(cf[o], s, acc[o][m]);
       }
     }
     __syncthreads();
@@ -270,8 +274,14 @@ static void launch_kron_job(iga_ctx* ctx, const KronJob<T>& job, const KronTile&
     for (int o = 0; o < NY; ++o) outs += job.beta[o] != T(0) ? 2.0 : 1.0;
     prof_count(ctx, N * sizeof(T) * (nin + outs), 6.0 * B * N * job.nterms);
   }
+  KronJob<T> jm = job;
+  for (int t = 0; t < jm.nterms; ++t) {
+    jm.cmask[t] = 0;
+    for (int o = 0; o < NY; ++o)
+      if (jm.coef[t][o] != T(0)) jm.cmask[t] |= (unsigned char)(1u << o);
+  }
   IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P, NY>), (unsigned)(g.nt1 * g.nt2 * g.nt3), KRON_THREADS,
-             smem, job, g);
+             smem, jm, g);
 }
 
 template <typename T>

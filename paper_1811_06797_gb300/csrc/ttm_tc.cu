@@ -186,7 +186,6 @@ struct TtmTcArgs {
   int T1, T3, nt3;
   int NV;              // stages of the A2-column ring (2..4)
   int tcols;           // tensor-memory columns allocated (power of two >= 32)
-  int nacc;            // accumulator slots per half (2P+1 .. TTM_MAXACC)
   int* err;            // set to IGA_ETIMEOUT when a bounded wait gives up
 };
 
@@ -254,7 +253,7 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
   float* a3s = a1s + T1 * B * S1;                                       // [k S3 + o R2p + b]
   float* part = a3s + T3 * S3;
   uint64_t* bars = reinterpret_cast<uint64_t*>(part + 2 * PTS * B);
-  const int NA = g.nacc;                 // accumulator ring depth (>= B)
+  constexpr int NA = B;                  // accumulator ring: the 2P+1 planes in use
   const uint32_t z_full = su32(bars), z_free = z_full + 16, v_full = z_full + 32,
                  v_free = v_full + 32, acc_full = v_free + 32, acc_empty = acc_full + 8 * NA,
                  mma_done = acc_empty + 8 * NA;
@@ -353,14 +352,16 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
         }
       }
       unsigned char* zr = zrow + s * H * ZH;
-      for (int c = 0; c < R2p / EPC; ++c) {
-        float acc[EPC];
+      // two 16-byte chunks per pass (R2p / EPC is even): 2 EPC independent
+      // accumulation chains of length B
+      for (int c = 0; c < R2p / EPC; c += 2) {
+        float acc[2 * EPC];
 #pragma unroll
-        for (int u = 0; u < EPC; ++u) acc[u] = 0.f;
+        for (int u = 0; u < 2 * EPC; ++u) acc[u] = 0.f;
 #pragma unroll
         for (int o = 0; o < B; ++o) {
 #pragma unroll
-          for (int u4 = 0; u4 < EPC / 4; ++u4) {
+          for (int u4 = 0; u4 < EPC / 2; ++u4) {
             const float4 a = a3r[o * R2q + c * (EPC / 4) + u4];
             acc[4 * u4 + 0] = fmaf(a.x, xw[o], acc[4 * u4 + 0]);
             acc[4 * u4 + 1] = fmaf(a.y, xw[o], acc[4 * u4 + 1]);
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
           }
         }
         store_z_chunk<BF>(zr + c * 128, acc);
+        store_z_chunk<BF>(zr + (c + 1) * 128, acc + EPC);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
@@ -393,9 +395,13 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
       bool ok = true;
       if (lane == 0) ok = mbar_wait(acc_full + 8 * acc, (uint32_t)(i2 / NA) & 1, abort_);
       ok = __shfl_sync(0xffffffffu, ok, 0);
-      float c[B];
+      // four partial sums per band offset o (independent FMA chains), added
+      // at the end
+      float c[B], cp[B][4];
 #pragma unroll
-      for (int o = 0; o < B; ++o) c[o] = 0.f;
+      for (int o = 0; o < B; ++o)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cp[o][u] = 0.f;
       if (ok) {
         tc_fence_after();
         const uint32_t col0 = (uint32_t)((h * NA + acc) * R1p);
@@ -410,10 +416,10 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const float4 av = ar[u];
-                c[o] = fmaf(av.x, d[4 * u], c[o]);
-                c[o] = fmaf(av.y, d[4 * u + 1], c[o]);
-                c[o] = fmaf(av.z, d[4 * u + 2], c[o]);
-                c[o] = fmaf(av.w, d[4 * u + 3], c[o]);
+                cp[o][0] = fmaf(av.x, d[4 * u], cp[o][0]);
+                cp[o][1] = fmaf(av.y, d[4 * u + 1], cp[o][1]);
+                cp[o][2] = fmaf(av.z, d[4 * u + 2], cp[o][2]);
+                cp[o][3] = fmaf(av.w, d[4 * u + 3], cp[o][3]);
               }
             }
           }
@@ -424,6 +430,8 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty + 8 * acc);
       }
+#pragma unroll
+      for (int o = 0; o < B; ++o) c[o] = (cp[o][0] + cp[o][1]) + (cp[o][2] + cp[o][3]);
       float* pb = part + (i2 & 1) * PTS * B;
 #pragma unroll
       for (int o = 0; o < B; ++o) pb[pt * B + o] = c[o];
@@ -564,24 +572,22 @@ __global__ void ttm_tc_pack_kernel(const float* __restrict__ A2, int R1, int R2,
 
 struct TtmTcPlan {
   bool ok = false;
-  int H = 1, T1 = 0, T3 = 0, R1p = 0, R2p = 0, NV = 2, tcols = 0, nacc = 0;
+  int H = 1, T1 = 0, T3 = 0, R1p = 0, R2p = 0, NV = 2, tcols = 0;
   size_t smem = 0;
 };
 
 static constexpr size_t TTM_TC_SMEM_MAX = 227 * 1024;
-// deepest accumulator ring (the CTA's mbarrier block holds 2 x 9 ring barriers)
-static constexpr int TTM_MAXACC = 9;
 
 // Tile plan.  Per slab a CTA spends about H * 128 * B * R1p * R2p / rate
 // cycles in MMAs (rate: TF32 ~1500, BF16 ~3000 multiply-adds per SM and
 // cycle) plus about 1500 H cycles of CUDA-core work (the mode-3 and mode-1
 // products of 128 H points), and waits up to ~2500 cycles for one A2-column
-// copy, which an NV-stage ring spreads over NV - 1 slabs.  The accumulator
-// ring takes as many slots as tensor memory allows (H nacc R1p <= 512
-// columns, nacc <= 9); with only the 2P+1 slots that are in use at once, the
-// MMAs of every slab wait for the epilogue of the plane completed one slab
-// earlier, which costs about 1000 cycles per slab more.  The plan with the
-// least (waves of CTAs) x (cycles per slab) that fits shared memory wins.
+// copy, which an NV-stage ring spreads over NV - 1 slabs; the plan with the
+// least (waves of CTAs) x (cycles per slab) that fits tensor memory
+// (H B R1p <= 512 columns) and shared memory wins.  The accumulator ring
+// holds the 2P+1 planes in use at once: deeper rings (up to 9 slots at
+// H = 1) were measured slower (4.58 against 4.38 ms at 320^3, and they
+// exclude H = 2, which the 512^3 shape needs: 16.8 against 9.9 ms).
 static TtmTcPlan ttm_tc_plan(int n1, int n3, int R1, int R2, int P, bool bf16, int nsm) {
   TtmTcPlan best;
   const int B = 2 * P + 1, es = bf16 ? 2 : 4, kstep = bf16 ? 16 : 8;
@@ -600,18 +606,15 @@ static TtmTcPlan ttm_tc_plan(int n1, int n3, int R1, int R2, int P, bool bf16, i
         const long nt = (long)((n1 + T1 - 1) / T1) * ((n3 + T3 - 1) / T3);
         // per-slab cost: a fixed part (barrier hand-offs, the copy latency
         // spread over NV - 1 slabs) and a part proportional to the points
-        const int nacc = std::min(TTM_MAXACC, 512 / (H * R1p));
-        const double slab = vlat / (NV - 1) + H * (128.0 * B * R1p * R2p / rate + 1500.0) +
-                            (nacc == B ? 1000.0 : 0.0);
+        const double slab = vlat / (NV - 1) + H * (128.0 * B * R1p * R2p / rate + 1500.0);
         const double c = std::ceil((double)nt / nsm) * slab;
         if (c < bestc * (1 - 1e-9)) {
           bestc = c;
           best.ok = true;
           best.H = H; best.T1 = T1; best.T3 = T3; best.R1p = R1p; best.R2p = R2p; best.NV = NV;
           best.smem = smem;
-          best.nacc = nacc;
           int tc = 32;
-          while (tc < H * nacc * R1p) tc *= 2;
+          while (tc < H * B * R1p) tc *= 2;
           best.tcols = tc;
         }
       }
@@ -669,7 +672,6 @@ bool ttm_tc_block(iga_ctx* ctx, const float* A1, const float* A2, const float* A
   a.T1 = pl.T1; a.T3 = pl.T3; a.nt3 = (n[2] + pl.T3 - 1) / pl.T3;
   a.NV = pl.NV;
   a.tcols = pl.tcols;
-  a.nacc = pl.nacc;
   a.err = ctx->dflag + 1;
   const unsigned grid = (unsigned)(((n[0] + pl.T1 - 1) / pl.T1) * a.nt3);
   {
