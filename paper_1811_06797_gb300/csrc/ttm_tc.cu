@@ -134,17 +134,24 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t dtmem, uint64_t a, uint64_t
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// tcgen05.ld without the wait: the registers are valid only after
+// tc_wait_ld16 on the same array (which names them as read-write operands, so
+// that no use is moved above the wait)
+__device__ __forceinline__ void tc_ld16_async(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tc_wait_ld16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 __device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
   const uint32_t z = 0u;
@@ -405,9 +412,15 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
       if (ok) {
         tc_fence_after();
         const uint32_t col0 = (uint32_t)((h * NA + acc) * R1p);
+        // chunks of 16 columns (loading the next chunk while the current one
+        // is used was measured slower)
         for (int ch = 0; ch < R1p; ch += 16) {
+          uint32_t rn[16];
+          tc_ld16_async(la + col0 + ch, rn);
+          tc_wait_ld16(rn);
           float d[16];
-          tc_ld16(la + col0 + ch, d);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) d[j] = __uint_as_float(rn[j]);
 #pragma unroll
           for (int o = 0; o < B; ++o) {
             const int ii = jj - o;
