@@ -425,7 +425,8 @@ def config5_assembly(ctx, iga, torch):
 def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, rows=512):
     """The random-volume KKT solve (degree 2, 512 elements per direction,
     beta 1e-6, 1.34e8 unknowns per field) without any full-size operator
-    apply (IGA_RESID_LOCAL, the solution as the block TT), mixed precision:
+    apply (IGA_RESID_LOCAL, the solution as the block TT), mixed precision
+    (IGA_TF32: local contractions on the tensor cores, FP64 local refinement):
     wall time of the solve, its sweeps, ranks and projected residual, and the
     true relative residual estimated from `rows` uniformly sampled rows of
     the three KKT equations (iga_kkt_residual_rows)."""
@@ -449,7 +450,7 @@ def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, rows=512):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ty, tu, tl, info = iga.iga_kkt_solve_amen_tt(ctx, M, K, load, work.beta, tol=tol,
-                                                 precision=iga.IGA_FP32,
+                                                 precision=iga.IGA_TF32,
                                                  residual=iga.IGA_RESID_LOCAL,
                                                  max_sweeps=max_sweeps, trunc_tol=trunc_tol)
     torch.cuda.synchronize()
@@ -704,6 +705,8 @@ def run_gpu(args, world, rank, local):
         "assembly_routes_ms": assembly_routes(assemble, work, torch),
         "rank_tables": rank_tables(ctx),
         "config5_assembly": config5_assembly(ctx, iga, torch),
+        "config5_solve": config5_solve(ctx, iga, torch, args.c5_tol, args.c5_trunc,
+                                       args.c5_sweeps),
         "storage": {work.name: report.storage(ctx, work.geometry, work.space, work.target,
                                               work.tol)},
         "alu_rates_measured_tflops": {"fp64": iga.iga_measure_fma(ctx, iga.IGA_FP64),

@@ -212,6 +212,111 @@ __global__ void kr_left_apply_kernel(const double* __restrict__ Psi, const doubl
   }
 }
 
+// ---- banded contraction of the middle core on the tensor cores (IGA_TF32)
+//
+// For a high-rank operator the middle core's bands couple every left rank
+// index al of a TT-matrix block with every right index bl of that block, and
+// the contraction out[al](va, i, b) = sum_{bl, o} A^{al,bl}(i, o)
+// t1[bl](va, i + o - P, b) is, for each output plane i and block k, a dense
+// product W_i (R1k x (2P+1) R2k) T_i ((2P+1) R2k x Q) over Q = 3 r0 r1
+// columns.  Stored block by block as T[k][j + P][bl][q] (zero planes at both
+// ends), the rows of T_i are contiguous, so one batched TF32 GEMM per block
+// and field covers every plane.  The result is reordered so that the left
+// interface product is one GEMM per block and field as well.
+constexpr int BTC_MAXBLK = 16;
+struct BandTcMeta {
+  int nb;
+  int R1[BTC_MAXBLK], R2[BTC_MAXBLK], b0[BTC_MAXBLK], a0[BTC_MAXBLK];
+  long long tb[BTC_MAXBLK + 1];     // start of block k in T (elements)
+  long long ob[BTC_MAXBLK + 1];     // start of block k in Out / Ot
+};
+
+// T[tb_k + ((j') R2k + bl) Q + q] = t1[b0k + bl] at (va, j' - P, b), q = va r1 + b
+template <typename E>
+__global__ void band_tc_pack_t_kernel(const E* __restrict__ t1, E* __restrict__ T,
+                                      BandTcMeta m, int r3, int n, int r1, int P) {
+  const long long Q = (long long)r3 * r1;
+  const long long total = m.tb[m.nb];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < m.nb && idx >= m.tb[k + 1]) ++k;
+    const long long rem = idx - m.tb[k];
+    const int q = (int)(rem % Q);
+    const long long rest = rem / Q;
+    const int bl = (int)(rest % m.R2[k]);
+    const int j = (int)(rest / m.R2[k]) - P;
+    E v = E(0);
+    if (j >= 0 && j < n) {
+      const int va = q / r1, b = q - va * r1;
+      v = t1[(((size_t)(m.b0[k] + bl) * r3 + va) * n + j) * r1 + b];
+    }
+    T[idx] = v;
+  }
+}
+
+// W[wb_k + ((i R1k + al) B + o) R2k + bl] = band (al, bl) of block k, row i, entry o
+template <typename E>
+__global__ void band_tc_pack_w_kernel(const E* __restrict__ band, E* __restrict__ W,
+                                      const long long* __restrict__ wb,
+                                      const long long* __restrict__ boff, const int* __restrict__ R1,
+                                      const int* __restrict__ R2, int nb, int n, int B) {
+  const long long total = wb[nb];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < nb && idx >= wb[k + 1]) ++k;
+    long long r = idx - wb[k];
+    const int bl = (int)(r % R2[k]);
+    r /= R2[k];
+    const int o = (int)(r % B);
+    r /= B;
+    const int al = (int)(r % R1[k]);
+    const int i = (int)(r / R1[k]);
+    W[idx] = band[(boff[k] + (long long)al * R2[k] + bl) * n * B + (long long)i * B + o];
+  }
+}
+
+// Ot[ob_k + (((v R1k + al) r0 + a) n + i) r1 + b] = Out[ob_k + (((i 3 + v) R1k + al) r0 + a) r1 + b]
+template <typename E>
+__global__ void band_tc_reorder_kernel(const E* __restrict__ Out, E* __restrict__ Ot,
+                                       BandTcMeta m, int r0, int n, int r1) {
+  const long long total = m.ob[m.nb];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < m.nb && idx >= m.ob[k + 1]) ++k;
+    long long r = idx - m.ob[k];
+    const int b = (int)(r % r1);
+    r /= r1;
+    const int i = (int)(r % n);
+    r /= n;
+    const int a = (int)(r % r0);
+    r /= r0;
+    const int al = (int)(r % m.R1[k]);
+    const int v = (int)(r / m.R1[k]);
+    Ot[idx] = Out[m.ob[k] + ((((long long)i * 3 + v) * m.R1[k] + al) * r0 + a) * r1 + b];
+  }
+}
+
+// P2[pb_k + (a R1k + al) r0 + a'] = PhiL[a0k + al](a, a')
+template <typename E>
+__global__ void band_tc_pack_phil_kernel(const E* __restrict__ PL, E* __restrict__ P2,
+                                         BandTcMeta m, int r0) {
+  const long long total = (long long)(m.a0[m.nb - 1] + m.R1[m.nb - 1]) * r0 * r0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < m.nb && idx >= (long long)m.a0[k + 1] * r0 * r0) ++k;
+    long long r = idx - (long long)m.a0[k] * r0 * r0;
+    const int ap = (int)(r % r0);
+    r /= r0;
+    const int al = (int)(r % m.R1[k]);
+    const int a = (int)(r / m.R1[k]);
+    P2[idx] = PL[((long long)(m.a0[k] + al) * r0 + a) * r0 + ap];
+  }
+}
+
 // (3, r, n, r1) block core -> row-major ((a,i) x (l,b)) matrix
 __global__ void permute_fwd_kernel(const double* __restrict__ Xh, int r, int n, int r1,
                                    double* __restrict__ Mx) {
@@ -1253,6 +1358,18 @@ struct Solver {
   int local_iters = 0;
   uint64_t seed = 0x51ed2701ull;
   int verbose = 0;
+  // the middle core's banded contraction as batched GEMMs for operators whose
+  // blocks have TT ranks of at least 4 x 4 (packed bands per operator): TF32
+  // tensor cores in IGA_TF32 solves, the library's FP64 GEMM for the FP64
+  // local operator
+  struct BandTc {
+    bool ready = false, use = false;
+    BandTcMeta meta{};
+    std::vector<long long> wb;
+    DevBuf<float> W32;
+    DevBuf<double> W64;
+  };
+  BandTc btc[2];
   // IGA_RESID_LOCAL: Khatri-Rao sketch interfaces and the local residual
   bool kr_mode = false;
   int kr_k = 0;                        // sketch columns of the current draw
@@ -1738,10 +1855,10 @@ struct Solver {
     }
     if constexpr (sizeof(U) == 4) {
       if (tc_local) {
-        // t_s (rows (v, a, i), r1) = x (rows, r1) op(R_s): K-major x, one product per s
-        for (int q = 0; q < S; ++q)
-          tc_gemm_tf32(ctx, false, !transR, false, nv * r0 * nn, r1, r1, 1.f, x, r1, 0,
-                       R + (size_t)q * r1 * r1, r1, 0, 0.f, t + (size_t)q * per, r1, 0, 1);
+        // t_s (rows (v, a, i), r1) = x (rows, r1) op(R_s): K-major x, every s
+        // in one batched launch
+        tc_gemm_tf32(ctx, false, !transR, false, nv * r0 * nn, r1, r1, 1.f, x, r1, 0, R, r1,
+                     (long long)r1 * r1, 0.f, t, r1, (long long)per, S);
         return;
       }
     }
@@ -1773,6 +1890,123 @@ struct Solver {
     }
   }
 
+  // set up (once per operator) the GEMM form of the middle core's banded
+  // contraction: used when some block has TT ranks of at least 4 x 4
+  // (rank-one operators keep the element kernel)
+  bool band_tc_ready(int o) {
+    BandTc& bt = btc[o];
+    if (bt.ready) return bt.use;
+    bt.ready = true;
+    const iga_op* A = op[o];
+    const int nb = (int)A->blocks.size();
+    int big = 0;
+    for (const OpBlock& blk : A->blocks) big = std::max(big, std::min(blk.R1, blk.R2));
+    if (nb > BTC_MAXBLK || big < 4) return false;
+    const int n1 = A->n[1], B = 2 * A->p[1] + 1;
+    BandTcMeta& m = bt.meta;
+    m.nb = nb;
+    bt.wb.assign(nb + 1, 0);
+    std::vector<long long> boff(nb);
+    std::vector<int> R1(nb), R2(nb);
+    int a0 = 0, b0 = 0;
+    for (int k = 0; k < nb; ++k) {
+      const OpBlock& blk = A->blocks[k];
+      m.R1[k] = R1[k] = blk.R1;
+      m.R2[k] = R2[k] = blk.R2;
+      m.a0[k] = a0;
+      m.b0[k] = b0;
+      a0 += blk.R1;
+      b0 += blk.R2;
+      boff[k] = (long long)blk.off[1];
+      bt.wb[k + 1] = bt.wb[k] + (long long)n1 * blk.R1 * B * blk.R2;
+    }
+    const long long tot = bt.wb[nb];
+    DevBuf<long long> dwb(nb + 1), dboff(nb);
+    DevBuf<int> dR1(nb), dR2(nb);
+    IGA_CUDA(cudaMemcpyAsync(dwb.p, bt.wb.data(), (nb + 1) * 8, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(dboff.p, boff.data(), nb * 8, cudaMemcpyHostToDevice, ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(dR1.p, R1.data(), nb * 4, cudaMemcpyHostToDevice, ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(dR2.p, R2.data(), nb * 4, cudaMemcpyHostToDevice, ctx->stream));
+    const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 4096);
+    bt.W64.alloc((size_t)tot);
+    IGA_LAUNCH(ctx, band_tc_pack_w_kernel<double>, g, 256, 0, A->band64[1].p, bt.W64.p, dwb.p,
+               dboff.p, dR1.p, dR2.p, nb, n1, B);
+    if (tc_local && A->band32[1].p) {
+      bt.W32.alloc((size_t)tot);
+      IGA_LAUNCH(ctx, band_tc_pack_w_kernel<float>, g, 256, 0, A->band32[1].p, bt.W32.p, dwb.p,
+                 dboff.p, dR1.p, dR2.p, nb, n1, B);
+    }
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    bt.use = true;
+    return true;
+  }
+
+  // out (3, r0, n, r1) = sum_al PL[al] (banded contraction of t1) for the
+  // middle core as batched GEMMs (replaces band_group_kernel + left_mult):
+  // TF32 on the tensor cores for U = float (IGA_TF32 solves), the library's
+  // FP64 GEMM for U = double
+  template <typename U>
+  void band_left_gemm(int o, const Local& c, const U* t1, const U* PL, U* out) {
+    BandTc& bt = btc[o];
+    BandTcMeta m = bt.meta;
+    const int r0 = c.r0, nn = c.nn, r1 = c.r1, P = op[o]->p[c.d], B = 2 * P + 1;
+    const long long Q = 3LL * r0 * r1;
+    m.tb[0] = 0;
+    m.ob[0] = 0;
+    for (int k = 0; k < m.nb; ++k) {
+      m.tb[k + 1] = m.tb[k] + (long long)(nn + 2 * P) * m.R2[k] * Q;
+      m.ob[k + 1] = m.ob[k] + (long long)nn * 3 * m.R1[k] * r0 * r1;
+    }
+    const int sb = sizeof(U) == 4 ? 100 : 104;
+    U* Tb = scratch<U>(ctx, SLOT_AMEN_BASE + sb, (size_t)m.tb[m.nb]);
+    U* Out = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 1, (size_t)m.ob[m.nb]);
+    U* Ot = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 2, (size_t)m.ob[m.nb]);
+    const int R0s = m.a0[m.nb - 1] + m.R1[m.nb - 1];
+    U* P2 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 3, (size_t)R0s * r0 * r0);
+    const U* W = nullptr;
+    if constexpr (sizeof(U) == 4) W = bt.W32.p;
+    else W = bt.W64.p;
+    auto grid = [](long long cnt) {
+      return (unsigned)std::min<long long>((cnt + 255) / 256, 8 * 152);
+    };
+    IGA_LAUNCH(ctx, band_tc_pack_t_kernel<U>, grid(m.tb[m.nb]), 256, 0, t1, Tb, m, 3 * r0, nn, r1,
+               P);
+    // middle: Out_k[i][v] (R1k x r0 r1) = W_k[i] (R1k x B R2k) T_k[i] (B R2k x Q, field v)
+    for (int k = 0; k < m.nb; ++k)
+      for (int v = 0; v < 3; ++v) {
+        const U* Ak = W + bt.wb[k];
+        const U* Bk = Tb + m.tb[k] + (long long)v * r0 * r1;
+        U* Ck = Out + m.ob[k] + (long long)v * m.R1[k] * r0 * r1;
+        const int K = B * m.R2[k];
+        if constexpr (sizeof(U) == 4)
+          tc_gemm_tf32(ctx, true, true, true, r0 * r1, m.R1[k], K, 1.f, Bk, (int)Q,
+                       (long long)m.R2[k] * Q, Ak, K, (long long)m.R1[k] * K, 0.f, Ck, r0 * r1,
+                       3LL * m.R1[k] * r0 * r1, nn);
+        else
+          gemm_rm_batched<double>(ctx, false, false, m.R1[k], r0 * r1, K, 1.0, Ak, K,
+                                  (long long)m.R1[k] * K, Bk, (int)Q, (long long)m.R2[k] * Q, 0.0,
+                                  Ck, r0 * r1, 3LL * m.R1[k] * r0 * r1, nn);
+      }
+    IGA_LAUNCH(ctx, band_tc_reorder_kernel<U>, grid(m.ob[m.nb]), 256, 0, Out, Ot, m, r0, nn, r1);
+    IGA_LAUNCH(ctx, band_tc_pack_phil_kernel<U>, grid((long long)R0s * r0 * r0), 256, 0, PL, P2,
+               m, r0);
+    // left: out[v] (r0 x n r1) += P2_k (r0 x R1k r0) Ot_k[v] (R1k r0 x n r1)
+    for (int k = 0; k < m.nb; ++k)
+      for (int v = 0; v < 3; ++v) {
+        const U* Ak = P2 + (long long)m.a0[k] * r0 * r0;
+        const U* Bk = Ot + m.ob[k] + (long long)v * m.R1[k] * r0 * nn * r1;
+        U* Ck = out + (long long)v * r0 * nn * r1;
+        const int K = m.R1[k] * r0;
+        if constexpr (sizeof(U) == 4)
+          tc_gemm_tf32(ctx, true, true, true, nn * r1, r0, K, 1.f, Bk, nn * r1, 0, Ak, K, 0,
+                       k ? 1.f : 0.f, Ck, nn * r1, 0, 1);
+        else
+          gemm_rm_batched<double>(ctx, false, false, r0, nn * r1, K, 1.0, Ak, K, 0, Bk, nn * r1,
+                                  0, k ? 1.0 : 0.0, Ck, nn * r1, 0, 1);
+      }
+  }
+
   // local KKT operator applied with interfaces PL/PR and bands of type U:
   // out = [M y + K lam, beta M u - M lam, K y - M u]
   template <typename U>
@@ -1787,6 +2021,13 @@ struct Solver {
       U* t2 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 3, per * z.R0);
       U* out = o ? Kv : Mv;
       right_mult<U>(PR[o], x, z.R1, 3, c.r0, c.nn, c.r1, 0, t1);
+      // high-rank middle cores: the banded contraction as batched GEMMs (TF32
+      // tensor cores in IGA_TF32 solves, FP64 for the FP64 operator; the FP32
+      // operator of IGA_FP32 keeps the element kernel)
+      if (c.d == 1 && (sizeof(U) == 8 || tc_local) && band_tc_ready(o)) {
+        band_left_gemm<U>(o, c, t1, PL[o], out);
+        continue;
+      }
       IGA_LAUNCH(ctx, band_group_kernel<U>, nblk(per * z.R0), 256, 0, bands_of<U>(op[o], c.d),
                  z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, 3 * c.r0, c.nn, c.r1,
                  op[o]->p[c.d], t2);
@@ -2125,21 +2366,27 @@ struct Solver {
       // corrections are added to the FP64 block core until it meets tol_abs
       // refine well below the SVD truncation threshold so that FP32 round-off
       // in the block core does not show up as extra TT rank
+      // With the banded contraction on the tensor cores the local operator is
+      // accurate to TF32 (about 1e-3 relative): each Krylov pass then only
+      // aims at 1e-3 and the FP64 refinement takes more, cheaper passes
+      const bool tcb = tc_local && d == 1 && (band_tc_ready(0) || band_tc_ready(1));
+      const double rel32 = tcb ? 1e-3 : 2e-6;
+      const int passes = tcb ? 6 : 4;
       double rn = device_norm2(ctx, rhs, per);
       double tref = std::min(tol_abs, 1e-9 * rn);
-      double t32 = std::max(tref, 2e-6 * rn);
+      double t32 = std::max(tref, rel32 * rn);
       local_iters += gmres(c, bt, xt, t32, maxit);
       IGA_LAUNCH(ctx, from_type_kernel<T>, nblk(per), 256, 0, xt, Xh.p, per);
       double* r64 = slot(15 + 60, per);
       double* ax = slot(16 + 60, per);
-      for (int it = 0; it < 4; ++it) {
+      for (int it = 0; it < passes; ++it) {
         local_op64(c, Xh.p, ax);
         IGA_LAUNCH(ctx, sub_kernel, nblk(per), 256, 0, rhs, ax, r64, per);
         double res = device_norm2(ctx, r64, per);
         if (res <= tref || !std::isfinite(res)) break;
         IGA_LAUNCH(ctx, to_type_kernel<T>, nblk(per), 256, 0, r64, bt, per);
         IGA_CUDA(cudaMemsetAsync(xt, 0, per * sizeof(T), ctx->stream));
-        local_iters += gmres(c, bt, xt, std::max(tref, 2e-6 * res), maxit);
+        local_iters += gmres(c, bt, xt, std::max(tref, rel32 * res), maxit);
         IGA_LAUNCH(ctx, axpy_from_type_kernel<T>, nblk(per), 256, 0, Xh.p, xt, per);
       }
     }

@@ -181,3 +181,29 @@ def test_residual_rows_match_the_full_residual(env):
     assert np.abs(ref).max() > 1e-9 * scale
     with pytest.raises(iga.IgaError):
         iga.iga_kkt_residual_rows(ctx, M, K, work.beta, load, ty, tu, tl, [[ni[0], 0, 0]])
+
+
+@pytest.mark.parametrize("name,work", CASES[2:], ids=[c[0] for c in CASES[2:]])
+@pytest.mark.parametrize("resid", [0, 1], ids=["full", "local"])
+def test_tf32_solve_with_tensor_core_band_contraction(env, name, work, resid):
+    """IGA_TF32 on the random volume: the middle core's banded contraction of
+    the TT-matrix operators (blocks of TT ranks >= 4) runs as batched TF32
+    GEMMs on the tensor cores, the local systems are refined in FP64, and the
+    solution must match the oracle's direct solve as in the FP64 path."""
+    ctx, torch, iga = env
+    M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    assert max(min(M.block_ranks(k)) for k in range(M.info()["nblocks"])) >= 4
+    N = int(np.prod(M.info()["n"]))
+    y, u, lam = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+    ctx.profile_begin("tc_gemm_tf32_kernel")
+    info = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, y, u, lam, tol=1e-10,
+                                  precision=iga.IGA_TF32, residual=resid, max_sweeps=12)
+    prof = ctx.profile_end()
+    assert info["converged"], info
+    assert prof["launches"] > 0          # the tensor-core path ran
+    Mo, Ko, b = _oracle_system(work)
+    y, u, lam = (t.cpu().numpy() for t in (y, u, lam))
+    assert kkt_residual(Mo, Ko, work.beta, b, y, u, lam) < 1e-8
+    yo, uo, lo = kkt_solve(Mo, Ko, work.beta, b)
+    for got, ref in ((y, yo), (u, uo), (lam, lo)):
+        assert _rel(got, ref) < 1e-6, (name, _rel(got, ref))
