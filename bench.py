@@ -77,9 +77,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--roofline-kernel", default="auto",
                     help="kernel name for the roofline entry, or auto (largest device time)")
-    ap.add_argument("--only", default=None, choices=["ttm", "c5solve"],
+    ap.add_argument("--only", default=None, choices=["ttm", "c5solve", "step"],
                     help="ttm: only the tensor-core TT apply measurement (a profiling case); "
-                         "c5solve: only the random-volume solve without full-size applies")
+                         "c5solve: only the random-volume solve without full-size applies; "
+                         "step: only the timed steps of the workload")
     ap.add_argument("--c5-tol", type=float, default=1e-4)
     ap.add_argument("--c5-trunc", type=float, default=1e-6)
     ap.add_argument("--c5-sweeps", type=int, default=4)
@@ -583,6 +584,11 @@ def run_gpu(args, world, rank, local):
     ms = aggregate_ms(sum(times) / len(times), dist)
     clocks = clk.summary()
     info = state["info"]
+    if args.only == "step":
+        # profiling case: the timed steps of the workload alone
+        return {"metric": METRIC, "value": ms / 1e3, "unit": "s", "steps": args.steps,
+                "warmup": args.warmup, "gpu_launches": launches // max(1, args.steps),
+                "config": {"workload": work.name}, "only": "step"}, work, {}
 
     # the other precision path, same workload (solve only, assembly excluded)
     other = iga.IGA_FP32 if prec == iga.IGA_FP64 else iga.IGA_FP64
@@ -785,7 +791,7 @@ def main():
         return
     line, work, solutions = run_gpu(args, world, rank, local)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.only is None:
             try:
                 leg, base = oracle_baseline(work, 2, args.weights)
                 line["cpu_baseline"] = base

@@ -575,6 +575,30 @@ __device__ __forceinline__ T& bwin(T* A, const BandLayout& L, int row, int col) 
   return A[(size_t)row * L.W + (col - row + L.kl)];
 }
 
+// Block values of the preconditioner, stage one: the right interfaces
+// contracted into the bands row by row of the core's CSR structure,
+//   G[l][(i B + o)][b] = sum_{z in row l} band_z(i, o) dR[r_z][b]
+// (stage two, a GEMM with the left diagonals, gives V[a][(i B + o)][b]).
+template <typename T>
+__global__ void precond_stage1_kernel(const T* __restrict__ band, const int* __restrict__ rowptr,
+                                      const int* __restrict__ rowsrc,
+                                      const long long* __restrict__ rowoff,
+                                      const T* __restrict__ dR, int R0, int nB, int r1,
+                                      T* __restrict__ G) {
+  const long long total = (long long)R0 * nB * r1;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % r1);
+    const long long q = idx / r1;
+    const int io = (int)(q % nB);
+    const int l = (int)(q / nB);
+    T acc = T(0);
+    for (int z = rowptr[l]; z < rowptr[l + 1]; ++z)
+      acc = fma(band[rowoff[z] + io], dR[(size_t)rowsrc[z] * r1 + b], acc);
+    G[idx] = acc;
+  }
+}
+
 template <typename T>
 __global__ void kkt_block_factor_kernel(
     BandLayout L, T beta,
@@ -584,7 +608,7 @@ __global__ void kkt_block_factor_kernel(
     const long long* __restrict__ nzK_off, int nnzK,
     const T* __restrict__ dLM, const T* __restrict__ dRM, const T* __restrict__ dLK,
     const T* __restrict__ dRK, T* __restrict__ Aout, int* __restrict__ piv, int* __restrict__ flag,
-    int use_smem) {
+    int use_smem, const T* __restrict__ VM, const T* __restrict__ VK) {
   extern __shared__ unsigned char smraw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
@@ -599,7 +623,7 @@ __global__ void kkt_block_factor_kernel(
   // assemble the block: every (i, o) writes six distinct entries.  The
   // interface products s_z = dL(z, a) dR(z, b) are computed once per lane
   // (lane z) and broadcast by shuffles.
-  const int nzt = nnzM + nnzK;
+  const int nzt = VM ? 0 : nnzM + nnzK;
   for (int e0 = 0; e0 < n * B; e0 += 32) {
     const int e = e0 + lane;
     const bool ok = e < n * B;
@@ -607,6 +631,13 @@ __global__ void kkt_block_factor_kernel(
     const int j = i + o - p;
     const bool in = ok && j >= 0 && j < n;
     T m = T(0), k = T(0), kt = T(0);
+    if (VM && in) {
+      // pre-assembled: V[a][(i B + o)][b], the transpose from row j
+      const size_t base = (size_t)a * n * B;
+      m = VM[(base + (size_t)i * B + o) * L.r1 + b];
+      k = VK[(base + (size_t)i * B + o) * L.r1 + b];
+      kt = VK[(base + (size_t)j * B + (2 * p - o)) * L.r1 + b];
+    }
     for (int z0 = 0; z0 < nzt; z0 += 32) {
       T sz = T(0);
       const int z = z0 + lane;
@@ -2166,6 +2197,34 @@ struct Solver {
                  tdRM, tdLK, tdRK, F, ctx->dflag);
       return;
     }
+    // many operator terms (high-rank TT-matrix operators): contract the
+    // interfaces into the bands once for all rank pairs (stage one per row of
+    // the core's structure, stage two a GEMM with the left diagonals) instead
+    // of summing every term in every pair's assembly
+    const P* VM = nullptr;
+    const P* VK = nullptr;
+    if (zM.l.size() + zK.l.size() > 64) {
+      const int nB = c.nn * (2 * BL.p + 1);
+      const CoreNZ* zs[2] = {&zM, &zK};
+      const P* dLs[2] = {tdLM, tdLK};
+      const P* dRs[2] = {tdRM, tdRK};
+      P* Vs2[2];
+      for (int o = 0; o < 2; ++o) {
+        const CoreNZ& z = *zs[o];
+        P* G = scratch<P>(ctx, SLOT_AMEN_BASE + 110 + o, (size_t)z.R0 * nB * r1);
+        const long long tot = (long long)z.R0 * nB * r1;
+        IGA_LAUNCH(ctx, precond_stage1_kernel<P>,
+                   (unsigned)std::min<long long>((tot + 255) / 256, 8 * 152), 256, 0,
+                   bands_of<P>(op[o], c.d), z.rowptr.p, z.rowsrc.p, z.rowoff.p, dRs[o], z.R0, nB,
+                   r1, G);
+        Vs2[o] = scratch<P>(ctx, SLOT_AMEN_BASE + 112 + o, (size_t)r0 * nB * r1);
+        // V (r0 x nB r1) = dL^T (r0 x R0) G (R0 x nB r1), dL stored (R0 x r0)
+        gemm_rm_batched<P>(ctx, true, false, r0, nB * r1, z.R0, P(1), dLs[o], r0, 0, G, nB * r1,
+                           0, P(0), Vs2[o], nB * r1, 0, 1);
+      }
+      VM = Vs2[0];
+      VK = Vs2[1];
+    }
     P* A = scratch<P>(ctx, SLOT_AMEN_BASE + 48, (size_t)BL.N * BL.W * BL.NB);
     int* piv = scratch<int>(ctx, SLOT_AMEN_BASE + 49, (size_t)BL.N * BL.NB);
     IGA_CUDA(cudaMemsetAsync(ctx->dflag, 0, sizeof(int), ctx->stream));
@@ -2181,7 +2240,7 @@ struct Solver {
     IGA_LAUNCH(ctx, kkt_block_factor_kernel<P>, nblk(BL.NB, wpb), 32 * wpb, smem, BL, (P)beta,
                bands_of<P>(op[0], c.d), zM.dl.p, zM.dr.p, zM.doff.p, (int)zM.l.size(),
                bands_of<P>(op[1], c.d), zK.dl.p, zK.dr.p, zK.doff.p, (int)zK.l.size(), tdLM, tdRM,
-               tdLK, tdRK, A, piv, ctx->dflag, use_smem);
+               tdLK, tdRK, A, piv, ctx->dflag, use_smem, VM, VK);
   }
 
   void precond_apply(const Local& c, const T* v, T* z) {

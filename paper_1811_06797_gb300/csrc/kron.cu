@@ -63,6 +63,8 @@ kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
   T* a1 = z2 + (size_t)H1 * T2 * T3;            // T1 * B
   T* a2 = a1 + T1 * B;                          // T2 * B
   T* a3 = a2 + T2 * B;                          // T3 * B
+  const int T3h = T3 + 2 * P;
+  T* xs = a3 + T3 * B;                          // H1 * H2 * T3h: the x slab of the tile
   int bid = blockIdx.x;
   int t3 = bid % g.nt3;
   int t2 = (bid / g.nt3) % g.nt2;
@@ -76,12 +78,12 @@ kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
 #pragma unroll
     for (int k = 0; k < KRON_MO; ++k) acc[o][k] = T(0);
 
+  int staged = -1;
   for (int t = 0; t < job.nterms; ++t) {
     const T* A1 = job.b[0][t];
     const T* A2 = job.b[1][t];
     const T* A3 = job.b[2][t];
     const int xi = job.xin[t];
-    const T* __restrict__ x = xi == 0 ? job.x[0] : (xi == 1 ? job.x[1] : job.x[2]);
     for (int idx = threadIdx.x; idx < (T1 + T2 + T3) * B; idx += blockDim.x) {
       int r = idx / B, o = idx - r * B;
       T v = T(0);
@@ -89,8 +91,24 @@ kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
       else if (r < T1 + T2) { int i = I2 + r - T1; if (i < n2) v = A2[(size_t)i * B + o]; a2[(r - T1) * B + o] = v; }
       else { int i = I3 + r - T1 - T2; if (i < n3) v = A3[(size_t)i * B + o]; a3[(r - T1 - T2) * B + o] = v; }
     }
+    if (xi != staged) {
+      // the (H1 x H2 x T3+2P) slab of this term's input, zero outside the
+      // domain, read once per input (the terms are grouped by input)
+      const T* __restrict__ x = xi == 0 ? job.x[0] : (xi == 1 ? job.x[1] : job.x[2]);
+      for (int idx = threadIdx.x; idx < H1 * H2 * T3h; idx += blockDim.x) {
+        const int kk = idx % T3h;
+        const int ac = idx / T3h;
+        const int c = ac % H2, a = ac / H2;
+        const int j1 = I1 + a - P, j2 = I2 + c - P, j3 = I3 + kk - P;
+        T v = T(0);
+        if (j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < n2 && j3 >= 0 && j3 < n3)
+          v = __ldg(x + ((size_t)j1 * n2 + j2) * n3 + j3);
+        xs[idx] = v;
+      }
+      staged = xi;
+    }
     __syncthreads();
-    // mode 3 on the (H1 x H2) halo slab of the i3 tile
+    // mode 3 on the (H1 x H2) halo slab of the i3 tile, from shared memory
     for (int idx = threadIdx.x; idx < H1 * H2 * T3; idx += blockDim.x) {
       int k = idx % T3;
       int ac = idx / T3;
@@ -98,12 +116,9 @@ kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
       int j1 = I1 + a - P, j2 = I2 + c - P, i3 = I3 + k;
       T s = T(0);
       if (j1 >= 0 && j1 < n1 && j2 >= 0 && j2 < n2 && i3 < n3) {
-        const T* xr = x + ((size_t)j1 * n2 + j2) * n3;
+        const T* xr = xs + (size_t)ac * T3h + k;
 #pragma unroll
-        for (int o = 0; o < B; ++o) {
-          int j3 = i3 + o - P;
-          if (j3 >= 0 && j3 < n3) s += a3[k * B + o] * __ldg(xr + j3);
-        }
+        for (int o = 0; o < B; ++o) s += a3[k * B + o] * xr[o];
       }
       z3[idx] = s;
     }
@@ -205,15 +220,15 @@ __global__ void mode_product_kernel(const T* __restrict__ A, int mode, int n1, i
 // rows outside the domain cost nothing (the kernel skips them), so a
 // direction covered by one or two tiles pays little halo.  Ties go to the
 // thicker i3 slab, which re-reads less of the x halo.
-static KronTile choose_tile(int n1, int n2, int n3, int P, int nsm) {
-  struct Key { int n1, n2, n3, P, nsm; };
+static KronTile choose_tile(int n1, int n2, int n3, int P, int nsm, int es) {
+  struct Key { int n1, n2, n3, P, nsm, es; };
   static std::mutex mu;
   static std::vector<std::pair<Key, KronTile>> cache;
   {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& e : cache)
       if (e.first.n1 == n1 && e.first.n2 == n2 && e.first.n3 == n3 && e.first.P == P &&
-          e.first.nsm == nsm)
+          e.first.nsm == nsm && e.first.es == es)
         return e.second;
   }
   auto span = [](int n, int T, int P) {
@@ -234,6 +249,12 @@ static KronTile choose_tile(int n1, int n2, int n3, int P, int nsm) {
       for (int t3 = 1; t3 <= max3; ++t3) {
         int nt3 = (n3 + t3 - 1) / t3;
         if (nt3 > 1 && (n3 + nt3 - 1) / nt3 != t3) continue;    // balanced slabs only
+        // shared memory (mode-3 and mode-2 results, bands, the x slab) small
+        // enough for two CTAs per SM
+        const size_t h1f = t1 + 2 * P, h2f = t2 + 2 * P;
+        const size_t sm = (h1f * h2f * t3 + h1f * t2 * t3 + (size_t)(t1 + t2 + t3) * (2 * P + 1) +
+                           h1f * h2f * (t3 + 2 * P)) * es;
+        if (sm > 113 * 1024) continue;
         double w = (double)t3 * ((double)h1 * h2 + (double)h1 * t2 + (double)t1 * t2);
         double waves = std::ceil((double)nt12 * nt3 / nsm);
         double c = waves * w;
@@ -249,7 +270,7 @@ static KronTile choose_tile(int n1, int n2, int n3, int P, int nsm) {
   best.nt3 = (n3 + best.T3 - 1) / best.T3;
   std::lock_guard<std::mutex> lk(mu);
   if (cache.size() > 64) cache.clear();
-  cache.push_back({Key{n1, n2, n3, P, nsm}, best});
+  cache.push_back({Key{n1, n2, n3, P, nsm, es}, best});
   return best;
 }
 
@@ -257,7 +278,8 @@ template <typename T, int P, int NY>
 static void launch_kron_job(iga_ctx* ctx, const KronJob<T>& job, const KronTile& g) {
   constexpr int B = 2 * P + 1;
   size_t H1 = g.T1 + 2 * P, H2 = g.T2 + 2 * P;
-  size_t smem = (H1 * H2 * g.T3 + H1 * g.T2 * g.T3 + (size_t)(g.T1 + g.T2 + g.T3) * B) * sizeof(T);
+  size_t smem = (H1 * H2 * g.T3 + H1 * g.T2 * g.T3 + (size_t)(g.T1 + g.T2 + g.T3) * B +
+                 H1 * H2 * (g.T3 + 2 * P)) * sizeof(T);
   IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: tile does not fit in shared memory");
   func_attr(kron_rank1_kernel<T, P, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   {
@@ -293,7 +315,7 @@ static const T* band_ptr(const iga_op* A, int d, size_t k) {
 
 template <typename T, int P>
 static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T beta, T* y) {
-  KronTile g = choose_tile(A->n[0], A->n[1], A->n[2], P, ctx->nsm);
+  KronTile g = choose_tile(A->n[0], A->n[1], A->n[2], P, ctx->nsm, (int)sizeof(T));
   // terms in chunks of KRON_MAXTERMS (beta applies to the first chunk only)
   size_t nterm = A->blocks.size();
   for (size_t c0 = 0; c0 < nterm || c0 == 0; c0 += KRON_MAXTERMS) {
@@ -320,7 +342,7 @@ static void kron_rank1(iga_ctx* ctx, const iga_op* A, T alpha, const T* x, T bet
 template <typename T, int P>
 static void kkt_rank1(iga_ctx* ctx, const iga_op* M, const iga_op* K, T beta, const T* z,
                       T* out) {
-  KronTile g = choose_tile(M->n[0], M->n[1], M->n[2], P, ctx->nsm);
+  KronTile g = choose_tile(M->n[0], M->n[1], M->n[2], P, ctx->nsm, (int)sizeof(T));
   size_t N = (size_t)M->n[0] * M->n[1] * M->n[2];
   KronJob<T> job{};
   int cnt = 0;
