@@ -84,6 +84,7 @@ def parse():
     ap.add_argument("--c5-tol", type=float, default=1e-4)
     ap.add_argument("--c5-trunc", type=float, default=1e-6)
     ap.add_argument("--c5-sweeps", type=int, default=4)
+    ap.add_argument("--c5-state-weight", type=float, default=1.0)
     ap.add_argument("--ttm-elements", type=int, default=512,
                     help="elements per direction of the --only ttm grid")
     ap.add_argument("--ttm-kinds", default="tf32,bf16", help="operand types of --only ttm")
@@ -423,7 +424,7 @@ def config5_assembly(ctx, iga, torch):
     return out
 
 
-def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, rows=512):
+def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, state_weight=1.0, rows=512):
     """The random-volume KKT solve (degree 2, 512 elements per direction,
     beta 1e-6, 1.34e8 unknowns per field) without any full-size operator
     apply (IGA_RESID_LOCAL, the solution as the block TT), mixed precision
@@ -447,13 +448,14 @@ def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, rows=512):
     pts = np.stack([rng.integers(0, ni[d], rows) for d in range(3)], axis=1)
     out = {"workload": work.name, "unknowns_per_field": N, "beta": work.beta,
            "residual_mode": "projected residuals, Khatri-Rao sketches (IGA_RESID_LOCAL)",
-           "tol_projected": tol, "trunc_tol": trunc_tol}
+           "tol_projected": tol, "trunc_tol": trunc_tol, "state_weight": state_weight}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ty, tu, tl, info = iga.iga_kkt_solve_amen_tt(ctx, M, K, load, work.beta, tol=tol,
                                                  precision=iga.IGA_TF32,
                                                  residual=iga.IGA_RESID_LOCAL,
-                                                 max_sweeps=max_sweeps, trunc_tol=trunc_tol)
+                                                 max_sweeps=max_sweeps, trunc_tol=trunc_tol,
+                                                 state_weight=state_weight)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     res = iga.iga_kkt_residual_rows(ctx, M, K, work.beta, load, ty, tu, tl, pts)
@@ -463,7 +465,27 @@ def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, rows=512):
                     "projected_residual": info["residual"], "converged": info["converged"],
                     "residual_estimate": est, "rows_sampled": rows,
                     "device_s_by_phase": {"local": info["t_local"], "move": info["t_move"]}}
-    del M, K, load, ty, tu, tl
+    del ty, tu, tl
+    # the tensor-core GEMMs of the local operator (right-interface products,
+    # banded middle-core contraction, left-interface products) against the
+    # TF32 rate, over the first two sweeps of the same solve (a separate run:
+    # the per-launch events would slow the timed one)
+    pk, pk_kind = peaks()
+    ctx.profile_begin("tc_gemm_tf32_kernel")
+    iga.iga_kkt_solve_amen_tt(ctx, M, K, load, work.beta, tol=tol, precision=iga.IGA_TF32,
+                              residual=iga.IGA_RESID_LOCAL, max_sweeps=2, trunc_tol=trunc_tol,
+                              state_weight=state_weight)
+    p = ctx.profile_end()
+    if p["launches"] > 0 and p["ms"] > 0:
+        ach = p["flops"] / (p["ms"] * 1e-3) / 1e12
+        peak = pk["bf16_tflops"] * TF32_PER_BF16
+        out["local_contraction_roofline"] = {
+            "kernel": "tc_gemm_tf32_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "launches": p["launches"],
+            "device_ms": p["ms"], "algorithmic_flops": p["flops"],
+            "peak_kind": f"{pk_kind} BF16 GEMM rate x 1.1/2.25 (nominal TF32/BF16)",
+            "sample": "first two sweeps"}
+    del M, K, load
     torch.cuda.empty_cache()
     return out
 
@@ -712,7 +734,7 @@ def run_gpu(args, world, rank, local):
         "rank_tables": rank_tables(ctx),
         "config5_assembly": config5_assembly(ctx, iga, torch),
         "config5_solve": config5_solve(ctx, iga, torch, args.c5_tol, args.c5_trunc,
-                                       args.c5_sweeps),
+                                       args.c5_sweeps, args.c5_state_weight),
         "storage": {work.name: report.storage(ctx, work.geometry, work.space, work.target,
                                               work.tol)},
         "alu_rates_measured_tflops": {"fp64": iga.iga_measure_fma(ctx, iga.IGA_FP64),
@@ -785,7 +807,8 @@ def main():
         from paper_1811_06797_gb300 import build, iga
         build.build()
         torch.cuda.set_device(local)
-        out = config5_solve(iga.Context(), iga, torch, args.c5_tol, args.c5_trunc, args.c5_sweeps)
+        out = config5_solve(iga.Context(), iga, torch, args.c5_tol, args.c5_trunc, args.c5_sweeps,
+                            args.c5_state_weight)
         if rank == 0:
             print(json.dumps({"config5_solve": out}))
         return

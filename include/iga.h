@@ -432,6 +432,11 @@ typedef struct {
   int truncation;      /* how the block index moves: IGA_TRUNC_PIVOTED or
                           IGA_TRUNC_SVD (see iga_trunc) */
   int residual;        /* IGA_RESID_FULL or IGA_RESID_LOCAL (see iga_residual) */
+  double state_weight; /* weight of the state y in the truncation of the block
+                          core: y is kept to a relative error of about
+                          trunc_tol / state_weight, u and lambda to trunc_tol
+                          (the stiffness operator amplifies the error of y in
+                          the state equation's residual); <= 1: no weight */
 } iga_solve_opts;
 
 typedef struct {

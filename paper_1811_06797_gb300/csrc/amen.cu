@@ -333,9 +333,11 @@ __global__ void permute_fwd_kernel(const double* __restrict__ Xh, int r, int n, 
 }
 
 // Normalise the three field components inside a block Gram matrix: for the
-// index layout (l, j), j < r, G_(l j),(m k) *= s_l s_m with s_l = 1 / ||block l||,
+// index layout (l, j), j < r, G_(l j),(m k) *= s_l s_m with s_l = w_l / ||block l||
+// (w_0 = w0, the state's weight; w_1 = w_2 = 1),
 // ||block l||^2 = sum_j G_(l j),(l j).  Returns the scales in s (3 values).
-__global__ void gram_block_scale_kernel(double* __restrict__ G, int r, double* __restrict__ s) {
+__global__ void gram_block_scale_kernel(double* __restrict__ G, int r, double* __restrict__ s,
+                                        double w0) {
   __shared__ double sc[3];
   int k = 3 * r;
   if (threadIdx.x < 3) {
@@ -344,7 +346,7 @@ __global__ void gram_block_scale_kernel(double* __restrict__ G, int r, double* _
       int i = threadIdx.x * r + j;
       t += G[(size_t)i * k + i];
     }
-    sc[threadIdx.x] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    sc[threadIdx.x] = t > 0.0 ? (threadIdx.x == 0 ? w0 : 1.0) / sqrt(t) : 0.0;
     s[threadIdx.x] = sc[threadIdx.x];
   }
   __syncthreads();
@@ -1378,6 +1380,7 @@ struct Solver {
   double inner_tol;
   double trunc_tol;
   bool svd_moves = false;        // Gram eigen-decomposition instead of pivoted Cholesky
+  double w0 = 1.0;               // weight of the state y in the truncation
   bool tc_local = false;         // FP32 solve: large interface products on the tensor cores (TF32)
   CoreNZ nz[2][3];
   DevBuf<double> X[3];                 // TT cores (FP64 master)
@@ -1747,7 +1750,7 @@ struct Solver {
     const int jm = std::min(rmax, m);
     double* Q = slot(11, (size_t)m * std::min(jm + ke, m));
     int* rkd = scratch<int>(ctx, SLOT_AMEN_BASE + 18, 1);
-    qrcp_truncate(ctx, B, m, c3, si, sa, rg, E, ke, trunc_tol, jm, Q, rkd);
+    qrcp_truncate(ctx, B, m, c3, si, sa, rg, E, ke, trunc_tol, jm, Q, rkd, w0);
     int rk = 1;
     IGA_CUDA(cudaMemcpyAsync(&rk, rkd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1772,7 +1775,7 @@ struct Solver {
       // block core is normalised before the eigen-decomposition (the kept
       // coefficients below are exact projections of the unscaled core)
       double* sc = slot(17, 3);
-      IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r1, sc);
+      IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r1, sc, w0);
       jacobi_eig(ctx, G, V, w, c3);      // V col-major: columns = right singular vectors
       IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r1, sc);
       std::vector<double> lam(c3);
@@ -1822,7 +1825,7 @@ struct Solver {
       double* w = slot(9, c3);
       rm_gemm(ctx, false, true, c3, c3, m, Mx, m, Mx, m, G, c3);
       double* sc = slot(17, 3);
-      IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r0, sc);
+      IGA_LAUNCH(ctx, gram_block_scale_kernel, 1, 256, 0, G, r0, sc, w0);
       jacobi_eig(ctx, G, V, w, c3);                 // columns: left singular vectors
       IGA_LAUNCH(ctx, scale_vrows_kernel, nblk((size_t)c3 * c3), 256, 0, V, r0, sc);
       std::vector<double> lam(c3);
@@ -2509,6 +2512,7 @@ static void solver_init(Solver<T>& S, iga_ctx* ctx, const iga_op* M, const iga_o
   // the solution, so truncate well below the residual target
   S.trunc_tol = o->trunc_tol > 0.0 ? o->trunc_tol : 1e-3 * tol;
   S.svd_moves = o->truncation == IGA_TRUNC_SVD;
+  S.w0 = o->state_weight > 1.0 ? o->state_weight : 1.0;
   S.tc_local = o->precision == IGA_TF32;
   S.verbose = o->verbose;
   for (int op = 0; op < 2; ++op)
@@ -2712,6 +2716,8 @@ extern "C" void iga_solve_opts_default(iga_solve_opts* o) {
   o->verbose = 0;
   o->trunc_tol = 0.0;
   o->truncation = IGA_TRUNC_PIVOTED;
+  o->residual = IGA_RESID_FULL;
+  o->state_weight = 1.0;
 }
 
 // The solve behind both entry points: the fields into y, u, lam (full

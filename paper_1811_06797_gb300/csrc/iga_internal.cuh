@@ -239,11 +239,13 @@ void gen_eig_prep(iga_ctx* ctx, const double* PM, int SM, const double* PK, int 
                   double* work, double* C, double* Linv);
 void householder_qr(iga_ctx* ctx, double* Y, double* Q, int m, int k);  // Y overwritten
 // truncated QR with column pivoting of B (m x c3, B(i, a) = B[i si + a sa],
-// field groups of r columns normalised), then kick extra columns E (m x kick
+// field groups of r columns normalised, the first one weighted by w0), then
+// kick extra columns E (m x kick
 // col-major) orthogonalised; Q (m x min(rk + kick, m), col-major) and *rk_dev
 // (device) receive the basis and the number of pivoted columns
 void qrcp_truncate(iga_ctx* ctx, const double* B, int m, int c3, int si, int sa, int r,
-                   const double* E, int kick, double rel, int jmax, double* Q, int* rk_dev);
+                   const double* E, int kick, double rel, int jmax, double* Q, int* rk_dev,
+                   double w0 = 1.0);
 void fill_gaussian(iga_ctx* ctx, double* x, size_t n, uint64_t seed);
 void transpose_cm(iga_ctx* ctx, const double* A, int rows, int cols, double* B);
 

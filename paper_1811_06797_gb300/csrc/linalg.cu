@@ -378,6 +378,7 @@ struct QrcpArgs {
   double* gwork;     // nullptr: slices in shared memory
   int* rk;           // device: number of pivoted columns
   double rel;
+  double w0;         // weight of the first field group
   int m, c3, si, sa, r, kick, jmax, mc;
 };
 
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
   }
   double sc[3], tot = 0.0;
   for (int g = 0; g < 3; ++g) {
-    sc[g] = gsum[g] > 0.0 ? 1.0 / sqrt(gsum[g]) : 0.0;
+    sc[g] = gsum[g] > 0.0 ? (g == 0 ? a.w0 : 1.0) / sqrt(gsum[g]) : 0.0;
     tot += gsum[g] > 0.0 ? 1.0 : 0.0;
   }
   for (int t = tid; t < mc * a.c3; t += blockDim.x) A[t] *= sc[(t / mc) / a.r];
@@ -616,7 +617,8 @@ __global__ void __launch_bounds__(256) qrcp_cluster_kernel(QrcpArgs a) {
 static int qr_cluster_max(iga_ctx* ctx);
 
 void qrcp_truncate(iga_ctx* ctx, const double* B, int m, int c3, int si, int sa, int r,
-                   const double* E, int kick, double rel, int jmax, double* Q, int* rk_dev) {
+                   const double* E, int kick, double rel, int jmax, double* Q, int* rk_dev,
+                   double w0) {
   IGA_REQUIRE(m >= 1 && c3 >= 1 && r >= 1 && c3 <= 3 * r && kick >= 0, "qrcp: bad sizes");
   const size_t limit = 200 * 1024;
   const int cmax = qr_cluster_max(ctx);
@@ -629,7 +631,7 @@ void qrcp_truncate(iga_ctx* ctx, const double* B, int m, int c3, int si, int sa,
   const size_t slice = (size_t)mc * ncol * sizeof(double);
   IGA_REQUIRE(head <= limit, "qrcp: too many columns");
   QrcpArgs a;
-  a.B = B; a.E = E; a.Q = Q; a.rk = rk_dev; a.rel = rel;
+  a.B = B; a.E = E; a.Q = Q; a.rk = rk_dev; a.rel = rel; a.w0 = w0 > 1.0 ? w0 : 1.0;
   a.m = m; a.c3 = c3; a.si = si; a.sa = sa; a.r = r; a.kick = kick;
   a.jmax = std::max(1, std::min(jmax, m)); a.mc = mc;
   a.gwork = head + slice <= limit ? nullptr : scratch<double>(ctx, SLOT_QRCP_WORK, (size_t)C * mc * ncol);

@@ -49,7 +49,8 @@ class SolveOpts_(C.Structure):
     _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("max_sweeps", C.c_int),
                 ("kick_rank", C.c_int), ("rmax", C.c_int), ("local_maxit", C.c_int),
                 ("refine_max", C.c_int), ("precision", C.c_int), ("verbose", C.c_int),
-                ("trunc_tol", C.c_double), ("truncation", C.c_int), ("residual", C.c_int)]
+                ("trunc_tol", C.c_double), ("truncation", C.c_int), ("residual", C.c_int),
+                ("state_weight", C.c_double)]
 
 
 class SolveInfo_(C.Structure):
