@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--c5-tol", type=float, default=1e-4)
     ap.add_argument("--c5-trunc", type=float, default=1e-6)
     ap.add_argument("--c5-sweeps", type=int, default=4)
-    ap.add_argument("--c5-state-weight", type=float, default=1.0)
+    ap.add_argument("--c5-state-weight", type=float, default=1000.0)
     ap.add_argument("--ttm-elements", type=int, default=512,
                     help="elements per direction of the --only ttm grid")
     ap.add_argument("--ttm-kinds", default="tf32,bf16", help="operand types of --only ttm")
