@@ -207,3 +207,22 @@ def test_tf32_solve_with_tensor_core_band_contraction(env, name, work, resid):
     yo, uo, lo = kkt_solve(Mo, Ko, work.beta, b)
     for got, ref in ((y, yo), (u, uo), (lam, lo)):
         assert _rel(got, ref) < 1e-6, (name, _rel(got, ref))
+
+
+@pytest.mark.parametrize("trunc", [0, 1], ids=["pivoted", "svd"])
+def test_state_weight_keeps_the_solution(env, trunc):
+    """A weighted state in the truncation (state_weight) changes the ranks the
+    solve keeps, never the solution it converges to."""
+    ctx, torch, iga = env
+    work = CASES[3][1]
+    M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    N = int(np.prod(M.info()["n"]))
+    y, u, lam = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+    info = iga.iga_kkt_solve_amen(ctx, M, K, load, work.beta, y, u, lam, tol=1e-10,
+                                  truncation=trunc, residual=iga.IGA_RESID_LOCAL,
+                                  max_sweeps=12, state_weight=1e3)
+    assert info["converged"], info
+    Mo, Ko, b = _oracle_system(work)
+    yo, uo, lo = kkt_solve(Mo, Ko, work.beta, b)
+    for got, ref in ((y, yo), (u, uo), (lam, lo)):
+        assert _rel(got.cpu().numpy(), ref) < 1e-6
