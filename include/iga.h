@@ -127,9 +127,11 @@ iga_status iga_measure_fma(iga_ctx* ctx, iga_prec prec, double* tflops);
  * op(A_i) M x K, op(B_i) K x N, A_i = A + i sA (elements; likewise B, C),
  * op = transpose when tA / tB is nonzero (A_i then K x M with leading
  * dimension lda).  Device pointers in FP64 (prec IGA_FP64) or FP32
- * (IGA_FP32); the caller owns them.  Deterministic: a reduction split over K
- * is summed in a fixed order.  Queued on the context stream (no
- * synchronisation).  IGA_EINVAL for a null pointer, a negative size or a
+ * (IGA_FP32 on the CUDA cores; IGA_TF32 on the tcgen05 tensor cores with
+ * TF32 operands and FP32 accumulation, which synchronises and returns
+ * IGA_ETIMEOUT if a bounded wait of its pipeline gives up); the caller owns
+ * them.  Deterministic: a reduction split over K is summed in a fixed order.
+ * Queued on the context stream (no synchronisation) except for IGA_TF32.  IGA_EINVAL for a null pointer, a negative size or a
  * leading dimension shorter than a row. */
 iga_status iga_gemm_batched(iga_ctx* ctx, iga_prec prec, int tA, int tB, int M, int N, int K,
                             double alpha, const void* A, int lda, long long sA, const void* B,

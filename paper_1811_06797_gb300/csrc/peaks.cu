@@ -92,8 +92,13 @@ extern "C" iga_status iga_gemm_batched(iga_ctx* ctx, iga_prec prec, int tA, int 
       gemm_rm_batched<float>(ctx, tA != 0, tB != 0, M, N, K, (float)alpha, (const float*)A, lda,
                              sA, (const float*)B, ldb, sB, (float)beta, (float*)C, ldc, sC,
                              count);
-    else
-      throw Error(IGA_EINVAL, "gemm_batched: precision must be IGA_FP64 or IGA_FP32");
+    else if (prec == IGA_TF32) {
+      tc_flag_reset(ctx);
+      tc_gemm_tf32(ctx, tA != 0, tB != 0, false, M, N, K, (float)alpha, (const float*)A, lda, sA,
+                   (const float*)B, ldb, sB, (float)beta, (float*)C, ldc, sC, count);
+    } else
+      throw Error(IGA_EINVAL, "gemm_batched: precision must be IGA_FP64, IGA_FP32 or IGA_TF32");
+    if (prec == IGA_TF32) tc_flag_check(ctx, "gemm_batched");
     return IGA_OK;
   } catch (const Error& e) {
     set_error(ctx, e.what());

@@ -68,6 +68,7 @@ struct TcGemmArgs {
   int ldc;
   long long sC;
   int tA, tB, tC;
+  int vecA, vecB;        // 16-byte loads (aligned base, stride and batch stride)
   int NT;                // columns per CTA (multiple of 16, <= 256)
   int tcols;             // tensor-memory columns allocated
   int* err;
@@ -126,27 +127,84 @@ __global__ void __launch_bounds__(TCG_THREADS) tc_gemm_tf32_kernel(const TcGemmA
     const int k0 = c * TCG_KC;
     unsigned char* a_st = sA + s * AST;
     unsigned char* b_st = sB + s * BST;
-    // op(A): 16 row groups x 8 k-quads = 128 core matrices, 32 per warp
-    for (int cm = warp; cm < 128; cm += 4) {
-      const int rg = cm >> 3, kq = cm & 7;
-      int r, kk;
-      if (g.tA) { r = lane & 7; kk = lane >> 3; }
-      else { r = lane >> 2; kk = lane & 3; }
-      const int m = m0 + rg * 8 + r, k = k0 + kq * 4 + kk;
-      float v = 0.f;
-      if (m < g.M && k < g.K) v = g.tA ? A[(size_t)k * g.lda + m] : A[(size_t)m * g.lda + k];
-      *reinterpret_cast<float*>(a_st + rg * SBO + kq * 128 + r * 16 + kk * 4) = v;
+    // op(A): 16 row groups x 8 k-quads = 128 core matrices
+    if (g.vecA) {
+      // 16-byte loads of four elements contiguous in memory (k for a
+      // row-major A, m for a transposed one): a warp covers four core matrices
+      for (int cm0 = warp * 4; cm0 < 128; cm0 += 16) {
+        const int cm = cm0 + (lane >> 3), rg = cm >> 3, kq = cm & 7, t = lane & 7;
+        if (!g.tA) {
+          const int m = m0 + rg * 8 + t, k = k0 + kq * 4;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (m < g.M && k + 3 < g.K)
+            v = *reinterpret_cast<const float4*>(A + (size_t)m * g.lda + k);
+          else if (m < g.M)
+            for (int u = 0; u < 4; ++u)
+              if (k + u < g.K) (&v.x)[u] = A[(size_t)m * g.lda + k + u];
+          *reinterpret_cast<float4*>(a_st + rg * SBO + kq * 128 + t * 16) = v;
+        } else {
+          const int kk = t & 3, mq = t >> 2;
+          const int m = m0 + rg * 8 + mq * 4, k = k0 + kq * 4 + kk;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (k < g.K && m + 3 < g.M)
+            v = *reinterpret_cast<const float4*>(A + (size_t)k * g.lda + m);
+          else if (k < g.K)
+            for (int u = 0; u < 4; ++u)
+              if (m + u < g.M) (&v.x)[u] = A[(size_t)k * g.lda + m + u];
+          unsigned char* base = a_st + rg * SBO + kq * 128 + (mq * 4) * 16 + kk * 4;
+          for (int u = 0; u < 4; ++u) *reinterpret_cast<float*>(base + u * 16) = (&v.x)[u];
+        }
+      }
+    } else {
+      for (int cm = warp; cm < 128; cm += 4) {
+        const int rg = cm >> 3, kq = cm & 7;
+        int r, kk;
+        if (g.tA) { r = lane & 7; kk = lane >> 3; }
+        else { r = lane >> 2; kk = lane & 3; }
+        const int m = m0 + rg * 8 + r, k = k0 + kq * 4 + kk;
+        float v = 0.f;
+        if (m < g.M && k < g.K) v = g.tA ? A[(size_t)k * g.lda + m] : A[(size_t)m * g.lda + k];
+        *reinterpret_cast<float*>(a_st + rg * SBO + kq * 128 + r * 16 + kk * 4) = v;
+      }
     }
     // op(B)^T: NT/8 row groups (rows n) x 8 k-quads
-    for (int cm = warp; cm < (NT / 8) * 8; cm += 4) {
-      const int rg = cm >> 3, kq = cm & 7;
-      int r, kk;
-      if (g.tB) { r = lane >> 2; kk = lane & 3; }
-      else { r = lane & 7; kk = lane >> 3; }
-      const int n = n0 + rg * 8 + r, k = k0 + kq * 4 + kk;
-      float v = 0.f;
-      if (n < g.N && k < g.K) v = g.tB ? B[(size_t)n * g.ldb + k] : B[(size_t)k * g.ldb + n];
-      *reinterpret_cast<float*>(b_st + rg * SBO + kq * 128 + r * 16 + kk * 4) = v;
+    if (g.vecB) {
+      for (int cm0 = warp * 4; cm0 < (NT / 8) * 8; cm0 += 16) {
+        const int cm = cm0 + (lane >> 3), rg = cm >> 3, kq = cm & 7, t = lane & 7;
+        if (cm >= (NT / 8) * 8) continue;
+        if (g.tB) {
+          const int n = n0 + rg * 8 + t, k = k0 + kq * 4;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (n < g.N && k + 3 < g.K)
+            v = *reinterpret_cast<const float4*>(B + (size_t)n * g.ldb + k);
+          else if (n < g.N)
+            for (int u = 0; u < 4; ++u)
+              if (k + u < g.K) (&v.x)[u] = B[(size_t)n * g.ldb + k + u];
+          *reinterpret_cast<float4*>(b_st + rg * SBO + kq * 128 + t * 16) = v;
+        } else {
+          const int kk = t & 3, nq = t >> 2;
+          const int n = n0 + rg * 8 + nq * 4, k = k0 + kq * 4 + kk;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (k < g.K && n + 3 < g.N)
+            v = *reinterpret_cast<const float4*>(B + (size_t)k * g.ldb + n);
+          else if (k < g.K)
+            for (int u = 0; u < 4; ++u)
+              if (n + u < g.N) (&v.x)[u] = B[(size_t)k * g.ldb + n + u];
+          unsigned char* base = b_st + rg * SBO + kq * 128 + (nq * 4) * 16 + kk * 4;
+          for (int u = 0; u < 4; ++u) *reinterpret_cast<float*>(base + u * 16) = (&v.x)[u];
+        }
+      }
+    } else {
+      for (int cm = warp; cm < (NT / 8) * 8; cm += 4) {
+        const int rg = cm >> 3, kq = cm & 7;
+        int r, kk;
+        if (g.tB) { r = lane >> 2; kk = lane & 3; }
+        else { r = lane & 7; kk = lane >> 3; }
+        const int n = n0 + rg * 8 + r, k = k0 + kq * 4 + kk;
+        float v = 0.f;
+        if (n < g.N && k < g.K) v = g.tB ? B[(size_t)n * g.ldb + k] : B[(size_t)k * g.ldb + n];
+        *reinterpret_cast<float*>(b_st + rg * SBO + kq * 128 + r * 16 + kk * 4) = v;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -218,6 +276,12 @@ void tc_gemm_tf32(iga_ctx* ctx, bool tA, bool tB, bool tC, int M, int N, int K, 
   a.A = A; a.lda = lda; a.sA = sA; a.B = B; a.ldb = ldb; a.sB = sB;
   a.C = C; a.ldc = ldc; a.sC = sC;
   a.tA = tA; a.tB = tB; a.tC = tC;
+  // 16-byte operand loads when every row (or column) starts 16-byte aligned
+  auto al16 = [](const float* p, int ld, long long st) {
+    return ((uintptr_t)p % 16 == 0) && ld % 4 == 0 && st % 4 == 0;
+  };
+  a.vecA = al16(A, lda, sA);
+  a.vecB = al16(B, ldb, sB);
   a.NT = std::min(256, (N + 15) / 16 * 16);
   a.tcols = 32;
   while (a.tcols < a.NT) a.tcols *= 2;

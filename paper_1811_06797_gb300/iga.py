@@ -219,10 +219,10 @@ def iga_measure_fma(ctx, prec):
     return r.value
 
 
-def iga_gemm_batched(ctx, A, B, C, alpha=1.0, beta=0.0, tA=False, tB=False):
+def iga_gemm_batched(ctx, A, B, C, alpha=1.0, beta=0.0, tA=False, tB=False, tf32=False):
     """C[i] = alpha op(A[i]) op(B[i]) + beta C[i] for contiguous CUDA tensors
     of shape (count, rows, cols), all FP64 or all FP32, through the library's
-    own dense product."""
+    own dense product (tf32: FP32 tensors on the tensor cores)."""
     import torch
     for t in (A, B, C):
         if not (t.is_cuda and t.is_contiguous() and t.dim() == 3):
@@ -237,6 +237,10 @@ def iga_gemm_batched(ctx, A, B, C, alpha=1.0, beta=0.0, tA=False, tB=False):
     if Kb != K or tuple(C.shape) != (count, M, N) or B.shape[0] != count:
         raise IgaError(1, "gemm_batched: shape mismatch")
     prec = IGA_FP64 if A.dtype == torch.float64 else IGA_FP32
+    if tf32:
+        if prec != IGA_FP32:
+            raise IgaError(1, "gemm_batched: the TF32 path takes FP32 tensors")
+        prec = IGA_TF32
     _check(ctx, lib().iga_gemm_batched(
         ctx.handle, prec, int(tA), int(tB), M, N, K, float(alpha), _ptr(A), A.shape[2],
         A.shape[1] * A.shape[2], _ptr(B), B.shape[2], B.shape[1] * B.shape[2], float(beta),

@@ -93,3 +93,28 @@ def test_gemm_rejects_mismatched_shapes(ctx):
         iga.iga_gemm_batched(ctx, A, B, C)
     with pytest.raises(iga.IgaError):
         iga.iga_gemm_batched(ctx, A, B.float(), C)
+
+
+# shapes whose leading dimensions are multiples of 4 (16-byte operand loads,
+# with ragged tiles) and shapes whose are not (scalar loads)
+@pytest.mark.parametrize("shape", [(4, 128, 256, 96), (2, 260, 44, 36), (1, 300, 40, 70),
+                                   (3, 775, 38, 190), (2, 33, 17, 5), (1, 1000, 130, 33)])
+@pytest.mark.parametrize("tA,tB", [(False, False), (True, False), (False, True), (True, True)])
+def test_gemm_tf32_tensor_cores_match_torch(ctx, shape, tA, tB):
+    """The tcgen05 TF32 product against the FP64 product of the same FP32
+    inputs, within the TF32 rounding of the operands (10-bit mantissa)."""
+    from paper_1811_06797_gb300 import iga
+    count, M, N, K = shape
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 7 * K)
+    A = torch.randn((count, K, M) if tA else (count, M, K), device="cuda", dtype=torch.float32,
+                    generator=g)
+    B = torch.randn((count, N, K) if tB else (count, K, N), device="cuda", dtype=torch.float32,
+                    generator=g)
+    C0 = torch.randn((count, M, N), device="cuda", dtype=torch.float32, generator=g)
+    C = C0.clone()
+    iga.iga_gemm_batched(ctx, A, B, C, alpha=0.5, beta=-1.0, tA=tA, tB=tB, tf32=True)
+    a = A.transpose(1, 2) if tA else A
+    b = B.transpose(1, 2) if tB else B
+    ref = 0.5 * torch.bmm(a.double(), b.double()) - C0.double()
+    tol = 4 * 2.0 ** -10 * K ** 0.5 + 1e-5
+    assert (C.double() - ref).abs().max().item() <= tol
