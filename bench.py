@@ -726,7 +726,8 @@ def run_gpu(args, world, rank, local):
         "paths": paths,
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(3 * N * 8)},
-        "gpu_launches": int(launches / max(1, args.steps)),
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": int(launches / max(1, args.steps)),
         "roofline": roof,
         "kron_roofline": kron_roof,
         "ttm_roofline": ttm_roofline(ctx, iga, torch, pk, pk_kind),
