@@ -23,11 +23,11 @@
 //   * one thread issues the MMAs: slab j2 contributes to the 2P+1 outputs
 //     i2 = j2 - P + t, whose FP32 accumulators form a ring of 2P+1 tensor-
 //     memory column blocks (per half of the tile); contiguous targets are
-//     one MMA with N = (targets) x R1p columns;
+//     one MMA with N = (targets) x R1p columns, and the first MMA into a
+//     target (its first slab, first K step) overwrites the accumulator;
 //   * epilogue warps drain an accumulator as soon as its last slab is in
-//     (tcgen05.ld), zero it for its next use (tcgen05.st), apply the banded
-//     mode-1 product across the lanes through shared memory and add the
-//     result into y.
+//     (tcgen05.ld), apply the banded mode-1 product across the lanes
+//     through shared memory and add the result into y.
 // Z and the A2 column are double buffered, so the mode-3 product and the copy
 // of slab j2+1 overlap the MMAs of slab j2, and the epilogue of i2 overlaps
 // them too.  Every wait on an mbarrier is bounded: a wait that gives up sets
@@ -152,16 +152,6 @@ __device__ __forceinline__ void tc_wait_ld16(uint32_t* r) {
                  "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
                :
                : "memory");
-}
-__device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
-  const uint32_t z = 0u;
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
-      "r"(z)
-      : "memory");
-}
-__device__ __forceinline__ void tc_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 // named barrier over the epilogue warps with an OR of `pred` handed to all
 __device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
@@ -310,17 +300,7 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  // accumulators start at zero (every MMA accumulates; the epilogue zeroes an
-  // accumulator again after draining it)
-  if (warp >= NPW && warp < 2 * NPW) {
-    const int e = warp - NPW, h = e >> 2, q = e & 3;
-    const uint32_t la = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * NA * R1p);
-    for (int c = 0; c < NA * R1p; c += 16) tc_st16_zero(la + c);
-    tc_wait_st();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
+  // (no zeroing of the accumulators: the first MMA into a target overwrites)
 
   if (warp < NPW) {
     // ---- producers: mode-3 slabs
@@ -436,9 +416,7 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
               }
             }
           }
-          tc_st16_zero(la + col0 + ch);
         }
-        tc_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty + 8 * acc);
@@ -465,7 +443,9 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
     if (lane == 0) {
       // ---- MMA issuer
       const int maxrun = 256 / R1p;
-      auto issue = [&](int j2, int s, int sv, int ta, int tb) {
+      // `first`: these targets start with this slab, so the MMA of the first
+      // K step overwrites the accumulator (no zeroing pass in the epilogue)
+      auto issue = [&](int j2, int s, int sv, int ta, int tb, bool first) {
         int t = ta;
         while (t <= tb) {
           const int c0 = (j2 - P + t) % NA;
@@ -477,8 +457,9 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
 #pragma unroll
             for (int h = 0; h < H; ++h) {
               const uint64_t ad = umma_desc(su32(zbuf + (s * H + h) * ZH) + kb * 256, 128, SBO);
-              if (BF) tc_mma_bf16(tbase + (uint32_t)((h * NA + c0) * R1p), ad, bd, idesc, 1u);
-              else tc_mma_tf32(tbase + (uint32_t)((h * NA + c0) * R1p), ad, bd, idesc, 1u);
+              const uint32_t acc = (first && kb == 0) ? 0u : 1u;
+              if (BF) tc_mma_bf16(tbase + (uint32_t)((h * NA + c0) * R1p), ad, bd, idesc, acc);
+              else tc_mma_tf32(tbase + (uint32_t)((h * NA + c0) * R1p), ad, bd, idesc, acc);
             }
           }
           t += len;
@@ -493,20 +474,27 @@ __global__ void __launch_bounds__((8 * H + 2) * 32, 1) ttm_tc_kernel(const TtmTc
         }
         tc_fence_after();
         const int tlo = max(0, P - j2), thi = min(B - 1, n2 - 1 - j2 + P);
-        const bool fresh = (j2 + P < n2) && (j2 + P >= NA);  // target i2 = j2 + P reuses a slot
-        issue(j2, s, sv, tlo, fresh ? B - 2 : thi);
-        // accumulator i2 = j2 - P is complete with these MMAs: hand it to the
-        // epilogue before waiting for the slot of the fresh target, so that the
-        // epilogue of i2 runs under the MMAs of the next slab
-        if (j2 - P >= 0) tc_commit(acc_full + 8 * ((j2 - P) % NA));
-        if (fresh) {
-          const int i2n = j2 + P;
-          if (!mbar_wait(acc_empty + 8 * (i2n % NA), (uint32_t)(i2n / NA - 1) & 1, abort_)) {
-            fail();
-            break;
+        if (j2 == 0) {
+          // every target of the first slab starts here
+          issue(j2, s, sv, tlo, thi, true);
+        } else {
+          // target i2 = j2 + P starts with this slab (the others continue)
+          const bool newt = j2 + P < n2;
+          issue(j2, s, sv, tlo, newt ? B - 2 : thi, false);
+          // accumulator i2 = j2 - P is complete with these MMAs: hand it to
+          // the epilogue before waiting for the slot of the new target, so
+          // that the epilogue of i2 runs under the MMAs of the next slab
+          if (j2 - P >= 0) tc_commit(acc_full + 8 * ((j2 - P) % NA));
+          if (newt) {
+            const int i2n = j2 + P;
+            if (i2n >= NA &&
+                !mbar_wait(acc_empty + 8 * (i2n % NA), (uint32_t)(i2n / NA - 1) & 1, abort_)) {
+              fail();
+              break;
+            }
+            tc_fence_after();
+            issue(j2, s, sv, B - 1, B - 1, true);
           }
-          tc_fence_after();
-          issue(j2, s, sv, B - 1, B - 1);
         }
         tc_commit(z_free + 8 * s);
         tc_commit(v_free + 8 * sv);
