@@ -27,6 +27,10 @@ blocking or fusion beyond the definition):
                weightEquationSolve), mapped to the Gauss points
   solve     -- the KKT solve at sizes beyond the direct solve: low-rank
                operators and CG on the reduced system
+  parabolic -- the time-dependent KKT system (Sec. 4 eqs. timeDiscrete /
+               KKTSystem with N_t steps), direct solve, implicit Euler
+               sweeps of the state and the adjoint, objective and reduced
+               gradient
 
 Parity status per function is stated in each module header; every function
 listed above is pinned by a ``-m "not gpu"`` test against a closed form,

@@ -238,3 +238,48 @@ def test_interpolation_without_the_collocation_solve_fails_its_pin(monkeypatch):
     monkeypatch.setattr(ointerp, "node_to_gauss", wrong)
     with pytest.raises(AssertionError):
         pins_interp.test_polynomial_weights_are_reproduced_exactly("cubic")
+
+
+@pytest.mark.parametrize("mistake", ["forward_difference_sign", "untransposed_kk", "tau_dropped"])
+def test_wrong_space_time_system_fails_the_time_stepping(monkeypatch, mistake):
+    # eq. KKTSystem with KK = I (x) tau K + C (x) M: a +1 below C's diagonal,
+    # KK instead of KK^T in the first block row, or I (x) K without tau
+    import oracle.parabolic as opar
+    import test_oracle_parabolic as pins_par
+    if mistake == "forward_difference_sign":
+        monkeypatch.setattr(opar, "time_difference", lambda nt: sp.diags(
+            [np.ones(nt), np.ones(nt - 1)], [0, -1], shape=(nt, nt), format="csr"))
+    elif mistake == "untransposed_kk":
+        def wrong(M, K, tau, beta, nt):
+            MM, KK = opar.space_time_operators(M, K, tau, nt)
+            return sp.bmat([[tau * MM, None, KK], [None, tau * beta * MM, -tau * MM],
+                            [KK, -tau * MM, None]], format="csc")
+        monkeypatch.setattr(opar, "kkt_matrix_parabolic", wrong)
+    else:
+        def wrong(M, K, tau, nt):
+            I = sp.identity(nt, format="csr")
+            return (sp.kron(I, M, format="csr"),
+                    sp.kron(I, K, format="csr") + sp.kron(opar.time_difference(nt), M, format="csr"))
+        monkeypatch.setattr(opar, "space_time_operators", wrong)
+    with pytest.raises(AssertionError):
+        pins_par.test_time_stepping_reproduces_the_kkt_solution(4, 0.25, 1e-2)
+
+
+def test_adjoint_sweep_with_a_flipped_coupling_fails_finite_differences(monkeypatch):
+    # M lam_{k+1} entering the backward sweep with the wrong sign
+    import oracle.parabolic as opar
+    import scipy.sparse.linalg as spla
+    import test_oracle_parabolic as pins_par
+
+    def wrong(M, K, tau, b, y):
+        lu = spla.splu(sp.csc_matrix(M + tau * K.T))
+        lam = np.zeros_like(y)
+        nxt = np.zeros(y.shape[1])
+        for k in range(y.shape[0] - 1, -1, -1):
+            lam[k] = lu.solve(-(M @ nxt) + b[k] - tau * (M @ y[k]))
+            nxt = lam[k]
+        return lam
+    monkeypatch.setattr(opar, "adjoint_stepping", wrong)
+    monkeypatch.setattr(pins_par, "reduced_gradient_parabolic", opar.reduced_gradient_parabolic)
+    with pytest.raises(AssertionError):
+        pins_par.test_reduced_gradient_matches_finite_differences()
