@@ -500,6 +500,27 @@ iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const iga_op* K,
                                  const iga_tt* load, double beta, const iga_solve_opts* opts,
                                  iga_tt** y, iga_tt** u, iga_tt** lam, iga_solve_info* info);
 
+/* Solve the parabolic KKT system of Sec. 4 (eq. timeDiscrete discretised by
+ * nt implicit Euler steps of size tau, eq. KKTSystem):
+ *   [ tau MM   0            KK^T    ] [y  ]   [b]
+ *   [ 0        tau beta MM  -tau MM ] [u  ] = [0]
+ *   [ KK       -tau MM      0       ] [lam]   [0]
+ * with MM = I_nt (x) M, KK = I_nt (x) tau K + C (x) M and C the lower
+ * bidiagonal time difference (ones on the diagonal, minus ones below), by
+ * block AMEn on the space-time TT (the time index as a fourth TT core in
+ * front of the spatial ones; Sec. 5 eqs. M_kron, K_kron, KKT_red) inside
+ * FP64 iterative refinement of the full residual.  M, K: the spatial
+ * operators (same sizes and degrees).  load: device FP64 (nt, N), the y-row
+ * right-hand side b = [b_1; ...; b_nt] (b_k = tau M yhat_k for a desired
+ * state yhat), or NULL for zero.  y, u, lam: device FP64 (nt, N) each, time
+ * the slow index.  opts->residual must be IGA_RESID_FULL.  IGA_EINVAL for
+ * nt < 1, tau <= 0, beta <= 0 or mismatched operators; IGA_ENOCONV (best
+ * iterate written) when the tolerance is not reached. */
+iga_status iga_kkt_solve_parabolic(iga_ctx* ctx, const iga_op* M, const iga_op* K, int nt,
+                                   double tau, const double* load, double beta,
+                                   const iga_solve_opts* opts, double* y, double* u, double* lam,
+                                   iga_solve_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,34 @@ __global__ void band_group_kernel(const T* __restrict__ band, const int* __restr
   out[idx] = s;
 }
 
+// the same with every band transposed: A^T(i, j) = A(j, i) = band[j][i - j + p]
+template <typename T>
+__global__ void band_group_tr_kernel(const T* __restrict__ band, const int* __restrict__ gptr,
+                                     const int* __restrict__ src,
+                                     const long long* __restrict__ boff, const T* __restrict__ in,
+                                     int G, int r, int n, int r1, int p, T* __restrict__ out) {
+  const int B = 2 * p + 1;
+  size_t per = (size_t)r * n * r1;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)G * per) return;
+  int g = (int)(idx / per);
+  size_t rem = idx - (size_t)g * per;
+  int b = (int)(rem % r1);
+  size_t q = rem / r1;
+  int i = (int)(q % n);
+  int a = (int)(q / n);
+  T s = T(0);
+  for (int z = gptr[g]; z < gptr[g + 1]; ++z) {
+    const T* bz = band + boff[z];
+    const T* x = in + (size_t)src[z] * per + (size_t)a * n * r1 + b;
+    for (int o = 0; o < B; ++o) {
+      int j = i + o - p;
+      if (j >= 0 && j < n) s += bz[(size_t)j * B + (2 * p - o)] * x[(size_t)j * r1];
+    }
+  }
+  out[idx] = s;
+}
+
 // t[s][v](a,i,b) = sum_b' R[s](b,b') x[v](a,i,b')   (nv vectors, S right factors)
 template <typename T>
 __global__ void right_mult_kernel(const T* __restrict__ R, const T* __restrict__ x, int S, int nv,
@@ -118,6 +146,19 @@ __global__ void kkt_combine_kernel(const T* __restrict__ Mv, const T* __restrict
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L) return;
   out[i] = Mv[i] + Kv[2 * L + i];
+  out[L + i] = beta * Mv[L + i] - Mv[2 * L + i];
+  out[2 * L + i] = Kv[i] - Mv[L + i];
+}
+
+// the same when K is not symmetric (the space-time KK): the y-row takes
+// KK^T lam, given separately
+template <typename T>
+__global__ void kkt_combine_t_kernel(const T* __restrict__ Mv, const T* __restrict__ Kv,
+                                     const T* __restrict__ KTl, size_t L, T beta,
+                                     T* __restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  out[i] = Mv[i] + KTl[i];
   out[L + i] = beta * Mv[L + i] - Mv[2 * L + i];
   out[2 * L + i] = Kv[i] - Mv[L + i];
 }
@@ -1308,33 +1349,45 @@ struct CoreNZ {
   DevBuf<long long> doff, rowoff, coloff;
 };
 
+// A 4-D (space-time) operator puts one time band per block in front: the
+// time core has the blocks as its right rank index, the first spatial core
+// the blocks as its left one.
 static void build_core_nz(iga_ctx* ctx, const iga_op* op, int d, CoreNZ& c) {
   c.l.clear(); c.r.clear(); c.off.clear();
   size_t len = (size_t)op->n[d] * (2 * op->p[d] + 1);
-  int a0 = 0, b0 = 0;
+  const bool st = op->dims == 4;
+  const int sd = st ? d - 1 : d;                // spatial direction (-1: time)
+  int a0 = 0, b0 = 0, k = 0;
   for (const OpBlock& blk : op->blocks) {
-    if (d == 0) {
+    if (sd < 0) {
+      c.l.push_back(0); c.r.push_back(k);
+      c.off.push_back((long long)(blk.off[d] * len));
+    } else if (sd == 0) {
       for (int a = 0; a < blk.R1; ++a) {
-        c.l.push_back(0); c.r.push_back(a0 + a);
-        c.off.push_back((long long)((blk.off[0] + a) * len));
+        c.l.push_back(st ? k : 0); c.r.push_back(a0 + a);
+        c.off.push_back((long long)((blk.off[d] + a) * len));
       }
-    } else if (d == 1) {
+    } else if (sd == 1) {
       for (int a = 0; a < blk.R1; ++a)
         for (int b = 0; b < blk.R2; ++b) {
           c.l.push_back(a0 + a); c.r.push_back(b0 + b);
-          c.off.push_back((long long)((blk.off[1] + (size_t)a * blk.R2 + b) * len));
+          c.off.push_back((long long)((blk.off[d] + (size_t)a * blk.R2 + b) * len));
         }
     } else {
       for (int b = 0; b < blk.R2; ++b) {
         c.l.push_back(b0 + b); c.r.push_back(0);
-        c.off.push_back((long long)((blk.off[2] + b) * len));
+        c.off.push_back((long long)((blk.off[d] + b) * len));
       }
     }
     a0 += blk.R1;
     b0 += blk.R2;
+    ++k;
   }
-  c.R0 = d == 0 ? 1 : (d == 1 ? a0 : b0);
-  c.R1 = d == 0 ? a0 : (d == 1 ? b0 : 1);
+  const int nb = (int)op->blocks.size();
+  if (sd < 0) { c.R0 = 1; c.R1 = nb; }
+  else if (sd == 0) { c.R0 = st ? nb : 1; c.R1 = a0; }
+  else if (sd == 1) { c.R0 = a0; c.R1 = b0; }
+  else { c.R0 = b0; c.R1 = 1; }
   int nnz = (int)c.l.size();
   // CSR by left index (groups = alpha, sources = beta) and CSC (groups = beta, sources = alpha)
   std::vector<int> rp(c.R0 + 1, 0), cp(c.R1 + 1, 0), rs(nnz), cs(nnz);
@@ -1371,21 +1424,22 @@ template <typename T>
 struct Solver {
   using P = float;                     // precision of the block preconditioner
   iga_ctx* ctx;
-  const iga_op* op[2];                 // 0: M, 1: K
+  const iga_op* op[2];                 // 0: M, 1: K (parabolic: A_M and KK, 4-D)
   double beta;
-  int n[3];
+  int D = 3;                           // TT dimensions (4: the time index in front)
+  int n[4];
   size_t N;
-  int r[4];
+  int r[5];
   int kick, rmax;
   double inner_tol;
   double trunc_tol;
   bool svd_moves = false;        // Gram eigen-decomposition instead of pivoted Cholesky
   double w0 = 1.0;               // weight of the state y in the truncation
   bool tc_local = false;         // FP32 solve: large interface products on the tensor cores (TF32)
-  CoreNZ nz[2][3];
-  DevBuf<double> X[3];                 // TT cores (FP64 master)
+  CoreNZ nz[2][4];
+  DevBuf<double> X[4];                 // TT cores (FP64 master)
   DevBuf<double> Xh;                   // block core (3, r_d, n_d, r_{d+1})
-  DevBuf<double> PhiL[2][4], PhiR[2][4];   // PhiL[o][d]: (R_{d-1}, r_d, r_d) left of core d
+  DevBuf<double> PhiL[2][5], PhiR[2][5];   // PhiL[o][d]: (R_{d-1}, r_d, r_d) left of core d
   DevBuf<T> PLt[2], PRt[2];            // precision-T copies for the current core
   const T* PLp[2] = {nullptr, nullptr};   // interfaces of the local operator (the FP64
   const T* PRp[2] = {nullptr, nullptr};   // interfaces themselves, or the copies)
@@ -1460,6 +1514,130 @@ struct Solver {
     IGA_CUDA(cudaStreamSynchronize(ctx->stream));
   }
 
+  // frames of any dimension (the space-time TT) ---------------------------
+  size_t prod_n(int a, int b) const {
+    size_t q = 1;
+    for (int i = a; i < b; ++i) q *= (size_t)n[i];
+    return q;
+  }
+  // X_{<d} as (n_0 .. n_{d-1}) x r_d row-major; null for d = 0
+  const double* left_frame_g(int d) {
+    if (d == 0) return nullptr;
+    const double* cur = X[0].p;               // (n_0 x r_1)
+    size_t P = n[0];
+    int w = 0;
+    for (int j = 1; j < d; ++j) {
+      double* out = slot(130 + w, P * n[j] * r[j + 1]);
+      rm_gemm(ctx, false, false, (int)P, n[j] * r[j + 1], r[j], cur, r[j], X[j].p,
+              n[j] * r[j + 1], out, n[j] * r[j + 1]);
+      cur = out;
+      P *= n[j];
+      w ^= 1;
+    }
+    return cur;
+  }
+  // X_{>d} as r_{d+1} x (n_{d+1} .. n_{D-1}) row-major; null for d = D - 1
+  const double* right_frame_g(int d) {
+    if (d == D - 1) return nullptr;
+    const double* cur = X[D - 1].p;           // (r_{D-1} x n_{D-1})
+    size_t Q = n[D - 1];
+    int w = 0;
+    for (int j = D - 2; j > d; --j) {
+      double* out = slot(132 + w, (size_t)r[j] * n[j] * Q);
+      rm_gemm(ctx, false, false, r[j] * n[j], (int)Q, r[j + 1], X[j].p, r[j + 1], cur, (int)Q,
+              out, (int)Q);
+      cur = out;
+      Q *= n[j];
+      w ^= 1;
+    }
+    return cur;
+  }
+  // rhs_l = (X_{<d} (x) I (x) X_{>d})^T F_l for the three fields
+  void project_g(const double* F, int d, double* rhs) {
+    const size_t nle = prod_n(0, d), nd = n[d], ngt = prod_n(d + 1, D);
+    const size_t loc = (size_t)r[d] * nd * r[d + 1];
+    const double* Lf = left_frame_g(d);
+    const double* Rf = right_frame_g(d);
+    const double* sp = F;
+    long long ss = (long long)N;
+    if (Rf) {
+      double* s = slot(134, 3 * nle * nd * r[d + 1]);
+      ss = (long long)(nle * nd * r[d + 1]);
+      gemm_rm_batched<double>(ctx, false, true, (int)(nle * nd), r[d + 1], (int)ngt, 1.0, F,
+                              (int)ngt, (long long)N, Rf, (int)ngt, 0, 0.0, s, r[d + 1], ss, 3);
+      sp = s;
+    }
+    if (Lf)
+      gemm_rm_batched<double>(ctx, true, false, r[d], (int)(nd * r[d + 1]), (int)nle, 1.0, Lf,
+                              r[d], 0, sp, (int)(nd * r[d + 1]), ss, 0.0, rhs,
+                              (int)(nd * r[d + 1]), (long long)loc, 3);
+    else
+      for (int l = 0; l < 3; ++l)
+        IGA_CUDA(cudaMemcpyAsync(rhs + l * loc, sp + l * ss, loc * 8, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+  }
+  // out_l = (X_{<d} (x) I (x) X_{>d}) Xh_l
+  void expand_g(int d, double* out) {
+    const size_t nle = prod_n(0, d), nd = n[d], ngt = prod_n(d + 1, D);
+    const size_t loc = (size_t)r[d] * nd * r[d + 1];
+    const double* Lf = left_frame_g(d);
+    const double* Rf = right_frame_g(d);
+    const double* tp = Xh.p;
+    long long ts = (long long)loc;
+    if (Lf) {
+      double* t = Rf ? slot(134, 3 * nle * nd * r[d + 1]) : out;
+      ts = Rf ? (long long)(nle * nd * r[d + 1]) : (long long)N;
+      gemm_rm_batched<double>(ctx, false, false, (int)nle, (int)(nd * r[d + 1]), r[d], 1.0, Lf,
+                              r[d], 0, Xh.p, (int)(nd * r[d + 1]), (long long)loc, 0.0, t,
+                              (int)(nd * r[d + 1]), ts, 3);
+      tp = t;
+    }
+    if (Rf)
+      gemm_rm_batched<double>(ctx, false, false, (int)(nle * nd), (int)ngt, r[d + 1], 1.0, tp,
+                              r[d + 1], ts, Rf, (int)ngt, 0, 0.0, out, (int)ngt, (long long)N, 3);
+    else if (!Lf)
+      for (int l = 0; l < 3; ++l)
+        IGA_CUDA(cudaMemcpyAsync(out + l * N, Xh.p + l * loc, loc * 8, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+  }
+  // Gaussian sketch of the residual: forward E (r_d n_d x k) =
+  // (X_{<d} (x) I)^T sum_l res_l Om_l^T over n_{>d}; backward E^T (k x n_d r_{d+1})
+  // = sum_l Om_l^T res_l over n_{<d}, then X_{>d}^T; returns E^T (k x m)
+  void sketch_g(const double* res, int d, bool forward, double* Et) {
+    const size_t nle = prod_n(0, d), nd = n[d], ngt = prod_n(d + 1, D);
+    const int k = kick;
+    if (forward) {
+      double* Om = slot(4, (size_t)3 * k * ngt);
+      fill_gaussian(ctx, Om, (size_t)3 * k * ngt, seed++);
+      double* Ts = slot(5, nle * nd * k);
+      for (int l = 0; l < 3; ++l)
+        gemm_rm_batched<double>(ctx, false, true, (int)(nle * nd), k, (int)ngt, 1.0, res + l * N,
+                                (int)ngt, 0, Om + (size_t)l * k * ngt, (int)ngt, 0,
+                                l ? 1.0 : 0.0, Ts, k, 0, 1);
+      const double* E = Ts;
+      const int m = r[d] * (int)nd;
+      if (const double* Lf = left_frame_g(d)) {
+        double* E2 = slot(135, (size_t)m * k);
+        rm_gemm(ctx, true, false, r[d], (int)nd * k, (int)nle, Lf, r[d], Ts, (int)nd * k, E2,
+                (int)nd * k);
+        E = E2;
+      }
+      transpose_cm(ctx, E, k, m, Et);
+      return;
+    }
+    double* Om = slot(4, (size_t)3 * nle * k);
+    fill_gaussian(ctx, Om, (size_t)3 * nle * k, seed++);
+    const double* Rf = right_frame_g(d);
+    double* Ts = Rf ? slot(5, (size_t)k * nd * ngt) : Et;
+    for (int l = 0; l < 3; ++l)
+      gemm_rm_batched<double>(ctx, true, false, k, (int)(nd * ngt), (int)nle, 1.0,
+                              Om + (size_t)l * nle * k, k, 0, res + l * N, (int)(nd * ngt), 0,
+                              l ? 1.0 : 0.0, Ts, (int)(nd * ngt), 0, 1);
+    if (Rf)
+      rm_gemm(ctx, false, true, k * (int)nd, r[d + 1], (int)ngt, Ts, (int)ngt, Rf, (int)ngt, Et,
+              r[d + 1]);
+  }
+
   // full tensors ----------------------------------------------------------
   // frame pieces: Xr = X_{>0} (r1 x n2 n3), Xl = X_{<2} (n1 n2 x r2)
   void right_frame(double* Xr) {
@@ -1473,6 +1651,10 @@ struct Solver {
 
   // local rhs F_{!=d}^T f_l for the three components of a full (3, N) tensor
   void project(const double* F, int d, double* rhs) {
+    if (D != 3) {
+      project_g(F, d, rhs);
+      return;
+    }
     int n1 = n[0], n2 = n[1], n3 = n[2];
     size_t loc = (size_t)r[d] * n[d] * r[d + 1];
     if (d == 0) {
@@ -1501,6 +1683,10 @@ struct Solver {
 
   // full (3, N) tensor of the TT with block core Xh at position d
   void expand(int d, double* out) {
+    if (D != 3) {
+      expand_g(d, out);
+      return;
+    }
     int n1 = n[0], n2 = n[1], n3 = n[2];
     size_t loc = (size_t)r[d] * n[d] * r[d + 1];
     if (d == 0) {
@@ -1527,6 +1713,10 @@ struct Solver {
   void sketch(const double* res, int d, bool forward, double* Et, int m) {
     if (kr_mode) {
       kr_sketch(d, forward, Et, m);
+      return;
+    }
+    if (D != 3) {
+      sketch_g(res, d, forward, Et);
       return;
     }
     int n1 = n[0], n2 = n[1], n3 = n[2];
@@ -1931,6 +2121,7 @@ struct Solver {
     BandTc& bt = btc[o];
     if (bt.ready) return bt.use;
     bt.ready = true;
+    if (D != 3) return false;        // the space-time solve keeps the element kernels
     const iga_op* A = op[o];
     const int nb = (int)A->blocks.size();
     int big = 0;
@@ -2066,6 +2257,21 @@ struct Solver {
                  z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, 3 * c.r0, c.nn, c.r1,
                  op[o]->p[c.d], t2);
       left_mult<U>(PL[o], t2, z.R0, 3, c.r0, c.nn, c.r1, 0, out);
+    }
+    if (D == 4) {
+      // KK is not symmetric: the y-row takes the local KK^T, every factor of
+      // Phi_L (x) A_d (x) Phi_R transposed, on lambda
+      const CoreNZ& z = nz[1][c.d];
+      U* t1 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 2, c.L * z.R1);
+      U* t2 = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 3, c.L * z.R0);
+      U* KT = scratch<U>(ctx, SLOT_AMEN_BASE + sb + 120, c.L);
+      right_mult<U>(PR[1], x + 2 * c.L, z.R1, 1, c.r0, c.nn, c.r1, 1, t1);
+      IGA_LAUNCH(ctx, band_group_tr_kernel<U>, nblk(c.L * z.R0), 256, 0, bands_of<U>(op[1], c.d),
+                 z.rowptr.p, z.rowsrc.p, z.rowoff.p, t1, z.R0, c.r0, c.nn, c.r1, op[1]->p[c.d],
+                 t2);
+      left_mult<U>(PL[1], t2, z.R0, 1, c.r0, c.nn, c.r1, 1, KT);
+      IGA_LAUNCH(ctx, kkt_combine_t_kernel<U>, nblk(c.L), 256, 0, Mv, Kv, KT, c.L, (U)beta, y);
+      return;
     }
     IGA_LAUNCH(ctx, kkt_combine_kernel<U>, nblk(c.L), 256, 0, Mv, Kv, c.L, (U)beta, y);
   }
@@ -2493,18 +2699,39 @@ static double kkt_residual(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   return device_norm2(ctx, res, 3 * N);
 }
 
-// A solver on (M, K, beta) with a random initial TT of rank kick_rank,
-// right-orthogonal, the block index at core 0 (zero block core), and the
-// right interfaces of both operators
+// The KKT system a solve works on: the stationary system of (M, K, beta)
+// or the parabolic one of nt implicit Euler steps of size tau, whose solver
+// operators are the space-time A_M = tau I (x) M and KK = I (x) tau K + C (x) M.
+struct KktSystem {
+  const iga_op* M = nullptr;          // spatial operators
+  const iga_op* K = nullptr;
+  double beta = 1.0;
+  int nt = 0;                         // 0: stationary
+  double tau = 1.0;
+  const iga_op* AM = nullptr;         // the solver's operators (M and K when stationary)
+  const iga_op* AK = nullptr;
+  size_t N = 0;                       // unknowns per field
+  // res = F - KKT z (FP64, full), returns ||res||_2 (synchronises)
+  double residual(iga_ctx* ctx, const double* F, const double* z, double* res) const {
+    if (nt == 0) return kkt_residual(ctx, M, K, beta, F, z, res, N);
+    return parabolic_residual(ctx, M, K, beta, nt, tau, F, z, res, N / nt);
+  }
+};
+
+// A solver on the system's operators with a random initial TT of rank
+// kick_rank, right-orthogonal, the block index at core 0 (zero block core),
+// and the right interfaces of both operators
 template <typename T>
-static void solver_init(Solver<T>& S, iga_ctx* ctx, const iga_op* M, const iga_op* K,
-                        double beta, double tol, const iga_solve_opts* o) {
+static void solver_init(Solver<T>& S, iga_ctx* ctx, const KktSystem& sys, double tol,
+                        const iga_solve_opts* o) {
   S.ctx = ctx;
-  S.op[0] = M;
-  S.op[1] = K;
-  S.beta = beta;
-  for (int d = 0; d < 3; ++d) S.n[d] = M->n[d];
-  S.N = (size_t)S.n[0] * S.n[1] * S.n[2];
+  S.op[0] = sys.AM;
+  S.op[1] = sys.AK;
+  S.beta = sys.beta;
+  S.D = sys.AM->dims;
+  const int D = S.D;
+  for (int d = 0; d < D; ++d) S.n[d] = sys.AM->n[d];
+  S.N = S.prod_n(0, D);
   S.kick = std::max(1, o->kick_rank);
   S.rmax = std::max(2, o->rmax);
   S.inner_tol = tol;
@@ -2516,48 +2743,46 @@ static void solver_init(Solver<T>& S, iga_ctx* ctx, const iga_op* M, const iga_o
   S.tc_local = o->precision == IGA_TF32;
   S.verbose = o->verbose;
   for (int op = 0; op < 2; ++op)
-    for (int d = 0; d < 3; ++d) build_core_nz(ctx, S.op[op], d, S.nz[op][d]);
-  // initial TT: rank kick Gaussian cores, right-orthogonalised by QR; block index at core 0
-  int r0 = std::min({S.kick, S.n[0], S.n[1] * S.n[2]});
-  int r1 = std::min({S.kick, S.n[2], S.n[0] * S.n[1]});
-  S.r[0] = 1; S.r[1] = r0; S.r[2] = r1; S.r[3] = 1;
-  {
-    // X[2] = Q^T of a Gaussian (n3 x r2) block; X[1] = Q^T of a Gaussian (n2 r2 x r1) block
-    double* Y = S.slot(10, (size_t)S.n[2] * r1);
-    double* Q = S.slot(11, (size_t)S.n[2] * r1);
-    fill_gaussian(ctx, Y, (size_t)S.n[2] * r1, 77);
-    householder_qr(ctx, Y, Q, S.n[2], r1);
-    S.X[2].alloc((size_t)r1 * S.n[2]);
-    IGA_CUDA(cudaMemcpyAsync(S.X[2].p, Q, (size_t)r1 * S.n[2] * 8, cudaMemcpyDeviceToDevice,
-                             ctx->stream));
-    int m = S.n[1] * r1;
-    double* Y2 = S.slot(10, (size_t)m * r0);
-    double* Q2 = S.slot(11, (size_t)m * r0);
-    fill_gaussian(ctx, Y2, (size_t)m * r0, 78);
-    householder_qr(ctx, Y2, Q2, m, r0);
-    S.X[1].alloc((size_t)r0 * m);
-    IGA_CUDA(cudaMemcpyAsync(S.X[1].p, Q2, (size_t)r0 * m * 8, cudaMemcpyDeviceToDevice,
-                             ctx->stream));
-    S.X[0].alloc((size_t)S.n[0] * r0);
-    S.Xh.alloc((size_t)3 * S.n[0] * r0);
-    IGA_CUDA(cudaMemsetAsync(S.Xh.p, 0, (size_t)3 * S.n[0] * r0 * 8, ctx->stream));
+    for (int d = 0; d < D; ++d) build_core_nz(ctx, S.op[op], d, S.nz[op][d]);
+  // initial TT: rank-kick Gaussian cores, right-orthogonalised by QR from
+  // the last core on; block index at core 0.  Rank r_d is at most kick and
+  // both sizes of the unfolding at d.
+  S.r[0] = 1;
+  S.r[D] = 1;
+  for (int d = 1; d < D; ++d) {
+    const size_t lo = S.prod_n(0, d), hi = S.prod_n(d, D);
+    S.r[d] = (int)std::min<size_t>({(size_t)S.kick, lo, hi});
   }
+  for (int d = D - 1; d >= 1; --d) S.r[d] = std::min(S.r[d], S.n[d] * S.r[d + 1]);
+  for (int d = D - 1; d >= 1; --d) {
+    // X[d] = Q^T of a Gaussian (n_d r_{d+1} x r_d) block
+    const int m = S.n[d] * S.r[d + 1], k = S.r[d];
+    double* Y = S.slot(10, (size_t)m * k);
+    double* Q = S.slot(11, (size_t)m * k);
+    fill_gaussian(ctx, Y, (size_t)m * k, 77 + (D - 1 - d));
+    householder_qr(ctx, Y, Q, m, k);
+    S.X[d].alloc((size_t)k * m);
+    IGA_CUDA(cudaMemcpyAsync(S.X[d].p, Q, (size_t)k * m * 8, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+  }
+  S.X[0].alloc((size_t)S.n[0] * S.r[1]);
+  S.Xh.alloc((size_t)3 * S.n[0] * S.r[1]);
+  IGA_CUDA(cudaMemsetAsync(S.Xh.p, 0, (size_t)3 * S.n[0] * S.r[1] * 8, ctx->stream));
   for (int op = 0; op < 2; ++op) {
     S.set_ones(S.PhiL[op][0]);
-    S.set_ones(S.PhiR[op][2]);
-    S.right_update(op, 2);
-    S.right_update(op, 1);
+    S.set_ones(S.PhiR[op][D - 1]);
+    for (int d = D - 1; d >= 1; --d) S.right_update(op, d);
   }
 }
 
 template <typename T>
-static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta,
-                           const double* F, double Fnorm, double tol, const iga_solve_opts* o,
-                           double* delta, int* sweeps_out, int* maxrank, int* liters, double* resid,
-                           PhaseClock* clk) {
+static int amen_correction(iga_ctx* ctx, const KktSystem& sys, const double* F, double Fnorm,
+                           double tol, const iga_solve_opts* o, double* delta, int* sweeps_out,
+                           int* maxrank, int* liters, double* resid, PhaseClock* clk) {
   Solver<T> S;
-  solver_init(S, ctx, M, K, beta, tol, o);
+  solver_init(S, ctx, sys, tol, o);
   const size_t N = S.N;
+  const int D = S.D;
   double* res = S.slot(15, 3 * N);
   double rel = 1.0;
   int sweep = 0;
@@ -2573,10 +2798,8 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   double rel_prev = std::numeric_limits<double>::infinity();
   for (sweep = 0; sweep < maxsw; ++sweep) {
     bool fwd = (sweep % 2) == 0;
-    int order[3] = {0, 1, 2};
-    if (!fwd) { order[0] = 2; order[2] = 0; }
-    for (int s = 0; s < 3; ++s) {
-      int d = order[s];
+    for (int s = 0; s < D; ++s) {
+      int d = fwd ? s : D - 1 - s;
       if (sweep > 0 && s == 0) {
         // the first core of this sweep was solved last in the previous sweep
         clk->mark(PH_MOVE);
@@ -2588,13 +2811,13 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
       S.local_solve(d, F, tol_abs, maxit);
       clk->mark(PH_RESID);
       S.expand(d, delta);
-      double rn = kkt_residual(ctx, M, K, beta, F, delta, res, N);
+      double rn = sys.residual(ctx, F, delta, res);
       rel = rn / Fnorm;
       if (S.verbose)
-        fprintf(stderr, "[amen] sweep %d core %d ranks (%d,%d) local_it %d resid %.3e\n", sweep,
-                d, S.r[1], S.r[2], S.local_iters, rel);
+        fprintf(stderr, "[amen] sweep %d core %d ranks (%d,%d,%d) local_it %d resid %.3e\n",
+                sweep, d, S.r[1], S.r[2], D > 3 ? S.r[3] : 1, S.local_iters, rel);
       if (rel <= tol) { ++sweep; goto done; }
-      if (s < 2) {
+      if (s < D - 1) {
         clk->mark(PH_MOVE);
         if (fwd) S.move_forward(d, res);
         else S.move_backward(d, res);
@@ -2608,7 +2831,7 @@ static int amen_correction(iga_ctx* ctx, const iga_op* M, const iga_op* K, doubl
   }
 done:
   *sweeps_out += sweep;
-  *maxrank = std::max(*maxrank, std::max(S.r[1], S.r[2]));
+  for (int d = 1; d < D; ++d) *maxrank = std::max(*maxrank, S.r[d]);
   *liters += S.local_iters;
   *resid = rel;
   return rel <= tol;
@@ -2627,7 +2850,12 @@ static bool amen_local(iga_ctx* ctx, const iga_op* M, const iga_op* K, double be
                        iga_tt* out[3], iga_solve_info* inf, PhaseClock* clk) {
   Solver<T> S;
   const double tol = o->tol;
-  solver_init(S, ctx, M, K, beta, tol, o);
+  KktSystem sys;
+  sys.M = sys.AM = M;
+  sys.K = sys.AK = K;
+  sys.beta = beta;
+  sys.N = (size_t)M->n[0] * M->n[1] * M->n[2];
+  solver_init(S, ctx, sys, tol, o);
   S.kr_mode = true;
   S.Fsk = F;
   const int maxsw = std::max(1, o->max_sweeps);
@@ -2720,6 +2948,42 @@ extern "C" void iga_solve_opts_default(iga_solve_opts* o) {
   o->state_weight = 1.0;
 }
 
+// FP64 iterative refinement (full residual): z <- z + delta with delta from a
+// block-AMEn correction solve of KKT delta = r, until ||F - KKT z|| <= tol ||F||
+// or refine_max corrections; z holds the start (zero), r and delta are
+// scratch of the same size.  Returns whether the tolerance was met; *rel
+// receives the final relative residual.
+static bool refine_solve(iga_ctx* ctx, const KktSystem& sys, const double* F, double Fn,
+                         const iga_solve_opts& o, double* z, double* r, double* delta,
+                         iga_solve_info* inf, PhaseClock* clk, double* rel) {
+  const size_t L = 3 * sys.N;
+  double rn = Fn;
+  IGA_CUDA(cudaMemcpyAsync(r, F, L * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  const double inner = std::max(o.inner_tol, o.tol);
+  for (int it = 0; it <= o.refine_max; ++it) {
+    if (rn / Fn <= o.tol || it == o.refine_max) break;
+    // correction: KKT delta = r to relative accuracy `inner` (capped so the
+    // last step does not overshoot the target much)
+    const double itol = std::max(inner, 0.5 * o.tol * Fn / rn);
+    double cres = 1.0;
+    if (o.precision == IGA_FP64)
+      amen_correction<double>(ctx, sys, r, rn, itol, &o, delta, &inf->sweeps, &inf->max_rank,
+                              &inf->local_iters, &cres, clk);
+    else
+      amen_correction<float>(ctx, sys, r, rn, itol, &o, delta, &inf->sweeps, &inf->max_rank,
+                             &inf->local_iters, &cres, clk);
+    clk->mark(PH_REFINE);
+    IGA_LAUNCH(ctx, axpy_kernel, nblk(L), 256, 0, z, delta, 1.0, L);
+    rn = sys.residual(ctx, F, z, r);
+    inf->refinements = it + 1;
+    if (o.verbose)
+      fprintf(stderr, "[amen] refinement %d: correction resid %.3e, total resid %.3e\n", it, cres,
+              rn / Fn);
+  }
+  *rel = rn / Fn;
+  return *rel <= o.tol;
+}
+
 // The solve behind both entry points: the fields into y, u, lam (full
 // vectors, device) or, with tt_out (IGA_RESID_LOCAL only), as TT handles.
 static iga_status kkt_solve_impl(iga_ctx* ctx, const iga_op* M, const iga_op* K,
@@ -2786,33 +3050,12 @@ static iga_status kkt_solve_impl(iga_ctx* ctx, const iga_op* M, const iga_op* K,
         ok = amen_local<float>(ctx, M, K, beta, F, Fn, &o, z, tt_out, &inf, &clk);
       rel = inf.residual;
     } else if (!ok) {
-      double rn = Fn;
-      IGA_CUDA(cudaMemcpyAsync(r, F, 3 * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-      double inner = std::max(o.inner_tol, o.tol);
-      for (int it = 0; it <= o.refine_max; ++it) {
-        rel = rn / Fn;
-        if (rel <= o.tol) { ok = true; break; }
-        if (it == o.refine_max) break;
-        // correction: KKT delta = r to relative accuracy `inner` (capped so the
-        // last step does not overshoot the target much)
-        double itol = std::max(inner, 0.5 * o.tol * Fn / rn);
-        double cres = 1.0;
-        if (o.precision == IGA_FP64)
-          amen_correction<double>(ctx, M, K, beta, r, rn, itol, &o, delta, &inf.sweeps,
-                                  &inf.max_rank, &inf.local_iters, &cres, &clk);
-        else
-          amen_correction<float>(ctx, M, K, beta, r, rn, itol, &o, delta, &inf.sweeps,
-                                 &inf.max_rank, &inf.local_iters, &cres, &clk);
-        clk.mark(PH_REFINE);
-        IGA_LAUNCH(ctx, axpy_kernel, nblk(3 * N), 256, 0, z, delta, 1.0, 3 * N);
-        rn = kkt_residual(ctx, M, K, beta, F, z, r, N);
-        inf.refinements = it + 1;
-        if (o.verbose)
-          fprintf(stderr, "[amen] refinement %d: correction resid %.3e, total resid %.3e\n", it,
-                  cres, rn / Fn);
-      }
-      rel = rn / Fn;
-      ok = rel <= o.tol;
+      KktSystem sys;
+      sys.M = sys.AM = M;
+      sys.K = sys.AK = K;
+      sys.beta = beta;
+      sys.N = N;
+      ok = refine_solve(ctx, sys, F, Fn, o, z, r, delta, &inf, &clk, &rel);
     }
     if (z) {
       IGA_CUDA(cudaMemcpyAsync(y, z, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -2897,6 +3140,91 @@ extern "C" iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const
     *u = out[1];
     *lam = out[2];
     return st;
+  } catch (const Error& e) {
+    set_error(ctx, e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    set_error(ctx, e.what());
+    return IGA_ECUDA;
+  }
+}
+
+// The parabolic KKT system (Sec. 4, eq. KKTSystem with N_t = nt implicit
+// Euler steps of size tau): block AMEn on the space-time TT (the time index
+// as a fourth TT core in front of the three spatial ones, Sec. 5 eqs.
+// M_kron and K_kron) inside FP64 iterative refinement of the full residual.
+extern "C" iga_status iga_kkt_solve_parabolic(iga_ctx* ctx, const iga_op* M, const iga_op* K,
+                                              int nt, double tau, const double* load,
+                                              double beta, const iga_solve_opts* opts, double* y,
+                                              double* u, double* lam, iga_solve_info* info) {
+  if (!ctx) return IGA_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    AllocScope scope(ctx->stream);
+    IGA_REQUIRE(M && K && y && u && lam, "kkt_solve_parabolic: null argument");
+    IGA_REQUIRE(nt >= 1, "kkt_solve_parabolic: nt must be at least 1");
+    IGA_REQUIRE(tau > 0.0 && std::isfinite(tau), "kkt_solve_parabolic: tau must be positive");
+    IGA_REQUIRE(beta > 0.0, "kkt_solve_parabolic: beta must be positive");
+    IGA_REQUIRE(M->dims == 3 && K->dims == 3, "kkt_solve_parabolic: 3-D operators expected");
+    for (int d = 0; d < 3; ++d)
+      IGA_REQUIRE(M->n[d] == K->n[d] && M->p[d] == K->p[d], "kkt_solve_parabolic: M, K mismatch");
+    iga_solve_opts o;
+    if (opts) o = *opts; else iga_solve_opts_default(&o);
+    IGA_REQUIRE(o.tol > 0.0 && o.inner_tol >= 0.0, "kkt_solve_parabolic: bad tolerances");
+    IGA_REQUIRE(o.truncation == IGA_TRUNC_PIVOTED || o.truncation == IGA_TRUNC_SVD,
+                "kkt_solve_parabolic: unknown truncation");
+    IGA_REQUIRE(o.precision == IGA_FP64 || o.precision == IGA_FP32 || o.precision == IGA_TF32,
+                "kkt_solve_parabolic: precision must be IGA_FP64, IGA_FP32 or IGA_TF32");
+    IGA_REQUIRE(o.residual == IGA_RESID_FULL,
+                "kkt_solve_parabolic: only IGA_RESID_FULL is supported");
+    const size_t Ns = (size_t)M->n[0] * M->n[1] * M->n[2];
+    const size_t NT = (size_t)nt * Ns;
+    double* F = scratch<double>(ctx, SLOT_AMEN_BASE - 4, 3 * NT);
+    double* z = scratch<double>(ctx, SLOT_AMEN_BASE - 3, 3 * NT);
+    double* delta = scratch<double>(ctx, SLOT_AMEN_BASE - 2, 3 * NT);
+    double* r = scratch<double>(ctx, SLOT_AMEN_BASE - 1, 3 * NT);
+    IGA_CUDA(cudaMemsetAsync(F, 0, 3 * NT * 8, ctx->stream));
+    IGA_CUDA(cudaMemsetAsync(z, 0, 3 * NT * 8, ctx->stream));
+    if (load)
+      IGA_CUDA(cudaMemcpyAsync(F, load, NT * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    const double Fn = device_norm2(ctx, F, 3 * NT);
+    IGA_REQUIRE(std::isfinite(Fn), "kkt_solve_parabolic: load is not finite");
+    std::unique_ptr<iga_op> AM, AK;
+    space_time_ops(ctx, M, K, nt, tau, AM, AK);
+    KktSystem sys;
+    sys.M = M;
+    sys.K = K;
+    sys.beta = beta;
+    sys.nt = nt;
+    sys.tau = tau;
+    sys.AM = AM.get();
+    sys.AK = AK.get();
+    sys.N = NT;
+    iga_solve_info inf{};
+    PhaseClock clk;
+    clk.stream = ctx->stream;
+    double rel = 0.0;
+    bool ok = Fn == 0.0;
+    if (!ok) ok = refine_solve(ctx, sys, F, Fn, o, z, r, delta, &inf, &clk, &rel);
+    IGA_CUDA(cudaMemcpyAsync(y, z, NT * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(u, z + NT, NT * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    IGA_CUDA(cudaMemcpyAsync(lam, z + 2 * NT, NT * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    clk.mark(-1);
+    IGA_CUDA(cudaStreamSynchronize(ctx->stream));
+    double ph[PH_COUNT] = {0.0, 0.0, 0.0, 0.0};
+    clk.collect(ph);
+    inf.t_local = ph[PH_LOCAL];
+    inf.t_residual = ph[PH_RESID];
+    inf.t_move = ph[PH_MOVE];
+    inf.t_refine = ph[PH_REFINE];
+    inf.residual = rel;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    if (!ok) {
+      set_error(ctx, "kkt_solve_parabolic: tolerance not reached");
+      return IGA_ENOCONV;
+    }
+    return IGA_OK;
   } catch (const Error& e) {
     set_error(ctx, e.what());
     return e.status;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -122,10 +123,13 @@ struct SpaceTables {
 };
 
 // Device-resident Kronecker / TT-matrix operator (Dirichlet-reduced).
+// Operators of the library are 3-D; the parabolic solve builds 4-D
+// space-time operators internally (direction 0 = time), which never cross
+// the C ABI.
 struct OpBlock {
   int R1 = 1, R2 = 1;
-  size_t off[3] = {0, 0, 0};          // offsets (in bands) into the per-direction arrays
-  int deriv[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  size_t off[4] = {0, 0, 0, 0};       // offsets (in bands) into the per-direction arrays
+  int deriv[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 };
 
 }  // namespace iga
@@ -153,16 +157,17 @@ struct iga_ctx {
 };
 
 struct iga_op {
-  int n[3] = {0, 0, 0};               // interior sizes
-  int p[3] = {0, 0, 0};
+  int dims = 3;                       // 3; 4 for the internal space-time operators
+  int n[4] = {0, 0, 0, 0};            // interior sizes
+  int p[4] = {0, 0, 0, 0};
   std::vector<iga::OpBlock> blocks;
-  size_t nbands[3] = {0, 0, 0};
-  iga::DevBuf<double> band64[3];      // (nbands[d], n[d], 2p+1)
-  iga::DevBuf<float> band32[3];
+  size_t nbands[4] = {0, 0, 0, 0};
+  iga::DevBuf<double> band64[4];      // (nbands[d], n[d], 2p+1)
+  iga::DevBuf<float> band32[4];
   bool rank1 = true;
   size_t bytes() const {
     size_t s = 0;
-    for (int d = 0; d < 3; ++d) s += band64[d].n * 8 + band32[d].n * 4;
+    for (int d = 0; d < dims; ++d) s += band64[d].n * 8 + band32[d].n * 4;
     return s;
   }
 };
@@ -205,6 +210,7 @@ enum {
   SLOT_TTSVD_W, SLOT_TTSVD_C, SLOT_TTSVD_NORM, SLOT_QRCP_WORK, SLOT_ASM_W, SLOT_ASM_SAMPLES, SLOT_KRON_Z,
   SLOT_KRON_Z2, SLOT_LOCAL_T1, SLOT_LOCAL_T2, SLOT_KKT_TMP, SLOT_MISC0, SLOT_MISC1,
   SLOT_TTM_W, SLOT_QNORM, SLOT_TTSVD_Y2, SLOT_TTSVD_PART, SLOT_GEMM_PART, SLOT_GEMM_DOT,
+  SLOT_PARA_ZT, SLOT_PARA_S, SLOT_PARA_MV,
   SLOT_AMEN_BASE = 32
 };
 
@@ -295,6 +301,16 @@ void tc_flag_reset(iga_ctx* ctx);
 void tc_flag_check(iga_ctx* ctx, const char* what);
 
 void set_error(iga_ctx* ctx, const std::string& m);
+
+// parabolic.cu: the space-time operators of N_t implicit Euler steps,
+// A_M = tau I (x) M and KK = I (x) tau K + C (x) M, as internal 4-D operators
+// (direction 0 = time), and the FP64 residual res = F - A z of the parabolic
+// KKT system for z, F, res laid out (3, nt, N); returns ||res||_2
+// (synchronises)
+void space_time_ops(iga_ctx* ctx, const iga_op* M, const iga_op* K, int nt, double tau,
+                    std::unique_ptr<iga_op>& AM, std::unique_ptr<iga_op>& AK);
+double parabolic_residual(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta, int nt,
+                          double tau, const double* F, const double* z, double* res, size_t N);
 
 // gemm.cu: row-major strided batch C_i = alpha op(A_i) op(B_i) + beta C_i
 // (op(A) is M x K: A[m lda + k], or A[k lda + m] when tA), the local GMRES's

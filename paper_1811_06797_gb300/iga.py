@@ -123,6 +123,8 @@ def lib():
                                     P(SolveInfo_)]),
         "iga_kkt_solve_amen_tt": (st, [vp, vp, vp, vp, d, P(SolveOpts_), P(vp), P(vp), P(vp),
                                        P(SolveInfo_)]),
+        "iga_kkt_solve_parabolic": (st, [vp, vp, vp, i, d, vp, d, P(SolveOpts_), vp, vp, vp,
+                                         P(SolveInfo_)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -666,6 +668,31 @@ def iga_kkt_residual_rows(ctx, M, K, beta, load, y, u, lam, rows):
         y.handle, u.handle, lam.handle, r.shape[0],
         r.ctypes.data_as(C.POINTER(C.c_int)), out.ctypes.data_as(C.POINTER(C.c_double))))
     return out
+
+
+def iga_kkt_solve_parabolic(ctx, M, K, nt, tau, load, beta, y, u, lam, **opts):
+    """The parabolic KKT solve (nt implicit Euler steps of size tau): load,
+    y, u, lam are float64 CUDA tensors of nt x N elements (time the slow
+    index; load may be None).  Returns the solve info with `converged`."""
+    import torch
+    N = int(np.prod(M.info()["n"]))
+    ts = [t for t in (load, y, u, lam) if t is not None]
+    for t in ts:
+        if t.dtype != torch.float64 or t.numel() != int(nt) * N:
+            raise IgaError(1, "kkt_solve_parabolic: expected float64 tensors of nt * N elements")
+        if t.device != y.device:
+            raise IgaError(1, "kkt_solve_parabolic: tensors on different devices")
+    o = solve_opts(**opts)
+    info = SolveInfo_()
+    with torch.cuda.device(y.device):
+        st = lib().iga_kkt_solve_parabolic(ctx.handle, M.handle, K.handle, int(nt), float(tau),
+                                           _ptr(load), float(beta), C.byref(o), _ptr(y), _ptr(u),
+                                           _ptr(lam), C.byref(info))
+    res = {f: getattr(info, f) for f, _ in SolveInfo_._fields_}
+    if st not in (0, 4):
+        _check(ctx, st)
+    res["converged"] = st == 0
+    return res
 
 
 def iga_kkt_solve_amen_tt(ctx, M, K, load, beta, **opts):

@@ -1,0 +1,119 @@
+"""GPU parity of the parabolic KKT solve (Sec. 4 eqs. timeDiscrete and
+KKTSystem; block AMEn on the space-time TT, Sec. 5) against the oracle's
+direct solve of the assembled space-time system, element by element.
+
+Both sides take the same desired-state load: the spatial load vector of the
+target (each side its own assembly) times a time profile, b_k = tau g(t_k) b."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.assemble import Discretisation, assemble_band, band_to_csr
+from oracle.parabolic import kkt_residual_parabolic, kkt_solve_parabolic
+from paper_1811_06797_gb300 import workloads as wl
+from gpu_util import ctx_and_torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return ctx_and_torch()
+
+
+def _profile(nt, tau):
+    t = tau * np.arange(1, nt + 1)
+    return 0.5 + np.sin(math.pi * t)
+
+
+def _oracle(work, nt, tau):
+    disc = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+    Mb, Kb, b = assemble_band(work.geometry, disc, work.target)
+    M, K = band_to_csr(Mb, True), band_to_csr(Kb, True)
+    b = b[1:-1, 1:-1, 1:-1].ravel()
+    B = tau * _profile(nt, tau)[:, None] * b[None, :]
+    return M, K, B
+
+
+def _solve(env, work, nt, tau, zero_load=False, **opts):
+    ctx, torch, iga = env
+    M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    N = int(np.prod(M.info()["n"]))
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    load.full(ctx, b)
+    g = torch.tensor(tau * _profile(nt, tau), dtype=torch.float64, device="cuda")
+    B = (g[:, None] * b[None, :]).contiguous()
+    if zero_load:
+        B.zero_()
+    y, u, lam = (torch.empty((nt, N), dtype=torch.float64, device="cuda") for _ in range(3))
+    info = iga.iga_kkt_solve_parabolic(ctx, M, K, nt, tau, B, work.beta, y, u, lam, **opts)
+    return info, y.cpu().numpy(), u.cpu().numpy(), lam.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+CASES = [
+    ("cube_nt4", wl.small(wl.unit_cube(), 2, 5, beta=1e-2, tol=1e-12), 4, 0.25),
+    ("annulus_nt6", wl.small(wl.quarter_annulus(), 3, 5,
+                             wl.Target(wl.TARGET_GAUSS, wl.ANNULUS_CENTROID, 0.1), beta=1e-4,
+                             tol=1e-12), 6, 1.0 / 6),
+    ("twisted_nt10", wl.small(wl.quarter_annulus(twist=math.pi / 4), 2, 6,
+                              wl.Target(wl.TARGET_GAUSS, wl.ANNULUS_CENTROID, 0.1), beta=1e-3,
+                              tol=1e-12), 10, 0.1),
+    # TT-matrix operators with weight ranks > 1 (random cubic volume)
+    ("random_nt3", wl.small(wl.random_volume(), 2, 5, wl.Target(wl.TARGET_SINPROD), beta=1e-4,
+                            tol=1e-12), 3, 0.2),
+    # one step: the stationary layout with K + M / tau
+    ("annulus_nt1", wl.small(wl.quarter_annulus(), 2, 6,
+                             wl.Target(wl.TARGET_GAUSS, wl.ANNULUS_CENTROID, 0.1), beta=1e-3,
+                             tol=1e-12), 1, 0.5),
+]
+
+
+@pytest.mark.parametrize("name,work,nt,tau", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_parabolic_solve_matches_direct(env, name, work, nt, tau, prec):
+    info, y, u, lam = _solve(env, work, nt, tau, tol=1e-10, precision=prec)
+    assert info["converged"], info
+    M, K, B = _oracle(work, nt, tau)
+    # the GPU solution's residual in the oracle's assembled space-time system
+    assert kkt_residual_parabolic(M, K, tau, work.beta, B, y, u, lam) < 1e-9
+    yo, uo, lo = kkt_solve_parabolic(M, K, tau, work.beta, B)
+    for got, ref in ((y, yo), (u, uo), (lam, lo)):
+        assert _rel(got, ref) < 1e-6, (name, _rel(got, ref))
+
+
+def test_parabolic_solve_with_svd_moves(env):
+    name, work, nt, tau = CASES[1]
+    info, y, u, lam = _solve(env, work, nt, tau, tol=1e-10, truncation=1)
+    assert info["converged"], info
+    M, K, B = _oracle(work, nt, tau)
+    yo, uo, lo = kkt_solve_parabolic(M, K, tau, work.beta, B)
+    for got, ref in ((y, yo), (u, uo), (lam, lo)):
+        assert _rel(got, ref) < 1e-6
+
+
+def test_parabolic_zero_load_gives_zero(env):
+    name, work, nt, tau = CASES[0]
+    info, y, u, lam = _solve(env, work, nt, tau, zero_load=True)
+    assert info["converged"]
+    assert not y.any() and not u.any() and not lam.any()
+
+
+def test_parabolic_rejects_bad_arguments(env):
+    ctx, torch, iga = env
+    work = CASES[0][1]
+    M, K, load = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    N = int(np.prod(M.info()["n"]))
+    t = [torch.zeros((2, N), dtype=torch.float64, device="cuda") for _ in range(4)]
+    for nt, tau, beta, kw in ((0, 0.5, 1e-2, {}), (2, 0.0, 1e-2, {}), (2, 0.5, 0.0, {}),
+                              (2, 0.5, 1e-2, {"residual": 1})):
+        B = t[0] if nt == 2 else None
+        with pytest.raises(iga.IgaError):
+            iga.iga_kkt_solve_parabolic(ctx, M, K, nt, tau, B, beta, t[1], t[2], t[3], **kw)
+    with pytest.raises(iga.IgaError):
+        # wrong element count
+        iga.iga_kkt_solve_parabolic(ctx, M, K, 3, 0.5, t[0], 1e-2, t[1], t[2], t[3])
