@@ -77,10 +77,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--roofline-kernel", default="auto",
                     help="kernel name for the roofline entry, or auto (largest device time)")
-    ap.add_argument("--only", default=None, choices=["ttm", "c5solve", "step"],
+    ap.add_argument("--only", default=None, choices=["ttm", "c5solve", "step", "parabolic"],
                     help="ttm: only the tensor-core TT apply measurement (a profiling case); "
                          "c5solve: only the random-volume solve without full-size applies; "
-                         "step: only the timed steps of the workload")
+                         "step: only the timed steps of the workload; "
+                         "parabolic: only the parabolic solve on the workload's operators")
+    ap.add_argument("--nt", type=int, default=10, help="time steps of the parabolic solve")
     ap.add_argument("--c5-tol", type=float, default=1e-4)
     ap.add_argument("--c5-trunc", type=float, default=1e-6)
     ap.add_argument("--c5-sweeps", type=int, default=4)
@@ -774,7 +776,7 @@ def run_gpu(args, world, rank, local):
         "config5_assembly": config5_assembly(ctx, iga, torch),
         "config5_solve": config5_solve(ctx, iga, torch, args.c5_tol, args.c5_trunc,
                                        args.c5_sweeps, args.c5_state_weight),
-        "parabolic_solve": parabolic_solve(ctx, iga, torch, work, *state["ops"]),
+        "parabolic_solve": parabolic_solve(ctx, iga, torch, work, *state["ops"], nt=args.nt),
         "storage": {work.name: report.storage(ctx, work.geometry, work.space, work.target,
                                               work.tol)},
         "alu_rates_measured_tflops": {"fp64": iga.iga_measure_fma(ctx, iga.IGA_FP64),
@@ -851,6 +853,20 @@ def main():
                             args.c5_state_weight)
         if rank == 0:
             print(json.dumps({"config5_solve": out}))
+        return
+    if args.only == "parabolic":
+        import torch
+        from paper_1811_06797_gb300 import build, iga, workloads as wl
+        build.build()
+        torch.cuda.set_device(local)
+        ctx = iga.Context()
+        work = wl.config(args.config)
+        M, K, load = iga.iga_lowrank_assemble_interp(ctx, work.geometry, work.space, work.target,
+                                                     work.tol)
+        out = parabolic_solve(ctx, iga, torch, work, M, K, load, nt=args.nt, tol=args.tol,
+                              reps=max(1, args.steps))
+        if rank == 0:
+            print(json.dumps({"parabolic_solve": out}))
         return
     line, work, solutions = run_gpu(args, world, rank, local)
     if rank == 0:

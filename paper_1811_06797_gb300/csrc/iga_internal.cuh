@@ -283,6 +283,12 @@ bool kkt_apply_fused(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta
                      void* out, iga_prec prec);
 void kron_apply_impl(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
                      void* y, iga_prec prec);
+// the parabolic KKT rows of one time step in one FP64 launch when M and K
+// are rank-1 Kronecker sums: out_y -= M a + tau K lam_k, out_u -= M d,
+// out_lam -= tau K y_k + M f for in = {a, d, f, y_k, lam_k} (false: not
+// applicable, nothing launched)
+bool parabolic_rows_fused(iga_ctx* ctx, const iga_op* M, const iga_op* K, double tau,
+                          const double* const in[5], double* const out[3]);
 // the same with A^T (every band transposed)
 void kron_apply_transposed(iga_ctx* ctx, const iga_op* A, double alpha, const void* x, double beta,
                            void* y, iga_prec prec);

@@ -39,7 +39,7 @@ struct KronJob {
   unsigned char cmask[KRON_MAXTERMS];   // bit o set when coef[t][o] != 0
   unsigned char xin[KRON_MAXTERMS];
   int nterms;
-  const T* x[3];
+  const T* x[5];
   T* y[3];
   T beta[3];
 };
@@ -94,7 +94,9 @@ kron_rank1_kernel(const __grid_constant__ KronJob<T> job, KronTile g) {
     if (xi != staged) {
       // the (H1 x H2 x T3+2P) slab of this term's input, zero outside the
       // domain, read once per input (the terms are grouped by input)
-      const T* __restrict__ x = xi == 0 ? job.x[0] : (xi == 1 ? job.x[1] : job.x[2]);
+      const T* __restrict__ x =
+          xi == 0 ? job.x[0]
+                  : (xi == 1 ? job.x[1] : (xi == 2 ? job.x[2] : (xi == 3 ? job.x[3] : job.x[4])));
       for (int idx = threadIdx.x; idx < H1 * H2 * T3h; idx += blockDim.x) {
         const int kk = idx % T3h;
         const int ac = idx / T3h;
@@ -287,7 +289,7 @@ static void launch_kron_job(iga_ctx* ctx, const KronJob<T>& job, const KronTile&
     // accumulating); 3 banded mode products of 2(2P+1) flop per point and term
     double N = (double)g.n1 * g.n2 * g.n3;
     int nin = 0;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 5; ++i) {
       bool used = false;
       for (int t = 0; t < job.nterms; ++t) used |= job.xin[t] == i;
       nin += used;
@@ -369,6 +371,60 @@ static void kkt_rank1(iga_ctx* ctx, const iga_op* M, const iga_op* K, T beta, co
     job.beta[i] = T(0);
   }
   launch_kron_job<T, P, 3>(ctx, job, g);
+}
+
+// The parabolic KKT rows of one time step (Sec. 4, eq. KKTSystem) in one
+// launch, accumulated into out[] (which holds the right-hand side):
+//   out_y -= M a + tau K lam_k,  out_u -= M d,  out_lam -= tau K y_k + M f
+// with in = {a, d, f, y_k, lam_k} formed by the caller (the time differences
+// and scalings folded into a, d and f), so that every product is formed
+// once: three with M and two with K, as in the stationary KKT apply.
+template <typename T, int P>
+static void parabolic_rank1(iga_ctx* ctx, const iga_op* M, const iga_op* K, T tau,
+                            const T* const in[5], T* const out[3]) {
+  KronTile g = choose_tile(M->n[0], M->n[1], M->n[2], P, ctx->nsm, (int)sizeof(T));
+  KronJob<T> job{};
+  int cnt = 0;
+  auto add = [&](const iga_op* A, int xin, T c0, T c1, T c2) {
+    for (const OpBlock& blk : A->blocks) {
+      for (int d = 0; d < 3; ++d) job.b[d][cnt] = band_ptr<T>(A, d, blk.off[d]);
+      job.xin[cnt] = (unsigned char)xin;
+      job.coef[cnt][0] = c0;
+      job.coef[cnt][1] = c1;
+      job.coef[cnt][2] = c2;
+      ++cnt;
+    }
+  };
+  // terms grouped by input so that each input slab is staged once
+  add(M, 0, T(-1), T(0), T(0));      // M a      -> y-row
+  add(M, 1, T(0), T(-1), T(0));      // M d      -> u-row
+  add(M, 2, T(0), T(0), T(-1));      // M f      -> lambda-row
+  add(K, 3, T(0), T(0), -tau);       // K y_k    -> lambda-row
+  add(K, 4, -tau, T(0), T(0));       // K lam_k  -> y-row
+  job.nterms = cnt;
+  for (int i = 0; i < 5; ++i) job.x[i] = in[i];
+  for (int o = 0; o < 3; ++o) {
+    job.y[o] = out[o];
+    job.beta[o] = T(1);
+  }
+  launch_kron_job<T, P, 3>(ctx, job, g);
+}
+
+bool parabolic_rows_fused(iga_ctx* ctx, const iga_op* M, const iga_op* K, double tau,
+                          const double* const in[5], double* const out[3]) {
+  int P = M->p[0];
+  for (int d = 0; d < 3; ++d)
+    if (M->p[d] != P || K->p[d] != P || M->n[d] != K->n[d]) return false;
+  if (!M->rank1 || !K->rank1 || M->blocks.empty() || K->blocks.empty() ||
+      3 * M->blocks.size() + 2 * K->blocks.size() > (size_t)KRON_MAXTERMS)
+    return false;
+  switch (P) {
+    case 1: parabolic_rank1<double, 1>(ctx, M, K, tau, in, out); return true;
+    case 2: parabolic_rank1<double, 2>(ctx, M, K, tau, in, out); return true;
+    case 3: parabolic_rank1<double, 3>(ctx, M, K, tau, in, out); return true;
+    case 4: parabolic_rank1<double, 4>(ctx, M, K, tau, in, out); return true;
+    default: return false;
+  }
 }
 
 template <typename T, int P>

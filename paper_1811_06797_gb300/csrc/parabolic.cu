@@ -82,6 +82,27 @@ __global__ void parabolic_combine_kernel(const double* __restrict__ F,
   }
 }
 
+// inputs of the fused step rows, each (nt, N), from z (3, nt, N):
+//   a_k = tau y_k + lam_k - lam_{k+1},  d_k = tau (beta u_k - lam_k),
+//   f_k = y_k - y_{k-1} - tau u_k       (lam_{nt} = 0, y_{-1} = 0)
+__global__ void parabolic_inputs_kernel(const double* __restrict__ z, int nt, size_t N,
+                                        double tau, double beta, double* __restrict__ a,
+                                        double* __restrict__ dd, double* __restrict__ f) {
+  const size_t NT = (size_t)nt * N;
+  const double* y = z;
+  const double* u = z + NT;
+  const double* l = z + 2 * NT;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NT;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / N);
+    const double lnext = k + 1 < nt ? l[idx + N] : 0.0;
+    const double yprev = k > 0 ? y[idx - N] : 0.0;
+    a[idx] = tau * y[idx] + l[idx] - lnext;
+    dd[idx] = tau * (beta * u[idx] - l[idx]);
+    f[idx] = y[idx] - yprev - tau * u[idx];
+  }
+}
+
 unsigned grid_for(size_t n, int nsm) {
   return (unsigned)std::min<size_t>((n + 255) / 256, (size_t)8 * nsm);
 }
@@ -159,6 +180,24 @@ void space_time_ops(iga_ctx* ctx, const iga_op* M, const iga_op* K, int nt, doub
 double parabolic_residual(iga_ctx* ctx, const iga_op* M, const iga_op* K, double beta, int nt,
                           double tau, const double* F, const double* z, double* res, size_t N) {
   const size_t tot = (size_t)3 * nt * N;
+  const size_t NT = (size_t)nt * N;
+  if (M->rank1 && K->rank1) {
+    // rank-one operators: res = F, then the three rows of every step in one
+    // fused launch (five products per step, as in the stationary KKT apply)
+    double* in3 = scratch<double>(ctx, SLOT_PARA_S, tot);
+    IGA_CUDA(cudaMemcpyAsync(res, F, tot * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    IGA_LAUNCH(ctx, parabolic_inputs_kernel, grid_for(NT, ctx->nsm), 256, 0, z, nt, N, tau, beta,
+               in3, in3 + NT, in3 + 2 * NT);
+    bool fused = true;
+    for (int k = 0; k < nt && fused; ++k) {
+      const size_t o = (size_t)k * N;
+      const double* in[5] = {in3 + o, in3 + NT + o, in3 + 2 * NT + o, z + o, z + 2 * NT + o};
+      double* out[3] = {res + o, res + NT + o, res + 2 * NT + o};
+      fused = parabolic_rows_fused(ctx, M, K, tau, in, out);
+      IGA_REQUIRE(fused || k == 0, "parabolic residual: fused rows not applicable");
+    }
+    if (fused) return device_norm2(ctx, res, tot);
+  }
   double* zt = scratch<double>(ctx, SLOT_PARA_ZT, tot);
   double* S = scratch<double>(ctx, SLOT_PARA_S, tot);
   double* MyMl = scratch<double>(ctx, SLOT_PARA_MV, (size_t)2 * nt * N);

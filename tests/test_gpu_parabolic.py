@@ -117,3 +117,51 @@ def test_parabolic_rejects_bad_arguments(env):
     with pytest.raises(iga.IgaError):
         # wrong element count
         iga.iga_kkt_solve_parabolic(ctx, M, K, 3, 0.5, t[0], 1e-2, t[1], t[2], t[3])
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_parabolic_bench_workload_rows(env, prec):
+    """The bench's parabolic case at full size: the quarter annulus of degree 3
+    with 64 elements per direction (interpolated weights), 10 steps of size
+    0.1, b_k = tau (1/2 + sin(pi t_k)) b.  Sampled rows of the three
+    equations, every step, evaluated with the oracle's own row integrals of
+    M and K and load entries applied to the GPU solution; a row's residual
+    never exceeds the residual's 2-norm."""
+    from oracle.assemble import sampled_load, sampled_rows
+    from test_gpu_config2 import _apply_row
+    ctx, torch, iga = env
+    work = wl.config(2)
+    nt, tau = 10, 0.1
+    M, K, load = iga.iga_lowrank_assemble_interp(ctx, work.geometry, work.space, work.target,
+                                                 work.tol)
+    ni = M.info()["n"]
+    N = int(np.prod(ni))
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    load.full(ctx, b)
+    g = tau * _profile(nt, tau)
+    B = (torch.tensor(g, dtype=torch.float64, device="cuda")[:, None] * b[None, :]).contiguous()
+    y, u, lam = (torch.empty((nt, N), dtype=torch.float64, device="cuda") for _ in range(3))
+    info = iga.iga_kkt_solve_parabolic(ctx, M, K, nt, tau, B, work.beta, y, u, lam, tol=1e-6,
+                                       precision=prec)
+    assert info["converged"] and info["residual"] <= 1e-6, info
+    Fn = float(B.norm())
+    disc = Discretisation(work.space.degree, work.space.knots, work.space.nquad)
+    n = disc.n
+    rng = np.random.default_rng(1010)
+    rows = np.stack([rng.integers(1, n[d] - 1, 6) for d in range(3)], axis=1)
+    rows[0] = (1, 1, 1)
+    Mr, Kr = sampled_rows(work.geometry, disc, rows)
+    br = sampled_load(work.geometry, disc, work.target, rows)
+    Y, U, L = (t.cpu().numpy().reshape((nt,) + tuple(ni)) for t in (y, u, lam))
+    bound = (1e-6 + 10 * work.tol) * Fn
+    for s, r in enumerate(rows):
+        my = [_apply_row(Mr[s], Y[k], r, n) for k in range(nt)]
+        ml = [_apply_row(Mr[s], L[k], r, n) for k in range(nt)]
+        for k in range(nt):
+            ky, kl = _apply_row(Kr[s], Y[k], r, n), _apply_row(Kr[s], L[k], r, n)
+            mu = _apply_row(Mr[s], U[k], r, n)
+            ry = tau * (my[k] + kl) + ml[k] - (ml[k + 1] if k + 1 < nt else 0.0) - g[k] * br[s]
+            ru = tau * (work.beta * mu - ml[k])
+            rl = tau * (ky - mu) + my[k] - (my[k - 1] if k > 0 else 0.0)
+            for e, v in enumerate((ry, ru, rl)):
+                assert abs(v) <= bound, (s, r, k, e, v, bound)
