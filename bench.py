@@ -77,7 +77,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--roofline-kernel", default="auto",
                     help="kernel name for the roofline entry, or auto (largest device time)")
-    ap.add_argument("--only", default=None, choices=["ttm", "c5solve", "step", "parabolic"],
+    ap.add_argument("--only", default=None,
+                    choices=["ttm", "c5solve", "step", "parabolic", "kron32"],
                     help="ttm: only the tensor-core TT apply measurement (a profiling case); "
                          "c5solve: only the random-volume solve without full-size applies; "
                          "step: only the timed steps of the workload; "
@@ -156,7 +157,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -492,6 +493,66 @@ def config5_solve(ctx, iga, torch, tol, trunc_tol, max_sweeps, state_weight=1.0,
     return out
 
 
+def kron_fp32_roofline(ctx, iga, torch, pk, pk_kind, reps=8):
+    """The fused rank-1 Kronecker apply in FP32 storage (the bulk apply of
+    the mixed path) at the twisted-annulus size of 256 elements per direction
+    (degree 3, 257^3 = 1.7e7 points): the mass operator alone (one term, 8 B
+    and 42 flop per point: HBM-bound) and the whole KKT operator (three
+    inputs, three outputs, every term), each against the roofline that binds
+    it.  L2 is flushed (256 MB write) before every launch; the launches are
+    timed with CUDA events on the context stream."""
+    import numpy as np
+    from paper_1811_06797_gb300 import workloads as wl
+    work = wl.config(3)
+    M, K, _ = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, work.tol)
+    N = int(np.prod(M.info()["n"]))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(3)
+    out = {"workload": work.name, "points": N, "l2": "flushed before every launch"}
+    fp32_peak = alu_peak_tflops("fp32", pk)
+
+    def measure(fn):
+        fn()
+        torch.cuda.synchronize()
+        # the marching kernel takes the large FP32 applies; the tiled one the rest
+        for kernel in ("kron_march_kernel", "kron_rank1_kernel"):
+            ctx.profile_begin(kernel)
+            for _ in range(reps):
+                flush.zero_()
+                fn()
+            p = ctx.profile_end()
+            torch.cuda.synchronize()
+            if p["launches"] > 0:
+                break
+        avg = p["ms"] / p["launches"]
+        by, fl = p["bytes"] / p["launches"], p["flops"] / p["launches"]
+        t_hbm = by / (pk["hbm_gbs"] * 1e9)
+        t_alu = fl / (fp32_peak * 1e12)
+        if t_hbm >= t_alu:
+            ach = by / (avg * 1e-3) / 1e9
+            r = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": ach / pk["hbm_gbs"], "peak_kind": pk_kind}
+        else:
+            ach = fl / (avg * 1e-3) / 1e12
+            r = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "frac": ach / fp32_peak,
+                 "peak_kind": "FP32 FMA rate from unit counts and the maximum SM clock"}
+        r.update({"kernel": kernel, "avg_us": avg * 1e3, "launches": p["launches"],
+                  "algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": fl})
+        return r
+
+    x = torch.randn(N, generator=g, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    out["mass_apply"] = measure(lambda: iga.iga_kron_apply(ctx, M, 1.0, x, 0.0, y))
+    del x, y
+    z = torch.randn(3 * N, generator=g, device="cuda", dtype=torch.float32)
+    zo = torch.empty_like(z)
+    out["kkt_apply"] = measure(lambda: iga.iga_kkt_apply(ctx, M, K, work.beta, z, zo))
+    del z, zo, flush, M, K
+    torch.cuda.empty_cache()
+    return out
+
+
 def parabolic_solve(ctx, iga, torch, work, M, K, load, nt=10, tol=1e-6, reps=2):
     """The parabolic KKT solve (Sec. 4 eq. KKTSystem, nt implicit Euler steps
     on [0, 1], tau = 1/nt; nt = 10 as in the paper's optimal-control runs) on
@@ -771,6 +832,7 @@ def run_gpu(args, world, rank, local):
         "roofline": roof,
         "kron_roofline": kron_roof,
         "ttm_roofline": ttm_roofline(ctx, iga, torch, pk, pk_kind),
+        "kron_fp32_roofline": kron_fp32_roofline(ctx, iga, torch, pk, pk_kind),
         "assembly_routes_ms": assembly_routes(assemble, work, torch),
         "rank_tables": rank_tables(ctx),
         "config5_assembly": config5_assembly(ctx, iga, torch),
@@ -853,6 +915,16 @@ def main():
                             args.c5_state_weight)
         if rank == 0:
             print(json.dumps({"config5_solve": out}))
+        return
+    if args.only == "kron32":
+        import torch
+        from paper_1811_06797_gb300 import build, iga
+        build.build()
+        torch.cuda.set_device(local)
+        pk, pk_kind = peaks()
+        out = kron_fp32_roofline(iga.Context(), iga, torch, pk, pk_kind)
+        if rank == 0:
+            print(json.dumps({"kron_fp32_roofline": out}))
         return
     if args.only == "parabolic":
         import torch

@@ -276,6 +276,257 @@ static KronTile choose_tile(int n1, int n2, int n3, int P, int nsm, int es) {
   return best;
 }
 
+// ---- marching apply for large grids (HBM-bound FP32 applies)
+//
+// One CTA owns a KM_T2 x KM_T3 column of (i2, i3) points and a chunk
+// [I1a, I1b) of i1.  It streams the input planes j1 = I1a - P .. I1b + P - 1
+// through shared memory (cp.async, KM_STAGES planes of one input in
+// flight), applies modes 3 and 2 of every term to the plane (a 2-D halo of P
+// rows and columns only), and scatters mode 1 into a register ring of 2P+1
+// output planes: plane j1 adds A1(i1, j1) w(j1) to every i1 in
+// [j1 - P, j1 + P], so plane j1 - P is complete after plane j1 and is
+// written once.  Every x element comes from DRAM about once (the halos of
+// neighbouring columns from L2), y is written once, and the index
+// arithmetic uses compile-time tile sizes.
+constexpr int KM_T2 = 16, KM_T3 = 32, KM_THREADS = 256, KM_STAGES = 4;
+
+struct KronRuns {
+  int nrun;
+  int xin[5];
+  int t0[6];          // terms of run k: [t0[k], t0[k + 1])
+};
+
+template <typename T>
+__device__ __forceinline__ void km_cp_async(T* smem, const T* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+
+// stage unit u = (plane jbeg + u / nrun, run u % nrun) of the marching
+// apply into buffer u % KM_STAGES (zero outside the grid), then commit
+template <typename T, int P>
+__device__ __forceinline__ void km_issue(T* xs, const KronJob<T>& job, const KronRuns& runs,
+                                         int u, int nunits, int nrun, int jbeg, int n1, int n2,
+                                         int n3, int I2, int I3, int tid) {
+  constexpr int H2 = KM_T2 + 2 * P, W3 = KM_T3 + 2 * P;
+  if (u < nunits) {
+    const int j1 = jbeg + u / nrun;
+    if (j1 >= 0 && j1 < n1) {
+      const int k = u - (u / nrun) * nrun;
+      const int xi = runs.xin[k];
+      const T* __restrict__ x =
+          xi == 0 ? job.x[0]
+                  : (xi == 1 ? job.x[1] : (xi == 2 ? job.x[2] : (xi == 3 ? job.x[3] : job.x[4])));
+      T* dst = xs + (u % KM_STAGES) * (H2 * W3);
+      const T* plane = x + (size_t)j1 * n2 * n3;
+      for (int e = tid; e < H2 * W3; e += KM_THREADS) {
+        const int r = e / W3, cc = e - r * W3;
+        const int i2 = I2 - P + r, i3 = I3 - P + cc;
+        const bool ok = i2 >= 0 && i2 < n2 && i3 >= 0 && i3 < n3;
+        km_cp_async(dst + e, ok ? plane + (size_t)i2 * n3 + i3 : x, ok);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+
+template <typename T, int P, int NY>
+__global__ void __launch_bounds__(KM_THREADS)
+kron_march_kernel(const __grid_constant__ KronJob<T> job, const __grid_constant__ KronRuns runs,
+                  int n1, int n2, int n3, int L1, int nb3, int nb2) {
+  constexpr int B = 2 * P + 1;
+  constexpr int W = 2 * P + 1;                 // ring of output planes
+  constexpr int H2 = KM_T2 + 2 * P, W3 = KM_T3 + 2 * P;
+  extern __shared__ unsigned char smraw[];
+  T* xs = reinterpret_cast<T*>(smraw);                      // KM_STAGES x H2 x W3
+  T* v = xs + KM_STAGES * H2 * W3;                          // H2 x KM_T3
+  T* a3s = v + H2 * KM_T3;                                  // nterms x KM_T3 x B
+  T* a2s = a3s + job.nterms * KM_T3 * B;                    // nterms x KM_T2 x B
+  const int tid = threadIdx.x, c = tid & 31, ty = tid >> 5;
+  int bid = blockIdx.x;
+  const int b3 = bid % nb3;
+  bid /= nb3;
+  const int b2 = bid % nb2;
+  const int ch = bid / nb2;
+  const int I3 = b3 * KM_T3, I2 = b2 * KM_T2;
+  const int I1a = ch * L1, I1b = min(n1, I1a + L1);
+  // the bands of modes 3 and 2 for this column, zero outside the matrix
+  for (int e = tid; e < job.nterms * KM_T3 * B; e += KM_THREADS) {
+    const int t = e / (KM_T3 * B), r = e - t * (KM_T3 * B), cc = r / B, o = r - cc * B;
+    const int i = I3 + cc, j = i + o - P;
+    a3s[e] = (i < n3 && j >= 0 && j < n3) ? job.b[2][t][(size_t)i * B + o] : T(0);
+  }
+  for (int e = tid; e < job.nterms * KM_T2 * B; e += KM_THREADS) {
+    const int t = e / (KM_T2 * B), r = e - t * (KM_T2 * B), rr = r / B, o = r - rr * B;
+    const int i = I2 + rr, j = i + o - P;
+    a2s[e] = (i < n2 && j >= 0 && j < n2) ? job.b[1][t][(size_t)i * B + o] : T(0);
+  }
+  const int jbeg = I1a - P, jend = I1b + P;
+  const int nrun = runs.nrun;
+  const int nunits = (jend - jbeg) * nrun;
+  T acc[W][2][NY];
+#pragma unroll
+  for (int s = 0; s < W; ++s)
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int o = 0; o < NY; ++o) acc[s][p][o] = T(0);
+#pragma unroll
+  for (int u = 0; u < KM_STAGES - 1; ++u)
+    km_issue<T, P>(xs, job, runs, u, nunits, nrun, jbeg, n1, n2, n3, I2, I3, tid);
+  int u = 0;
+  const int rp0 = ty, rp1 = ty + 8;
+  for (int jb = jbeg; jb < jend; jb += W) {
+#pragma unroll
+    for (int s = 0; s < W; ++s) {
+      const int j1 = jb + s;
+      if (j1 < jend) {
+        for (int k = 0; k < nrun; ++k, ++u) {
+          km_issue<T, P>(xs, job, runs, u + KM_STAGES - 1, nunits, nrun, jbeg, n1, n2, n3, I2,
+                         I3, tid);
+          asm volatile("cp.async.wait_group %0;\n" ::"n"(KM_STAGES - 1));
+          __syncthreads();
+          if (j1 >= 0 && j1 < n1) {
+            const T* xb = xs + (u % KM_STAGES) * (H2 * W3);
+            for (int t = runs.t0[k]; t < runs.t0[k + 1]; ++t) {
+              // mode 3 on the H2 halo rows of the column
+              const T* a3 = a3s + (t * KM_T3 + c) * B;
+              T c3[B];
+#pragma unroll
+              for (int o = 0; o < B; ++o) c3[o] = a3[o];
+#pragma unroll
+              for (int rr = 0; rr < (H2 + 7) / 8; ++rr) {
+                const int r = ty + 8 * rr;
+                if (r < H2) {
+                  const T* xr = xb + r * W3 + c;
+                  T sv = T(0);
+#pragma unroll
+                  for (int o = 0; o < B; ++o) sv = fma(c3[o], xr[o], sv);
+                  v[r * KM_T3 + c] = sv;
+                }
+              }
+              __syncthreads();
+              // mode 2 for the thread's two rows
+              T w0 = T(0), w1 = T(0);
+              {
+                const T* a20 = a2s + (t * KM_T2 + rp0) * B;
+                const T* a21 = a2s + (t * KM_T2 + rp1) * B;
+#pragma unroll
+                for (int o = 0; o < B; ++o) {
+                  w0 = fma(a20[o], v[(rp0 + o) * KM_T3 + c], w0);
+                  w1 = fma(a21[o], v[(rp1 + o) * KM_T3 + c], w1);
+                }
+              }
+              // mode 1 scattered into the ring: i1 = j1 + q, A1(i1, j1) at
+              // band[i1][P - q]
+              const T* A1 = job.b[0][t];
+              T cf[NY];
+#pragma unroll
+              for (int o = 0; o < NY; ++o) cf[o] = job.coef[t][o];
+              const unsigned cm = job.cmask[t];
+#pragma unroll
+              for (int q = -P; q <= P; ++q) {
+                const int i1 = j1 + q;
+                if (i1 >= I1a && i1 < I1b) {
+                  const T a1 = __ldg(A1 + (size_t)i1 * B + (P - q));
+                  const int sl = ((s + q) % W + W) % W;     // compile-time slot
+                  const T p0 = a1 * w0, p1 = a1 * w1;
+#pragma unroll
+                  for (int o = 0; o < NY; ++o)
+                    if (cm & (1u << o)) {
+#pragma unroll
+                      for (int z = 0; z < W; ++z)
+                        if (z == sl) {
+                          acc[z][0][o] = fma(cf[o], p0, acc[z][0][o]);
+                          acc[z][1][o] = fma(cf[o], p1, acc[z][1][o]);
+                        }
+                    }
+                }
+              }
+              __syncthreads();
+            }
+          }
+        }
+        // plane j1 - P is complete: write it and clear its slot
+        const int i1 = j1 - P;
+        if (i1 >= I1a && i1 < I1b) {
+          const int sl = ((s - P) % W + W) % W;
+          const int i3 = I3 + c;
+#pragma unroll
+          for (int z = 0; z < W; ++z)
+            if (z == sl) {
+#pragma unroll
+              for (int p = 0; p < 2; ++p) {
+                const int i2 = I2 + (p ? rp1 : rp0);
+                if (i2 < n2 && i3 < n3) {
+                  const size_t off = ((size_t)i1 * n2 + i2) * n3 + i3;
+#pragma unroll
+                  for (int o = 0; o < NY; ++o) {
+                    T val = acc[z][p][o];
+                    if (job.beta[o] != T(0)) val += job.beta[o] * job.y[o][off];
+                    job.y[o][off] = val;
+                  }
+                }
+#pragma unroll
+                for (int o = 0; o < NY; ++o) acc[z][p][o] = T(0);
+              }
+            }
+        }
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// The marching kernel takes the FP32 applies of large grids, which are
+// bound by HBM (one term) or by the FP32 units (the KKT operator); the FP64
+// applies keep the tiled kernel, whose halo work is hidden behind the
+// FP64 pipe.
+static bool use_march(const KronTile& g, int es) {
+  return es == 4 && (double)g.n1 * g.n2 * g.n3 >= 4194304.0 && g.n2 >= KM_T2 && g.n3 >= KM_T3;
+}
+
+template <typename T, int P, int NY>
+static void launch_march(iga_ctx* ctx, const KronJob<T>& jm, int n1, int n2, int n3) {
+  constexpr int B = 2 * P + 1;
+  constexpr int H2 = KM_T2 + 2 * P, W3 = KM_T3 + 2 * P;
+  KronRuns runs{};
+  runs.nrun = 0;
+  for (int t = 0; t < jm.nterms; ++t)
+    if (t == 0 || jm.xin[t] != jm.xin[t - 1]) {
+      IGA_REQUIRE(runs.nrun < 5, "kron_apply: too many input runs");
+      runs.xin[runs.nrun] = jm.xin[t];
+      runs.t0[runs.nrun] = t;
+      ++runs.nrun;
+    }
+  runs.t0[runs.nrun] = jm.nterms;
+  const size_t smem = ((size_t)KM_STAGES * H2 * W3 + (size_t)H2 * KM_T3 +
+                       (size_t)jm.nterms * (KM_T3 + KM_T2) * B) * sizeof(T);
+  IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: marching tile does not fit in shared memory");
+  func_attr(kron_march_kernel<T, P, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)smem);
+  int occ = 1;
+  IGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kron_march_kernel<T, P, NY>,
+                                                         KM_THREADS, smem));
+  occ = std::max(1, occ);
+  const int nb3 = (n3 + KM_T3 - 1) / KM_T3, nb2 = (n2 + KM_T2 - 1) / KM_T2;
+  // chunks of i1 so that the columns fill the resident CTAs once; a chunk
+  // of at least 4 (2P+1) planes keeps the recomputed halo planes below a
+  // quarter
+  const int cols = nb3 * nb2;
+  int nch = std::max(1, (ctx->nsm * occ + cols - 1) / cols);
+  const int L1min = 4 * B;
+  nch = std::max(1, std::min(nch, (n1 + L1min - 1) / L1min));
+  const int L1 = (n1 + nch - 1) / nch;
+  nch = (n1 + L1 - 1) / L1;
+  IGA_LAUNCH(ctx, (kron_march_kernel<T, P, NY>), (unsigned)(cols * nch), KM_THREADS, smem, jm,
+             runs, n1, n2, n3, L1, nb3, nb2);
+}
+
 template <typename T, int P, int NY>
 static void launch_kron_job(iga_ctx* ctx, const KronJob<T>& job, const KronTile& g) {
   constexpr int B = 2 * P + 1;
@@ -303,6 +554,10 @@ static void launch_kron_job(iga_ctx* ctx, const KronJob<T>& job, const KronTile&
     jm.cmask[t] = 0;
     for (int o = 0; o < NY; ++o)
       if (jm.coef[t][o] != T(0)) jm.cmask[t] |= (unsigned char)(1u << o);
+  }
+  if (use_march(g, (int)sizeof(T))) {
+    launch_march<T, P, NY>(ctx, jm, g.n1, g.n2, g.n3);
+    return;
   }
   IGA_LAUNCH(ctx, (kron_rank1_kernel<T, P, NY>), (unsigned)(g.nt1 * g.nt2 * g.nt3), KRON_THREADS,
              smem, jm, g);

@@ -197,3 +197,41 @@ def test_operator_from_bands_and_its_transpose(env, prec, transpose):
                        tf32=prec == "tf32", bf16=prec == "bf16", transpose=transpose)
     err = np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref)
     assert err < {"fp64": 1e-13, "fp32": 1e-5, "tf32": 5e-3, "bf16": 2.5e-2}[prec], err
+
+
+@pytest.mark.parametrize("p,E", [(3, 165), (2, 170)])
+def test_marching_fp32_apply_on_large_grids(env, p, E):
+    """Grids of over 4M points take the marching FP32 kernel (planes
+    streamed along i1, modes 3 and 2 in shared memory, mode 1 scattered into
+    a register ring): a single operator with beta = 0 and with beta != 0,
+    and the whole KKT operator, against the FP64 tiled kernel on the same
+    operators, over ragged column tiles and i1 chunks."""
+    ctx, torch, iga = env
+    work = wl.small(wl.quarter_annulus(twist=np.pi / 4), p, E, beta=1e-3)
+    M, K, _ = iga.iga_lowrank_assemble(ctx, work.geometry, work.space, work.target, 1e-10)
+    N = int(np.prod(M.info()["n"]))
+    assert N >= 4194304
+    g = torch.Generator(device="cuda").manual_seed(E)
+    x = torch.randn(N, generator=g, device="cuda", dtype=torch.float64)
+    y0 = torch.randn(N, generator=g, device="cuda", dtype=torch.float64)
+    for op in (M, K):
+        for beta in (0.0, -0.5):
+            ref = y0.clone()
+            iga.iga_kron_apply(ctx, op, 1.5, x, beta, ref)
+            y32 = y0.float()
+            ctx.profile_begin("kron_march_kernel")
+            iga.iga_kron_apply(ctx, op, 1.5, x.float(), beta, y32)
+            prof = ctx.profile_end()
+            assert prof["launches"] >= 1, prof
+            err = float((y32.double() - ref).norm() / ref.norm())
+            assert err < 1e-5, (beta, err)
+    z = torch.randn(3 * N, generator=g, device="cuda", dtype=torch.float64)
+    ref = torch.empty_like(z)
+    iga.iga_kkt_apply(ctx, M, K, work.beta, z, ref)
+    out = torch.empty(3 * N, device="cuda", dtype=torch.float32)
+    ctx.profile_begin("kron_march_kernel")
+    iga.iga_kkt_apply(ctx, M, K, work.beta, z.float(), out)
+    prof = ctx.profile_end()
+    assert prof["launches"] == 1, prof
+    err = float((out.double() - ref).norm() / ref.norm())
+    assert err < 1e-5, err
