@@ -307,12 +307,16 @@ __device__ __forceinline__ void km_cp_async(T* smem, const T* gmem, bool valid) 
 }
 
 // stage unit u = (plane jbeg + u / nrun, run u % nrun) of the marching
-// apply into buffer u % KM_STAGES (zero outside the grid), then commit
+// apply into buffer u % KM_STAGES, then commit.  off[m] / okmask bit m: the
+// in-plane offset and validity of the thread's m-th staged element, the
+// same for every plane (zero fill outside the grid).
 template <typename T, int P>
 __device__ __forceinline__ void km_issue(T* xs, const KronJob<T>& job, const KronRuns& runs,
-                                         int u, int nunits, int nrun, int jbeg, int n1, int n2,
-                                         int n3, int I2, int I3, int tid) {
+                                         int u, int nunits, int nrun, int jbeg, int n1,
+                                         size_t plane_len, const int* off, unsigned okmask,
+                                         int tid) {
   constexpr int H2 = KM_T2 + 2 * P, W3 = KM_T3 + 2 * P;
+  constexpr int NE = (H2 * W3 + KM_THREADS - 1) / KM_THREADS;
   if (u < nunits) {
     const int j1 = jbeg + u / nrun;
     if (j1 >= 0 && j1 < n1) {
@@ -322,12 +326,14 @@ __device__ __forceinline__ void km_issue(T* xs, const KronJob<T>& job, const Kro
           xi == 0 ? job.x[0]
                   : (xi == 1 ? job.x[1] : (xi == 2 ? job.x[2] : (xi == 3 ? job.x[3] : job.x[4])));
       T* dst = xs + (u % KM_STAGES) * (H2 * W3);
-      const T* plane = x + (size_t)j1 * n2 * n3;
-      for (int e = tid; e < H2 * W3; e += KM_THREADS) {
-        const int r = e / W3, cc = e - r * W3;
-        const int i2 = I2 - P + r, i3 = I3 - P + cc;
-        const bool ok = i2 >= 0 && i2 < n2 && i3 >= 0 && i3 < n3;
-        km_cp_async(dst + e, ok ? plane + (size_t)i2 * n3 + i3 : x, ok);
+      const T* plane = x + (size_t)j1 * plane_len;
+#pragma unroll
+      for (int m = 0; m < NE; ++m) {
+        const int e = tid + m * KM_THREADS;
+        if (e < H2 * W3) {
+          const bool ok = (okmask >> m) & 1u;
+          km_cp_async(dst + e, ok ? plane + off[m] : x, ok);
+        }
       }
     }
   }
@@ -341,10 +347,11 @@ kron_march_kernel(const __grid_constant__ KronJob<T> job, const __grid_constant_
   constexpr int B = 2 * P + 1;
   constexpr int W = 2 * P + 1;                 // ring of output planes
   constexpr int H2 = KM_T2 + 2 * P, W3 = KM_T3 + 2 * P;
+  constexpr int NE = (H2 * W3 + KM_THREADS - 1) / KM_THREADS;
   extern __shared__ unsigned char smraw[];
   T* xs = reinterpret_cast<T*>(smraw);                      // KM_STAGES x H2 x W3
-  T* v = xs + KM_STAGES * H2 * W3;                          // H2 x KM_T3
-  T* a3s = v + H2 * KM_T3;                                  // nterms x KM_T3 x B
+  T* v = xs + KM_STAGES * H2 * W3;                          // 2 x H2 x KM_T3
+  T* a3s = v + 2 * H2 * KM_T3;                              // nterms x KM_T3 x B
   T* a2s = a3s + job.nterms * KM_T3 * B;                    // nterms x KM_T2 x B
   const int tid = threadIdx.x, c = tid & 31, ty = tid >> 5;
   int bid = blockIdx.x;
@@ -365,119 +372,125 @@ kron_march_kernel(const __grid_constant__ KronJob<T> job, const __grid_constant_
     const int i = I2 + rr, j = i + o - P;
     a2s[e] = (i < n2 && j >= 0 && j < n2) ? job.b[1][t][(size_t)i * B + o] : T(0);
   }
+  int off[NE];
+  unsigned okmask = 0u;
+#pragma unroll
+  for (int m = 0; m < NE; ++m) {
+    const int e = tid + m * KM_THREADS;
+    const int r = e / W3, cc = e - r * W3;
+    const int i2 = I2 - P + r, i3 = I3 - P + cc;
+    const bool ok = e < H2 * W3 && i2 >= 0 && i2 < n2 && i3 >= 0 && i3 < n3;
+    off[m] = ok ? i2 * n3 + i3 : 0;
+    okmask |= ok ? (1u << m) : 0u;
+  }
+  const size_t plane_len = (size_t)n2 * n3;
   const int jbeg = I1a - P, jend = I1b + P;
   const int nrun = runs.nrun;
   const int nunits = (jend - jbeg) * nrun;
+  // acc[z] collects output plane j1 - P + z while plane j1 is processed
   T acc[W][2][NY];
 #pragma unroll
-  for (int s = 0; s < W; ++s)
+  for (int z = 0; z < W; ++z)
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int o = 0; o < NY; ++o) acc[s][p][o] = T(0);
+      for (int o = 0; o < NY; ++o) acc[z][p][o] = T(0);
 #pragma unroll
   for (int u = 0; u < KM_STAGES - 1; ++u)
-    km_issue<T, P>(xs, job, runs, u, nunits, nrun, jbeg, n1, n2, n3, I2, I3, tid);
-  int u = 0;
+    km_issue<T, P>(xs, job, runs, u, nunits, nrun, jbeg, n1, plane_len, off, okmask, tid);
+  int u = 0, par = 0;
   const int rp0 = ty, rp1 = ty + 8;
-  for (int jb = jbeg; jb < jend; jb += W) {
+  for (int j1 = jbeg; j1 < jend; ++j1) {
+    for (int k = 0; k < nrun; ++k, ++u) {
+      km_issue<T, P>(xs, job, runs, u + KM_STAGES - 1, nunits, nrun, jbeg, n1, plane_len, off,
+                     okmask, tid);
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(KM_STAGES - 1));
+      __syncthreads();
+      if (j1 >= 0 && j1 < n1) {
+        const T* xb = xs + (u % KM_STAGES) * (H2 * W3);
+        for (int t = runs.t0[k]; t < runs.t0[k + 1]; ++t, par ^= 1) {
+          // mode 3 on the H2 halo rows of the column (v double-buffered by
+          // term, so one barrier per term suffices)
+          T* vb = v + par * (H2 * KM_T3);
+          const T* a3 = a3s + (t * KM_T3 + c) * B;
+          T c3[B];
 #pragma unroll
-    for (int s = 0; s < W; ++s) {
-      const int j1 = jb + s;
-      if (j1 < jend) {
-        for (int k = 0; k < nrun; ++k, ++u) {
-          km_issue<T, P>(xs, job, runs, u + KM_STAGES - 1, nunits, nrun, jbeg, n1, n2, n3, I2,
-                         I3, tid);
-          asm volatile("cp.async.wait_group %0;\n" ::"n"(KM_STAGES - 1));
+          for (int o = 0; o < B; ++o) c3[o] = a3[o];
+#pragma unroll
+          for (int rr = 0; rr < (H2 + 7) / 8; ++rr) {
+            const int r = ty + 8 * rr;
+            if (r < H2) {
+              const T* xr = xb + r * W3 + c;
+              T sv = T(0);
+#pragma unroll
+              for (int o = 0; o < B; ++o) sv = fma(c3[o], xr[o], sv);
+              vb[r * KM_T3 + c] = sv;
+            }
+          }
           __syncthreads();
-          if (j1 >= 0 && j1 < n1) {
-            const T* xb = xs + (u % KM_STAGES) * (H2 * W3);
-            for (int t = runs.t0[k]; t < runs.t0[k + 1]; ++t) {
-              // mode 3 on the H2 halo rows of the column
-              const T* a3 = a3s + (t * KM_T3 + c) * B;
-              T c3[B];
+          // mode 2 for the thread's two rows
+          T w0 = T(0), w1 = T(0);
+          {
+            const T* a20 = a2s + (t * KM_T2 + rp0) * B;
+            const T* a21 = a2s + (t * KM_T2 + rp1) * B;
 #pragma unroll
-              for (int o = 0; o < B; ++o) c3[o] = a3[o];
+            for (int o = 0; o < B; ++o) {
+              w0 = fma(a20[o], vb[(rp0 + o) * KM_T3 + c], w0);
+              w1 = fma(a21[o], vb[(rp1 + o) * KM_T3 + c], w1);
+            }
+          }
+          // mode 1 scattered into the ring: i1 = j1 + q (slot q + P),
+          // A1(i1, j1) at band[i1][P - q]
+          const T* A1 = job.b[0][t];
+          T cf[NY];
 #pragma unroll
-              for (int rr = 0; rr < (H2 + 7) / 8; ++rr) {
-                const int r = ty + 8 * rr;
-                if (r < H2) {
-                  const T* xr = xb + r * W3 + c;
-                  T sv = T(0);
+          for (int o = 0; o < NY; ++o) cf[o] = job.coef[t][o];
+          const unsigned cm = job.cmask[t];
 #pragma unroll
-                  for (int o = 0; o < B; ++o) sv = fma(c3[o], xr[o], sv);
-                  v[r * KM_T3 + c] = sv;
+          for (int q = -P; q <= P; ++q) {
+            const int i1 = j1 + q;
+            if ((unsigned)i1 < (unsigned)n1) {
+              const T a1 = __ldg(A1 + (size_t)i1 * B + (P - q));
+              const T p0 = a1 * w0, p1 = a1 * w1;
+#pragma unroll
+              for (int o = 0; o < NY; ++o)
+                if (cm & (1u << o)) {
+                  acc[q + P][0][o] = fma(cf[o], p0, acc[q + P][0][o]);
+                  acc[q + P][1][o] = fma(cf[o], p1, acc[q + P][1][o]);
                 }
-              }
-              __syncthreads();
-              // mode 2 for the thread's two rows
-              T w0 = T(0), w1 = T(0);
-              {
-                const T* a20 = a2s + (t * KM_T2 + rp0) * B;
-                const T* a21 = a2s + (t * KM_T2 + rp1) * B;
-#pragma unroll
-                for (int o = 0; o < B; ++o) {
-                  w0 = fma(a20[o], v[(rp0 + o) * KM_T3 + c], w0);
-                  w1 = fma(a21[o], v[(rp1 + o) * KM_T3 + c], w1);
-                }
-              }
-              // mode 1 scattered into the ring: i1 = j1 + q, A1(i1, j1) at
-              // band[i1][P - q]
-              const T* A1 = job.b[0][t];
-              T cf[NY];
-#pragma unroll
-              for (int o = 0; o < NY; ++o) cf[o] = job.coef[t][o];
-              const unsigned cm = job.cmask[t];
-#pragma unroll
-              for (int q = -P; q <= P; ++q) {
-                const int i1 = j1 + q;
-                if (i1 >= I1a && i1 < I1b) {
-                  const T a1 = __ldg(A1 + (size_t)i1 * B + (P - q));
-                  const int sl = ((s + q) % W + W) % W;     // compile-time slot
-                  const T p0 = a1 * w0, p1 = a1 * w1;
-#pragma unroll
-                  for (int o = 0; o < NY; ++o)
-                    if (cm & (1u << o)) {
-#pragma unroll
-                      for (int z = 0; z < W; ++z)
-                        if (z == sl) {
-                          acc[z][0][o] = fma(cf[o], p0, acc[z][0][o]);
-                          acc[z][1][o] = fma(cf[o], p1, acc[z][1][o]);
-                        }
-                    }
-                }
-              }
-              __syncthreads();
             }
           }
         }
-        // plane j1 - P is complete: write it and clear its slot
-        const int i1 = j1 - P;
-        if (i1 >= I1a && i1 < I1b) {
-          const int sl = ((s - P) % W + W) % W;
-          const int i3 = I3 + c;
+      }
+    }
+    // plane j1 - P is complete: write slot 0, then shift the ring
+    const int i1 = j1 - P;
+    if (i1 >= I1a && i1 < I1b) {
+      const int i3 = I3 + c;
 #pragma unroll
-          for (int z = 0; z < W; ++z)
-            if (z == sl) {
+      for (int p = 0; p < 2; ++p) {
+        const int i2 = I2 + (p ? rp1 : rp0);
+        if (i2 < n2 && i3 < n3) {
+          const size_t o2 = ((size_t)i1 * n2 + i2) * n3 + i3;
 #pragma unroll
-              for (int p = 0; p < 2; ++p) {
-                const int i2 = I2 + (p ? rp1 : rp0);
-                if (i2 < n2 && i3 < n3) {
-                  const size_t off = ((size_t)i1 * n2 + i2) * n3 + i3;
-#pragma unroll
-                  for (int o = 0; o < NY; ++o) {
-                    T val = acc[z][p][o];
-                    if (job.beta[o] != T(0)) val += job.beta[o] * job.y[o][off];
-                    job.y[o][off] = val;
-                  }
-                }
-#pragma unroll
-                for (int o = 0; o < NY; ++o) acc[z][p][o] = T(0);
-              }
-            }
+          for (int o = 0; o < NY; ++o) {
+            T val = acc[0][p][o];
+            if (job.beta[o] != T(0)) val += job.beta[o] * job.y[o][o2];
+            job.y[o][o2] = val;
+          }
         }
       }
     }
+#pragma unroll
+    for (int z = 0; z + 1 < W; ++z)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int o = 0; o < NY; ++o) acc[z][p][o] = acc[z + 1][p][o];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int o = 0; o < NY; ++o) acc[W - 1][p][o] = T(0);
   }
   asm volatile("cp.async.wait_group 0;\n" ::);
 }
@@ -504,7 +517,7 @@ static void launch_march(iga_ctx* ctx, const KronJob<T>& jm, int n1, int n2, int
       ++runs.nrun;
     }
   runs.t0[runs.nrun] = jm.nterms;
-  const size_t smem = ((size_t)KM_STAGES * H2 * W3 + (size_t)H2 * KM_T3 +
+  const size_t smem = ((size_t)KM_STAGES * H2 * W3 + (size_t)2 * H2 * KM_T3 +
                        (size_t)jm.nterms * (KM_T3 + KM_T2) * B) * sizeof(T);
   IGA_REQUIRE(smem <= 227 * 1024, "kron_apply: marching tile does not fit in shared memory");
   func_attr(kron_march_kernel<T, P, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
