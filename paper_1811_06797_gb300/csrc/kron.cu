@@ -306,34 +306,31 @@ __device__ __forceinline__ void km_cp_async(T* smem, const T* gmem, bool valid) 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
 }
 
-// stage unit u = (plane jbeg + u / nrun, run u % nrun) of the marching
-// apply into buffer u % KM_STAGES, then commit.  off[m] / okmask bit m: the
-// in-plane offset and validity of the thread's m-th staged element, the
-// same for every plane (zero fill outside the grid).
+// stage plane j1 of run k's input into buffer `stage` of the marching
+// apply (nothing for a plane outside the grid or past the last unit), then
+// commit.  off[m] / okmask bit m: the in-plane offset and validity of the
+// thread's m-th staged element, the same for every plane (zero fill outside
+// the grid).
 template <typename T, int P>
 __device__ __forceinline__ void km_issue(T* xs, const KronJob<T>& job, const KronRuns& runs,
-                                         int u, int nunits, int nrun, int jbeg, int n1,
+                                         bool live, int j1, int k, int stage, int n1,
                                          size_t plane_len, const int* off, unsigned okmask,
                                          int tid) {
   constexpr int H2 = KM_T2 + 2 * P, W3 = KM_T3 + 2 * P;
   constexpr int NE = (H2 * W3 + KM_THREADS - 1) / KM_THREADS;
-  if (u < nunits) {
-    const int j1 = jbeg + u / nrun;
-    if (j1 >= 0 && j1 < n1) {
-      const int k = u - (u / nrun) * nrun;
-      const int xi = runs.xin[k];
-      const T* __restrict__ x =
-          xi == 0 ? job.x[0]
-                  : (xi == 1 ? job.x[1] : (xi == 2 ? job.x[2] : (xi == 3 ? job.x[3] : job.x[4])));
-      T* dst = xs + (u % KM_STAGES) * (H2 * W3);
-      const T* plane = x + (size_t)j1 * plane_len;
+  if (live && j1 >= 0 && j1 < n1) {
+    const int xi = runs.xin[k];
+    const T* __restrict__ x =
+        xi == 0 ? job.x[0]
+                : (xi == 1 ? job.x[1] : (xi == 2 ? job.x[2] : (xi == 3 ? job.x[3] : job.x[4])));
+    T* dst = xs + stage * (H2 * W3);
+    const T* plane = x + (size_t)j1 * plane_len;
 #pragma unroll
-      for (int m = 0; m < NE; ++m) {
-        const int e = tid + m * KM_THREADS;
-        if (e < H2 * W3) {
-          const bool ok = (okmask >> m) & 1u;
-          km_cp_async(dst + e, ok ? plane + off[m] : x, ok);
-        }
+    for (int m = 0; m < NE; ++m) {
+      const int e = tid + m * KM_THREADS;
+      if (e < H2 * W3) {
+        const bool ok = (okmask >> m) & 1u;
+        km_cp_async(dst + e, ok ? plane + off[m] : x, ok);
       }
     }
   }
@@ -395,15 +392,28 @@ kron_march_kernel(const __grid_constant__ KronJob<T> job, const __grid_constant_
     for (int p = 0; p < 2; ++p)
 #pragma unroll
       for (int o = 0; o < NY; ++o) acc[z][p][o] = T(0);
+  // the next unit to stage: plane ij of run ik, unit number iu
+  int ij = jbeg, ik = 0, iu = 0;
+  auto stage_next = [&]() {
+    km_issue<T, P>(xs, job, runs, iu < nunits, ij, ik, iu % KM_STAGES, n1, plane_len, off,
+                   okmask, tid);
+    ++iu;
+    if (++ik == nrun) {
+      ik = 0;
+      ++ij;
+    }
+  };
 #pragma unroll
-  for (int u = 0; u < KM_STAGES - 1; ++u)
-    km_issue<T, P>(xs, job, runs, u, nunits, nrun, jbeg, n1, plane_len, off, okmask, tid);
+  for (int q = 0; q < KM_STAGES - 1; ++q) stage_next();
   int u = 0, par = 0;
   const int rp0 = ty, rp1 = ty + 8;
+  // output offsets of the thread's two points within a plane
+  const size_t yo0 = (size_t)(I2 + rp0) * n3 + I3 + c, yo1 = (size_t)(I2 + rp1) * n3 + I3 + c;
   for (int j1 = jbeg; j1 < jend; ++j1) {
+    // planes whose whole band lies inside the grid need no row checks
+    const bool inner = j1 >= P && j1 + P < n1;
     for (int k = 0; k < nrun; ++k, ++u) {
-      km_issue<T, P>(xs, job, runs, u + KM_STAGES - 1, nunits, nrun, jbeg, n1, plane_len, off,
-                     okmask, tid);
+      stage_next();
       asm volatile("cp.async.wait_group %0;\n" ::"n"(KM_STAGES - 1));
       __syncthreads();
       if (j1 >= 0 && j1 < n1) {
@@ -440,17 +450,16 @@ kron_march_kernel(const __grid_constant__ KronJob<T> job, const __grid_constant_
             }
           }
           // mode 1 scattered into the ring: i1 = j1 + q (slot q + P),
-          // A1(i1, j1) at band[i1][P - q]
-          const T* A1 = job.b[0][t];
+          // A1(i1, j1) at band[i1][P - q] = A1r[q (B - 1)]
+          const T* A1r = job.b[0][t] + (ptrdiff_t)j1 * B + P;
           T cf[NY];
 #pragma unroll
           for (int o = 0; o < NY; ++o) cf[o] = job.coef[t][o];
           const unsigned cm = job.cmask[t];
 #pragma unroll
           for (int q = -P; q <= P; ++q) {
-            const int i1 = j1 + q;
-            if ((unsigned)i1 < (unsigned)n1) {
-              const T a1 = __ldg(A1 + (size_t)i1 * B + (P - q));
+            if (inner || (unsigned)(j1 + q) < (unsigned)n1) {
+              const T a1 = __ldg(A1r + q * (B - 1));
               const T p0 = a1 * w0, p1 = a1 * w1;
 #pragma unroll
               for (int o = 0; o < NY; ++o)
@@ -471,7 +480,7 @@ kron_march_kernel(const __grid_constant__ KronJob<T> job, const __grid_constant_
       for (int p = 0; p < 2; ++p) {
         const int i2 = I2 + (p ? rp1 : rp0);
         if (i2 < n2 && i3 < n3) {
-          const size_t o2 = ((size_t)i1 * n2 + i2) * n3 + i3;
+          const size_t o2 = (size_t)i1 * plane_len + (p ? yo1 : yo0);
 #pragma unroll
           for (int o = 0; o < NY; ++o) {
             T val = acc[0][p][o];

@@ -165,3 +165,18 @@ def test_parabolic_bench_workload_rows(env, prec):
             rl = tau * (ky - mu) + my[k] - (my[k - 1] if k > 0 else 0.0)
             for e, v in enumerate((ry, ru, rl)):
                 assert abs(v) <= bound, (s, r, k, e, v, bound)
+
+
+@pytest.mark.parametrize("nt", [2, 24])
+def test_parabolic_tf32_and_longer_horizons(env, nt):
+    """IGA_TF32 (interface products on the tensor cores once they are large,
+    FP64 refinement) and horizons of 2 and 24 steps against the direct
+    solve."""
+    work = CASES[0][1]
+    tau = 1.0 / nt
+    info, y, u, lam = _solve(env, work, nt, tau, tol=1e-10, precision=2)
+    assert info["converged"], info
+    M, K, B = _oracle(work, nt, tau)
+    yo, uo, lo = kkt_solve_parabolic(M, K, tau, work.beta, B)
+    for got, ref in ((y, yo), (u, uo), (lam, lo)):
+        assert _rel(got, ref) < 1e-6
