@@ -513,7 +513,8 @@ iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const iga_op* K,
  * operators (same sizes and degrees).  load: device FP64 (nt, N), the y-row
  * right-hand side b = [b_1; ...; b_nt] (b_k = tau M yhat_k for a desired
  * state yhat), or NULL for zero.  y, u, lam: device FP64 (nt, N) each, time
- * the slow index.  opts->residual must be IGA_RESID_FULL.  IGA_EINVAL for
+ * the slow index; load must not overlap y, u or lam.  opts->residual must be
+ * IGA_RESID_FULL.  Synchronises the context stream.  IGA_EINVAL for
  * nt < 1, tau <= 0, beta <= 0 or mismatched operators; IGA_ENOCONV (best
  * iterate written) when the tolerance is not reached. */
 iga_status iga_kkt_solve_parabolic(iga_ctx* ctx, const iga_op* M, const iga_op* K, int nt,
