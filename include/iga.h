@@ -515,7 +515,7 @@ iga_status iga_kkt_solve_amen_tt(iga_ctx* ctx, const iga_op* M, const iga_op* K,
  * state yhat), or NULL for zero.  y, u, lam: device FP64 (nt, N) each, time
  * the slow index; load must not overlap y, u or lam.  opts->residual must be
  * IGA_RESID_FULL.  Synchronises the context stream.  IGA_EINVAL for
- * nt < 1, tau <= 0, beta <= 0 or mismatched operators; IGA_ENOCONV (best
+ * nt < 1, tau <= 0, beta <= 0, nt N of 2^31 or more or mismatched operators; IGA_ENOCONV (best
  * iterate written) when the tolerance is not reached. */
 iga_status iga_kkt_solve_parabolic(iga_ctx* ctx, const iga_op* M, const iga_op* K, int nt,
                                    double tau, const double* load, double beta,

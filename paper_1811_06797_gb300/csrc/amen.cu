@@ -3179,6 +3179,8 @@ extern "C" iga_status iga_kkt_solve_parabolic(iga_ctx* ctx, const iga_op* M, con
                 "kkt_solve_parabolic: only IGA_RESID_FULL is supported");
     const size_t Ns = (size_t)M->n[0] * M->n[1] * M->n[2];
     const size_t NT = (size_t)nt * Ns;
+    // the frame products index one field of the space-time vector with int
+    IGA_REQUIRE(NT < (size_t)INT32_MAX, "kkt_solve_parabolic: nt * N must be below 2^31");
     double* F = scratch<double>(ctx, SLOT_AMEN_BASE - 4, 3 * NT);
     double* z = scratch<double>(ctx, SLOT_AMEN_BASE - 3, 3 * NT);
     double* delta = scratch<double>(ctx, SLOT_AMEN_BASE - 2, 3 * NT);
