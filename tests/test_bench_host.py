@@ -102,3 +102,12 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_profiling_cases_parse(monkeypatch):
+    # the single-measurement cases of the bench: the TT apply, the random-volume
+    # solve, the timed steps alone, the parabolic solve and the FP32 applies
+    for case in ("ttm", "c5solve", "step", "parabolic", "kron32"):
+        monkeypatch.setattr("sys.argv", ["bench.py", "--only", case, "--nt", "4"])
+        a = bench.parse()
+        assert a.only == case and a.nt == 4 and a.gpus == 1
